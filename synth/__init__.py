@@ -1,0 +1,401 @@
+"""Seeded synthetic inputs for the map-making problem (shared by the oracle tests and the CUDA path).
+
+This module only *makes inputs*: scanning strategies (pixel index and polarisation angle per time
+sample), a sky, 1/f noise realisations and the banded inverse-noise first rows that the map-maker
+takes as its noise weights.  It implements none of the map-making arithmetic (no pointing
+operator, no Toeplitz product, no preconditioner, no solver).
+
+Everything is written with torch so the same recipe runs on the CPU (small parity cases, handed to
+the oracle as numpy arrays) and on a CUDA device (full-size workloads, generated directly in HBM).
+
+Recipe (stand-ins for the TOAST ground and satellite simulations of Sect. 4, which are not
+available here):
+
+* Ground raster: constant-elevation back-and-forth sweeps across a flat ``side x side`` patch at
+  ``speed`` px/sample, one row advance per sweep, detectors offset on a focal-plane grid, a
+  continuously rotating half-wave plate.  The stored angle is psi = phi_det + hwp_factor * phi_hwp so
+  that the pointing weights (1, cos 2psi, sin 2psi) carry 2 phi + 4 phi_hwp as in the HWP data
+  model of Sect. 2 (hwp_factor = 2).
+* Satellite: spin + precession of a boresight on the sphere, equal-area pixels in (z, phi).
+* Noise: stationary 1/f per (detector, interval) block with PSD sigma^2 (1 + (f_k/|f|)^alpha),
+  P(0) := 0, drawn by circulant embedding.
+* Weights: the first row of each inverse-noise Toeplitz block per Eq. MADCAP: inverse PSD on the
+  circulant embedding grid, inverse FFT, cut at the half-bandwidth lambda (lambda + 1
+  coefficients), with a positivity gate on the band's symbol.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, asdict
+from typing import Optional
+
+import torch
+
+SEED_BASE = 2112_03370_00
+
+
+def seed_for(config_id: int, stream: int) -> int:
+    """Seed of one random stream of one workload."""
+    return SEED_BASE + 1000 * config_id + stream
+
+
+# --------------------------------------------------------------------------------------------
+# workload descriptions
+# --------------------------------------------------------------------------------------------
+
+
+@dataclass
+class GroundConfig:
+    """Raster-scan workload: n_det x n_int blocks of n_samp samples each (det-major)."""
+
+    name: str = "tiny"
+    config_id: int = 0
+    n_det: int = 4
+    n_int: int = 1
+    n_samp: int = 65536
+    side: int = 128
+    speed: float = 0.25          # px per sample
+    fs: float = 100.0            # Hz
+    hwp_hz: float = 2.0
+    hwp_factor: int = 2
+    det_layout: str = "column"   # "column": offsets (0, j); "grid23": first n_det nodes of 23x23
+    det_angle_mod: int = 4       # phi_j = (j mod det_angle_mod) * 45 deg
+    cross_link: bool = False     # odd intervals sweep along y instead of x
+    sigma_lo: float = 1.0
+    sigma_hi: float = 1.0
+    f_knee: float = 0.5
+    alpha: float = 1.0
+    lam: int = 1024
+    tol: float = 1e-8
+    sigma_I: float = 1.0
+    sigma_QU: float = 0.1
+    gap_frac: float = 0.0        # fraction of samples flagged (pix = -1), in short runs
+
+    @property
+    def n_blocks(self) -> int:
+        return self.n_det * self.n_int
+
+    @property
+    def n_total(self) -> int:
+        return self.n_blocks * self.n_samp
+
+    @property
+    def n_pix(self) -> int:
+        return self.side * self.side
+
+
+def tiny_config(**kw) -> GroundConfig:
+    """4 dets x 65,536 samples at 100 Hz on a 128x128 patch, lambda = 1024, eps = 1e-8."""
+    c = GroundConfig()
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def ground_config(**kw) -> GroundConfig:
+    """512 dets x 4 intervals x 524,288 samples on a 1024x1024 patch, lambda = 8192."""
+    c = GroundConfig(name="ground", config_id=1, n_det=512, n_int=4, n_samp=524288, side=1024,
+                     speed=2.0, fs=100.0, hwp_hz=2.0, det_layout="grid23", det_angle_mod=4,
+                     cross_link=True, sigma_lo=0.8, sigma_hi=1.2, f_knee=1.0, alpha=1.5,
+                     lam=8192, tol=1e-6)
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def batched_config(**kw) -> GroundConfig:
+    """Ground geometry cut to 128 dets x 1 interval x 524,288 samples."""
+    c = ground_config(name="batched", config_id=3, n_det=128, n_int=1)
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+# --------------------------------------------------------------------------------------------
+# scanning strategies
+# --------------------------------------------------------------------------------------------
+
+
+def _det_offsets(cfg: GroundConfig):
+    j = torch.arange(cfg.n_det, dtype=torch.int64)
+    if cfg.det_layout == "column":
+        return torch.zeros_like(j), j
+    if cfg.det_layout == "grid23":
+        return (j % 23) - 11, (j // 23) - 11
+    raise ValueError(cfg.det_layout)
+
+
+def ground_pointing(cfg: GroundConfig, device="cpu", det_range: Optional[tuple] = None):
+    """Pixel index (int32, -1 = flagged) and angle psi (float32, radians in [0, 2 pi)).
+
+    Returns flat arrays over the blocks of detectors ``det_range`` (default: all), det-major,
+    each block ``n_samp`` long.
+    """
+    d0, d1 = det_range if det_range is not None else (0, cfg.n_det)
+    dev = torch.device(device)
+    n = cfg.n_samp
+    sweep = int(round(cfg.side / cfg.speed))
+    i = torch.arange(n, device=dev, dtype=torch.int64)
+    s = i // sweep
+    u = torch.floor((i % sweep).to(torch.float64) * cfg.speed).to(torch.int64)
+    xb = torch.where(s % 2 == 0, u, (cfg.side - 1) - u)
+    yb = s % cfg.side
+    dx_all, dy_all = _det_offsets(cfg)
+    pix_out, psi_out = [], []
+    two_pi = 2.0 * math.pi
+    for det in range(d0, d1):
+        dx, dy = int(dx_all[det]), int(dy_all[det])
+        phi_det = (det % cfg.det_angle_mod) * (math.pi / 4.0)
+        for k in range(cfg.n_int):
+            if cfg.cross_link and (k % 2 == 1):
+                px, py = yb, xb
+            else:
+                px, py = xb, yb
+            px = (px + dx) % cfg.side
+            py = (py + dy) % cfg.side
+            pix = (py * cfg.side + px).to(torch.int32)
+            t = (k * n + i).to(torch.float64) / cfg.fs
+            ang = phi_det + cfg.hwp_factor * (two_pi * cfg.hwp_hz * t)
+            psi = torch.remainder(ang, two_pi).to(torch.float32)
+            psi = torch.where(psi >= two_pi, torch.zeros_like(psi), psi)   # f32 rounding up to 2 pi
+            pix_out.append(pix)
+            psi_out.append(psi)
+    return torch.cat(pix_out), torch.cat(psi_out)
+
+
+def flag_gaps(pix: torch.Tensor, frac: float, seed: int, run: int = 37) -> torch.Tensor:
+    """Flag about ``frac`` of the samples as gaps (pix = -1) in runs of ``run`` samples."""
+    if frac <= 0:
+        return pix
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    n_runs = max(1, int(frac * pix.numel() / run))
+    starts = torch.randint(0, max(1, pix.numel() - run), (n_runs,), generator=g)
+    idx = (starts[:, None] + torch.arange(run)[None, :]).reshape(-1).to(pix.device)
+    out = pix.clone()
+    out[idx] = -1
+    return out
+
+
+# --------------------------------------------------------------------------------------------
+# sky, noise, weights
+# --------------------------------------------------------------------------------------------
+
+
+def sky(n_pix: int, sigma_I: float, sigma_QU: float, seed: int, device="cpu") -> torch.Tensor:
+    """I ~ N(0, sigma_I^2), Q, U ~ N(0, sigma_QU^2), i.i.d. per pixel: float64 [n_pix, 3]."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    m = torch.randn(n_pix, 3, generator=g, dtype=torch.float64)
+    m[:, 0] *= sigma_I
+    m[:, 1:] *= sigma_QU
+    return m.to(device)
+
+
+def psd(f: torch.Tensor, sigma: float, f_knee: float, alpha: float) -> torch.Tensor:
+    """sigma^2 (1 + (f_knee/|f|)^alpha), per-sample variance density; P(0) := 0 (1/f limit)."""
+    af = f.abs()
+    out = torch.zeros_like(af)
+    nz = af > 0
+    if f_knee > 0:
+        out[nz] = sigma * sigma * (1.0 + (f_knee / af[nz]) ** alpha)
+    else:
+        out[nz] = sigma * sigma
+        out[~nz] = sigma * sigma
+    return out
+
+
+def noise_block(n: int, fs: float, sigma: float, f_knee: float, alpha: float,
+                gen: torch.Generator, device="cpu") -> torch.Tensor:
+    """One stationary noise stream of length n by circulant embedding on 2^ceil(log2 2n) points."""
+    n_emb = 1 << int(math.ceil(math.log2(2 * n)))
+    w = torch.randn(n_emb, generator=gen, dtype=torch.float64, device=gen.device).to(device)
+    W = torch.fft.rfft(w)
+    f = torch.arange(W.numel(), dtype=torch.float64, device=device) * (fs / n_emb)
+    W = W * torch.sqrt(psd(f, sigma, f_knee, alpha))
+    return torch.fft.irfft(W, n=n_emb)[:n]
+
+
+def symbol_min(c: torch.Tensor) -> float:
+    """Minimum over a fine grid of s(w) = c0 + 2 sum_k c_k cos(k w) (band's Fourier symbol)."""
+    lam = c.numel() - 1
+    n_s = 1 << int(math.ceil(math.log2(16 * (lam + 1))))
+    h = torch.zeros(n_s, dtype=torch.float64)
+    h[0] = c[0]
+    if lam > 0:
+        h[1:lam + 1] = c[1:]
+        h[n_s - lam:] = torch.flip(c[1:], [0])
+    return float(torch.fft.rfft(h).real.min())
+
+
+@dataclass
+class BandInfo:
+    tapered: bool = False
+    lift: float = 0.0
+    min_symbol: float = 0.0
+
+
+def inverse_noise_band(n_block: int, lam: int, fs: float, sigma: float, f_knee: float,
+                       alpha: float, gauss_taper: bool = False):
+    """First row c[0..lam] of the approximate inverse-noise Toeplitz block (Eq. MADCAP).
+
+    The inverse PSD is sampled on the circulant-embedding grid of n_fft = 2^ceil(log2 max(n_block,
+    4(lam+1))) points (1/P(0) := 0), inverse-transformed and cut at |tau| <= lam.  If the cut band
+    has a non-positive symbol it is tapered by a Gaussian window of width lam/2 (the smoothing of
+    Sect. 3.2) and, if still needed, lifted on the diagonal so every finite block is SPD.
+    """
+    n_fft = 1 << int(math.ceil(math.log2(max(n_block, 4 * (lam + 1)))))
+    f = torch.arange(n_fft // 2 + 1, dtype=torch.float64) * (fs / n_fft)
+    p = psd(f, sigma, f_knee, alpha)
+    inv = torch.zeros_like(p)
+    nz = p > 0
+    inv[nz] = 1.0 / p[nz]
+    c = torch.fft.irfft(inv.to(torch.complex128), n=n_fft)[: lam + 1].clone()
+    info = BandInfo()
+    if gauss_taper and lam > 0:
+        tau = torch.arange(lam + 1, dtype=torch.float64)
+        c = c * torch.exp(-0.5 * (tau / (lam / 2.0)) ** 2)
+        info.tapered = True
+    smin = symbol_min(c)
+    if smin <= 0 and not info.tapered and lam > 0:
+        tau = torch.arange(lam + 1, dtype=torch.float64)
+        c = c * torch.exp(-0.5 * (tau / (lam / 2.0)) ** 2)
+        info.tapered = True
+        smin = symbol_min(c)
+    if smin <= 0:
+        lift = abs(smin) * (1.0 + 1e-3) + 1e-12 * float(c[0])
+        c[0] += lift
+        info.lift = lift
+        smin = symbol_min(c)
+    info.min_symbol = smin
+    return c, info
+
+
+# --------------------------------------------------------------------------------------------
+# assembled problems
+# --------------------------------------------------------------------------------------------
+
+
+@dataclass
+class Problem:
+    """One map-making problem: all arrays are torch tensors on one device."""
+
+    n_det: int
+    n_int: int
+    block_len: torch.Tensor      # int64 [n_blocks] (host)
+    n_pix: int
+    pix: torch.Tensor            # int32 [N], -1 = gap
+    psi: torch.Tensor            # float32 [N]
+    lam: int
+    band: torch.Tensor           # float64 [n_blocks, lam + 1]
+    d: Optional[torch.Tensor]    # float64 [N] (or None)
+    m_sky: Optional[torch.Tensor]
+    tol: float
+    band_info: BandInfo = field(default_factory=BandInfo)
+    sigmas: Optional[torch.Tensor] = None
+
+    @property
+    def n_total(self) -> int:
+        return int(self.pix.numel())
+
+
+def make_ground_problem(cfg: GroundConfig, device="cpu", with_noise: bool = True,
+                        with_signal: bool = True, det_range: Optional[tuple] = None,
+                        n_real: int = 1, real_offset: int = 0) -> Problem:
+    """Build one ground-raster problem (pointing, bands, sky, data) for ``cfg``.
+
+    ``det_range`` restricts to a contiguous subset of detectors (same per-detector recipe and
+    seeds as the full problem).  ``n_real`` > 1 returns d as [n_real, N] noise realisations
+    (realisation r uses noise stream 100 + r + real_offset).
+    """
+    d0, d1 = det_range if det_range is not None else (0, cfg.n_det)
+    dev = torch.device(device)
+    pix, psi = ground_pointing(cfg, device=dev, det_range=(d0, d1))
+    if cfg.gap_frac > 0:
+        pix = flag_gaps(pix.cpu(), cfg.gap_frac, seed_for(cfg.config_id, 7)).to(dev)
+    n_det = d1 - d0
+    gs = torch.Generator(device="cpu").manual_seed(seed_for(cfg.config_id, 2))
+    sig_all = cfg.sigma_lo + (cfg.sigma_hi - cfg.sigma_lo) * torch.rand(
+        cfg.n_det, generator=gs, dtype=torch.float64)
+    sig = sig_all[d0:d1]
+    shape, info = inverse_noise_band(cfg.n_samp, cfg.lam, cfg.fs, 1.0, cfg.f_knee, cfg.alpha)
+    band = torch.empty(n_det * cfg.n_int, cfg.lam + 1, dtype=torch.float64)
+    for j in range(n_det):
+        band[j * cfg.n_int:(j + 1) * cfg.n_int] = shape / (sig[j] ** 2)
+    block_len = torch.full((n_det * cfg.n_int,), cfg.n_samp, dtype=torch.int64)
+    m = sky(cfg.n_pix, cfg.sigma_I, cfg.sigma_QU, seed_for(cfg.config_id, 1), device=dev)
+    d = None
+    if with_noise or with_signal:
+        reals = []
+        for r in range(n_real):
+            dd = torch.zeros(pix.numel(), dtype=torch.float64, device=dev)
+            if with_signal:
+                ok = pix >= 0
+                pl = pix.clamp(min=0).long()
+                two = 2.0 * psi.to(torch.float64)
+                sig_t = m[pl, 0] + torch.cos(two) * m[pl, 1] + torch.sin(two) * m[pl, 2]
+                dd += torch.where(ok, sig_t, torch.zeros_like(sig_t))
+            if with_noise:
+                stream = 100 + r + real_offset
+                gn = torch.Generator(device=dev).manual_seed(seed_for(cfg.config_id, stream)
+                                                              + 7919 * d0)
+                for j in range(n_det):
+                    for k in range(cfg.n_int):
+                        b = j * cfg.n_int + k
+                        lo = b * cfg.n_samp
+                        dd[lo:lo + cfg.n_samp] += noise_block(cfg.n_samp, cfg.fs, float(sig[j]),
+                                                              cfg.f_knee, cfg.alpha, gn, dev)
+            reals.append(dd)
+        d = reals[0] if n_real == 1 else torch.stack(reals)
+    return Problem(n_det=n_det, n_int=cfg.n_int, block_len=block_len, n_pix=cfg.n_pix, pix=pix,
+                   psi=psi, lam=cfg.lam, band=band, d=d, m_sky=m, tol=cfg.tol, band_info=info,
+                   sigmas=sig)
+
+
+def random_problem(n_blocks: int, block_len, n_pix: int, lam: int, seed: int,
+                   gap_frac: float = 0.0, f_knee: float = 0.5, alpha: float = 1.0,
+                   hits_per_pix_min: int = 0, device="cpu") -> Problem:
+    """Small unstructured problem: random pixels and angles, arbitrary (ragged) block lengths.
+
+    Used for edge cases (ragged blocks, blocks shorter than lambda, gaps, lambda = 0).  Angles are
+    uniform, so every pixel with a few hits is well conditioned.
+    """
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    if isinstance(block_len, int):
+        block_len = [block_len] * n_blocks
+    bl = torch.tensor(block_len, dtype=torch.int64)
+    n = int(bl.sum())
+    pix = torch.randint(0, n_pix, (n,), generator=g, dtype=torch.int64)
+    if hits_per_pix_min > 0:
+        base = torch.arange(n_pix).repeat_interleave(hits_per_pix_min)
+        k = min(base.numel(), n)
+        perm = torch.randperm(n, generator=g)[:k]
+        pix[perm] = base[:k]
+    pix = pix.to(torch.int32)
+    psi = (torch.rand(n, generator=g, dtype=torch.float64) * 2 * math.pi).to(torch.float32)
+    if gap_frac > 0:
+        gm = torch.rand(n, generator=g) < gap_frac
+        pix[gm] = -1
+    band = torch.empty(n_blocks, lam + 1, dtype=torch.float64)
+    for b in range(n_blocks):
+        sig = 0.8 + 0.4 * float(torch.rand(1, generator=g))
+        shape, _ = inverse_noise_band(max(int(bl[b]), 1), lam, 100.0, 1.0, f_knee, alpha)
+        band[b] = shape / sig ** 2
+    m = sky(n_pix, 1.0, 0.1, seed + 1)
+    two = 2.0 * psi.to(torch.float64)
+    pl = pix.clamp(min=0).long()
+    d = torch.where(pix >= 0, m[pl, 0] + torch.cos(two) * m[pl, 1] + torch.sin(two) * m[pl, 2],
+                    torch.zeros(n, dtype=torch.float64))
+    d = d + 0.1 * torch.randn(n, generator=g, dtype=torch.float64)
+    return Problem(n_det=n_blocks, n_int=1, block_len=bl, n_pix=n_pix, pix=pix.to(device),
+                   psi=psi.to(device), lam=lam, band=band, d=d.to(device), m_sky=m, tol=1e-8)
+
+
+def to_numpy(prob: Problem) -> dict:
+    """The problem as plain numpy arrays (what the oracle consumes)."""
+    out = dict(n_det=prob.n_det, n_int=prob.n_int, n_pix=prob.n_pix, lam=prob.lam, tol=prob.tol,
+               block_len=prob.block_len.cpu().numpy(), pix=prob.pix.cpu().numpy(),
+               psi=prob.psi.cpu().numpy(), band=prob.band.cpu().numpy())
+    if prob.d is not None:
+        out["d"] = prob.d.cpu().numpy()
+    if prob.m_sky is not None:
+        out["m_sky"] = prob.m_sky.cpu().numpy()
+    return out

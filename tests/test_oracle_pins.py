@@ -1,0 +1,294 @@
+"""Pins of the FP64 oracle to facts the paper and the mathematics fix (no GPU).
+
+Each test is chosen so that a plausible slip in the oracle (a dropped term, a wrong sign, a wrong
+factor in the angle, a transposed operand, wrap-around in the Toeplitz product) fails it.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+
+def tiny_problem(seed=0, n_blocks=3, block_len=(300, 170, 41), n_pix=40, lam=12, gap=0.05,
+                 hits_min=6):
+    p = synth.random_problem(n_blocks, list(block_len), n_pix, lam, seed, gap_frac=gap,
+                             hits_per_pix_min=hits_min)
+    return synth.to_numpy(p)
+
+
+def plan_of(pb, **kw):
+    return O.make_plan(pb["pix"], pb["psi"], pb["block_len"], pb["band"], pb["n_pix"], **kw)
+
+
+# ---------------------------------------------------------------- pointing (Sect. 2 HWP model)
+
+def test_weights_closed_form():
+    psi = np.array([0.0, math.pi / 8, math.pi / 4, math.pi / 2, 3 * math.pi / 4], np.float32)
+    w = O.pointing_weights(psi)
+    h = math.sqrt(0.5)
+    want = np.array([[1, 1, 0], [1, h, h], [1, 0, 1], [1, -1, 0], [1, 0, -1]], float)
+    np.testing.assert_allclose(w, want, atol=2e-7)   # float32 angle rounding only
+
+
+def test_unpoint_intensity_only_is_one():
+    pb = tiny_problem()
+    pl = plan_of(pb)
+    m = np.zeros((pl.n_obs, 3))
+    m[:, 0] = 1.0
+    t = O.unpoint(pl, m)
+    np.testing.assert_array_equal(t, np.where(pl.lpix >= 0, 1.0, 0.0))
+
+
+def test_point_is_adjoint_of_unpoint():
+    pb = tiny_problem(seed=3)
+    pl = plan_of(pb)
+    rng = np.random.default_rng(1)
+    m = rng.standard_normal((pl.n_obs, 3))
+    t = rng.standard_normal(pl.lpix.size)
+    lhs = np.dot(O.unpoint(pl, m), t)
+    rhs = np.vdot(m, O.point(pl, t))
+    assert abs(lhs - rhs) <= 1e-13 * (abs(lhs) + np.linalg.norm(m) * np.linalg.norm(t))
+
+
+def test_point_of_ones_gives_hits():
+    pb = tiny_problem(seed=4)
+    pl = plan_of(pb)
+    out = O.point(pl, np.ones(pl.lpix.size))
+    cnt = np.bincount(pl.lpix[pl.lpix >= 0], minlength=pl.n_obs)
+    np.testing.assert_array_equal(out[:, 0], cnt)
+
+
+# ---------------------------------------------------------------- Toeplitz (Eq. MADCAP, stbmm)
+
+@pytest.mark.parametrize("lam", [0, 1, 5, 40, 400])
+def test_toeplitz_direct_equals_dense(lam):
+    rng = np.random.default_rng(lam)
+    bl = np.array([37, 1, 200, 64])
+    band = rng.standard_normal((bl.size, lam + 1))
+    t = rng.standard_normal(bl.sum())
+    y = O.toeplitz_direct(band, bl, t)
+    off = O.block_offsets(bl)
+    for b in range(bl.size):
+        T = O.toeplitz_dense(band[b], bl[b])
+        np.testing.assert_allclose(y[off[b]:off[b + 1]], T @ t[off[b]:off[b + 1]],
+                                   rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("lam", [0, 3, 64, 300])
+def test_toeplitz_fft_equals_direct(lam):
+    rng = np.random.default_rng(10 + lam)
+    bl = np.array([1000, 5, 129, 2048])
+    band = rng.standard_normal((bl.size, lam + 1))
+    t = rng.standard_normal(bl.sum())
+    y1 = O.toeplitz_direct(band, bl, t)
+    y2 = O.toeplitz_fft(band, bl, t)
+    assert np.max(np.abs(y1 - y2)) <= 1e-12 * np.max(np.abs(y1))
+
+
+def test_toeplitz_no_wrap_no_cross_block():
+    lam = 7
+    bl = np.array([50, 50])
+    band = np.tile(np.arange(1.0, lam + 2.0), (2, 1))
+    t = np.zeros(100)
+    t[50] = 1.0                      # first sample of block 1
+    y = O.toeplitz_fft(band, bl, t)
+    assert np.all(y[:50] == 0)       # nothing leaks into block 0
+    np.testing.assert_allclose(y[50:50 + lam + 1], band[1], atol=1e-13)
+    assert np.all(np.abs(y[50 + lam + 1:]) < 1e-13)   # and nothing wraps to the block's end
+
+
+def test_toeplitz_white_band_is_scaled_identity():
+    sig = 1.3
+    c, _ = synth.inverse_noise_band(4096, 16, 100.0, sig, 0.0, 1.0)
+    assert abs(float(c[0]) - 1 / sig ** 2) < 1e-14
+    assert np.max(np.abs(c[1:].numpy())) < 1e-14
+    t = np.random.default_rng(0).standard_normal(300)
+    y = O.toeplitz_fft(c.numpy()[None, :], [300], t)
+    np.testing.assert_allclose(y, t / sig ** 2, atol=1e-13)
+
+
+# ---------------------------------------------------------------- BD block and excision (Sect. 2.4)
+
+@pytest.mark.parametrize("n", [3, 4, 7, 16])
+def test_bd_uniform_angles_cond_two(n):
+    psi = (np.arange(n) * math.pi / n).astype(np.float32)   # 2psi uniform on [0, 2pi)
+    c0 = 2.5
+    band = np.array([[c0, 0.3, 0.1]])
+    B, hits = O.bd_blocks(np.zeros(n, np.int32), psi, [n], band, 1)
+    np.testing.assert_allclose(B[0], c0 * np.diag([n, n / 2, n / 2]), atol=1e-5)
+    keep, cond = O.excise(B, hits)
+    assert keep[0] and abs(cond[0] - 2.0) < 1e-5
+
+
+def test_excision_rules():
+    # pixel 0: 2 hits (excised); pixel 1: all samples at the same angle (singular, excised);
+    # pixel 2: well sampled (kept)
+    pix = np.array([0, 0, 1, 1, 1, 1, 2, 2, 2, 2], np.int32)
+    psi = np.array([0, 1, .3, .3, .3, .3, 0, .4, .8, 1.2], np.float32)
+    band = np.array([[1.0, 0.0]])
+    B, hits = O.bd_blocks(pix, psi, [10], band, 3)
+    keep, cond = O.excise(B, hits, 1e3)
+    assert list(keep) == [False, False, True]
+    pl = O.make_plan(pix, psi, [10], band, 3)
+    assert pl.n_obs == 1 and list(pl.lpix) == [-1] * 6 + [0] * 4
+
+
+def test_excision_cond_threshold_tie_kept():
+    pix = np.zeros(4, np.int32)
+    psi = (np.arange(4) * math.pi / 4).astype(np.float32)
+    band = np.array([[1.0]])
+    B, hits = O.bd_blocks(pix, psi, [4], band, 1)
+    _, cond = O.excise(B, hits)
+    keep, _ = O.excise(B, hits, cond_max=float(cond[0]))
+    assert keep[0]
+    keep, _ = O.excise(B, hits, cond_max=float(cond[0]) * (1 - 1e-9))
+    assert not keep[0]
+
+
+# ---------------------------------------------------------------- A = P^T N^-1 P (Sect. 3.2)
+
+def test_apply_A_equals_dense_and_is_spd():
+    pb = tiny_problem(seed=5)
+    pl = plan_of(pb)
+    A = O.dense_A(pl)
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((pl.n_obs, 3))
+    np.testing.assert_allclose(O.apply_A(pl, x).reshape(-1), A @ x.reshape(-1),
+                               rtol=0, atol=1e-11 * np.max(np.abs(A)) * np.abs(x).sum() / x.size
+                               * 10)
+    np.testing.assert_allclose(A, A.T, atol=1e-12 * np.max(np.abs(A)))
+    assert np.linalg.eigvalsh(A).min() > 0
+
+
+def test_apply_A_direct_and_fft_agree():
+    pb = tiny_problem(seed=6, lam=60)
+    p1 = plan_of(pb, toeplitz="direct")
+    p2 = plan_of(pb, toeplitz="fft")
+    x = np.random.default_rng(3).standard_normal((p1.n_obs, 3))
+    y1, y2 = O.apply_A(p1, x), O.apply_A(p2, x)
+    assert np.max(np.abs(y1 - y2)) <= 1e-12 * np.max(np.abs(y1))
+
+
+def test_rhs_masks_gap_samples_of_d():
+    pb = tiny_problem(seed=7)
+    pl = plan_of(pb)
+    d = pb["d"].copy()
+    b1 = O.rhs(pl, d)
+    d[pl.lpix < 0] = 1e6          # garbage at flagged/excised samples must not leak through N^-1
+    b2 = O.rhs(pl, d)
+    np.testing.assert_array_equal(b1, b2)
+
+
+# ---------------------------------------------------------------- Algorithm 1 and special cases
+
+def test_pcg_matches_dense_cholesky():
+    pb = tiny_problem(seed=8)
+    pl = plan_of(pb)
+    b = O.rhs(pl, pb["d"])
+    ms = O.dense_solve(pl, b)
+    res = O.pcg(pl, b, tol=1e-12, max_iter=2000)
+    assert res.converged
+    assert np.linalg.norm(res.x - ms) <= 1e-9 * np.linalg.norm(ms)
+
+
+def test_noiseless_recovers_sky():
+    pb = tiny_problem(seed=9, lam=20)
+    pl = plan_of(pb)
+    m_true = np.random.default_rng(4).standard_normal((pl.n_obs, 3))
+    d = O.unpoint(pl, m_true)
+    res = O.pcg(pl, O.rhs(pl, d), tol=1e-13, max_iter=5000)
+    assert np.linalg.norm(res.x - m_true) <= 1e-9 * np.linalg.norm(m_true)
+
+
+def test_lambda_zero_one_iteration_binned_map():
+    pb = tiny_problem(seed=10, lam=0)
+    pl = plan_of(pb)
+    b = O.rhs(pl, pb["d"])
+    res = O.pcg(pl, b, tol=1e-10, max_iter=10)
+    assert res.iters == 1
+    np.testing.assert_allclose(res.x, O.binned_map(pl, pb["d"]), rtol=1e-10, atol=1e-12)
+
+
+def test_pcg_history_monotone_in_A_norm_error():
+    pb = tiny_problem(seed=11)
+    pl = plan_of(pb)
+    A = O.dense_A(pl)
+    b = O.rhs(pl, pb["d"])
+    ms = O.dense_solve(pl, b).reshape(-1)
+    res = O.pcg(pl, b, tol=1e-10, max_iter=500, keep_iterates=True)
+    errs = [float((x.reshape(-1) - ms) @ A @ (x.reshape(-1) - ms)) for x in res.iterates]
+    assert all(e2 <= e1 * (1 + 1e-8) + 1e-24 for e1, e2 in zip(errs, errs[1:]))
+
+
+# ---------------------------------------------------------------- Algorithm 2 (block, Orthomin)
+
+def test_block_cg_s1_equals_pcg():
+    pb = tiny_problem(seed=12)
+    pl = plan_of(pb)
+    b = O.rhs(pl, pb["d"])
+    ref = O.pcg(pl, b, tol=1e-9, max_iter=500)
+    blk = O.block_cg(pl, b[None], tol=1e-9, max_iter=500)
+    assert blk.iters == ref.iters
+    assert np.linalg.norm(blk.X[0] - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+
+
+def test_block_cg_multi_rhs_columns_match_pcg():
+    pb = tiny_problem(seed=13)
+    pl = plan_of(pb)
+    rng = np.random.default_rng(5)
+    Bm = np.stack([O.rhs(pl, pb["d"] + rng.standard_normal(pb["d"].size)) for _ in range(4)])
+    blk = O.block_cg(pl, Bm, tol=1e-10, max_iter=500)
+    A = O.dense_A(pl)
+    for j in range(4):
+        xs = np.linalg.solve(A, Bm[j].reshape(-1))
+        assert blk.converged[j]
+        assert np.linalg.norm(blk.X[j].reshape(-1) - xs) <= 1e-7 * np.linalg.norm(xs)
+    ref_iters = max(O.pcg(pl, Bm[j], tol=1e-10).iters for j in range(4))
+    assert blk.iters <= ref_iters
+
+
+# ---------------------------------------------------------------- Algorithm 3 and A-DEF1
+
+def test_lanczos_relation():
+    pb = tiny_problem(seed=14)
+    pl = plan_of(pb)
+    b = O.rhs(pl, pb["d"]).reshape(-1)
+    m = 8
+    T, V, AV, beta, vnext = O.lanczos(pl, b, m)
+    A = O.dense_A(pl)
+    np.testing.assert_allclose(AV, A @ V, atol=1e-10 * np.abs(A).max())
+    em = np.zeros(m)
+    em[-1] = 1
+    resid = A @ V - V @ T - beta * np.outer(vnext, em)
+    assert np.abs(resid).max() <= 1e-9 * np.abs(A).max()
+    assert np.abs(V.T @ V - np.eye(m)).max() < 1e-6
+    np.testing.assert_allclose(V[:, 0], b / np.linalg.norm(b), atol=1e-15)
+
+
+def test_two_level_deflation_identities():
+    pb = tiny_problem(seed=15)
+    pl = plan_of(pb)
+    b = O.rhs(pl, pb["d"])
+    tl = O.two_level_from_lanczos(pl, b, 6)
+    A = O.dense_A(pl)
+    Z = tl.Z
+    Q = Z @ tl.Einv @ Z.T
+    lhs = (np.eye(A.shape[0]) - A @ Q) @ A @ Z            # (I - AQ) A Z = 0
+    assert np.abs(lhs).max() <= 1e-8 * np.abs(A @ Z).max()
+    for j in range(Z.shape[1]):                            # M_2lvl A Z = Z
+        out = O.precond_2lvl(pl, tl, (A @ Z[:, j]).reshape(-1, 3)).reshape(-1)
+        np.testing.assert_allclose(out, Z[:, j], atol=1e-8 * np.abs(Z[:, j]).max())
+
+
+def test_two_level_never_more_iterations_than_bd():
+    pb = tiny_problem(seed=16, n_pix=60, lam=30)
+    pl = plan_of(pb)
+    b = O.rhs(pl, pb["d"])
+    bd = O.pcg(pl, b, tol=1e-8)
+    tl = O.two_level_from_lanczos(pl, b, 8)
+    two = O.pcg(pl, b, tol=1e-8, precond=lambda r: O.precond_2lvl(pl, tl, r))
+    assert two.converged and two.iters <= bd.iters
+    assert np.linalg.norm(two.x - bd.x) <= 1e-5 * np.linalg.norm(bd.x)
