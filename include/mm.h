@@ -1,0 +1,172 @@
+/*
+ * mm.h — C ABI of libmm, a single-GPU (GB300, sm_103a) maximum-likelihood CMB map-maker.
+ *
+ * The library solves (P^T N^-1 P) m = P^T N^-1 d by preconditioned conjugate gradients
+ * (El Bouhargani et al., "MAPPRAISER", Sect. 2 and 3):
+ *   P      pointing matrix, one row per time sample with the three weights (1, cos 2psi, sin 2psi)
+ *          at the sample's sky pixel (Sect. 2, data model with a half-wave plate);
+ *   N^-1   block-diagonal inverse-noise weights, one symmetric banded Toeplitz block per
+ *          (detector, stationary interval) with half-bandwidth lambda (Eq. MADCAP);
+ *   M_BD   block-Jacobi preconditioner (P^T diag(N^-1) P)^-1, one 3x3 block per pixel (Sect. 3.2);
+ *   PCG    Algorithm 1 with x_0 = 0 and the stop rule ||r_k|| < eps ||b|| (Sect. 3.2).
+ *
+ * Conventions shared by every entry point
+ *   - Status: every call returns an mm_status value and never throws across the ABI.  On error,
+ *     mm_last_error() returns a message for the calling thread.
+ *   - Ownership: mm_plan copies every input it is given (host or device memory) into plan-owned
+ *     device memory and keeps no caller pointer after it returns.  Output buffers belong to the
+ *     caller.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  All
+ *     calls except mm_plan / mm_plan_destroy / mm_pcg_solve are asynchronous on that stream.
+ *   - Map vectors passed to mm_apply_A / mm_precond / mm_pcg_solve / mm_rhs are float64 device
+ *     arrays in the plan's compacted pixel order, laid out [nrhs][n_obs][3] (I, Q, U per pixel).
+ *     Time-domain vectors (mm_apply_P / mm_apply_Pt / mm_apply_Ninv) are float64 [N] device arrays
+ *     in the sample order of the plan (blocks det-major, contiguous).
+ *   - A plan is not thread-safe: calls on one plan must be serialised by the caller.
+ */
+#ifndef MM_H
+#define MM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mm_plan_s* mm_plan_t;
+
+typedef enum {
+  MM_OK = 0,
+  MM_EINVAL = 1,      /* invalid argument (sizes, pointers, pixel ids, non-finite band, ...) */
+  MM_ENOMEM = 2,      /* device allocation failed */
+  MM_ENOTSPD = 3,     /* a band's Fourier symbol is not positive, or no pixel survives excision */
+  MM_EBREAKDOWN = 4,  /* <p, A p> <= 0 or not finite inside CG */
+  MM_ENOTCONV = 5,    /* max_iter reached; the partial solution is returned */
+  MM_ETIMEOUT = 6,    /* host-side deadline passed; the partial solution is returned */
+  MM_EBUSY = 7,
+  MM_ECUDA = 8        /* a CUDA runtime call failed */
+} mm_status;
+
+/* Arithmetic of the bulk operators P, N^-1, P^T. */
+enum { MM_FP64 = 0, MM_FP32 = 1 };
+/* Algorithm of the block-Toeplitz product. */
+enum { MM_TPLZ_AUTO = 0, MM_TPLZ_FFT = 1, MM_TPLZ_DIRECT = 3 };
+/* Preconditioner. */
+enum { MM_PREC_BD = 0 };
+
+/*
+ * Problem description (the map-making problem statement of Sect. 2 and 3).
+ *   n_det, n_int   blocks are det-major: block b = det * n_int + interval, stored contiguously.
+ *   block_len      HOST array [n_det * n_int] of samples per block (each >= 0); N = their sum.
+ *   n_pix          number of global sky pixels; pix values must lie in [-1, n_pix).
+ *   pix            [N] int32 global pixel per sample, -1 = flagged sample (a gap).
+ *   psi            [N] float32 polarisation angle (radians); weights are (1, cos 2psi, sin 2psi).
+ *   lambda         half-bandwidth: each block's first row has lambda + 1 coefficients c_0..c_lambda
+ *                  (Eq. MADCAP keeps |t - t'| <= lambda).  0 <= lambda <= 12288.
+ *   band           [n_det * n_int][lambda + 1] float64 first rows; every block's symbol
+ *                  c_0 + 2 sum_k c_k cos(k w) must be positive (checked: MM_ENOTSPD).
+ *   cond_max       pixels with fewer than 3 hits or cond_2 of their 3x3 block above cond_max are
+ *                  excised together with their samples (Sect. 2.4); <= 0 selects 1e3.
+ *   precision      MM_FP64 or MM_FP32: arithmetic of mm_apply_A.
+ *   toeplitz_algo  MM_TPLZ_AUTO/MM_TPLZ_FFT (shared-memory overlap-save FFT) or MM_TPLZ_DIRECT
+ *                  (band sum by the definition, O(lambda) per sample; for checks and tiny lambda).
+ *   inputs_on_device  non-zero: pix, psi and band are device pointers; zero: host pointers.
+ */
+typedef struct {
+  int32_t n_det;
+  int32_t n_int;
+  const int64_t* block_len;
+  int64_t n_pix;
+  const int32_t* pix;
+  const float* psi;
+  int32_t lambda;
+  const double* band;
+  double cond_max;
+  int32_t precision;
+  int32_t toeplitz_algo;
+  int32_t inputs_on_device;
+} mm_problem_desc;
+
+/*
+ * PCG options.
+ *   tol            eps of the stop rule ||r|| < eps ||b|| (recursive residual of Algorithm 1).
+ *   max_iter       cap on iterations (MM_ENOTCONV when reached).
+ *   precond        MM_PREC_BD.
+ *   precision      MM_FP64: plain FP64 PCG.  MM_FP32: P, N^-1, P^T in FP32 with FP64 vectors,
+ *                  dot products, alpha/beta and 3x3 blocks, and reliable updates: the recursive
+ *                  residual is replaced by the FP64 true residual b - A x every `reliable_every`
+ *                  iterations and before the solve is declared converged.
+ *   reliable_every FP32 path only; <= 0 selects 50.
+ *   check_every    iterations launched between host reads of the convergence flag (<= 0: 8).
+ *   deadline_us    host-side wall-clock limit in microseconds (<= 0: none) -> MM_ETIMEOUT.
+ */
+typedef struct {
+  double tol;
+  int32_t max_iter;
+  int32_t precond;
+  int32_t precision;
+  int32_t reliable_every;
+  int32_t check_every;
+  int64_t deadline_us;
+} mm_solve_opts;
+
+/* Per right-hand side outcome of a solve. */
+typedef struct {
+  int32_t status;        /* mm_status of this right-hand side */
+  int32_t iters;         /* PCG iterations (A-applications inside the loop) */
+  double rel_res;        /* final recursive ||r|| / ||b|| */
+  double true_rel_res;   /* ||b - A x|| / ||b|| from an FP64 A-application after the solve */
+  double t_ms;           /* wall time of the solve */
+  int32_t n_true_res;    /* FP64 true-residual evaluations (FP32 path) */
+  int32_t pad_;
+} mm_solve_info;
+
+/* Build a plan: validate, copy inputs, compact observed pixels, build and invert the 3x3 BD
+ * blocks, excise ill-conditioned pixels, precompute the Toeplitz spectra.  Synchronous.
+ * Sect. 3.1 (local pixel indexation, Toeplitz blocks), Sect. 2.4 and 3.2 (BD, excision). */
+int mm_plan(const mm_problem_desc* desc, void* stream, mm_plan_t* out);
+
+/* Sizes of a plan: n_obs kept pixels (map vectors hold 3 * n_obs values per right-hand side),
+ * a device pointer to the [n_obs] compacted -> global pixel map (owned by the plan), the
+ * number of samples and the plan's device footprint in bytes.  Any output may be NULL. */
+int mm_plan_query(mm_plan_t plan, int64_t* n_obs, const int32_t** obs_to_global_dev,
+                  int64_t* n_samples, size_t* bytes);
+
+/* Release a plan and all its device memory.  NULL is a no-op. */
+void mm_plan_destroy(mm_plan_t plan);
+
+/* t = P~ x (un-pointing, Sect. 3.1): x [n_obs][3] -> t [N]; t = 0 at flagged/excised samples. */
+int mm_apply_P(mm_plan_t plan, const double* x, double* t, void* stream);
+
+/* y = P~^T t (pointing, Sect. 3.1): t [N] -> y [n_obs][3]; flagged/excised samples ignored. */
+int mm_apply_Pt(mm_plan_t plan, const double* t, double* y, void* stream);
+
+/* y = blockdiag_b T(c_b) t (stbmm, Sect. 3.1; Eq. MADCAP): t [N] -> y [N], FP64, no masking,
+ * no wrap-around and no coupling across blocks. */
+int mm_apply_Ninv(mm_plan_t plan, const double* t, double* y, void* stream);
+
+/* b = P~^T N^-1 G d for nrhs data vectors: d [nrhs][N] device, float64 (d_is_fp32 = 0) or
+ * float32 (d_is_fp32 = 1); b [nrhs][n_obs][3].  G zeroes flagged and excised samples of d. */
+int mm_rhs(mm_plan_t plan, const void* d, int d_is_fp32, int nrhs, double* b, void* stream);
+
+/* y = A x = P~^T N^-1 P~ x (Sect. 3.2, right to left) for nrhs vectors, in the plan's precision. */
+int mm_apply_A(mm_plan_t plan, const double* x, double* y, int nrhs, void* stream);
+
+/* z = M_BD r (block-Jacobi, Sect. 3.2) for nrhs vectors. */
+int mm_precond(mm_plan_t plan, const double* r, double* z, int nrhs, void* stream);
+
+/* Solve A x = b for nrhs independent right-hand sides by PCG (Algorithm 1), x_0 = 0.
+ * b, x: [nrhs][n_obs][3] device.  info: HOST array [nrhs].  Blocks the calling thread until the
+ * solve ends.  Returns the worst per-column status. */
+int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_solve_opts* opts,
+                 mm_solve_info* info, void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* mm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MM_H */

@@ -1,0 +1,251 @@
+// In-shared-memory complex FFT used by the overlap-save Toeplitz tiles.
+//
+// Layout: MS complex values per CTA in shared memory with one padding element per 16
+// (physical index i + i/16), which makes the strided radix-16 passes and the final
+// short-stride pass free of bank conflicts for 8-byte (FP32) elements.
+//
+// Forward transform: decimation in frequency, radix-16 passes then one radix-2^REM pass;
+// natural-order input, digit-reversed output.  Inverse: the same passes in reverse order
+// (decimation in time), digit-reversed input, natural-order output, unnormalised.  Forward and
+// inverse are used back to back with a pointwise step in between, so no reordering pass is run.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mm {
+
+template <typename T> struct V2;
+template <> struct V2<float> { using t = float2; };
+template <> struct V2<double> { using t = double2; };
+
+template <typename C> __device__ __forceinline__ C c_add(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C c_sub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C c_mul(C a, C b) {
+  return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C c_mulc(C a, C b) {
+  return C{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+
+__host__ __device__ __forceinline__ constexpr int smem_pad(int i) { return i + (i >> 4); }
+
+// cos(2 pi e / 16), sin(2 pi e / 16)
+__device__ __forceinline__ constexpr double cos16(int e) {
+  switch (e & 15) {
+    case 0: return 1.0;
+    case 1: return 0.92387953251128675613;
+    case 2: return 0.70710678118654752440;
+    case 3: return 0.38268343236508977173;
+    case 4: return 0.0;
+    case 5: return -0.38268343236508977173;
+    case 6: return -0.70710678118654752440;
+    case 7: return -0.92387953251128675613;
+    case 8: return -1.0;
+    case 9: return -0.92387953251128675613;
+    case 10: return -0.70710678118654752440;
+    case 11: return -0.38268343236508977173;
+    case 12: return 0.0;
+    case 13: return 0.38268343236508977173;
+    case 14: return 0.70710678118654752440;
+    default: return 0.92387953251128675613;
+  }
+}
+__device__ __forceinline__ constexpr double sin16(int e) { return cos16(e - 4); }
+
+// a * w16^e with w16 = exp(-2 pi i / 16) (FWD) or exp(+2 pi i / 16) (inverse).  After full
+// unrolling e is a constant, so the axis cases cost nothing.
+template <bool FWD, typename C>
+__device__ __forceinline__ C rot16(C a, int e) {
+  e &= 15;
+  if (e == 0) return a;
+  if (e == 8) return C{-a.x, -a.y};
+  if (e == 4) return FWD ? C{a.y, -a.x} : C{-a.y, a.x};
+  if (e == 12) return FWD ? C{-a.y, a.x} : C{a.y, -a.x};
+  using T = decltype(a.x);
+  const T c = (T)cos16(e);
+  const T s = FWD ? (T)(-sin16(e)) : (T)sin16(e);
+  return C{a.x * c - a.y * s, a.x * s + a.y * c};
+}
+
+template <bool FWD, typename C>
+__device__ __forceinline__ void dft2(C& a0, C& a1) {
+  C t = a0;
+  a0 = c_add(t, a1);
+  a1 = c_sub(t, a1);
+}
+
+template <bool FWD, typename C>
+__device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+  C s02 = c_add(a0, a2), d02 = c_sub(a0, a2), s13 = c_add(a1, a3), d13 = c_sub(a1, a3);
+  C jd = FWD ? C{d13.y, -d13.x} : C{-d13.y, d13.x};   // (-i or +i) * d13
+  a0 = c_add(s02, s13);
+  a2 = c_sub(s02, s13);
+  a1 = c_add(d02, jd);
+  a3 = c_sub(d02, jd);
+}
+
+// R-point DFT of a[0..R) into natural order (y_k = sum_m a_m w_R^{km}).
+template <int R, bool FWD, typename C>
+__device__ __forceinline__ void dft_small(C (&a)[R]) {
+  if constexpr (R == 2) {
+    dft2<FWD>(a[0], a[1]);
+  } else if constexpr (R == 4) {
+    dft4<FWD>(a[0], a[1], a[2], a[3]);
+  } else if constexpr (R == 8) {
+    // m = 2 m1 + m0, k = k0 + 4 k1
+#pragma unroll
+    for (int m0 = 0; m0 < 2; m0++) dft4<FWD>(a[m0], a[2 + m0], a[4 + m0], a[6 + m0]);
+    // u[m0][k0] at a[2 k0 + m0]; twiddle w8^{m0 k0} = w16^{2 m0 k0}
+#pragma unroll
+    for (int k0 = 0; k0 < 4; k0++) a[2 * k0 + 1] = rot16<FWD>(a[2 * k0 + 1], 2 * k0);
+    C b[8];
+#pragma unroll
+    for (int k0 = 0; k0 < 4; k0++) {
+      C u0 = a[2 * k0], u1 = a[2 * k0 + 1];
+      dft2<FWD>(u0, u1);
+      b[k0] = u0;
+      b[k0 + 4] = u1;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; i++) a[i] = b[i];
+  } else {
+    static_assert(R == 16, "radix");
+    // m = 4 m1 + m0, k = k0 + 4 k1
+#pragma unroll
+    for (int m0 = 0; m0 < 4; m0++) dft4<FWD>(a[m0], a[4 + m0], a[8 + m0], a[12 + m0]);
+    // u[m0][k0] now at a[4 k0 + m0]
+#pragma unroll
+    for (int k0 = 1; k0 < 4; k0++)
+#pragma unroll
+      for (int m0 = 1; m0 < 4; m0++) a[4 * k0 + m0] = rot16<FWD>(a[4 * k0 + m0], m0 * k0);
+    C b[16];
+#pragma unroll
+    for (int k0 = 0; k0 < 4; k0++) {
+      C u0 = a[4 * k0], u1 = a[4 * k0 + 1], u2 = a[4 * k0 + 2], u3 = a[4 * k0 + 3];
+      dft4<FWD>(u0, u1, u2, u3);
+      b[k0] = u0;
+      b[k0 + 4] = u1;
+      b[k0 + 8] = u2;
+      b[k0 + 12] = u3;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; i++) a[i] = b[i];
+  }
+}
+
+// Twiddles w_j = W_C^{n1 j}, j = 1..R-1, from the table tw[k] = W_M^k (M = full tile size):
+// W_C^{n1 j} = tw[n1 j (M / C)].  Powers 1, 2, 4, 8 are read; the rest are products of at most
+// two reads.
+template <int R, typename C>
+__device__ __forceinline__ void twiddles(const C* __restrict__ tw, int base_idx, C (&w)[R]) {
+  w[1] = __ldg(tw + base_idx);
+  if constexpr (R > 2) {
+    w[2] = __ldg(tw + 2 * base_idx);
+    w[3] = c_mul(w[1], w[2]);
+  }
+  if constexpr (R > 4) {
+    w[4] = __ldg(tw + 4 * base_idx);
+    w[5] = c_mul(w[4], w[1]);
+    w[6] = c_mul(w[4], w[2]);
+    w[7] = c_mul(w[4], w[3]);
+  }
+  if constexpr (R > 8) {
+    w[8] = __ldg(tw + 8 * base_idx);
+#pragma unroll
+    for (int j = 1; j < 8; j++) w[8 + j] = c_mul(w[8], w[j]);
+  }
+}
+
+// One decimation-in-frequency (FWD) or decimation-in-time (inverse) pass over sub-transforms of
+// size Cs with radix R.  `ms` = transform size held by this CTA, `mfull_over_cs` = M / Cs.
+template <int R, bool FWD, int NT, typename C>
+__device__ __forceinline__ void fft_pass(C* __restrict__ sm, const C* __restrict__ tw, int ms,
+                                         int cs, int mfull_over_cs) {
+  const int s = cs / R;
+  const int nbf = ms / R;
+  for (int q = threadIdx.x; q < nbf; q += NT) {
+    const int chunk = q / s;
+    const int n1 = q - chunk * s;
+    const int base = chunk * cs + n1;
+    C a[R];
+#pragma unroll
+    for (int m = 0; m < R; m++) a[m] = sm[smem_pad(base + m * s)];
+    if (FWD) {
+      dft_small<R, true>(a);
+      if (s > 1 && n1 != 0) {
+        C w[R];
+        twiddles<R>(tw, n1 * mfull_over_cs, w);
+#pragma unroll
+        for (int j = 1; j < R; j++) a[j] = c_mul(a[j], w[j]);
+      }
+    } else {
+      if (s > 1 && n1 != 0) {
+        C w[R];
+        twiddles<R>(tw, n1 * mfull_over_cs, w);
+#pragma unroll
+        for (int j = 1; j < R; j++) a[j] = c_mulc(a[j], w[j]);
+      }
+      dft_small<R, false>(a);
+    }
+#pragma unroll
+    for (int m = 0; m < R; m++) sm[smem_pad(base + m * s)] = a[m];
+  }
+}
+
+// Transform of MS = 2^LOGMS points held by one CTA.  MFULL = size of the twiddle table's
+// transform (the whole tile, MFULL >= MS).
+template <int LOGMS, int MFULL, int NT>
+struct SmemFFT {
+  static constexpr int MS = 1 << LOGMS;
+  static constexpr int NP16 = LOGMS / 4;
+  static constexpr int REM = LOGMS % 4;
+
+  template <typename C>
+  __device__ static void forward(C* sm, const C* tw) {
+#pragma unroll 1
+    for (int p = 0; p < NP16; p++) {
+      const int cs = MS >> (4 * p);
+      fft_pass<16, true, NT>(sm, tw, MS, cs, MFULL / cs);
+      __syncthreads();
+    }
+    if constexpr (REM > 0) {
+      fft_pass<(1 << REM), true, NT>(sm, tw, MS, 1 << REM, MFULL >> REM);
+      __syncthreads();
+    }
+  }
+
+  template <typename C>
+  __device__ static void inverse(C* sm, const C* tw) {
+    if constexpr (REM > 0) {
+      fft_pass<(1 << REM), false, NT>(sm, tw, MS, 1 << REM, MFULL >> REM);
+      __syncthreads();
+    }
+#pragma unroll 1
+    for (int p = NP16 - 1; p >= 0; p--) {
+      const int cs = MS >> (4 * p);
+      fft_pass<16, false, NT>(sm, tw, MS, cs, MFULL / cs);
+      __syncthreads();
+    }
+  }
+
+  // Position in shared memory (before padding) of frequency k after `forward`.
+  __host__ __device__ static int storage_of(int k) {
+    int j = 0;
+#pragma unroll
+    for (int i = 0; i < NP16; i++) j |= ((k >> (4 * i)) & 15) << (REM + 4 * (NP16 - 1 - i));
+    if (REM > 0) j |= (k >> (4 * NP16)) & ((1 << REM) - 1);
+    return j;
+  }
+  // Frequency held at position j after `forward`.
+  __host__ __device__ static int freq_of(int j) {
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < NP16; i++) k |= ((j >> (REM + 4 * (NP16 - 1 - i))) & 15) << (4 * i);
+    if (REM > 0) k |= (j & ((1 << REM) - 1)) << (4 * NP16);
+    return k;
+  }
+};
+
+}  // namespace mm

@@ -1,0 +1,268 @@
+// Plan-time kernels: input validation, block-Jacobi blocks, pixel excision and compaction.
+//
+// Block-Jacobi preconditioner (Sect. 3.2): B_p = sum_{t: p_t = p} c_0,b(t) w_t w_t^T with
+// w_t = (1, cos 2psi_t, sin 2psi_t); the diagonal of N^-1 on sample t is its block's c_0.
+// Excision (Sect. 2.4): a pixel with fewer than 3 hits or cond_2(B_p) > cond_max is dropped with
+// all its samples.  Local pixel ids are assigned in ascending global order over kept pixels
+// (Sect. 3.1 local indexation).
+#include "mm_internal.cuh"
+
+namespace mm {
+
+__global__ void k_validate(const int32_t* __restrict__ pix, const float* __restrict__ psi, int64_t N,
+                           int64_t n_pix, int32_t* bad) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p = pix[i];
+    const float a = psi[i];
+    if (p < -1 || (int64_t)p >= n_pix) atomicOr(bad, 1);
+    if (!isfinite(a)) atomicOr(bad, 2);
+  }
+}
+
+cudaError_t launch_validate(const int32_t* pix, const float* psi, int64_t N, int64_t n_pix,
+                            int32_t* bad, cudaStream_t s) {
+  if (N == 0) return cudaSuccess;
+  k_validate<<<4 * 152, 256, 0, s>>>(pix, psi, N, n_pix, bad);
+  return cudaGetLastError();
+}
+
+// Block index of sample i (block_off has n_blocks + 1 entries).
+__device__ __forceinline__ int block_of(const int64_t* __restrict__ off, int32_t n_blocks, int64_t i) {
+  int lo = 0, hi = n_blocks;   // find the last b with off[b] <= i
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(off + mid) <= i) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_bd_accum(const int32_t* __restrict__ pix, const float* __restrict__ psi,
+                           const int64_t* __restrict__ off, const double* __restrict__ c0_blk,
+                           int32_t n_blocks, int64_t N, double* __restrict__ B6,
+                           int32_t* __restrict__ hits) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p = pix[i];
+    if (p < 0) continue;
+    const double c0 = c0_blk[block_of(off, n_blocks, i)];
+    double s, c;
+    sincos(2.0 * (double)psi[i], &s, &c);
+    double* b = B6 + 6 * (int64_t)p;
+    atomicAdd(b + 0, c0);
+    atomicAdd(b + 1, c0 * c);
+    atomicAdd(b + 2, c0 * s);
+    atomicAdd(b + 3, c0 * c * c);
+    atomicAdd(b + 4, c0 * c * s);
+    atomicAdd(b + 5, c0 * s * s);
+    atomicAdd(hits + p, 1);
+  }
+}
+
+cudaError_t launch_bd_accum(const int32_t* pix, const float* psi, const int64_t* block_off,
+                            const double* c0_blk, int32_t n_blocks, int64_t N, double* B6,
+                            int32_t* hits, cudaStream_t s) {
+  if (N == 0) return cudaSuccess;
+  k_bd_accum<<<8 * 152, 256, 0, s>>>(pix, psi, block_off, c0_blk, n_blocks, N, B6, hits);
+  return cudaGetLastError();
+}
+
+// Eigenvalues of a symmetric 3x3 matrix (closed form, trigonometric solution of the
+// characteristic cubic; Smith, Comm. ACM 4, 1961).  Returns lo <= hi.
+__device__ void sym3_eig_range(const double a[6], double& lo, double& hi) {
+  const double a00 = a[0], a01 = a[1], a02 = a[2], a11 = a[3], a12 = a[4], a22 = a[5];
+  const double p1 = a01 * a01 + a02 * a02 + a12 * a12;
+  const double q = (a00 + a11 + a22) / 3.0;
+  if (p1 == 0.0) {
+    lo = fmin(a00, fmin(a11, a22));
+    hi = fmax(a00, fmax(a11, a22));
+    return;
+  }
+  const double b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
+  const double p2 = b00 * b00 + b11 * b11 + b22 * b22 + 2.0 * p1;
+  const double p = sqrt(p2 / 6.0);
+  const double ip = 1.0 / p;
+  const double c00 = b00 * ip, c11 = b11 * ip, c22 = b22 * ip;
+  const double c01 = a01 * ip, c02 = a02 * ip, c12 = a12 * ip;
+  const double det = c00 * (c11 * c22 - c12 * c12) - c01 * (c01 * c22 - c12 * c02) +
+                     c02 * (c01 * c12 - c11 * c02);
+  double r = 0.5 * det;
+  r = fmin(1.0, fmax(-1.0, r));
+  const double phi = acos(r) / 3.0;
+  const double two_pi_3 = 2.0943951023931954923;
+  const double e1 = q + 2.0 * p * cos(phi);
+  const double e3 = q + 2.0 * p * cos(phi + two_pi_3);
+  const double e2 = 3.0 * q - e1 - e3;
+  hi = fmax(e1, fmax(e2, e3));
+  lo = fmin(e1, fmin(e2, e3));
+}
+
+__global__ void k_bd_finalize(const double* __restrict__ B6, const int32_t* __restrict__ hits,
+                              int64_t n_pix, double cond_max, int32_t* __restrict__ keep,
+                              double* __restrict__ inv6) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_pix) return;
+  double a[6];
+#pragma unroll
+  for (int i = 0; i < 6; i++) a[i] = B6[6 * p + i];
+  int ok = hits[p] >= 3;
+  if (ok) {
+    double lo, hi;
+    sym3_eig_range(a, lo, hi);
+    ok = (lo > 0.0) && (hi <= cond_max * lo);
+  }
+  keep[p] = ok;
+  if (!ok) return;
+  // inverse of the symmetric block by cofactors
+  const double a00 = a[0], a01 = a[1], a02 = a[2], a11 = a[3], a12 = a[4], a22 = a[5];
+  const double c00 = a11 * a22 - a12 * a12;
+  const double c01 = a02 * a12 - a01 * a22;
+  const double c02 = a01 * a12 - a02 * a11;
+  const double c11 = a00 * a22 - a02 * a02;
+  const double c12 = a01 * a02 - a00 * a12;
+  const double c22 = a00 * a11 - a01 * a01;
+  const double det = a00 * c00 + a01 * c01 + a02 * c02;
+  const double id = 1.0 / det;
+  double* o = inv6 + 6 * p;
+  o[0] = c00 * id; o[1] = c01 * id; o[2] = c02 * id;
+  o[3] = c11 * id; o[4] = c12 * id; o[5] = c22 * id;
+}
+
+cudaError_t launch_bd_finalize(const double* B6, const int32_t* hits, int64_t n_pix, double cond_max,
+                               int32_t* keep, double* inv6, cudaStream_t s) {
+  if (n_pix == 0) return cudaSuccess;
+  k_bd_finalize<<<(unsigned)((n_pix + 255) / 256), 256, 0, s>>>(B6, hits, n_pix, cond_max, keep, inv6);
+  return cudaGetLastError();
+}
+
+// ---- exclusive scan of the keep flags (three passes: tile sums, scan of sums, tile scans) ----
+constexpr int kScanTile = 1024;   // elements per CTA (256 threads x 4)
+
+__global__ void k_scan_tile_sums(const int32_t* __restrict__ in, int64_t n, int32_t* __restrict__ sums) {
+  __shared__ int32_t red[256];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int32_t v = 0;
+  for (int i = threadIdx.x; i < kScanTile; i += 256) {
+    const int64_t g = base + i;
+    if (g < n) v += in[g] != 0;
+  }
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sums[blockIdx.x] = red[0];
+}
+
+// single CTA: exclusive scan of the tile sums in place; total written to *total
+__global__ void k_scan_sums(int32_t* sums, int64_t n_tiles, int32_t* total) {
+  __shared__ int32_t buf[1024];
+  int32_t carry = 0;
+  for (int64_t base = 0; base < n_tiles; base += 1024) {
+    const int64_t g = base + threadIdx.x;
+    const int32_t v = g < n_tiles ? sums[g] : 0;
+    buf[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+      const int32_t t = threadIdx.x >= off ? buf[threadIdx.x - off] : 0;
+      __syncthreads();
+      buf[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (g < n_tiles) sums[g] = carry + buf[threadIdx.x] - v;
+    const int32_t tile_total = buf[1023];
+    __syncthreads();
+    carry += tile_total;
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan_tiles(const int32_t* __restrict__ in, int64_t n, const int32_t* __restrict__ sums,
+                             int32_t* __restrict__ out) {
+  __shared__ int32_t buf[kScanTile];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  for (int i = threadIdx.x; i < kScanTile; i += 256) {
+    const int64_t g = base + i;
+    buf[i] = (g < n && in[g] != 0) ? 1 : 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {   // 1024 adds: negligible next to the rest of the plan
+    int32_t acc = sums[blockIdx.x];
+    for (int i = 0; i < kScanTile; i++) {
+      const int32_t v = buf[i];
+      buf[i] = acc;
+      acc += v;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kScanTile; i += 256) {
+    const int64_t g = base + i;
+    if (g < n) out[g] = buf[i];
+  }
+}
+
+size_t scan_scratch_len(int64_t n) { return (size_t)((n + kScanTile - 1) / kScanTile) + 1; }
+
+cudaError_t launch_scan_keep(const int32_t* keep, int64_t n, int32_t* lid, int32_t* total,
+                             int32_t* scratch, int64_t scratch_len, cudaStream_t s) {
+  const int64_t nt = (n + kScanTile - 1) / kScanTile;
+  if (nt + 1 > scratch_len) return cudaErrorInvalidValue;
+  if (n == 0) return cudaMemsetAsync(total, 0, sizeof(int32_t), s);
+  k_scan_tile_sums<<<(unsigned)nt, 256, 0, s>>>(keep, n, scratch);
+  k_scan_sums<<<1, 1024, 0, s>>>(scratch, nt, total);
+  k_scan_tiles<<<(unsigned)nt, 256, 0, s>>>(keep, n, scratch, lid);
+  return cudaGetLastError();
+}
+
+__global__ void k_compact(const int32_t* __restrict__ keep, const int32_t* __restrict__ lid,
+                          const double* __restrict__ inv6_glob, int64_t n_pix,
+                          int32_t* __restrict__ obs_to_global, double* __restrict__ minv) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_pix || !keep[p]) return;
+  const int32_t l = lid[p];
+  obs_to_global[l] = (int32_t)p;
+#pragma unroll
+  for (int i = 0; i < 6; i++) minv[6 * (int64_t)l + i] = inv6_glob[6 * p + i];
+}
+
+cudaError_t launch_compact(const int32_t* keep, const int32_t* lid, const double* inv6_glob,
+                           int64_t n_pix, int32_t* obs_to_global, double* minv, cudaStream_t s) {
+  if (n_pix == 0) return cudaSuccess;
+  k_compact<<<(unsigned)((n_pix + 255) / 256), 256, 0, s>>>(keep, lid, inv6_glob, n_pix,
+                                                             obs_to_global, minv);
+  return cudaGetLastError();
+}
+
+__global__ void k_localize(const int32_t* __restrict__ pix, const int32_t* __restrict__ keep,
+                           const int32_t* __restrict__ lid, int64_t N, int32_t* __restrict__ lpix) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p = pix[i];
+    lpix[i] = (p >= 0 && keep[p]) ? lid[p] : -1;
+  }
+}
+
+cudaError_t launch_localize(const int32_t* pix, const int32_t* keep, const int32_t* lid, int64_t N,
+                            int32_t* lpix, cudaStream_t s) {
+  if (N == 0) return cudaSuccess;
+  k_localize<<<8 * 152, 256, 0, s>>>(pix, keep, lid, N, lpix);
+  return cudaGetLastError();
+}
+
+__global__ void k_weights64(const float* __restrict__ psi, int64_t N, double2* __restrict__ w) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s, c;
+    sincos(2.0 * (double)psi[i], &s, &c);
+    w[i] = make_double2(c, s);
+  }
+}
+
+cudaError_t launch_weights64(const float* psi, int64_t N, double2* w64, cudaStream_t s) {
+  if (N == 0) return cudaSuccess;
+  k_weights64<<<8 * 152, 256, 0, s>>>(psi, N, w64);
+  return cudaGetLastError();
+}
+
+}  // namespace mm

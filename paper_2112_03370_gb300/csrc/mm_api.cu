@@ -1,0 +1,761 @@
+// C ABI of libmm: plan construction, the operators of the map-making system and the PCG driver.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "mm_cg.cuh"
+#include "mm_internal.cuh"
+
+namespace mm {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return MM_ECUDA;
+}
+
+namespace {
+
+// Solver workspace, grown on demand and kept with the plan.
+struct CgState {
+  int64_t n = 0;
+  int nrhs_cap = 0;
+  double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  float *p32 = nullptr, *q32 = nullptr;
+  double* partials = nullptr;
+  unsigned* counters = nullptr;
+  CgScalars* scal = nullptr;
+  CgScalars* scal_host = nullptr;   // pinned
+  // cached graph of `chunk` iterations
+  cudaGraphExec_t exec = nullptr;
+  int g_nrhs = -1, g_fp32 = -1, g_chunk = -1, g_maxit = -1;
+  double g_tol2 = -1.0;
+};
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+int grow(Plan* P, double** buf, size_t* cap, size_t n) {
+  if (*cap >= n && *buf) return MM_OK;
+  dfree(*buf);
+  *cap = 0;
+  int st = dalloc(P, buf, n);
+  if (st == MM_OK) *cap = n;
+  return st;
+}
+int grow32(Plan* P, float** buf, size_t* cap, size_t n) {
+  if (*cap >= n && *buf) return MM_OK;
+  dfree(*buf);
+  *cap = 0;
+  int st = dalloc(P, buf, n);
+  if (st == MM_OK) *cap = n;
+  return st;
+}
+
+void free_cg(CgState* c) {
+  if (!c) return;
+  dfree(c->b); dfree(c->x); dfree(c->r); dfree(c->z); dfree(c->p); dfree(c->q);
+  dfree(c->p32); dfree(c->q32); dfree(c->partials); dfree(c->counters); dfree(c->scal);
+  if (c->scal_host) cudaFreeHost(c->scal_host);
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  delete c;
+}
+
+void free_plan(Plan* P) {
+  if (!P) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(P->device);
+  if (P->stream) cudaStreamSynchronize(P->stream);
+  dfree(P->lpix); dfree(P->psi); dfree(P->w64); dfree(P->obs_to_global); dfree(P->minv);
+  dfree(P->band); dfree(P->block_off_dev); dfree(P->c0_blk); dfree(P->tab32); dfree(P->tab64);
+  dfree(P->tw32); dfree(P->tw64); dfree(P->tiles); dfree(P->map32_in); dfree(P->map32_out);
+  dfree(P->map64_in); dfree(P->map64_out); dfree(P->td_a); dfree(P->td_b);
+  free_cg(reinterpret_cast<CgState*>(P->cg));
+  if (P->stream) cudaStreamDestroy(P->stream);
+  cudaSetDevice(cur);
+  delete P;
+}
+
+struct DeviceGuard {
+  int prev = 0;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() { cudaSetDevice(prev); }
+};
+
+// ---- band de-duplication: blocks whose rows are scalar multiples share one spectrum table ----
+struct BandTables {
+  std::vector<int32_t> blk_tab;     // [n_blocks]
+  std::vector<double> blk_scale;    // [n_blocks]
+  std::vector<int32_t> tab_src;     // block whose row defines the table
+};
+
+uint64_t row_key(const double* c, int lam) {
+  uint64_t h = 1469598103934665603ull;
+  const int idx[3] = {std::min(1, lam), lam / 2, lam};
+  for (int k = 0; k < 3; k++) {
+    const double v = c[idx[k]] / c[0];
+    const long long q = (long long)std::llround(v * 1e9);
+    h ^= (uint64_t)q;
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+bool rows_match(const double* a, const double* b, int lam) {
+  const double a0 = a[0], b0 = b[0];
+  double amax = 0.0;
+  for (int k = 0; k <= lam; k++) amax = std::max(amax, std::fabs(b[k] / b0));
+  for (int k = 0; k <= lam; k++) {
+    if (std::fabs(a[k] / a0 - b[k] / b0) > 1e-14 * amax) return false;
+  }
+  return true;
+}
+
+BandTables dedupe_bands(const std::vector<double>& band, int nb, int lam) {
+  BandTables t;
+  t.blk_tab.resize(nb);
+  t.blk_scale.resize(nb);
+  std::unordered_map<uint64_t, std::vector<int32_t>> buckets;
+  for (int b = 0; b < nb; b++) {
+    const double* row = band.data() + (size_t)b * (lam + 1);
+    const uint64_t key = row_key(row, lam);
+    int found = -1;
+    auto it = buckets.find(key);
+    if (it != buckets.end()) {
+      for (int32_t tab : it->second) {
+        const double* ref = band.data() + (size_t)t.tab_src[tab] * (lam + 1);
+        if (rows_match(row, ref, lam)) {
+          found = tab;
+          break;
+        }
+      }
+    }
+    if (found < 0) {
+      found = (int)t.tab_src.size();
+      t.tab_src.push_back(b);
+      buckets[key].push_back(found);
+    }
+    t.blk_tab[b] = found;
+    t.blk_scale[b] = row[0] / band[(size_t)t.tab_src[found] * (lam + 1)];
+  }
+  return t;
+}
+
+// Overlap-save tiles of every block: consecutive output ranges of V' = L - 2 lambda - 4 samples;
+// each tile's input window starts at a multiple of 4 at most lambda + 3 samples before its output.
+std::vector<TileDesc> make_tiles(const std::vector<int64_t>& off, const BandTables& bt, int lam) {
+  std::vector<TileDesc> tiles;
+  const int64_t vstep = (int64_t)kL - 2 * (int64_t)lam - 4;
+  const int nb = (int)off.size() - 1;
+  for (int b = 0; b < nb; b++) {
+    const int64_t lo = off[b], hi = off[b + 1];
+    for (int64_t o = lo; o < hi; o += vstep) {
+      TileDesc td{};
+      const int64_t start = o - lam;
+      td.in0 = (start >= 0) ? (start & ~(int64_t)3) : -((-start + 3) & ~(int64_t)3);
+      td.out_lo = o;
+      td.out_hi = std::min(o + vstep, hi);
+      td.blk_lo = lo;
+      td.blk_hi = hi;
+      td.tab = bt.blk_tab[b];
+      td.scale = bt.blk_scale[b];
+      tiles.push_back(td);
+    }
+  }
+  return tiles;
+}
+
+int validate_desc(const mm_problem_desc* d) {
+  if (!d) return fail(MM_EINVAL, "desc is NULL");
+  if (d->n_det <= 0 || d->n_int <= 0) return fail(MM_EINVAL, "n_det and n_int must be >= 1");
+  if (!d->block_len) return fail(MM_EINVAL, "block_len is NULL");
+  if (d->n_pix <= 0 || d->n_pix >= (int64_t)0x7fffffff) return fail(MM_EINVAL, "n_pix out of range");
+  if (d->lambda < 0 || d->lambda > kMaxLambda)
+    return fail(MM_EINVAL, "lambda must lie in [0, " + std::to_string(kMaxLambda) + "]");
+  if (!d->pix || !d->psi || !d->band) return fail(MM_EINVAL, "pix, psi and band must be non-NULL");
+  if (d->precision != MM_FP64 && d->precision != MM_FP32) return fail(MM_EINVAL, "bad precision");
+  if (d->toeplitz_algo != MM_TPLZ_AUTO && d->toeplitz_algo != MM_TPLZ_FFT &&
+      d->toeplitz_algo != MM_TPLZ_DIRECT)
+    return fail(MM_EINVAL, "bad toeplitz_algo");
+  return MM_OK;
+}
+
+#define MM_TRY(expr)              \
+  do {                            \
+    int st_ = (expr);             \
+    if (st_ != MM_OK) return st_; \
+  } while (0)
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Plan-time scratch: freed when the plan build returns, on every path.
+struct Scratch {
+  std::vector<void*> ptrs;
+  ~Scratch() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <typename T>
+  int alloc(T** p, size_t n) {
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e != cudaSuccess) {
+      *p = nullptr;
+      return fail(MM_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    ptrs.push_back((void*)*p);
+    return MM_OK;
+  }
+};
+
+int build_plan(const mm_problem_desc* d, cudaStream_t us, Plan* P) {
+  MM_CUDA(cudaGetDevice(&P->device));
+  MM_TRY(tile_kernels_init());
+  P->n_det = d->n_det;
+  P->n_int = d->n_int;
+  P->n_blocks = d->n_det * d->n_int;
+  P->n_pix = d->n_pix;
+  P->lambda = d->lambda;
+  P->precision = d->precision;
+  P->algo = (d->toeplitz_algo == MM_TPLZ_DIRECT) ? MM_TPLZ_DIRECT : MM_TPLZ_FFT;
+  P->cond_max = d->cond_max > 0 ? d->cond_max : 1e3;
+  const int nb = P->n_blocks, lam = P->lambda;
+  P->block_off.assign(nb + 1, 0);
+  for (int b = 0; b < nb; b++) {
+    if (d->block_len[b] < 0) return fail(MM_EINVAL, "negative block length");
+    P->block_off[b + 1] = P->block_off[b] + d->block_len[b];
+  }
+  P->N = P->block_off[nb];
+  if (P->N <= 0) return fail(MM_EINVAL, "no samples");
+  MM_CUDA(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
+  cudaStream_t s = P->stream;
+  // order after the caller's stream (inputs may be produced there)
+  cudaEvent_t ev;
+  MM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  MM_CUDA(cudaEventRecord(ev, us));
+  MM_CUDA(cudaStreamWaitEvent(s, ev, 0));
+  cudaEventDestroy(ev);
+
+  const cudaMemcpyKind kind = d->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  // band rows on the host for checks and de-duplication
+  std::vector<double> band((size_t)nb * (lam + 1));
+  if (d->inputs_on_device) {
+    MM_CUDA(cudaMemcpyAsync(band.data(), d->band, band.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MM_CUDA(cudaStreamSynchronize(s));
+  } else {
+    std::memcpy(band.data(), d->band, band.size() * sizeof(double));
+  }
+  std::vector<double> c0(nb);
+  for (int b = 0; b < nb; b++) {
+    for (int k = 0; k <= lam; k++)
+      if (!std::isfinite(band[(size_t)b * (lam + 1) + k])) return fail(MM_EINVAL, "non-finite band");
+    c0[b] = band[(size_t)b * (lam + 1)];
+    if (!(c0[b] > 0.0)) return fail(MM_ENOTSPD, "band c_0 must be positive (block " + std::to_string(b) + ")");
+  }
+
+  Scratch scr;
+  // inputs
+  int32_t* pix = nullptr;
+  MM_TRY(scr.alloc(&pix, P->N));
+  MM_TRY(dalloc(P, &P->psi, P->N));
+  MM_CUDA(cudaMemcpyAsync(pix, d->pix, P->N * sizeof(int32_t), kind, s));
+  MM_CUDA(cudaMemcpyAsync(P->psi, d->psi, P->N * sizeof(float), kind, s));
+  MM_TRY(dalloc(P, &P->block_off_dev, nb + 1));
+  MM_TRY(dalloc(P, &P->c0_blk, nb));
+  MM_TRY(dalloc(P, &P->band, (size_t)nb * (lam + 1)));
+  MM_CUDA(cudaMemcpyAsync(P->block_off_dev, P->block_off.data(), (nb + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  MM_CUDA(cudaMemcpyAsync(P->c0_blk, c0.data(), nb * sizeof(double), cudaMemcpyHostToDevice, s));
+  MM_CUDA(cudaMemcpyAsync(P->band, band.data(), band.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+
+  // validation
+  int32_t* flag = nullptr;
+  MM_TRY(scr.alloc(&flag, 4));
+  MM_CUDA(cudaMemsetAsync(flag, 0, 4 * sizeof(int32_t), s));
+  MM_CUDA(launch_validate(pix, P->psi, P->N, P->n_pix, flag, s));
+  int32_t hflag[4] = {0, 0, 0, 0};
+  MM_CUDA(cudaMemcpyAsync(hflag, flag, sizeof(hflag), cudaMemcpyDeviceToHost, s));
+  MM_CUDA(cudaStreamSynchronize(s));
+  if (hflag[0] & 1) return fail(MM_EINVAL, "pix values must lie in [-1, n_pix)");
+  if (hflag[0] & 2) return fail(MM_EINVAL, "psi has non-finite values");
+
+  // block-Jacobi blocks, excision, compaction
+  double* B6 = nullptr;
+  double* inv6 = nullptr;
+  int32_t *hits = nullptr, *keep = nullptr, *lid = nullptr, *scan_scratch = nullptr;
+  const size_t sl = scan_scratch_len(P->n_pix);
+  MM_TRY(scr.alloc(&B6, 6 * P->n_pix));
+  MM_TRY(scr.alloc(&inv6, 6 * P->n_pix));
+  MM_TRY(scr.alloc(&hits, P->n_pix));
+  MM_TRY(scr.alloc(&keep, P->n_pix));
+  MM_TRY(scr.alloc(&lid, P->n_pix));
+  MM_TRY(scr.alloc(&scan_scratch, sl));
+  MM_CUDA(cudaMemsetAsync(B6, 0, 6 * P->n_pix * sizeof(double), s));
+  MM_CUDA(cudaMemsetAsync(hits, 0, P->n_pix * sizeof(int32_t), s));
+  MM_CUDA(launch_bd_accum(pix, P->psi, P->block_off_dev, P->c0_blk, nb, P->N, B6, hits, s));
+  MM_CUDA(launch_bd_finalize(B6, hits, P->n_pix, P->cond_max, keep, inv6, s));
+  MM_CUDA(launch_scan_keep(keep, P->n_pix, lid, flag + 1, scan_scratch, (int64_t)sl, s));
+  MM_CUDA(cudaMemcpyAsync(hflag, flag, sizeof(hflag), cudaMemcpyDeviceToHost, s));
+  MM_CUDA(cudaStreamSynchronize(s));
+  P->n_obs = hflag[1];
+  if (P->n_obs == 0) return fail(MM_ENOTSPD, "no pixel survives excision");
+  MM_TRY(dalloc(P, &P->obs_to_global, P->n_obs));
+  MM_TRY(dalloc(P, &P->minv, 6 * P->n_obs));
+  MM_TRY(dalloc(P, &P->lpix, P->N));
+  MM_CUDA(launch_compact(keep, lid, inv6, P->n_pix, P->obs_to_global, P->minv, s));
+  MM_CUDA(launch_localize(pix, keep, lid, P->N, P->lpix, s));
+  MM_TRY(dalloc(P, &P->w64, P->N));
+  MM_CUDA(launch_weights64(P->psi, P->N, P->w64, s));
+
+  // Toeplitz spectra: L-point circulant spectrum of each distinct band, then the pair tables
+  BandTables bt = dedupe_bands(band, nb, lam);
+  P->n_tab = (int32_t)bt.tab_src.size();
+  std::vector<double> rows((size_t)P->n_tab * (lam + 1));
+  for (int t = 0; t < P->n_tab; t++)
+    std::memcpy(rows.data() + (size_t)t * (lam + 1), band.data() + (size_t)bt.tab_src[t] * (lam + 1),
+                (lam + 1) * sizeof(double));
+  std::vector<double> costab(kL);
+  for (int i = 0; i < kL; i++) costab[i] = std::cos(2.0 * M_PI * (double)i / (double)kL);
+  double *rows_d = nullptr, *costab_d = nullptr, *H = nullptr;
+  MM_TRY(scr.alloc(&rows_d, rows.size()));
+  MM_TRY(scr.alloc(&costab_d, kL));
+  MM_TRY(scr.alloc(&H, (size_t)P->n_tab * (kM + 1)));
+  MM_TRY(dalloc(P, &P->tab32, (size_t)P->n_tab * kM));
+  MM_TRY(dalloc(P, &P->tab64, (size_t)P->n_tab * kM));
+  MM_TRY(dalloc(P, &P->tw32, kM));
+  MM_TRY(dalloc(P, &P->tw64, kM));
+  MM_CUDA(cudaMemcpyAsync(rows_d, rows.data(), rows.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  MM_CUDA(cudaMemcpyAsync(costab_d, costab.data(), kL * sizeof(double), cudaMemcpyHostToDevice, s));
+  MM_CUDA(launch_spectra(rows_d, P->n_tab, lam, H, costab_d, s));
+  MM_CUDA(launch_pair_tables(H, P->n_tab, costab_d, P->tab64, P->tab32, s));
+  MM_CUDA(launch_twiddles(P->tw64, P->tw32, costab_d, s));
+  std::vector<double> Hh((size_t)P->n_tab * (kM + 1));
+  MM_CUDA(cudaMemcpyAsync(Hh.data(), H, Hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+
+  std::vector<TileDesc> tiles = make_tiles(P->block_off, bt, lam);
+  P->n_tiles = (int64_t)tiles.size();
+  MM_TRY(dalloc(P, &P->tiles, tiles.size()));
+  MM_CUDA(cudaMemcpyAsync(P->tiles, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, s));
+  MM_CUDA(cudaStreamSynchronize(s));
+
+  // the band's symbol sampled on the tile's circulant must be positive (A is then SPD)
+  for (int t = 0; t < P->n_tab; t++) {
+    double mn = Hh[(size_t)t * (kM + 1)];
+    for (int j = 0; j <= kM; j++) mn = std::min(mn, Hh[(size_t)t * (kM + 1) + j]);
+    if (!(mn > 0.0))
+      return fail(MM_ENOTSPD, "a band's Fourier symbol is not positive (min " + std::to_string(mn) + ")");
+  }
+  MM_CUDA(cudaGetLastError());
+  return MM_OK;
+}
+
+// internal map buffers [nrhs][n_obs][4]
+int ensure_maps(Plan* P, int nrhs, bool need32) {
+  const size_t n4 = (size_t)nrhs * P->n_obs * 4;
+  MM_TRY(grow(P, &P->map64_in, &P->map64_in_cap, n4));
+  MM_TRY(grow(P, &P->map64_out, &P->map64_out_cap, n4));
+  if (need32) {
+    MM_TRY(grow32(P, &P->map32_in, &P->map32_in_cap, n4));
+    MM_TRY(grow32(P, &P->map32_out, &P->map32_out_cap, n4));
+  }
+  return MM_OK;
+}
+
+int ensure_td(Plan* P) {
+  if (P->td_cap >= (size_t)P->N && P->td_a && P->td_b) return MM_OK;
+  dfree(P->td_a);
+  dfree(P->td_b);
+  P->td_cap = 0;
+  MM_TRY(dalloc(P, &P->td_a, P->N));
+  MM_TRY(dalloc(P, &P->td_b, P->N));
+  P->td_cap = P->N;
+  return MM_OK;
+}
+
+TileArgs base_args(const Plan* P, bool fp32) {
+  TileArgs a{};
+  a.tiles = P->tiles;
+  a.n_tiles = P->n_tiles;
+  a.nrhs = 1;
+  a.N = P->N;
+  a.lpix = P->lpix;
+  a.psi = P->psi;
+  a.w64 = P->w64;
+  a.tab = fp32 ? (const void*)P->tab32 : (const void*)P->tab64;
+  a.tw = fp32 ? (const void*)P->tw32 : (const void*)P->tw64;
+  a.done = nullptr;
+  a.done_stride = 0;
+  return a;
+}
+
+// y4 (accumulated, pre-zeroed by the caller) += A x4 in FP64, [nrhs][n_obs][4]
+int apply64_internal(Plan* P, const double* x4, double* y4, int nrhs, cudaStream_t s,
+                     const int32_t* done = nullptr, int done_stride = 0) {
+  if (P->algo == MM_TPLZ_DIRECT) {
+    MM_TRY(ensure_td(P));
+    for (int r = 0; r < nrhs; r++) {
+      MM_CUDA(launch_unpoint64(P->lpix, P->w64, P->N, x4 + (size_t)r * P->n_obs * 4, P->td_a, s));
+      MM_CUDA(launch_toeplitz_direct(P->band, P->block_off_dev, P->n_blocks, P->lambda, P->N,
+                                     P->td_a, P->td_b, s));
+      MM_CUDA(launch_point64(P->lpix, P->w64, P->N, P->td_b, y4 + (size_t)r * P->n_obs * 4, s));
+    }
+    return MM_OK;
+  }
+  TileArgs a = base_args(P, false);
+  a.nrhs = nrhs;
+  a.x = x4;
+  a.x_stride = P->n_obs * 4;
+  a.y = y4;
+  a.y_stride = P->n_obs * 4;
+  a.done = done;
+  a.done_stride = done_stride;
+  MM_CUDA(launch_tiles_fp64(MODE_APPLY, a, s));
+  return MM_OK;
+}
+
+// y32 (accumulated, pre-zeroed) += A x32 in FP32, [nrhs][n_obs][4] float
+int apply32_internal(Plan* P, const float* x32, float* y32, int nrhs, cudaStream_t s,
+                     const int32_t* done = nullptr, int done_stride = 0) {
+  TileArgs a = base_args(P, true);
+  a.nrhs = nrhs;
+  a.x = x32;
+  a.x_stride = P->n_obs * 4;
+  a.y = y32;
+  a.y_stride = P->n_obs * 4;
+  a.done = done;
+  a.done_stride = done_stride;
+  MM_CUDA(launch_tiles_fp32(MODE_APPLY, a, s));
+  return MM_OK;
+}
+
+int ensure_cg(Plan* P, int nrhs, bool fp32, CgState** out) {
+  CgState* c = reinterpret_cast<CgState*>(P->cg);
+  if (!c) {
+    c = new CgState();
+    P->cg = c;
+  }
+  if (c->nrhs_cap < nrhs || c->n != P->n_obs) {
+    if (c->exec) {
+      cudaGraphExecDestroy(c->exec);
+      c->exec = nullptr;
+    }
+    dfree(c->b); dfree(c->x); dfree(c->r); dfree(c->z); dfree(c->p); dfree(c->q);
+    dfree(c->p32); dfree(c->q32); dfree(c->partials); dfree(c->counters); dfree(c->scal);
+    if (c->scal_host) { cudaFreeHost(c->scal_host); c->scal_host = nullptr; }
+    const size_t n4 = (size_t)nrhs * P->n_obs * 4;
+    MM_TRY(dalloc(P, &c->b, n4)); MM_TRY(dalloc(P, &c->x, n4)); MM_TRY(dalloc(P, &c->r, n4));
+    MM_TRY(dalloc(P, &c->z, n4)); MM_TRY(dalloc(P, &c->p, n4)); MM_TRY(dalloc(P, &c->q, n4));
+    MM_TRY(dalloc(P, &c->p32, n4)); MM_TRY(dalloc(P, &c->q32, n4));
+    MM_TRY(dalloc(P, &c->partials, (size_t)nrhs * 1024 * 4));
+    MM_TRY(dalloc(P, &c->counters, nrhs));
+    MM_TRY(dalloc(P, &c->scal, nrhs));
+    MM_CUDA(cudaMemset(c->counters, 0, nrhs * sizeof(unsigned)));
+    MM_CUDA(cudaMallocHost((void**)&c->scal_host, nrhs * sizeof(CgScalars)));
+    c->nrhs_cap = nrhs;
+    c->n = P->n_obs;
+  }
+  (void)fp32;
+  *out = c;
+  return MM_OK;
+}
+
+CgWork make_work(Plan* P, CgState* c, int nrhs, bool fp32, double tol, int max_iter) {
+  CgWork w{};
+  w.n = P->n_obs;
+  w.nrhs = nrhs;
+  w.n_blocks = cg_blocks_for(P->n_obs);
+  w.fp32 = fp32 ? 1 : 0;
+  w.tol2 = tol * tol;
+  w.max_iter = max_iter;
+  w.minv = P->minv;
+  w.b = c->b; w.x = c->x; w.r = c->r; w.z = c->z; w.p = c->p; w.q = c->q;
+  w.p32 = c->p32; w.q32 = c->q32;
+  w.partials = c->partials;
+  w.counters = c->counters;
+  w.scal = c->scal;
+  return w;
+}
+
+// One PCG iteration: p = z + beta p; q = A p; alpha; x, r, z, beta.
+int enqueue_iteration(Plan* P, const CgWork& w, int nrhs, bool fp32, cudaStream_t s) {
+  MM_CUDA(launch_cg(CG_PUPDATE, w, s));
+  const int32_t* halt = reinterpret_cast<const int32_t*>(w.scal) + kHaltOffsetInts;
+  if (fp32) {
+    MM_TRY(apply32_internal(P, w.p32, w.q32, nrhs, s, halt, kScalStrideInts));
+  } else {
+    MM_TRY(apply64_internal(P, w.p, w.q, nrhs, s, halt, kScalStrideInts));
+  }
+  MM_CUDA(launch_cg(CG_DOT_PQ, w, s));
+  MM_CUDA(launch_cg(CG_UPDATE, w, s));
+  return MM_OK;
+}
+
+}  // namespace
+}  // namespace mm
+
+using namespace mm;
+
+extern "C" {
+
+const char* mm_last_error(void) { return g_err.c_str(); }
+
+int mm_plan(const mm_problem_desc* desc, void* stream, mm_plan_t* out) {
+  if (!out) return fail(MM_EINVAL, "out is NULL");
+  *out = nullptr;
+  MM_TRY(validate_desc(desc));
+  Plan* P = new Plan();
+  const int st = build_plan(desc, as_stream(stream), P);
+  if (st != MM_OK) {
+    free_plan(P);
+    return st;
+  }
+  *out = reinterpret_cast<mm_plan_t>(P);
+  return MM_OK;
+}
+
+int mm_plan_query(mm_plan_t plan, int64_t* n_obs, const int32_t** obs_to_global_dev, int64_t* n_samples,
+                  size_t* bytes) {
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  if (!P) return fail(MM_EINVAL, "plan is NULL");
+  if (n_obs) *n_obs = P->n_obs;
+  if (obs_to_global_dev) *obs_to_global_dev = P->obs_to_global;
+  if (n_samples) *n_samples = P->N;
+  if (bytes) *bytes = P->bytes;
+  return MM_OK;
+}
+
+void mm_plan_destroy(mm_plan_t plan) { free_plan(reinterpret_cast<Plan*>(plan)); }
+
+int mm_apply_P(mm_plan_t plan, const double* x, double* t, void* stream) {
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  if (!P || !x || !t) return fail(MM_EINVAL, "NULL argument");
+  DeviceGuard g(P->device);
+  cudaStream_t s = as_stream(stream);
+  MM_TRY(ensure_maps(P, 1, false));
+  MM_CUDA(launch_pack3to4(x, P->n_obs, 1, P->map64_in, s));
+  MM_CUDA(launch_unpoint64(P->lpix, P->w64, P->N, P->map64_in, t, s));
+  return MM_OK;
+}
+
+int mm_apply_Pt(mm_plan_t plan, const double* t, double* y, void* stream) {
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  if (!P || !t || !y) return fail(MM_EINVAL, "NULL argument");
+  DeviceGuard g(P->device);
+  cudaStream_t s = as_stream(stream);
+  MM_TRY(ensure_maps(P, 1, false));
+  MM_CUDA(cudaMemsetAsync(P->map64_out, 0, P->n_obs * 4 * sizeof(double), s));
+  MM_CUDA(launch_point64(P->lpix, P->w64, P->N, t, P->map64_out, s));
+  MM_CUDA(launch_unpack4to3(P->map64_out, P->n_obs, 1, y, s));
+  return MM_OK;
+}
+
+int mm_apply_Ninv(mm_plan_t plan, const double* t, double* y, void* stream) {
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  if (!P || !t || !y) return fail(MM_EINVAL, "NULL argument");
+  if (t == y) return fail(MM_EINVAL, "mm_apply_Ninv cannot run in place");
+  DeviceGuard g(P->device);
+  cudaStream_t s = as_stream(stream);
+  if (P->algo == MM_TPLZ_DIRECT) {
+    MM_CUDA(launch_toeplitz_direct(P->band, P->block_off_dev, P->n_blocks, P->lambda, P->N, t, y, s));
+    return MM_OK;
+  }
+  TileArgs a = base_args(P, false);
+  a.x = t;
+  a.x_stride = P->N;
+  a.y = y;
+  a.y_stride = P->N;
+  MM_CUDA(launch_tiles_fp64(MODE_NINV, a, s));
+  return MM_OK;
+}
+
+int mm_rhs(mm_plan_t plan, const void* d, int d_is_fp32, int nrhs, double* b, void* stream) {
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  if (!P || !d || !b || nrhs <= 0) return fail(MM_EINVAL, "bad argument");
+  DeviceGuard g(P->device);
+  cudaStream_t s = as_stream(stream);
+  MM_TRY(ensure_maps(P, nrhs, false));
+  const size_t n4 = (size_t)nrhs * P->n_obs * 4;
+  MM_CUDA(cudaMemsetAsync(P->map64_out, 0, n4 * sizeof(double), s));
+  if (P->algo == MM_TPLZ_DIRECT) {
+    MM_TRY(ensure_td(P));
+    const size_t esz = d_is_fp32 ? sizeof(float) : sizeof(double);
+    for (int r = 0; r < nrhs; r++) {
+      const void* dr = reinterpret_cast<const char*>(d) + (size_t)r * P->N * esz;
+      MM_CUDA(launch_mask_d(P->lpix, dr, d_is_fp32, P->N, P->td_a, s));
+      MM_CUDA(launch_toeplitz_direct(P->band, P->block_off_dev, P->n_blocks, P->lambda, P->N,
+                                     P->td_a, P->td_b, s));
+      MM_CUDA(launch_point64(P->lpix, P->w64, P->N, P->td_b, P->map64_out + (size_t)r * P->n_obs * 4, s));
+    }
+  } else {
+    TileArgs a = base_args(P, false);
+    a.nrhs = nrhs;
+    a.x = d;
+    a.x_is_fp32 = d_is_fp32 ? 1 : 0;
+    a.x_stride = P->N;
+    a.y = P->map64_out;
+    a.y_stride = P->n_obs * 4;
+    MM_CUDA(launch_tiles_fp64(MODE_RHS, a, s));
+  }
+  MM_CUDA(launch_unpack4to3(P->map64_out, P->n_obs, nrhs, b, s));
+  return MM_OK;
+}
+
+int mm_apply_A(mm_plan_t plan, const double* x, double* y, int nrhs, void* stream) {
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  if (!P || !x || !y || nrhs <= 0) return fail(MM_EINVAL, "bad argument");
+  DeviceGuard g(P->device);
+  cudaStream_t s = as_stream(stream);
+  const bool fp32 = P->precision == MM_FP32 && P->algo != MM_TPLZ_DIRECT;
+  MM_TRY(ensure_maps(P, nrhs, fp32));
+  const size_t n4 = (size_t)nrhs * P->n_obs * 4;
+  MM_CUDA(launch_pack3to4(x, P->n_obs, nrhs, P->map64_in, s));
+  if (fp32) {
+    MM_CUDA(launch_to32(P->map64_in, (int64_t)(n4 / 4), P->map32_in, s));
+    MM_CUDA(cudaMemsetAsync(P->map32_out, 0, n4 * sizeof(float), s));
+    MM_TRY(apply32_internal(P, P->map32_in, P->map32_out, nrhs, s));
+    MM_CUDA(launch_to64(P->map32_out, (int64_t)(n4 / 4), P->map64_out, s));
+  } else {
+    MM_CUDA(cudaMemsetAsync(P->map64_out, 0, n4 * sizeof(double), s));
+    MM_TRY(apply64_internal(P, P->map64_in, P->map64_out, nrhs, s));
+  }
+  MM_CUDA(launch_unpack4to3(P->map64_out, P->n_obs, nrhs, y, s));
+  return MM_OK;
+}
+
+int mm_precond(mm_plan_t plan, const double* r, double* z, int nrhs, void* stream) {
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  if (!P || !r || !z || nrhs <= 0) return fail(MM_EINVAL, "bad argument");
+  DeviceGuard g(P->device);
+  cudaStream_t s = as_stream(stream);
+  MM_TRY(ensure_maps(P, nrhs, false));
+  MM_CUDA(launch_pack3to4(r, P->n_obs, nrhs, P->map64_in, s));
+  MM_CUDA(launch_bd_apply(P->minv, P->n_obs, nrhs, P->map64_in, P->map64_out, s));
+  MM_CUDA(launch_unpack4to3(P->map64_out, P->n_obs, nrhs, z, s));
+  return MM_OK;
+}
+
+int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_solve_opts* opts,
+                 mm_solve_info* info, void* stream) {
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  if (!P || !b || !x || !opts || !info || nrhs <= 0) return fail(MM_EINVAL, "bad argument");
+  if (!(opts->tol > 0.0) || opts->max_iter < 0) return fail(MM_EINVAL, "bad tol / max_iter");
+  if (opts->precond != MM_PREC_BD) return fail(MM_EINVAL, "unsupported preconditioner");
+  if (opts->precision != MM_FP64 && opts->precision != MM_FP32) return fail(MM_EINVAL, "bad precision");
+  DeviceGuard g(P->device);
+  const auto t0 = std::chrono::steady_clock::now();
+  const bool fp32 = opts->precision == MM_FP32 && P->algo != MM_TPLZ_DIRECT;
+  const int chunk = opts->check_every > 0 ? opts->check_every : 8;
+  const int rel_every = opts->reliable_every > 0 ? opts->reliable_every : 50;
+  cudaStream_t us = as_stream(stream);
+  cudaStream_t s = P->stream;
+  CgState* c = nullptr;
+  MM_TRY(ensure_cg(P, nrhs, fp32, &c));
+  CgWork w = make_work(P, c, nrhs, fp32, opts->tol, opts->max_iter);
+  if (P->algo == MM_TPLZ_DIRECT) MM_TRY(ensure_td(P));
+
+  cudaEvent_t ev;
+  MM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  MM_CUDA(cudaEventRecord(ev, us));
+  MM_CUDA(cudaStreamWaitEvent(s, ev, 0));
+
+  MM_CUDA(launch_pack3to4(b, P->n_obs, nrhs, c->b, s));
+  MM_CUDA(launch_cg(CG_INIT, w, s));
+
+  // graph of `chunk` iterations, cached on the plan
+  if (!c->exec || c->g_nrhs != nrhs || c->g_fp32 != (int)fp32 || c->g_chunk != chunk ||
+      c->g_tol2 != w.tol2 || c->g_maxit != opts->max_iter) {
+    if (c->exec) {
+      cudaGraphExecDestroy(c->exec);
+      c->exec = nullptr;
+    }
+    cudaGraph_t graph;
+    MM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int st = MM_OK;
+    for (int k = 0; k < chunk && st == MM_OK; k++) st = enqueue_iteration(P, w, nrhs, fp32, s);
+    cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    if (st != MM_OK) return st;
+    MM_CUDA(ce);
+    ce = cudaGraphInstantiate(&c->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    MM_CUDA(ce);
+    c->g_nrhs = nrhs;
+    c->g_fp32 = fp32;
+    c->g_chunk = chunk;
+    c->g_tol2 = w.tol2;
+    c->g_maxit = opts->max_iter;
+  }
+
+  std::vector<int> timed_out(nrhs, 0);
+  while (true) {
+    MM_CUDA(cudaMemcpyAsync(c->scal_host, c->scal, nrhs * sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    MM_CUDA(cudaStreamSynchronize(s));
+    bool all_done = true, need_rep = false;
+    for (int r = 0; r < nrhs; r++) {
+      const CgScalars& sc = c->scal_host[r];
+      if (!sc.done) all_done = false;
+      if (!sc.done && fp32 && (sc.paused || sc.since_rep >= rel_every)) need_rep = true;
+    }
+    if (all_done) break;
+    const double el_us =
+        std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
+    if (opts->deadline_us > 0 && el_us > (double)opts->deadline_us) {
+      for (int r = 0; r < nrhs; r++) timed_out[r] = !c->scal_host[r].done;
+      break;
+    }
+    if (need_rep) {
+      // residual replacement: r = b - A x with A in FP64
+      MM_CUDA(cudaMemsetAsync(c->q, 0, (size_t)nrhs * P->n_obs * 4 * sizeof(double), s));
+      MM_TRY(apply64_internal(P, c->x, c->q, nrhs, s,
+                              reinterpret_cast<const int32_t*>(c->scal) + kDoneOffsetInts, kScalStrideInts));
+      MM_CUDA(launch_cg(CG_REPLACE, w, s));
+      continue;
+    }
+    MM_CUDA(cudaGraphLaunch(c->exec, s));
+  }
+
+  // true residual ||b - A x|| in FP64 for the report
+  MM_CUDA(cudaMemsetAsync(c->q, 0, (size_t)nrhs * P->n_obs * 4 * sizeof(double), s));
+  MM_TRY(apply64_internal(P, c->x, c->q, nrhs, s));
+  MM_CUDA(launch_cg(CG_TRUE_RES, w, s));
+  MM_CUDA(launch_unpack4to3(c->x, P->n_obs, nrhs, x, s));
+  MM_CUDA(cudaMemcpyAsync(c->scal_host, c->scal, nrhs * sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+  MM_CUDA(cudaStreamSynchronize(s));
+  MM_CUDA(cudaEventRecord(ev, s));
+  MM_CUDA(cudaStreamWaitEvent(us, ev, 0));
+  cudaEventDestroy(ev);
+  const double t_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  int worst = MM_OK;
+  for (int r = 0; r < nrhs; r++) {
+    const CgScalars& sc = c->scal_host[r];
+    mm_solve_info& in = info[r];
+    in.iters = sc.iters;
+    in.rel_res = sc.bnorm2 > 0 ? std::sqrt(sc.rr / sc.bnorm2) : 0.0;
+    in.true_rel_res = sc.bnorm2 > 0 ? std::sqrt(sc.rr_true / sc.bnorm2) : 0.0;
+    in.t_ms = t_ms;
+    in.n_true_res = sc.n_true;
+    int st = sc.status;
+    if (st == MM_OK && !sc.done) st = timed_out[r] ? MM_ETIMEOUT : MM_ENOTCONV;
+    in.status = st;
+    if (st != MM_OK && (worst == MM_OK || st < worst)) worst = st;
+  }
+  if (worst != MM_OK) set_error("solve did not converge for every right-hand side");
+  return worst;
+}
+
+}  // extern "C"

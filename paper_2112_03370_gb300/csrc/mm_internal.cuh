@@ -1,0 +1,180 @@
+// Internal declarations of libmm shared by its translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mm.h"
+
+namespace mm {
+
+// ---------------------------------------------------------------------------------------------
+// Toeplitz tile geometry.  One tile = L = 2M real samples gathered into M packed complex values
+// (z[n] = t[2n] + i t[2n+1]); the tile's output range holds the samples whose whole band
+// [g - lambda, g + lambda] lies inside the tile (overlap-save, Sect. 3.1 shift-and-overlap).
+// ---------------------------------------------------------------------------------------------
+constexpr int kLogM = 14;                 // complex points per tile (both precisions)
+constexpr int kM = 1 << kLogM;            // 16384 complex = 32768 real samples
+constexpr int kL = 2 * kM;
+constexpr int kMaxLambda = 12288;         // keeps >= 8192 valid outputs per tile
+constexpr int kCl32 = 1;                  // FP32: one CTA holds the whole tile (128 KB smem)
+constexpr int kCl64 = 2;                  // FP64: a 2-CTA cluster holds it (2 x 128 KB smem)
+constexpr int kTileThreads = 512;
+
+struct TileDesc {
+  int64_t in0;      // global sample index of the tile's first input sample (multiple of 4)
+  int64_t out_lo;   // output range [out_lo, out_hi) of this tile
+  int64_t out_hi;
+  int64_t blk_lo;   // the block's sample range: samples outside read as 0
+  int64_t blk_hi;
+  int32_t tab;      // spectrum table id
+  int32_t pad_;
+  double scale;     // block band / table band
+};
+
+enum Mode { MODE_APPLY = 0, MODE_RHS = 1, MODE_NINV = 2 };
+
+// Arguments of the fused Toeplitz-tile kernels.
+struct TileArgs {
+  const TileDesc* tiles;
+  int64_t n_tiles;
+  int32_t nrhs;
+  int64_t N;
+  const int32_t* lpix;      // [N] local pixel or -1
+  const float* psi;         // [N]            (FP32 path)
+  const double2* w64;       // [N] (cos, sin) (FP64 path)
+  const void* tab;          // [n_tab][cl][M/cl] (a, b) of float2 / double2
+  const void* tw;           // [M] twiddles W_M^k (float2 / double2)
+  const void* x;            // APPLY: map in, [nrhs][n_obs][4]; RHS: d [nrhs][N]; NINV: t [N]
+  int32_t x_is_fp32;        // RHS only: d in float32
+  int64_t x_stride;         // elements between right-hand sides of x
+  void* y;                  // APPLY/RHS: map out [nrhs][n_obs][4] (accumulated); NINV: y [N]
+  int64_t y_stride;
+  const int32_t* done;      // optional: skip the work of column r when done[r * done_stride] != 0
+  int32_t done_stride;
+};
+
+// ---------------------------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------------------------
+struct Plan {
+  int device = 0;
+  int32_t n_det = 0, n_int = 0, n_blocks = 0;
+  int64_t N = 0, n_pix = 0, n_obs = 0;
+  int32_t lambda = 0, precision = MM_FP64, algo = MM_TPLZ_FFT;
+  double cond_max = 1e3;
+  std::vector<int64_t> block_off;      // host [n_blocks + 1]
+
+  // device state
+  int32_t* lpix = nullptr;             // [N]
+  float* psi = nullptr;                // [N]
+  double2* w64 = nullptr;              // [N] cos 2psi, sin 2psi in FP64 (FP64 operators)
+  int32_t* obs_to_global = nullptr;    // [n_obs]
+  double* minv = nullptr;              // [n_obs][6] symmetric inverse BD blocks (00 01 02 11 12 22)
+  double* band = nullptr;              // [n_blocks][lambda + 1]
+  int64_t* block_off_dev = nullptr;    // [n_blocks + 1]
+  double* c0_blk = nullptr;            // [n_blocks]
+
+  // Toeplitz FFT state
+  int32_t n_tab = 0;
+  float2* tab32 = nullptr;             // [n_tab][M]
+  double2* tab64 = nullptr;            // [n_tab][M]
+  float2* tw32 = nullptr;              // [M]
+  double2* tw64 = nullptr;             // [M]
+  TileDesc* tiles = nullptr;
+  int64_t n_tiles = 0;
+
+  // work buffers (grown on demand)
+  float* map32_in = nullptr;  size_t map32_in_cap = 0;
+  float* map32_out = nullptr; size_t map32_out_cap = 0;
+  double* map64_in = nullptr; size_t map64_in_cap = 0;
+  double* map64_out = nullptr; size_t map64_out_cap = 0;
+
+  // time-domain scratch of the direct path and of the P / P^T / N^-1 entry points
+  double* td_a = nullptr;
+  double* td_b = nullptr;
+  size_t td_cap = 0;
+
+  cudaStream_t stream = nullptr;       // plan-owned stream (graph capture)
+  void* cg = nullptr;                  // solver workspace (mm_api.cu)
+
+  size_t bytes = 0;
+};
+
+// error state
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define MM_CUDA(call)                                              \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return ::mm::cuda_fail(e_, #call);      \
+  } while (0)
+
+template <typename T>
+int dalloc(Plan* p, T** ptr, size_t n) {
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)ptr, n * sizeof(T));
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    return fail(MM_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  p->bytes += n * sizeof(T);
+  return MM_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// launchers (each returns a cudaError_t of its launch)
+// ---------------------------------------------------------------------------------------------
+// plan kernels (k_plan.cu)
+cudaError_t launch_bd_accum(const int32_t* pix, const float* psi, const int64_t* block_off,
+                            const double* c0_blk, int32_t n_blocks, int64_t N, double* B6,
+                            int32_t* hits, cudaStream_t s);
+cudaError_t launch_bd_finalize(const double* B6, const int32_t* hits, int64_t n_pix,
+                               double cond_max, int32_t* keep, double* inv6, cudaStream_t s);
+cudaError_t launch_scan_keep(const int32_t* keep, int64_t n, int32_t* lid, int32_t* total,
+                             int32_t* scratch, int64_t scratch_len, cudaStream_t s);
+size_t scan_scratch_len(int64_t n);
+cudaError_t launch_compact(const int32_t* keep, const int32_t* lid, const double* inv6_glob,
+                           int64_t n_pix, int32_t* obs_to_global, double* minv, cudaStream_t s);
+cudaError_t launch_localize(const int32_t* pix, const int32_t* keep, const int32_t* lid,
+                            int64_t N, int32_t* lpix, cudaStream_t s);
+cudaError_t launch_weights64(const float* psi, int64_t N, double2* w64, cudaStream_t s);
+cudaError_t launch_validate(const int32_t* pix, const float* psi, int64_t N, int64_t n_pix,
+                            int32_t* bad, cudaStream_t s);
+cudaError_t launch_spectra(const double* band_rows, int32_t n_tab, int32_t lambda,
+                           double* H /* [n_tab][M+1] */, const double* costab /* [L] */,
+                           cudaStream_t s);
+cudaError_t launch_pair_tables(const double* H, int32_t n_tab, const double* costab,
+                               double2* tab64, float2* tab32, cudaStream_t s);
+cudaError_t launch_twiddles(double2* tw64, float2* tw32, const double* costab, cudaStream_t s);
+
+// Toeplitz-tile kernels (k_toeplitz.cu)
+cudaError_t launch_tiles_fp32(int mode, const TileArgs& a, cudaStream_t s);
+cudaError_t launch_tiles_fp64(int mode, const TileArgs& a, cudaStream_t s);
+int tile_kernels_init();   // sets smem attributes once per process
+
+// direct / elementwise kernels (k_vec.cu)
+cudaError_t launch_toeplitz_direct(const double* band, const int64_t* block_off, int32_t n_blocks,
+                                   int32_t lambda, int64_t N, const double* t, double* y,
+                                   cudaStream_t s);
+cudaError_t launch_unpoint64(const int32_t* lpix, const double2* w64, int64_t N,
+                             const double* x4, double* t, cudaStream_t s);
+cudaError_t launch_point64(const int32_t* lpix, const double2* w64, int64_t N, const double* t,
+                           double* y4, cudaStream_t s);
+cudaError_t launch_mask_d(const int32_t* lpix, const void* d, int d_is_fp32, int64_t N,
+                          double* out, cudaStream_t s);
+cudaError_t launch_pack3to4(const double* x3, int64_t n, int nrhs, double* x4, cudaStream_t s);
+cudaError_t launch_unpack4to3(const double* x4, int64_t n, int nrhs, double* x3, cudaStream_t s);
+cudaError_t launch_to32(const double* x4, int64_t n4, float* y4, cudaStream_t s);
+cudaError_t launch_to64(const float* x4, int64_t n4, double* y4, cudaStream_t s);
+cudaError_t launch_bd_apply(const double* minv, int64_t n, int nrhs, const double* r4, double* z4,
+                            cudaStream_t s);
+
+// CG kernels (k_vec.cu)
+struct CgScalars;   // defined in k_vec.cu
+}  // namespace mm

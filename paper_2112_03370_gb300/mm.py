@@ -1,0 +1,235 @@
+"""Thin ctypes binding of libmm (include/mm.h).  Argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts torch tensors to pointers and
+status codes to exceptions.  Importing it without a built libmm.so raises immediately: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmm.so")
+
+MM_OK, MM_EINVAL, MM_ENOMEM, MM_ENOTSPD, MM_EBREAKDOWN, MM_ENOTCONV, MM_ETIMEOUT, MM_EBUSY, \
+    MM_ECUDA = range(9)
+MM_FP64, MM_FP32 = 0, 1
+MM_TPLZ_AUTO, MM_TPLZ_FFT, MM_TPLZ_DIRECT = 0, 1, 3
+MM_PREC_BD = 0
+STATUS_NAMES = {0: "MM_OK", 1: "MM_EINVAL", 2: "MM_ENOMEM", 3: "MM_ENOTSPD", 4: "MM_EBREAKDOWN",
+                5: "MM_ENOTCONV", 6: "MM_ETIMEOUT", 7: "MM_EBUSY", 8: "MM_ECUDA"}
+
+# the exported entry points of include/mm.h
+EXPORTS = ("mm_plan", "mm_plan_query", "mm_plan_destroy", "mm_apply_P", "mm_apply_Pt",
+           "mm_apply_Ninv", "mm_rhs", "mm_apply_A", "mm_precond", "mm_pcg_solve", "mm_last_error")
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("n_det", ctypes.c_int32), ("n_int", ctypes.c_int32),
+                ("block_len", ctypes.POINTER(ctypes.c_int64)), ("n_pix", ctypes.c_int64),
+                ("pix", ctypes.c_void_p), ("psi", ctypes.c_void_p), ("lambda_", ctypes.c_int32),
+                ("band", ctypes.c_void_p), ("cond_max", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("toeplitz_algo", ctypes.c_int32),
+                ("inputs_on_device", ctypes.c_int32)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
+                ("precond", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("reliable_every", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("deadline_us", ctypes.c_int64)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("rel_res", ctypes.c_double),
+                ("true_rel_res", ctypes.c_double), ("t_ms", ctypes.c_double),
+                ("n_true_res", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+
+class MMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libmm.so is not built ({_LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(_LIB_PATH)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    lib.mm_plan.argtypes = [ctypes.POINTER(ProblemDesc), vp, ctypes.POINTER(vp)]
+    lib.mm_plan_query.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(vp), ctypes.POINTER(i64),
+                                  ctypes.POINTER(ctypes.c_size_t)]
+    lib.mm_plan_destroy.argtypes = [vp]
+    lib.mm_plan_destroy.restype = None
+    for name in ("mm_apply_P", "mm_apply_Pt", "mm_apply_Ninv"):
+        getattr(lib, name).argtypes = [vp, vp, vp, vp]
+    lib.mm_rhs.argtypes = [vp, vp, i32, i32, vp, vp]
+    lib.mm_apply_A.argtypes = [vp, vp, vp, i32, vp]
+    lib.mm_precond.argtypes = [vp, vp, vp, i32, vp]
+    lib.mm_pcg_solve.argtypes = [vp, vp, vp, i32, ctypes.POINTER(SolveOpts),
+                                 ctypes.POINTER(SolveInfo), vp]
+    lib.mm_last_error.restype = ctypes.c_char_p
+    for n in EXPORTS:
+        if n not in ("mm_plan_destroy", "mm_last_error"):
+            getattr(lib, n).restype = ctypes.c_int
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def mm_last_error() -> str:
+    return _lib.mm_last_error().decode()
+
+
+def _check(code: int):
+    if code != MM_OK:
+        raise MMError(code, mm_last_error())
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return t.data_ptr()
+
+
+def _dev(t: torch.Tensor, dtype: torch.dtype, name: str):
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    return t
+
+
+@dataclass
+class Plan:
+    handle: int
+    n_obs: int
+    n_samples: int
+    obs_to_global: torch.Tensor   # int32 [n_obs] (copy, on the plan's device)
+    bytes: int
+
+    def __del__(self):
+        try:
+            if self.handle:
+                _lib.mm_plan_destroy(ctypes.c_void_p(self.handle))
+                self.handle = 0
+        except Exception:
+            pass
+
+    def destroy(self):
+        if self.handle:
+            _lib.mm_plan_destroy(ctypes.c_void_p(self.handle))
+            self.handle = 0
+
+
+def mm_plan(n_det: int, n_int: int, block_len: Sequence[int], n_pix: int, pix: torch.Tensor,
+            psi: torch.Tensor, lam: int, band: torch.Tensor, cond_max: float = 1e3,
+            precision: int = MM_FP64, toeplitz_algo: int = MM_TPLZ_AUTO, stream=None) -> Plan:
+    """Build a plan.  pix/psi/band are either all CUDA tensors or all CPU tensors."""
+    on_dev = pix.is_cuda
+    if (psi.is_cuda != on_dev) or (band.is_cuda != on_dev):
+        raise ValueError("pix, psi and band must all be on the device or all on the host")
+    for t, dt, nm in ((pix, torch.int32, "pix"), (psi, torch.float32, "psi"),
+                      (band, torch.float64, "band")):
+        if t.dtype != dt or not t.is_contiguous():
+            raise TypeError(f"{nm} must be a contiguous {dt} tensor")
+    bl = (ctypes.c_int64 * len(block_len))(*[int(v) for v in block_len])
+    d = ProblemDesc(n_det=n_det, n_int=n_int, block_len=bl, n_pix=n_pix, pix=_ptr(pix),
+                    psi=_ptr(psi), lambda_=lam, band=_ptr(band), cond_max=cond_max,
+                    precision=precision, toeplitz_algo=toeplitz_algo,
+                    inputs_on_device=1 if on_dev else 0)
+    h = ctypes.c_void_p()
+    _check(_lib.mm_plan(ctypes.byref(d), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)))
+    n_obs = ctypes.c_int64()
+    o2g = ctypes.c_void_p()
+    ns = ctypes.c_int64()
+    nb = ctypes.c_size_t()
+    _check(_lib.mm_plan_query(h, ctypes.byref(n_obs), ctypes.byref(o2g), ctypes.byref(ns),
+                              ctypes.byref(nb)))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    o2g_t = torch.empty(n_obs.value, dtype=torch.int32, device=dev)
+    if n_obs.value:
+        cuda_copy_dtod(o2g_t.data_ptr(), o2g.value, 4 * n_obs.value)
+    return Plan(handle=h.value, n_obs=n_obs.value, n_samples=ns.value, obs_to_global=o2g_t,
+                bytes=nb.value)
+
+
+def cuda_copy_dtod(dst: int, src: int, nbytes: int):
+    """Device-to-device copy of raw pointers (marshalling of the plan's pixel map)."""
+    class _Arr:
+        def __init__(self, ptr, n):
+            self.__cuda_array_interface__ = {"shape": (n,), "typestr": "|u1", "data": (ptr, False),
+                                             "version": 3}
+    d = torch.as_tensor(_Arr(dst, nbytes), device="cuda")
+    s = torch.as_tensor(_Arr(src, nbytes), device="cuda")
+    d.copy_(s)
+
+
+def mm_apply_P(plan: Plan, x: torch.Tensor, t: torch.Tensor, stream=None):
+    _dev(x, torch.float64, "x"); _dev(t, torch.float64, "t")
+    _check(_lib.mm_apply_P(ctypes.c_void_p(plan.handle), _ptr(x), _ptr(t), _stream_ptr(stream)))
+
+
+def mm_apply_Pt(plan: Plan, t: torch.Tensor, y: torch.Tensor, stream=None):
+    _dev(t, torch.float64, "t"); _dev(y, torch.float64, "y")
+    _check(_lib.mm_apply_Pt(ctypes.c_void_p(plan.handle), _ptr(t), _ptr(y), _stream_ptr(stream)))
+
+
+def mm_apply_Ninv(plan: Plan, t: torch.Tensor, y: torch.Tensor, stream=None):
+    _dev(t, torch.float64, "t"); _dev(y, torch.float64, "y")
+    _check(_lib.mm_apply_Ninv(ctypes.c_void_p(plan.handle), _ptr(t), _ptr(y), _stream_ptr(stream)))
+
+
+def mm_rhs(plan: Plan, d: torch.Tensor, b: torch.Tensor, stream=None):
+    """b [nrhs, n_obs, 3] (or [n_obs, 3]) = P~^T N^-1 G d for d [nrhs, N] (or [N])."""
+    if d.dtype not in (torch.float64, torch.float32):
+        raise TypeError("d must be float64 or float32")
+    _dev(d, d.dtype, "d"); _dev(b, torch.float64, "b")
+    nrhs = 1 if d.dim() == 1 else d.shape[0]
+    _check(_lib.mm_rhs(ctypes.c_void_p(plan.handle), _ptr(d), 1 if d.dtype == torch.float32 else 0,
+                       nrhs, _ptr(b), _stream_ptr(stream)))
+
+
+def mm_apply_A(plan: Plan, x: torch.Tensor, y: torch.Tensor, stream=None):
+    _dev(x, torch.float64, "x"); _dev(y, torch.float64, "y")
+    nrhs = 1 if x.dim() <= 2 else x.shape[0]
+    _check(_lib.mm_apply_A(ctypes.c_void_p(plan.handle), _ptr(x), _ptr(y), nrhs, _stream_ptr(stream)))
+
+
+def mm_precond(plan: Plan, r: torch.Tensor, z: torch.Tensor, stream=None):
+    _dev(r, torch.float64, "r"); _dev(z, torch.float64, "z")
+    nrhs = 1 if r.dim() <= 2 else r.shape[0]
+    _check(_lib.mm_precond(ctypes.c_void_p(plan.handle), _ptr(r), _ptr(z), nrhs, _stream_ptr(stream)))
+
+
+def mm_pcg_solve(plan: Plan, b: torch.Tensor, x: torch.Tensor, tol: float = 1e-6,
+                 max_iter: int = 10000, precision: int = MM_FP64, reliable_every: int = 0,
+                 check_every: int = 0, deadline_us: int = 0, stream=None, raise_on_error=True):
+    """Solve A x = b (b, x: [nrhs, n_obs, 3] or [n_obs, 3]); returns a list of SolveInfo."""
+    _dev(b, torch.float64, "b"); _dev(x, torch.float64, "x")
+    nrhs = 1 if b.dim() <= 2 else b.shape[0]
+    opts = SolveOpts(tol=tol, max_iter=max_iter, precond=MM_PREC_BD, precision=precision,
+                     reliable_every=reliable_every, check_every=check_every,
+                     deadline_us=deadline_us)
+    infos = (SolveInfo * nrhs)()
+    code = _lib.mm_pcg_solve(ctypes.c_void_p(plan.handle), _ptr(b), _ptr(x), nrhs,
+                             ctypes.byref(opts), infos, _stream_ptr(stream))
+    if raise_on_error and code not in (MM_OK,):
+        raise MMError(code, mm_last_error())
+    return list(infos)
