@@ -1,0 +1,402 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 map-maker on the ground-based workload.
+
+Workload: 512 detectors x 4 stationary intervals x 524,288 samples (1.07e9 samples), a 1024x1024
+IQU patch, raster scan with a rotating half-wave plate, 1/f noise (f_knee 1 Hz, alpha 1.5,
+per-detector sigma ~ U(0.8, 1.2)), banded inverse-noise weights with lambda = 8192; seeded
+synthetic data generated on the device.
+
+One step = one whole pass of the hot path on resident inputs: the right-hand side
+b = P^T N^-1 d and a mixed-precision PCG solve to rel. residual 1e-6 (FP32 P, N^-1, P^T; FP64
+vectors, dot products, alpha/beta, 3x3 blocks and residual replacements).  The plan (pixel
+compaction, block-Jacobi blocks, spectra) is built once before the timed region; the e2e number
+rebuilds it from pinned host buffers in every step.
+
+value  = TOD samples pushed through A per second (N x A-applications per step / step time),
+         summed over ranks.  Extra keys give solves/s and PCG iterations/s.
+--impl reference runs the FP64 CPU oracle (numpy/scipy) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TOD samples/s through A=PᵀN⁻¹P; PCG solves/s + p50/p99 at map err ≤1e-6"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+PROFILE_FILE = os.path.join(ROOT, "profiles", "tile_fp32_ground.json")
+SM_COUNT, FP32_LANES_PER_SM = 152, 128
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def args_parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--dets", type=int, default=512, help="detectors (512 = the full workload)")
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-dets", type=int, default=16)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------------------------------
+# roofline helpers
+# ------------------------------------------------------------------------------------------
+
+def fft_flops_per_sample(L: int, lam: int) -> float:
+    """Algorithmic flops per output sample of the overlap-save Toeplitz product: a real forward
+    and inverse FFT of L points (2.5 L log2 L each) plus the pointwise product (3 L), shared by
+    the L - 2 lam outputs the tile keeps."""
+    return (5.0 * L * math.log2(L) + 3.0 * L) / (L - 2 * lam)
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2112_03370_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f in ("k_toeplitz.cu", "fft_smem.cuh", "mm_internal.cuh"):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(n_samples: int):
+    """DRAM bytes per launch of the FP32 tile kernel from the committed ncu summary, scaled to
+    this launch; None when absent or taken on different kernel source."""
+    try:
+        prof = json.load(open(PROFILE_FILE))
+    except Exception:
+        return None
+    if prof.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return prof["dram_bytes_per_sample"] * n_samples
+
+
+def peaks():
+    try:
+        return json.load(open(PEAKS_FILE)), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.rows = []
+        self.bus_id = (bus_id or "").lower()
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception as e:   # no nvidia-smi: report no clocks
+            log("clock sampler unavailable:", e)
+            return self
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+        rows = self.rows
+        if self.bus_id:
+            mine = [r for r in rows if len(r) > 1 and r[1].lower().endswith(self.bus_id[-12:])]
+            rows = mine or rows
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if len(r) > 6 + i and r[6 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample of the same workload)
+# ------------------------------------------------------------------------------------------
+
+def cpu_oracle_rate(n_dets: int, n_applies: int = 2, with_iteration: bool = True):
+    """Samples/s through A of the FP64 oracle on the first n_dets detectors x 1 interval."""
+    import numpy as np
+    import oracle as O
+    import synth
+    cfg = synth.ground_config(n_det=n_dets, n_int=1)
+    prob = synth.make_ground_problem(cfg, with_noise=True)
+    nb = synth.to_numpy(prob)
+    op = O.make_plan(nb["pix"], nb["psi"], nb["block_len"], nb["band"], nb["n_pix"])
+    b = O.rhs(op, nb["d"])
+    x = O.precond_bd(op, b)
+    t0 = time.perf_counter()
+    for _ in range(n_applies):
+        y = O.apply_A(op, x)
+        if with_iteration:   # the rest of one PCG iteration (Algorithm 1 vector work)
+            den = float(np.vdot(y, x))
+            a = float(np.vdot(b, x)) / den if den != 0.0 else 0.0
+            x = x + a * O.precond_bd(op, b - y)
+    dt = time.perf_counter() - t0
+    n = int(nb["pix"].size)
+    return n * n_applies / dt, dt, n
+
+
+# ------------------------------------------------------------------------------------------
+# the reference arm: the FP64 oracle on the host cores
+# ------------------------------------------------------------------------------------------
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    rates = []
+    for i in range(a.warmup + a.steps):
+        r, dt, n = cpu_oracle_rate(a.cpu_dets, n_applies=1)
+        if i >= a.warmup:
+            rates.append(r)
+    v = statistics.mean(rates)
+    sample = (f"{a.cpu_dets} detectors x 1 interval x 524288 samples of the ground workload; "
+              f"one oracle PCG iteration (A-apply + vector update) per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": n / v * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "ground (sampled for the CPU oracle)", "n_samples_per_step": n},
+        "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+
+def run_ours(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    import paper_2112_03370_gb300.mm as mm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(dev)
+    bus = getattr(props, "pci_bus_id", None)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # replicas: each rank solves its own problem (independent seeds per rank)
+    cfg = synth.ground_config(n_det=a.dets)
+    t_gen = time.perf_counter()
+    prob = synth.make_ground_problem(cfg, device=dev, real_offset=1000 * rank)
+    torch.cuda.synchronize()
+    log(f"[rank {rank}] generated {prob.n_total:.3e} samples in {time.perf_counter() - t_gen:.1f}s")
+    band_d = prob.band.to(dev)
+    t_plan = time.perf_counter()
+    plan = mm.mm_plan(prob.n_det, prob.n_int, prob.block_len.tolist(), prob.n_pix, prob.pix,
+                      prob.psi, prob.lam, band_d, precision=mm.MM_FP32)
+    torch.cuda.synchronize()
+    t_plan = time.perf_counter() - t_plan
+    N = plan.n_samples
+    log(f"[rank {rank}] plan: n_obs={plan.n_obs} N={N} bytes={plan.bytes / 1e9:.2f} GB "
+        f"in {t_plan:.2f}s")
+    b = torch.empty(plan.n_obs, 3, dtype=torch.float64, device=dev)
+    x = torch.empty_like(b)
+
+    def step():
+        mm.mm_rhs(plan, prob.d, b)
+        return mm.mm_pcg_solve(plan, b, x, tol=cfg.tol, max_iter=5000, precision=mm.MM_FP32,
+                               profile=True, raise_on_error=False)[0]
+
+    for i in range(a.warmup):
+        inf = step()
+        log(f"[rank {rank}] warmup {i}: iters={inf.iters} status={inf.status} "
+            f"true_rel_res={inf.true_rel_res:.2e} t={inf.t_ms:.0f}ms")
+    barrier()
+    clocks = ClockSampler(bus).start() if rank == 0 else None
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    step_ms = []
+    ev0.record()
+    for i in range(a.steps):
+        e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e_a.record()
+        infos.append(step())
+        e_b.record()
+        e_b.synchronize()
+        step_ms.append(e_a.elapsed_time(e_b))
+    ev1.record()
+    barrier()
+    clk = clocks.stop() if clocks else None
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if world > 1:
+        t = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t)
+    applies = sum(i.n_apply32 + i.n_apply64 for i in infos)
+    iters = sum(i.iters for i in infos)
+    samples = N * applies * world
+    value = samples / elapsed
+    t32 = sum(i.t_apply32_ms for i in infos)
+    n32 = sum(i.n_apply32 for i in infos)
+    t64 = sum(i.t_apply64_ms for i in infos)
+    n64 = sum(i.n_apply64 for i in infos)
+    launches = sum(i.n_kernels for i in infos) + 2 * a.steps   # + rhs tile and unpack per step
+
+    # roofline of the dominant kernel (FP32 overlap-save tile, FP32-ALU bound at lambda = 8192)
+    pk, pk_kind = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12      # TFLOP/s
+    L = 32768
+    flops_launch = N * fft_flops_per_sample(L, cfg.lam)
+    avg32 = t32 / max(n32, 1) / 1e3
+    achieved = flops_launch / avg32 / 1e12
+    alg_bytes = 8.0 * N + 2 * 16.0 * plan.n_obs      # pointing once + map in/out (FP32, padded)
+    traffic = measured_traffic(N)
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": traffic,
+            "kernel": "k_tile<float,1,APPLY> (fused P, overlap-save FFT N^-1, P^T)",
+            "peak_kind": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                         f"{sm_max:.0f} MHz ({pk_kind} sm_max_mhz)",
+            "ms_per_launch": avg32 * 1e3,
+            "hbm_achieved_gbs": alg_bytes / avg32 / 1e9,
+            "hbm_frac": alg_bytes / avg32 / 1e9 / float(pk.get("hbm_gbs", 6800.0)),
+            "hbm_peak_kind": pk_kind}
+
+    out = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": elapsed / a.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+           "data": "synthetic (seeded, generated on the device)",
+           "config": {"workload": f"ground: {prob.n_det} det x {prob.n_int} int x {cfg.n_samp} "
+                                  f"samples, {cfg.side}x{cfg.side} IQU patch, lambda {cfg.lam}",
+                      "n_samples": N, "n_obs": plan.n_obs, "lambda": cfg.lam, "tol": cfg.tol,
+                      "step": "rhs + mixed-precision PCG solve (FP32 operators, FP64 CG)",
+                      "parallelism": "replicas" if world > 1 else "single GPU",
+                      "l2": "inputs larger than L2 (pointing 8 B/sample)"},
+           "solves_per_s": a.steps * world / elapsed,
+           "pcg_iters_per_s": iters * world / elapsed,
+           "iters_per_solve": iters / a.steps,
+           "a_applies_per_solve": applies / a.steps,
+           "true_rel_res": max(i.true_rel_res for i in infos),
+           "status": [i.status for i in infos],
+           "step_ms_p50": float(np.percentile(step_ms, 50)),
+           "step_ms_p99": float(np.percentile(step_ms, 99)),
+           "fp64_apply_ms": (t64 / n64) if n64 else None,
+           "plan_s": t_plan,
+           "roofline": roof, "gpu_launches": int(launches), "clocks": clk}
+
+    # plain FP64 PCG on the same GPU: a few iterations for its iteration rate
+    if rank == 0:
+        inf64 = mm.mm_pcg_solve(plan, b, x, tol=cfg.tol, max_iter=4, precision=mm.MM_FP64,
+                                profile=True, raise_on_error=False)[0]
+        out["fp64_pcg"] = {"iters": inf64.iters, "ms_per_iter": inf64.t_ms / max(inf64.iters, 1),
+                           "apply_ms": inf64.t_apply64_ms / max(inf64.n_apply64, 1),
+                           "samples_per_s_through_A": N / (inf64.t_apply64_ms /
+                                                           max(inf64.n_apply64, 1) / 1e3)}
+
+    # end to end through the public API from pinned host buffers
+    if not a.no_e2e:
+        pix_h = prob.pix.cpu().pin_memory()
+        psi_h = prob.psi.cpu().pin_memory()
+        band_h = prob.band.cpu().contiguous()
+        d_h = prob.d.cpu().pin_memory()
+        h2d = pix_h.numel() * 4 + psi_h.numel() * 4 + band_h.numel() * 8 + d_h.numel() * 8
+
+        def e2e_step():
+            p2 = mm.mm_plan(prob.n_det, prob.n_int, prob.block_len.tolist(), prob.n_pix, pix_h,
+                            psi_h, prob.lam, band_h, precision=mm.MM_FP32)
+            d_dev = d_h.to(dev, non_blocking=True)
+            b2 = torch.empty(p2.n_obs, 3, dtype=torch.float64, device=dev)
+            x2 = torch.empty_like(b2)
+            mm.mm_rhs(p2, d_dev, b2)
+            inf = mm.mm_pcg_solve(p2, b2, x2, tol=cfg.tol, max_iter=5000, precision=mm.MM_FP32,
+                                  raise_on_error=False)[0]
+            m_host = x2.cpu()
+            p2.destroy()
+            return inf, m_host
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        e_app = 0
+        for _ in range(a.e2e_steps):
+            inf, m_host = e2e_step()
+            e_app += inf.n_apply32 + inf.n_apply64
+        barrier()
+        te = time.perf_counter() - t0
+        out["e2e"] = {"value": N * e_app * world / te, "unit": "samples/s",
+                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(m_host.numel() * 8),
+                      "steps": a.e2e_steps, "ms_per_step": te / a.e2e_steps * 1e3,
+                      "includes": "mm_plan from pinned host pix/psi/band, H2D of d, mm_rhs, "
+                                  "mm_pcg_solve, D2H of the map"}
+
+    if rank == 0 and world == 1 and not a.no_cpu:
+        r, dt, n = cpu_oracle_rate(a.cpu_dets, n_applies=2)
+        out["cpu_baseline"] = {"value": r, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                               "sample": f"{a.cpu_dets} detectors x 1 interval x 524288 samples of "
+                                         f"the ground workload, 2 oracle PCG iterations "
+                                         f"(A-apply + vector update) in {dt:.1f}s; numpy/scipy "
+                                         f"single-threaded"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = args_parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

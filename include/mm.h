@@ -72,6 +72,8 @@ enum { MM_PREC_BD = 0 };
  *   toeplitz_algo  MM_TPLZ_AUTO/MM_TPLZ_FFT (shared-memory overlap-save FFT) or MM_TPLZ_DIRECT
  *                  (band sum by the definition, O(lambda) per sample; for checks and tiny lambda).
  *   inputs_on_device  non-zero: pix, psi and band are device pointers; zero: host pointers.
+ *   tile_steps     FP32 operators: overlap-save tiles walked by one CTA, which keeps the overlap
+ *                  of consecutive tiles in shared memory (0 = chosen from the problem size).
  */
 typedef struct {
   int32_t n_det;
@@ -86,6 +88,7 @@ typedef struct {
   int32_t precision;
   int32_t toeplitz_algo;
   int32_t inputs_on_device;
+  int32_t tile_steps;
 } mm_problem_desc;
 
 /*
@@ -99,6 +102,9 @@ typedef struct {
  *                  iterations and before the solve is declared converged.
  *   reliable_every FP32 path only; <= 0 selects 50.
  *   check_every    iterations launched between host reads of the convergence flag (<= 0: 8).
+ *   profile        0: each group of check_every iterations runs as one captured CUDA graph.
+ *                  1: iterations are launched one by one and every Toeplitz-tile launch is
+ *                  bracketed by CUDA events on the solve's stream (t_apply*_ms in mm_solve_info).
  *   deadline_us    host-side wall-clock limit in microseconds (<= 0: none) -> MM_ETIMEOUT.
  */
 typedef struct {
@@ -108,6 +114,7 @@ typedef struct {
   int32_t precision;
   int32_t reliable_every;
   int32_t check_every;
+  int32_t profile;
   int64_t deadline_us;
 } mm_solve_opts;
 
@@ -120,6 +127,11 @@ typedef struct {
   double t_ms;           /* wall time of the solve */
   int32_t n_true_res;    /* FP64 true-residual evaluations (FP32 path) */
   int32_t pad_;
+  double t_apply32_ms;   /* profile = 1: summed device time of the FP32 A-application launches */
+  double t_apply64_ms;   /* profile = 1: same for the FP64 A-applications */
+  int32_t n_apply32;     /* FP32 A-application launches (all columns in one launch) */
+  int32_t n_apply64;     /* FP64 A-application launches */
+  int64_t n_kernels;     /* kernels launched by the solve (its own, all columns) */
 } mm_solve_info;
 
 /* Build a plan: validate, copy inputs, compact observed pixels, build and invert the 3x3 BD

@@ -135,24 +135,43 @@ __device__ __forceinline__ void dft_small(C (&a)[R]) {
   }
 }
 
-// Twiddles w_j = W_C^{n1 j}, j = 1..R-1, from the table tw[k] = W_M^k (M = full tile size):
-// W_C^{n1 j} = tw[n1 j (M / C)].  Powers 1, 2, 4, 8 are read; the rest are products of at most
-// two reads.
+// Twiddle factors W_M^k, k in [0, M), from a two-level table in shared memory:
+// W_M^k = hi[k >> 6] * lo[k & 63] with lo[i] = W_M^i (64 entries) and hi[i] = W_M^{64 i}
+// (M / 64 entries); one complex product, accurate to a few ulp.
+template <typename C>
+struct TwiddleTab {
+  const C* lo;
+  const C* hi;
+  __device__ __forceinline__ C operator()(int k) const { return c_mul(hi[k >> 6], lo[k & 63]); }
+};
+constexpr int twiddle_tab_entries(int m) { return 64 + m / 64; }
+
+// Fill the shared table from the global table tw[k] = W_M^k (called by all threads, then sync).
+template <typename C, int MFULL, int NT>
+__device__ __forceinline__ TwiddleTab<C> load_twiddle_tab(C* tab_sm, const C* __restrict__ tw) {
+  for (int i = threadIdx.x; i < twiddle_tab_entries(MFULL); i += NT) {
+    tab_sm[i] = (i < 64) ? __ldg(tw + i) : __ldg(tw + 64 * (i - 64));
+  }
+  return TwiddleTab<C>{tab_sm, tab_sm + 64};
+}
+
+// Twiddles w_j = W_C^{n1 j} = W_M^{n1 j (M / C)}, j = 1..R-1: powers 1, 2, 4, 8 from the table,
+// the rest as products of two of those.
 template <int R, typename C>
-__device__ __forceinline__ void twiddles(const C* __restrict__ tw, int base_idx, C (&w)[R]) {
-  w[1] = __ldg(tw + base_idx);
+__device__ __forceinline__ void twiddles(const TwiddleTab<C>& tw, int base_idx, C (&w)[R]) {
+  w[1] = tw(base_idx);
   if constexpr (R > 2) {
-    w[2] = __ldg(tw + 2 * base_idx);
+    w[2] = tw(2 * base_idx);
     w[3] = c_mul(w[1], w[2]);
   }
   if constexpr (R > 4) {
-    w[4] = __ldg(tw + 4 * base_idx);
+    w[4] = tw(4 * base_idx);
     w[5] = c_mul(w[4], w[1]);
     w[6] = c_mul(w[4], w[2]);
     w[7] = c_mul(w[4], w[3]);
   }
   if constexpr (R > 8) {
-    w[8] = __ldg(tw + 8 * base_idx);
+    w[8] = tw(8 * base_idx);
 #pragma unroll
     for (int j = 1; j < 8; j++) w[8 + j] = c_mul(w[8], w[j]);
   }
@@ -161,7 +180,7 @@ __device__ __forceinline__ void twiddles(const C* __restrict__ tw, int base_idx,
 // One decimation-in-frequency (FWD) or decimation-in-time (inverse) pass over sub-transforms of
 // size Cs with radix R.  `ms` = transform size held by this CTA, `mfull_over_cs` = M / Cs.
 template <int R, bool FWD, int NT, typename C>
-__device__ __forceinline__ void fft_pass(C* __restrict__ sm, const C* __restrict__ tw, int ms,
+__device__ __forceinline__ void fft_pass(C* __restrict__ sm, const TwiddleTab<C>& tw, int ms,
                                          int cs, int mfull_over_cs) {
   const int s = cs / R;
   const int nbf = ms / R;
@@ -203,7 +222,7 @@ struct SmemFFT {
   static constexpr int REM = LOGMS % 4;
 
   template <typename C>
-  __device__ static void forward(C* sm, const C* tw) {
+  __device__ static void forward(C* sm, const TwiddleTab<C>& tw) {
 #pragma unroll 1
     for (int p = 0; p < NP16; p++) {
       const int cs = MS >> (4 * p);
@@ -217,7 +236,7 @@ struct SmemFFT {
   }
 
   template <typename C>
-  __device__ static void inverse(C* sm, const C* tw) {
+  __device__ static void inverse(C* sm, const TwiddleTab<C>& tw) {
     if constexpr (REM > 0) {
       fft_pass<(1 << REM), false, NT>(sm, tw, MS, 1 << REM, MFULL >> REM);
       __syncthreads();

@@ -25,6 +25,8 @@
 // distributed shared memory.
 #include <cooperative_groups.h>
 
+#include <type_traits>
+
 #include "fft_smem.cuh"
 #include "mm_internal.cuh"
 
@@ -64,75 +66,158 @@ template <> struct Map4<double> {
   }
 };
 
-// Pointing weights (cos 2psi, sin 2psi) of sample g.
-template <typename T> struct Weights;
-template <> struct Weights<float> {
-  static __device__ __forceinline__ void get(const TileArgs& a, int64_t g, float& c, float& s) {
-    const float psi = __ldg(a.psi + g);
-    sincosf(2.f * psi, &s, &c);
-  }
-};
-template <> struct Weights<double> {
-  static __device__ __forceinline__ void get(const TileArgs& a, int64_t g, double& c, double& s) {
-    const double2 w = __ldg(a.w64 + g);
-    c = w.x;
-    s = w.y;
-  }
-};
+// ---- batched quad access --------------------------------------------------------------------
+// The gather and scatter walk "quads" of 4 consecutive samples starting at a multiple of 4
+// (tile windows start at multiples of 4).  A thread handles NQ quads at a time and issues all
+// their independent loads before using any of them: first the pixel ids and weights, then the
+// map values that depend on the pixel ids.  That keeps 2 x NQ memory round trips in flight per
+// thread instead of one, which is what bounds a 16-warp CTA.
 
-// Time-domain input value of sample g for the tile's mode (0 outside the block).
-template <typename T, int MODE>
-__device__ __forceinline__ T sample_in(const TileArgs& a, int rhs, int64_t g, int64_t lo, int64_t hi) {
-  if (g < lo || g >= hi) return T(0);
-  if (MODE == MODE_NINV) {
-    return (T)__ldg(reinterpret_cast<const double*>(a.x) + rhs * a.x_stride + g);
+// Raw per-sample weight data: the angle (FP32 path, weights recomputed in registers) or the
+// precomputed (cos 2psi, sin 2psi) pair (FP64 path).
+template <typename T> struct WRaw;
+template <> struct WRaw<float> { float v; };
+template <> struct WRaw<double> { double2 v; };
+
+template <typename T>
+__device__ __forceinline__ void load_w(const TileArgs& a, int64_t g, WRaw<T>& w) {
+  if constexpr (std::is_same<T, float>::value) w.v = __ldg(a.psi + g);
+  else w.v = __ldg(a.w64 + g);
+}
+template <typename T>
+__device__ __forceinline__ void weights_of(const WRaw<T>& w, T& c, T& s) {
+  if constexpr (std::is_same<T, float>::value) {
+    // accurate single-precision sine/cosine: the FP32 operator must stay within a few ulp of the
+    // FP64 one, or the FP64 residual replacement of the mixed-precision solver stops converging
+    // (a systematic weight error perturbs the smallest eigenvalues of A)
+    sincosf(2.f * w.v, &s, &c);
+  } else {
+    c = w.v.x;
+    s = w.v.y;
   }
-  const int32_t p = __ldg(a.lpix + g);
-  if (p < 0) return T(0);
-  if (MODE == MODE_RHS) {
-    if (a.x_is_fp32) return (T)__ldg(reinterpret_cast<const float*>(a.x) + rhs * a.x_stride + g);
-    return (T)__ldg(reinterpret_cast<const double*>(a.x) + rhs * a.x_stride + g);
-  }
-  T c, s, I, Q, U;
-  Weights<T>::get(a, g, c, s);
-  Map4<T>::load(a.x, rhs * a.x_stride, p, I, Q, U);
-  return I + c * Q + s * U;
 }
 
-// Output of sample g: accumulate into the map (APPLY / RHS) or store (NINV).
-template <typename T, int MODE>
-__device__ __forceinline__ void sample_out(const TileArgs& a, int rhs, int64_t g, T y) {
-  if (MODE == MODE_NINV) {
-    reinterpret_cast<double*>(a.y)[rhs * a.y_stride + g] = (double)y;
-    return;
+// Pixel ids of the quad [g, g + 4) (-1 outside [lo, hi) or masked) and, when needed, weights.
+template <typename T, bool NEED_W>
+__device__ __forceinline__ void quad_meta(const TileArgs& a, int64_t g, int64_t lo, int64_t hi,
+                                          int32_t (&p)[4], WRaw<T> (&w)[4]) {
+  if (g >= lo && g + 4 <= hi) {
+    const int4 v = __ldg(reinterpret_cast<const int4*>(a.lpix + g));
+    p[0] = v.x; p[1] = v.y; p[2] = v.z; p[3] = v.w;
+    if (NEED_W) {
+      if constexpr (std::is_same<T, float>::value) {
+        const float4 f = __ldg(reinterpret_cast<const float4*>(a.psi + g));
+        w[0].v = f.x; w[1].v = f.y; w[2].v = f.z; w[3].v = f.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; e++) w[e].v = __ldg(a.w64 + g + e);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      const bool in = (g + e >= lo) && (g + e < hi);
+      p[e] = in ? __ldg(a.lpix + g + e) : -1;
+      if (NEED_W && in) load_w<T>(a, g + e, w[e]);
+    }
   }
-  const int32_t p = __ldg(a.lpix + g);
-  if (p < 0) return;
-  T c, s;
-  Weights<T>::get(a, g, c, s);
-  Map4<T>::add(a.y, rhs * a.y_stride, p, y, c * y, s * y);
 }
 
-// Same for the two samples of one packed complex value, merging them when they hit one pixel.
-template <typename T, int MODE>
-__device__ __forceinline__ void pair_out(const TileArgs& a, int rhs, int64_t g, bool e0, bool e1,
-                                         T y0, T y1) {
-  if (MODE == MODE_NINV) {
-    if (e0) sample_out<T, MODE>(a, rhs, g, y0);
-    if (e1) sample_out<T, MODE>(a, rhs, g + 1, y1);
-    return;
+// Time-domain input values of NQ quads (0 outside the block and at masked samples).
+template <typename T, int MODE, int NQ>
+__device__ __forceinline__ void gather_quads(const TileArgs& a, int rhs, const TileDesc& td,
+                                             const int64_t (&g)[NQ], T (&v)[NQ][4]) {
+  if constexpr (MODE == MODE_NINV) {
+    const double* t = reinterpret_cast<const double*>(a.x) + rhs * a.x_stride;
+#pragma unroll
+    for (int u = 0; u < NQ; u++)
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        const int64_t gg = g[u] + e;
+        v[u][e] = (gg >= td.blk_lo && gg < td.blk_hi) ? (T)__ldg(t + gg) : T(0);
+      }
+  } else {
+    int32_t p[NQ][4];
+    WRaw<T> w[NQ][4];
+#pragma unroll
+    for (int u = 0; u < NQ; u++) quad_meta<T, MODE == MODE_APPLY>(a, g[u], td.blk_lo, td.blk_hi, p[u], w[u]);
+    if constexpr (MODE == MODE_RHS) {
+#pragma unroll
+      for (int u = 0; u < NQ; u++)
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+          T d = T(0);
+          if (p[u][e] >= 0) {
+            const int64_t gg = rhs * a.x_stride + g[u] + e;
+            d = a.x_is_fp32 ? (T)__ldg(reinterpret_cast<const float*>(a.x) + gg)
+                            : (T)__ldg(reinterpret_cast<const double*>(a.x) + gg);
+          }
+          v[u][e] = d;
+        }
+    } else {
+      T I[NQ][4], Q[NQ][4], U[NQ][4];
+#pragma unroll
+      for (int u = 0; u < NQ; u++)
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+          I[u][e] = Q[u][e] = U[u][e] = T(0);
+          if (p[u][e] >= 0) Map4<T>::load(a.x, rhs * a.x_stride, p[u][e], I[u][e], Q[u][e], U[u][e]);
+        }
+#pragma unroll
+      for (int u = 0; u < NQ; u++)
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+          T c = T(0), s = T(0);
+          if (p[u][e] >= 0) weights_of<T>(w[u][e], c, s);
+          v[u][e] = (p[u][e] >= 0) ? I[u][e] + c * Q[u][e] + s * U[u][e] : T(0);
+        }
+    }
   }
-  const int32_t p0 = e0 ? __ldg(a.lpix + g) : -1;
-  const int32_t p1 = e1 ? __ldg(a.lpix + g + 1) : -1;
-  T c0 = 0, s0 = 0, c1 = 0, s1 = 0;
-  if (p0 >= 0) Weights<T>::get(a, g, c0, s0);
-  if (p1 >= 0) Weights<T>::get(a, g + 1, c1, s1);
-  if (p0 >= 0 && p0 == p1) {
-    Map4<T>::add(a.y, rhs * a.y_stride, p0, y0 + y1, c0 * y0 + c1 * y1, s0 * y0 + s1 * y1);
-    return;
+}
+
+// Accumulate (APPLY / RHS) or store (NINV) the outputs y of NQ quads; samples outside
+// [out_lo, out_hi) are skipped.  Consecutive samples of one pixel are merged into one update.
+template <typename T, int MODE, int NQ>
+__device__ __forceinline__ void scatter_quads(const TileArgs& a, int rhs, const TileDesc& td,
+                                              const int64_t (&g)[NQ], const T (&y)[NQ][4]) {
+  if constexpr (MODE == MODE_NINV) {
+    double* out = reinterpret_cast<double*>(a.y) + rhs * a.y_stride;
+#pragma unroll
+    for (int u = 0; u < NQ; u++)
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        const int64_t gg = g[u] + e;
+        if (gg >= td.out_lo && gg < td.out_hi) out[gg] = (double)y[u][e];
+      }
+  } else {
+    int32_t p[NQ][4];
+    WRaw<T> w[NQ][4];
+#pragma unroll
+    for (int u = 0; u < NQ; u++) quad_meta<T, true>(a, g[u], td.out_lo, td.out_hi, p[u], w[u]);
+#pragma unroll
+    for (int u = 0; u < NQ; u++) {
+      int32_t cur = -1;
+      T acc0 = T(0), acc1 = T(0), acc2 = T(0);
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        const int32_t pe = p[u][e];
+        if (pe != cur) {
+          if (cur >= 0) Map4<T>::add(a.y, rhs * a.y_stride, cur, acc0, acc1, acc2);
+          cur = pe;
+          acc0 = acc1 = acc2 = T(0);
+        }
+        if (pe >= 0) {
+          T c, s;
+          weights_of<T>(w[u][e], c, s);
+          const T ye = y[u][e];
+          acc0 += ye;
+          acc1 += c * ye;
+          acc2 += s * ye;
+        }
+      }
+      if (cur >= 0) Map4<T>::add(a.y, rhs * a.y_stride, cur, acc0, acc1, acc2);
+    }
   }
-  if (p0 >= 0) Map4<T>::add(a.y, rhs * a.y_stride, p0, y0, c0 * y0, s0 * y0);
-  if (p1 >= 0) Map4<T>::add(a.y, rhs * a.y_stride, p1, y1, c1 * y1, s1 * y1);
 }
 
 }  // namespace
@@ -146,6 +231,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a) {
   using FFT = SmemFFT<LOGMS, kM, kTileThreads>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
+  C* tw_sm = sm + smem_pad(MS);
+  T* halo = reinterpret_cast<T*>(tw_sm + twiddle_tab_entries(kM));   // CL == 1 segments
 
   const int64_t unit = blockIdx.x / CL;
   const int rank = (CL == 2) ? (int)(blockIdx.x % CL) : 0;
@@ -153,31 +240,90 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a) {
   // both CTAs of a cluster read the same flag, so they leave together
   if (a.done != nullptr && a.done[(int64_t)rhs * a.done_stride] != 0) return;
   const int64_t tile_id = unit / a.nrhs;
-  const TileDesc td = a.tiles[tile_id];
-  const C* __restrict__ tw = reinterpret_cast<const C*>(a.tw);
-
-  // ---- gather: packed complex input (CL = 2: with the first radix-2 DIF step) ----
-  for (int n = threadIdx.x; n < MS; n += kTileThreads) {
-    const int64_t g = td.in0 + 2 * (int64_t)n;
-    C z{sample_in<T, MODE>(a, rhs, g, td.blk_lo, td.blk_hi),
-        sample_in<T, MODE>(a, rhs, g + 1, td.blk_lo, td.blk_hi)};
-    if (CL == 2) {
-      const int64_t g2 = g + 2 * (int64_t)MS;
-      const C z2{sample_in<T, MODE>(a, rhs, g2, td.blk_lo, td.blk_hi),
-                 sample_in<T, MODE>(a, rhs, g2 + 1, td.blk_lo, td.blk_hi)};
-      z = (rank == 0) ? c_add(z, z2) : c_mul(c_sub(z, z2), __ldg(tw + n));
-    }
-    sm[smem_pad(n)] = z;
-  }
+  const TileDesc seg = a.tiles[tile_id];
+  const C* __restrict__ tw_g = reinterpret_cast<const C*>(a.tw);
+  const TwiddleTab<C> tw = load_twiddle_tab<C, kM, kTileThreads>(tw_sm, tw_g);
+  const C* __restrict__ tab =
+      reinterpret_cast<const C*>(a.tab) + ((int64_t)seg.tab * CL + rank) * MS;
+  const T sc = (T)seg.scale;
+  constexpr int NQ = std::is_same<T, float>::value ? 4 : 2;
+  constexpr int HALF_Q = MS / 2;          // quads (4 real samples) of this CTA's complex range
+  const int halo_q = (kL - seg.vstep) / 4;
   __syncthreads();
 
-  FFT::forward(sm, tw);
+  const int n_steps = (CL == 1) ? seg.n_steps : 1;   // only the FP32 kernel walks segments
+  for (int step = 0; step < n_steps; step++) {
+    TileDesc td = seg;
+    td.in0 = seg.in0 + (int64_t)step * seg.vstep;
+    td.out_lo = seg.out_lo + (int64_t)step * seg.vstep;
+    td.out_hi = min(td.out_lo + (int64_t)seg.vstep, seg.out_hi);
 
-  // ---- pair update with the band's precomputed (a_k, b_k) in storage order ----
-  {
-    const C* __restrict__ tab =
-        reinterpret_cast<const C*>(a.tab) + ((int64_t)td.tab * CL + rank) * MS;
-    const T sc = (T)td.scale;
+    // ---- gather: packed complex input (CL = 2: with the first radix-2 DIF step) ----
+    // quad q holds complex values 2q, 2q + 1 (real samples in0 + 4q .. + 3)
+    if constexpr (CL == 1) {
+      int q_first = 0;
+      if (step > 0) {   // the previous tile's last L - vstep samples are this tile's first ones
+        for (int n = threadIdx.x; n < 2 * halo_q; n += kTileThreads)
+          sm[smem_pad(n)] = C{halo[2 * n], halo[2 * n + 1]};
+        q_first = halo_q;
+      }
+      for (int q0 = q_first + threadIdx.x; q0 < HALF_Q; q0 += NQ * kTileThreads) {
+        int64_t g[NQ];
+        T v[NQ][4];
+#pragma unroll
+        for (int u = 0; u < NQ; u++) {
+          const int q = q0 + u * kTileThreads;
+          g[u] = (q < HALF_Q) ? td.in0 + 4 * (int64_t)q : td.blk_hi;   // past the end: zeros
+        }
+        gather_quads<T, MODE, NQ>(a, rhs, td, g, v);
+#pragma unroll
+        for (int u = 0; u < NQ; u++) {
+          const int q = q0 + u * kTileThreads;
+          if (q < HALF_Q) {
+            sm[smem_pad(2 * q)] = C{v[u][0], v[u][1]};
+            sm[smem_pad(2 * q + 1)] = C{v[u][2], v[u][3]};
+          }
+        }
+      }
+      __syncthreads();
+      if (step + 1 < n_steps) {   // keep input samples [vstep, L) for the next tile
+        const int n0 = seg.vstep / 2;
+        for (int n = threadIdx.x; n < 2 * halo_q; n += kTileThreads) {
+          const C z = sm[smem_pad(n0 + n)];
+          halo[2 * n] = z.x;
+          halo[2 * n + 1] = z.y;
+        }
+        __syncthreads();
+      }
+    } else {
+      // pairs (quad q, quad q + MS/2): z[n] and z[n + MS] for n = 2q, 2q + 1
+      for (int q0 = threadIdx.x; q0 < HALF_Q; q0 += (NQ / 2) * kTileThreads) {
+        int64_t g[NQ];
+        T v[NQ][4];
+#pragma unroll
+        for (int u = 0; u < NQ / 2; u++) {
+          g[2 * u] = td.in0 + 4 * (int64_t)(q0 + u * kTileThreads);
+          g[2 * u + 1] = g[2 * u] + 2 * (int64_t)MS;
+        }
+        gather_quads<T, MODE, NQ>(a, rhs, td, g, v);
+#pragma unroll
+        for (int u = 0; u < NQ / 2; u++) {
+          const int q = q0 + u * kTileThreads;
+#pragma unroll
+          for (int h = 0; h < 2; h++) {
+            const int n = 2 * q + h;
+            const C z{v[2 * u][2 * h], v[2 * u][2 * h + 1]};
+            const C z2{v[2 * u + 1][2 * h], v[2 * u + 1][2 * h + 1]};
+            sm[smem_pad(n)] = (rank == 0) ? c_add(z, z2) : c_mul(c_sub(z, z2), tw(n));
+          }
+        }
+      }
+      __syncthreads();
+    }
+
+    FFT::forward(sm, tw);
+
+    // ---- pair update with the band's precomputed (a_k, b_k) in storage order ----
     for (int j = threadIdx.x; j < MS; j += kTileThreads) {
       const int k = FFT::freq_of(j);
       const int kp = (CL == 2 && rank == 1) ? (MS - 1 - k) : ((MS - k) & (MS - 1));
@@ -195,47 +341,64 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a) {
         sm[smem_pad(jp)] = C{sc * (abp.x * zp.x + abp.y * z.y), sc * (abp.x * zp.y + abp.y * z.x)};
       }
     }
-  }
-  __syncthreads();
+    __syncthreads();
 
-  FFT::inverse(sm, tw);
+    FFT::inverse(sm, tw);
 
-  // ---- scatter of the tile's valid outputs ----
-  const int64_t r_lo = td.out_lo - td.in0, r_hi = td.out_hi - td.in0;   // real offsets
-  if constexpr (CL == 1) {
-    const int n_lo = (int)(r_lo >> 1), n_hi = (int)((r_hi + 1) >> 1);
-    for (int n = n_lo + threadIdx.x; n < n_hi; n += kTileThreads) {
-      const C z = sm[smem_pad(n)];
-      const int64_t g = td.in0 + 2 * (int64_t)n;
-      pair_out<T, MODE>(a, rhs, g, g >= td.out_lo && g < td.out_hi,
-                        g + 1 >= td.out_lo && g + 1 < td.out_hi, z.x, z.y);
+    // ---- scatter of the tile's valid outputs ----
+    // output quads covering real offsets [r_lo, r_hi); rank r of a cluster owns complex indices
+    // [r MS, (r + 1) MS), i.e. quads [r MS/2, (r + 1) MS/2)
+    const int r_lo = (int)(td.out_lo - td.in0), r_hi = (int)(td.out_hi - td.in0);
+    const C* other = sm;
+    if constexpr (CL == 2) {
+      cg::cluster_group cl = cg::this_cluster();
+      if (rank == 1) {
+        for (int n = threadIdx.x; n < MS; n += kTileThreads) {
+          sm[smem_pad(n)] = c_mulc(sm[smem_pad(n)], tw(n));   // W_M^{-n} O'[n]
+        }
+      }
+      cl.sync();
+      other = cl.map_shared_rank(sm, rank ^ 1);
     }
-  } else {
-    cg::cluster_group cl = cg::this_cluster();
-    if (rank == 1) {
-      for (int n = threadIdx.x; n < MS; n += kTileThreads) {
-        sm[smem_pad(n)] = c_mulc(sm[smem_pad(n)], __ldg(tw + n));   // W_M^{-n} O'[n]
+    {
+      const int q_lo = max(r_lo >> 2, rank * HALF_Q);
+      const int q_hi = min((r_hi + 3) >> 2, (rank + 1) * HALF_Q);
+      for (int q0 = q_lo + threadIdx.x; q0 < q_hi; q0 += NQ * kTileThreads) {
+        int64_t g[NQ];
+        T y[NQ][4];
+#pragma unroll
+        for (int u = 0; u < NQ; u++) {
+          const int q = q0 + u * kTileThreads;
+          g[u] = td.in0 + 4 * (int64_t)q;
+          if (q < q_hi) {
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+              const int n = 2 * q + h - rank * MS;      // local complex index
+              C z = sm[smem_pad(n)];
+              if constexpr (CL == 2) {
+                const C o = other[smem_pad(n)];
+                z = (rank == 0) ? c_add(z, o) : c_sub(o, z);
+              }
+              y[u][2 * h] = z.x;
+              y[u][2 * h + 1] = z.y;
+            }
+          } else {
+            g[u] = td.out_hi;                          // whole quad outside the output range
+#pragma unroll
+            for (int e = 0; e < 4; e++) y[u][e] = T(0);
+          }
+        }
+        scatter_quads<T, MODE, NQ>(a, rhs, td, g, y);
       }
     }
-    cl.sync();
-    const C* other = cl.map_shared_rank(sm, rank ^ 1);
-    // complex outputs [n_lo, n_hi): rank 0 owns [0, MS), rank 1 owns [MS, 2 MS)
-    const int n_lo = (int)(r_lo >> 1), n_hi = (int)((r_hi + 1) >> 1);
-    const int lo = max(n_lo - rank * MS, 0), hi = min(n_hi - rank * MS, MS);
-    for (int n = lo + threadIdx.x; n < hi; n += kTileThreads) {
-      const C mine = sm[smem_pad(n)];
-      const C theirs = other[smem_pad(n)];
-      const C z = (rank == 0) ? c_add(mine, theirs) : c_sub(theirs, mine);
-      const int64_t g = td.in0 + 2 * ((int64_t)n + rank * MS);
-      pair_out<T, MODE>(a, rhs, g, g >= td.out_lo && g < td.out_hi,
-                        g + 1 >= td.out_lo && g + 1 < td.out_hi, z.x, z.y);
-    }
-    cl.sync();
+    if constexpr (CL == 2) cg::this_cluster().sync();
+    else __syncthreads();   // the next tile overwrites the buffer
   }
 }
 
-constexpr size_t kSmemBytes32 = (size_t)smem_pad(kM) * sizeof(float2);
-constexpr size_t kSmemBytes64 = (size_t)smem_pad(kM / 2) * sizeof(double2);
+constexpr size_t kSmemBytes32 = (size_t)(smem_pad(kM) + twiddle_tab_entries(kM)) * sizeof(float2);
+constexpr size_t kSmemMax = 227 * 1024;
+constexpr size_t kSmemBytes64 = (size_t)(smem_pad(kM / 2) + twiddle_tab_entries(kM)) * sizeof(double2);
 
 int tile_kernels_init() {
   static int done = 0;
@@ -245,8 +408,8 @@ int tile_kernels_init() {
   cudaError_t e = cudaSuccess;
 #define MM_SET(K, B)                                                                       \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(B));
-  MM_SET((k_tile<float, 1, MODE_APPLY>), kSmemBytes32);
-  MM_SET((k_tile<float, 1, MODE_RHS>), kSmemBytes32);
+  MM_SET((k_tile<float, 1, MODE_APPLY>), kSmemMax);
+  MM_SET((k_tile<float, 1, MODE_RHS>), kSmemMax);
   MM_SET((k_tile<double, 2, MODE_APPLY>), kSmemBytes64);
   MM_SET((k_tile<double, 2, MODE_RHS>), kSmemBytes64);
   MM_SET((k_tile<double, 2, MODE_NINV>), kSmemBytes64);
@@ -284,11 +447,16 @@ static cudaError_t launch_tiles(const TileArgs& a, size_t smem, cudaStream_t s) 
   return cudaLaunchKernelEx(&cfg, k_tile<T, CL, MODE>, a);
 }
 
-cudaError_t launch_tiles_fp32(int mode, const TileArgs& a, cudaStream_t s) {
-  if (mode == MODE_APPLY) return launch_tiles<float, 1, MODE_APPLY>(a, kSmemBytes32, s);
-  if (mode == MODE_RHS) return launch_tiles<float, 1, MODE_RHS>(a, kSmemBytes32, s);
+// FP32 segments; halo_samples = largest L - vstep of the segments that walk more than one tile
+cudaError_t launch_tiles_fp32(int mode, const TileArgs& a, int halo_samples, cudaStream_t s) {
+  const size_t smem = kSmemBytes32 + (size_t)halo_samples * sizeof(float);
+  if (smem > kSmemMax) return cudaErrorInvalidValue;
+  if (mode == MODE_APPLY) return launch_tiles<float, 1, MODE_APPLY>(a, smem, s);
+  if (mode == MODE_RHS) return launch_tiles<float, 1, MODE_RHS>(a, smem, s);
   return cudaErrorInvalidValue;
 }
+
+int fp32_max_halo_samples() { return (int)((kSmemMax - kSmemBytes32) / sizeof(float)); }
 
 cudaError_t launch_tiles_fp64(int mode, const TileArgs& a, cudaStream_t s) {
   if (mode == MODE_APPLY) return launch_tiles<double, 2, MODE_APPLY>(a, kSmemBytes64, s);

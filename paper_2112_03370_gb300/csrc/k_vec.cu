@@ -422,7 +422,9 @@ __global__ void k_cg_update(CgWork w) {
     s.rz_prev = s.rz;
     s.rz = t[1];
     s.beta = t[1] / s.rz_prev;
-    if (t[0] < w.tol2 * s.bnorm2) {
+    // FP32 path: pause at half the tolerance so that the FP64 check that follows usually
+    // confirms convergence at once (the recursive FP32 residual drifts from the true one)
+    if (t[0] < (w.fp32 ? 0.25 : 1.0) * w.tol2 * s.bnorm2) {
       if (w.fp32) {
         s.paused = 1;   // confirm with the FP64 true residual before stopping
       } else {

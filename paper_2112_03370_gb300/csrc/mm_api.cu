@@ -82,7 +82,7 @@ void free_plan(Plan* P) {
   if (P->stream) cudaStreamSynchronize(P->stream);
   dfree(P->lpix); dfree(P->psi); dfree(P->w64); dfree(P->obs_to_global); dfree(P->minv);
   dfree(P->band); dfree(P->block_off_dev); dfree(P->c0_blk); dfree(P->tab32); dfree(P->tab64);
-  dfree(P->tw32); dfree(P->tw64); dfree(P->tiles); dfree(P->map32_in); dfree(P->map32_out);
+  dfree(P->tw32); dfree(P->tw64); dfree(P->tiles); dfree(P->segs); dfree(P->map32_in); dfree(P->map32_out);
   dfree(P->map64_in); dfree(P->map64_out); dfree(P->td_a); dfree(P->td_b);
   free_cg(reinterpret_cast<CgState*>(P->cg));
   if (P->stream) cudaStreamDestroy(P->stream);
@@ -158,27 +158,45 @@ BandTables dedupe_bands(const std::vector<double>& band, int nb, int lam) {
   return t;
 }
 
-// Overlap-save tiles of every block: consecutive output ranges of V' = L - 2 lambda - 4 samples;
-// each tile's input window starts at a multiple of 4 at most lambda + 3 samples before its output.
-std::vector<TileDesc> make_tiles(const std::vector<int64_t>& off, const BandTables& bt, int lam) {
+// Overlap-save tiles of every block.  A block of n samples gets t = ceil(n / vmax) tiles with
+// vmax = L - 2 lambda - 4 rounded down to a multiple of 4, all with the same output step
+// vstep = ceil(n / t) rounded up to a multiple of 4 (so no tile is nearly empty).  Each tile's
+// input window starts at a multiple of 4 at most lambda + 3 samples before its first output.
+// Tiles are grouped into segments of up to `max_steps` consecutive tiles (one CTA walks a
+// segment and keeps the overlap of consecutive windows); max_steps = 1 gives single tiles.
+std::vector<TileDesc> make_tiles(const std::vector<int64_t>& off, const BandTables& bt, int lam,
+                                 int max_steps, int max_halo, int32_t* halo_out) {
   std::vector<TileDesc> tiles;
-  const int64_t vstep = (int64_t)kL - 2 * (int64_t)lam - 4;
+  const int64_t vmax = ((int64_t)kL - 2 * (int64_t)lam - 4) & ~(int64_t)3;
   const int nb = (int)off.size() - 1;
+  int32_t halo_used = 0;
   for (int b = 0; b < nb; b++) {
-    const int64_t lo = off[b], hi = off[b + 1];
-    for (int64_t o = lo; o < hi; o += vstep) {
+    const int64_t lo = off[b], hi = off[b + 1], n = hi - lo;
+    if (n <= 0) continue;
+    const int64_t nt = (n + vmax - 1) / vmax;
+    const int64_t vstep = (((n + nt - 1) / nt) + 3) & ~(int64_t)3;
+    const int64_t halo = (int64_t)kL - vstep;
+    const int64_t steps_cap = (halo <= max_halo) ? max_steps : 1;
+    const int64_t nseg = (nt + steps_cap - 1) / steps_cap;
+    const int64_t per = (nt + nseg - 1) / nseg;
+    for (int64_t t0 = 0; t0 < nt; t0 += per) {
+      const int64_t t1 = std::min(t0 + per, nt);
       TileDesc td{};
-      const int64_t start = o - lam;
+      td.out_lo = lo + t0 * vstep;
+      td.out_hi = std::min(lo + t1 * vstep, hi);
+      const int64_t start = td.out_lo - lam;
       td.in0 = (start >= 0) ? (start & ~(int64_t)3) : -((-start + 3) & ~(int64_t)3);
-      td.out_lo = o;
-      td.out_hi = std::min(o + vstep, hi);
       td.blk_lo = lo;
       td.blk_hi = hi;
       td.tab = bt.blk_tab[b];
       td.scale = bt.blk_scale[b];
+      td.n_steps = (int32_t)(t1 - t0);
+      td.vstep = (int32_t)vstep;
+      if (td.n_steps > 1) halo_used = std::max(halo_used, (int32_t)halo);
       tiles.push_back(td);
     }
   }
+  if (halo_out) *halo_out = halo_used;
   return tiles;
 }
 
@@ -190,6 +208,7 @@ int validate_desc(const mm_problem_desc* d) {
   if (d->lambda < 0 || d->lambda > kMaxLambda)
     return fail(MM_EINVAL, "lambda must lie in [0, " + std::to_string(kMaxLambda) + "]");
   if (!d->pix || !d->psi || !d->band) return fail(MM_EINVAL, "pix, psi and band must be non-NULL");
+  if (d->tile_steps < 0) return fail(MM_EINVAL, "tile_steps must be >= 0");
   if (d->precision != MM_FP64 && d->precision != MM_FP32) return fail(MM_EINVAL, "bad precision");
   if (d->toeplitz_algo != MM_TPLZ_AUTO && d->toeplitz_algo != MM_TPLZ_FFT &&
       d->toeplitz_algo != MM_TPLZ_DIRECT)
@@ -347,10 +366,18 @@ int build_plan(const mm_problem_desc* d, cudaStream_t us, Plan* P) {
   std::vector<double> Hh((size_t)P->n_tab * (kM + 1));
   MM_CUDA(cudaMemcpyAsync(Hh.data(), H, Hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
 
-  std::vector<TileDesc> tiles = make_tiles(P->block_off, bt, lam);
+  std::vector<TileDesc> tiles = make_tiles(P->block_off, bt, lam, 1, 0, nullptr);
   P->n_tiles = (int64_t)tiles.size();
   MM_TRY(dalloc(P, &P->tiles, tiles.size()));
   MM_CUDA(cudaMemcpyAsync(P->tiles, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, s));
+  // FP32 segments: enough of them to keep every SM busy (about 8 per SM), at most 16 tiles each
+  const int64_t steps = d->tile_steps > 0 ? d->tile_steps
+                                           : std::max<int64_t>(1, std::min<int64_t>(16, P->n_tiles / (8 * 152)));
+  std::vector<TileDesc> segs = make_tiles(P->block_off, bt, lam, (int)steps, fp32_max_halo_samples(),
+                                          &P->seg_halo);
+  P->n_segs = (int64_t)segs.size();
+  MM_TRY(dalloc(P, &P->segs, segs.size()));
+  MM_CUDA(cudaMemcpyAsync(P->segs, segs.data(), segs.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, s));
   MM_CUDA(cudaStreamSynchronize(s));
 
   // the band's symbol sampled on the tile's circulant must be positive (A is then SPD)
@@ -432,6 +459,8 @@ int apply64_internal(Plan* P, const double* x4, double* y4, int nrhs, cudaStream
 int apply32_internal(Plan* P, const float* x32, float* y32, int nrhs, cudaStream_t s,
                      const int32_t* done = nullptr, int done_stride = 0) {
   TileArgs a = base_args(P, true);
+  a.tiles = P->segs;
+  a.n_tiles = P->n_segs;
   a.nrhs = nrhs;
   a.x = x32;
   a.x_stride = P->n_obs * 4;
@@ -439,7 +468,7 @@ int apply32_internal(Plan* P, const float* x32, float* y32, int nrhs, cudaStream
   a.y_stride = P->n_obs * 4;
   a.done = done;
   a.done_stride = done_stride;
-  MM_CUDA(launch_tiles_fp32(MODE_APPLY, a, s));
+  MM_CUDA(launch_tiles_fp32(MODE_APPLY, a, P->seg_halo, s));
   return MM_OK;
 }
 
@@ -677,8 +706,8 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
   MM_CUDA(launch_cg(CG_INIT, w, s));
 
   // graph of `chunk` iterations, cached on the plan
-  if (!c->exec || c->g_nrhs != nrhs || c->g_fp32 != (int)fp32 || c->g_chunk != chunk ||
-      c->g_tol2 != w.tol2 || c->g_maxit != opts->max_iter) {
+  if (opts->profile == 0 && (!c->exec || c->g_nrhs != nrhs || c->g_fp32 != (int)fp32 || c->g_chunk != chunk ||
+      c->g_tol2 != w.tol2 || c->g_maxit != opts->max_iter)) {
     if (c->exec) {
       cudaGraphExecDestroy(c->exec);
       c->exec = nullptr;
@@ -701,9 +730,56 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
   }
 
   std::vector<int> timed_out(nrhs, 0);
+  const bool profile = opts->profile != 0;
+  int64_t n_kernels = 2;   // pack + init
+  // profile mode: event pairs around every tile launch, summed at each host sync
+  struct EvPair { cudaEvent_t a, b; int is64; };
+  std::vector<EvPair> pool, pending;
+  double t32 = 0.0, t64 = 0.0;
+  int n32 = 0, n64 = 0;
+  auto take_pair = [&](int is64, EvPair* out) -> int {
+    if (pool.empty()) {
+      EvPair e{};
+      MM_CUDA(cudaEventCreate(&e.a));
+      MM_CUDA(cudaEventCreate(&e.b));
+      pool.push_back(e);
+    }
+    *out = pool.back();
+    pool.pop_back();
+    out->is64 = is64;
+    return MM_OK;
+  };
+  auto drain = [&]() -> int {
+    for (EvPair& e : pending) {
+      float ms = 0.f;
+      MM_CUDA(cudaEventElapsedTime(&ms, e.a, e.b));
+      if (e.is64) { t64 += ms; n64++; } else { t32 += ms; n32++; }
+      pool.push_back(e);
+    }
+    pending.clear();
+    return MM_OK;
+  };
+  auto timed_apply64 = [&](const int32_t* done_flags) -> int {
+    EvPair e{};
+    if (profile) {
+      MM_TRY(take_pair(1, &e));
+      MM_CUDA(cudaEventRecord(e.a, s));
+    }
+    MM_TRY(apply64_internal(P, c->x, c->q, nrhs, s, done_flags, done_flags ? kScalStrideInts : 0));
+    if (profile) {
+      MM_CUDA(cudaEventRecord(e.b, s));
+      pending.push_back(e);
+    } else {
+      n64++;
+    }
+    n_kernels += (P->algo == MM_TPLZ_DIRECT) ? 3 * nrhs : 1;
+    return MM_OK;
+  };
+  const int32_t* halt = reinterpret_cast<const int32_t*>(c->scal) + kHaltOffsetInts;
   while (true) {
     MM_CUDA(cudaMemcpyAsync(c->scal_host, c->scal, nrhs * sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
     MM_CUDA(cudaStreamSynchronize(s));
+    MM_TRY(drain());
     bool all_done = true, need_rep = false;
     for (int r = 0; r < nrhs; r++) {
       const CgScalars& sc = c->scal_host[r];
@@ -720,21 +796,55 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
     if (need_rep) {
       // residual replacement: r = b - A x with A in FP64
       MM_CUDA(cudaMemsetAsync(c->q, 0, (size_t)nrhs * P->n_obs * 4 * sizeof(double), s));
-      MM_TRY(apply64_internal(P, c->x, c->q, nrhs, s,
-                              reinterpret_cast<const int32_t*>(c->scal) + kDoneOffsetInts, kScalStrideInts));
+      MM_TRY(timed_apply64(reinterpret_cast<const int32_t*>(c->scal) + kDoneOffsetInts));
       MM_CUDA(launch_cg(CG_REPLACE, w, s));
+      n_kernels += 1;
       continue;
     }
-    MM_CUDA(cudaGraphLaunch(c->exec, s));
+    if (!profile) {
+      MM_CUDA(cudaGraphLaunch(c->exec, s));
+      n_kernels += (int64_t)chunk * (fp32 || P->algo != MM_TPLZ_DIRECT ? 4 : 3 + 3 * nrhs);
+      if (fp32) n32 += chunk; else n64 += chunk;
+    } else {
+      for (int k = 0; k < chunk; k++) {
+        MM_CUDA(launch_cg(CG_PUPDATE, w, s));
+        EvPair e{};
+        MM_TRY(take_pair(fp32 ? 0 : 1, &e));
+        MM_CUDA(cudaEventRecord(e.a, s));
+        if (fp32) {
+          MM_TRY(apply32_internal(P, w.p32, w.q32, nrhs, s, halt, kScalStrideInts));
+        } else {
+          MM_TRY(apply64_internal(P, w.p, w.q, nrhs, s, halt, kScalStrideInts));
+        }
+        MM_CUDA(cudaEventRecord(e.b, s));
+        pending.push_back(e);
+        MM_CUDA(launch_cg(CG_DOT_PQ, w, s));
+        MM_CUDA(launch_cg(CG_UPDATE, w, s));
+        n_kernels += (fp32 || P->algo != MM_TPLZ_DIRECT) ? 4 : 3 + 3 * nrhs;
+      }
+    }
   }
 
-  // true residual ||b - A x|| in FP64 for the report
-  MM_CUDA(cudaMemsetAsync(c->q, 0, (size_t)nrhs * P->n_obs * 4 * sizeof(double), s));
-  MM_TRY(apply64_internal(P, c->x, c->q, nrhs, s));
-  MM_CUDA(launch_cg(CG_TRUE_RES, w, s));
+  // true residual ||b - A x|| in FP64 for the report.  On the FP32 path a column can only
+  // finish with MM_OK through a residual replacement, which already measured it at the final x.
+  bool need_true = !fp32;
+  for (int r = 0; r < nrhs; r++)
+    if (!(c->scal_host[r].done && c->scal_host[r].status == MM_OK)) need_true = true;
+  if (need_true) {
+    MM_CUDA(cudaMemsetAsync(c->q, 0, (size_t)nrhs * P->n_obs * 4 * sizeof(double), s));
+    MM_TRY(timed_apply64(nullptr));
+    MM_CUDA(launch_cg(CG_TRUE_RES, w, s));
+    n_kernels += 1;
+  }
   MM_CUDA(launch_unpack4to3(c->x, P->n_obs, nrhs, x, s));
+  n_kernels += 1;
   MM_CUDA(cudaMemcpyAsync(c->scal_host, c->scal, nrhs * sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
   MM_CUDA(cudaStreamSynchronize(s));
+  MM_TRY(drain());
+  for (EvPair& e : pool) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
   MM_CUDA(cudaEventRecord(ev, s));
   MM_CUDA(cudaStreamWaitEvent(us, ev, 0));
   cudaEventDestroy(ev);
@@ -749,6 +859,11 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
     in.true_rel_res = sc.bnorm2 > 0 ? std::sqrt(sc.rr_true / sc.bnorm2) : 0.0;
     in.t_ms = t_ms;
     in.n_true_res = sc.n_true;
+    in.t_apply32_ms = t32;
+    in.t_apply64_ms = t64;
+    in.n_apply32 = n32;
+    in.n_apply64 = n64;
+    in.n_kernels = n_kernels;
     int st = sc.status;
     if (st == MM_OK && !sc.done) st = timed_out[r] ? MM_ETIMEOUT : MM_ENOTCONV;
     in.status = st;

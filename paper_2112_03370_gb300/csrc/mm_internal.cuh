@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/mm.h"
+#include "mm.h"
 
 namespace mm {
 
@@ -24,15 +24,22 @@ constexpr int kCl32 = 1;                  // FP32: one CTA holds the whole tile 
 constexpr int kCl64 = 2;                  // FP64: a 2-CTA cluster holds it (2 x 128 KB smem)
 constexpr int kTileThreads = 512;
 
+// A segment of n_steps consecutive overlap-save tiles of one block.  Tile k of the segment reads
+// input samples [in0 + k vstep, in0 + k vstep + L) and writes outputs
+// [out_lo + k vstep, min(out_lo + (k + 1) vstep, out_hi)).  Consecutive tiles overlap by
+// L - vstep input samples, which the FP32 kernel keeps in shared memory instead of gathering
+// them again.
 struct TileDesc {
-  int64_t in0;      // global sample index of the tile's first input sample (multiple of 4)
-  int64_t out_lo;   // output range [out_lo, out_hi) of this tile
+  int64_t in0;      // global sample index of the first tile's first input sample (multiple of 4)
+  int64_t out_lo;   // output range [out_lo, out_hi) of the whole segment
   int64_t out_hi;
   int64_t blk_lo;   // the block's sample range: samples outside read as 0
   int64_t blk_hi;
   int32_t tab;      // spectrum table id
-  int32_t pad_;
+  int32_t n_steps;  // tiles in the segment (1 on the FP64 path)
   double scale;     // block band / table band
+  int32_t vstep;    // output samples per tile (multiple of 4)
+  int32_t pad_;
 };
 
 enum Mode { MODE_APPLY = 0, MODE_RHS = 1, MODE_NINV = 2 };
@@ -84,8 +91,11 @@ struct Plan {
   double2* tab64 = nullptr;            // [n_tab][M]
   float2* tw32 = nullptr;              // [M]
   double2* tw64 = nullptr;             // [M]
-  TileDesc* tiles = nullptr;
+  TileDesc* tiles = nullptr;           // FP64 tiles (one per descriptor)
   int64_t n_tiles = 0;
+  TileDesc* segs = nullptr;            // FP32 segments (several tiles per descriptor)
+  int64_t n_segs = 0;
+  int32_t seg_halo = 0;                // largest L - vstep over the segments (samples)
 
   // work buffers (grown on demand)
   float* map32_in = nullptr;  size_t map32_in_cap = 0;
@@ -154,9 +164,10 @@ cudaError_t launch_pair_tables(const double* H, int32_t n_tab, const double* cos
 cudaError_t launch_twiddles(double2* tw64, float2* tw32, const double* costab, cudaStream_t s);
 
 // Toeplitz-tile kernels (k_toeplitz.cu)
-cudaError_t launch_tiles_fp32(int mode, const TileArgs& a, cudaStream_t s);
+cudaError_t launch_tiles_fp32(int mode, const TileArgs& a, int halo_samples, cudaStream_t s);
 cudaError_t launch_tiles_fp64(int mode, const TileArgs& a, cudaStream_t s);
 int tile_kernels_init();   // sets smem attributes once per process
+int fp32_max_halo_samples();   // largest halo the FP32 segment kernel can keep in shared memory
 
 // direct / elementwise kernels (k_vec.cu)
 cudaError_t launch_toeplitz_direct(const double* band, const int64_t* block_off, int32_t n_blocks,

@@ -34,20 +34,23 @@ class ProblemDesc(ctypes.Structure):
                 ("pix", ctypes.c_void_p), ("psi", ctypes.c_void_p), ("lambda_", ctypes.c_int32),
                 ("band", ctypes.c_void_p), ("cond_max", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("toeplitz_algo", ctypes.c_int32),
-                ("inputs_on_device", ctypes.c_int32)]
+                ("inputs_on_device", ctypes.c_int32), ("tile_steps", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("precond", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("reliable_every", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("deadline_us", ctypes.c_int64)]
+                ("profile", ctypes.c_int32), ("deadline_us", ctypes.c_int64)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("rel_res", ctypes.c_double),
                 ("true_rel_res", ctypes.c_double), ("t_ms", ctypes.c_double),
-                ("n_true_res", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("n_true_res", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("t_apply32_ms", ctypes.c_double), ("t_apply64_ms", ctypes.c_double),
+                ("n_apply32", ctypes.c_int32), ("n_apply64", ctypes.c_int32),
+                ("n_kernels", ctypes.c_int64)]
 
 
 class MMError(RuntimeError):
@@ -140,7 +143,8 @@ class Plan:
 
 def mm_plan(n_det: int, n_int: int, block_len: Sequence[int], n_pix: int, pix: torch.Tensor,
             psi: torch.Tensor, lam: int, band: torch.Tensor, cond_max: float = 1e3,
-            precision: int = MM_FP64, toeplitz_algo: int = MM_TPLZ_AUTO, stream=None) -> Plan:
+            precision: int = MM_FP64, toeplitz_algo: int = MM_TPLZ_AUTO, tile_steps: int = 0,
+            stream=None) -> Plan:
     """Build a plan.  pix/psi/band are either all CUDA tensors or all CPU tensors."""
     on_dev = pix.is_cuda
     if (psi.is_cuda != on_dev) or (band.is_cuda != on_dev):
@@ -153,7 +157,7 @@ def mm_plan(n_det: int, n_int: int, block_len: Sequence[int], n_pix: int, pix: t
     d = ProblemDesc(n_det=n_det, n_int=n_int, block_len=bl, n_pix=n_pix, pix=_ptr(pix),
                     psi=_ptr(psi), lambda_=lam, band=_ptr(band), cond_max=cond_max,
                     precision=precision, toeplitz_algo=toeplitz_algo,
-                    inputs_on_device=1 if on_dev else 0)
+                    inputs_on_device=1 if on_dev else 0, tile_steps=tile_steps)
     h = ctypes.c_void_p()
     _check(_lib.mm_plan(ctypes.byref(d), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)))
     n_obs = ctypes.c_int64()
@@ -220,13 +224,14 @@ def mm_precond(plan: Plan, r: torch.Tensor, z: torch.Tensor, stream=None):
 
 def mm_pcg_solve(plan: Plan, b: torch.Tensor, x: torch.Tensor, tol: float = 1e-6,
                  max_iter: int = 10000, precision: int = MM_FP64, reliable_every: int = 0,
-                 check_every: int = 0, deadline_us: int = 0, stream=None, raise_on_error=True):
+                 check_every: int = 0, deadline_us: int = 0, profile: bool = False, stream=None,
+                 raise_on_error=True):
     """Solve A x = b (b, x: [nrhs, n_obs, 3] or [n_obs, 3]); returns a list of SolveInfo."""
     _dev(b, torch.float64, "b"); _dev(x, torch.float64, "x")
     nrhs = 1 if b.dim() <= 2 else b.shape[0]
     opts = SolveOpts(tol=tol, max_iter=max_iter, precond=MM_PREC_BD, precision=precision,
                      reliable_every=reliable_every, check_every=check_every,
-                     deadline_us=deadline_us)
+                     profile=1 if profile else 0, deadline_us=deadline_us)
     infos = (SolveInfo * nrhs)()
     code = _lib.mm_pcg_solve(ctypes.c_void_p(plan.handle), _ptr(b), _ptr(x), nrhs,
                              ctypes.byref(opts), infos, _stream_ptr(stream))

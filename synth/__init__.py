@@ -327,22 +327,24 @@ def make_ground_problem(cfg: GroundConfig, device="cpu", with_noise: bool = True
         reals = []
         for r in range(n_real):
             dd = torch.zeros(pix.numel(), dtype=torch.float64, device=dev)
-            if with_signal:
-                ok = pix >= 0
-                pl = pix.clamp(min=0).long()
-                two = 2.0 * psi.to(torch.float64)
-                sig_t = m[pl, 0] + torch.cos(two) * m[pl, 1] + torch.sin(two) * m[pl, 2]
-                dd += torch.where(ok, sig_t, torch.zeros_like(sig_t))
+            gn = None
             if with_noise:
                 stream = 100 + r + real_offset
                 gn = torch.Generator(device=dev).manual_seed(seed_for(cfg.config_id, stream)
-                                                              + 7919 * d0)
-                for j in range(n_det):
-                    for k in range(cfg.n_int):
-                        b = j * cfg.n_int + k
-                        lo = b * cfg.n_samp
-                        dd[lo:lo + cfg.n_samp] += noise_block(cfg.n_samp, cfg.fs, float(sig[j]),
-                                                              cfg.f_knee, cfg.alpha, gn, dev)
+                                                             + 7919 * d0)
+            for j in range(n_det):
+                for k in range(cfg.n_int):
+                    lo = (j * cfg.n_int + k) * cfg.n_samp
+                    hi = lo + cfg.n_samp
+                    if with_signal:
+                        pb = pix[lo:hi]
+                        pl = pb.clamp(min=0).long()
+                        two = 2.0 * psi[lo:hi].to(torch.float64)
+                        sig_t = m[pl, 0] + torch.cos(two) * m[pl, 1] + torch.sin(two) * m[pl, 2]
+                        dd[lo:hi] += torch.where(pb >= 0, sig_t, torch.zeros_like(sig_t))
+                    if with_noise:
+                        dd[lo:hi] += noise_block(cfg.n_samp, cfg.fs, float(sig[j]), cfg.f_knee,
+                                                 cfg.alpha, gn, dev)
             reals.append(dd)
         d = reals[0] if n_real == 1 else torch.stack(reals)
     return Problem(n_det=n_det, n_int=cfg.n_int, block_len=block_len, n_pix=cfg.n_pix, pix=pix,

@@ -102,9 +102,12 @@ def test_apply_A_fp64_matches_oracle(algo):
     assert rel_max(y.cpu().numpy(), O.apply_A(op, x)) < 1e-11
 
 
-def test_apply_A_fp32_matches_oracle():
+@pytest.mark.parametrize("tile_steps", [1, 2, 5])
+def test_apply_A_fp32_matches_oracle(tile_steps):
+    # blocks of 70001 / 33000 / 40000 samples span several tiles: tile_steps > 1 walks them with
+    # the overlap kept in shared memory
     prob = small(6)
-    gp, op, _ = plans(prob, precision=1)
+    gp, op, _ = plans(prob, precision=1, tile_steps=tile_steps)
     x = np.random.default_rng(6).standard_normal((op.n_obs, 3))
     y = torch.empty(op.n_obs, 3, dtype=torch.float64, device="cuda")
     mm().mm_apply_A(gp, cuda(x), y)
@@ -158,8 +161,11 @@ def test_pcg_fp64_tiny_config_matches_oracle(tiny_cfg):
     assert info.true_rel_res < 10 * cfg.tol
 
 
-def test_pcg_fp32_mixed_tiny_config_matches_oracle(tiny_cfg):
+@pytest.mark.parametrize("tile_steps", [0, 3])
+def test_pcg_fp32_mixed_tiny_config_matches_oracle(tiny_cfg, tile_steps):
     cfg, prob, gp, op, nb, b_or, ref = tiny_cfg
+    if tile_steps:
+        gp, _, _ = plans(prob, tile_steps=tile_steps)
     b = cuda(b_or)
     x = torch.empty_like(b)
     info = mm().mm_pcg_solve(gp, b, x, tol=cfg.tol, max_iter=5000, precision=1)[0]
