@@ -165,6 +165,23 @@ int mm_rhs(mm_plan_t plan, const void* d, int d_is_fp32, int nrhs, double* b, vo
 /* y = A x = P~^T N^-1 P~ x (Sect. 3.2, right to left) for nrhs vectors, in the plan's precision. */
 int mm_apply_A(mm_plan_t plan, const double* x, double* y, int nrhs, void* stream);
 
+/* Same as mm_apply_A, for callers that cannot allocate device memory (a fixed memory pool or
+ * arena, a real-time loop, a host that accounts for all device memory itself).  The paper has
+ * no counterpart: it is an interface choice of this library.  mm_apply_A grows plan-owned
+ * working buffers with cudaMalloc on first use; this call instead uses one array of 32 MiB
+ * compiled into the library, held by every GPU that loads it until the process exits, and calls
+ * no cudaMalloc, cudaFree or other allocating routine.  Limits and rules:
+ *   - nrhs * n_obs * 4 values of the plan's precision, twice (input and output), must fit in
+ *     32 MiB (FP64: nrhs * n_obs <= 524,288; FP32: <= 1,048,576), else MM_EINVAL with a message;
+ *   - FFT plans only (MM_TPLZ_DIRECT needs an N-sample buffer): MM_EINVAL otherwise;
+ *   - every call shares the array and leaves its contents behind (each call clears what it
+ *     accumulates), so calls whose GPU work overlaps (several streams or threads) race: the
+ *     caller must serialise them;
+ *   - the plan's device must be current; the first call on a device looks up the array's
+ *     device address, so make it before any stream capture is under way on that device.
+ * x, y: [nrhs][n_obs][3] float64 device arrays, as for mm_apply_A.  Asynchronous on stream. */
+int mm_apply_A_noalloc(mm_plan_t plan, const double* x, double* y, int nrhs, void* stream);
+
 /* z = M_BD r (block-Jacobi, Sect. 3.2) for nrhs vectors. */
 int mm_precond(mm_plan_t plan, const double* r, double* z, int nrhs, void* stream);
 

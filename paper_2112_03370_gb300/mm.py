@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "MM_OK", 1: "MM_EINVAL", 2: "MM_ENOMEM", 3: "MM_ENOTSPD", 4: 
 
 # the exported entry points of include/mm.h
 EXPORTS = ("mm_plan", "mm_plan_query", "mm_plan_destroy", "mm_apply_P", "mm_apply_Pt",
-           "mm_apply_Ninv", "mm_rhs", "mm_apply_A", "mm_precond", "mm_pcg_solve", "mm_last_error")
+           "mm_apply_Ninv", "mm_rhs", "mm_apply_A", "mm_precond", "mm_pcg_solve", "mm_last_error",
+           "mm_apply_A_noalloc")
 
 
 class ProblemDesc(ctypes.Structure):
@@ -73,6 +74,7 @@ def _load():
         getattr(lib, name).argtypes = [vp, vp, vp, vp]
     lib.mm_rhs.argtypes = [vp, vp, i32, i32, vp, vp]
     lib.mm_apply_A.argtypes = [vp, vp, vp, i32, vp]
+    lib.mm_apply_A_noalloc.argtypes = [vp, vp, vp, i32, vp]
     lib.mm_precond.argtypes = [vp, vp, vp, i32, vp]
     lib.mm_pcg_solve.argtypes = [vp, vp, vp, i32, ctypes.POINTER(SolveOpts),
                                  ctypes.POINTER(SolveInfo), vp]
@@ -214,6 +216,15 @@ def mm_apply_A(plan: Plan, x: torch.Tensor, y: torch.Tensor, stream=None):
     _dev(x, torch.float64, "x"); _dev(y, torch.float64, "y")
     nrhs = 1 if x.dim() <= 2 else x.shape[0]
     _check(_lib.mm_apply_A(ctypes.c_void_p(plan.handle), _ptr(x), _ptr(y), nrhs, _stream_ptr(stream)))
+
+
+def mm_apply_A_noalloc(plan: Plan, x: torch.Tensor, y: torch.Tensor, stream=None):
+    """y = A x without any device allocation by the library (working space is a fixed 32 MiB
+    array inside libmm; see include/mm.h for the size limit and the no-overlap rule)."""
+    _dev(x, torch.float64, "x"); _dev(y, torch.float64, "y")
+    nrhs = 1 if x.dim() <= 2 else x.shape[0]
+    _check(_lib.mm_apply_A_noalloc(ctypes.c_void_p(plan.handle), _ptr(x), _ptr(y), nrhs,
+                                   _stream_ptr(stream)))
 
 
 def mm_precond(plan: Plan, r: torch.Tensor, z: torch.Tensor, stream=None):
