@@ -191,6 +191,23 @@ int mm_precond(mm_plan_t plan, const double* r, double* z, int nrhs, void* strea
 int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_solve_opts* opts,
                  mm_solve_info* info, void* stream);
 
+/* Solve A X = B for nrhs right-hand sides by block conjugate gradients: Algorithm 2 (Sect. 3.2)
+ * in its block Orthomin form, applied with R_0 = [b_1 .. b_s] (s independent right-hand sides,
+ * e.g. noise realisations, instead of one right-hand side split over subdomains):
+ *   P_k = Z_k (Z_k^T A Z_k)^{-1/2} through a pivoted Cholesky factor (directions that became
+ *   dependent are dropped; the paper leaves this case open), alpha_k = P_k^T R_{k-1},
+ *   X_k = X_{k-1} + P_k alpha_k, R_k = R_{k-1} - A P_k alpha_k,
+ *   Z_{k+1} = (I - P_k P_k^T A) M_BD R_k over the columns not yet converged.
+ * The nrhs columns are solved in groups of block_width (0: min(nrhs, 64); at most 64), each group
+ * sharing one batched A-application per iteration.  opts->precision selects FP32 or FP64
+ * operators; the search blocks are FP32, X, R and the block_width x block_width matrices FP64.
+ * A column stops when ||R_j|| < tol ||b_j||, confirmed by an FP64 true residual; columns above tol
+ * restart from their true residual.  b, x: [nrhs][n_obs][3] device; info: HOST [nrhs]
+ * (iters = block iterations to convergence).  Blocks the calling thread.  Returns the worst
+ * per-column status (MM_ENOTCONV after opts->max_iter block iterations, MM_EBREAKDOWN). */
+int mm_block_cg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, int block_width,
+                      const mm_solve_opts* opts, mm_solve_info* info, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* mm_last_error(void);
 

@@ -1,0 +1,348 @@
+// Block conjugate gradients on s right-hand sides (Algorithm 2 in its block Orthomin form with
+// R_0 = [b_1 .. b_s]): tall-skinny block products and the small dense steps.
+//
+// Layouts: a block of t pixel-domain vectors is [t][n][4] (IQU + pad per pixel, pad = 0).
+// Search blocks (Z, A Z, P, A P, M R) are float32; X, R and every t x t matrix are float64.
+// Tall-skinny products run on the FP32 units (GB300's FP64 rate is 1/64 of FP32) with FP64
+// accumulation across CTAs; the solver's accuracy is restored by FP64 residual checks.
+#include "mm_block.cuh"
+#include "mm_internal.cuh"
+
+namespace mm {
+
+namespace {
+constexpr int kNT = 256;
+constexpr int kChunk = 16;    // pixels staged in shared memory per step of a Gram CTA
+}  // namespace
+
+// out_part[blk][i][j] = sum over this CTA's pixels of <A_i, B_j> (3 components), FP32 products,
+// FP64 per-CTA totals.  ta, tb <= kMaxBlk.  A, B are float4 blocks or float64 blocks (B may be
+// FP64: R); A_i selected through idx_a (or identity when null).
+template <typename TB>
+__global__ void __launch_bounds__(kNT) k_bgram(const float4* __restrict__ A, int ta,
+                                                const int* __restrict__ idx_a,
+                                                const TB* __restrict__ B, int tb,
+                                                const int* __restrict__ idx_b, int64_t n,
+                                                double* __restrict__ out_part) {
+  __shared__ float sa[kChunk][kMaxBlk * 3 + 1];
+  __shared__ float sb[kChunk][kMaxBlk * 3 + 1];
+  const int npair = ta * tb;
+  float acc[kMaxBlk * kMaxBlk / kNT];
+#pragma unroll
+  for (int u = 0; u < kMaxBlk * kMaxBlk / kNT; u++) acc[u] = 0.f;
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t p0 = (int64_t)blockIdx.x * per, p1 = min(n, p0 + per);
+  for (int64_t base = p0; base < p1; base += kChunk) {
+    const int cnt = (int)min((int64_t)kChunk, p1 - base);
+    for (int e = threadIdx.x; e < kChunk * ta; e += kNT) {
+      const int r = e % kChunk, i = e / kChunk;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < cnt) v = A[(int64_t)(idx_a ? idx_a[i] : i) * n + base + r];
+      sa[r][3 * i] = v.x; sa[r][3 * i + 1] = v.y; sa[r][3 * i + 2] = v.z;
+    }
+    for (int e = threadIdx.x; e < kChunk * tb; e += kNT) {
+      const int r = e % kChunk, j = e / kChunk;
+      float x = 0.f, y = 0.f, z = 0.f;
+      if (r < cnt) {
+        const int64_t col = idx_b ? idx_b[j] : j;
+        if constexpr (sizeof(TB) == sizeof(float4)) {
+          const float4 v = reinterpret_cast<const float4*>(B)[col * n + base + r];
+          x = v.x; y = v.y; z = v.z;
+        } else {
+          const double* v = reinterpret_cast<const double*>(B) + 4 * (col * n + base + r);
+          x = (float)v[0]; y = (float)v[1]; z = (float)v[2];
+        }
+      }
+      sb[r][3 * j] = x; sb[r][3 * j + 1] = y; sb[r][3 * j + 2] = z;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kMaxBlk * kMaxBlk / kNT; u++) {
+      const int pr = threadIdx.x + u * kNT;
+      if (pr < npair) {
+        const int i = pr / tb, j = pr % tb;
+        float s = 0.f;
+        for (int r = 0; r < cnt; r++)
+          s += sa[r][3 * i] * sb[r][3 * j] + sa[r][3 * i + 1] * sb[r][3 * j + 1] +
+               sa[r][3 * i + 2] * sb[r][3 * j + 2];
+        acc[u] += s;
+      }
+    }
+    __syncthreads();
+  }
+  double* o = out_part + (int64_t)blockIdx.x * kMaxBlk * kMaxBlk;
+#pragma unroll
+  for (int u = 0; u < kMaxBlk * kMaxBlk / kNT; u++) {
+    const int pr = threadIdx.x + u * kNT;
+    if (pr < npair) o[pr] = (double)acc[u];
+  }
+}
+
+// G[i][j] = sum over CTAs of out_part (fixed order: deterministic)
+__global__ void k_bgram_reduce(const double* __restrict__ part, int nblk, int npair,
+                               double* __restrict__ G) {
+  const int pr = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pr >= npair) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; b++) s += part[(int64_t)b * kMaxBlk * kMaxBlk + pr];
+  G[pr] = s;
+}
+
+cudaError_t launch_bgram(const float* A, int ta, const int* idx_a, const void* B, int b_is_fp64,
+                         int tb, const int* idx_b, int64_t n, double* part, int nblk, double* G,
+                         cudaStream_t s) {
+  if (ta <= 0 || tb <= 0) return cudaSuccess;
+  if (ta > kMaxBlk || tb > kMaxBlk) return cudaErrorInvalidValue;
+  if (b_is_fp64)
+    k_bgram<double4_16a><<<nblk, kNT, 0, s>>>(reinterpret_cast<const float4*>(A), ta, idx_a,
+                                              reinterpret_cast<const double4_16a*>(B), tb, idx_b, n, part);
+  else
+    k_bgram<float4><<<nblk, kNT, 0, s>>>(reinterpret_cast<const float4*>(A), ta, idx_a,
+                                         reinterpret_cast<const float4*>(B), tb, idx_b, n, part);
+  k_bgram_reduce<<<(ta * tb + 255) / 256, 256, 0, s>>>(part, nblk, ta * tb, G);
+  return cudaGetLastError();
+}
+
+// out_j (+)= sign * sum_i A_i C[i][j] for j < v (A: float32 [t][n]; C: FP64 [t][v] row-major;
+// out: FP64 or FP32 block, column j stored at idx_out[j] (or j)).  mode 0: out = sum,
+// mode 1: out += sign * sum.  Each thread keeps 16 outputs of one pixel in registers per pass
+// over A.  With norm_part != null (FP64 outputs), per-CTA partials of ||out_j||^2 are written.
+constexpr int kCombJ = 16;
+template <typename TO>
+__global__ void __launch_bounds__(kNT) k_bcombine(TO* __restrict__ out, const int* __restrict__ idx_out,
+                                                   int v, const float4* __restrict__ A, int t,
+                                                   const double* __restrict__ C, int ldc, double sign,
+                                                   int mode, int64_t n, double* __restrict__ norm_part) {
+  __shared__ float cs[kMaxBlk * kMaxBlk];
+  __shared__ double red[kNT];
+  for (int e = threadIdx.x; e < t * v; e += kNT) cs[e] = (float)C[(e / v) * ldc + (e % v)];
+  __syncthreads();
+  for (int j0 = 0; j0 < v; j0 += kCombJ) {
+    const int nj = min(kCombJ, v - j0);
+    double nrm[kCombJ];
+#pragma unroll
+    for (int jj = 0; jj < kCombJ; jj++) nrm[jj] = 0.0;
+    for (int64_t p = (int64_t)blockIdx.x * kNT + threadIdx.x; p < n; p += (int64_t)gridDim.x * kNT) {
+      float ax[kCombJ], ay[kCombJ], az[kCombJ];
+#pragma unroll
+      for (int jj = 0; jj < kCombJ; jj++) ax[jj] = ay[jj] = az[jj] = 0.f;
+      for (int i = 0; i < t; i++) {
+        const float4 a = __ldg(A + (int64_t)i * n + p);
+#pragma unroll
+        for (int jj = 0; jj < kCombJ; jj++) {
+          const float c = (jj < nj) ? cs[i * v + j0 + jj] : 0.f;
+          ax[jj] = fmaf(a.x, c, ax[jj]);
+          ay[jj] = fmaf(a.y, c, ay[jj]);
+          az[jj] = fmaf(a.z, c, az[jj]);
+        }
+      }
+#pragma unroll
+      for (int jj = 0; jj < kCombJ; jj++) {
+        if (jj >= nj) break;
+        const int64_t col = idx_out ? idx_out[j0 + jj] : (j0 + jj);
+        if constexpr (sizeof(TO) == sizeof(float4)) {
+          float4* o = reinterpret_cast<float4*>(out) + col * n + p;
+          float4 cur = mode ? *o : make_float4(0.f, 0.f, 0.f, 0.f);
+          cur.x += (float)sign * ax[jj]; cur.y += (float)sign * ay[jj]; cur.z += (float)sign * az[jj];
+          cur.w = 0.f;
+          *o = cur;
+        } else {
+          double* o = reinterpret_cast<double*>(out) + 4 * (col * n + p);
+          double x0 = mode ? o[0] : 0.0, x1 = mode ? o[1] : 0.0, x2 = mode ? o[2] : 0.0;
+          x0 += sign * (double)ax[jj]; x1 += sign * (double)ay[jj]; x2 += sign * (double)az[jj];
+          o[0] = x0; o[1] = x1; o[2] = x2; o[3] = 0.0;
+          nrm[jj] += x0 * x0 + x1 * x1 + x2 * x2;
+        }
+      }
+    }
+    if (norm_part) {
+      for (int jj = 0; jj < nj; jj++) {
+        red[threadIdx.x] = nrm[jj];
+        __syncthreads();
+        for (int sh = kNT / 2; sh > 0; sh >>= 1) {
+          if (threadIdx.x < sh) red[threadIdx.x] += red[threadIdx.x + sh];
+          __syncthreads();
+        }
+        if (threadIdx.x == 0) norm_part[(int64_t)(j0 + jj) * gridDim.x + blockIdx.x] = red[0];
+        __syncthreads();
+      }
+    }
+  }
+}
+
+__global__ void k_norm_reduce(const double* __restrict__ part, int nblk, int v, double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= v) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; b++) s += part[(int64_t)j * nblk + b];
+  out[j] = s;
+}
+
+cudaError_t launch_bcombine(void* out, int out_is_fp64, const int* idx_out, int v, const float* A, int t,
+                            const double* C, int ldc, double sign, int mode, int64_t n, double* norm_part,
+                            int nblk, double* norms, cudaStream_t s) {
+  if (v <= 0) return cudaSuccess;
+  if (t > kMaxBlk || v > kMaxBlk) return cudaErrorInvalidValue;
+  if (out_is_fp64)
+    k_bcombine<double4_16a><<<nblk, kNT, 0, s>>>(reinterpret_cast<double4_16a*>(out), idx_out, v,
+                                                 reinterpret_cast<const float4*>(A), t, C, ldc, sign, mode,
+                                                 n, norm_part);
+  else
+    k_bcombine<float4><<<nblk, kNT, 0, s>>>(reinterpret_cast<float4*>(out), idx_out, v,
+                                            reinterpret_cast<const float4*>(A), t, C, ldc, sign, mode, n,
+                                            nullptr);
+  if (norm_part && out_is_fp64) k_norm_reduce<<<(v + 63) / 64, 64, 0, s>>>(norm_part, nblk, v, norms);
+  return cudaGetLastError();
+}
+
+// W_j = M_BD R_{idx_j} in FP32 (j < v)
+__global__ void k_bprecond(const double* __restrict__ minv, const double* __restrict__ R,
+                           const int* __restrict__ idx, int v, int64_t n, float4* __restrict__ W) {
+  const int64_t tot = (int64_t)v * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / n);
+    const int64_t p = e - (int64_t)j * n;
+    const double* r = R + 4 * ((int64_t)idx[j] * n + p);
+    const double* m = minv + 6 * p;
+    const double z0 = m[0] * r[0] + m[1] * r[1] + m[2] * r[2];
+    const double z1 = m[1] * r[0] + m[3] * r[1] + m[4] * r[2];
+    const double z2 = m[2] * r[0] + m[4] * r[1] + m[5] * r[2];
+    W[e] = make_float4((float)z0, (float)z1, (float)z2, 0.f);
+  }
+}
+
+cudaError_t launch_bprecond(const double* minv, const double* R, const int* idx, int v, int64_t n,
+                            float* W, cudaStream_t s) {
+  if (v <= 0) return cudaSuccess;
+  const int64_t tot = (int64_t)v * n;
+  int64_t g = (tot + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_bprecond<<<(unsigned)g, 256, 0, s>>>(minv, R, idx, v, n, reinterpret_cast<float4*>(W));
+  return cudaGetLastError();
+}
+
+// Small dense step of one iteration, one CTA, FP64:
+//   G (t x t, symmetrised) = L L^T by a pivoted Cholesky with relative tolerance rank_tol;
+//   Linv = L^-1 (rank x rank, lower); piv[0..rank) = pivoted columns; *rank_out = rank.
+// The caller forms P = Linv Z[piv] and A P = Linv (A Z)[piv] (rows are block columns).
+__global__ void k_bchol(const double* __restrict__ G, int t, double rank_tol, double* __restrict__ Linv_out,
+                        int* __restrict__ piv_out, int* __restrict__ rank_out) {
+  // The factorisation is O(t^3) <= ~90K flops: one thread does it, with explicit indexing.
+  extern __shared__ double dsm[];      // g [kMaxBlk * kLd] then L [kMaxBlk * kLd]
+  constexpr int kLd = kMaxBlk + 1;
+  double* g = dsm;
+  double* L = dsm + kMaxBlk * kLd;
+  if (threadIdx.x != 0) return;
+  int piv[kMaxBlk];
+  double mx = 0.0;
+  for (int i = 0; i < t; i++) {
+    piv[i] = i;
+    for (int j = 0; j < t; j++) {
+      g[i * kLd + j] = 0.5 * (G[i * t + j] + G[j * t + i]);
+      L[i * kLd + j] = 0.0;
+    }
+    mx = fmax(mx, fabs(g[i * kLd + i]));
+  }
+  const double scale = mx > 0.0 ? mx : 1e-300;
+  int r = t;
+  for (int k = 0; k < t; k++) {
+    int best = k;
+    double bd = -1.0;
+    for (int i = k; i < t; i++) {
+      double d = g[i * kLd + i];
+      for (int m = 0; m < k; m++) d -= L[i * kLd + m] * L[i * kLd + m];
+      if (d > bd) { bd = d; best = i; }
+    }
+    if (!(bd > rank_tol * scale)) { r = k; break; }
+    if (best != k) {   // symmetric swap of rows/columns k and best, and of the computed rows of L
+      for (int j = 0; j < t; j++) { const double tmp = g[k * kLd + j]; g[k * kLd + j] = g[best * kLd + j]; g[best * kLd + j] = tmp; }
+      for (int j = 0; j < t; j++) { const double tmp = g[j * kLd + k]; g[j * kLd + k] = g[j * kLd + best]; g[j * kLd + best] = tmp; }
+      for (int m = 0; m < k; m++) { const double tmp = L[k * kLd + m]; L[k * kLd + m] = L[best * kLd + m]; L[best * kLd + m] = tmp; }
+      const int tp = piv[k]; piv[k] = piv[best]; piv[best] = tp;
+    }
+    L[k * kLd + k] = sqrt(bd);
+    for (int i = k + 1; i < t; i++) {
+      double sacc = g[i * kLd + k];
+      for (int m = 0; m < k; m++) sacc -= L[i * kLd + m] * L[k * kLd + m];
+      L[i * kLd + k] = sacc / L[k * kLd + k];
+    }
+  }
+  // Linv = L^-1 (r x r, lower) by forward substitution, column by column
+  for (int e = 0; e < kMaxBlk * kMaxBlk; e++) Linv_out[e] = 0.0;
+  for (int c = 0; c < r; c++) {
+    for (int i = c; i < r; i++) {
+      double sacc = (i == c) ? 1.0 : 0.0;
+      for (int m = c; m < i; m++) sacc -= L[i * kLd + m] * Linv_out[m * kMaxBlk + c];
+      Linv_out[i * kMaxBlk + c] = sacc / L[i * kLd + i];
+    }
+  }
+  for (int i = 0; i < t; i++) piv_out[i] = piv[i];
+  *rank_out = r;
+}
+
+cudaError_t launch_bchol(const double* G, int t, double rank_tol, double* Linv, int* piv, int* rank,
+                         cudaStream_t s) {
+  if (t > kMaxBlk) return cudaErrorInvalidValue;
+  const size_t smem = 2 * kMaxBlk * (kMaxBlk + 1) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k_bchol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_bchol<<<1, 32, smem, s>>>(G, t, rank_tol, Linv, piv, rank);
+  return cudaGetLastError();
+}
+
+// Linv as a [t][t] coefficient matrix for the combine kernel: Cmb[k][i] = Linv[i][pos(k)] where
+// block column k = piv[pos]; rows/cols beyond the rank are zero.  out_i = sum_k Z_k Cmb[k][i].
+__global__ void k_linv_coef(const double* __restrict__ Linv, const int* __restrict__ piv,
+                            const int* __restrict__ rank, int t, double* __restrict__ Cmb) {
+  const int r = *rank;
+  for (int e = threadIdx.x; e < t * t; e += blockDim.x) {
+    const int k = e / t, i = e % t;
+    double c = 0.0;
+    if (i < r) {
+      for (int pos = 0; pos < r; pos++)
+        if (piv[pos] == k) c = Linv[i * kMaxBlk + pos];
+    }
+    Cmb[k * t + i] = c;
+  }
+}
+
+cudaError_t launch_linv_coef(const double* Linv, const int* piv, const int* rank, int t, double* Cmb,
+                             cudaStream_t s) {
+  k_linv_coef<<<1, 256, 0, s>>>(Linv, piv, rank, t, Cmb);
+  return cudaGetLastError();
+}
+
+// R_j = B_j - AX_j (FP64) and norms_part of ||R_j||^2 (j < v); grid (nblk, v)
+__global__ void k_bresid(const double* __restrict__ B, const double* __restrict__ AX, int64_t n,
+                         double* __restrict__ R, double* __restrict__ norm_part) {
+  __shared__ double red[kNT];
+  const int j = blockIdx.y;
+  double nrm = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * kNT + threadIdx.x; p < n; p += (int64_t)gridDim.x * kNT) {
+    const int64_t o = 4 * ((int64_t)j * n + p);
+    const double r0 = B[o] - AX[o], r1 = B[o + 1] - AX[o + 1], r2 = B[o + 2] - AX[o + 2];
+    R[o] = r0; R[o + 1] = r1; R[o + 2] = r2; R[o + 3] = 0.0;
+    nrm += r0 * r0 + r1 * r1 + r2 * r2;
+  }
+  red[threadIdx.x] = nrm;
+  __syncthreads();
+  for (int sh = kNT / 2; sh > 0; sh >>= 1) {
+    if (threadIdx.x < sh) red[threadIdx.x] += red[threadIdx.x + sh];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) norm_part[(int64_t)j * gridDim.x + blockIdx.x] = red[0];
+}
+
+cudaError_t launch_bresid(const double* B, const double* AX, int v, int64_t n, double* R,
+                          double* norm_part, int nblk, double* norms, cudaStream_t s) {
+  if (v <= 0) return cudaSuccess;
+  k_bresid<<<dim3(nblk, v), kNT, 0, s>>>(B, AX, n, R, norm_part);
+  k_norm_reduce<<<(v + 63) / 64, 64, 0, s>>>(norm_part, nblk, v, norms);
+  return cudaGetLastError();
+}
+
+}  // namespace mm

@@ -7,6 +7,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "mm_block.cuh"
 #include "mm_cg.cuh"
 #include "mm_internal.cuh"
 
@@ -42,6 +43,20 @@ struct CgState {
   double g_tol2 = -1.0;
 };
 
+// Block-CG workspace, grown on demand and kept with the plan.
+struct BlkState {
+  int64_t n = 0;
+  int s_cap = 0;
+  double *X = nullptr, *R = nullptr, *B = nullptr, *AX = nullptr;   // [s][n][4] FP64
+  float *Z = nullptr, *AZ = nullptr, *P = nullptr, *AP = nullptr;   // [s][n][4] FP32
+  double *part = nullptr, *G = nullptr, *Linv = nullptr, *Cmb = nullptr, *alpha = nullptr,
+         *C2 = nullptr, *norms = nullptr, *norm_part = nullptr;
+  int *piv = nullptr, *rank = nullptr, *idx = nullptr;
+  double* T64 = nullptr;    // [s][n][4] FP64 apply output (FP64 operator path)
+  double* host = nullptr;   // pinned: norms
+  int* host_i = nullptr;    // pinned: rank
+};
+
 template <typename T>
 void dfree(T*& p) {
   if (p) cudaFree((void*)p);
@@ -74,6 +89,17 @@ void free_cg(CgState* c) {
   delete c;
 }
 
+void free_blk(BlkState* b) {
+  if (!b) return;
+  dfree(b->X); dfree(b->R); dfree(b->B); dfree(b->AX); dfree(b->Z); dfree(b->AZ); dfree(b->P);
+  dfree(b->AP); dfree(b->part); dfree(b->G); dfree(b->Linv); dfree(b->Cmb); dfree(b->alpha);
+  dfree(b->C2); dfree(b->norms); dfree(b->norm_part); dfree(b->piv); dfree(b->rank); dfree(b->idx);
+  dfree(b->T64);
+  if (b->host) cudaFreeHost(b->host);
+  if (b->host_i) cudaFreeHost(b->host_i);
+  delete b;
+}
+
 void free_plan(Plan* P) {
   if (!P) return;
   int cur = 0;
@@ -85,6 +111,7 @@ void free_plan(Plan* P) {
   dfree(P->tw32); dfree(P->tw64); dfree(P->tiles); dfree(P->segs); dfree(P->map32_in); dfree(P->map32_out);
   dfree(P->map64_in); dfree(P->map64_out); dfree(P->td_a); dfree(P->td_b);
   free_cg(reinterpret_cast<CgState*>(P->cg));
+  free_blk(reinterpret_cast<BlkState*>(P->blk));
   if (P->stream) cudaStreamDestroy(P->stream);
   cudaSetDevice(cur);
   delete P;
@@ -534,6 +561,52 @@ int enqueue_iteration(Plan* P, const CgWork& w, int nrhs, bool fp32, cudaStream_
   return MM_OK;
 }
 
+constexpr int kBlkCtas = 2 * 152;
+
+int ensure_blk(Plan* P, int s, BlkState** out) {
+  BlkState* b = reinterpret_cast<BlkState*>(P->blk);
+  if (!b) {
+    b = new BlkState();
+    P->blk = b;
+  }
+  if (b->s_cap < s || b->n != P->n_obs) {
+    BlkState fresh;
+    std::swap(*b, fresh);
+    free_blk(new BlkState(fresh));   // releases the old buffers
+    const size_t n4 = (size_t)s * P->n_obs * 4;
+    MM_TRY(dalloc(P, &b->X, n4)); MM_TRY(dalloc(P, &b->R, n4)); MM_TRY(dalloc(P, &b->B, n4));
+    MM_TRY(dalloc(P, &b->AX, n4)); MM_TRY(dalloc(P, &b->T64, n4));
+    MM_TRY(dalloc(P, &b->Z, n4)); MM_TRY(dalloc(P, &b->AZ, n4)); MM_TRY(dalloc(P, &b->P, n4));
+    MM_TRY(dalloc(P, &b->AP, n4));
+    MM_TRY(dalloc(P, &b->part, (size_t)kBlkCtas * kMaxBlk * kMaxBlk));
+    MM_TRY(dalloc(P, &b->G, kMaxBlk * kMaxBlk)); MM_TRY(dalloc(P, &b->Linv, kMaxBlk * kMaxBlk));
+    MM_TRY(dalloc(P, &b->Cmb, kMaxBlk * kMaxBlk)); MM_TRY(dalloc(P, &b->alpha, kMaxBlk * kMaxBlk));
+    MM_TRY(dalloc(P, &b->C2, kMaxBlk * kMaxBlk)); MM_TRY(dalloc(P, &b->norms, kMaxBlk));
+    MM_TRY(dalloc(P, &b->norm_part, (size_t)kMaxBlk * kBlkCtas));
+    MM_TRY(dalloc(P, &b->piv, kMaxBlk)); MM_TRY(dalloc(P, &b->rank, 4)); MM_TRY(dalloc(P, &b->idx, kMaxBlk));
+    MM_CUDA(cudaMallocHost((void**)&b->host, kMaxBlk * sizeof(double)));
+    MM_CUDA(cudaMallocHost((void**)&b->host_i, 4 * sizeof(int)));
+    b->s_cap = s;
+    b->n = P->n_obs;
+  }
+  *out = b;
+  return MM_OK;
+}
+
+// A Z for t FP32 columns (AZ zeroed and accumulated), with the plan's FP32 or FP64 operator.
+int blk_apply(Plan* P, BlkState* b, int t, bool fp32, cudaStream_t s) {
+  const size_t n4 = (size_t)t * P->n_obs * 4;
+  if (fp32) {
+    MM_CUDA(cudaMemsetAsync(b->AZ, 0, n4 * sizeof(float), s));
+    return apply32_internal(P, b->Z, b->AZ, t, s);
+  }
+  MM_CUDA(launch_to64(b->Z, (int64_t)(n4 / 4), b->AX, s));
+  MM_CUDA(cudaMemsetAsync(b->T64, 0, n4 * sizeof(double), s));
+  MM_TRY(apply64_internal(P, b->AX, b->T64, t, s));
+  MM_CUDA(launch_to32(b->T64, (int64_t)(n4 / 4), b->AZ, s));
+  return MM_OK;
+}
+
 }  // namespace
 }  // namespace mm
 
@@ -870,6 +943,157 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
     if (st != MM_OK && (worst == MM_OK || st < worst)) worst = st;
   }
   if (worst != MM_OK) set_error("solve did not converge for every right-hand side");
+  return worst;
+}
+
+int mm_block_cg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, int block_width,
+                      const mm_solve_opts* opts, mm_solve_info* info, void* stream) {
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  if (!P || !b || !x || !opts || !info || nrhs <= 0) return fail(MM_EINVAL, "bad argument");
+  if (!(opts->tol > 0.0) || opts->max_iter < 0) return fail(MM_EINVAL, "bad tol / max_iter");
+  if (opts->precond != MM_PREC_BD) return fail(MM_EINVAL, "unsupported preconditioner");
+  if (opts->precision != MM_FP64 && opts->precision != MM_FP32) return fail(MM_EINVAL, "bad precision");
+  if (block_width < 0 || block_width > kMaxBlk) return fail(MM_EINVAL, "block_width must lie in [0, 64]");
+  if (P->algo == MM_TPLZ_DIRECT) return fail(MM_EINVAL, "block CG needs an FFT plan");
+  DeviceGuard g(P->device);
+  const auto t0 = std::chrono::steady_clock::now();
+  const int sw = block_width > 0 ? block_width : std::min(nrhs, kMaxBlk);
+  const bool fp32 = opts->precision == MM_FP32;
+  const double tol2 = opts->tol * opts->tol;
+  const int64_t n = P->n_obs;
+  cudaStream_t us = as_stream(stream);
+  cudaStream_t s = P->stream;
+  BlkState* B = nullptr;
+  MM_TRY(ensure_blk(P, sw, &B));
+  cudaEvent_t ev;
+  MM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  MM_CUDA(cudaEventRecord(ev, us));
+  MM_CUDA(cudaStreamWaitEvent(s, ev, 0));
+  int worst = MM_OK;
+  int64_t n_kernels = 0;
+  int n_apply = 0, n_apply64 = 0;
+  auto read_norms = [&](int v) -> int {
+    MM_CUDA(cudaMemcpyAsync(B->host, B->norms, v * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MM_CUDA(cudaStreamSynchronize(s));
+    return MM_OK;
+  };
+  for (int g0 = 0; g0 < nrhs; g0 += sw) {
+    const int sg = std::min(sw, nrhs - g0);
+    const size_t n4 = (size_t)sg * n * 4;
+    MM_CUDA(launch_pack3to4(b + (size_t)g0 * n * 3, n, sg, B->B, s));
+    MM_CUDA(cudaMemsetAsync(B->X, 0, n4 * sizeof(double), s));
+    MM_CUDA(cudaMemsetAsync(B->AX, 0, n4 * sizeof(double), s));
+    MM_CUDA(launch_bresid(B->B, B->AX, sg, n, B->R, B->norm_part, kBlkCtas, B->norms, s));   // R = B
+    n_kernels += 3;
+    MM_TRY(read_norms(sg));
+    std::vector<double> bn2(B->host, B->host + sg), rn2(bn2), tn2(bn2);
+    std::vector<int> conv(sg, 0), iters(sg, 0), status(sg, MM_OK);
+    std::vector<int> active;
+    for (int j = 0; j < sg; j++) {
+      if (bn2[j] == 0.0) conv[j] = 1; else active.push_back(j);
+    }
+    int it = 0, restarts = 0, r = 0;
+    bool fresh = true;   // Z = M R without the A-orthogonalisation (first step, or a restart)
+    while (!active.empty()) {
+      const int t = (int)active.size();
+      MM_CUDA(cudaMemcpyAsync(B->idx, active.data(), t * sizeof(int), cudaMemcpyHostToDevice, s));
+      MM_CUDA(launch_bprecond(P->minv, B->R, B->idx, t, n, B->Z, s));   // Z = M R[active]
+      n_kernels += 1;
+      if (!fresh && r > 0) {   // Z = (I - P P^T A) M R: Z -= P (AP^T Z)
+        MM_CUDA(launch_bgram(B->AP, r, nullptr, B->Z, 0, t, nullptr, n, B->part, kBlkCtas, B->C2, s));
+        MM_CUDA(launch_bcombine(B->Z, 0, nullptr, t, B->P, r, B->C2, t, -1.0, 1, n, nullptr, kBlkCtas,
+                                nullptr, s));
+        n_kernels += 3;
+      }
+      fresh = false;
+      if (it >= opts->max_iter) break;
+      MM_TRY(blk_apply(P, B, t, fp32, s));                                 // AZ = A Z
+      n_kernels += fp32 ? 1 : 3;
+      n_apply += 1;
+      MM_CUDA(launch_bgram(B->Z, t, nullptr, B->AZ, 0, t, nullptr, n, B->part, kBlkCtas, B->G, s));
+      MM_CUDA(launch_bchol(B->G, t, 1e-10, B->Linv, B->piv, B->rank, s));
+      MM_CUDA(cudaMemcpyAsync(B->host_i, B->rank, sizeof(int), cudaMemcpyDeviceToHost, s));
+      MM_CUDA(cudaStreamSynchronize(s));
+      r = B->host_i[0];
+      n_kernels += 3;
+      if (r == 0) {
+        for (int j : active) status[j] = MM_EBREAKDOWN;
+        break;
+      }
+      MM_CUDA(launch_linv_coef(B->Linv, B->piv, B->rank, t, B->Cmb, s));
+      MM_CUDA(launch_bcombine(B->P, 0, nullptr, r, B->Z, t, B->Cmb, t, 1.0, 0, n, nullptr, kBlkCtas, nullptr, s));
+      MM_CUDA(launch_bcombine(B->AP, 0, nullptr, r, B->AZ, t, B->Cmb, t, 1.0, 0, n, nullptr, kBlkCtas, nullptr, s));
+      // alpha = P^T R over all sg columns; X += P alpha; R -= AP alpha
+      MM_CUDA(launch_bgram(B->P, r, nullptr, B->R, 1, sg, nullptr, n, B->part, kBlkCtas, B->alpha, s));
+      MM_CUDA(launch_bcombine(B->X, 1, nullptr, sg, B->P, r, B->alpha, sg, 1.0, 1, n, nullptr, kBlkCtas,
+                              nullptr, s));
+      MM_CUDA(launch_bcombine(B->R, 1, nullptr, sg, B->AP, r, B->alpha, sg, -1.0, 1, n, B->norm_part,
+                              kBlkCtas, B->norms, s));
+      n_kernels += 9;
+      it += 1;
+      MM_TRY(read_norms(sg));
+      active.clear();
+      for (int j = 0; j < sg; j++) {
+        rn2[j] = B->host[j];
+        if (!conv[j] && rn2[j] < tol2 * bn2[j]) {
+          conv[j] = 1;
+          iters[j] = it;
+        }
+        if (!conv[j]) active.push_back(j);
+        if (!std::isfinite(rn2[j])) status[j] = MM_EBREAKDOWN;
+      }
+      bool bad = false;
+      for (int j = 0; j < sg; j++) bad = bad || status[j] == MM_EBREAKDOWN;
+      if (bad) break;
+      if (active.empty() || it >= opts->max_iter) {
+        // FP64 true residual R = B - A X; columns above tol restart from it
+        MM_CUDA(cudaMemsetAsync(B->AX, 0, n4 * sizeof(double), s));
+        MM_TRY(apply64_internal(P, B->X, B->AX, sg, s));
+        MM_CUDA(launch_bresid(B->B, B->AX, sg, n, B->R, B->norm_part, kBlkCtas, B->norms, s));
+        n_kernels += 3;
+        n_apply64 += 1;
+        MM_TRY(read_norms(sg));
+        active.clear();
+        for (int j = 0; j < sg; j++) {
+          tn2[j] = B->host[j];
+          rn2[j] = tn2[j];
+          if (bn2[j] > 0.0 && !(tn2[j] < tol2 * bn2[j])) {
+            conv[j] = 0;
+            active.push_back(j);
+          }
+        }
+        if (active.empty() || it >= opts->max_iter || restarts >= 8) break;
+        restarts += 1;
+        fresh = true;
+      }
+    }
+    for (int j = 0; j < sg; j++) {
+      if (status[j] == MM_OK && !conv[j]) status[j] = MM_ENOTCONV;
+      if (status[j] == MM_OK && iters[j] == 0 && bn2[j] > 0.0) iters[j] = it;
+    }
+    MM_CUDA(launch_unpack4to3(B->X, n, sg, x + (size_t)g0 * n * 3, s));
+    n_kernels += 1;
+    MM_CUDA(cudaStreamSynchronize(s));
+    const double t_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (int j = 0; j < sg; j++) {
+      mm_solve_info& in = info[g0 + j];
+      std::memset(&in, 0, sizeof(in));
+      in.status = status[j];
+      in.iters = iters[j];
+      in.rel_res = bn2[j] > 0 ? std::sqrt(rn2[j] / bn2[j]) : 0.0;
+      in.true_rel_res = bn2[j] > 0 ? std::sqrt(tn2[j] / bn2[j]) : 0.0;
+      in.t_ms = t_ms;
+      in.n_true_res = restarts + 1;
+      in.n_apply32 = fp32 ? n_apply : 0;
+      in.n_apply64 = (fp32 ? 0 : n_apply) + n_apply64;
+      in.n_kernels = n_kernels;
+      if (status[j] != MM_OK && (worst == MM_OK || status[j] < worst)) worst = status[j];
+    }
+  }
+  MM_CUDA(cudaEventRecord(ev, s));
+  MM_CUDA(cudaStreamWaitEvent(us, ev, 0));
+  cudaEventDestroy(ev);
+  if (worst != MM_OK) set_error("block CG did not converge for every right-hand side");
   return worst;
 }
 

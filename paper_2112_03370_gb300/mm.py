@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "MM_OK", 1: "MM_EINVAL", 2: "MM_ENOMEM", 3: "MM_ENOTSPD", 4: 
 # the exported entry points of include/mm.h
 EXPORTS = ("mm_plan", "mm_plan_query", "mm_plan_destroy", "mm_apply_P", "mm_apply_Pt",
            "mm_apply_Ninv", "mm_rhs", "mm_apply_A", "mm_precond", "mm_pcg_solve", "mm_last_error",
-           "mm_apply_A_noalloc")
+           "mm_apply_A_noalloc", "mm_block_cg_solve")
 
 
 class ProblemDesc(ctypes.Structure):
@@ -78,6 +78,8 @@ def _load():
     lib.mm_precond.argtypes = [vp, vp, vp, i32, vp]
     lib.mm_pcg_solve.argtypes = [vp, vp, vp, i32, ctypes.POINTER(SolveOpts),
                                  ctypes.POINTER(SolveInfo), vp]
+    lib.mm_block_cg_solve.argtypes = [vp, vp, vp, i32, i32, ctypes.POINTER(SolveOpts),
+                                      ctypes.POINTER(SolveInfo), vp]
     lib.mm_last_error.restype = ctypes.c_char_p
     for n in EXPORTS:
         if n not in ("mm_plan_destroy", "mm_last_error"):
@@ -247,5 +249,20 @@ def mm_pcg_solve(plan: Plan, b: torch.Tensor, x: torch.Tensor, tol: float = 1e-6
     code = _lib.mm_pcg_solve(ctypes.c_void_p(plan.handle), _ptr(b), _ptr(x), nrhs,
                              ctypes.byref(opts), infos, _stream_ptr(stream))
     if raise_on_error and code not in (MM_OK,):
+        raise MMError(code, mm_last_error())
+    return list(infos)
+
+
+def mm_block_cg_solve(plan: Plan, b: torch.Tensor, x: torch.Tensor, block_width: int = 0,
+                      tol: float = 1e-6, max_iter: int = 10000, precision: int = MM_FP32,
+                      stream=None, raise_on_error=True):
+    """Block CG on nrhs right-hand sides (b, x: [nrhs, n_obs, 3]); returns a list of SolveInfo."""
+    _dev(b, torch.float64, "b"); _dev(x, torch.float64, "x")
+    nrhs = 1 if b.dim() <= 2 else b.shape[0]
+    opts = SolveOpts(tol=tol, max_iter=max_iter, precond=MM_PREC_BD, precision=precision)
+    infos = (SolveInfo * nrhs)()
+    code = _lib.mm_block_cg_solve(ctypes.c_void_p(plan.handle), _ptr(b), _ptr(x), nrhs, block_width,
+                                  ctypes.byref(opts), infos, _stream_ptr(stream))
+    if raise_on_error and code != MM_OK:
         raise MMError(code, mm_last_error())
     return list(infos)
