@@ -52,8 +52,9 @@ typedef enum {
 enum { MM_FP64 = 0, MM_FP32 = 1 };
 /* Algorithm of the block-Toeplitz product. */
 enum { MM_TPLZ_AUTO = 0, MM_TPLZ_FFT = 1, MM_TPLZ_DIRECT = 3 };
-/* Preconditioner. */
-enum { MM_PREC_BD = 0 };
+/* Preconditioner: block-Jacobi, or the two-level a-posteriori A-DEF1 preconditioner built by
+ * mm_deflation_build (Sect. 3.2, Eq. 2lvlDef). */
+enum { MM_PREC_BD = 0, MM_PREC_2LVL_POST = 1 };
 
 /*
  * Problem description (the map-making problem statement of Sect. 2 and 3).
@@ -95,7 +96,7 @@ typedef struct {
  * PCG options.
  *   tol            eps of the stop rule ||r|| < eps ||b|| (recursive residual of Algorithm 1).
  *   max_iter       cap on iterations (MM_ENOTCONV when reached).
- *   precond        MM_PREC_BD.
+ *   precond        MM_PREC_BD, or MM_PREC_2LVL_POST (needs mm_deflation_build on the plan).
  *   precision      MM_FP64: plain FP64 PCG.  MM_FP32: P, N^-1, P^T in FP32 with FP64 vectors,
  *                  dot products, alpha/beta and 3x3 blocks, and reliable updates: the recursive
  *                  residual is replaced by the FP64 true residual b - A x every `reliable_every`
@@ -207,6 +208,23 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
  * per-column status (MM_ENOTCONV after opts->max_iter block iterations, MM_EBREAKDOWN). */
 int mm_block_cg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, int block_width,
                       const mm_solve_opts* opts, mm_solve_info* info, void* stream);
+
+/* Build the two-level a-posteriori deflation space of the plan (Sect. 3.2): m steps of the Lanczos
+ * algorithm (Algorithm 3) on A (not M_BD A) from v_1 = b / ||b|| (x_0 = 0), storing A V_m; the
+ * Ritz vectors of T_m = X Theta X^T give Z = V_m X and Z' = (A V_m) X (all m of them, as the paper
+ * takes "all the precomputed vectors"); E = Z^T Z' and its pseudo-inverse (eigenvalues below
+ * 1e-12 of the largest dropped).  b: [n_obs][3] float64 device; 1 <= m <= 64; precision selects
+ * the FP32 or FP64 operator for the m A-applications.  Z, Z' are kept in FP32 on the plan and
+ * replace any previous space.  Synchronous.  MM_EBREAKDOWN if b = 0. */
+int mm_deflation_build(mm_plan_t plan, const double* b, int m, int precision, void* stream);
+
+/* The plan's deflation space: *k columns; Z [k][n_obs][3] float64 device (may be NULL) and the
+ * Ritz values theta [k] (HOST, may be NULL).  *k = 0 when none was built. */
+int mm_deflation_get(mm_plan_t plan, int* k, double* Z, double* theta, void* stream);
+
+/* z = M_2lvl r = M_BD (r - Z' E^-1 Z^T r) + Z E^-1 Z^T r (Eq. 2lvlDef0, applied right to left)
+ * for nrhs vectors [nrhs][n_obs][3]; needs mm_deflation_build.  Asynchronous on stream. */
+int mm_deflation_apply(mm_plan_t plan, const double* r, double* z, int nrhs, void* stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* mm_last_error(void);

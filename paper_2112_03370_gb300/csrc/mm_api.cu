@@ -9,6 +9,7 @@
 
 #include "mm_block.cuh"
 #include "mm_cg.cuh"
+#include "mm_defl.cuh"
 #include "mm_internal.cuh"
 
 namespace mm {
@@ -39,7 +40,7 @@ struct CgState {
   CgScalars* scal_host = nullptr;   // pinned
   // cached graph of `chunk` iterations
   cudaGraphExec_t exec = nullptr;
-  int g_nrhs = -1, g_fp32 = -1, g_chunk = -1, g_maxit = -1;
+  int g_nrhs = -1, g_fp32 = -1, g_chunk = -1, g_maxit = -1, g_prec = -1;
   double g_tol2 = -1.0;
 };
 
@@ -55,6 +56,18 @@ struct BlkState {
   double* T64 = nullptr;    // [s][n][4] FP64 apply output (FP64 operator path)
   double* host = nullptr;   // pinned: norms
   int* host_i = nullptr;    // pinned: rank
+};
+
+// Two-level deflation space and its per-solve work buffers.
+struct DeflState {
+  int k = 0;
+  int64_t n = 0;
+  float *Z = nullptr, *Zp = nullptr;            // [k][n][4]
+  double* Einv = nullptr;                      // [k][k]
+  std::vector<double> theta;                   // Ritz values (host copy)
+  int nrhs_cap = 0;
+  double *y = nullptr, *part = nullptr, *part2 = nullptr;
+  unsigned *counters = nullptr, *counters2 = nullptr;
 };
 
 template <typename T>
@@ -100,6 +113,13 @@ void free_blk(BlkState* b) {
   delete b;
 }
 
+void free_defl(DeflState* d) {
+  if (!d) return;
+  dfree(d->Z); dfree(d->Zp); dfree(d->Einv); dfree(d->y); dfree(d->part); dfree(d->part2);
+  dfree(d->counters); dfree(d->counters2);
+  delete d;
+}
+
 void free_plan(Plan* P) {
   if (!P) return;
   int cur = 0;
@@ -112,6 +132,7 @@ void free_plan(Plan* P) {
   dfree(P->map64_in); dfree(P->map64_out); dfree(P->td_a); dfree(P->td_b);
   free_cg(reinterpret_cast<CgState*>(P->cg));
   free_blk(reinterpret_cast<BlkState*>(P->blk));
+  free_defl(reinterpret_cast<DeflState*>(P->defl));
   if (P->stream) cudaStreamDestroy(P->stream);
   cudaSetDevice(cur);
   delete P;
@@ -547,8 +568,9 @@ CgWork make_work(Plan* P, CgState* c, int nrhs, bool fp32, double tol, int max_i
   return w;
 }
 
-// One PCG iteration: p = z + beta p; q = A p; alpha; x, r, z, beta.
-int enqueue_iteration(Plan* P, const CgWork& w, int nrhs, bool fp32, cudaStream_t s) {
+// One PCG iteration: p = z + beta p; q = A p; alpha; x, r, z, beta (z = M_2lvl r when dw != null).
+int enqueue_iteration(Plan* P, const CgWork& w, int nrhs, bool fp32, cudaStream_t s,
+                      const DeflWork* dw = nullptr) {
   MM_CUDA(launch_cg(CG_PUPDATE, w, s));
   const int32_t* halt = reinterpret_cast<const int32_t*>(w.scal) + kHaltOffsetInts;
   if (fp32) {
@@ -558,6 +580,34 @@ int enqueue_iteration(Plan* P, const CgWork& w, int nrhs, bool fp32, cudaStream_
   }
   MM_CUDA(launch_cg(CG_DOT_PQ, w, s));
   MM_CUDA(launch_cg(CG_UPDATE, w, s));
+  if (dw) MM_CUDA(launch_defl_step(*dw, w, s));
+  return MM_OK;
+}
+
+// per-solve buffers of the deflated preconditioner for nrhs columns
+int ensure_defl_work(Plan* P, DeflState* d, int nrhs, int n_blocks, DeflWork* out) {
+  if (d->nrhs_cap < nrhs) {
+    dfree(d->y); dfree(d->part); dfree(d->part2); dfree(d->counters); dfree(d->counters2);
+    d->nrhs_cap = 0;
+    MM_TRY(dalloc(P, &d->y, (size_t)nrhs * kMaxDefl));
+    MM_TRY(dalloc(P, &d->part, (size_t)nrhs * 1024 * kMaxDefl));
+    MM_TRY(dalloc(P, &d->part2, (size_t)nrhs * 1024));
+    MM_TRY(dalloc(P, &d->counters, nrhs));
+    MM_TRY(dalloc(P, &d->counters2, nrhs));
+    MM_CUDA(cudaMemset(d->counters, 0, nrhs * sizeof(unsigned)));
+    MM_CUDA(cudaMemset(d->counters2, 0, nrhs * sizeof(unsigned)));
+    d->nrhs_cap = nrhs;
+  }
+  (void)n_blocks;
+  out->k = d->k;
+  out->Z = d->Z;
+  out->Zp = d->Zp;
+  out->Einv = d->Einv;
+  out->y = d->y;
+  out->part = d->part;
+  out->part2 = d->part2;
+  out->counters = d->counters;
+  out->counters2 = d->counters2;
   return MM_OK;
 }
 
@@ -756,7 +806,11 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
   Plan* P = reinterpret_cast<Plan*>(plan);
   if (!P || !b || !x || !opts || !info || nrhs <= 0) return fail(MM_EINVAL, "bad argument");
   if (!(opts->tol > 0.0) || opts->max_iter < 0) return fail(MM_EINVAL, "bad tol / max_iter");
-  if (opts->precond != MM_PREC_BD) return fail(MM_EINVAL, "unsupported preconditioner");
+  if (opts->precond != MM_PREC_BD && opts->precond != MM_PREC_2LVL_POST)
+    return fail(MM_EINVAL, "unsupported preconditioner");
+  DeflState* dst = reinterpret_cast<DeflState*>(P->defl);
+  if (opts->precond == MM_PREC_2LVL_POST && (!dst || dst->k == 0))
+    return fail(MM_EINVAL, "MM_PREC_2LVL_POST needs mm_deflation_build on the plan");
   if (opts->precision != MM_FP64 && opts->precision != MM_FP32) return fail(MM_EINVAL, "bad precision");
   DeviceGuard g(P->device);
   const auto t0 = std::chrono::steady_clock::now();
@@ -769,6 +823,12 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
   MM_TRY(ensure_cg(P, nrhs, fp32, &c));
   CgWork w = make_work(P, c, nrhs, fp32, opts->tol, opts->max_iter);
   if (P->algo == MM_TPLZ_DIRECT) MM_TRY(ensure_td(P));
+  DeflWork dw{};
+  const DeflWork* dwp = nullptr;
+  if (opts->precond == MM_PREC_2LVL_POST) {
+    MM_TRY(ensure_defl_work(P, dst, nrhs, w.n_blocks, &dw));
+    dwp = &dw;
+  }
 
   cudaEvent_t ev;
   MM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -777,10 +837,11 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
 
   MM_CUDA(launch_pack3to4(b, P->n_obs, nrhs, c->b, s));
   MM_CUDA(launch_cg(CG_INIT, w, s));
+  if (dwp) MM_CUDA(launch_defl_step(dw, w, s));
 
   // graph of `chunk` iterations, cached on the plan
   if (opts->profile == 0 && (!c->exec || c->g_nrhs != nrhs || c->g_fp32 != (int)fp32 || c->g_chunk != chunk ||
-      c->g_tol2 != w.tol2 || c->g_maxit != opts->max_iter)) {
+      c->g_tol2 != w.tol2 || c->g_maxit != opts->max_iter || c->g_prec != opts->precond)) {
     if (c->exec) {
       cudaGraphExecDestroy(c->exec);
       c->exec = nullptr;
@@ -788,7 +849,7 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
     cudaGraph_t graph;
     MM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     int st = MM_OK;
-    for (int k = 0; k < chunk && st == MM_OK; k++) st = enqueue_iteration(P, w, nrhs, fp32, s);
+    for (int k = 0; k < chunk && st == MM_OK; k++) st = enqueue_iteration(P, w, nrhs, fp32, s, dwp);
     cudaError_t ce = cudaStreamEndCapture(s, &graph);
     if (st != MM_OK) return st;
     MM_CUDA(ce);
@@ -800,6 +861,7 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
     c->g_chunk = chunk;
     c->g_tol2 = w.tol2;
     c->g_maxit = opts->max_iter;
+    c->g_prec = opts->precond;
   }
 
   std::vector<int> timed_out(nrhs, 0);
@@ -872,11 +934,17 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
       MM_TRY(timed_apply64(reinterpret_cast<const int32_t*>(c->scal) + kDoneOffsetInts));
       MM_CUDA(launch_cg(CG_REPLACE, w, s));
       n_kernels += 1;
+      if (dwp) {
+        DeflWork dr = dw;
+        dr.restart = 1;
+        MM_CUDA(launch_defl_step(dr, w, s));
+        n_kernels += 2;
+      }
       continue;
     }
     if (!profile) {
       MM_CUDA(cudaGraphLaunch(c->exec, s));
-      n_kernels += (int64_t)chunk * (fp32 || P->algo != MM_TPLZ_DIRECT ? 4 : 3 + 3 * nrhs);
+      n_kernels += (int64_t)chunk * ((fp32 || P->algo != MM_TPLZ_DIRECT ? 4 : 3 + 3 * nrhs) + (dwp ? 2 : 0));
       if (fp32) n32 += chunk; else n64 += chunk;
     } else {
       for (int k = 0; k < chunk; k++) {
@@ -894,6 +962,10 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
         MM_CUDA(launch_cg(CG_DOT_PQ, w, s));
         MM_CUDA(launch_cg(CG_UPDATE, w, s));
         n_kernels += (fp32 || P->algo != MM_TPLZ_DIRECT) ? 4 : 3 + 3 * nrhs;
+        if (dwp) {
+          MM_CUDA(launch_defl_step(dw, w, s));
+          n_kernels += 2;
+        }
       }
     }
   }
@@ -1095,6 +1167,150 @@ int mm_block_cg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, int 
   cudaEventDestroy(ev);
   if (worst != MM_OK) set_error("block CG did not converge for every right-hand side");
   return worst;
+}
+
+int mm_deflation_build(mm_plan_t plan, const double* b, int m, int precision, void* stream) {
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  if (!P || !b) return fail(MM_EINVAL, "bad argument");
+  if (m < 1 || m > kMaxDefl) return fail(MM_EINVAL, "m must lie in [1, 64]");
+  if (precision != MM_FP64 && precision != MM_FP32) return fail(MM_EINVAL, "bad precision");
+  if (P->algo == MM_TPLZ_DIRECT && precision == MM_FP32) precision = MM_FP64;
+  DeviceGuard g(P->device);
+  cudaStream_t us = as_stream(stream);
+  cudaStream_t s = P->stream;
+  cudaEvent_t ev;
+  MM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  MM_CUDA(cudaEventRecord(ev, us));
+  MM_CUDA(cudaStreamWaitEvent(s, ev, 0));
+  cudaEventDestroy(ev);
+  const int64_t n = P->n_obs, n4 = 4 * n;
+  Scratch scr;
+  double *v_prev = nullptr, *v = nullptr, *wv = nullptr, *av = nullptr, *part = nullptr, *dot = nullptr;
+  double *alpha_d = nullptr, *beta_d = nullptr, *work = nullptr, *U = nullptr, *X = nullptr, *wvals = nullptr,
+         *E = nullptr, *gpart = nullptr;
+  float *V32 = nullptr, *AV32 = nullptr, *x32 = nullptr, *y32 = nullptr;
+  const int nblk = 4 * 152;
+  MM_TRY(scr.alloc(&v_prev, n4)); MM_TRY(scr.alloc(&v, n4)); MM_TRY(scr.alloc(&wv, n4)); MM_TRY(scr.alloc(&av, n4));
+  MM_TRY(scr.alloc(&part, nblk)); MM_TRY(scr.alloc(&dot, 2));
+  MM_TRY(scr.alloc(&alpha_d, kMaxDefl)); MM_TRY(scr.alloc(&beta_d, kMaxDefl));
+  MM_TRY(scr.alloc(&work, kMaxDefl * kMaxDefl)); MM_TRY(scr.alloc(&U, kMaxDefl * kMaxDefl));
+  MM_TRY(scr.alloc(&X, kMaxDefl * kMaxDefl)); MM_TRY(scr.alloc(&wvals, kMaxDefl));
+  MM_TRY(scr.alloc(&E, kMaxDefl * kMaxDefl));
+  MM_TRY(scr.alloc(&gpart, (size_t)2 * 152 * kMaxBlk * kMaxBlk));
+  MM_TRY(scr.alloc(&V32, (size_t)m * n4)); MM_TRY(scr.alloc(&AV32, (size_t)m * n4));
+  if (precision == MM_FP32) { MM_TRY(scr.alloc(&x32, n4)); MM_TRY(scr.alloc(&y32, n4)); }
+  auto host_dot = [&](const double* a_, const double* b_, double* out) -> int {
+    MM_CUDA(launch_ldot(a_, b_, n4, part, nblk, dot, s));
+    MM_CUDA(cudaMemcpyAsync(out, dot, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MM_CUDA(cudaStreamSynchronize(s));
+    return MM_OK;
+  };
+  // v_1 = b / ||b||, v_0 = 0
+  MM_CUDA(launch_pack3to4(b, n, 1, v, s));
+  MM_CUDA(cudaMemsetAsync(v_prev, 0, n4 * sizeof(double), s));
+  double bb = 0.0;
+  MM_TRY(host_dot(v, v, &bb));
+  if (!(bb > 0.0) || !std::isfinite(bb)) return fail(MM_EBREAKDOWN, "mm_deflation_build: b = 0");
+  MM_CUDA(launch_laxpby(0.0, v, 1.0 / std::sqrt(bb), v, n4, s));
+  std::vector<double> alphas, betas;
+  double beta_k = 0.0;
+  const double eps = 2.220446049250313e-16;
+  for (int kk = 0; kk < m; kk++) {
+    // A v_k (stored), then w = A v_k - beta_k v_{k-1}; alpha = <w, v_k>; w -= alpha v_k
+    MM_CUDA(cudaMemsetAsync(av, 0, n4 * sizeof(double), s));
+    if (precision == MM_FP32) {
+      MM_CUDA(launch_to32(v, n, x32, s));
+      MM_CUDA(cudaMemsetAsync(y32, 0, n4 * sizeof(float), s));
+      MM_TRY(apply32_internal(P, x32, y32, 1, s));
+      MM_CUDA(launch_to64(y32, n, av, s));
+    } else {
+      MM_TRY(apply64_internal(P, v, av, 1, s));
+    }
+    MM_CUDA(launch_to32(v, n, V32 + (size_t)kk * n4, s));
+    MM_CUDA(launch_to32(av, n, AV32 + (size_t)kk * n4, s));
+    MM_CUDA(cudaMemcpyAsync(wv, av, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    MM_CUDA(launch_laxpby(-beta_k, v_prev, 1.0, wv, n4, s));
+    double al = 0.0;
+    MM_TRY(host_dot(wv, v, &al));
+    MM_CUDA(launch_laxpby(-al, v, 1.0, wv, n4, s));
+    double ww = 0.0;
+    MM_TRY(host_dot(wv, wv, &ww));
+    alphas.push_back(al);
+    const double beta_next = std::sqrt(std::max(ww, 0.0));
+    if (!std::isfinite(al) || !std::isfinite(beta_next)) return fail(MM_EBREAKDOWN, "Lanczos breakdown");
+    if (beta_next < eps) break;
+    betas.push_back(beta_next);
+    beta_k = beta_next;
+    std::swap(v_prev, v);                                       // v_prev = v_k
+    MM_CUDA(launch_laxpby(1.0 / beta_next, wv, 0.0, v, n4, s));   // v = w / beta
+  }
+  const int k = (int)alphas.size();
+  std::vector<double> bpad(kMaxDefl, 0.0);
+  for (int i = 0; i + 1 < k; i++) bpad[i] = betas[i];
+  MM_CUDA(cudaMemcpyAsync(alpha_d, alphas.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
+  MM_CUDA(cudaMemcpyAsync(beta_d, bpad.data(), kMaxDefl * sizeof(double), cudaMemcpyHostToDevice, s));
+  MM_CUDA(launch_tridiag_eig(alpha_d, beta_d, k, work, wvals, X, s));
+  // replace the plan's space
+  DeflState* d = reinterpret_cast<DeflState*>(P->defl);
+  if (!d) {
+    d = new DeflState();
+    P->defl = d;
+  }
+  dfree(d->Z); dfree(d->Zp); dfree(d->Einv);
+  d->k = 0;
+  MM_TRY(dalloc(P, &d->Z, (size_t)k * n4));
+  MM_TRY(dalloc(P, &d->Zp, (size_t)k * n4));
+  MM_TRY(dalloc(P, &d->Einv, (size_t)k * k));
+  // Z = V X, Z' = (A V) X, E = Z^T Z', Einv = pinv(E)
+  MM_CUDA(launch_bcombine(d->Z, 0, nullptr, k, V32, k, X, k, 1.0, 0, n, nullptr, 2 * 152, nullptr, s));
+  MM_CUDA(launch_bcombine(d->Zp, 0, nullptr, k, AV32, k, X, k, 1.0, 0, n, nullptr, 2 * 152, nullptr, s));
+  MM_CUDA(launch_bgram(d->Z, k, nullptr, d->Zp, 0, k, nullptr, n, gpart, 2 * 152, E, s));
+  MM_CUDA(launch_pinv_sym(E, k, 1e-12, work, U, wvals + 0, d->Einv, s));
+  std::vector<double> th(k);
+  MM_CUDA(launch_tridiag_eig(alpha_d, beta_d, k, work, wvals, X, s));   // Ritz values again (wvals reused)
+  MM_CUDA(cudaMemcpyAsync(th.data(), wvals, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MM_CUDA(cudaStreamSynchronize(s));
+  d->theta = th;
+  d->k = k;
+  d->n = n;
+  return MM_OK;
+}
+
+int mm_deflation_get(mm_plan_t plan, int* k, double* Z, double* theta, void* stream) {
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  if (!P || !k) return fail(MM_EINVAL, "bad argument");
+  DeflState* d = reinterpret_cast<DeflState*>(P->defl);
+  *k = d ? d->k : 0;
+  if (!d || d->k == 0) return MM_OK;
+  DeviceGuard g(P->device);
+  cudaStream_t s = as_stream(stream);
+  if (Z) {
+    // float32 [k][n][4] -> float64 [k][n][3] through a temporary FP64 copy in the map buffers
+    MM_TRY(ensure_maps(P, d->k, false));
+    MM_CUDA(launch_to64(d->Z, (int64_t)d->k * P->n_obs, P->map64_in, s));
+    MM_CUDA(launch_unpack4to3(P->map64_in, P->n_obs, d->k, Z, s));
+  }
+  if (theta) std::memcpy(theta, d->theta.data(), d->k * sizeof(double));
+  return MM_OK;
+}
+
+int mm_deflation_apply(mm_plan_t plan, const double* r, double* z, int nrhs, void* stream) {
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  if (!P || !r || !z || nrhs <= 0) return fail(MM_EINVAL, "bad argument");
+  DeflState* d = reinterpret_cast<DeflState*>(P->defl);
+  if (!d || d->k == 0) return fail(MM_EINVAL, "no deflation space: call mm_deflation_build first");
+  DeviceGuard g(P->device);
+  cudaStream_t s = as_stream(stream);
+  CgState* c = nullptr;
+  MM_TRY(ensure_cg(P, nrhs, false, &c));
+  CgWork w = make_work(P, c, nrhs, false, 1.0, 1);
+  DeflWork dw{};
+  MM_TRY(ensure_defl_work(P, d, nrhs, w.n_blocks, &dw));
+  MM_CUDA(launch_pack3to4(r, P->n_obs, nrhs, c->r, s));
+  MM_CUDA(cudaMemsetAsync(c->scal, 0, nrhs * sizeof(CgScalars), s));   // halt = 0
+  MM_CUDA(launch_defl_step(dw, w, s));
+  MM_CUDA(launch_unpack4to3(c->z, P->n_obs, nrhs, z, s));
+  return MM_OK;
 }
 
 }  // extern "C"

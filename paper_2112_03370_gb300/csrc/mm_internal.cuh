@@ -111,6 +111,7 @@ struct Plan {
   cudaStream_t stream = nullptr;       // plan-owned stream (graph capture)
   void* cg = nullptr;                  // solver workspace (mm_api.cu)
   void* blk = nullptr;                 // block-CG workspace (mm_api.cu)
+  void* defl = nullptr;                // two-level deflation space (mm_api.cu)
 
   size_t bytes = 0;
 };

@@ -19,14 +19,15 @@ MM_OK, MM_EINVAL, MM_ENOMEM, MM_ENOTSPD, MM_EBREAKDOWN, MM_ENOTCONV, MM_ETIMEOUT
     MM_ECUDA = range(9)
 MM_FP64, MM_FP32 = 0, 1
 MM_TPLZ_AUTO, MM_TPLZ_FFT, MM_TPLZ_DIRECT = 0, 1, 3
-MM_PREC_BD = 0
+MM_PREC_BD, MM_PREC_2LVL_POST = 0, 1
 STATUS_NAMES = {0: "MM_OK", 1: "MM_EINVAL", 2: "MM_ENOMEM", 3: "MM_ENOTSPD", 4: "MM_EBREAKDOWN",
                 5: "MM_ENOTCONV", 6: "MM_ETIMEOUT", 7: "MM_EBUSY", 8: "MM_ECUDA"}
 
 # the exported entry points of include/mm.h
 EXPORTS = ("mm_plan", "mm_plan_query", "mm_plan_destroy", "mm_apply_P", "mm_apply_Pt",
            "mm_apply_Ninv", "mm_rhs", "mm_apply_A", "mm_precond", "mm_pcg_solve", "mm_last_error",
-           "mm_apply_A_noalloc", "mm_block_cg_solve")
+           "mm_apply_A_noalloc", "mm_block_cg_solve", "mm_deflation_build", "mm_deflation_get",
+           "mm_deflation_apply")
 
 
 class ProblemDesc(ctypes.Structure):
@@ -80,6 +81,9 @@ def _load():
                                  ctypes.POINTER(SolveInfo), vp]
     lib.mm_block_cg_solve.argtypes = [vp, vp, vp, i32, i32, ctypes.POINTER(SolveOpts),
                                       ctypes.POINTER(SolveInfo), vp]
+    lib.mm_deflation_build.argtypes = [vp, vp, i32, i32, vp]
+    lib.mm_deflation_get.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp, vp, vp]
+    lib.mm_deflation_apply.argtypes = [vp, vp, vp, i32, vp]
     lib.mm_last_error.restype = ctypes.c_char_p
     for n in EXPORTS:
         if n not in ("mm_plan_destroy", "mm_last_error"):
@@ -238,11 +242,11 @@ def mm_precond(plan: Plan, r: torch.Tensor, z: torch.Tensor, stream=None):
 def mm_pcg_solve(plan: Plan, b: torch.Tensor, x: torch.Tensor, tol: float = 1e-6,
                  max_iter: int = 10000, precision: int = MM_FP64, reliable_every: int = 0,
                  check_every: int = 0, deadline_us: int = 0, profile: bool = False, stream=None,
-                 raise_on_error=True):
+                 raise_on_error=True, precond: int = MM_PREC_BD):
     """Solve A x = b (b, x: [nrhs, n_obs, 3] or [n_obs, 3]); returns a list of SolveInfo."""
     _dev(b, torch.float64, "b"); _dev(x, torch.float64, "x")
     nrhs = 1 if b.dim() <= 2 else b.shape[0]
-    opts = SolveOpts(tol=tol, max_iter=max_iter, precond=MM_PREC_BD, precision=precision,
+    opts = SolveOpts(tol=tol, max_iter=max_iter, precond=precond, precision=precision,
                      reliable_every=reliable_every, check_every=check_every,
                      profile=1 if profile else 0, deadline_us=deadline_us)
     infos = (SolveInfo * nrhs)()
@@ -266,3 +270,33 @@ def mm_block_cg_solve(plan: Plan, b: torch.Tensor, x: torch.Tensor, block_width:
     if raise_on_error and code != MM_OK:
         raise MMError(code, mm_last_error())
     return list(infos)
+
+
+def mm_deflation_build(plan: Plan, b: torch.Tensor, m: int, precision: int = MM_FP64, stream=None):
+    """Two-level a-posteriori deflation space from m Lanczos steps started at b ([n_obs, 3])."""
+    _dev(b, torch.float64, "b")
+    _check(_lib.mm_deflation_build(ctypes.c_void_p(plan.handle), _ptr(b), m, precision,
+                                   _stream_ptr(stream)))
+
+
+def mm_deflation_get(plan: Plan, stream=None):
+    """(k, Z [k, n_obs, 3] float64 CUDA tensor, Ritz values [k] numpy)."""
+    import numpy as np
+    k = ctypes.c_int()
+    _check(_lib.mm_deflation_get(ctypes.c_void_p(plan.handle), ctypes.byref(k), None, None,
+                                 _stream_ptr(stream)))
+    if k.value == 0:
+        return 0, None, None
+    Z = torch.empty(k.value, plan.n_obs, 3, dtype=torch.float64, device="cuda")
+    theta = np.zeros(k.value)
+    _check(_lib.mm_deflation_get(ctypes.c_void_p(plan.handle), ctypes.byref(k), _ptr(Z),
+                                 theta.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream)))
+    return k.value, Z, theta
+
+
+def mm_deflation_apply(plan: Plan, r: torch.Tensor, z: torch.Tensor, stream=None):
+    """z = M_2lvl r (Eq. 2lvlDef0) for r, z [nrhs, n_obs, 3] or [n_obs, 3]."""
+    _dev(r, torch.float64, "r"); _dev(z, torch.float64, "z")
+    nrhs = 1 if r.dim() <= 2 else r.shape[0]
+    _check(_lib.mm_deflation_apply(ctypes.c_void_p(plan.handle), _ptr(r), _ptr(z), nrhs,
+                                   _stream_ptr(stream)))
