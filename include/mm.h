@@ -35,6 +35,8 @@ extern "C" {
 #endif
 
 typedef struct mm_plan_s* mm_plan_t;
+typedef struct mm_server_s* mm_server_t;
+typedef int64_t mm_req_t;
 
 typedef enum {
   MM_OK = 0,
@@ -127,12 +129,13 @@ typedef struct {
   double true_rel_res;   /* ||b - A x|| / ||b|| from an FP64 A-application after the solve */
   double t_ms;           /* wall time of the solve */
   int32_t n_true_res;    /* FP64 true-residual evaluations (FP32 path) */
-  int32_t pad_;
+  int32_t batch;         /* server: most requests that shared an A-application launch with it */
   double t_apply32_ms;   /* profile = 1: summed device time of the FP32 A-application launches */
   double t_apply64_ms;   /* profile = 1: same for the FP64 A-applications */
   int32_t n_apply32;     /* FP32 A-application launches (all columns in one launch) */
   int32_t n_apply64;     /* FP64 A-application launches */
   int64_t n_kernels;     /* kernels launched by the solve (its own, all columns) */
+  double t_queue_ms;     /* server: time from mm_submit to admission (t_ms then runs to completion) */
 } mm_solve_info;
 
 /* Build a plan: validate, copy inputs, compact observed pixels, build and invert the 3x3 BD
@@ -225,6 +228,34 @@ int mm_deflation_get(mm_plan_t plan, int* k, double* Z, double* theta, void* str
 /* z = M_2lvl r = M_BD (r - Z' E^-1 Z^T r) + Z E^-1 Z^T r (Eq. 2lvlDef0, applied right to left)
  * for nrhs vectors [nrhs][n_obs][3]; needs mm_deflation_build.  Asynchronous on stream. */
 int mm_deflation_apply(mm_plan_t plan, const double* r, double* z, int nrhs, void* stream);
+
+/*
+ * Serving: a request loop with continuous batching (the serving form of the spec task; the
+ * paper has none).  A server thread owns one CUDA stream on the current device.  Requests wait in a
+ * queue and are admitted while fewer than max_slots run and the estimated device footprint of the
+ * running ones stays within hbm_budget; an admitted request's plan (pointing, bands, spectra,
+ * block-Jacobi blocks) and PCG state stay resident until it finishes.  Every step runs one PCG
+ * iteration of every running request with a single Toeplitz-tile launch over all of their tiles
+ * (FP32 operators; FP64 residual replacement per request as in mm_pcg_solve); requests join and
+ * leave between steps.
+ */
+/* Create a server (hbm_budget in bytes, 0 = 80% of the free device memory; max_slots >= 1). */
+int mm_server_create(size_t hbm_budget, int max_slots, mm_server_t* out);
+/* Queue a map-making solve.  desc and d are HOST memory (desc->inputs_on_device must be 0) and are
+ * copied before the call returns; d is the float64 TOD [N].  opts->precision must be MM_FP32.
+ * Non-blocking; *id identifies the request.  MM_EINVAL on bad input (validated again at admission:
+ * a request that fails there finishes with that status). */
+int mm_submit(mm_server_t server, const mm_problem_desc* desc, const double* d, const mm_solve_opts* opts,
+              mm_req_t* id);
+/* MM_EBUSY while the request is queued or running; MM_OK (info filled) once it has finished. */
+int mm_poll(mm_server_t server, mm_req_t id, mm_solve_info* info);
+/* Wait up to timeout_us (< 0: forever) for the request, then copy its map into map_host
+ * ([n_pix][3] float64 in global pixel order, 0 at unobserved or excised pixels; may be NULL) and
+ * its info, and forget the request.  MM_ETIMEOUT if it did not finish in time (it keeps running);
+ * otherwise the request's own status. */
+int mm_wait(mm_server_t server, mm_req_t id, int64_t timeout_us, double* map_host, mm_solve_info* info);
+/* Stop the server thread (running requests are abandoned) and free everything.  NULL is a no-op. */
+void mm_server_destroy(mm_server_t server);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* mm_last_error(void);

@@ -223,8 +223,8 @@ __device__ __forceinline__ void scatter_quads(const TileArgs& a, int rhs, const 
 }  // namespace
 
 // One overlap-save tile (CL = 1) or half a tile (CL = 2) per CTA.
-template <typename T, int CL, int MODE>
-__global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a) {
+template <typename T, int CL, int MODE, bool MULTI = false>
+__global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
   using C = typename V2<T>::t;
   constexpr int LOGMS = kLogM - (CL == 2 ? 1 : 0);
   constexpr int MS = 1 << LOGMS;
@@ -236,11 +236,17 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a) {
 
   const int64_t unit = blockIdx.x / CL;
   const int rank = (CL == 2) ? (int)(blockIdx.x % CL) : 0;
-  const int rhs = (int)(unit % a.nrhs);
+  const int rhs = (int)(unit % a_in.nrhs);
+  const int64_t tile_id = unit / a_in.nrhs;
+  const TileDesc seg = a_in.tiles[tile_id];
+  TileArgs a = a_in;
+  if constexpr (MULTI) {   // this tile's problem
+    const ProbPtrs pp = a_in.probs[seg.prob];
+    a.lpix = pp.lpix; a.psi = pp.psi; a.w64 = pp.w64; a.tab = pp.tab;
+    a.x = pp.x; a.y = pp.y; a.done = pp.done;
+  }
   // both CTAs of a cluster read the same flag, so they leave together
   if (a.done != nullptr && a.done[(int64_t)rhs * a.done_stride] != 0) return;
-  const int64_t tile_id = unit / a.nrhs;
-  const TileDesc seg = a.tiles[tile_id];
   const C* __restrict__ tw_g = reinterpret_cast<const C*>(a.tw);
   const TwiddleTab<C> tw = load_twiddle_tab<C, kM, kTileThreads>(tw_sm, tw_g);
   const C* __restrict__ tab =
@@ -410,6 +416,7 @@ int tile_kernels_init() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(B));
   MM_SET((k_tile<float, 1, MODE_APPLY>), kSmemMax);
   MM_SET((k_tile<float, 1, MODE_RHS>), kSmemMax);
+  MM_SET((k_tile<float, 1, MODE_APPLY, true>), kSmemMax);
   MM_SET((k_tile<double, 2, MODE_APPLY>), kSmemBytes64);
   MM_SET((k_tile<double, 2, MODE_RHS>), kSmemBytes64);
   MM_SET((k_tile<double, 2, MODE_NINV>), kSmemBytes64);
@@ -423,7 +430,7 @@ int tile_kernels_init() {
   return status;
 }
 
-template <typename T, int CL, int MODE>
+template <typename T, int CL, int MODE, bool MULTI = false>
 static cudaError_t launch_tiles(const TileArgs& a, size_t smem, cudaStream_t s) {
   const int64_t n_cta = a.n_tiles * a.nrhs * CL;
   if (n_cta == 0) return cudaSuccess;
@@ -444,7 +451,7 @@ static cudaError_t launch_tiles(const TileArgs& a, size_t smem, cudaStream_t s) 
   }
   cfg.attrs = attr;
   cfg.numAttrs = na;
-  return cudaLaunchKernelEx(&cfg, k_tile<T, CL, MODE>, a);
+  return cudaLaunchKernelEx(&cfg, k_tile<T, CL, MODE, MULTI>, a);
 }
 
 // FP32 segments; halo_samples = largest L - vstep of the segments that walk more than one tile
@@ -454,6 +461,12 @@ cudaError_t launch_tiles_fp32(int mode, const TileArgs& a, int halo_samples, cud
   if (mode == MODE_APPLY) return launch_tiles<float, 1, MODE_APPLY>(a, smem, s);
   if (mode == MODE_RHS) return launch_tiles<float, 1, MODE_RHS>(a, smem, s);
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_tiles_fp32_multi(const TileArgs& a, int halo_samples, cudaStream_t s) {
+  const size_t smem = kSmemBytes32 + (size_t)halo_samples * sizeof(float);
+  if (smem > kSmemMax || a.nrhs != 1 || a.probs == nullptr) return cudaErrorInvalidValue;
+  return launch_tiles<float, 1, MODE_APPLY, true>(a, smem, s);
 }
 
 int fp32_max_halo_samples() { return (int)((kSmemMax - kSmemBytes32) / sizeof(float)); }

@@ -179,6 +179,23 @@ cudaError_t launch_to64(const float* x4, int64_t n4, double* y4, cudaStream_t s)
   return cudaGetLastError();
 }
 
+// map [n_pix][3] (pre-zeroed) at obs_to_global[i] <- x [n_obs][4]
+__global__ void k_to_global(const double* __restrict__ x4, const int32_t* __restrict__ o2g, int64_t n,
+                            double* __restrict__ map3) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = o2g[i];
+    map3[3 * p] = x4[4 * i];
+    map3[3 * p + 1] = x4[4 * i + 1];
+    map3[3 * p + 2] = x4[4 * i + 2];
+  }
+}
+
+cudaError_t launch_to_global(const double* x4, const int32_t* o2g, int64_t n, double* map3, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_to_global<<<grid_for(n), kNT, 0, s>>>(x4, o2g, n, map3);
+  return cudaGetLastError();
+}
+
 // z = M_BD r per pixel (symmetric 3x3 stored as 00 01 02 11 12 22)
 __device__ __forceinline__ void bd3(const double* __restrict__ m, double r0, double r1, double r2,
                                     double& z0, double& z1, double& z2) {

@@ -1,6 +1,10 @@
 // C ABI of libmm: plan construction, the operators of the map-making system and the PCG driver.
 #include <algorithm>
 #include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -424,6 +428,7 @@ int build_plan(const mm_problem_desc* d, cudaStream_t us, Plan* P) {
   std::vector<TileDesc> segs = make_tiles(P->block_off, bt, lam, (int)steps, fp32_max_halo_samples(),
                                           &P->seg_halo);
   P->n_segs = (int64_t)segs.size();
+  P->segs_host = segs;
   MM_TRY(dalloc(P, &P->segs, segs.size()));
   MM_CUDA(cudaMemcpyAsync(P->segs, segs.data(), segs.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, s));
   MM_CUDA(cudaStreamSynchronize(s));
@@ -655,6 +660,265 @@ int blk_apply(Plan* P, BlkState* b, int t, bool fp32, cudaStream_t s) {
   MM_TRY(apply64_internal(P, b->AX, b->T64, t, s));
   MM_CUDA(launch_to32(b->T64, (int64_t)(n4 / 4), b->AZ, s));
   return MM_OK;
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// serving: continuous batching of PCG solves
+// ---------------------------------------------------------------------------------------------
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  mm_req_t id = 0;
+  mm_problem_desc desc{};
+  std::vector<int64_t> block_len;
+  std::vector<int32_t> pix;
+  std::vector<float> psi;
+  std::vector<double> band;
+  std::vector<double> d;
+  mm_solve_opts opts{};
+  size_t footprint = 0;
+  int state = 0;                  // 0 queued, 1 running, 2 finished
+  Plan* plan = nullptr;
+  CgState* cg = nullptr;
+  CgWork w{};
+  double* d_dev = nullptr;
+  double* b_dev = nullptr;
+  CgScalars* scal_host = nullptr; // pinned
+  std::vector<double> map;        // [n_pix][3]
+  mm_solve_info info{};
+  int batch = 1;
+  int launched = 0;
+  Clock::time_point t_submit, t_admit;
+};
+
+struct Server {
+  size_t budget = 0;
+  int max_slots = 1;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request*> queue;
+  std::vector<Request*> running;   // touched by the server thread only
+  std::unordered_map<mm_req_t, Request*> all;
+  size_t used = 0;
+  bool stop = false;
+  mm_req_t next_id = 1;
+  std::thread th;
+  TileDesc* tiles_dev = nullptr;
+  size_t tiles_cap = 0;
+  ProbPtrs* probs_dev = nullptr;
+  size_t probs_cap = 0;
+  int64_t n_tiles = 0;
+  int halo = 0;
+  bool dirty = true;
+};
+
+size_t estimate_footprint(const Request& r) {
+  int64_t N = 0;
+  for (int64_t v : r.block_len) N += v;
+  return (size_t)N * 44 + (size_t)r.desc.n_pix * 480 + ((size_t)64 << 20);
+}
+
+void finish_request(Server* S, Request* r, int status) {
+  if (r->plan) {
+    free_plan(r->plan);
+    r->plan = nullptr;
+  }
+  if (r->d_dev) cudaFree(r->d_dev);
+  if (r->b_dev) cudaFree(r->b_dev);
+  r->d_dev = r->b_dev = nullptr;
+  if (r->scal_host) cudaFreeHost(r->scal_host);
+  r->scal_host = nullptr;
+  r->info.status = status;
+  r->info.batch = r->batch;
+  std::lock_guard<std::mutex> lock(S->mu);
+  r->state = 2;
+  S->used -= std::min(S->used, r->footprint);
+  r->pix.clear(); r->pix.shrink_to_fit();
+  r->psi.clear(); r->psi.shrink_to_fit();
+  r->d.clear(); r->d.shrink_to_fit();
+  S->cv_done.notify_all();
+}
+
+// plan + right-hand side + PCG initialisation of an admitted request
+int start_request(Server* S, Request* r) {
+  r->desc.block_len = r->block_len.data();
+  r->desc.pix = r->pix.data();
+  r->desc.psi = r->psi.data();
+  r->desc.band = r->band.data();
+  r->desc.inputs_on_device = 0;
+  r->desc.precision = MM_FP32;
+  r->plan = new Plan();
+  int st = build_plan(&r->desc, S->stream, r->plan);
+  if (st != MM_OK) return st;
+  Plan* P = r->plan;
+  MM_CUDA(cudaMalloc((void**)&r->d_dev, P->N * sizeof(double)));
+  MM_CUDA(cudaMalloc((void**)&r->b_dev, P->n_obs * 3 * sizeof(double)));
+  MM_CUDA(cudaMemcpyAsync(r->d_dev, r->d.data(), P->N * sizeof(double), cudaMemcpyHostToDevice, S->stream));
+  st = mm_rhs(reinterpret_cast<mm_plan_t>(P), r->d_dev, 0, 1, r->b_dev, S->stream);
+  if (st != MM_OK) return st;
+  MM_TRY(ensure_cg(P, 1, true, &r->cg));
+  r->w = make_work(P, r->cg, 1, true, r->opts.tol, r->opts.max_iter);
+  MM_CUDA(cudaMallocHost((void**)&r->scal_host, sizeof(CgScalars)));
+  MM_CUDA(launch_pack3to4(r->b_dev, P->n_obs, 1, r->cg->b, S->stream));
+  MM_CUDA(launch_cg(CG_INIT, r->w, S->stream));
+  r->t_admit = Clock::now();
+  return MM_OK;
+}
+
+// combined tile list and per-problem pointers of the running requests
+int rebuild_launch(Server* S) {
+  std::vector<TileDesc> tiles;
+  std::vector<ProbPtrs> probs;
+  int halo = 0;
+  for (size_t i = 0; i < S->running.size(); i++) {
+    Request* r = S->running[i];
+    Plan* P = r->plan;
+    for (TileDesc td : P->segs_host) {
+      td.prob = (int32_t)i;
+      tiles.push_back(td);
+    }
+    halo = std::max(halo, (int)P->seg_halo);
+    ProbPtrs pp{};
+    pp.lpix = P->lpix;
+    pp.psi = P->psi;
+    pp.w64 = P->w64;
+    pp.tab = P->tab32;
+    pp.x = r->cg->p32;
+    pp.y = r->cg->q32;
+    pp.done = reinterpret_cast<const int32_t*>(r->cg->scal) + kHaltOffsetInts;
+    probs.push_back(pp);
+  }
+  if (tiles.size() > S->tiles_cap) {
+    if (S->tiles_dev) cudaFree(S->tiles_dev);
+    S->tiles_cap = tiles.size() * 2;
+    MM_CUDA(cudaMalloc((void**)&S->tiles_dev, S->tiles_cap * sizeof(TileDesc)));
+  }
+  if (probs.size() > S->probs_cap) {
+    if (S->probs_dev) cudaFree(S->probs_dev);
+    S->probs_cap = probs.size() * 2 + 4;
+    MM_CUDA(cudaMalloc((void**)&S->probs_dev, S->probs_cap * sizeof(ProbPtrs)));
+  }
+  if (!tiles.empty())
+    MM_CUDA(cudaMemcpyAsync(S->tiles_dev, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, S->stream));
+  if (!probs.empty())
+    MM_CUDA(cudaMemcpyAsync(S->probs_dev, probs.data(), probs.size() * sizeof(ProbPtrs), cudaMemcpyHostToDevice, S->stream));
+  MM_CUDA(cudaStreamSynchronize(S->stream));   // host vectors go out of scope
+  S->n_tiles = (int64_t)tiles.size();
+  S->halo = halo;
+  S->dirty = false;
+  return MM_OK;
+}
+
+// map in global pixel order
+int collect_map(Server* S, Request* r) {
+  Plan* P = r->plan;
+  double* gmap = nullptr;
+  MM_CUDA(cudaMalloc((void**)&gmap, (size_t)P->n_pix * 3 * sizeof(double)));
+  MM_CUDA(cudaMemsetAsync(gmap, 0, (size_t)P->n_pix * 3 * sizeof(double), S->stream));
+  MM_CUDA(launch_to_global(r->cg->x, P->obs_to_global, P->n_obs, gmap, S->stream));
+  r->map.resize((size_t)P->n_pix * 3);
+  MM_CUDA(cudaMemcpyAsync(r->map.data(), gmap, r->map.size() * sizeof(double), cudaMemcpyDeviceToHost, S->stream));
+  MM_CUDA(cudaStreamSynchronize(S->stream));
+  cudaFree(gmap);
+  return MM_OK;
+}
+
+void server_loop(Server* S) {
+  cudaSetDevice(S->device);
+  int step = 0;
+  while (true) {
+    // admission
+    {
+      std::unique_lock<std::mutex> lock(S->mu);
+      if (S->running.empty() && S->queue.empty() && !S->stop)
+        S->cv_work.wait_for(lock, std::chrono::milliseconds(50));
+      if (S->stop) break;
+      while (!S->queue.empty() && (int)S->running.size() < S->max_slots &&
+             (S->running.empty() || S->used + S->queue.front()->footprint <= S->budget)) {
+        Request* r = S->queue.front();
+        S->queue.pop_front();
+        S->used += r->footprint;
+        r->state = 1;
+        lock.unlock();
+        const int st = start_request(S, r);
+        lock.lock();
+        if (st != MM_OK) {
+          lock.unlock();
+          finish_request(S, r, st);
+          lock.lock();
+          continue;
+        }
+        S->running.push_back(r);
+        S->dirty = true;
+      }
+    }
+    if (S->running.empty()) continue;
+    if (S->dirty && rebuild_launch(S) != MM_OK) break;
+    const int nb = (int)S->running.size();
+    for (Request* r : S->running) r->batch = std::max(r->batch, nb);
+    // one PCG iteration of every running request, one tile launch for all of them
+    cudaStream_t s = S->stream;
+    for (Request* r : S->running) launch_cg(CG_PUPDATE, r->w, s);
+    TileArgs a{};
+    a.tiles = S->tiles_dev;
+    a.n_tiles = S->n_tiles;
+    a.nrhs = 1;
+    a.tw = S->running[0]->plan->tw32;
+    a.probs = S->probs_dev;
+    a.done_stride = 0;
+    launch_tiles_fp32_multi(a, S->halo, s);
+    for (Request* r : S->running) {
+      launch_cg(CG_DOT_PQ, r->w, s);
+      launch_cg(CG_UPDATE, r->w, s);
+      r->launched += 1;
+    }
+    step += 1;
+    if (step % 4 != 0) continue;
+    for (Request* r : S->running)
+      cudaMemcpyAsync(r->scal_host, r->cg->scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    std::vector<Request*> still;
+    for (Request* r : S->running) {
+      const CgScalars sc = *r->scal_host;
+      const int rel_every = r->opts.reliable_every > 0 ? r->opts.reliable_every : 50;
+      if (!sc.done && (sc.paused || sc.since_rep >= rel_every)) {   // FP64 residual replacement
+        Plan* P = r->plan;
+        cudaMemsetAsync(r->cg->q, 0, P->n_obs * 4 * sizeof(double), s);
+        apply64_internal(P, r->cg->x, r->cg->q, 1, s,
+                         reinterpret_cast<const int32_t*>(r->cg->scal) + kDoneOffsetInts, kScalStrideInts);
+        launch_cg(CG_REPLACE, r->w, s);
+        cudaMemcpyAsync(r->scal_host, r->cg->scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+      }
+      const CgScalars sc2 = *r->scal_host;
+      const double el = std::chrono::duration<double, std::micro>(Clock::now() - r->t_admit).count();
+      const bool late = r->opts.deadline_us > 0 && el > (double)r->opts.deadline_us;
+      if (sc2.done || late) {
+        mm_solve_info& in = r->info;
+        in.iters = sc2.iters;
+        in.rel_res = sc2.bnorm2 > 0 ? std::sqrt(sc2.rr / sc2.bnorm2) : 0.0;
+        in.true_rel_res = sc2.bnorm2 > 0 ? std::sqrt(sc2.rr_true / sc2.bnorm2) : 0.0;
+        in.n_true_res = sc2.n_true;
+        in.t_queue_ms = std::chrono::duration<double, std::milli>(r->t_admit - r->t_submit).count();
+        in.t_ms = std::chrono::duration<double, std::milli>(Clock::now() - r->t_admit).count();
+        in.n_apply32 = r->launched;
+        int st = sc2.done ? sc2.status : MM_ETIMEOUT;
+        if (st == MM_OK && !sc2.done) st = MM_ENOTCONV;
+        if (collect_map(S, r) != MM_OK && st == MM_OK) st = MM_ECUDA;
+        finish_request(S, r, st);
+        S->dirty = true;
+      } else {
+        still.push_back(r);
+      }
+    }
+    S->running.swap(still);
+  }
+  // abandoned requests
+  for (Request* r : S->running) finish_request(S, r, MM_ECUDA);
+  S->running.clear();
 }
 
 }  // namespace
@@ -1004,6 +1268,8 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
     in.true_rel_res = sc.bnorm2 > 0 ? std::sqrt(sc.rr_true / sc.bnorm2) : 0.0;
     in.t_ms = t_ms;
     in.n_true_res = sc.n_true;
+    in.batch = 1;
+    in.t_queue_ms = 0.0;
     in.t_apply32_ms = t32;
     in.t_apply64_ms = t64;
     in.n_apply32 = n32;
@@ -1311,6 +1577,112 @@ int mm_deflation_apply(mm_plan_t plan, const double* r, double* z, int nrhs, voi
   MM_CUDA(launch_defl_step(dw, w, s));
   MM_CUDA(launch_unpack4to3(c->z, P->n_obs, nrhs, z, s));
   return MM_OK;
+}
+
+int mm_server_create(size_t hbm_budget, int max_slots, mm_server_t* out) {
+  if (!out || max_slots < 1) return fail(MM_EINVAL, "bad argument");
+  *out = nullptr;
+  MM_TRY(tile_kernels_init());
+  Server* S = new Server();
+  cudaGetDevice(&S->device);
+  if (hbm_budget == 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    hbm_budget = (size_t)(0.8 * (double)fr);
+  }
+  S->budget = hbm_budget;
+  S->max_slots = max_slots;
+  const cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete S;
+    return cuda_fail(e, "cudaStreamCreate");
+  }
+  S->th = std::thread(server_loop, S);
+  *out = reinterpret_cast<mm_server_t>(S);
+  return MM_OK;
+}
+
+int mm_submit(mm_server_t server, const mm_problem_desc* desc, const double* d, const mm_solve_opts* opts,
+              mm_req_t* id) {
+  Server* S = reinterpret_cast<Server*>(server);
+  if (!S || !desc || !d || !opts || !id) return fail(MM_EINVAL, "bad argument");
+  MM_TRY(validate_desc(desc));
+  if (desc->inputs_on_device) return fail(MM_EINVAL, "mm_submit takes host inputs");
+  if (opts->precision != MM_FP32) return fail(MM_EINVAL, "the server runs the FP32 operators (MM_FP32)");
+  if (opts->precond != MM_PREC_BD) return fail(MM_EINVAL, "the server runs the block-Jacobi preconditioner");
+  if (!(opts->tol > 0.0) || opts->max_iter < 0) return fail(MM_EINVAL, "bad tol / max_iter");
+  Request* r = new Request();
+  r->desc = *desc;
+  const int nb = desc->n_det * desc->n_int;
+  r->block_len.assign(desc->block_len, desc->block_len + nb);
+  int64_t N = 0;
+  for (int64_t v : r->block_len) {
+    if (v < 0) { delete r; return fail(MM_EINVAL, "negative block length"); }
+    N += v;
+  }
+  r->pix.assign(desc->pix, desc->pix + N);
+  r->psi.assign(desc->psi, desc->psi + N);
+  r->band.assign(desc->band, desc->band + (size_t)nb * (desc->lambda + 1));
+  r->d.assign(d, d + N);
+  r->opts = *opts;
+  r->footprint = estimate_footprint(*r);
+  r->t_submit = Clock::now();
+  std::lock_guard<std::mutex> lock(S->mu);
+  r->id = S->next_id++;
+  S->all[r->id] = r;
+  S->queue.push_back(r);
+  *id = r->id;
+  S->cv_work.notify_all();
+  return MM_OK;
+}
+
+int mm_poll(mm_server_t server, mm_req_t id, mm_solve_info* info) {
+  Server* S = reinterpret_cast<Server*>(server);
+  if (!S) return fail(MM_EINVAL, "bad argument");
+  std::lock_guard<std::mutex> lock(S->mu);
+  auto it = S->all.find(id);
+  if (it == S->all.end()) return fail(MM_EINVAL, "unknown request");
+  if (it->second->state != 2) return MM_EBUSY;
+  if (info) *info = it->second->info;
+  return MM_OK;
+}
+
+int mm_wait(mm_server_t server, mm_req_t id, int64_t timeout_us, double* map_host, mm_solve_info* info) {
+  Server* S = reinterpret_cast<Server*>(server);
+  if (!S) return fail(MM_EINVAL, "bad argument");
+  std::unique_lock<std::mutex> lock(S->mu);
+  auto it = S->all.find(id);
+  if (it == S->all.end()) return fail(MM_EINVAL, "unknown request");
+  Request* r = it->second;
+  auto pred = [&] { return r->state == 2; };
+  if (timeout_us < 0) {
+    S->cv_done.wait(lock, pred);
+  } else if (!S->cv_done.wait_for(lock, std::chrono::microseconds(timeout_us), pred)) {
+    return fail(MM_ETIMEOUT, "request still running");
+  }
+  if (map_host && !r->map.empty()) std::memcpy(map_host, r->map.data(), r->map.size() * sizeof(double));
+  if (info) *info = r->info;
+  const int st = r->info.status;
+  S->all.erase(it);
+  delete r;
+  if (st != MM_OK) set_error("request finished with an error status");
+  return st;
+}
+
+void mm_server_destroy(mm_server_t server) {
+  Server* S = reinterpret_cast<Server*>(server);
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->stop = true;
+    S->cv_work.notify_all();
+  }
+  if (S->th.joinable()) S->th.join();
+  for (auto& kv : S->all) delete kv.second;
+  if (S->tiles_dev) cudaFree(S->tiles_dev);
+  if (S->probs_dev) cudaFree(S->probs_dev);
+  if (S->stream) cudaStreamDestroy(S->stream);
+  delete S;
 }
 
 }  // extern "C"

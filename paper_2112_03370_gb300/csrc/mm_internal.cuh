@@ -39,7 +39,18 @@ struct TileDesc {
   int32_t n_steps;  // tiles in the segment (1 on the FP64 path)
   double scale;     // block band / table band
   int32_t vstep;    // output samples per tile (multiple of 4)
-  int32_t pad_;
+  int32_t prob;     // problem index of a multi-problem launch (0 otherwise)
+};
+
+// Per-problem pointers of a launch that batches the tiles of several plans (serving).
+struct ProbPtrs {
+  const int32_t* lpix;
+  const float* psi;
+  const double2* w64;
+  const void* tab;
+  const void* x;
+  void* y;
+  const int32_t* done;
 };
 
 enum Mode { MODE_APPLY = 0, MODE_RHS = 1, MODE_NINV = 2 };
@@ -62,6 +73,7 @@ struct TileArgs {
   int64_t y_stride;
   const int32_t* done;      // optional: skip the work of column r when done[r * done_stride] != 0
   int32_t done_stride;
+  const ProbPtrs* probs;    // multi-problem launches: per-tile pointers (tile.prob), else null
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -95,6 +107,7 @@ struct Plan {
   int64_t n_tiles = 0;
   TileDesc* segs = nullptr;            // FP32 segments (several tiles per descriptor)
   int64_t n_segs = 0;
+  std::vector<TileDesc> segs_host;     // host copy (multi-problem launches)
   int32_t seg_halo = 0;                // largest L - vstep over the segments (samples)
 
   // work buffers (grown on demand)
@@ -167,6 +180,8 @@ cudaError_t launch_twiddles(double2* tw64, float2* tw32, const double* costab, c
 
 // Toeplitz-tile kernels (k_toeplitz.cu)
 cudaError_t launch_tiles_fp32(int mode, const TileArgs& a, int halo_samples, cudaStream_t s);
+// FP32 A-application over the tiles of several plans at once (a.probs set, nrhs = 1)
+cudaError_t launch_tiles_fp32_multi(const TileArgs& a, int halo_samples, cudaStream_t s);
 cudaError_t launch_tiles_fp64(int mode, const TileArgs& a, cudaStream_t s);
 int tile_kernels_init();   // sets smem attributes once per process
 int fp32_max_halo_samples();   // largest halo the FP32 segment kernel can keep in shared memory
@@ -185,6 +200,7 @@ cudaError_t launch_pack3to4(const double* x3, int64_t n, int nrhs, double* x4, c
 cudaError_t launch_unpack4to3(const double* x4, int64_t n, int nrhs, double* x3, cudaStream_t s);
 cudaError_t launch_to32(const double* x4, int64_t n4, float* y4, cudaStream_t s);
 cudaError_t launch_to64(const float* x4, int64_t n4, double* y4, cudaStream_t s);
+cudaError_t launch_to_global(const double* x4, const int32_t* o2g, int64_t n, double* map3, cudaStream_t s);
 cudaError_t launch_bd_apply(const double* minv, int64_t n, int nrhs, const double* r4, double* z4,
                             cudaStream_t s);
 

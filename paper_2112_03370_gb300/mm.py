@@ -27,7 +27,8 @@ STATUS_NAMES = {0: "MM_OK", 1: "MM_EINVAL", 2: "MM_ENOMEM", 3: "MM_ENOTSPD", 4: 
 EXPORTS = ("mm_plan", "mm_plan_query", "mm_plan_destroy", "mm_apply_P", "mm_apply_Pt",
            "mm_apply_Ninv", "mm_rhs", "mm_apply_A", "mm_precond", "mm_pcg_solve", "mm_last_error",
            "mm_apply_A_noalloc", "mm_block_cg_solve", "mm_deflation_build", "mm_deflation_get",
-           "mm_deflation_apply")
+           "mm_deflation_apply", "mm_server_create", "mm_submit", "mm_poll", "mm_wait",
+           "mm_server_destroy")
 
 
 class ProblemDesc(ctypes.Structure):
@@ -49,10 +50,10 @@ class SolveOpts(ctypes.Structure):
 class SolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("rel_res", ctypes.c_double),
                 ("true_rel_res", ctypes.c_double), ("t_ms", ctypes.c_double),
-                ("n_true_res", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("n_true_res", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("t_apply32_ms", ctypes.c_double), ("t_apply64_ms", ctypes.c_double),
                 ("n_apply32", ctypes.c_int32), ("n_apply64", ctypes.c_int32),
-                ("n_kernels", ctypes.c_int64)]
+                ("n_kernels", ctypes.c_int64), ("t_queue_ms", ctypes.c_double)]
 
 
 class MMError(RuntimeError):
@@ -84,9 +85,16 @@ def _load():
     lib.mm_deflation_build.argtypes = [vp, vp, i32, i32, vp]
     lib.mm_deflation_get.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp, vp, vp]
     lib.mm_deflation_apply.argtypes = [vp, vp, vp, i32, vp]
+    lib.mm_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
+    lib.mm_submit.argtypes = [vp, ctypes.POINTER(ProblemDesc), vp, ctypes.POINTER(SolveOpts),
+                              ctypes.POINTER(i64)]
+    lib.mm_poll.argtypes = [vp, i64, ctypes.POINTER(SolveInfo)]
+    lib.mm_wait.argtypes = [vp, i64, i64, vp, ctypes.POINTER(SolveInfo)]
+    lib.mm_server_destroy.argtypes = [vp]
+    lib.mm_server_destroy.restype = None
     lib.mm_last_error.restype = ctypes.c_char_p
     for n in EXPORTS:
-        if n not in ("mm_plan_destroy", "mm_last_error"):
+        if n not in ("mm_plan_destroy", "mm_last_error", "mm_server_destroy"):
             getattr(lib, n).restype = ctypes.c_int
     return lib
 
@@ -300,3 +308,66 @@ def mm_deflation_apply(plan: Plan, r: torch.Tensor, z: torch.Tensor, stream=None
     nrhs = 1 if r.dim() <= 2 else r.shape[0]
     _check(_lib.mm_deflation_apply(ctypes.c_void_p(plan.handle), _ptr(r), _ptr(z), nrhs,
                                    _stream_ptr(stream)))
+
+
+class Server:
+    """mm_server_* : continuous-batching solve server on the current device (host inputs)."""
+
+    def __init__(self, hbm_budget: int = 0, max_slots: int = 8):
+        h = ctypes.c_void_p()
+        _check(_lib.mm_server_create(hbm_budget, max_slots, ctypes.byref(h)))
+        self.handle = h.value
+        self._keep = {}
+
+    def submit(self, n_det, n_int, block_len, n_pix, pix, psi, lam, band, d, tol=1e-6,
+               max_iter=5000, cond_max=1e3, reliable_every=0, deadline_us=0) -> int:
+        import numpy as np
+        pix = np.ascontiguousarray(np.asarray(pix, dtype=np.int32))
+        psi = np.ascontiguousarray(np.asarray(psi, dtype=np.float32))
+        band = np.ascontiguousarray(np.asarray(band, dtype=np.float64))
+        d = np.ascontiguousarray(np.asarray(d, dtype=np.float64))
+        bl = (ctypes.c_int64 * len(block_len))(*[int(v) for v in block_len])
+        desc = ProblemDesc(n_det=n_det, n_int=n_int, block_len=bl, n_pix=n_pix,
+                           pix=pix.ctypes.data, psi=psi.ctypes.data, lambda_=lam,
+                           band=band.ctypes.data, cond_max=cond_max, precision=MM_FP32,
+                           toeplitz_algo=MM_TPLZ_AUTO, inputs_on_device=0, tile_steps=0)
+        opts = SolveOpts(tol=tol, max_iter=max_iter, precond=MM_PREC_BD, precision=MM_FP32,
+                         reliable_every=reliable_every, deadline_us=deadline_us)
+        rid = ctypes.c_int64()
+        _check(_lib.mm_submit(ctypes.c_void_p(self.handle), ctypes.byref(desc),
+                              d.ctypes.data, ctypes.byref(opts), ctypes.byref(rid)))
+        self._keep[rid.value] = n_pix
+        return rid.value
+
+    def poll(self, rid: int):
+        info = SolveInfo()
+        code = _lib.mm_poll(ctypes.c_void_p(self.handle), rid, ctypes.byref(info))
+        if code == MM_EBUSY:
+            return None
+        _check(code)
+        return info
+
+    def wait(self, rid: int, timeout_us: int = -1, raise_on_error=True):
+        import numpy as np
+        n_pix = self._keep[rid]
+        m = np.zeros((n_pix, 3))
+        info = SolveInfo()
+        code = _lib.mm_wait(ctypes.c_void_p(self.handle), rid, timeout_us,
+                            m.ctypes.data, ctypes.byref(info))
+        if code == MM_ETIMEOUT:
+            raise MMError(code, mm_last_error())
+        self._keep.pop(rid, None)
+        if raise_on_error and code != MM_OK:
+            raise MMError(code, mm_last_error())
+        return m, info
+
+    def close(self):
+        if self.handle:
+            _lib.mm_server_destroy(ctypes.c_void_p(self.handle))
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,93 @@
+"""Serving with continuous batching: each request's map is the same solved alone (one slot) and
+in a mix that shares A-application launches, and matches the FP64 oracle (mixed-precision
+tolerance: rel. map error <= 1e-5 at the same tol)."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from gpu_helpers import mm
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-8
+
+
+def requests():
+    out = []
+    for i, (side, ndet, nsamp, lam) in enumerate([(64, 2, 32768, 512), (128, 4, 65536, 1024),
+                                                 (96, 3, 40000, 2048)]):
+        cfg = synth.tiny_config(side=side, n_det=ndet, n_samp=nsamp, lam=lam, config_id=40 + i,
+                                speed=0.25 * side / 128)
+        out.append(synth.to_numpy(synth.make_ground_problem(cfg)))
+    return out
+
+
+def submit(srv, p):
+    return srv.submit(p["n_det"], p["n_int"], p["block_len"].tolist(), p["n_pix"], p["pix"], p["psi"],
+                      p["lam"], p["band"], p["d"], tol=TOL)
+
+
+def oracle_map(p):
+    op = O.make_plan(p["pix"], p["psi"], p["block_len"], p["band"], p["n_pix"])
+    x = O.pcg(op, O.rhs(op, p["d"]), tol=TOL, max_iter=5000).x
+    m = np.zeros((p["n_pix"], 3))
+    m[op.obs_to_global] = x
+    return m
+
+
+@pytest.fixture(scope="module")
+def probs():
+    return requests()
+
+
+def test_alone_equals_mix_and_oracle(probs):
+    m = mm()
+    alone = []
+    srv = m.Server(max_slots=1)
+    for p in probs:
+        mp, info = srv.wait(submit(srv, p))
+        assert info.status == 0 and info.batch == 1 and info.true_rel_res < TOL
+        alone.append(mp)
+    srv.close()
+    srv = m.Server(max_slots=8)
+    ids = [submit(srv, p) for p in probs]
+    mixed = [srv.wait(i) for i in ids]
+    srv.close()
+    assert max(info.batch for _, info in mixed) >= 2          # A-applies shared a launch
+    for p, a, (mx, info) in zip(probs, alone, mixed):
+        assert info.status == 0 and info.true_rel_res < TOL
+        assert np.linalg.norm(mx - a) <= 1e-6 * np.linalg.norm(a)
+        ref = oracle_map(p)
+        assert np.linalg.norm(mx - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+def test_request_admitted_while_another_runs(probs):
+    m = mm()
+    srv = m.Server(max_slots=4)
+    big = submit(srv, probs[1])
+    time.sleep(0.01)
+    small = submit(srv, probs[0])
+    ms, i_small = srv.wait(small)
+    mb, i_big = srv.wait(big)
+    srv.close()
+    assert i_small.status == 0 and i_big.status == 0
+    assert i_small.batch >= 2 and i_big.batch >= 2            # they ran side by side
+
+
+def test_admission_respects_budget_and_bad_request(probs):
+    m = mm()
+    srv = m.Server(hbm_budget=1, max_slots=8)                 # one request at a time
+    ids = [submit(srv, p) for p in probs]
+    infos = [srv.wait(i)[1] for i in ids]
+    assert all(i.status == 0 and i.batch == 1 for i in infos)
+    p = dict(probs[0])
+    p["pix"] = p["pix"].copy()
+    p["pix"][3] = p["n_pix"] + 5                              # invalid pixel: fails at admission
+    bad = submit(srv, p)
+    with pytest.raises(m.MMError) as e:
+        srv.wait(bad)
+    assert e.value.code == m.MM_EINVAL
+    srv.close()
