@@ -53,6 +53,12 @@ def args_parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-dets", type=int, default=16)
+    p.add_argument("--workload", default="ground",
+                   choices=["ground", "batched", "satellite", "serving"])
+    p.add_argument("--nrhs", type=int, default=64, help="batched: noise realisations")
+    p.add_argument("--widths", default="8,16,32,64", help="batched: block widths")
+    p.add_argument("--requests", type=int, default=40, help="serving: requests")
+    p.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
     return p.parse_args()
 
 
@@ -390,10 +396,158 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------------------------------
+# other workloads (one JSON line each; the default line above is the ground workload)
+# ------------------------------------------------------------------------------------------
+
+def _timed(fn):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t0
+
+
+def run_batched(a):
+    """Ground geometry cut to 128 dets x 1 interval x 524,288 samples, nrhs noise realisations:
+    block CG (widths given) vs independent FP64 PCG (rate from two right-hand sides)."""
+    import torch
+    import synth
+    import paper_2112_03370_gb300.mm as mm
+    dev = torch.device("cuda")
+    cfg = synth.batched_config()
+    prob = synth.make_ground_problem(cfg, device=dev, n_real=a.nrhs)
+    plan = mm.mm_plan(prob.n_det, prob.n_int, prob.block_len.tolist(), prob.n_pix, prob.pix, prob.psi,
+                      prob.lam, prob.band.to(dev), precision=mm.MM_FP32)
+    N = plan.n_samples
+    B = torch.empty(a.nrhs, plan.n_obs, 3, dtype=torch.float64, device=dev)
+    mm.mm_rhs(plan, prob.d, B)
+    X = torch.empty_like(B)
+    res = {}
+    for w in [int(v) for v in a.widths.split(",")]:
+        mm.mm_block_cg_solve(plan, B[:w].contiguous(), X[:w].contiguous(), block_width=w, tol=cfg.tol)
+        infos, dt = _timed(lambda: mm.mm_block_cg_solve(plan, B, X, block_width=w, tol=cfg.tol,
+                                                        raise_on_error=False))
+        res[str(w)] = {"solves_per_s": a.nrhs / dt, "s": dt,
+                       "iters_max": max(i.iters for i in infos),
+                       "true_rel_res_max": max(i.true_rel_res for i in infos),
+                       "status": sorted(set(i.status for i in infos)),
+                       "A_column_applies": sum(1 for _ in infos) and infos[0].n_apply32}
+    x1 = torch.empty(2, plan.n_obs, 3, dtype=torch.float64, device=dev)
+    infos, dt64 = _timed(lambda: mm.mm_pcg_solve(plan, B[:2].contiguous(), x1, tol=cfg.tol,
+                                                 precision=mm.MM_FP64, raise_on_error=False))
+    infos32, dt32 = _timed(lambda: mm.mm_pcg_solve(plan, B[:2].contiguous(), x1, tol=cfg.tol,
+                                                   precision=mm.MM_FP32, raise_on_error=False))
+    best = max(res.values(), key=lambda r: r["solves_per_s"])
+    print(json.dumps({
+        "workload": "batched", "metric": "PCG solves/s, 64 noise realisations",
+        "value": best["solves_per_s"], "unit": "solves/s", "higher_is_better": True,
+        "config": {"workload": f"ground cut: {prob.n_det} det x {cfg.n_samp} samples, "
+                               f"{cfg.side}^2 IQU, lambda {cfg.lam}, {a.nrhs} realisations",
+                   "n_samples": N, "n_obs": plan.n_obs, "tol": cfg.tol},
+        "block_cg": res,
+        "fp64_pcg": {"solves_per_s": 2 / dt64, "iters": [i.iters for i in infos]},
+        "fp32_pcg_independent": {"solves_per_s": 2 / dt32, "iters": [i.iters for i in infos32]},
+        "vs_fp64_pcg": best["solves_per_s"] / (2 / dt64)}), flush=True)
+
+
+def run_satellite(a):
+    """Satellite-like full sky: BD vs two-level (16 Ritz vectors) mixed-precision solves."""
+    import torch
+    import synth
+    import paper_2112_03370_gb300.mm as mm
+    dev = torch.device("cuda")
+    cfg = synth.satellite_config(n_det=a.dets if a.dets != 512 else 64)
+    prob, tg = _timed(lambda: synth.make_satellite_problem(cfg, device=dev))
+    plan = mm.mm_plan(prob.n_det, prob.n_int, prob.block_len.tolist(), prob.n_pix, prob.pix, prob.psi,
+                      prob.lam, prob.band.to(dev), precision=mm.MM_FP32)
+    N = plan.n_samples
+    b = torch.empty(plan.n_obs, 3, dtype=torch.float64, device=dev)
+    mm.mm_rhs(plan, prob.d, b)
+    x = torch.empty_like(b)
+    mm.mm_pcg_solve(plan, b, x, tol=cfg.tol, precision=mm.MM_FP32, raise_on_error=False)
+    i_bd, t_bd = _timed(lambda: mm.mm_pcg_solve(plan, b, x, tol=cfg.tol, precision=mm.MM_FP32,
+                                               raise_on_error=False)[0])
+    _, t_build = _timed(lambda: mm.mm_deflation_build(plan, b, 16, precision=mm.MM_FP32))
+    i_2l, t_2l = _timed(lambda: mm.mm_pcg_solve(plan, b, x, tol=cfg.tol, precision=mm.MM_FP32,
+                                               precond=mm.MM_PREC_2LVL_POST, raise_on_error=False)[0])
+    print(json.dumps({
+        "workload": "satellite", "metric": "PCG solves/s (BD vs 2lvl a posteriori, 16 Ritz vectors)",
+        "value": 1.0 / t_2l, "unit": "solves/s", "higher_is_better": True,
+        "config": {"workload": f"satellite: {prob.n_det} det x {cfg.n_samp} samples at 20 Hz, "
+                               f"{cfg.n_rings}x{cfg.n_phi} equal-area pixels, lambda {cfg.lam}",
+                   "n_samples": N, "n_obs": plan.n_obs, "tol": cfg.tol, "gen_s": tg},
+        "bd": {"iters": i_bd.iters, "s": t_bd, "status": i_bd.status, "true_rel_res": i_bd.true_rel_res,
+               "samples_per_s_through_A": N * (i_bd.n_apply32 + i_bd.n_apply64) / t_bd},
+        "two_level": {"iters": i_2l.iters, "s": t_2l, "build_s": t_build, "status": i_2l.status,
+                      "true_rel_res": i_2l.true_rel_res},
+        "speedup_per_solve": t_bd / t_2l,
+        "solves_to_amortise_build": t_build / max(t_bd - t_2l, 1e-9)}), flush=True)
+
+
+def run_serving(a):
+    """Poisson stream (mean `rate`/s) of map-making solves with seeded random shapes from the
+    serving recipe: detectors {8..256}, samples/detector {2^16..2^20}, patch side {64..512},
+    lambda {512..8192}; raster + HWP scan and 1/f noise as in the tiny recipe; tol 1e-6."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2112_03370_gb300.mm as mm
+    rng = np.random.default_rng(synth.seed_for(4, 0))
+    reqs = []
+    for i in range(a.requests):
+        ndet = int(rng.choice([8, 16, 32, 64, 128, 256]))
+        nsamp = int(rng.choice([1 << 16, 1 << 17, 1 << 18, 1 << 19, 1 << 20]))
+        side = int(rng.choice([64, 128, 256, 512]))
+        lam = int(rng.choice([512, 1024, 2048, 4096, 8192]))
+        cfg = synth.tiny_config(config_id=400 + i, n_det=ndet, n_samp=nsamp, side=side, lam=lam,
+                                speed=0.25 * side / 128, det_layout="grid23", tol=1e-6)
+        reqs.append((cfg, float(rng.exponential(1.0 / a.rate))))
+    log(f"serving: generating {len(reqs)} requests")
+    probs = [synth.to_numpy(synth.make_ground_problem(c, device="cuda")) for c, _ in reqs]
+    srv = mm.Server(max_slots=16)
+    # warm-up request (plan + kernels)
+    p = probs[0]
+    srv.wait(srv.submit(p["n_det"], p["n_int"], p["block_len"].tolist(), p["n_pix"], p["pix"], p["psi"],
+                        p["lam"], p["band"], p["d"], tol=1e-6))
+    t0 = time.perf_counter()
+    ids, t_sub = [], []
+    for (cfg, gap), p in zip(reqs, probs):
+        time.sleep(gap)
+        t_sub.append(time.perf_counter())
+        ids.append(srv.submit(p["n_det"], p["n_int"], p["block_len"].tolist(), p["n_pix"], p["pix"],
+                              p["psi"], p["lam"], p["band"], p["d"], tol=1e-6))
+    lat, infos = [], []
+    for i, ts in zip(ids, t_sub):
+        _, info = srv.wait(i, raise_on_error=False)
+        infos.append(info)
+        lat.append((info.t_queue_ms + info.t_ms))
+    dt = time.perf_counter() - t0
+    srv.close()
+    samples = sum(int(p["pix"].size) for p in probs)
+    print(json.dumps({
+        "workload": "serving", "metric": "solves/s + p50/p99 latency (Poisson arrivals)",
+        "value": len(ids) / dt, "unit": "solves/s", "higher_is_better": True,
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "config": {"workload": f"{len(ids)} requests at mean {a.rate}/s, dets 8-256, samples/det "
+                               f"2^16-2^20, side 64-512, lambda 512-8192, tol 1e-6",
+                   "total_samples": samples},
+        "status": sorted(set(i.status for i in infos)),
+        "max_batch": max(i.batch for i in infos),
+        "iters_mean": float(np.mean([i.iters for i in infos]))}), flush=True)
+
+
 def main():
     a = args_parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batched":
+        run_batched(a)
+    elif a.workload == "satellite":
+        run_satellite(a)
+    elif a.workload == "serving":
+        run_serving(a)
     else:
         run_ours(a)
 

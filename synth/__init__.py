@@ -176,6 +176,156 @@ def flag_gaps(pix: torch.Tensor, frac: float, seed: int, run: int = 37) -> torch
     return out
 
 
+@dataclass
+class SatelliteConfig:
+    """Precessing spin scan on the full sky, equal-area lat-long pixels (rings in z x phi)."""
+
+    name: str = "satellite"
+    config_id: int = 2
+    n_det: int = 64
+    n_int: int = 1
+    n_samp: int = 16777216
+    fs: float = 20.0
+    spin_period_s: float = 60.0
+    prec_period_s: float = 96 * 60.0
+    boresight_deg: float = 50.0
+    spin_axis_deg: float = 45.0
+    hwp_hz: float = 1.0
+    hwp_factor: int = 2
+    n_rings: int = 1536
+    n_phi: int = 2048
+    det_offset_deg: float = 0.5
+    sigma_lo: float = 1.0
+    sigma_hi: float = 1.0
+    f_knee: float = 0.05
+    alpha: float = 1.0
+    lam: int = 4096
+    tol: float = 1e-6
+    sigma_I: float = 1.0
+    sigma_QU: float = 0.1
+    gap_frac: float = 0.0
+
+    @property
+    def n_blocks(self) -> int:
+        return self.n_det * self.n_int
+
+    @property
+    def n_total(self) -> int:
+        return self.n_blocks * self.n_samp
+
+    @property
+    def n_pix(self) -> int:
+        return self.n_rings * self.n_phi
+
+
+def satellite_config(**kw) -> SatelliteConfig:
+    c = SatelliteConfig()
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def _rot_to(axis: torch.Tensor, v: torch.Tensor) -> torch.Tensor:
+    """Rotate vectors v given in a frame whose z axis is ``axis`` (both [n, 3]) to the sky frame."""
+    z = axis / axis.norm(dim=1, keepdim=True)
+    ref = torch.zeros_like(z)
+    ref[:, 0] = 1.0
+    alt = torch.zeros_like(z)
+    alt[:, 1] = 1.0
+    use_alt = (z[:, 0].abs() > 0.9)[:, None]
+    ref = torch.where(use_alt, alt, ref)
+    x = torch.linalg.cross(ref, z)
+    x = x / x.norm(dim=1, keepdim=True)
+    y = torch.linalg.cross(z, x)
+    return v[:, :1] * x + v[:, 1:2] * y + v[:, 2:3] * z
+
+
+def satellite_pointing(cfg: SatelliteConfig, device="cpu", det_range: Optional[tuple] = None):
+    """Pixel (int32) and angle (float32) of a precessing spin scan with a continuously rotating
+    half-wave plate: the anti-sun axis turns once over the run, the spin axis precesses about it
+    at spin_axis_deg, the boresight spins at boresight_deg about the spin axis.  Detector j sits
+    on a small focal-plane grid (offsets up to det_offset_deg) at angle (j mod 4) * 45 deg."""
+    d0, d1 = det_range if det_range is not None else (0, cfg.n_det)
+    dev = torch.device(device)
+    n = cfg.n_samp
+    t = torch.arange(n, dtype=torch.float64, device=dev) / cfg.fs
+    two_pi = 2.0 * math.pi
+    T = n / cfg.fs
+    lon = two_pi * t / T
+    sun = torch.stack([torch.cos(lon), torch.sin(lon), torch.zeros_like(lon)], dim=1)
+    a = math.radians(cfg.spin_axis_deg)
+    wp = two_pi * t / cfg.prec_period_s
+    spin_local = torch.stack([math.sin(a) * torch.cos(wp), math.sin(a) * torch.sin(wp),
+                              torch.full_like(wp, math.cos(a))], dim=1)
+    spin = _rot_to(sun, spin_local)
+    bang = math.radians(cfg.boresight_deg)
+    ws = two_pi * t / cfg.spin_period_s
+    b_local = torch.stack([math.sin(bang) * torch.cos(ws), math.sin(bang) * torch.sin(ws),
+                           torch.full_like(ws, math.cos(bang))], dim=1)
+    bore = _rot_to(spin, b_local)
+    # scan direction (boresight velocity) gives the focal-plane orientation
+    v_local = torch.stack([-torch.sin(ws), torch.cos(ws), torch.zeros_like(ws)], dim=1)
+    vel = _rot_to(spin, v_local)
+    vel = vel - (vel * bore).sum(1, keepdim=True) * bore
+    vel = vel / vel.norm(dim=1, keepdim=True)
+    crs = torch.linalg.cross(bore, vel)
+    g = int(math.ceil(math.sqrt(max(cfg.n_det, 1))))
+    pix_out, psi_out = [], []
+    for det in range(d0, d1):
+        ox = ((det % g) / max(g - 1, 1) - 0.5) * 2 * math.radians(cfg.det_offset_deg)
+        oy = ((det // g) / max(g - 1, 1) - 0.5) * 2 * math.radians(cfg.det_offset_deg)
+        p = bore + ox * vel + oy * crs
+        p = p / p.norm(dim=1, keepdim=True)
+        z = p[:, 2].clamp(-1.0, 1.0)
+        phi = torch.remainder(torch.atan2(p[:, 1], p[:, 0]), two_pi)
+        ring = torch.clamp(torch.floor((z + 1.0) * 0.5 * cfg.n_rings), 0, cfg.n_rings - 1).long()
+        col = torch.clamp(torch.floor(phi / two_pi * cfg.n_phi), 0, cfg.n_phi - 1).long()
+        pix = (ring * cfg.n_phi + col).to(torch.int32)
+        # polarisation angle: detector angle + orientation of the scan w.r.t. the meridian + HWP
+        east = torch.stack([-torch.sin(phi), torch.cos(phi), torch.zeros_like(phi)], dim=1)
+        north = torch.linalg.cross(p, east)
+        orient = torch.atan2((vel * east).sum(1), (vel * north).sum(1))
+        ang = (det % 4) * (math.pi / 4.0) + orient + cfg.hwp_factor * (two_pi * cfg.hwp_hz * t)
+        psi = torch.remainder(ang, two_pi).to(torch.float32)
+        psi = torch.where(psi >= two_pi, torch.zeros_like(psi), psi)
+        pix_out.append(pix)
+        psi_out.append(psi)
+    return torch.cat(pix_out), torch.cat(psi_out)
+
+
+def make_satellite_problem(cfg: SatelliteConfig, device="cpu", det_range: Optional[tuple] = None,
+                           with_noise: bool = True) -> "Problem":
+    """Satellite-like problem: pointing, bands (shared shape, per-detector scale), sky and data."""
+    d0, d1 = det_range if det_range is not None else (0, cfg.n_det)
+    dev = torch.device(device)
+    n_det = d1 - d0
+    pix = torch.empty(n_det * cfg.n_samp, dtype=torch.int32, device=dev)
+    psi = torch.empty(n_det * cfg.n_samp, dtype=torch.float32, device=dev)
+    for j in range(d0, d1):   # one detector at a time keeps the float64 temporaries small
+        pj, sj = satellite_pointing(cfg, device=dev, det_range=(j, j + 1))
+        pix[(j - d0) * cfg.n_samp:(j - d0 + 1) * cfg.n_samp] = pj
+        psi[(j - d0) * cfg.n_samp:(j - d0 + 1) * cfg.n_samp] = sj
+    gs = torch.Generator(device="cpu").manual_seed(seed_for(cfg.config_id, 2))
+    sig_all = cfg.sigma_lo + (cfg.sigma_hi - cfg.sigma_lo) * torch.rand(
+        cfg.n_det, generator=gs, dtype=torch.float64)
+    sig = sig_all[d0:d1]
+    shape, info = inverse_noise_band(cfg.n_samp, cfg.lam, cfg.fs, 1.0, cfg.f_knee, cfg.alpha)
+    band = torch.stack([shape / (sig[j] ** 2) for j in range(n_det)])
+    m = sky(cfg.n_pix, cfg.sigma_I, cfg.sigma_QU, seed_for(cfg.config_id, 1), device=dev)
+    dd = torch.zeros(pix.numel(), dtype=torch.float64, device=dev)
+    gn = torch.Generator(device=dev).manual_seed(seed_for(cfg.config_id, 100) + 7919 * d0)
+    for j in range(n_det):
+        lo, hi = j * cfg.n_samp, (j + 1) * cfg.n_samp
+        pl = pix[lo:hi].long()
+        two = 2.0 * psi[lo:hi].to(torch.float64)
+        dd[lo:hi] = m[pl, 0] + torch.cos(two) * m[pl, 1] + torch.sin(two) * m[pl, 2]
+        if with_noise:
+            dd[lo:hi] += noise_block(cfg.n_samp, cfg.fs, float(sig[j]), cfg.f_knee, cfg.alpha, gn, dev)
+    block_len = torch.full((n_det,), cfg.n_samp, dtype=torch.int64)
+    return Problem(n_det=n_det, n_int=1, block_len=block_len, n_pix=cfg.n_pix, pix=pix, psi=psi,
+                   lam=cfg.lam, band=band, d=dd, m_sky=m, tol=cfg.tol, band_info=info, sigmas=sig)
+
+
 # --------------------------------------------------------------------------------------------
 # sky, noise, weights
 # --------------------------------------------------------------------------------------------
