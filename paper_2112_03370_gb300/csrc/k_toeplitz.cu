@@ -220,6 +220,100 @@ __device__ __forceinline__ void scatter_quads(const TileArgs& a, int rhs, const 
   }
 }
 
+
+// ---- strided pair access (one CTA per tile, FP32) -------------------------------------------
+// Lane l of a warp handles complex value n0 + l (samples in0 + 2n, + 1), so one warp-wide load
+// instruction covers 64 consecutive samples: the pointing loads are fully coalesced and the map
+// gathers of a scan that moves a few pixels per sample fall on a few cache lines.  A thread keeps
+// NB complex values (2 NB map loads) in flight.
+
+// pixel ids and angles of the pair (g, g + 1), masked to [lo, hi)
+template <typename T>
+__device__ __forceinline__ void pair_meta(const TileArgs& a, int64_t g, int64_t lo, int64_t hi, bool need_w,
+                                          int32_t (&p)[2], WRaw<T> (&w)[2]) {
+  if (g >= lo && g + 2 <= hi) {
+    const int2 v = __ldg(reinterpret_cast<const int2*>(a.lpix + g));
+    p[0] = v.x; p[1] = v.y;
+    if (need_w) {
+      if constexpr (std::is_same<T, float>::value) {
+        const float2 f = __ldg(reinterpret_cast<const float2*>(a.psi + g));
+        w[0].v = f.x; w[1].v = f.y;
+      } else {
+        w[0].v = __ldg(a.w64 + g); w[1].v = __ldg(a.w64 + g + 1);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+      const bool in = (g + e >= lo) && (g + e < hi);
+      p[e] = in ? __ldg(a.lpix + g + e) : -1;
+      if (need_w && in) load_w<T>(a, g + e, w[e]);
+    }
+  }
+}
+
+template <typename T, int MODE, int NB>
+__device__ __forceinline__ void gather_pairs(const TileArgs& a, int rhs, const TileDesc& td,
+                                             const int64_t (&g)[NB], T (&v)[NB][2]) {
+  int32_t p[NB][2];
+  WRaw<T> w[NB][2];
+#pragma unroll
+  for (int u = 0; u < NB; u++) pair_meta<T>(a, g[u], td.blk_lo, td.blk_hi, MODE == MODE_APPLY, p[u], w[u]);
+  if constexpr (MODE == MODE_RHS) {
+#pragma unroll
+    for (int u = 0; u < NB; u++)
+#pragma unroll
+      for (int e = 0; e < 2; e++) {
+        T d = T(0);
+        if (p[u][e] >= 0) {
+          const int64_t gg = rhs * a.x_stride + g[u] + e;
+          d = a.x_is_fp32 ? (T)__ldg(reinterpret_cast<const float*>(a.x) + gg)
+                          : (T)__ldg(reinterpret_cast<const double*>(a.x) + gg);
+        }
+        v[u][e] = d;
+      }
+  } else {
+    T I[NB][2], Q[NB][2], U[NB][2];
+#pragma unroll
+    for (int u = 0; u < NB; u++)
+#pragma unroll
+      for (int e = 0; e < 2; e++) {
+        I[u][e] = Q[u][e] = U[u][e] = T(0);
+        if (p[u][e] >= 0) Map4<T>::load(a.x, rhs * a.x_stride, p[u][e], I[u][e], Q[u][e], U[u][e]);
+      }
+#pragma unroll
+    for (int u = 0; u < NB; u++)
+#pragma unroll
+      for (int e = 0; e < 2; e++) {
+        T c = T(0), s = T(0);
+        if (p[u][e] >= 0) weights_of<T>(w[u][e], c, s);
+        v[u][e] = (p[u][e] >= 0) ? I[u][e] + c * Q[u][e] + s * U[u][e] : T(0);
+      }
+  }
+}
+
+template <typename T, int MODE, int NB>
+__device__ __forceinline__ void scatter_pairs(const TileArgs& a, int rhs, const TileDesc& td,
+                                              const int64_t (&g)[NB], const T (&y)[NB][2]) {
+  int32_t p[NB][2];
+  WRaw<T> w[NB][2];
+#pragma unroll
+  for (int u = 0; u < NB; u++) pair_meta<T>(a, g[u], td.out_lo, td.out_hi, true, p[u], w[u]);
+#pragma unroll
+  for (int u = 0; u < NB; u++) {
+    T c0 = T(0), s0 = T(0), c1 = T(0), s1 = T(0);
+    if (p[u][0] >= 0) weights_of<T>(w[u][0], c0, s0);
+    if (p[u][1] >= 0) weights_of<T>(w[u][1], c1, s1);
+    const T y0 = y[u][0], y1 = y[u][1];
+    if (p[u][0] >= 0 && p[u][0] == p[u][1]) {
+      Map4<T>::add(a.y, rhs * a.y_stride, p[u][0], y0 + y1, c0 * y0 + c1 * y1, s0 * y0 + s1 * y1);
+    } else {
+      if (p[u][0] >= 0) Map4<T>::add(a.y, rhs * a.y_stride, p[u][0], y0, c0 * y0, s0 * y0);
+      if (p[u][1] >= 0) Map4<T>::add(a.y, rhs * a.y_stride, p[u][1], y1, c1 * y1, s1 * y1);
+    }
+  }
+}
+
 }  // namespace
 
 // One overlap-save tile (CL = 1) or half a tile (CL = 2) per CTA.
@@ -273,22 +367,21 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
           sm[smem_pad(n)] = C{halo[2 * n], halo[2 * n + 1]};
         q_first = halo_q;
       }
-      for (int q0 = q_first + threadIdx.x; q0 < HALF_Q; q0 += NQ * kTileThreads) {
-        int64_t g[NQ];
-        T v[NQ][4];
+      constexpr int NB = 8;
+      const int n_first = 2 * q_first;
+      for (int n0 = n_first + threadIdx.x; n0 < MS; n0 += NB * kTileThreads) {
+        int64_t g[NB];
+        T v[NB][2];
 #pragma unroll
-        for (int u = 0; u < NQ; u++) {
-          const int q = q0 + u * kTileThreads;
-          g[u] = (q < HALF_Q) ? td.in0 + 4 * (int64_t)q : td.blk_hi;   // past the end: zeros
+        for (int u = 0; u < NB; u++) {
+          const int n = n0 + u * kTileThreads;
+          g[u] = (n < MS) ? td.in0 + 2 * (int64_t)n : td.blk_hi;   // past the end: zeros
         }
-        gather_quads<T, MODE, NQ>(a, rhs, td, g, v);
+        gather_pairs<T, MODE, NB>(a, rhs, td, g, v);
 #pragma unroll
-        for (int u = 0; u < NQ; u++) {
-          const int q = q0 + u * kTileThreads;
-          if (q < HALF_Q) {
-            sm[smem_pad(2 * q)] = C{v[u][0], v[u][1]};
-            sm[smem_pad(2 * q + 1)] = C{v[u][2], v[u][3]};
-          }
+        for (int u = 0; u < NB; u++) {
+          const int n = n0 + u * kTileThreads;
+          if (n < MS) sm[smem_pad(n)] = C{v[u][0], v[u][1]};
         }
       }
       __syncthreads();
@@ -366,7 +459,28 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
       cl.sync();
       other = cl.map_shared_rank(sm, rank ^ 1);
     }
-    {
+    if constexpr (CL == 1) {
+      constexpr int NB = 8;
+      const int n_lo = r_lo >> 1, n_hi = (r_hi + 1) >> 1;
+      for (int n0 = n_lo + threadIdx.x; n0 < n_hi; n0 += NB * kTileThreads) {
+        int64_t g[NB];
+        T y[NB][2];
+#pragma unroll
+        for (int u = 0; u < NB; u++) {
+          const int n = n0 + u * kTileThreads;
+          if (n < n_hi) {
+            const C z = sm[smem_pad(n)];
+            g[u] = td.in0 + 2 * (int64_t)n;
+            y[u][0] = z.x;
+            y[u][1] = z.y;
+          } else {
+            g[u] = td.out_hi;                          // outside the output range
+            y[u][0] = y[u][1] = T(0);
+          }
+        }
+        scatter_pairs<T, MODE, NB>(a, rhs, td, g, y);
+      }
+    } else {
       const int q_lo = max(r_lo >> 2, rank * HALF_Q);
       const int q_hi = min((r_hi + 3) >> 2, (rank + 1) * HALF_Q);
       for (int q0 = q_lo + threadIdx.x; q0 < q_hi; q0 += NQ * kTileThreads) {
@@ -381,10 +495,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
             for (int h = 0; h < 2; h++) {
               const int n = 2 * q + h - rank * MS;      // local complex index
               C z = sm[smem_pad(n)];
-              if constexpr (CL == 2) {
-                const C o = other[smem_pad(n)];
-                z = (rank == 0) ? c_add(z, o) : c_sub(o, z);
-              }
+              const C o = other[smem_pad(n)];
+              z = (rank == 0) ? c_add(z, o) : c_sub(o, z);
               y[u][2 * h] = z.x;
               y[u][2 * h + 1] = z.y;
             }
