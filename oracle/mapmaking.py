@@ -525,7 +525,45 @@ def precond_2lvl(plan: OraclePlan, tl: TwoLevel, r) -> np.ndarray:
     return (t1 - t2 + tl.Z @ y).reshape(-1, 3)
 
 
-__all__ += ["precond_2lvl", "BlockCGResult"]
+__all__ += ["precond_2lvl", "BlockCGResult", "apply_A_at_pixels"]
+
+
+def apply_A_at_pixels(pix, psi, block_off, band, keep, x_glob, pixels, sample_idx=None):
+    """(A x)_p for a few global pixels p, one by one, for problems too large for `apply_A`.
+
+    Definitions of Sect. 3.2 evaluated at the samples t that hit p (mask G from `keep`):
+    y_t = sum_{|k| <= lambda, t+k in block(t)} c_|k| (P~ x)_{t+k}  (Eq. MADCAP), then
+    (A x)_p = sum_t w_t y_t.  x_glob is indexed by global pixel ([n_pix, 3]); samples of pixels
+    with keep = False, and gaps, are masked on both sides.  `sample_idx[i]` (optional) lists the
+    samples of pixels[i].  Returns values [len(pixels), 3] and, per pixel, the sum of the absolute
+    values of the terms (the scale against which rounding errors are judged).
+    """
+    pix = np.asarray(pix)
+    block_off = np.asarray(block_off, dtype=np.int64)
+    band = np.asarray(band, dtype=np.float64)
+    lam = band.shape[1] - 1
+    out = np.zeros((len(pixels), 3))
+    scale = np.zeros(len(pixels))
+    kk = np.arange(-lam, lam + 1)
+    for i, p in enumerate(pixels):
+        S = np.nonzero(pix == p)[0] if sample_idx is None else np.asarray(sample_idx[i])
+        b = np.searchsorted(block_off, S, side="right") - 1
+        lo, hi = block_off[b], block_off[b + 1]
+        W = S[:, None] + kk[None, :]                       # band windows
+        inb = (W >= lo[:, None]) & (W < hi[:, None])
+        Wc = np.clip(W, 0, pix.size - 1)
+        pw = pix[Wc]
+        ok = inb & (pw >= 0)
+        ok &= np.where(pw >= 0, keep[np.clip(pw, 0, None)], False)
+        wgt = pointing_weights(np.asarray(psi)[Wc.ravel()]).reshape(W.shape + (3,))
+        xm = x_glob[np.clip(pw, 0, None)]
+        t = np.where(ok, (wgt * xm).sum(axis=2), 0.0)      # (P~ x) on the windows
+        c = band[b][:, np.abs(kk)]                         # c_|k| of each sample's block
+        y = (c * t).sum(axis=1)
+        wt = pointing_weights(np.asarray(psi)[S])
+        out[i] = (wt * y[:, None]).sum(axis=0)
+        scale[i] = (np.abs(c * t).sum(axis=1)[:, None] * np.abs(wt)).sum()
+    return out, scale
 
 
 def cpu_threads() -> int:

@@ -1079,7 +1079,8 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
   DeviceGuard g(P->device);
   const auto t0 = std::chrono::steady_clock::now();
   const bool fp32 = opts->precision == MM_FP32 && P->algo != MM_TPLZ_DIRECT;
-  const int chunk = opts->check_every > 0 ? opts->check_every : 8;
+  // profiling launches one iteration per host check, so no halted launch is timed or counted
+  const int chunk = opts->profile ? 1 : (opts->check_every > 0 ? opts->check_every : 8);
   const int rel_every = opts->reliable_every > 0 ? opts->reliable_every : 50;
   cudaStream_t us = as_stream(stream);
   cudaStream_t s = P->stream;

@@ -292,3 +292,14 @@ def test_two_level_never_more_iterations_than_bd():
     two = O.pcg(pl, b, tol=1e-8, precond=lambda r: O.precond_2lvl(pl, tl, r))
     assert two.converged and two.iters <= bd.iters
     assert np.linalg.norm(two.x - bd.x) <= 1e-5 * np.linalg.norm(bd.x)
+
+
+def test_apply_A_at_pixels_equals_apply_A():
+    pb = tiny_problem(seed=17, lam=25)
+    pl = plan_of(pb)
+    rng = np.random.default_rng(8)
+    xg = rng.standard_normal((pb["n_pix"], 3))
+    full = O.apply_A(pl, xg[pl.obs_to_global])
+    pixels = pl.obs_to_global[[0, 3, 7]]
+    vals, scale = O.apply_A_at_pixels(pb["pix"], pb["psi"], pl.offsets, pb["band"], pl.keep, xg, pixels)
+    np.testing.assert_allclose(vals, full[[0, 3, 7]], rtol=1e-12, atol=1e-12 * scale.max())
