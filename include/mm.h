@@ -136,6 +136,7 @@ typedef struct {
   int32_t n_apply64;     /* FP64 A-application launches */
   int64_t n_kernels;     /* kernels launched by the solve (its own, all columns) */
   double t_queue_ms;     /* server: time from mm_submit to admission (t_ms then runs to completion) */
+  double t_unpoint32_ms; /* profile = 1: part of t_apply32_ms spent in the separate t = P x kernel */
 } mm_solve_info;
 
 /* Build a plan: validate, copy inputs, compact observed pixels, build and invert the 3x3 BD

@@ -255,6 +255,17 @@ __device__ __forceinline__ void pair_meta(const TileArgs& a, int64_t g, int64_t 
 template <typename T, int MODE, int NB>
 __device__ __forceinline__ void gather_pairs(const TileArgs& a, int rhs, const TileDesc& td,
                                              const int64_t (&g)[NB], T (&v)[NB][2]) {
+  if constexpr (MODE == MODE_APPLY_T) {   // coalesced read of t = P x, zero outside the block
+    const float* t = reinterpret_cast<const float*>(a.x) + rhs * a.x_stride;
+#pragma unroll
+    for (int u = 0; u < NB; u++)
+#pragma unroll
+      for (int e = 0; e < 2; e++) {
+        const int64_t gg = g[u] + e;
+        v[u][e] = (gg >= td.blk_lo && gg < td.blk_hi) ? (T)__ldg(t + gg) : T(0);
+      }
+    return;
+  }
   int32_t p[NB][2];
   WRaw<T> w[NB][2];
 #pragma unroll
@@ -423,21 +434,63 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
     FFT::forward(sm, tw);
 
     // ---- pair update with the band's precomputed (a_k, b_k) in storage order ----
-    for (int j = threadIdx.x; j < MS; j += kTileThreads) {
-      const int k = FFT::freq_of(j);
-      const int kp = (CL == 2 && rank == 1) ? (MS - 1 - k) : ((MS - k) & (MS - 1));
-      const int jp = FFT::storage_of(kp);
-      if (j > jp) continue;
-      const C ab = __ldg(tab + j);
-      const C z = sm[smem_pad(j)];
-      if (j == jp) {
-        sm[smem_pad(j)] = C{sc * (ab.x * z.x + ab.y * z.y), sc * (ab.x * z.y + ab.y * z.x)};
-      } else {
-        const C abp = __ldg(tab + jp);
-        const C zp = sm[smem_pad(jp)];
-        // a Z + i b conj(Zp) = (a x + b yp, a y + b xp)
-        sm[smem_pad(j)] = C{sc * (ab.x * z.x + ab.y * zp.y), sc * (ab.x * z.y + ab.y * zp.x)};
-        sm[smem_pad(jp)] = C{sc * (abp.x * zp.x + abp.y * z.y), sc * (abp.x * zp.y + abp.y * z.x)};
+    // Frequencies k and M - k pair up.  In the digit-reversed storage order the lowest frequency
+    // digit d (base 16) is the top digit of the position, and the partner of a position with top
+    // digit d in 1..15 has top digit 16 - d and the remaining digits complemented: so positions
+    // with d in 1..7 pair upwards, d = 8 pairs within its own half, and only the d = 0 block
+    // (k a multiple of 16) needs the general rule.  On the odd-frequency CTA of a cluster the
+    // partner of position j is MS - 1 - j.  Work item u enumerates each pair once.
+    {
+      constexpr int D = MS / 16;
+      const int n_items = (CL == 2 && rank == 1) ? MS / 2 : (7 * D + D / 2 + D);
+      constexpr int PB = (MODE == MODE_APPLY && sizeof(T) == 4) ? 1 : 4;
+      for (int u0 = threadIdx.x; u0 < n_items; u0 += PB * kTileThreads) {
+        int jj[PB], jp[PB];
+        bool act[PB];
+        C ab[PB], abp[PB], z[PB], zp[PB];
+#pragma unroll
+        for (int b = 0; b < PB; b++) {
+          const int u = u0 + b * kTileThreads;
+          int j = 0, p = 0;
+          bool ok = u < n_items;
+          if (CL == 2 && rank == 1) {
+            j = u;
+            p = MS - 1 - u;
+          } else if (u < 7 * D) {
+            j = D + u;
+            p = (16 - (j / D)) * D + (D - 1 - (j % D));
+          } else if (u < 7 * D + D / 2) {
+            j = 8 * D + (u - 7 * D);
+            p = 8 * D + (D - 1 - (j % D));
+          } else {
+            j = u - (7 * D + D / 2);
+            p = FFT::storage_of((MS - FFT::freq_of(j)) & (MS - 1));
+            ok = ok && (j <= p);
+          }
+          jj[b] = j;
+          jp[b] = p;
+          act[b] = ok;
+          if (ok) {
+            ab[b] = __ldg(tab + j);
+            abp[b] = __ldg(tab + p);
+            z[b] = sm[smem_pad(j)];
+            zp[b] = sm[smem_pad(p)];
+          }
+        }
+#pragma unroll
+        for (int b = 0; b < PB; b++) {
+          if (!act[b]) continue;
+          if (jj[b] == jp[b]) {
+            sm[smem_pad(jj[b])] = C{sc * (ab[b].x * z[b].x + ab[b].y * z[b].y),
+                                    sc * (ab[b].x * z[b].y + ab[b].y * z[b].x)};
+          } else {
+            // a Z + i b conj(Zp) = (a x + b yp, a y + b xp)
+            sm[smem_pad(jj[b])] = C{sc * (ab[b].x * z[b].x + ab[b].y * zp[b].y),
+                                    sc * (ab[b].x * z[b].y + ab[b].y * zp[b].x)};
+            sm[smem_pad(jp[b])] = C{sc * (abp[b].x * zp[b].x + abp[b].y * z[b].y),
+                                    sc * (abp[b].x * zp[b].y + abp[b].y * z[b].x)};
+          }
+        }
       }
     }
     __syncthreads();
@@ -529,6 +582,7 @@ int tile_kernels_init() {
   MM_SET((k_tile<float, 1, MODE_APPLY>), kSmemMax);
   MM_SET((k_tile<float, 1, MODE_RHS>), kSmemMax);
   MM_SET((k_tile<float, 1, MODE_APPLY, true>), kSmemMax);
+  MM_SET((k_tile<float, 1, MODE_APPLY_T>), kSmemMax);
   MM_SET((k_tile<double, 2, MODE_APPLY>), kSmemBytes64);
   MM_SET((k_tile<double, 2, MODE_RHS>), kSmemBytes64);
   MM_SET((k_tile<double, 2, MODE_NINV>), kSmemBytes64);
@@ -571,8 +625,56 @@ cudaError_t launch_tiles_fp32(int mode, const TileArgs& a, int halo_samples, cud
   const size_t smem = kSmemBytes32 + (size_t)halo_samples * sizeof(float);
   if (smem > kSmemMax) return cudaErrorInvalidValue;
   if (mode == MODE_APPLY) return launch_tiles<float, 1, MODE_APPLY>(a, smem, s);
+  if (mode == MODE_APPLY_T) return launch_tiles<float, 1, MODE_APPLY_T>(a, smem, s);
   if (mode == MODE_RHS) return launch_tiles<float, 1, MODE_RHS>(a, smem, s);
   return cudaErrorInvalidValue;
+}
+
+// t = P x over all samples at full occupancy: lane = sample, so pointing loads coalesce and the map
+// gathers of a scan stay on a few cache lines per warp; the random loads of many warps overlap.
+__global__ void __launch_bounds__(256) k_unpoint32(const int32_t* __restrict__ lpix,
+                                                   const float* __restrict__ psi, int64_t N,
+                                                   const float4* __restrict__ x4, int64_t x_stride4,
+                                                   const int32_t* __restrict__ done, int done_stride,
+                                                   float* __restrict__ t) {
+  const int rhs = blockIdx.y;
+  if (done != nullptr && done[(int64_t)rhs * done_stride] != 0) return;
+  const float4* x = x4 + rhs * x_stride4;
+  float* tr = t + rhs * N;
+  constexpr int U = 4;
+  for (int64_t i0 = (int64_t)blockIdx.x * 256 * U + threadIdx.x; i0 < N; i0 += (int64_t)gridDim.x * 256 * U) {
+    int32_t p[U];
+    float a[U];
+    float4 m[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int64_t i = i0 + u * 256;
+      p[u] = (i < N) ? __ldg(lpix + i) : -1;
+      a[u] = (i < N) ? __ldg(psi + i) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) m[u] = (p[u] >= 0) ? __ldg(x + p[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int64_t i = i0 + u * 256;
+      if (i < N) {
+        float s, c;
+        sincosf(2.f * a[u], &s, &c);
+        tr[i] = (p[u] >= 0) ? m[u].x + c * m[u].y + s * m[u].z : 0.f;
+      }
+    }
+  }
+}
+
+cudaError_t launch_unpoint32(const int32_t* lpix, const float* psi, int64_t N, const float* x4,
+                             int64_t x_stride, int nrhs, const int32_t* done, int done_stride, float* t,
+                             cudaStream_t s) {
+  if (N == 0 || nrhs <= 0) return cudaSuccess;
+  int64_t g = (N + 1023) / 1024;
+  if (g > 152 * 16) g = 152 * 16;
+  k_unpoint32<<<dim3((unsigned)g, nrhs), 256, 0, s>>>(lpix, psi, N, reinterpret_cast<const float4*>(x4),
+                                                     x_stride / 4, done, done_stride, t);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_tiles_fp32_multi(const TileArgs& a, int halo_samples, cudaStream_t s) {

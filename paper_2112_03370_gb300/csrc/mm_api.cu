@@ -133,7 +133,7 @@ void free_plan(Plan* P) {
   dfree(P->lpix); dfree(P->psi); dfree(P->w64); dfree(P->obs_to_global); dfree(P->minv);
   dfree(P->band); dfree(P->block_off_dev); dfree(P->c0_blk); dfree(P->tab32); dfree(P->tab64);
   dfree(P->tw32); dfree(P->tw64); dfree(P->tiles); dfree(P->segs); dfree(P->map32_in); dfree(P->map32_out);
-  dfree(P->map64_in); dfree(P->map64_out); dfree(P->td_a); dfree(P->td_b);
+  dfree(P->map64_in); dfree(P->map64_out); dfree(P->td_a); dfree(P->td_b); dfree(P->t32);
   free_cg(reinterpret_cast<CgState*>(P->cg));
   free_blk(reinterpret_cast<BlkState*>(P->blk));
   free_defl(reinterpret_cast<DeflState*>(P->defl));
@@ -275,6 +275,9 @@ int validate_desc(const mm_problem_desc* d) {
   } while (0)
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// largest un-pointed FP32 buffer the split A-application may allocate (nrhs * N * 4 bytes)
+constexpr size_t kSplitTBytes = (size_t)24 << 30;
 
 // Plan-time scratch: freed when the plan build returns, on every path.
 struct Scratch {
@@ -508,20 +511,44 @@ int apply64_internal(Plan* P, const double* x4, double* y4, int nrhs, cudaStream
   return MM_OK;
 }
 
+// plan-owned un-pointed buffer of the split FP32 A-application (allocated outside graph capture)
+int ensure_t32(Plan* P, int nrhs) {
+  const size_t t_elems = (size_t)nrhs * (size_t)P->N;
+  if (t_elems * sizeof(float) > kSplitTBytes || P->t32_cap >= t_elems) return MM_OK;
+  dfree(P->t32);
+  P->t32_cap = 0;
+  MM_TRY(dalloc(P, &P->t32, t_elems));
+  P->t32_cap = t_elems;
+  return MM_OK;
+}
+
 // y32 (accumulated, pre-zeroed) += A x32 in FP32, [nrhs][n_obs][4] float
 int apply32_internal(Plan* P, const float* x32, float* y32, int nrhs, cudaStream_t s,
-                     const int32_t* done = nullptr, int done_stride = 0) {
+                     const int32_t* done = nullptr, int done_stride = 0, cudaEvent_t mid = nullptr) {
   TileArgs a = base_args(P, true);
   a.tiles = P->segs;
   a.n_tiles = P->n_segs;
   a.nrhs = nrhs;
-  a.x = x32;
-  a.x_stride = P->n_obs * 4;
   a.y = y32;
   a.y_stride = P->n_obs * 4;
   a.done = done;
   a.done_stride = done_stride;
-  MM_CUDA(launch_tiles_fp32(MODE_APPLY, a, P->seg_halo, s));
+  // Un-point first at full occupancy (t = P x into a plan-owned FP32 buffer), then the tiles
+  // stream t instead of gathering the map themselves; fused gather when the buffer would be large.
+  const size_t t_elems = (size_t)nrhs * (size_t)P->N;
+  if (t_elems * sizeof(float) <= kSplitTBytes) {
+    MM_TRY(ensure_t32(P, nrhs));
+    MM_CUDA(launch_unpoint32(P->lpix, P->psi, P->N, x32, P->n_obs * 4, nrhs, done, done_stride, P->t32, s));
+    if (mid) MM_CUDA(cudaEventRecord(mid, s));
+    a.x = P->t32;
+    a.x_stride = P->N;
+    MM_CUDA(launch_tiles_fp32(MODE_APPLY_T, a, P->seg_halo, s));
+  } else {
+    if (mid) MM_CUDA(cudaEventRecord(mid, s));
+    a.x = x32;
+    a.x_stride = P->n_obs * 4;
+    MM_CUDA(launch_tiles_fp32(MODE_APPLY, a, P->seg_halo, s));
+  }
   return MM_OK;
 }
 
@@ -1088,6 +1115,7 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
   MM_TRY(ensure_cg(P, nrhs, fp32, &c));
   CgWork w = make_work(P, c, nrhs, fp32, opts->tol, opts->max_iter);
   if (P->algo == MM_TPLZ_DIRECT) MM_TRY(ensure_td(P));
+  if (fp32) MM_TRY(ensure_t32(P, nrhs));
   DeflWork dw{};
   const DeflWork* dwp = nullptr;
   if (opts->precond == MM_PREC_2LVL_POST) {
@@ -1133,15 +1161,16 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
   const bool profile = opts->profile != 0;
   int64_t n_kernels = 2;   // pack + init
   // profile mode: event pairs around every tile launch, summed at each host sync
-  struct EvPair { cudaEvent_t a, b; int is64; };
+  struct EvPair { cudaEvent_t a, b, m; int is64; };
   std::vector<EvPair> pool, pending;
-  double t32 = 0.0, t64 = 0.0;
+  double t32 = 0.0, t64 = 0.0, tup = 0.0;
   int n32 = 0, n64 = 0;
   auto take_pair = [&](int is64, EvPair* out) -> int {
     if (pool.empty()) {
       EvPair e{};
       MM_CUDA(cudaEventCreate(&e.a));
       MM_CUDA(cudaEventCreate(&e.b));
+      MM_CUDA(cudaEventCreate(&e.m));
       pool.push_back(e);
     }
     *out = pool.back();
@@ -1153,7 +1182,13 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
     for (EvPair& e : pending) {
       float ms = 0.f;
       MM_CUDA(cudaEventElapsedTime(&ms, e.a, e.b));
-      if (e.is64) { t64 += ms; n64++; } else { t32 += ms; n32++; }
+      if (e.is64) { t64 += ms; n64++; } else {
+        t32 += ms;
+        n32++;
+        float mu = 0.f;
+        MM_CUDA(cudaEventElapsedTime(&mu, e.a, e.m));
+        tup += mu;
+      }
       pool.push_back(e);
     }
     pending.clear();
@@ -1218,7 +1253,7 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
         MM_TRY(take_pair(fp32 ? 0 : 1, &e));
         MM_CUDA(cudaEventRecord(e.a, s));
         if (fp32) {
-          MM_TRY(apply32_internal(P, w.p32, w.q32, nrhs, s, halt, kScalStrideInts));
+          MM_TRY(apply32_internal(P, w.p32, w.q32, nrhs, s, halt, kScalStrideInts, e.m));
         } else {
           MM_TRY(apply64_internal(P, w.p, w.q, nrhs, s, halt, kScalStrideInts));
         }
@@ -1254,6 +1289,7 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
   for (EvPair& e : pool) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
+    cudaEventDestroy(e.m);
   }
   MM_CUDA(cudaEventRecord(ev, s));
   MM_CUDA(cudaStreamWaitEvent(us, ev, 0));
@@ -1272,6 +1308,7 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
     in.batch = 1;
     in.t_queue_ms = 0.0;
     in.t_apply32_ms = t32;
+    in.t_unpoint32_ms = tup;
     in.t_apply64_ms = t64;
     in.n_apply32 = n32;
     in.n_apply64 = n64;

@@ -53,7 +53,8 @@ struct ProbPtrs {
   const int32_t* done;
 };
 
-enum Mode { MODE_APPLY = 0, MODE_RHS = 1, MODE_NINV = 2 };
+// MODE_APPLY_T: FP32 A-application whose un-pointed input t = P x was written beforehand
+enum Mode { MODE_APPLY = 0, MODE_RHS = 1, MODE_NINV = 2, MODE_APPLY_T = 3 };
 
 // Arguments of the fused Toeplitz-tile kernels.
 struct TileArgs {
@@ -108,6 +109,8 @@ struct Plan {
   TileDesc* segs = nullptr;            // FP32 segments (several tiles per descriptor)
   int64_t n_segs = 0;
   std::vector<TileDesc> segs_host;     // host copy (multi-problem launches)
+  float* t32 = nullptr;                // [nrhs][N] un-pointed FP32 input of the tiles
+  size_t t32_cap = 0;
   int32_t seg_halo = 0;                // largest L - vstep over the segments (samples)
 
   // work buffers (grown on demand)
@@ -182,6 +185,10 @@ cudaError_t launch_twiddles(double2* tw64, float2* tw32, const double* costab, c
 cudaError_t launch_tiles_fp32(int mode, const TileArgs& a, int halo_samples, cudaStream_t s);
 // FP32 A-application over the tiles of several plans at once (a.probs set, nrhs = 1)
 cudaError_t launch_tiles_fp32_multi(const TileArgs& a, int halo_samples, cudaStream_t s);
+// t [nrhs][N] float32 = P x for every sample (0 at masked samples), x float4 maps [nrhs][n_obs]
+cudaError_t launch_unpoint32(const int32_t* lpix, const float* psi, int64_t N, const float* x4,
+                             int64_t x_stride, int nrhs, const int32_t* done, int done_stride, float* t,
+                             cudaStream_t s);
 cudaError_t launch_tiles_fp64(int mode, const TileArgs& a, cudaStream_t s);
 int tile_kernels_init();   // sets smem attributes once per process
 int fp32_max_halo_samples();   // largest halo the FP32 segment kernel can keep in shared memory

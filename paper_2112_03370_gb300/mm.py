@@ -53,7 +53,8 @@ class SolveInfo(ctypes.Structure):
                 ("n_true_res", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("t_apply32_ms", ctypes.c_double), ("t_apply64_ms", ctypes.c_double),
                 ("n_apply32", ctypes.c_int32), ("n_apply64", ctypes.c_int32),
-                ("n_kernels", ctypes.c_int64), ("t_queue_ms", ctypes.c_double)]
+                ("n_kernels", ctypes.c_int64), ("t_queue_ms", ctypes.c_double),
+                ("t_unpoint32_ms", ctypes.c_double)]
 
 
 class MMError(RuntimeError):
