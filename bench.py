@@ -7,8 +7,10 @@ per-detector sigma ~ U(0.8, 1.2)), banded inverse-noise weights with lambda = 81
 synthetic data generated on the device.
 
 One step = one whole pass of the hot path on resident inputs: the right-hand side
-b = P^T N^-1 d and a mixed-precision PCG solve to rel. residual 1e-6 (FP32 P, N^-1, P^T; FP64
-vectors, dot products, alpha/beta, 3x3 blocks and residual replacements).  The plan (pixel
+b = P^T N^-1 d and a mixed-precision PCG solve to rel. residual 1e-6 (FP32 P, N^-1, P^T in the
+iterations; FP64 vectors, dot products, alpha/beta and 3x3 blocks; the right-hand side and the
+residual replacements apply the operators in double-float arithmetic, pairs of FP32 numbers with
+a 48-bit significand, which runs on the FP32 pipes).  The plan (pixel
 compaction, block-Jacobi blocks, spectra) is built once before the timed region; the e2e number
 rebuilds it from pinned host buffers in every step.
 
@@ -247,7 +249,7 @@ def run_ours(a):
     band_d = prob.band.to(dev)
     t_plan = time.perf_counter()
     plan = mm.mm_plan(prob.n_det, prob.n_int, prob.block_len.tolist(), prob.n_pix, prob.pix,
-                      prob.psi, prob.lam, band_d, precision=mm.MM_FP32)
+                      prob.psi, prob.lam, band_d, precision=mm.MM_FP32_DF64)
     torch.cuda.synchronize()
     t_plan = time.perf_counter() - t_plan
     N = plan.n_samples
@@ -329,12 +331,14 @@ def run_ours(a):
 
     out = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": elapsed / a.steps * 1e3,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64",
            "data": "synthetic (seeded, generated on the device)",
            "config": {"workload": f"ground: {prob.n_det} det x {prob.n_int} int x {cfg.n_samp} "
                                   f"samples, {cfg.side}x{cfg.side} IQU patch, lambda {cfg.lam}",
                       "n_samples": N, "n_obs": plan.n_obs, "lambda": cfg.lam, "tol": cfg.tol,
-                      "step": "rhs + mixed-precision PCG solve (FP32 operators, FP64 CG)",
+                      "step": "rhs + mixed-precision PCG solve (FP32 operators in the iterations; FP64 CG "
+                              "vectors, dots and scalars; rhs and residual replacement with "
+                              "double-float operators)",
                       "parallelism": "replicas" if world > 1 else "single GPU",
                       "l2": "inputs larger than L2 (pointing 8 B/sample)"},
            "solves_per_s": a.steps * world / elapsed,
@@ -345,15 +349,15 @@ def run_ours(a):
            "status": [i.status for i in infos],
            "step_ms_p50": float(np.percentile(step_ms, 50)),
            "step_ms_p99": float(np.percentile(step_ms, 99)),
-           "fp64_apply_ms": (t64 / n64) if n64 else None,
+           "df64_apply_ms": (t64 / n64) if n64 else None,
            "plan_s": t_plan,
            "roofline": roof, "gpu_launches": int(launches), "clocks": clk}
 
-    # plain FP64 PCG on the same GPU: a few iterations for its iteration rate
+    # FP64-class PCG (double-float operators) on the same GPU: a few iterations for its rate
     if rank == 0:
         inf64 = mm.mm_pcg_solve(plan, b, x, tol=cfg.tol, max_iter=4, precision=mm.MM_FP64,
                                 profile=True, raise_on_error=False)[0]
-        out["fp64_pcg"] = {"iters": inf64.iters, "ms_per_iter": inf64.t_ms / max(inf64.iters, 1),
+        out["df64_pcg"] = {"iters": inf64.iters, "ms_per_iter": inf64.t_ms / max(inf64.iters, 1),
                            "apply_ms": inf64.t_apply64_ms / max(inf64.n_apply64, 1),
                            "samples_per_s_through_A": N / (inf64.t_apply64_ms /
                                                            max(inf64.n_apply64, 1) / 1e3)}
@@ -368,7 +372,7 @@ def run_ours(a):
 
         def e2e_step():
             p2 = mm.mm_plan(prob.n_det, prob.n_int, prob.block_len.tolist(), prob.n_pix, pix_h,
-                            psi_h, prob.lam, band_h, precision=mm.MM_FP32)
+                            psi_h, prob.lam, band_h, precision=mm.MM_FP32_DF64)
             d_dev = d_h.to(dev, non_blocking=True)
             b2 = torch.empty(p2.n_obs, 3, dtype=torch.float64, device=dev)
             x2 = torch.empty_like(b2)
@@ -422,7 +426,8 @@ def _timed(fn):
 
 def run_batched(a):
     """Ground geometry cut to 128 dets x 1 interval x 524,288 samples, nrhs noise realisations:
-    block CG (widths given) vs independent FP64 PCG (rate from two right-hand sides)."""
+    block CG (widths given) vs independent FP64-class (double-float) PCG and independent mixed
+    FP32 PCG (rates from two right-hand sides)."""
     import torch
     import synth
     import paper_2112_03370_gb300.mm as mm
@@ -430,7 +435,7 @@ def run_batched(a):
     cfg = synth.batched_config()
     prob = synth.make_ground_problem(cfg, device=dev, n_real=a.nrhs)
     plan = mm.mm_plan(prob.n_det, prob.n_int, prob.block_len.tolist(), prob.n_pix, prob.pix, prob.psi,
-                      prob.lam, prob.band.to(dev), precision=mm.MM_FP32)
+                      prob.lam, prob.band.to(dev), precision=mm.MM_FP32_DF64)
     N = plan.n_samples
     B = torch.empty(a.nrhs, plan.n_obs, 3, dtype=torch.float64, device=dev)
     mm.mm_rhs(plan, prob.d, B)
@@ -458,9 +463,10 @@ def run_batched(a):
                                f"{cfg.side}^2 IQU, lambda {cfg.lam}, {a.nrhs} realisations",
                    "n_samples": N, "n_obs": plan.n_obs, "tol": cfg.tol},
         "block_cg": res,
-        "fp64_pcg": {"solves_per_s": 2 / dt64, "iters": [i.iters for i in infos]},
+        "df64_pcg": {"solves_per_s": 2 / dt64, "iters": [i.iters for i in infos]},
         "fp32_pcg_independent": {"solves_per_s": 2 / dt32, "iters": [i.iters for i in infos32]},
-        "vs_fp64_pcg": best["solves_per_s"] / (2 / dt64)}), flush=True)
+        "vs_df64_pcg": best["solves_per_s"] / (2 / dt64),
+        "vs_fp32_pcg": best["solves_per_s"] / (2 / dt32)}), flush=True)
 
 
 def run_satellite(a):
@@ -472,7 +478,7 @@ def run_satellite(a):
     cfg = synth.satellite_config(n_det=a.dets if a.dets != 512 else 64)
     prob, tg = _timed(lambda: synth.make_satellite_problem(cfg, device=dev))
     plan = mm.mm_plan(prob.n_det, prob.n_int, prob.block_len.tolist(), prob.n_pix, prob.pix, prob.psi,
-                      prob.lam, prob.band.to(dev), precision=mm.MM_FP32)
+                      prob.lam, prob.band.to(dev), precision=mm.MM_FP32_DF64)
     N = plan.n_samples
     b = torch.empty(plan.n_obs, 3, dtype=torch.float64, device=dev)
     mm.mm_rhs(plan, prob.d, b)

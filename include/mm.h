@@ -50,8 +50,16 @@ typedef enum {
   MM_ECUDA = 8        /* a CUDA runtime call failed */
 } mm_status;
 
-/* Arithmetic of the bulk operators P, N^-1, P^T. */
-enum { MM_FP64 = 0, MM_FP32 = 1 };
+/* Arithmetic of the bulk operators P, N^-1, P^T (plan precision; a solve's opts->precision is
+ * MM_FP64 or MM_FP32 and selects between the plan's FP64-class and FP32 operators).
+ *   MM_FP64       FP64-class operators in IEEE FP64.
+ *   MM_FP32       FP32 operators for the CG iterations; FP64-class operators in IEEE FP64.
+ *   MM_DF64       FP64-class operators in double-float arithmetic: each value is a pair of FP32
+ *                 numbers (hi + lo, a 48-bit significand) and the FFT runs on the FP32 pipes.
+ *                 Normwise relative error of A x about 1e-14 instead of 1e-16.
+ *   MM_FP32_DF64  FP32 operators for the CG iterations; FP64-class operators (right-hand side,
+ *                 residual replacement, true residual) in double-float. */
+enum { MM_FP64 = 0, MM_FP32 = 1, MM_DF64 = 2, MM_FP32_DF64 = 3 };
 /* Algorithm of the block-Toeplitz product. */
 enum { MM_TPLZ_AUTO = 0, MM_TPLZ_FFT = 1, MM_TPLZ_DIRECT = 3 };
 /* Preconditioner: block-Jacobi, or the two-level a-posteriori A-DEF1 preconditioner built by
@@ -71,7 +79,8 @@ enum { MM_PREC_BD = 0, MM_PREC_2LVL_POST = 1 };
  *                  c_0 + 2 sum_k c_k cos(k w) must be positive (checked: MM_ENOTSPD).
  *   cond_max       pixels with fewer than 3 hits or cond_2 of their 3x3 block above cond_max are
  *                  excised together with their samples (Sect. 2.4); <= 0 selects 1e3.
- *   precision      MM_FP64 or MM_FP32: arithmetic of mm_apply_A.
+ *   precision      MM_FP64, MM_FP32, MM_DF64 or MM_FP32_DF64 (above): arithmetic of mm_apply_A
+ *                  (FP32 for MM_FP32 and MM_FP32_DF64) and of mm_rhs (the FP64-class operators).
  *   toeplitz_algo  MM_TPLZ_AUTO/MM_TPLZ_FFT (shared-memory overlap-save FFT) or MM_TPLZ_DIRECT
  *                  (band sum by the definition, O(lambda) per sample; for checks and tiny lambda).
  *   inputs_on_device  non-zero: pix, psi and band are device pointers; zero: host pointers.
@@ -237,8 +246,9 @@ int mm_deflation_apply(mm_plan_t plan, const double* r, double* z, int nrhs, voi
  * running ones stays within hbm_budget; an admitted request's plan (pointing, bands, spectra,
  * block-Jacobi blocks) and PCG state stay resident until it finishes.  Every step runs one PCG
  * iteration of every running request with a single Toeplitz-tile launch over all of their tiles
- * (FP32 operators; FP64 residual replacement per request as in mm_pcg_solve); requests join and
- * leave between steps.
+ * (FP32 operators; right-hand side and residual replacement per request with the double-float
+ * FP64-class operators, as in mm_pcg_solve on an MM_FP32_DF64 plan; the request's desc->precision
+ * is ignored); requests join and leave between steps.
  */
 /* Create a server (hbm_budget in bytes, 0 = 80% of the free device memory; max_slots >= 1). */
 int mm_server_create(size_t hbm_budget, int max_slots, mm_server_t* out);

@@ -146,11 +146,15 @@ struct TwiddleTab {
 };
 constexpr int twiddle_tab_entries(int m) { return 64 + m / 64; }
 
+// Read-only load of one complex value; other complex types specialise it.
+template <typename C>
+__device__ __forceinline__ C ldg_c(const C* p) { return __ldg(p); }
+
 // Fill the shared table from the global table tw[k] = W_M^k (called by all threads, then sync).
 template <typename C, int MFULL, int NT>
 __device__ __forceinline__ TwiddleTab<C> load_twiddle_tab(C* tab_sm, const C* __restrict__ tw) {
   for (int i = threadIdx.x; i < twiddle_tab_entries(MFULL); i += NT) {
-    tab_sm[i] = (i < 64) ? __ldg(tw + i) : __ldg(tw + 64 * (i - 64));
+    tab_sm[i] = (i < 64) ? ldg_c(tw + i) : ldg_c(tw + 64 * (i - 64));
   }
   return TwiddleTab<C>{tab_sm, tab_sm + 64};
 }

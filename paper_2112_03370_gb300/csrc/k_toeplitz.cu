@@ -27,6 +27,7 @@
 
 #include <type_traits>
 
+#include "df64.cuh"
 #include "fft_smem.cuh"
 #include "mm_internal.cuh"
 
@@ -65,6 +66,15 @@ template <> struct Map4<double> {
     atomicAdd(q + 2, c);
   }
 };
+template <> struct Map4<df> {
+  // df64 outputs accumulate into the FP64 map
+  static __device__ __forceinline__ void add(void* base, int64_t off, int32_t p, df a, df b, df c) {
+    double* q = reinterpret_cast<double*>(base) + off + 4 * (int64_t)p;
+    atomicAdd(q, df_to_double(a));
+    atomicAdd(q + 1, df_to_double(b));
+    atomicAdd(q + 2, df_to_double(c));
+  }
+};
 
 // ---- batched quad access --------------------------------------------------------------------
 // The gather and scatter walk "quads" of 4 consecutive samples starting at a multiple of 4
@@ -78,10 +88,12 @@ template <> struct Map4<double> {
 template <typename T> struct WRaw;
 template <> struct WRaw<float> { float v; };
 template <> struct WRaw<double> { double2 v; };
+template <> struct WRaw<df> { float4 v; };   // (cos hi, cos lo, sin hi, sin lo)
 
 template <typename T>
 __device__ __forceinline__ void load_w(const TileArgs& a, int64_t g, WRaw<T>& w) {
   if constexpr (std::is_same<T, float>::value) w.v = __ldg(a.psi + g);
+  else if constexpr (std::is_same<T, df>::value) w.v = __ldg(a.wdf + g);
   else w.v = __ldg(a.w64 + g);
 }
 template <typename T>
@@ -91,6 +103,9 @@ __device__ __forceinline__ void weights_of(const WRaw<T>& w, T& c, T& s) {
     // FP64 one, or the FP64 residual replacement of the mixed-precision solver stops converging
     // (a systematic weight error perturbs the smallest eigenvalues of A)
     sincosf(2.f * w.v, &s, &c);
+  } else if constexpr (std::is_same<T, df>::value) {
+    c = df_make(w.v.x, w.v.y);
+    s = df_make(w.v.z, w.v.w);
   } else {
     c = w.v.x;
     s = w.v.y;
@@ -110,7 +125,7 @@ __device__ __forceinline__ void quad_meta(const TileArgs& a, int64_t g, int64_t 
         w[0].v = f.x; w[1].v = f.y; w[2].v = f.z; w[3].v = f.w;
       } else {
 #pragma unroll
-        for (int e = 0; e < 4; e++) w[e].v = __ldg(a.w64 + g + e);
+        for (int e = 0; e < 4; e++) load_w<T>(a, g + e, w[e]);
       }
     }
   } else {
@@ -127,7 +142,33 @@ __device__ __forceinline__ void quad_meta(const TileArgs& a, int64_t g, int64_t 
 template <typename T, int MODE, int NQ>
 __device__ __forceinline__ void gather_quads(const TileArgs& a, int rhs, const TileDesc& td,
                                              const int64_t (&g)[NQ], T (&v)[NQ][4]) {
-  if constexpr (MODE == MODE_NINV) {
+  if constexpr (MODE == MODE_APPLY_T) {
+    // df64 tiles: un-pointed input t = P x (or the masked TOD) as (hi, lo) pairs
+    static_assert(std::is_same<T, df>::value, "2-CTA APPLY_T tiles are the df64 ones");
+    const float2* t = reinterpret_cast<const float2*>(a.x) + rhs * a.x_stride;
+#pragma unroll
+    for (int u = 0; u < NQ; u++) {
+      if (g[u] >= td.blk_lo && g[u] + 4 <= td.blk_hi) {
+        const float4 v01 = __ldg(reinterpret_cast<const float4*>(t + g[u]));
+        const float4 v23 = __ldg(reinterpret_cast<const float4*>(t + g[u] + 2));
+        v[u][0] = df_make(v01.x, v01.y);
+        v[u][1] = df_make(v01.z, v01.w);
+        v[u][2] = df_make(v23.x, v23.y);
+        v[u][3] = df_make(v23.z, v23.w);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+          const int64_t gg = g[u] + e;
+          if (gg >= td.blk_lo && gg < td.blk_hi) {
+            const float2 f = __ldg(t + gg);
+            v[u][e] = df_make(f.x, f.y);
+          } else {
+            v[u][e] = T(0);
+          }
+        }
+      }
+    }
+  } else if constexpr (MODE == MODE_NINV) {
     const double* t = reinterpret_cast<const double*>(a.x) + rhs * a.x_stride;
 #pragma unroll
     for (int u = 0; u < NQ; u++)
@@ -471,8 +512,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
           jp[b] = p;
           act[b] = ok;
           if (ok) {
-            ab[b] = __ldg(tab + j);
-            abp[b] = __ldg(tab + p);
+            ab[b] = ldg_c(tab + j);
+            abp[b] = ldg_c(tab + p);
             z[b] = sm[smem_pad(j)];
             zp[b] = sm[smem_pad(p)];
           }
@@ -586,6 +627,7 @@ int tile_kernels_init() {
   MM_SET((k_tile<double, 2, MODE_APPLY>), kSmemBytes64);
   MM_SET((k_tile<double, 2, MODE_RHS>), kSmemBytes64);
   MM_SET((k_tile<double, 2, MODE_NINV>), kSmemBytes64);
+  MM_SET((k_tile<df, 2, MODE_APPLY_T>), kSmemBytes64);
 #undef MM_SET
   if (e == cudaSuccess) {
     // 2-CTA clusters with 136 KB of dynamic shared memory each are a non-portable size only in
@@ -684,6 +726,13 @@ cudaError_t launch_tiles_fp32_multi(const TileArgs& a, int halo_samples, cudaStr
 }
 
 int fp32_max_halo_samples() { return (int)((kSmemMax - kSmemBytes32) / sizeof(float)); }
+
+// df64 tiles: input t (float2 hi/lo pairs [nrhs][x_stride], x_stride a multiple of 4), output
+// accumulated into the FP64 map y [nrhs][n_obs][4]
+cudaError_t launch_tiles_df(const TileArgs& a, cudaStream_t s) {
+  if (a.x_stride % 4 != 0) return cudaErrorInvalidValue;
+  return launch_tiles<df, 2, MODE_APPLY_T>(a, kSmemBytes64, s);
+}
 
 cudaError_t launch_tiles_fp64(int mode, const TileArgs& a, cudaStream_t s) {
   if (mode == MODE_APPLY) return launch_tiles<double, 2, MODE_APPLY>(a, kSmemBytes64, s);

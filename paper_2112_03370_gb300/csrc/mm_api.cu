@@ -134,6 +134,7 @@ void free_plan(Plan* P) {
   dfree(P->band); dfree(P->block_off_dev); dfree(P->c0_blk); dfree(P->tab32); dfree(P->tab64);
   dfree(P->tw32); dfree(P->tw64); dfree(P->tiles); dfree(P->segs); dfree(P->map32_in); dfree(P->map32_out);
   dfree(P->map64_in); dfree(P->map64_out); dfree(P->td_a); dfree(P->td_b); dfree(P->t32);
+  dfree(P->wdf); dfree(P->tabdf); dfree(P->twdf); dfree(P->tdf); dfree(P->mapdf);
   free_cg(reinterpret_cast<CgState*>(P->cg));
   free_blk(reinterpret_cast<BlkState*>(P->blk));
   free_defl(reinterpret_cast<DeflState*>(P->defl));
@@ -261,7 +262,9 @@ int validate_desc(const mm_problem_desc* d) {
     return fail(MM_EINVAL, "lambda must lie in [0, " + std::to_string(kMaxLambda) + "]");
   if (!d->pix || !d->psi || !d->band) return fail(MM_EINVAL, "pix, psi and band must be non-NULL");
   if (d->tile_steps < 0) return fail(MM_EINVAL, "tile_steps must be >= 0");
-  if (d->precision != MM_FP64 && d->precision != MM_FP32) return fail(MM_EINVAL, "bad precision");
+  if (d->precision != MM_FP64 && d->precision != MM_FP32 && d->precision != MM_DF64 &&
+      d->precision != MM_FP32_DF64)
+    return fail(MM_EINVAL, "bad precision");
   if (d->toeplitz_algo != MM_TPLZ_AUTO && d->toeplitz_algo != MM_TPLZ_FFT &&
       d->toeplitz_algo != MM_TPLZ_DIRECT)
     return fail(MM_EINVAL, "bad toeplitz_algo");
@@ -306,8 +309,10 @@ int build_plan(const mm_problem_desc* d, cudaStream_t us, Plan* P) {
   P->n_blocks = d->n_det * d->n_int;
   P->n_pix = d->n_pix;
   P->lambda = d->lambda;
-  P->precision = d->precision;
+  // P->precision: arithmetic of the CG-iteration operators; P->df64: FP64-class ones in df64
+  P->precision = (d->precision == MM_FP32 || d->precision == MM_FP32_DF64) ? MM_FP32 : MM_FP64;
   P->algo = (d->toeplitz_algo == MM_TPLZ_DIRECT) ? MM_TPLZ_DIRECT : MM_TPLZ_FFT;
+  P->df64 = (d->precision == MM_DF64 || d->precision == MM_FP32_DF64) && P->algo == MM_TPLZ_FFT;
   P->cond_max = d->cond_max > 0 ? d->cond_max : 1e3;
   const int nb = P->n_blocks, lam = P->lambda;
   P->block_off.assign(nb + 1, 0);
@@ -418,6 +423,14 @@ int build_plan(const mm_problem_desc* d, cudaStream_t us, Plan* P) {
   MM_CUDA(launch_spectra(rows_d, P->n_tab, lam, H, costab_d, s));
   MM_CUDA(launch_pair_tables(H, P->n_tab, costab_d, P->tab64, P->tab32, s));
   MM_CUDA(launch_twiddles(P->tw64, P->tw32, costab_d, s));
+  if (P->df64) {
+    MM_TRY(dalloc(P, &P->wdf, P->N));
+    MM_TRY(dalloc(P, &P->tabdf, (size_t)P->n_tab * kM));
+    MM_TRY(dalloc(P, &P->twdf, kM));
+    MM_CUDA(launch_weights_df(P->psi, P->N, P->wdf, s));
+    MM_CUDA(launch_c64_to_df(P->tab64, (int64_t)P->n_tab * kM, P->tabdf, s));
+    MM_CUDA(launch_c64_to_df(P->tw64, kM, P->twdf, s));
+  }
   std::vector<double> Hh((size_t)P->n_tab * (kM + 1));
   MM_CUDA(cudaMemcpyAsync(Hh.data(), H, Hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
 
@@ -486,9 +499,74 @@ TileArgs base_args(const Plan* P, bool fp32) {
   return a;
 }
 
-// y4 (accumulated, pre-zeroed by the caller) += A x4 in FP64, [nrhs][n_obs][4]
+// df64 path: samples per right-hand side of the un-pointed buffer (N rounded up to 4, so every
+// column starts 16-byte aligned), and how many columns one pass of it holds
+int64_t df_stride(const Plan* P) { return (P->N + 3) / 4 * 4; }
+int df_cols(const Plan* P, int nrhs) {
+  const int64_t per = df_stride(P) * (int64_t)sizeof(float2);
+  const int64_t k = std::max<int64_t>(1, (int64_t)kSplitTBytes / per);
+  return (int)std::min<int64_t>(nrhs, k);
+}
+
+// df64 working buffers for nrhs columns (allocated outside graph capture)
+int ensure_df(Plan* P, int nrhs) {
+  if (!P->df64) return MM_OK;
+  const size_t t_elems = (size_t)df_cols(P, nrhs) * (size_t)df_stride(P);
+  if (P->tdf_cap < t_elems) {
+    dfree(P->tdf);
+    P->tdf_cap = 0;
+    MM_TRY(dalloc(P, &P->tdf, t_elems));
+    P->tdf_cap = t_elems;
+  }
+  const size_t m_elems = (size_t)df_cols(P, nrhs) * (size_t)P->n_obs * 2;
+  if (P->mapdf_cap < m_elems) {
+    dfree(P->mapdf);
+    P->mapdf_cap = 0;
+    MM_TRY(dalloc(P, &P->mapdf, m_elems));
+    P->mapdf_cap = m_elems;
+  }
+  return MM_OK;
+}
+
+TileArgs df_args(const Plan* P) {
+  TileArgs a = base_args(P, false);
+  a.wdf = P->wdf;
+  a.tab = P->tabdf;
+  a.tw = P->twdf;
+  a.x_stride = df_stride(P);
+  a.y_stride = P->n_obs * 4;
+  return a;
+}
+
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
+// y4 (accumulated, pre-zeroed by the caller) += A x4 with the FP64-class operators, [nrhs][n_obs][4]
 int apply64_internal(Plan* P, const double* x4, double* y4, int nrhs, cudaStream_t s,
                      const int32_t* done = nullptr, int done_stride = 0) {
+  if (P->df64) {
+    const int k = df_cols(P, nrhs);
+    if (capturing(s) && (P->tdf_cap < (size_t)k * df_stride(P) || P->mapdf_cap < (size_t)k * P->n_obs * 2))
+      return fail(MM_EINVAL, "df64 buffers must be allocated before graph capture");
+    MM_TRY(ensure_df(P, nrhs));
+    for (int r0 = 0; r0 < nrhs; r0 += k) {
+      const int g = std::min(k, nrhs - r0);
+      const int32_t* dn = done ? done + (int64_t)r0 * done_stride : nullptr;
+      MM_CUDA(launch_map_to_df(x4 + (size_t)r0 * P->n_obs * 4, (int64_t)g * P->n_obs, P->mapdf, s));
+      MM_CUDA(launch_unpoint_df(P->lpix, P->wdf, P->N, P->mapdf, P->n_obs, g, dn, done_stride, P->tdf,
+                                df_stride(P), s));
+      TileArgs a = df_args(P);
+      a.nrhs = g;
+      a.x = P->tdf;
+      a.y = y4 + (size_t)r0 * P->n_obs * 4;
+      a.done = dn;
+      a.done_stride = done_stride;
+      MM_CUDA(launch_tiles_df(a, s));
+    }
+    return MM_OK;
+  }
   if (P->algo == MM_TPLZ_DIRECT) {
     MM_TRY(ensure_td(P));
     for (int r = 0; r < nrhs; r++) {
@@ -745,7 +823,8 @@ struct Server {
 size_t estimate_footprint(const Request& r) {
   int64_t N = 0;
   for (int64_t v : r.block_len) N += v;
-  return (size_t)N * 44 + (size_t)r.desc.n_pix * 480 + ((size_t)64 << 20);
+  // pointing, FP64 and df64 weights, un-pointed FP32 and df64 buffers: 68 bytes per sample
+  return (size_t)N * 68 + (size_t)r.desc.n_pix * 480 + ((size_t)64 << 20);
 }
 
 void finish_request(Server* S, Request* r, int status) {
@@ -776,7 +855,7 @@ int start_request(Server* S, Request* r) {
   r->desc.psi = r->psi.data();
   r->desc.band = r->band.data();
   r->desc.inputs_on_device = 0;
-  r->desc.precision = MM_FP32;
+  r->desc.precision = MM_FP32_DF64;
   r->plan = new Plan();
   int st = build_plan(&r->desc, S->stream, r->plan);
   if (st != MM_OK) return st;
@@ -1044,6 +1123,20 @@ int mm_rhs(mm_plan_t plan, const void* d, int d_is_fp32, int nrhs, double* b, vo
                                      P->td_a, P->td_b, s));
       MM_CUDA(launch_point64(P->lpix, P->w64, P->N, P->td_b, P->map64_out + (size_t)r * P->n_obs * 4, s));
     }
+  } else if (P->df64) {
+    MM_TRY(ensure_df(P, nrhs));
+    const int k = df_cols(P, nrhs);
+    const size_t esz = d_is_fp32 ? sizeof(float) : sizeof(double);
+    for (int r0 = 0; r0 < nrhs; r0 += k) {
+      const int g = std::min(k, nrhs - r0);
+      MM_CUDA(launch_d_to_df(P->lpix, reinterpret_cast<const char*>(d) + (size_t)r0 * P->N * esz, d_is_fp32,
+                             P->N, g, P->tdf, df_stride(P), s));
+      TileArgs a = df_args(P);
+      a.nrhs = g;
+      a.x = P->tdf;
+      a.y = P->map64_out + (size_t)r0 * P->n_obs * 4;
+      MM_CUDA(launch_tiles_df(a, s));
+    }
   } else {
     TileArgs a = base_args(P, false);
     a.nrhs = nrhs;
@@ -1116,6 +1209,7 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
   CgWork w = make_work(P, c, nrhs, fp32, opts->tol, opts->max_iter);
   if (P->algo == MM_TPLZ_DIRECT) MM_TRY(ensure_td(P));
   if (fp32) MM_TRY(ensure_t32(P, nrhs));
+  MM_TRY(ensure_df(P, nrhs));
   DeflWork dw{};
   const DeflWork* dwp = nullptr;
   if (opts->precond == MM_PREC_2LVL_POST) {

@@ -53,7 +53,8 @@ struct ProbPtrs {
   const int32_t* done;
 };
 
-// MODE_APPLY_T: FP32 A-application whose un-pointed input t = P x was written beforehand
+// MODE_APPLY_T: A-application whose un-pointed input t = P x was written beforehand (FP32
+// tiles: float t; df64 tiles: (hi, lo) float pairs, also used for the masked TOD of the RHS)
 enum Mode { MODE_APPLY = 0, MODE_RHS = 1, MODE_NINV = 2, MODE_APPLY_T = 3 };
 
 // Arguments of the fused Toeplitz-tile kernels.
@@ -65,6 +66,7 @@ struct TileArgs {
   const int32_t* lpix;      // [N] local pixel or -1
   const float* psi;         // [N]            (FP32 path)
   const double2* w64;       // [N] (cos, sin) (FP64 path)
+  const float4* wdf;        // [N] (cos hi, cos lo, sin hi, sin lo) (df64 path)
   const void* tab;          // [n_tab][cl][M/cl] (a, b) of float2 / double2
   const void* tw;           // [M] twiddles W_M^k (float2 / double2)
   const void* x;            // APPLY: map in, [nrhs][n_obs][4]; RHS: d [nrhs][N]; NINV: t [N]
@@ -92,6 +94,8 @@ struct Plan {
   int32_t* lpix = nullptr;             // [N]
   float* psi = nullptr;                // [N]
   double2* w64 = nullptr;              // [N] cos 2psi, sin 2psi in FP64 (FP64 operators)
+  bool df64 = false;                   // FP64-class operators run in df64 arithmetic
+  float4* wdf = nullptr;               // [N] df64 weights (df64 plans)
   int32_t* obs_to_global = nullptr;    // [n_obs]
   double* minv = nullptr;              // [n_obs][6] symmetric inverse BD blocks (00 01 02 11 12 22)
   double* band = nullptr;              // [n_blocks][lambda + 1]
@@ -104,6 +108,12 @@ struct Plan {
   double2* tab64 = nullptr;            // [n_tab][M]
   float2* tw32 = nullptr;              // [M]
   double2* tw64 = nullptr;             // [M]
+  float4* tabdf = nullptr;             // [n_tab][M] df64 pair tables (df64 plans)
+  float4* twdf = nullptr;              // [M] df64 twiddles
+  float2* tdf = nullptr;               // [nrhs][N4] un-pointed df64 input, N4 = N rounded up to 4
+  size_t tdf_cap = 0;
+  float4* mapdf = nullptr;             // [nrhs][n_obs][2] df64 map: (I hi, I lo, Q hi, Q lo), (U hi, U lo, 0, 0)
+  size_t mapdf_cap = 0;
   TileDesc* tiles = nullptr;           // FP64 tiles (one per descriptor)
   int64_t n_tiles = 0;
   TileDesc* segs = nullptr;            // FP32 segments (several tiles per descriptor)
@@ -190,6 +200,16 @@ cudaError_t launch_unpoint32(const int32_t* lpix, const float* psi, int64_t N, c
                              int64_t x_stride, int nrhs, const int32_t* done, int done_stride, float* t,
                              cudaStream_t s);
 cudaError_t launch_tiles_fp64(int mode, const TileArgs& a, cudaStream_t s);
+// df64 tiles and their data preparation (k_df64.cu)
+cudaError_t launch_tiles_df(const TileArgs& a, cudaStream_t s);
+cudaError_t launch_weights_df(const float* psi, int64_t N, float4* wdf, cudaStream_t s);
+cudaError_t launch_c64_to_df(const double2* in, int64_t n, float4* out, cudaStream_t s);
+cudaError_t launch_map_to_df(const double* m4, int64_t n_pix4, float4* out, cudaStream_t s);
+cudaError_t launch_unpoint_df(const int32_t* lpix, const float4* wdf, int64_t N, const float4* mapdf,
+                              int64_t n_obs, int nrhs, const int32_t* done, int done_stride, float2* t,
+                              int64_t t_stride, cudaStream_t s);
+cudaError_t launch_d_to_df(const int32_t* lpix, const void* d, int d_is_fp32, int64_t N, int nrhs,
+                           float2* t, int64_t t_stride, cudaStream_t s);
 int tile_kernels_init();   // sets smem attributes once per process
 int fp32_max_halo_samples();   // largest halo the FP32 segment kernel can keep in shared memory
 

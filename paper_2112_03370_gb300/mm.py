@@ -17,7 +17,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmm.so")
 
 MM_OK, MM_EINVAL, MM_ENOMEM, MM_ENOTSPD, MM_EBREAKDOWN, MM_ENOTCONV, MM_ETIMEOUT, MM_EBUSY, \
     MM_ECUDA = range(9)
-MM_FP64, MM_FP32 = 0, 1
+MM_FP64, MM_FP32, MM_DF64, MM_FP32_DF64 = 0, 1, 2, 3
 MM_TPLZ_AUTO, MM_TPLZ_FFT, MM_TPLZ_DIRECT = 0, 1, 3
 MM_PREC_BD, MM_PREC_2LVL_POST = 0, 1
 STATUS_NAMES = {0: "MM_OK", 1: "MM_EINVAL", 2: "MM_ENOMEM", 3: "MM_ENOTSPD", 4: "MM_EBREAKDOWN",
