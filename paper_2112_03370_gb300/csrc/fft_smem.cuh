@@ -183,9 +183,10 @@ __device__ __forceinline__ void twiddles(const TwiddleTab<C>& tw, int base_idx, 
 
 // One decimation-in-frequency (FWD) or decimation-in-time (inverse) pass over sub-transforms of
 // size Cs with radix R.  `ms` = transform size held by this CTA, `mfull_over_cs` = M / Cs.
+// `ptab` (optional): this pass's twiddles precomputed as ptab[(j - 1) s + n1] = W_M^{j n1 M/Cs}.
 template <int R, bool FWD, int NT, typename C>
 __device__ __forceinline__ void fft_pass(C* __restrict__ sm, const TwiddleTab<C>& tw, int ms,
-                                         int cs, int mfull_over_cs) {
+                                         int cs, int mfull_over_cs, const C* __restrict__ ptab = nullptr) {
   const int s = cs / R;
   const int nbf = ms / R;
   for (int q = threadIdx.x; q < nbf; q += NT) {
@@ -198,17 +199,27 @@ __device__ __forceinline__ void fft_pass(C* __restrict__ sm, const TwiddleTab<C>
     if (FWD) {
       dft_small<R, true>(a);
       if (s > 1 && n1 != 0) {
-        C w[R];
-        twiddles<R>(tw, n1 * mfull_over_cs, w);
+        if (ptab) {
 #pragma unroll
-        for (int j = 1; j < R; j++) a[j] = c_mul(a[j], w[j]);
+          for (int j = 1; j < R; j++) a[j] = c_mul(a[j], ptab[(j - 1) * s + n1]);
+        } else {
+          C w[R];
+          twiddles<R>(tw, n1 * mfull_over_cs, w);
+#pragma unroll
+          for (int j = 1; j < R; j++) a[j] = c_mul(a[j], w[j]);
+        }
       }
     } else {
       if (s > 1 && n1 != 0) {
-        C w[R];
-        twiddles<R>(tw, n1 * mfull_over_cs, w);
+        if (ptab) {
 #pragma unroll
-        for (int j = 1; j < R; j++) a[j] = c_mulc(a[j], w[j]);
+          for (int j = 1; j < R; j++) a[j] = c_mulc(a[j], ptab[(j - 1) * s + n1]);
+        } else {
+          C w[R];
+          twiddles<R>(tw, n1 * mfull_over_cs, w);
+#pragma unroll
+          for (int j = 1; j < R; j++) a[j] = c_mulc(a[j], w[j]);
+        }
       }
       dft_small<R, false>(a);
     }
@@ -225,12 +236,37 @@ struct SmemFFT {
   static constexpr int NP16 = LOGMS / 4;
   static constexpr int REM = LOGMS % 4;
 
+  // Radix-16 passes p >= 1 have few distinct sub-transform offsets n1 (s = MS / 16^(p+1)), so
+  // their 15 s twiddles are tabulated once per CTA in shared memory; pass 0 (s = MS / 16)
+  // computes them from the two-level table.
+  static constexpr int pass_s(int p) { return (MS >> (4 * p)) / 16; }
+  static constexpr int pass_tab_offset(int p) {
+    int o = 0;
+    for (int q = 1; q < p; q++) o += 15 * pass_s(q);
+    return o;
+  }
+  static constexpr int kPassTabEntries = pass_tab_offset(NP16);
+
+  // Fill the pass tables (all threads; the caller synchronises before the first transform).
   template <typename C>
-  __device__ static void forward(C* sm, const TwiddleTab<C>& tw) {
+  __device__ static void build_pass_tables(C* ptab, const TwiddleTab<C>& tw) {
+    for (int i = threadIdx.x; i < kPassTabEntries; i += NT) {
+      int p = 1;
+      while (p + 1 < NP16 && i >= pass_tab_offset(p + 1)) p++;
+      const int s = pass_s(p);
+      const int r = i - pass_tab_offset(p);
+      const int j = r / s + 1, n1 = r % s;
+      const int cs = MS >> (4 * p);
+      ptab[i] = tw(j * n1 * (MFULL / cs));
+    }
+  }
+
+  template <typename C>
+  __device__ static void forward(C* sm, const TwiddleTab<C>& tw, const C* ptab) {
 #pragma unroll 1
     for (int p = 0; p < NP16; p++) {
       const int cs = MS >> (4 * p);
-      fft_pass<16, true, NT>(sm, tw, MS, cs, MFULL / cs);
+      fft_pass<16, true, NT>(sm, tw, MS, cs, MFULL / cs, p > 0 ? ptab + pass_tab_offset(p) : nullptr);
       __syncthreads();
     }
     if constexpr (REM > 0) {
@@ -240,7 +276,7 @@ struct SmemFFT {
   }
 
   template <typename C>
-  __device__ static void inverse(C* sm, const TwiddleTab<C>& tw) {
+  __device__ static void inverse(C* sm, const TwiddleTab<C>& tw, const C* ptab) {
     if constexpr (REM > 0) {
       fft_pass<(1 << REM), false, NT>(sm, tw, MS, 1 << REM, MFULL >> REM);
       __syncthreads();
@@ -248,7 +284,7 @@ struct SmemFFT {
 #pragma unroll 1
     for (int p = NP16 - 1; p >= 0; p--) {
       const int cs = MS >> (4 * p);
-      fft_pass<16, false, NT>(sm, tw, MS, cs, MFULL / cs);
+      fft_pass<16, false, NT>(sm, tw, MS, cs, MFULL / cs, p > 0 ? ptab + pass_tab_offset(p) : nullptr);
       __syncthreads();
     }
   }

@@ -259,6 +259,25 @@ __global__ void k_weights64(const float* __restrict__ psi, int64_t N, double2* _
   }
 }
 
+// (cos 2psi, sin 2psi) in FP32 with the accurate single-precision sincosf: the FP32 operator must
+// stay within a few ulp of the FP64 one, or the FP64-class residual replacement of the
+// mixed-precision solver stops converging (a systematic weight error perturbs the smallest
+// eigenvalues of A)
+__global__ void k_weights32(const float* __restrict__ psi, int64_t N, float2* __restrict__ w) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float s, c;
+    sincosf(2.f * psi[i], &s, &c);
+    w[i] = make_float2(c, s);
+  }
+}
+
+cudaError_t launch_weights32(const float* psi, int64_t N, float2* w32, cudaStream_t s) {
+  if (N == 0) return cudaSuccess;
+  k_weights32<<<8 * 152, 256, 0, s>>>(psi, N, w32);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_weights64(const float* psi, int64_t N, double2* w64, cudaStream_t s) {
   if (N == 0) return cudaSuccess;
   k_weights64<<<8 * 152, 256, 0, s>>>(psi, N, w64);

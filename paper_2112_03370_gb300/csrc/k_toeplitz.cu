@@ -83,26 +83,24 @@ template <> struct Map4<df> {
 // map values that depend on the pixel ids.  That keeps 2 x NQ memory round trips in flight per
 // thread instead of one, which is what bounds a 16-warp CTA.
 
-// Raw per-sample weight data: the angle (FP32 path, weights recomputed in registers) or the
-// precomputed (cos 2psi, sin 2psi) pair (FP64 path).
+// Raw per-sample weight data: the (cos 2psi, sin 2psi) pair precomputed at plan time, in the
+// precision of the tile (FP32 / FP64 / df64).
 template <typename T> struct WRaw;
-template <> struct WRaw<float> { float v; };
+template <> struct WRaw<float> { float2 v; };
 template <> struct WRaw<double> { double2 v; };
 template <> struct WRaw<df> { float4 v; };   // (cos hi, cos lo, sin hi, sin lo)
 
 template <typename T>
 __device__ __forceinline__ void load_w(const TileArgs& a, int64_t g, WRaw<T>& w) {
-  if constexpr (std::is_same<T, float>::value) w.v = __ldg(a.psi + g);
+  if constexpr (std::is_same<T, float>::value) w.v = __ldg(a.w32 + g);
   else if constexpr (std::is_same<T, df>::value) w.v = __ldg(a.wdf + g);
   else w.v = __ldg(a.w64 + g);
 }
 template <typename T>
 __device__ __forceinline__ void weights_of(const WRaw<T>& w, T& c, T& s) {
   if constexpr (std::is_same<T, float>::value) {
-    // accurate single-precision sine/cosine: the FP32 operator must stay within a few ulp of the
-    // FP64 one, or the FP64 residual replacement of the mixed-precision solver stops converging
-    // (a systematic weight error perturbs the smallest eigenvalues of A)
-    sincosf(2.f * w.v, &s, &c);
+    c = w.v.x;
+    s = w.v.y;
   } else if constexpr (std::is_same<T, df>::value) {
     c = df_make(w.v.x, w.v.y);
     s = df_make(w.v.z, w.v.w);
@@ -121,8 +119,10 @@ __device__ __forceinline__ void quad_meta(const TileArgs& a, int64_t g, int64_t 
     p[0] = v.x; p[1] = v.y; p[2] = v.z; p[3] = v.w;
     if (NEED_W) {
       if constexpr (std::is_same<T, float>::value) {
-        const float4 f = __ldg(reinterpret_cast<const float4*>(a.psi + g));
-        w[0].v = f.x; w[1].v = f.y; w[2].v = f.z; w[3].v = f.w;
+        const float4 f01 = __ldg(reinterpret_cast<const float4*>(a.w32 + g));
+        const float4 f23 = __ldg(reinterpret_cast<const float4*>(a.w32 + g + 2));
+        w[0].v = make_float2(f01.x, f01.y); w[1].v = make_float2(f01.z, f01.w);
+        w[2].v = make_float2(f23.x, f23.y); w[3].v = make_float2(f23.z, f23.w);
       } else {
 #pragma unroll
         for (int e = 0; e < 4; e++) load_w<T>(a, g + e, w[e]);
@@ -277,8 +277,8 @@ __device__ __forceinline__ void pair_meta(const TileArgs& a, int64_t g, int64_t 
     p[0] = v.x; p[1] = v.y;
     if (need_w) {
       if constexpr (std::is_same<T, float>::value) {
-        const float2 f = __ldg(reinterpret_cast<const float2*>(a.psi + g));
-        w[0].v = f.x; w[1].v = f.y;
+        const float4 f = __ldg(reinterpret_cast<const float4*>(a.w32 + g));
+        w[0].v = make_float2(f.x, f.y); w[1].v = make_float2(f.z, f.w);
       } else {
         w[0].v = __ldg(a.w64 + g); w[1].v = __ldg(a.w64 + g + 1);
       }
@@ -371,14 +371,16 @@ __device__ __forceinline__ void scatter_pairs(const TileArgs& a, int rhs, const 
 // One overlap-save tile (CL = 1) or half a tile (CL = 2) per CTA.
 template <typename T, int CL, int MODE, bool MULTI = false>
 __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
+  constexpr int NT = kTileThreads;
   using C = typename V2<T>::t;
   constexpr int LOGMS = kLogM - (CL == 2 ? 1 : 0);
   constexpr int MS = 1 << LOGMS;
-  using FFT = SmemFFT<LOGMS, kM, kTileThreads>;
+  using FFT = SmemFFT<LOGMS, kM, NT>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
   C* tw_sm = sm + smem_pad(MS);
-  T* halo = reinterpret_cast<T*>(tw_sm + twiddle_tab_entries(kM));   // CL == 1 segments
+  C* ptab = tw_sm + twiddle_tab_entries(kM);                          // per-pass twiddles
+  T* halo = reinterpret_cast<T*>(ptab + FFT::kPassTabEntries);       // CL == 1 segments
 
   const int64_t unit = blockIdx.x / CL;
   const int rank = (CL == 2) ? (int)(blockIdx.x % CL) : 0;
@@ -388,19 +390,21 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
   TileArgs a = a_in;
   if constexpr (MULTI) {   // this tile's problem
     const ProbPtrs pp = a_in.probs[seg.prob];
-    a.lpix = pp.lpix; a.psi = pp.psi; a.w64 = pp.w64; a.tab = pp.tab;
+    a.lpix = pp.lpix; a.w32 = pp.w32; a.w64 = pp.w64; a.tab = pp.tab;
     a.x = pp.x; a.y = pp.y; a.done = pp.done;
   }
   // both CTAs of a cluster read the same flag, so they leave together
   if (a.done != nullptr && a.done[(int64_t)rhs * a.done_stride] != 0) return;
   const C* __restrict__ tw_g = reinterpret_cast<const C*>(a.tw);
-  const TwiddleTab<C> tw = load_twiddle_tab<C, kM, kTileThreads>(tw_sm, tw_g);
+  const TwiddleTab<C> tw = load_twiddle_tab<C, kM, NT>(tw_sm, tw_g);
   const C* __restrict__ tab =
       reinterpret_cast<const C*>(a.tab) + ((int64_t)seg.tab * CL + rank) * MS;
   const T sc = (T)seg.scale;
   constexpr int NQ = std::is_same<T, float>::value ? 4 : 2;
   constexpr int HALF_Q = MS / 2;          // quads (4 real samples) of this CTA's complex range
   const int halo_q = (kL - seg.vstep) / 4;
+  __syncthreads();
+  FFT::build_pass_tables(ptab, tw);
   __syncthreads();
 
   const int n_steps = (CL == 1) ? seg.n_steps : 1;   // only the FP32 kernel walks segments
@@ -415,31 +419,31 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
     if constexpr (CL == 1) {
       int q_first = 0;
       if (step > 0) {   // the previous tile's last L - vstep samples are this tile's first ones
-        for (int n = threadIdx.x; n < 2 * halo_q; n += kTileThreads)
+        for (int n = threadIdx.x; n < 2 * halo_q; n += NT)
           sm[smem_pad(n)] = C{halo[2 * n], halo[2 * n + 1]};
         q_first = halo_q;
       }
       constexpr int NB = 8;
       const int n_first = 2 * q_first;
-      for (int n0 = n_first + threadIdx.x; n0 < MS; n0 += NB * kTileThreads) {
+      for (int n0 = n_first + threadIdx.x; n0 < MS; n0 += NB * NT) {
         int64_t g[NB];
         T v[NB][2];
 #pragma unroll
         for (int u = 0; u < NB; u++) {
-          const int n = n0 + u * kTileThreads;
+          const int n = n0 + u * NT;
           g[u] = (n < MS) ? td.in0 + 2 * (int64_t)n : td.blk_hi;   // past the end: zeros
         }
         gather_pairs<T, MODE, NB>(a, rhs, td, g, v);
 #pragma unroll
         for (int u = 0; u < NB; u++) {
-          const int n = n0 + u * kTileThreads;
+          const int n = n0 + u * NT;
           if (n < MS) sm[smem_pad(n)] = C{v[u][0], v[u][1]};
         }
       }
       __syncthreads();
       if (step + 1 < n_steps) {   // keep input samples [vstep, L) for the next tile
         const int n0 = seg.vstep / 2;
-        for (int n = threadIdx.x; n < 2 * halo_q; n += kTileThreads) {
+        for (int n = threadIdx.x; n < 2 * halo_q; n += NT) {
           const C z = sm[smem_pad(n0 + n)];
           halo[2 * n] = z.x;
           halo[2 * n + 1] = z.y;
@@ -448,18 +452,18 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
       }
     } else {
       // pairs (quad q, quad q + MS/2): z[n] and z[n + MS] for n = 2q, 2q + 1
-      for (int q0 = threadIdx.x; q0 < HALF_Q; q0 += (NQ / 2) * kTileThreads) {
+      for (int q0 = threadIdx.x; q0 < HALF_Q; q0 += (NQ / 2) * NT) {
         int64_t g[NQ];
         T v[NQ][4];
 #pragma unroll
         for (int u = 0; u < NQ / 2; u++) {
-          g[2 * u] = td.in0 + 4 * (int64_t)(q0 + u * kTileThreads);
+          g[2 * u] = td.in0 + 4 * (int64_t)(q0 + u * NT);
           g[2 * u + 1] = g[2 * u] + 2 * (int64_t)MS;
         }
         gather_quads<T, MODE, NQ>(a, rhs, td, g, v);
 #pragma unroll
         for (int u = 0; u < NQ / 2; u++) {
-          const int q = q0 + u * kTileThreads;
+          const int q = q0 + u * NT;
 #pragma unroll
           for (int h = 0; h < 2; h++) {
             const int n = 2 * q + h;
@@ -472,7 +476,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
       __syncthreads();
     }
 
-    FFT::forward(sm, tw);
+    FFT::forward(sm, tw, ptab);
 
     // ---- pair update with the band's precomputed (a_k, b_k) in storage order ----
     // Frequencies k and M - k pair up.  In the digit-reversed storage order the lowest frequency
@@ -485,13 +489,13 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
       constexpr int D = MS / 16;
       const int n_items = (CL == 2 && rank == 1) ? MS / 2 : (7 * D + D / 2 + D);
       constexpr int PB = (MODE == MODE_APPLY && sizeof(T) == 4) ? 1 : 4;
-      for (int u0 = threadIdx.x; u0 < n_items; u0 += PB * kTileThreads) {
+      for (int u0 = threadIdx.x; u0 < n_items; u0 += PB * NT) {
         int jj[PB], jp[PB];
         bool act[PB];
         C ab[PB], abp[PB], z[PB], zp[PB];
 #pragma unroll
         for (int b = 0; b < PB; b++) {
-          const int u = u0 + b * kTileThreads;
+          const int u = u0 + b * NT;
           int j = 0, p = 0;
           bool ok = u < n_items;
           if (CL == 2 && rank == 1) {
@@ -536,7 +540,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
     }
     __syncthreads();
 
-    FFT::inverse(sm, tw);
+    FFT::inverse(sm, tw, ptab);
 
     // ---- scatter of the tile's valid outputs ----
     // output quads covering real offsets [r_lo, r_hi); rank r of a cluster owns complex indices
@@ -546,7 +550,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
     if constexpr (CL == 2) {
       cg::cluster_group cl = cg::this_cluster();
       if (rank == 1) {
-        for (int n = threadIdx.x; n < MS; n += kTileThreads) {
+        for (int n = threadIdx.x; n < MS; n += NT) {
           sm[smem_pad(n)] = c_mulc(sm[smem_pad(n)], tw(n));   // W_M^{-n} O'[n]
         }
       }
@@ -556,12 +560,12 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
     if constexpr (CL == 1) {
       constexpr int NB = 8;
       const int n_lo = r_lo >> 1, n_hi = (r_hi + 1) >> 1;
-      for (int n0 = n_lo + threadIdx.x; n0 < n_hi; n0 += NB * kTileThreads) {
+      for (int n0 = n_lo + threadIdx.x; n0 < n_hi; n0 += NB * NT) {
         int64_t g[NB];
         T y[NB][2];
 #pragma unroll
         for (int u = 0; u < NB; u++) {
-          const int n = n0 + u * kTileThreads;
+          const int n = n0 + u * NT;
           if (n < n_hi) {
             const C z = sm[smem_pad(n)];
             g[u] = td.in0 + 2 * (int64_t)n;
@@ -577,12 +581,12 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
     } else {
       const int q_lo = max(r_lo >> 2, rank * HALF_Q);
       const int q_hi = min((r_hi + 3) >> 2, (rank + 1) * HALF_Q);
-      for (int q0 = q_lo + threadIdx.x; q0 < q_hi; q0 += NQ * kTileThreads) {
+      for (int q0 = q_lo + threadIdx.x; q0 < q_hi; q0 += NQ * NT) {
         int64_t g[NQ];
         T y[NQ][4];
 #pragma unroll
         for (int u = 0; u < NQ; u++) {
-          const int q = q0 + u * kTileThreads;
+          const int q = q0 + u * NT;
           g[u] = td.in0 + 4 * (int64_t)q;
           if (q < q_hi) {
 #pragma unroll
@@ -608,9 +612,13 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
   }
 }
 
-constexpr size_t kSmemBytes32 = (size_t)(smem_pad(kM) + twiddle_tab_entries(kM)) * sizeof(float2);
+constexpr size_t kSmemBytes32 =
+    (size_t)(smem_pad(kM) + twiddle_tab_entries(kM) + SmemFFT<kLogM, kM, kTileThreads>::kPassTabEntries) *
+    sizeof(float2);
 constexpr size_t kSmemMax = 227 * 1024;
-constexpr size_t kSmemBytes64 = (size_t)(smem_pad(kM / 2) + twiddle_tab_entries(kM)) * sizeof(double2);
+constexpr size_t kSmemBytes64 =
+    (size_t)(smem_pad(kM / 2) + twiddle_tab_entries(kM) + SmemFFT<kLogM - 1, kM, kTileThreads>::kPassTabEntries) *
+    sizeof(double2);
 
 int tile_kernels_init() {
   static int done = 0;
@@ -675,47 +683,43 @@ cudaError_t launch_tiles_fp32(int mode, const TileArgs& a, int halo_samples, cud
 // t = P x over all samples at full occupancy: lane = sample, so pointing loads coalesce and the map
 // gathers of a scan stay on a few cache lines per warp; the random loads of many warps overlap.
 __global__ void __launch_bounds__(256) k_unpoint32(const int32_t* __restrict__ lpix,
-                                                   const float* __restrict__ psi, int64_t N,
+                                                   const float2* __restrict__ w, int64_t N,
                                                    const float4* __restrict__ x4, int64_t x_stride4,
                                                    const int32_t* __restrict__ done, int done_stride,
-                                                   float* __restrict__ t) {
+                                                   float* __restrict__ t, int64_t t_stride) {
   const int rhs = blockIdx.y;
   if (done != nullptr && done[(int64_t)rhs * done_stride] != 0) return;
   const float4* x = x4 + rhs * x_stride4;
-  float* tr = t + rhs * N;
+  float* tr = t + rhs * t_stride;
   constexpr int U = 4;
   for (int64_t i0 = (int64_t)blockIdx.x * 256 * U + threadIdx.x; i0 < N; i0 += (int64_t)gridDim.x * 256 * U) {
     int32_t p[U];
-    float a[U];
+    float2 cs[U];
     float4 m[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int64_t i = i0 + u * 256;
       p[u] = (i < N) ? __ldg(lpix + i) : -1;
-      a[u] = (i < N) ? __ldg(psi + i) : 0.f;
+      cs[u] = (i < N) ? __ldg(w + i) : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int u = 0; u < U; u++) m[u] = (p[u] >= 0) ? __ldg(x + p[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int64_t i = i0 + u * 256;
-      if (i < N) {
-        float s, c;
-        sincosf(2.f * a[u], &s, &c);
-        tr[i] = (p[u] >= 0) ? m[u].x + c * m[u].y + s * m[u].z : 0.f;
-      }
+      if (i < N) tr[i] = (p[u] >= 0) ? m[u].x + cs[u].x * m[u].y + cs[u].y * m[u].z : 0.f;
     }
   }
 }
 
-cudaError_t launch_unpoint32(const int32_t* lpix, const float* psi, int64_t N, const float* x4,
+cudaError_t launch_unpoint32(const int32_t* lpix, const float2* w32, int64_t N, const float* x4,
                              int64_t x_stride, int nrhs, const int32_t* done, int done_stride, float* t,
-                             cudaStream_t s) {
+                             int64_t t_stride, cudaStream_t s) {
   if (N == 0 || nrhs <= 0) return cudaSuccess;
   int64_t g = (N + 1023) / 1024;
   if (g > 152 * 16) g = 152 * 16;
-  k_unpoint32<<<dim3((unsigned)g, nrhs), 256, 0, s>>>(lpix, psi, N, reinterpret_cast<const float4*>(x4),
-                                                     x_stride / 4, done, done_stride, t);
+  k_unpoint32<<<dim3((unsigned)g, nrhs), 256, 0, s>>>(lpix, w32, N, reinterpret_cast<const float4*>(x4),
+                                                     x_stride / 4, done, done_stride, t, t_stride);
   return cudaGetLastError();
 }
 

@@ -130,7 +130,7 @@ void free_plan(Plan* P) {
   cudaGetDevice(&cur);
   cudaSetDevice(P->device);
   if (P->stream) cudaStreamSynchronize(P->stream);
-  dfree(P->lpix); dfree(P->psi); dfree(P->w64); dfree(P->obs_to_global); dfree(P->minv);
+  dfree(P->lpix); dfree(P->psi); dfree(P->w32); dfree(P->w64); dfree(P->obs_to_global); dfree(P->minv);
   dfree(P->band); dfree(P->block_off_dev); dfree(P->c0_blk); dfree(P->tab32); dfree(P->tab64);
   dfree(P->tw32); dfree(P->tw64); dfree(P->tiles); dfree(P->segs); dfree(P->map32_in); dfree(P->map32_out);
   dfree(P->map64_in); dfree(P->map64_out); dfree(P->td_a); dfree(P->td_b); dfree(P->t32);
@@ -400,6 +400,8 @@ int build_plan(const mm_problem_desc* d, cudaStream_t us, Plan* P) {
   MM_CUDA(launch_localize(pix, keep, lid, P->N, P->lpix, s));
   MM_TRY(dalloc(P, &P->w64, P->N));
   MM_CUDA(launch_weights64(P->psi, P->N, P->w64, s));
+  MM_TRY(dalloc(P, &P->w32, P->N));
+  MM_CUDA(launch_weights32(P->psi, P->N, P->w32, s));
 
   // Toeplitz spectra: L-point circulant spectrum of each distinct band, then the pair tables
   BandTables bt = dedupe_bands(band, nb, lam);
@@ -490,7 +492,7 @@ TileArgs base_args(const Plan* P, bool fp32) {
   a.nrhs = 1;
   a.N = P->N;
   a.lpix = P->lpix;
-  a.psi = P->psi;
+  a.w32 = P->w32;
   a.w64 = P->w64;
   a.tab = fp32 ? (const void*)P->tab32 : (const void*)P->tab64;
   a.tw = fp32 ? (const void*)P->tw32 : (const void*)P->tw64;
@@ -590,8 +592,10 @@ int apply64_internal(Plan* P, const double* x4, double* y4, int nrhs, cudaStream
 }
 
 // plan-owned un-pointed buffer of the split FP32 A-application (allocated outside graph capture)
+int64_t t32_stride(const Plan* P) { return (P->N + 3) / 4 * 4; }
+
 int ensure_t32(Plan* P, int nrhs) {
-  const size_t t_elems = (size_t)nrhs * (size_t)P->N;
+  const size_t t_elems = (size_t)nrhs * (size_t)t32_stride(P);
   if (t_elems * sizeof(float) > kSplitTBytes || P->t32_cap >= t_elems) return MM_OK;
   dfree(P->t32);
   P->t32_cap = 0;
@@ -613,13 +617,14 @@ int apply32_internal(Plan* P, const float* x32, float* y32, int nrhs, cudaStream
   a.done_stride = done_stride;
   // Un-point first at full occupancy (t = P x into a plan-owned FP32 buffer), then the tiles
   // stream t instead of gathering the map themselves; fused gather when the buffer would be large.
-  const size_t t_elems = (size_t)nrhs * (size_t)P->N;
+  const size_t t_elems = (size_t)nrhs * (size_t)t32_stride(P);
   if (t_elems * sizeof(float) <= kSplitTBytes) {
     MM_TRY(ensure_t32(P, nrhs));
-    MM_CUDA(launch_unpoint32(P->lpix, P->psi, P->N, x32, P->n_obs * 4, nrhs, done, done_stride, P->t32, s));
+    MM_CUDA(launch_unpoint32(P->lpix, P->w32, P->N, x32, P->n_obs * 4, nrhs, done, done_stride, P->t32,
+                             t32_stride(P), s));
     if (mid) MM_CUDA(cudaEventRecord(mid, s));
     a.x = P->t32;
-    a.x_stride = P->N;
+    a.x_stride = t32_stride(P);
     MM_CUDA(launch_tiles_fp32(MODE_APPLY_T, a, P->seg_halo, s));
   } else {
     if (mid) MM_CUDA(cudaEventRecord(mid, s));
@@ -823,8 +828,8 @@ struct Server {
 size_t estimate_footprint(const Request& r) {
   int64_t N = 0;
   for (int64_t v : r.block_len) N += v;
-  // pointing, FP64 and df64 weights, un-pointed FP32 and df64 buffers: 68 bytes per sample
-  return (size_t)N * 68 + (size_t)r.desc.n_pix * 480 + ((size_t)64 << 20);
+  // pointing, FP32, FP64 and df64 weights, un-pointed FP32 and df64 buffers: 76 bytes per sample
+  return (size_t)N * 76 + (size_t)r.desc.n_pix * 480 + ((size_t)64 << 20);
 }
 
 void finish_request(Server* S, Request* r, int status) {
@@ -889,7 +894,7 @@ int rebuild_launch(Server* S) {
     halo = std::max(halo, (int)P->seg_halo);
     ProbPtrs pp{};
     pp.lpix = P->lpix;
-    pp.psi = P->psi;
+    pp.w32 = P->w32;
     pp.w64 = P->w64;
     pp.tab = P->tab32;
     pp.x = r->cg->p32;

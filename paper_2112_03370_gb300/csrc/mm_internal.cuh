@@ -45,7 +45,7 @@ struct TileDesc {
 // Per-problem pointers of a launch that batches the tiles of several plans (serving).
 struct ProbPtrs {
   const int32_t* lpix;
-  const float* psi;
+  const float2* w32;
   const double2* w64;
   const void* tab;
   const void* x;
@@ -64,7 +64,7 @@ struct TileArgs {
   int32_t nrhs;
   int64_t N;
   const int32_t* lpix;      // [N] local pixel or -1
-  const float* psi;         // [N]            (FP32 path)
+  const float2* w32;        // [N] (cos, sin) (FP32 path)
   const double2* w64;       // [N] (cos, sin) (FP64 path)
   const float4* wdf;        // [N] (cos hi, cos lo, sin hi, sin lo) (df64 path)
   const void* tab;          // [n_tab][cl][M/cl] (a, b) of float2 / double2
@@ -93,6 +93,7 @@ struct Plan {
   // device state
   int32_t* lpix = nullptr;             // [N]
   float* psi = nullptr;                // [N]
+  float2* w32 = nullptr;               // [N] cos 2psi, sin 2psi in FP32 (FP32 operators)
   double2* w64 = nullptr;              // [N] cos 2psi, sin 2psi in FP64 (FP64 operators)
   bool df64 = false;                   // FP64-class operators run in df64 arithmetic
   float4* wdf = nullptr;               // [N] df64 weights (df64 plans)
@@ -119,7 +120,8 @@ struct Plan {
   TileDesc* segs = nullptr;            // FP32 segments (several tiles per descriptor)
   int64_t n_segs = 0;
   std::vector<TileDesc> segs_host;     // host copy (multi-problem launches)
-  float* t32 = nullptr;                // [nrhs][N] un-pointed FP32 input of the tiles
+  float* t32 = nullptr;                // [nrhs][N4] un-pointed FP32 input of the tiles (N4 = N
+                                       // rounded up to 4)
   size_t t32_cap = 0;
   int32_t seg_halo = 0;                // largest L - vstep over the segments (samples)
 
@@ -182,6 +184,7 @@ cudaError_t launch_compact(const int32_t* keep, const int32_t* lid, const double
 cudaError_t launch_localize(const int32_t* pix, const int32_t* keep, const int32_t* lid,
                             int64_t N, int32_t* lpix, cudaStream_t s);
 cudaError_t launch_weights64(const float* psi, int64_t N, double2* w64, cudaStream_t s);
+cudaError_t launch_weights32(const float* psi, int64_t N, float2* w32, cudaStream_t s);
 cudaError_t launch_validate(const int32_t* pix, const float* psi, int64_t N, int64_t n_pix,
                             int32_t* bad, cudaStream_t s);
 cudaError_t launch_spectra(const double* band_rows, int32_t n_tab, int32_t lambda,
@@ -195,10 +198,11 @@ cudaError_t launch_twiddles(double2* tw64, float2* tw32, const double* costab, c
 cudaError_t launch_tiles_fp32(int mode, const TileArgs& a, int halo_samples, cudaStream_t s);
 // FP32 A-application over the tiles of several plans at once (a.probs set, nrhs = 1)
 cudaError_t launch_tiles_fp32_multi(const TileArgs& a, int halo_samples, cudaStream_t s);
-// t [nrhs][N] float32 = P x for every sample (0 at masked samples), x float4 maps [nrhs][n_obs]
-cudaError_t launch_unpoint32(const int32_t* lpix, const float* psi, int64_t N, const float* x4,
+// t [nrhs][t_stride] float32 = P x for every sample (0 at masked samples), x float4 maps
+// [nrhs][n_obs]
+cudaError_t launch_unpoint32(const int32_t* lpix, const float2* w32, int64_t N, const float* x4,
                              int64_t x_stride, int nrhs, const int32_t* done, int done_stride, float* t,
-                             cudaStream_t s);
+                             int64_t t_stride, cudaStream_t s);
 cudaError_t launch_tiles_fp64(int mode, const TileArgs& a, cudaStream_t s);
 // df64 tiles and their data preparation (k_df64.cu)
 cudaError_t launch_tiles_df(const TileArgs& a, cudaStream_t s);

@@ -120,7 +120,7 @@ extern "C" int mm_apply_A_noalloc(mm_plan_t plan, const double* x, double* y, in
   a.nrhs = nrhs;
   a.N = P->N;
   a.lpix = P->lpix;
-  a.psi = P->psi;
+  a.w32 = P->w32;
   a.w64 = P->w64;
   a.x = in4;
   a.x_stride = P->n_obs * 4;
