@@ -19,13 +19,19 @@ template <typename T> struct V2;
 template <> struct V2<float> { using t = float2; };
 template <> struct V2<double> { using t = double2; };
 
+// Complex types whose products have their own overloads (double-float) set this to false, so a
+// product that silently took the generic path would not compile.
+template <typename C> struct GenericProduct { static constexpr bool value = true; };
+
 template <typename C> __device__ __forceinline__ C c_add(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
 template <typename C> __device__ __forceinline__ C c_sub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
 template <typename C> __device__ __forceinline__ C c_mul(C a, C b) {
+  static_assert(GenericProduct<C>::value, "complex type with its own product");
   return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
 // a * conj(b)
 template <typename C> __device__ __forceinline__ C c_mulc(C a, C b) {
+  static_assert(GenericProduct<C>::value, "complex type with its own product");
   return C{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
 }
 
@@ -66,7 +72,7 @@ __device__ __forceinline__ C rot16(C a, int e) {
   using T = decltype(a.x);
   const T c = (T)cos16(e);
   const T s = FWD ? (T)(-sin16(e)) : (T)sin16(e);
-  return C{a.x * c - a.y * s, a.x * s + a.y * c};
+  return c_mul(a, C{c, s});
 }
 
 template <bool FWD, typename C>
