@@ -79,7 +79,7 @@ def kernel_source_hash() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2112_03370_gb300", "csrc")
     for f in sorted(os.listdir(d)):
-        if f in ("k_toeplitz.cu", "fft_smem.cuh", "mm_internal.cuh"):
+        if f in ("k_toeplitz.cu", "fft_smem.cuh", "df64.cuh", "mm_internal.cuh"):
             h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -311,8 +311,8 @@ def run_ours(a):
     avg_tile = (t32 - tup) / max(n32, 1) / 1e3
     avg_up = tup / max(n32, 1) / 1e3
     achieved = flops_launch / avg_tile / 1e12
-    tile_bytes = 4.0 * N + 8.0 * N + 16.0 * plan.n_obs   # t, pointing (scatter), map out
-    up_bytes = 8.0 * N + 4.0 * N + 16.0 * plan.n_obs     # pointing, t, map in
+    tile_bytes = 16.0 * N + 16.0 * plan.n_obs   # t, pixel and FP32 weights (scatter), map out
+    up_bytes = 16.0 * N + 16.0 * plan.n_obs     # pixel, FP32 weights, t out, map in
     traffic = measured_traffic(N)
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak, "traffic": traffic,
@@ -340,7 +340,7 @@ def run_ours(a):
                               "vectors, dots and scalars; rhs and residual replacement with "
                               "double-float operators)",
                       "parallelism": "replicas" if world > 1 else "single GPU",
-                      "l2": "inputs larger than L2 (pointing 8 B/sample)"},
+                      "l2": "inputs larger than L2 (pixel index and FP32 weights 12 B/sample, 12.9 GB)"},
            "solves_per_s": a.steps * world / elapsed,
            "pcg_iters_per_s": iters * world / elapsed,
            "iters_per_solve": iters / a.steps,
