@@ -188,26 +188,33 @@ __device__ __forceinline__ void twiddles(const TwiddleTab<C>& tw, int base_idx, 
 }
 
 // One decimation-in-frequency (FWD) or decimation-in-time (inverse) pass over sub-transforms of
-// size Cs with radix R.  `ms` = transform size held by this CTA, `mfull_over_cs` = M / Cs.
-// `ptab` (optional): this pass's twiddles precomputed as ptab[(j - 1) s + n1] = W_M^{j n1 M/Cs}.
-template <int R, bool FWD, int NT, typename C>
-__device__ __forceinline__ void fft_pass(C* __restrict__ sm, const TwiddleTab<C>& tw, int ms,
-                                         int cs, int mfull_over_cs, const C* __restrict__ ptab = nullptr) {
-  const int s = cs / R;
-  const int nbf = ms / R;
-  for (int q = threadIdx.x; q < nbf; q += NT) {
-    const int chunk = q / s;
-    const int n1 = q - chunk * s;
-    const int base = chunk * cs + n1;
+// size CS = R S with radix R and element stride S, over the MS points held by this CTA.
+// `mfull_over_cs` = M / CS.  `ptab` (optional): this pass's twiddles precomputed as
+// ptab[(j - 1) S + n1] = W_M^{j n1 M/CS}.
+// The padded position of element m of a butterfly is its first element's padded position plus
+// m S + (m S >> 4): the butterfly's first index and m S never carry across a 16-element padding
+// group.  S_CT > 0 makes S a compile-time constant, so the 2R shared-memory accesses use immediate
+// offsets; S_CT = 0 takes the stride s_rt at run time (one code body for several passes, for
+// element types whose butterflies are long).
+template <int R, bool FWD, int NT, int S_CT, int MS, typename C>
+__device__ __forceinline__ void fft_pass(C* __restrict__ sm, const TwiddleTab<C>& tw, int s_rt,
+                                         int mfull_over_cs, const C* __restrict__ ptab = nullptr) {
+  constexpr int NBF = MS / R;
+  const int S = S_CT > 0 ? S_CT : s_rt;
+#pragma unroll 1
+  for (int q = threadIdx.x; q < NBF; q += NT) {
+    const int chunk = q / S;
+    const int n1 = q - chunk * S;
+    C* __restrict__ b = sm + smem_pad(chunk * (R * S) + n1);
     C a[R];
 #pragma unroll
-    for (int m = 0; m < R; m++) a[m] = sm[smem_pad(base + m * s)];
+    for (int m = 0; m < R; m++) a[m] = b[m * S + ((m * S) >> 4)];
     if (FWD) {
       dft_small<R, true>(a);
-      if (s > 1 && n1 != 0) {
+      if (S > 1 && n1 != 0) {
         if (ptab) {
 #pragma unroll
-          for (int j = 1; j < R; j++) a[j] = c_mul(a[j], ptab[(j - 1) * s + n1]);
+          for (int j = 1; j < R; j++) a[j] = c_mul(a[j], ptab[(j - 1) * S + n1]);
         } else {
           C w[R];
           twiddles<R>(tw, n1 * mfull_over_cs, w);
@@ -216,10 +223,10 @@ __device__ __forceinline__ void fft_pass(C* __restrict__ sm, const TwiddleTab<C>
         }
       }
     } else {
-      if (s > 1 && n1 != 0) {
+      if (S > 1 && n1 != 0) {
         if (ptab) {
 #pragma unroll
-          for (int j = 1; j < R; j++) a[j] = c_mulc(a[j], ptab[(j - 1) * s + n1]);
+          for (int j = 1; j < R; j++) a[j] = c_mulc(a[j], ptab[(j - 1) * S + n1]);
         } else {
           C w[R];
           twiddles<R>(tw, n1 * mfull_over_cs, w);
@@ -230,13 +237,15 @@ __device__ __forceinline__ void fft_pass(C* __restrict__ sm, const TwiddleTab<C>
       dft_small<R, false>(a);
     }
 #pragma unroll
-    for (int m = 0; m < R; m++) sm[smem_pad(base + m * s)] = a[m];
+    for (int m = 0; m < R; m++) b[m * S + ((m * S) >> 4)] = a[m];
   }
 }
 
 // Transform of MS = 2^LOGMS points held by one CTA.  MFULL = size of the twiddle table's
 // transform (the whole tile, MFULL >= MS).
-template <int LOGMS, int MFULL, int NT>
+// UNROLL_PASSES: one specialised body per radix-16 pass (compile-time strides) rather than one
+// body looped over the passes.
+template <int LOGMS, int MFULL, int NT, bool UNROLL_PASSES = true>
 struct SmemFFT {
   static constexpr int MS = 1 << LOGMS;
   static constexpr int NP16 = LOGMS / 4;
@@ -267,31 +276,51 @@ struct SmemFFT {
     }
   }
 
+  // radix-16 pass p (sub-transforms of MS / 16^p points), then a barrier
+  template <int P, bool FWD, typename C>
+  __device__ static void pass16(C* sm, const TwiddleTab<C>& tw, const C* ptab) {
+    constexpr int CS = MS >> (4 * P);
+    fft_pass<16, FWD, NT, CS / 16, MS>(sm, tw, CS / 16, MFULL / CS, P > 0 ? ptab + pass_tab_offset(P) : nullptr);
+    __syncthreads();
+  }
+  template <bool FWD, typename C>
+  __device__ static void pass16_rt(C* sm, const TwiddleTab<C>& tw, const C* ptab, int p) {
+    const int cs = MS >> (4 * p);
+    fft_pass<16, FWD, NT, 0, MS>(sm, tw, cs / 16, MFULL / cs, p > 0 ? ptab + pass_tab_offset(p) : nullptr);
+    __syncthreads();
+  }
+  template <bool FWD, typename C>
+  __device__ static void pass_rem(C* sm, const TwiddleTab<C>& tw) {
+    if constexpr (REM > 0) {
+      fft_pass<(1 << REM), FWD, NT, 1, MS>(sm, tw, 1, MFULL >> REM);
+      __syncthreads();
+    }
+  }
+  static_assert(NP16 == 3, "the tiles use 2^13 or 2^14 points per CTA");
+
   template <typename C>
   __device__ static void forward(C* sm, const TwiddleTab<C>& tw, const C* ptab) {
+    if constexpr (UNROLL_PASSES) {
+      pass16<0, true>(sm, tw, ptab);
+      pass16<1, true>(sm, tw, ptab);
+      pass16<2, true>(sm, tw, ptab);
+    } else {
 #pragma unroll 1
-    for (int p = 0; p < NP16; p++) {
-      const int cs = MS >> (4 * p);
-      fft_pass<16, true, NT>(sm, tw, MS, cs, MFULL / cs, p > 0 ? ptab + pass_tab_offset(p) : nullptr);
-      __syncthreads();
+      for (int p = 0; p < NP16; p++) pass16_rt<true>(sm, tw, ptab, p);
     }
-    if constexpr (REM > 0) {
-      fft_pass<(1 << REM), true, NT>(sm, tw, MS, 1 << REM, MFULL >> REM);
-      __syncthreads();
-    }
+    pass_rem<true>(sm, tw);
   }
 
   template <typename C>
   __device__ static void inverse(C* sm, const TwiddleTab<C>& tw, const C* ptab) {
-    if constexpr (REM > 0) {
-      fft_pass<(1 << REM), false, NT>(sm, tw, MS, 1 << REM, MFULL >> REM);
-      __syncthreads();
-    }
+    pass_rem<false>(sm, tw);
+    if constexpr (UNROLL_PASSES) {
+      pass16<2, false>(sm, tw, ptab);
+      pass16<1, false>(sm, tw, ptab);
+      pass16<0, false>(sm, tw, ptab);
+    } else {
 #pragma unroll 1
-    for (int p = NP16 - 1; p >= 0; p--) {
-      const int cs = MS >> (4 * p);
-      fft_pass<16, false, NT>(sm, tw, MS, cs, MFULL / cs, p > 0 ? ptab + pass_tab_offset(p) : nullptr);
-      __syncthreads();
+      for (int p = NP16 - 1; p >= 0; p--) pass16_rt<false>(sm, tw, ptab, p);
     }
   }
 

@@ -375,7 +375,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
   using C = typename V2<T>::t;
   constexpr int LOGMS = kLogM - (CL == 2 ? 1 : 0);
   constexpr int MS = 1 << LOGMS;
-  using FFT = SmemFFT<LOGMS, kM, NT>;
+  // df64 butterflies are long: one pass body looped over the passes keeps the code in cache
+  using FFT = SmemFFT<LOGMS, kM, NT, !std::is_same<T, df>::value>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
   C* tw_sm = sm + smem_pad(MS);
