@@ -20,7 +20,9 @@ Notation (Sect. 2 and 3):
   M_BD = (P~^T diag(N^-1) P~)^-1, a 3x3 block per pixel (Sect. 3.2, block-Jacobi).
 
 Parity pins live in tests/test_oracle_pins.py.  Functions without a pin: none (the 2lvl
-construction is pinned by (I - AQ)AZ = 0 and M_2lvl A Z = Z; block CG by s = 1 == PCG).
+construction is pinned by (I - AQ)AZ = 0 and M_2lvl A Z = Z; block CG by s = 1 == PCG; enlarged
+CG by t = 1 == PCG iterate by iterate, the dense solve for t = 2..8 in both variants, the
+Galerkin condition P_k^T R_k = 0, and Orthomin == Orthodir on a well-conditioned problem).
 """
 from __future__ import annotations
 
@@ -450,6 +452,94 @@ def block_cg(plan: OraclePlan, Bm, tol: float = 1e-6, max_iter: int = 10000,
     return BlockCGResult(X=X.reshape(s, -1, 3), iters=k, converged=conv, rel_res=rel)
 
 
+def ecg_split(b, t: int) -> np.ndarray:
+    """Split of a residual into t columns that sum to it (Sect. 3.2, ECG): column i keeps the
+    unknowns of the pixels p with floor(p t / n_obs) = i (contiguous ranges of compacted pixels,
+    all three Stokes parameters of a pixel in the same subdomain) and is zero elsewhere."""
+    b = np.asarray(b, dtype=np.float64).reshape(-1, 3)
+    n = b.shape[0]
+    dom = (np.arange(n, dtype=np.int64) * t) // n
+    R = np.zeros((t, n, 3))
+    R[dom, np.arange(n)] = b
+    return R
+
+
+@dataclass
+class ECGResult:
+    x: np.ndarray           # [n_obs, 3], the sum of the t columns of X
+    iters: int
+    converged: bool
+    rel_res: float          # ||sum_i R_k^(i)|| / ||b||
+    iterates: Optional[list] = None
+    galerkin: Optional[list] = None   # max |P_k^T R_k| / ||b|| per iteration
+
+
+def ecg(plan: OraclePlan, b, t: int, tol: float = 1e-6, max_iter: int = 10000,
+        variant: str = "orthomin", rank_tol: float = 1e-12, keep_iterates: bool = False,
+        apply=None) -> ECGResult:
+    """Enlarged CG (Sect. 3.2, the ECG algorithm) for one right-hand side, x_0 = 0.
+
+    r_0 = b is split into t columns R_0 (ecg_split) with sum_i R_0^(i) = r_0; Z_1 = M R_0; then
+    P_k = Z_k (Z_k^T A Z_k)^{-1/2} (inverse Cholesky factor, dependent directions dropped by a
+    pivoted Cholesky), alpha_k = P_k^T R_{k-1}, X_k = X_{k-1} + P_k alpha_k,
+    R_k = R_{k-1} - A P_k alpha_k, stop when ||sum_i R_k^(i)|| < eps ||b||, and
+        Orthomin: Z_{k+1} = (I - P_k P_k^T A) M R_k,
+        Orthodir: Z_{k+1} = (I - P_k P_k^T A - P_{k-1} P_{k-1}^T A) M A P_k.
+    The answer is x_k = sum_i X_k^(i).  ``iters`` counts block A-applications.
+    """
+    if variant not in ("orthomin", "orthodir"):
+        raise ValueError("variant must be 'orthomin' or 'orthodir'")
+    A = apply if apply is not None else (lambda v: apply_A(plan, v))
+    b = np.asarray(b, dtype=np.float64).reshape(-1, 3)
+    n = b.shape[0]
+    bnorm = float(np.linalg.norm(b))
+    if bnorm == 0.0:
+        return ECGResult(x=np.zeros_like(b), iters=0, converged=True, rel_res=0.0)
+    R = ecg_split(b, t).reshape(t, -1)                 # rows = columns of R
+    X = np.zeros_like(R)
+    MR = lambda Rc: np.stack([precond_bd(plan, r.reshape(-1, 3)).reshape(-1) for r in Rc])
+    Ablk = lambda Zc: np.stack([A(z.reshape(-1, 3)).reshape(-1) for z in Zc])
+    Z = MR(R)
+    P_prev = AP_prev = None
+    its = [] if keep_iterates else None
+    gal = []
+    k = 0
+    rel = 1.0
+    converged = False
+    while k < max_iter and Z.shape[0] > 0:
+        AZ = Ablk(Z)
+        G = Z @ AZ.T                                   # Z^T A Z
+        G = 0.5 * (G + G.T)
+        L, piv, rank = _pivoted_cholesky(G, rank_tol)
+        if rank == 0:
+            break
+        Linv = scipy.linalg.solve_triangular(L, np.eye(rank), lower=True)
+        P = Linv @ Z[piv]                              # P_k = Z L^-T (rows)
+        AP = Linv @ AZ[piv]
+        alpha = P @ R.T                                # P_k^T R_{k-1}  (rank x t)
+        X = X + alpha.T @ P
+        R = R - alpha.T @ AP
+        k += 1
+        gal.append(float(np.max(np.abs(P @ R.T))) / bnorm)
+        rel = float(np.linalg.norm(R.sum(axis=0))) / bnorm
+        if keep_iterates:
+            its.append(X.sum(axis=0).reshape(-1, 3).copy())
+        if rel < tol:
+            converged = True
+            break
+        if variant == "orthomin":
+            W = MR(R)
+            Z = W - (W @ AP.T) @ P
+        else:
+            W = MR(AP)
+            Z = W - (W @ AP.T) @ P
+            if P_prev is not None:
+                Z = Z - (W @ AP_prev.T) @ P_prev
+        P_prev, AP_prev = P, AP
+    return ECGResult(x=X.sum(axis=0).reshape(-1, 3), iters=k, converged=converged, rel_res=rel,
+                     iterates=its, galerkin=gal)
+
+
 # ------------------------------------------------------------------------------------------
 # Algorithm 3 (Lanczos) and the two-level a-posteriori preconditioner (Sect. 3.2)
 # ------------------------------------------------------------------------------------------
@@ -525,7 +615,7 @@ def precond_2lvl(plan: OraclePlan, tl: TwoLevel, r) -> np.ndarray:
     return (t1 - t2 + tl.Z @ y).reshape(-1, 3)
 
 
-__all__ += ["precond_2lvl", "BlockCGResult", "apply_A_at_pixels"]
+__all__ += ["precond_2lvl", "BlockCGResult", "apply_A_at_pixels", "ecg_split", "ecg", "ECGResult"]
 
 
 def apply_A_at_pixels(pix, psi, block_off, band, keep, x_glob, pixels, sample_idx=None):

@@ -303,3 +303,64 @@ def test_apply_A_at_pixels_equals_apply_A():
     pixels = pl.obs_to_global[[0, 3, 7]]
     vals, scale = O.apply_A_at_pixels(pb["pix"], pb["psi"], pl.offsets, pb["band"], pl.keep, xg, pixels)
     np.testing.assert_allclose(vals, full[[0, 3, 7]], rtol=1e-12, atol=1e-12 * scale.max())
+
+
+# ---------------------------------------------------------------- enlarged CG (Sect. 3.2, ECG)
+
+def test_ecg_split_sums_to_residual():
+    b = np.random.default_rng(3).standard_normal((37, 3))
+    for t in (1, 2, 5, 37):
+        R = O.ecg_split(b, t)
+        assert R.shape == (t, 37, 3)
+        np.testing.assert_array_equal(R.sum(axis=0), b)
+        owner = np.argmax(np.any(R != 0, axis=2), axis=0)       # each pixel lives in one column
+        assert np.all(np.count_nonzero(np.any(R != 0, axis=2), axis=0) == 1)
+        assert np.all(np.diff(owner) >= 0)                       # contiguous, ordered ranges
+
+
+def test_ecg_t1_orthomin_equals_pcg_iterates():
+    # with one column the enlarged recurrence is PCG: P_1 = z / sqrt(z^T A z) etc.
+    pb = tiny_problem(seed=21)
+    pl = plan_of(pb)
+    b = O.rhs(pl, pb["d"])
+    ref = O.pcg(pl, b, tol=1e-9, max_iter=500, keep_iterates=True)
+    e = O.ecg(pl, b, 1, tol=1e-9, max_iter=500, keep_iterates=True)
+    assert e.iters == ref.iters and e.converged
+    for xe, xp in zip(e.iterates, ref.iterates):
+        assert np.linalg.norm(xe - xp) <= 1e-9 * np.linalg.norm(ref.x)
+
+
+@pytest.mark.parametrize("variant", ["orthomin", "orthodir"])
+@pytest.mark.parametrize("t", [2, 4, 8])
+def test_ecg_matches_dense_solve(variant, t):
+    pb = tiny_problem(seed=22)
+    pl = plan_of(pb)
+    b = O.rhs(pl, pb["d"])
+    xs = np.linalg.solve(O.dense_A(pl), b.reshape(-1))
+    e = O.ecg(pl, b, t, tol=1e-12, max_iter=2000, variant=variant)
+    assert e.converged
+    assert np.linalg.norm(e.x.reshape(-1) - xs) <= 1e-9 * np.linalg.norm(xs)
+    # the Galerkin condition of each step: the new residual block is orthogonal to P_k
+    assert max(e.galerkin) <= 1e-9
+
+
+def test_ecg_orthomin_and_orthodir_agree():
+    # equivalent in exact arithmetic when Z^T A Z stays well conditioned (Sect. 3.2)
+    pb = tiny_problem(seed=23)
+    pl = plan_of(pb)
+    b = O.rhs(pl, pb["d"])
+    a = O.ecg(pl, b, 4, tol=1e-8, max_iter=500, variant="orthomin", keep_iterates=True)
+    d = O.ecg(pl, b, 4, tol=1e-8, max_iter=500, variant="orthodir", keep_iterates=True)
+    assert abs(a.iters - d.iters) <= 1
+    for xa, xd in zip(a.iterates[:5], d.iterates[:5]):
+        assert np.linalg.norm(xa - xd) <= 1e-7 * np.linalg.norm(a.x)
+
+
+def test_ecg_enlarging_reduces_iterations():
+    # the enlarged Krylov space deflates the t smallest eigenvalues (Eq. RateConvECG)
+    pb = tiny_problem(seed=24, block_len=(900, 700, 400), n_pix=60, lam=40)
+    pl = plan_of(pb)
+    b = O.rhs(pl, pb["d"])
+    its = [O.ecg(pl, b, t, tol=1e-8, max_iter=2000).iters for t in (1, 2, 4, 8)]
+    assert its[3] < its[0], its
+    assert all(its[i + 1] <= its[i] + 1 for i in range(3)), its
