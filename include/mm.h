@@ -222,6 +222,33 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
 int mm_block_cg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, int block_width,
                       const mm_solve_opts* opts, mm_solve_info* info, void* stream);
 
+/* Variants of the enlarged CG recurrence (Sect. 3.2, ECG algorithm). */
+enum { MM_ECG_ORTHOMIN = 0, MM_ECG_ORTHODIR = 1 };
+
+/* Enlarged conjugate gradient for ONE right-hand side (Sect. 3.2, the ECG algorithm), x_0 = 0:
+ * r_0 = b is split into t columns R_0 that sum to it (column i keeps the compacted pixels p with
+ * floor(p t / n_obs) = i, all three Stokes parameters of a pixel together), Z_1 = M_BD R_0, and
+ *   P_k = Z_k (Z_k^T A Z_k)^{-1/2} (pivoted Cholesky factor; dependent directions dropped),
+ *   alpha_k = P_k^T R_{k-1}, X_k = X_{k-1} + P_k alpha_k, R_k = R_{k-1} - A P_k alpha_k,
+ *   stop when ||sum_i R_k^(i)|| < tol ||b||, then
+ *   MM_ECG_ORTHOMIN: Z_{k+1} = (I - P_k P_k^T A) M_BD R_k,
+ *   MM_ECG_ORTHODIR: Z_{k+1} = (I - P_k P_k^T A - P_{k-1} P_{k-1}^T A) M_BD A P_k,
+ * and x = sum_i X^(i).  Each iteration applies A to the whole t-column block at once (the batched
+ * A X the paper names as the missing piece for ECG).  The stop is confirmed by an FP64-class true
+ * residual ||b - A x||; above tol the recurrence restarts from it (at most 8 times).  The search
+ * blocks are FP32, so the recursive residual can level off near 1e-7 ||b|| (Orthodir builds its
+ * directions from A P_k and loses A-orthogonality in FP32): when ||sum_i R^(i)|| has not halved in
+ * 10 block iterations the solve also checks the true residual and restarts from it.
+ *   t            enlarging factor, 1 <= t <= 64 (t = 1 is PCG).
+ *   opts         tol, max_iter (block iterations), precision (MM_FP32: A on the search block in
+ *                FP32; MM_FP64: the plan's FP64-class operator); precond must be MM_PREC_BD.
+ * b, x: [n_obs][3] float64 device; info: HOST, one entry (iters = block iterations, batch = t).
+ * Blocks the calling thread.  MM_ENOTCONV after max_iter iterations, MM_EBREAKDOWN when the block
+ * loses all its directions or a norm is not finite; MM_EINVAL for bad arguments or a
+ * MM_TPLZ_DIRECT plan. */
+int mm_ecg_solve(mm_plan_t plan, const double* b, double* x, int t, int variant, const mm_solve_opts* opts,
+                 mm_solve_info* info, void* stream);
+
 /* Build the two-level a-posteriori deflation space of the plan (Sect. 3.2): m steps of the Lanczos
  * algorithm (Algorithm 3) on A (not M_BD A) from v_1 = b / ||b|| (x_0 = 0), storing A V_m; the
  * Ritz vectors of T_m = X Theta X^T give Z = V_m X and Z' = (A V_m) X (all m of them, as the paper

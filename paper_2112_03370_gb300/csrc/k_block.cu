@@ -195,29 +195,105 @@ cudaError_t launch_bcombine(void* out, int out_is_fp64, const int* idx_out, int 
   return cudaGetLastError();
 }
 
-// W_j = M_BD R_{idx_j} in FP32 (j < v)
-__global__ void k_bprecond(const double* __restrict__ minv, const double* __restrict__ R,
+// W_j = M_BD R_{idx_j} in FP32 (j < v; idx null = identity); R float64 [.][n][4] or float4
+template <typename TR>
+__global__ void k_bprecond(const double* __restrict__ minv, const TR* __restrict__ R,
                            const int* __restrict__ idx, int v, int64_t n, float4* __restrict__ W) {
   const int64_t tot = (int64_t)v * n;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
     const int j = (int)(e / n);
     const int64_t p = e - (int64_t)j * n;
-    const double* r = R + 4 * ((int64_t)idx[j] * n + p);
+    const int64_t o = (int64_t)(idx ? idx[j] : j) * n + p;
+    double r0, r1, r2;
+    if constexpr (sizeof(TR) == sizeof(float4)) {
+      const float4 f = R[o];
+      r0 = f.x; r1 = f.y; r2 = f.z;
+    } else {
+      const double* r = reinterpret_cast<const double*>(R) + 4 * o;
+      r0 = r[0]; r1 = r[1]; r2 = r[2];
+    }
     const double* m = minv + 6 * p;
-    const double z0 = m[0] * r[0] + m[1] * r[1] + m[2] * r[2];
-    const double z1 = m[1] * r[0] + m[3] * r[1] + m[4] * r[2];
-    const double z2 = m[2] * r[0] + m[4] * r[1] + m[5] * r[2];
+    const double z0 = m[0] * r0 + m[1] * r1 + m[2] * r2;
+    const double z1 = m[1] * r0 + m[3] * r1 + m[4] * r2;
+    const double z2 = m[2] * r0 + m[4] * r1 + m[5] * r2;
     W[e] = make_float4((float)z0, (float)z1, (float)z2, 0.f);
   }
+}
+
+static unsigned precond_grid(int64_t tot) {
+  int64_t g = (tot + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  return (unsigned)g;
 }
 
 cudaError_t launch_bprecond(const double* minv, const double* R, const int* idx, int v, int64_t n,
                             float* W, cudaStream_t s) {
   if (v <= 0) return cudaSuccess;
-  const int64_t tot = (int64_t)v * n;
-  int64_t g = (tot + 255) / 256;
-  if (g > 152 * 32) g = 152 * 32;
-  k_bprecond<<<(unsigned)g, 256, 0, s>>>(minv, R, idx, v, n, reinterpret_cast<float4*>(W));
+  k_bprecond<double><<<precond_grid((int64_t)v * n), 256, 0, s>>>(minv, R, idx, v, n, reinterpret_cast<float4*>(W));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bprecond32(const double* minv, const float* R, int v, int64_t n, float* W, cudaStream_t s) {
+  if (v <= 0) return cudaSuccess;
+  k_bprecond<float4><<<precond_grid((int64_t)v * n), 256, 0, s>>>(
+      minv, reinterpret_cast<const float4*>(R), nullptr, v, n, reinterpret_cast<float4*>(W));
+  return cudaGetLastError();
+}
+
+// Enlarged CG (Sect. 3.2, ECG): the split of one residual r [n][4] into t columns over contiguous
+// ranges of pixels (column i keeps the pixels p with floor(p t / n) = i, zero elsewhere).
+__global__ void k_bsplit(const double* __restrict__ r, int t, int64_t n, double* __restrict__ R) {
+  const int64_t tot = (int64_t)t * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n);
+    const int64_t p = e - (int64_t)i * n;
+    const bool own = (p * t) / n == i;
+    const double2* src = reinterpret_cast<const double2*>(r + 4 * p);
+    double2* dst = reinterpret_cast<double2*>(R + 4 * e);
+    dst[0] = own ? src[0] : make_double2(0.0, 0.0);
+    dst[1] = own ? make_double2(src[1].x, 0.0) : make_double2(0.0, 0.0);
+  }
+}
+
+cudaError_t launch_bsplit(const double* r4, int t, int64_t n, double* R, cudaStream_t s) {
+  if (t <= 0 || n <= 0) return cudaSuccess;
+  k_bsplit<<<precond_grid((int64_t)t * n), 256, 0, s>>>(r4, t, n, R);
+  return cudaGetLastError();
+}
+
+// s_p = sum_i X_i[p] over the t columns of a FP64 block; out (+)= s when out != null, and per-CTA
+// partials of ||s||^2 (norm of the summed residual of ECG, or of x = X 1).
+__global__ void k_bsum(const double* __restrict__ X, int t, int64_t n, double* __restrict__ out, int accumulate,
+                       double* __restrict__ norm_part) {
+  __shared__ double red[kNT];
+  double nrm = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * kNT + threadIdx.x; p < n; p += (int64_t)gridDim.x * kNT) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int i = 0; i < t; i++) {
+      const double* x = X + 4 * ((int64_t)i * n + p);
+      s0 += x[0]; s1 += x[1]; s2 += x[2];
+    }
+    if (out) {
+      double* o = out + 4 * p;
+      if (accumulate) { s0 += o[0]; s1 += o[1]; s2 += o[2]; }
+      o[0] = s0; o[1] = s1; o[2] = s2; o[3] = 0.0;
+    }
+    nrm += s0 * s0 + s1 * s1 + s2 * s2;
+  }
+  red[threadIdx.x] = nrm;
+  __syncthreads();
+  for (int sh = kNT / 2; sh > 0; sh >>= 1) {
+    if (threadIdx.x < sh) red[threadIdx.x] += red[threadIdx.x + sh];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) norm_part[blockIdx.x] = red[0];
+}
+
+cudaError_t launch_bsum(const double* X, int t, int64_t n, double* out, int accumulate, double* norm_part,
+                        int nblk, double* norm, cudaStream_t s) {
+  if (t <= 0 || t > kMaxBlk) return cudaErrorInvalidValue;
+  k_bsum<<<nblk, kNT, 0, s>>>(X, t, n, out, accumulate, norm_part);
+  k_norm_reduce<<<1, 64, 0, s>>>(norm_part, nblk, 1, norm);
   return cudaGetLastError();
 }
 

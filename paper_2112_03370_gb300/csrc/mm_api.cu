@@ -60,6 +60,9 @@ struct BlkState {
   double* T64 = nullptr;    // [s][n][4] FP64 apply output (FP64 operator path)
   double* host = nullptr;   // pinned: norms
   int* host_i = nullptr;    // pinned: rank
+  // enlarged CG: previous search block (Orthodir), accumulated solution, residual, A x
+  float *Pp = nullptr, *APp = nullptr;                               // [s][n][4] FP32
+  double *xe = nullptr, *re = nullptr, *ax = nullptr;                // [n][4] FP64
 };
 
 // Two-level deflation space and its per-solve work buffers.
@@ -111,7 +114,7 @@ void free_blk(BlkState* b) {
   dfree(b->X); dfree(b->R); dfree(b->B); dfree(b->AX); dfree(b->Z); dfree(b->AZ); dfree(b->P);
   dfree(b->AP); dfree(b->part); dfree(b->G); dfree(b->Linv); dfree(b->Cmb); dfree(b->alpha);
   dfree(b->C2); dfree(b->norms); dfree(b->norm_part); dfree(b->piv); dfree(b->rank); dfree(b->idx);
-  dfree(b->T64);
+  dfree(b->T64); dfree(b->Pp); dfree(b->APp); dfree(b->xe); dfree(b->re); dfree(b->ax);
   if (b->host) cudaFreeHost(b->host);
   if (b->host_i) cudaFreeHost(b->host_i);
   delete b;
@@ -755,6 +758,16 @@ int ensure_blk(Plan* P, int s, BlkState** out) {
     b->n = P->n_obs;
   }
   *out = b;
+  return MM_OK;
+}
+
+// enlarged-CG buffers on top of a block state of s_cap columns
+int ensure_ecg(Plan* P, BlkState* b) {
+  if (b->Pp && b->APp && b->xe && b->re && b->ax) return MM_OK;
+  const size_t n4 = (size_t)b->s_cap * P->n_obs * 4;
+  MM_TRY(dalloc(P, &b->Pp, n4)); MM_TRY(dalloc(P, &b->APp, n4));
+  MM_TRY(dalloc(P, &b->xe, (size_t)P->n_obs * 4)); MM_TRY(dalloc(P, &b->re, (size_t)P->n_obs * 4));
+  MM_TRY(dalloc(P, &b->ax, (size_t)P->n_obs * 4));
   return MM_OK;
 }
 
@@ -1570,6 +1583,165 @@ int mm_block_cg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, int 
   cudaEventDestroy(ev);
   if (worst != MM_OK) set_error("block CG did not converge for every right-hand side");
   return worst;
+}
+
+int mm_ecg_solve(mm_plan_t plan, const double* b, double* x, int t, int variant, const mm_solve_opts* opts,
+                 mm_solve_info* info, void* stream) {
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  if (!P || !b || !x || !opts || !info) return fail(MM_EINVAL, "bad argument");
+  if (t < 1 || t > kMaxBlk) return fail(MM_EINVAL, "the enlarging factor t must lie in [1, 64]");
+  if (variant != MM_ECG_ORTHOMIN && variant != MM_ECG_ORTHODIR) return fail(MM_EINVAL, "bad ECG variant");
+  if (!(opts->tol > 0.0) || opts->max_iter < 0) return fail(MM_EINVAL, "bad tol / max_iter");
+  if (opts->precond != MM_PREC_BD) return fail(MM_EINVAL, "ECG runs with the block-Jacobi preconditioner");
+  if (opts->precision != MM_FP64 && opts->precision != MM_FP32) return fail(MM_EINVAL, "bad precision");
+  if (P->algo == MM_TPLZ_DIRECT) return fail(MM_EINVAL, "ECG needs an FFT plan");
+  DeviceGuard g(P->device);
+  const auto t0 = std::chrono::steady_clock::now();
+  const bool fp32 = opts->precision == MM_FP32;
+  const double tol2 = opts->tol * opts->tol;
+  const int64_t n = P->n_obs;
+  cudaStream_t us = as_stream(stream);
+  cudaStream_t s = P->stream;
+  BlkState* B = nullptr;
+  MM_TRY(ensure_blk(P, t, &B));
+  MM_TRY(ensure_ecg(P, B));
+  cudaEvent_t ev;
+  MM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  MM_CUDA(cudaEventRecord(ev, us));
+  MM_CUDA(cudaStreamWaitEvent(s, ev, 0));
+  int64_t n_kernels = 0;
+  int n_apply = 0, n_apply64 = 0;
+  auto read_host = [&](const double* dev, int v) -> int {
+    MM_CUDA(cudaMemcpyAsync(B->host, dev, v * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MM_CUDA(cudaStreamSynchronize(s));
+    return MM_OK;
+  };
+  // b (column 0 of B->B), ||b||^2, x = 0, r = b
+  MM_CUDA(launch_pack3to4(b, n, 1, B->B, s));
+  MM_CUDA(launch_bsum(B->B, 1, n, B->re, 0, B->norm_part, kBlkCtas, B->norms, s));
+  MM_CUDA(cudaMemsetAsync(B->xe, 0, (size_t)n * 4 * sizeof(double), s));
+  n_kernels += 3;
+  MM_TRY(read_host(B->norms, 1));
+  const double bn2 = B->host[0];
+  double rel2 = bn2 > 0.0 ? 1.0 : 0.0, tn2 = bn2;
+  int it = 0, restarts = 0, status = MM_OK;
+  bool converged = !(bn2 > 0.0);
+  while (!converged) {
+    // R_0 = split of r, X = 0, Z_1 = M R_0
+    MM_CUDA(launch_bsplit(B->re, t, n, B->R, s));
+    MM_CUDA(cudaMemsetAsync(B->X, 0, (size_t)t * n * 4 * sizeof(double), s));
+    MM_CUDA(launch_bprecond(P->minv, B->R, nullptr, t, n, B->Z, s));
+    n_kernels += 2;
+    int tz = t, rprev = 0;
+    bool inner_conv = false, stalled = false;
+    // The search blocks are FP32: a recurrence whose directions do not come from the residual
+    // (Orthodir) loses A-orthogonality and its recursive residual levels off near 1e-7 ||b||.
+    // When ||sum R|| has not halved in kStall block iterations, restart from the true residual.
+    constexpr int kStall = 10;
+    double best = INFINITY;
+    int since_best = 0;
+    while (it < opts->max_iter) {
+      MM_TRY(blk_apply(P, B, tz, fp32, s));                                   // AZ = A Z
+      n_kernels += fp32 ? 2 : 3;
+      n_apply += 1;
+      MM_CUDA(launch_bgram(B->Z, tz, nullptr, B->AZ, 0, tz, nullptr, n, B->part, kBlkCtas, B->G, s));
+      MM_CUDA(launch_bchol(B->G, tz, 1e-10, B->Linv, B->piv, B->rank, s));
+      MM_CUDA(cudaMemcpyAsync(B->host_i, B->rank, sizeof(int), cudaMemcpyDeviceToHost, s));
+      MM_CUDA(cudaStreamSynchronize(s));
+      const int r = B->host_i[0];
+      n_kernels += 3;
+      if (r == 0) {
+        status = MM_EBREAKDOWN;
+        break;
+      }
+      // P_k = Z (Z^T A Z)^{-1/2} and A P_k; alpha = P_k^T R; X += P alpha; R -= A P alpha
+      MM_CUDA(launch_linv_coef(B->Linv, B->piv, B->rank, tz, B->Cmb, s));
+      MM_CUDA(launch_bcombine(B->P, 0, nullptr, r, B->Z, tz, B->Cmb, tz, 1.0, 0, n, nullptr, kBlkCtas, nullptr, s));
+      MM_CUDA(launch_bcombine(B->AP, 0, nullptr, r, B->AZ, tz, B->Cmb, tz, 1.0, 0, n, nullptr, kBlkCtas, nullptr, s));
+      MM_CUDA(launch_bgram(B->P, r, nullptr, B->R, 1, t, nullptr, n, B->part, kBlkCtas, B->alpha, s));
+      MM_CUDA(launch_bcombine(B->X, 1, nullptr, t, B->P, r, B->alpha, t, 1.0, 1, n, nullptr, kBlkCtas, nullptr, s));
+      MM_CUDA(launch_bcombine(B->R, 1, nullptr, t, B->AP, r, B->alpha, t, -1.0, 1, n, nullptr, kBlkCtas, nullptr, s));
+      MM_CUDA(launch_bsum(B->R, t, n, nullptr, 0, B->norm_part, kBlkCtas, B->norms, s));   // ||sum_i R_i||^2
+      n_kernels += 10;
+      it += 1;
+      MM_TRY(read_host(B->norms, 1));
+      rel2 = B->host[0] / bn2;
+      if (!std::isfinite(rel2)) {
+        status = MM_EBREAKDOWN;
+        break;
+      }
+      if (rel2 < tol2) {
+        inner_conv = true;
+        break;
+      }
+      if (rel2 < 0.25 * best) {
+        best = rel2;
+        since_best = 0;
+      } else if (++since_best >= kStall) {
+        stalled = true;
+        break;
+      }
+      if (variant == MM_ECG_ORTHOMIN) {
+        // Z_{k+1} = (I - P_k P_k^T A) M R_k
+        MM_CUDA(launch_bprecond(P->minv, B->R, nullptr, t, n, B->Z, s));
+        tz = t;
+        MM_CUDA(launch_bgram(B->AP, r, nullptr, B->Z, 0, tz, nullptr, n, B->part, kBlkCtas, B->C2, s));
+        MM_CUDA(launch_bcombine(B->Z, 0, nullptr, tz, B->P, r, B->C2, tz, -1.0, 1, n, nullptr, kBlkCtas, nullptr, s));
+        n_kernels += 4;
+      } else {
+        // Z_{k+1} = (I - P_k P_k^T A - P_{k-1} P_{k-1}^T A) M A P_k
+        MM_CUDA(launch_bprecond32(P->minv, B->AP, r, n, B->Z, s));
+        tz = r;
+        MM_CUDA(launch_bgram(B->AP, r, nullptr, B->Z, 0, tz, nullptr, n, B->part, kBlkCtas, B->C2, s));
+        MM_CUDA(launch_bcombine(B->Z, 0, nullptr, tz, B->P, r, B->C2, tz, -1.0, 1, n, nullptr, kBlkCtas, nullptr, s));
+        n_kernels += 4;
+        if (rprev > 0) {
+          MM_CUDA(launch_bgram(B->APp, rprev, nullptr, B->Z, 0, tz, nullptr, n, B->part, kBlkCtas, B->G, s));
+          MM_CUDA(launch_bcombine(B->Z, 0, nullptr, tz, B->Pp, rprev, B->G, tz, -1.0, 1, n, nullptr, kBlkCtas,
+                                  nullptr, s));
+          n_kernels += 3;
+        }
+        std::swap(B->P, B->Pp);
+        std::swap(B->AP, B->APp);
+        rprev = r;
+      }
+    }
+    // x += X 1, then the FP64-class true residual r = b - A x
+    MM_CUDA(launch_bsum(B->X, t, n, B->xe, 1, B->norm_part, kBlkCtas, B->norms, s));
+    MM_CUDA(cudaMemsetAsync(B->ax, 0, (size_t)n * 4 * sizeof(double), s));
+    MM_TRY(apply64_internal(P, B->xe, B->ax, 1, s));
+    MM_CUDA(launch_bresid(B->B, B->ax, 1, n, B->re, B->norm_part, kBlkCtas, B->norms, s));
+    n_kernels += 5;
+    n_apply64 += 1;
+    MM_TRY(read_host(B->norms, 1));
+    tn2 = B->host[0];
+    if (tn2 < tol2 * bn2) {
+      converged = true;
+      break;
+    }
+    if (status != MM_OK || !(inner_conv || stalled) || it >= opts->max_iter || restarts >= 8) break;
+    restarts += 1;   // restart from the true residual
+  }
+  if (status == MM_OK && !converged) status = MM_ENOTCONV;
+  MM_CUDA(launch_unpack4to3(B->xe, n, 1, x, s));
+  n_kernels += 1;
+  MM_CUDA(cudaEventRecord(ev, s));
+  MM_CUDA(cudaStreamWaitEvent(us, ev, 0));
+  MM_CUDA(cudaStreamSynchronize(s));
+  cudaEventDestroy(ev);
+  std::memset(info, 0, sizeof(*info));
+  info->status = status;
+  info->iters = it;
+  info->rel_res = bn2 > 0 ? std::sqrt(rel2) : 0.0;
+  info->true_rel_res = bn2 > 0 ? std::sqrt(tn2 / bn2) : 0.0;
+  info->t_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  info->n_true_res = restarts + 1;
+  info->batch = t;
+  info->n_apply32 = fp32 ? n_apply : 0;
+  info->n_apply64 = (fp32 ? 0 : n_apply) + n_apply64;
+  info->n_kernels = n_kernels;
+  if (status != MM_OK) set_error("ECG did not converge");
+  return status;
 }
 
 int mm_deflation_build(mm_plan_t plan, const double* b, int m, int precision, void* stream) {

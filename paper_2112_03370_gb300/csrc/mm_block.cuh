@@ -20,6 +20,13 @@ cudaError_t launch_bcombine(void* out, int out_is_fp64, const int* idx_out, int 
 // W_j = M_BD R_{idx[j]} (float32 out)
 cudaError_t launch_bprecond(const double* minv, const double* R, const int* idx, int v, int64_t n,
                             float* W, cudaStream_t s);
+// W_j = M_BD R_j (float32 block in and out, j < v)
+cudaError_t launch_bprecond32(const double* minv, const float* R, int v, int64_t n, float* W, cudaStream_t s);
+// enlarged CG: split of r (FP64 [n][4]) into t columns over contiguous pixel ranges (FP64 [t][n][4])
+cudaError_t launch_bsplit(const double* r4, int t, int64_t n, double* R, cudaStream_t s);
+// s = sum of the t columns of X; out (+)= s when out != null; *norm = ||s||^2
+cudaError_t launch_bsum(const double* X, int t, int64_t n, double* out, int accumulate, double* norm_part,
+                        int nblk, double* norm, cudaStream_t s);
 // pivoted Cholesky of the t x t Gram matrix and the inverse of its factor (one CTA)
 cudaError_t launch_bchol(const double* G, int t, double rank_tol, double* Linv, int* piv, int* rank,
                          cudaStream_t s);

@@ -20,13 +20,14 @@ MM_OK, MM_EINVAL, MM_ENOMEM, MM_ENOTSPD, MM_EBREAKDOWN, MM_ENOTCONV, MM_ETIMEOUT
 MM_FP64, MM_FP32, MM_DF64, MM_FP32_DF64 = 0, 1, 2, 3
 MM_TPLZ_AUTO, MM_TPLZ_FFT, MM_TPLZ_DIRECT = 0, 1, 3
 MM_PREC_BD, MM_PREC_2LVL_POST = 0, 1
+MM_ECG_ORTHOMIN, MM_ECG_ORTHODIR = 0, 1
 STATUS_NAMES = {0: "MM_OK", 1: "MM_EINVAL", 2: "MM_ENOMEM", 3: "MM_ENOTSPD", 4: "MM_EBREAKDOWN",
                 5: "MM_ENOTCONV", 6: "MM_ETIMEOUT", 7: "MM_EBUSY", 8: "MM_ECUDA"}
 
 # the exported entry points of include/mm.h
 EXPORTS = ("mm_plan", "mm_plan_query", "mm_plan_destroy", "mm_apply_P", "mm_apply_Pt",
            "mm_apply_Ninv", "mm_rhs", "mm_apply_A", "mm_precond", "mm_pcg_solve", "mm_last_error",
-           "mm_apply_A_noalloc", "mm_block_cg_solve", "mm_deflation_build", "mm_deflation_get",
+           "mm_apply_A_noalloc", "mm_block_cg_solve", "mm_ecg_solve", "mm_deflation_build", "mm_deflation_get",
            "mm_deflation_apply", "mm_server_create", "mm_submit", "mm_poll", "mm_wait",
            "mm_server_destroy")
 
@@ -83,6 +84,8 @@ def _load():
                                  ctypes.POINTER(SolveInfo), vp]
     lib.mm_block_cg_solve.argtypes = [vp, vp, vp, i32, i32, ctypes.POINTER(SolveOpts),
                                       ctypes.POINTER(SolveInfo), vp]
+    lib.mm_ecg_solve.argtypes = [vp, vp, vp, i32, i32, ctypes.POINTER(SolveOpts),
+                                 ctypes.POINTER(SolveInfo), vp]
     lib.mm_deflation_build.argtypes = [vp, vp, i32, i32, vp]
     lib.mm_deflation_get.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp, vp, vp]
     lib.mm_deflation_apply.argtypes = [vp, vp, vp, i32, vp]
@@ -279,6 +282,20 @@ def mm_block_cg_solve(plan: Plan, b: torch.Tensor, x: torch.Tensor, block_width:
     if raise_on_error and code != MM_OK:
         raise MMError(code, mm_last_error())
     return list(infos)
+
+
+def mm_ecg_solve(plan: Plan, b: torch.Tensor, x: torch.Tensor, t: int, variant: int = MM_ECG_ORTHOMIN,
+                 tol: float = 1e-6, max_iter: int = 10000, precision: int = MM_FP32, stream=None,
+                 raise_on_error=True):
+    """Enlarged CG with enlarging factor t for one right-hand side (b, x: [n_obs, 3])."""
+    _dev(b, torch.float64, "b"); _dev(x, torch.float64, "x")
+    opts = SolveOpts(tol=tol, max_iter=max_iter, precond=MM_PREC_BD, precision=precision)
+    info = SolveInfo()
+    code = _lib.mm_ecg_solve(ctypes.c_void_p(plan.handle), _ptr(b), _ptr(x), t, variant,
+                             ctypes.byref(opts), ctypes.byref(info), _stream_ptr(stream))
+    if raise_on_error and code != MM_OK:
+        raise MMError(code, mm_last_error())
+    return info
 
 
 def mm_deflation_build(plan: Plan, b: torch.Tensor, m: int, precision: int = MM_FP64, stream=None):
