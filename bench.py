@@ -56,9 +56,10 @@ def args_parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-dets", type=int, default=16)
     p.add_argument("--workload", default="ground",
-                   choices=["ground", "batched", "satellite", "serving"])
+                   choices=["ground", "batched", "satellite", "serving", "ecg"])
     p.add_argument("--nrhs", type=int, default=64, help="batched: noise realisations")
     p.add_argument("--widths", default="8,16,32,64", help="batched: block widths")
+    p.add_argument("--enlarge", default="1,4,16,64", help="ecg: enlarging factors t")
     p.add_argument("--requests", type=int, default=40, help="serving: requests")
     p.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
     return p.parse_args()
@@ -469,6 +470,46 @@ def run_batched(a):
         "vs_fp32_pcg": best["solves_per_s"] / (2 / dt32)}), flush=True)
 
 
+def run_ecg(a):
+    """Enlarged CG (Orthomin and Orthodir) for one right-hand side of the 128-detector ground cut,
+    against the mixed-precision PCG on the same plan: iterations, A column-applications and
+    time to solution per enlarging factor t."""
+    import torch
+    import synth
+    import paper_2112_03370_gb300.mm as mm
+    dev = torch.device("cuda")
+    cfg = synth.batched_config()
+    prob = synth.make_ground_problem(cfg, device=dev, n_real=1)
+    plan = mm.mm_plan(prob.n_det, prob.n_int, prob.block_len.tolist(), prob.n_pix, prob.pix, prob.psi,
+                      prob.lam, prob.band.to(dev), precision=mm.MM_FP32_DF64)
+    N = plan.n_samples
+    b = torch.empty(plan.n_obs, 3, dtype=torch.float64, device=dev)
+    mm.mm_rhs(plan, prob.d, b)
+    x = torch.empty_like(b)
+    mm.mm_pcg_solve(plan, b, x, tol=cfg.tol, precision=mm.MM_FP32)
+    ipcg, tpcg = _timed(lambda: mm.mm_pcg_solve(plan, b, x, tol=cfg.tol, precision=mm.MM_FP32)[0])
+    res = {}
+    for variant, vname in ((mm.MM_ECG_ORTHOMIN, "orthomin"), (mm.MM_ECG_ORTHODIR, "orthodir")):
+        for t in [int(v) for v in a.enlarge.split(",")]:
+            mm.mm_ecg_solve(plan, b, x, t, variant=variant, tol=cfg.tol, raise_on_error=False)
+            inf, dt = _timed(lambda: mm.mm_ecg_solve(plan, b, x, t, variant=variant, tol=cfg.tol,
+                                                     raise_on_error=False))
+            res[f"{vname}_t{t}"] = {"iters": inf.iters, "status": inf.status, "s": dt,
+                                    "true_rel_res": inf.true_rel_res, "restarts": inf.n_true_res - 1,
+                                    "column_applies": inf.iters * t,
+                                    "samples_per_s_through_A": N * t * inf.iters / dt,
+                                    "vs_pcg_time": tpcg / dt}
+    print(json.dumps({
+        "workload": "ecg", "metric": "time to solution, one right-hand side (ECG vs PCG)",
+        "value": min(r["s"] for r in res.values()), "unit": "s", "higher_is_better": False,
+        "config": {"workload": f"ground cut: {prob.n_det} det x {cfg.n_samp} samples, "
+                               f"{cfg.side}^2 IQU, lambda {cfg.lam}, one realisation",
+                   "n_samples": N, "n_obs": plan.n_obs, "tol": cfg.tol,
+                   "precision": "FP32 search blocks and operator, FP64 X/R and t x t, df64 true residual"},
+        "pcg": {"iters": ipcg.iters, "s": tpcg, "samples_per_s_through_A": N * ipcg.iters / tpcg},
+        "ecg": res}), flush=True)
+
+
 def run_satellite(a):
     """Satellite-like full sky: BD vs two-level (16 Ritz vectors) mixed-precision solves."""
     import torch
@@ -565,6 +606,8 @@ def main():
         run_satellite(a)
     elif a.workload == "serving":
         run_serving(a)
+    elif a.workload == "ecg":
+        run_ecg(a)
     else:
         run_ours(a)
 

@@ -237,8 +237,9 @@ enum { MM_ECG_ORTHOMIN = 0, MM_ECG_ORTHODIR = 1 };
  * A X the paper names as the missing piece for ECG).  The stop is confirmed by an FP64-class true
  * residual ||b - A x||; above tol the recurrence restarts from it (at most 8 times).  The search
  * blocks are FP32, so the recursive residual can level off near 1e-7 ||b|| (Orthodir builds its
- * directions from A P_k and loses A-orthogonality in FP32): when ||sum_i R^(i)|| has not halved in
- * 10 block iterations the solve also checks the true residual and restarts from it.
+ * directions from A P_k and loses A-orthogonality in FP32): once below 1e-6 ||b||, a residual
+ * ||sum_i R^(i)|| that has not halved in 10 block iterations also makes the solve check the true
+ * residual and restart from it.
  *   t            enlarging factor, 1 <= t <= 64 (t = 1 is PCG).
  *   opts         tol, max_iter (block iterations), precision (MM_FP32: A on the search block in
  *                FP32; MM_FP64: the plan's FP64-class operator); precond must be MM_PREC_BD.

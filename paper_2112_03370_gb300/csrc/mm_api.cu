@@ -1636,8 +1636,11 @@ int mm_ecg_solve(mm_plan_t plan, const double* b, double* x, int t, int variant,
     bool inner_conv = false, stalled = false;
     // The search blocks are FP32: a recurrence whose directions do not come from the residual
     // (Orthodir) loses A-orthogonality and its recursive residual levels off near 1e-7 ||b||.
-    // When ||sum R|| has not halved in kStall block iterations, restart from the true residual.
+    // Once below 1e-6 ||b|| (near that floor; slow progress above it is ordinary CG behaviour on
+    // ill-conditioned systems), ||sum R|| that has not halved in kStall block iterations
+    // restarts the recurrence from the true residual.
     constexpr int kStall = 10;
+    constexpr double kStallZone2 = 1e-12;
     double best = INFINITY;
     int since_best = 0;
     while (it < opts->max_iter) {
@@ -1677,7 +1680,7 @@ int mm_ecg_solve(mm_plan_t plan, const double* b, double* x, int t, int variant,
       if (rel2 < 0.25 * best) {
         best = rel2;
         since_best = 0;
-      } else if (++since_best >= kStall) {
+      } else if (best < kStallZone2 && ++since_best >= kStall) {
         stalled = true;
         break;
       }
