@@ -22,7 +22,9 @@ Notation (Sect. 2 and 3):
 Parity pins live in tests/test_oracle_pins.py.  Functions without a pin: none (the 2lvl
 construction is pinned by (I - AQ)AZ = 0 and M_2lvl A Z = Z; block CG by s = 1 == PCG; enlarged
 CG by t = 1 == PCG iterate by iterate, the dense solve for t = 2..8 in both variants, the
-Galerkin condition P_k^T R_k = 0, and Orthomin == Orthodir on a well-conditioned problem).
+Galerkin condition P_k^T R_k = 0, and Orthomin == Orthodir on a well-conditioned problem; the
+a-priori deflation space by hit counts taken sample by sample, the partition of unity, and the
+same deflation identities as the a-posteriori one).
 """
 from __future__ import annotations
 
@@ -606,6 +608,30 @@ def two_level_from_lanczos(plan: OraclePlan, b, m: int, rcond: float = 1e-12,
     return TwoLevel(Z=Z, Zp=Zp, E=E, Einv=Einv, theta=theta)
 
 
+def two_level_apriori(plan: OraclePlan, n_int: int, rcond: float = 1e-12, apply=None) -> TwoLevel:
+    """A-priori deflation space (Sect. 3.2, 2lvl a priori construction): one column per time
+    interval j (blocks are detector-major, block b belongs to interval b mod n_int).  With s_p^j the
+    number of kept samples of pixel p in interval j and s_p their sum, the column's total-intensity
+    entry at pixel p is s_p^j / s_p and its Q and U entries are 0, so the I rows of Z are a partition
+    of unity.  Z' = A Z, E = Z^T Z', E^-1 its SVD pseudo-inverse; theta is left at 0 (no Ritz
+    values)."""
+    A = apply if apply is not None else (lambda v: apply_A(plan, v))
+    n = plan.n_obs
+    s_pj = np.zeros((n, n_int))
+    for b in range(plan.block_len.size):
+        lp = plan.lpix[plan.offsets[b]:plan.offsets[b + 1]]
+        lp = lp[lp >= 0]
+        s_pj[:, b % n_int] += np.bincount(lp, minlength=n)
+    s_p = s_pj.sum(axis=1)
+    Z = np.zeros((n, 3, n_int))
+    Z[:, 0, :] = s_pj / s_p[:, None]
+    Z = Z.reshape(3 * n, n_int)
+    Zp = np.stack([A(Z[:, j].reshape(-1, 3)).reshape(-1) for j in range(n_int)], axis=1)
+    E = Z.T @ Zp
+    Einv = np.linalg.pinv(E, rcond=rcond)
+    return TwoLevel(Z=Z, Zp=Zp, E=E, Einv=Einv, theta=np.zeros(n_int))
+
+
 def precond_2lvl(plan: OraclePlan, tl: TwoLevel, r) -> np.ndarray:
     """Eq. 2lvlDef0: M_2lvl r = M_BD r - M_BD Z' E^-1 Z^T r + Z E^-1 Z^T r (right to left)."""
     r = np.asarray(r, dtype=np.float64).reshape(-1)
@@ -615,7 +641,8 @@ def precond_2lvl(plan: OraclePlan, tl: TwoLevel, r) -> np.ndarray:
     return (t1 - t2 + tl.Z @ y).reshape(-1, 3)
 
 
-__all__ += ["precond_2lvl", "BlockCGResult", "apply_A_at_pixels", "ecg_split", "ecg", "ECGResult"]
+__all__ += ["precond_2lvl", "BlockCGResult", "apply_A_at_pixels", "ecg_split", "ecg", "ECGResult",
+            "two_level_apriori"]
 
 
 def apply_A_at_pixels(pix, psi, block_off, band, keep, x_glob, pixels, sample_idx=None):

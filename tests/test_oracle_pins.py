@@ -364,3 +364,43 @@ def test_ecg_enlarging_reduces_iterations():
     its = [O.ecg(pl, b, t, tol=1e-8, max_iter=2000).iters for t in (1, 2, 4, 8)]
     assert its[3] < its[0], its
     assert all(its[i + 1] <= its[i] + 1 for i in range(3)), its
+
+
+# ---------------------------------------------------------------- 2lvl a priori (Sect. 3.2)
+
+def test_two_level_apriori_columns_by_counting():
+    # three blocks of one detector = three time intervals; count the kept hits by hand
+    pb = tiny_problem(seed=31)
+    pl = plan_of(pb)
+    tl = O.two_level_apriori(pl, 3)
+    n = pl.n_obs
+    Z = tl.Z.reshape(n, 3, 3)
+    counts = np.zeros((n, 3))
+    for b in range(3):
+        for t in range(pl.offsets[b], pl.offsets[b + 1]):
+            if pl.lpix[t] >= 0:
+                counts[pl.lpix[t], b] += 1
+    np.testing.assert_allclose(Z[:, 0, :], counts / counts.sum(axis=1, keepdims=True), rtol=0, atol=1e-15)
+    np.testing.assert_array_equal(Z[:, 1:, :], 0.0)                 # Q and U rows are zero
+    np.testing.assert_allclose(Z[:, 0, :].sum(axis=1), 1.0, atol=1e-14)   # partition of unity
+    one = O.two_level_apriori(pl, 1)                                 # a single interval: Z = 1 on I
+    np.testing.assert_allclose(one.Z.reshape(n, 3)[:, 0], 1.0, atol=1e-15)
+
+
+def test_two_level_apriori_deflation_identities_and_iterations():
+    pb = tiny_problem(seed=32, n_pix=60, lam=30)
+    pl = plan_of(pb)
+    tl = O.two_level_apriori(pl, 3)
+    A = O.dense_A(pl)
+    Z = tl.Z
+    Q = Z @ tl.Einv @ Z.T
+    lhs = (np.eye(A.shape[0]) - A @ Q) @ A @ Z
+    assert np.abs(lhs).max() <= 1e-8 * np.abs(A @ Z).max()
+    for j in range(Z.shape[1]):
+        out = O.precond_2lvl(pl, tl, (A @ Z[:, j]).reshape(-1, 3)).reshape(-1)
+        np.testing.assert_allclose(out, Z[:, j], atol=1e-8 * np.abs(Z[:, j]).max())
+    b = O.rhs(pl, pb["d"])
+    bd = O.pcg(pl, b, tol=1e-8)
+    two = O.pcg(pl, b, tol=1e-8, precond=lambda r: O.precond_2lvl(pl, tl, r))
+    assert two.converged and two.iters <= bd.iters + 1
+    assert np.linalg.norm(two.x - bd.x) <= 1e-6 * np.linalg.norm(bd.x)
