@@ -259,12 +259,23 @@ int mm_ecg_solve(mm_plan_t plan, const double* b, double* x, int t, int variant,
  * replace any previous space.  Synchronous.  MM_EBREAKDOWN if b = 0. */
 int mm_deflation_build(mm_plan_t plan, const double* b, int m, int precision, void* stream);
 
+/* Build the two-level a-priori deflation space of the plan (Sect. 3.2, 2lvl a priori construction):
+ * one column per stationary interval j (n_int of the plan; block b = det * n_int + j), whose total
+ * intensity entry at pixel p is s_p^j / s_p, the fraction of p's kept samples that fall in interval
+ * j (Q and U entries 0; the I rows are a partition of unity); then Z' = A Z, E = Z^T Z' and its
+ * pseudo-inverse, as for mm_deflation_build, which it replaces.  precision selects the FP32 or
+ * FP64-class operator for the n_int A-applications.  theta is left at 0.  Synchronous.
+ * MM_EINVAL when n_int > 64.  The same MM_PREC_2LVL_POST solves and mm_deflation_apply use it. */
+int mm_deflation_build_apriori(mm_plan_t plan, int precision, void* stream);
+
 /* The plan's deflation space: *k columns; Z [k][n_obs][3] float64 device (may be NULL) and the
- * Ritz values theta [k] (HOST, may be NULL).  *k = 0 when none was built. */
+ * Ritz values theta [k] (HOST, may be NULL; 0 for an a-priori space).  *k = 0 when none was
+ * built. */
 int mm_deflation_get(mm_plan_t plan, int* k, double* Z, double* theta, void* stream);
 
 /* z = M_2lvl r = M_BD (r - Z' E^-1 Z^T r) + Z E^-1 Z^T r (Eq. 2lvlDef0, applied right to left)
- * for nrhs vectors [nrhs][n_obs][3]; needs mm_deflation_build.  Asynchronous on stream. */
+ * for nrhs vectors [nrhs][n_obs][3]; needs mm_deflation_build or mm_deflation_build_apriori.
+ * Asynchronous on stream. */
 int mm_deflation_apply(mm_plan_t plan, const double* r, double* z, int nrhs, void* stream);
 
 /*

@@ -251,6 +251,44 @@ __global__ void k_defl_apply(DeflWork d, CgWork w) {
   }
 }
 
+// 2lvl a-priori space (Sect. 3.2): hits[j][p] += 1 for every kept sample of pixel p in time interval
+// j = block mod n_int (blocks are detector-major); one grid row per block
+__global__ void k_interval_hits(const int32_t* __restrict__ lpix, const int64_t* __restrict__ block_off,
+                                int n_int, int64_t n, int32_t* __restrict__ hits) {
+  const int b = blockIdx.y;
+  const int64_t lo = block_off[b], hi = block_off[b + 1];
+  int32_t* h = hits + (int64_t)(b % n_int) * n;
+  for (int64_t i = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p = __ldg(lpix + i);
+    if (p >= 0) atomicAdd(h + p, 1);
+  }
+}
+
+// Z_j[p] = (s_p^j / s_p, 0, 0, 0): the fraction of pixel p's kept hits in interval j (I rows only)
+__global__ void k_apriori_z(const int32_t* __restrict__ hits, int k, int64_t n, float4* __restrict__ Z) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    int64_t tot = 0;
+    for (int j = 0; j < k; j++) tot += hits[(int64_t)j * n + p];
+    const double inv = tot > 0 ? 1.0 / (double)tot : 0.0;
+    for (int j = 0; j < k; j++) Z[(int64_t)j * n + p] = make_float4((float)(hits[(int64_t)j * n + p] * inv), 0.f, 0.f, 0.f);
+  }
+}
+
+cudaError_t launch_apriori_z(const int32_t* lpix, const int64_t* block_off, int n_blocks, int n_int, int64_t n,
+                             int32_t* hits, float* Z, cudaStream_t s) {
+  if (n_blocks <= 0 || n <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(hits, 0, (size_t)n_int * n * sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
+  for (int b0 = 0; b0 < n_blocks; b0 += 65535) {   // gridDim.y limit
+    const int nb = n_blocks - b0 < 65535 ? n_blocks - b0 : 65535;
+    k_interval_hits<<<dim3(32, nb), 256, 0, s>>>(lpix, block_off + b0, n_int, n, hits);
+  }
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  k_apriori_z<<<(unsigned)g, 256, 0, s>>>(hits, n_int, n, reinterpret_cast<float4*>(Z));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_defl_step(const DeflWork& d, const CgWork& w, cudaStream_t s) {
   dim3 grid(w.n_blocks, w.nrhs);
   k_defl_dots<<<grid, kNT, 0, s>>>(d, w);

@@ -484,10 +484,15 @@ __global__ void k_cg_replace(CgWork w) {
     CgScalars& s = w.scal[col];
     s.n_true += 1;
     s.since_rep = 0;
+    // Keep the search direction (reliable update) while the true residual is close to the
+    // recursive one; when it is more than twice as large in norm (the recursion has run below the
+    // FP32 operator's accuracy) p was built for a residual that no longer exists, and CG restarts
+    // from p = z.
+    const bool restart = t[0] > 4.0 * s.rr;
     s.rr = t[0];
     s.rr_true = t[0];
     s.rz = t[1];
-    s.beta = t[1] / s.rz_prev;
+    s.beta = restart ? 0.0 : t[1] / s.rz_prev;
     s.paused = 0;
     if (t[0] < w.tol2 * s.bnorm2) {
       s.done = 1;

@@ -46,6 +46,7 @@ struct CgState {
   cudaGraphExec_t exec = nullptr;
   int g_nrhs = -1, g_fp32 = -1, g_chunk = -1, g_maxit = -1, g_prec = -1;
   double g_tol2 = -1.0;
+  uint64_t g_buf_gen = ~0ull;       // plan buffer generation the graph's pointers belong to
 };
 
 // Block-CG workspace, grown on demand and kept with the plan.
@@ -479,6 +480,7 @@ int ensure_maps(Plan* P, int nrhs, bool need32) {
 
 int ensure_td(Plan* P) {
   if (P->td_cap >= (size_t)P->N && P->td_a && P->td_b) return MM_OK;
+  P->buf_gen++;
   dfree(P->td_a);
   dfree(P->td_b);
   P->td_cap = 0;
@@ -518,6 +520,7 @@ int ensure_df(Plan* P, int nrhs) {
   if (!P->df64) return MM_OK;
   const size_t t_elems = (size_t)df_cols(P, nrhs) * (size_t)df_stride(P);
   if (P->tdf_cap < t_elems) {
+    P->buf_gen++;
     dfree(P->tdf);
     P->tdf_cap = 0;
     MM_TRY(dalloc(P, &P->tdf, t_elems));
@@ -525,6 +528,7 @@ int ensure_df(Plan* P, int nrhs) {
   }
   const size_t m_elems = (size_t)df_cols(P, nrhs) * (size_t)P->n_obs * 2;
   if (P->mapdf_cap < m_elems) {
+    P->buf_gen++;
     dfree(P->mapdf);
     P->mapdf_cap = 0;
     MM_TRY(dalloc(P, &P->mapdf, m_elems));
@@ -602,6 +606,7 @@ int ensure_t32(Plan* P, int nrhs) {
   if (t_elems * sizeof(float) > kSplitTBytes || P->t32_cap >= t_elems) return MM_OK;
   dfree(P->t32);
   P->t32_cap = 0;
+  P->buf_gen++;
   MM_TRY(dalloc(P, &P->t32, t_elems));
   P->t32_cap = t_elems;
   return MM_OK;
@@ -705,6 +710,7 @@ int enqueue_iteration(Plan* P, const CgWork& w, int nrhs, bool fp32, cudaStream_
 // per-solve buffers of the deflated preconditioner for nrhs columns
 int ensure_defl_work(Plan* P, DeflState* d, int nrhs, int n_blocks, DeflWork* out) {
   if (d->nrhs_cap < nrhs) {
+    P->buf_gen++;
     dfree(d->y); dfree(d->part); dfree(d->part2); dfree(d->counters); dfree(d->counters2);
     d->nrhs_cap = 0;
     MM_TRY(dalloc(P, &d->y, (size_t)nrhs * kMaxDefl));
@@ -1245,8 +1251,11 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
   if (dwp) MM_CUDA(launch_defl_step(dw, w, s));
 
   // graph of `chunk` iterations, cached on the plan
+  // A captured graph holds raw pointers: it is replayed only while none of the plan buffers it
+  // reads (t, df64 and direct-path scratch, deflation space and its work arrays) was reallocated.
   if (opts->profile == 0 && (!c->exec || c->g_nrhs != nrhs || c->g_fp32 != (int)fp32 || c->g_chunk != chunk ||
-      c->g_tol2 != w.tol2 || c->g_maxit != opts->max_iter || c->g_prec != opts->precond)) {
+      c->g_tol2 != w.tol2 || c->g_maxit != opts->max_iter || c->g_prec != opts->precond ||
+      c->g_buf_gen != P->buf_gen)) {
     if (c->exec) {
       cudaGraphExecDestroy(c->exec);
       c->exec = nullptr;
@@ -1267,6 +1276,7 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
     c->g_tol2 = w.tol2;
     c->g_maxit = opts->max_iter;
     c->g_prec = opts->precond;
+    c->g_buf_gen = P->buf_gen;
   }
 
   std::vector<int> timed_out(nrhs, 0);
@@ -1836,6 +1846,7 @@ int mm_deflation_build(mm_plan_t plan, const double* b, int m, int precision, vo
   }
   dfree(d->Z); dfree(d->Zp); dfree(d->Einv);
   d->k = 0;
+  P->buf_gen++;
   MM_TRY(dalloc(P, &d->Z, (size_t)k * n4));
   MM_TRY(dalloc(P, &d->Zp, (size_t)k * n4));
   MM_TRY(dalloc(P, &d->Einv, (size_t)k * k));
@@ -1849,6 +1860,63 @@ int mm_deflation_build(mm_plan_t plan, const double* b, int m, int precision, vo
   MM_CUDA(cudaMemcpyAsync(th.data(), wvals, k * sizeof(double), cudaMemcpyDeviceToHost, s));
   MM_CUDA(cudaStreamSynchronize(s));
   d->theta = th;
+  d->k = k;
+  d->n = n;
+  return MM_OK;
+}
+
+int mm_deflation_build_apriori(mm_plan_t plan, int precision, void* stream) {
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  if (!P) return fail(MM_EINVAL, "bad argument");
+  if (precision != MM_FP64 && precision != MM_FP32) return fail(MM_EINVAL, "bad precision");
+  if (P->algo == MM_TPLZ_DIRECT && precision == MM_FP32) precision = MM_FP64;
+  const int k = P->n_int;
+  if (k < 1 || k > kMaxDefl) return fail(MM_EINVAL, "the a-priori space needs 1 <= n_int <= 64 intervals");
+  DeviceGuard g(P->device);
+  cudaStream_t us = as_stream(stream);
+  cudaStream_t s = P->stream;
+  cudaEvent_t ev;
+  MM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  MM_CUDA(cudaEventRecord(ev, us));
+  MM_CUDA(cudaStreamWaitEvent(s, ev, 0));
+  cudaEventDestroy(ev);
+  const int64_t n = P->n_obs, n4 = 4 * n;
+  Scratch scr;
+  int32_t* hits = nullptr;
+  double *E = nullptr, *work = nullptr, *U = nullptr, *wvals = nullptr, *gpart = nullptr;
+  MM_TRY(scr.alloc(&hits, (size_t)k * n));
+  MM_TRY(scr.alloc(&E, kMaxDefl * kMaxDefl)); MM_TRY(scr.alloc(&work, kMaxDefl * kMaxDefl));
+  MM_TRY(scr.alloc(&U, kMaxDefl * kMaxDefl)); MM_TRY(scr.alloc(&wvals, kMaxDefl));
+  MM_TRY(scr.alloc(&gpart, (size_t)2 * 152 * kMaxBlk * kMaxBlk));
+  DeflState* d = reinterpret_cast<DeflState*>(P->defl);
+  if (!d) {
+    d = new DeflState();
+    P->defl = d;
+  }
+  dfree(d->Z); dfree(d->Zp); dfree(d->Einv);
+  d->k = 0;
+  P->buf_gen++;
+  MM_TRY(dalloc(P, &d->Z, (size_t)k * n4));
+  MM_TRY(dalloc(P, &d->Zp, (size_t)k * n4));
+  MM_TRY(dalloc(P, &d->Einv, (size_t)k * k));
+  MM_CUDA(launch_apriori_z(P->lpix, P->block_off_dev, P->n_blocks, k, n, hits, d->Z, s));
+  // Z' = A Z for the k columns at once
+  if (precision == MM_FP32) {
+    MM_CUDA(cudaMemsetAsync(d->Zp, 0, (size_t)k * n4 * sizeof(float), s));
+    MM_TRY(apply32_internal(P, d->Z, d->Zp, k, s));
+  } else {
+    MM_TRY(ensure_maps(P, k, false));
+    MM_TRY(ensure_df(P, k));
+    MM_CUDA(launch_to64(d->Z, (int64_t)k * n, P->map64_in, s));
+    MM_CUDA(cudaMemsetAsync(P->map64_out, 0, (size_t)k * n4 * sizeof(double), s));
+    MM_TRY(apply64_internal(P, P->map64_in, P->map64_out, k, s));
+    MM_CUDA(launch_to32(P->map64_out, (int64_t)k * n, d->Zp, s));
+  }
+  // E = Z^T Z', Einv = pinv(E)
+  MM_CUDA(launch_bgram(d->Z, k, nullptr, d->Zp, 0, k, nullptr, n, gpart, 2 * 152, E, s));
+  MM_CUDA(launch_pinv_sym(E, k, 1e-12, work, U, wvals, d->Einv, s));
+  MM_CUDA(cudaStreamSynchronize(s));
+  d->theta.assign(k, 0.0);
   d->k = k;
   d->n = n;
   return MM_OK;

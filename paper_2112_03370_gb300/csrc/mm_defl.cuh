@@ -32,6 +32,10 @@ cudaError_t launch_laxpby(double a, const double* x, double b, double* y, int64_
 cudaError_t launch_tridiag_eig(const double* alpha, const double* beta, int m, double* work, double* theta,
                                double* X, cudaStream_t s);
 // symmetric pseudo-inverse (eigenvalues below rcond * max |w| dropped)
+// 2lvl a-priori space: Z [n_int][n][4] float32 from the kept hits per time interval (hits:
+// scratch int32 [n_int][n]); block_off: device [n_blocks + 1]
+cudaError_t launch_apriori_z(const int32_t* lpix, const int64_t* block_off, int n_blocks, int n_int, int64_t n,
+                             int32_t* hits, float* Z, cudaStream_t s);
 cudaError_t launch_pinv_sym(const double* E, int k, double rcond, double* work, double* U, double* w,
                             double* Einv, cudaStream_t s);
 // z = M_2lvl r for every column not halted, then <r, z> and beta (PCG scalars)

@@ -27,7 +27,7 @@ STATUS_NAMES = {0: "MM_OK", 1: "MM_EINVAL", 2: "MM_ENOMEM", 3: "MM_ENOTSPD", 4: 
 # the exported entry points of include/mm.h
 EXPORTS = ("mm_plan", "mm_plan_query", "mm_plan_destroy", "mm_apply_P", "mm_apply_Pt",
            "mm_apply_Ninv", "mm_rhs", "mm_apply_A", "mm_precond", "mm_pcg_solve", "mm_last_error",
-           "mm_apply_A_noalloc", "mm_block_cg_solve", "mm_ecg_solve", "mm_deflation_build", "mm_deflation_get",
+           "mm_apply_A_noalloc", "mm_block_cg_solve", "mm_ecg_solve", "mm_deflation_build", "mm_deflation_build_apriori", "mm_deflation_get",
            "mm_deflation_apply", "mm_server_create", "mm_submit", "mm_poll", "mm_wait",
            "mm_server_destroy")
 
@@ -87,6 +87,7 @@ def _load():
     lib.mm_ecg_solve.argtypes = [vp, vp, vp, i32, i32, ctypes.POINTER(SolveOpts),
                                  ctypes.POINTER(SolveInfo), vp]
     lib.mm_deflation_build.argtypes = [vp, vp, i32, i32, vp]
+    lib.mm_deflation_build_apriori.argtypes = [vp, i32, vp]
     lib.mm_deflation_get.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp, vp, vp]
     lib.mm_deflation_apply.argtypes = [vp, vp, vp, i32, vp]
     lib.mm_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
@@ -303,6 +304,11 @@ def mm_deflation_build(plan: Plan, b: torch.Tensor, m: int, precision: int = MM_
     _dev(b, torch.float64, "b")
     _check(_lib.mm_deflation_build(ctypes.c_void_p(plan.handle), _ptr(b), m, precision,
                                    _stream_ptr(stream)))
+
+
+def mm_deflation_build_apriori(plan: Plan, precision: int = MM_FP64, stream=None):
+    """Two-level a-priori deflation space: one column per stationary interval of the plan."""
+    _check(_lib.mm_deflation_build_apriori(ctypes.c_void_p(plan.handle), precision, _stream_ptr(stream)))
 
 
 def mm_deflation_get(plan: Plan, stream=None):
