@@ -24,7 +24,9 @@ construction is pinned by (I - AQ)AZ = 0 and M_2lvl A Z = Z; block CG by s = 1 =
 CG by t = 1 == PCG iterate by iterate, the dense solve for t = 2..8 in both variants, the
 Galerkin condition P_k^T R_k = 0, and Orthomin == Orthodir on a well-conditioned problem; the
 a-priori deflation space by hit counts taken sample by sample, the partition of unity, and the
-same deflation identities as the a-posteriori one).
+same deflation identities as the a-posteriori one; the noise-weight estimator by one-sided
+Parseval, a pure cosine, gap handling by hand, exact recovery of a noise-free model, a noise
+realisation with known parameters, and the closed form and a brute-force inverse DFT of the band).
 """
 from __future__ import annotations
 
@@ -35,6 +37,7 @@ from typing import Optional
 
 import numpy as np
 import scipy.linalg
+import scipy.optimize
 import scipy.signal
 
 __all__ = [
@@ -685,3 +688,118 @@ def apply_A_at_pixels(pix, psi, block_off, band, keep, x_glob, pixels, sample_id
 
 def cpu_threads() -> int:
     return len(os.sched_getaffinity(0))
+
+
+# ------------------------------------------------------------------------------------------
+# noise weights from the data (Sect. 2.2, the MAPPRAISER weights paragraph; Eq. noisepowermodel)
+# ------------------------------------------------------------------------------------------
+
+NOISE_SEG = 32768   # periodogram segment and inverse-FFT length (frequencies k / NOISE_SEG)
+
+
+def periodogram(d, pix, block_len, seg: int = NOISE_SEG):
+    """Averaged periodogram of each block's gap-masked TOD G d ("the average periodogram of each
+    detector time stream").  A block of n samples gives max(1, floor(n / seg)) segments of seg
+    samples (one zero-padded segment when n < seg; a partial last segment is left out).  For each
+    segment P_k = |X_k|^2 / n_kept (X = real DFT of the seg samples, n_kept = kept samples in the
+    segment), averaged over the segments, k = 0..seg/2, frequency k / seg cycles per sample; white
+    noise of variance s^2 then has E P_k = s^2.  Returns (P [n_blocks, seg/2 + 1], segments used)."""
+    d = np.asarray(d, dtype=np.float64)
+    pix = np.asarray(pix)
+    off = block_offsets(block_len)
+    nb = len(block_len)
+    P = np.zeros((nb, seg // 2 + 1))
+    nseg = np.zeros(nb, dtype=np.int64)
+    for b in range(nb):
+        n = int(off[b + 1] - off[b])
+        gd = np.where(pix[off[b]:off[b + 1]] >= 0, d[off[b]:off[b + 1]], 0.0)
+        kept = pix[off[b]:off[b + 1]] >= 0
+        count = max(1, n // seg) if n > 0 else 0
+        used = 0
+        for s_ in range(count):
+            x = np.zeros(seg)
+            m = min(seg, n - s_ * seg)
+            x[:m] = gd[s_ * seg:s_ * seg + m]
+            nk = int(np.count_nonzero(kept[s_ * seg:s_ * seg + m]))
+            if nk == 0:
+                continue
+            P[b] += np.abs(np.fft.rfft(x)) ** 2 / nk
+            used += 1
+        if used:
+            P[b] /= used
+        nseg[b] = used
+    return P, nseg
+
+
+def psd_model(f, theta):
+    """Eq. noisepowermodel with f_0 = 0: P(f) = sigma^2 (1 + (f_knee / f)^alpha), theta =
+    (log sigma^2, log f_knee, alpha), f and f_knee in cycles per sample."""
+    ls2, lfk, a = theta
+    return np.exp(ls2) * (1.0 + np.exp(a * (lfk - np.log(f))))
+
+
+def psd_fit_init(P, seg: int = NOISE_SEG):
+    """Starting point of the fit: sigma^2 = mean of the upper half of the band (k >= seg/4); over
+    the bins with P_k > 3 sigma^2, a straight line through log(P_k / sigma^2 - 1) against log f
+    gives slope -alpha and intercept alpha log f_knee (alpha clipped to [0.2, 5]); with fewer than
+    three such bins alpha = 1 and f_knee = 1 / seg."""
+    P = np.asarray(P, dtype=np.float64)
+    k = np.arange(P.size)
+    s2 = float(np.mean(P[seg // 4:]))
+    sel = (k >= 1) & (P > 3.0 * s2)
+    if np.count_nonzero(sel) >= 3:
+        x = np.log(k[sel] / seg)
+        y = np.log(P[sel] / s2 - 1.0)
+        slope, icpt = np.polyfit(x, y, 1)
+        a = float(np.clip(-slope, 0.2, 5.0))
+        lfk = icpt / a
+    else:
+        a, lfk = 1.0, math.log(1.0 / seg)
+    return np.array([math.log(s2), lfk, a])
+
+
+def fit_psd(P, seg: int = NOISE_SEG):
+    """Least-squares fit of log P_k by log P(f_k; theta) over k = 1..seg/2 (the periodogram's
+    spread is multiplicative, so residuals are taken in log space), Levenberg-Marquardt from
+    psd_fit_init.  Returns theta = (log sigma^2, log f_knee, alpha)."""
+    P = np.asarray(P, dtype=np.float64)
+    k = np.arange(1, P.size)
+    f = k / seg
+    y = np.log(P[1:])
+    res = scipy.optimize.least_squares(lambda th: y - np.log(psd_model(f, th)), psd_fit_init(P, seg),
+                                       method="lm", xtol=1e-15, ftol=1e-15, gtol=1e-15, max_nfev=20000)
+    return res.x
+
+
+def band_from_psd(theta, lam: int, seg: int = NOISE_SEG):
+    """First row of the inverse-noise Toeplitz block from a fitted PSD: 1/P(f_k) on the seg-point
+    grid (1/P(0) := 0), inverse real DFT, Gaussian window N(0, lambda/2) on the lags, cut at
+    lambda (Sect. 2.2: "smoothed with a gaussian window ... and cut at the a priori specified half
+    bandwidth")."""
+    f = np.arange(seg // 2 + 1) / seg
+    S = np.zeros(f.size)
+    S[1:] = 1.0 / psd_model(f[1:], theta)
+    c = np.fft.irfft(S, n=seg)[:lam + 1]
+    if lam > 0:
+        tau = np.arange(lam + 1)
+        c = c * np.exp(-0.5 * (tau / (lam / 2.0)) ** 2)
+    return c
+
+
+def estimate_bands(d, pix, block_len, lam: int, seg: int = NOISE_SEG):
+    """The weights of each block from its own data: periodogram, fit, inverse band.  Returns
+    (bands [n_blocks, lam + 1], theta [n_blocks, 3]); blocks without a kept sample get zeros."""
+    P, nseg = periodogram(d, pix, block_len, seg)
+    nb = len(block_len)
+    bands = np.zeros((nb, lam + 1))
+    th = np.zeros((nb, 3))
+    for b in range(nb):
+        if nseg[b] == 0:
+            continue
+        th[b] = fit_psd(P[b], seg)
+        bands[b] = band_from_psd(th[b], lam, seg)
+    return bands, th
+
+
+__all__ += ["NOISE_SEG", "periodogram", "psd_model", "psd_fit_init", "fit_psd", "band_from_psd",
+            "estimate_bands"]

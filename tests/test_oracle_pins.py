@@ -404,3 +404,81 @@ def test_two_level_apriori_deflation_identities_and_iterations():
     two = O.pcg(pl, b, tol=1e-8, precond=lambda r: O.precond_2lvl(pl, tl, r))
     assert two.converged and two.iters <= bd.iters + 1
     assert np.linalg.norm(two.x - bd.x) <= 1e-6 * np.linalg.norm(bd.x)
+
+
+# ---------------------------------------------------------------- noise weights from the data
+
+def test_periodogram_parseval_and_white_level():
+    rng = np.random.default_rng(41)
+    seg = 256
+    d = rng.standard_normal(seg) * 1.7
+    P, nseg = O.periodogram(d, np.zeros(seg, np.int32), [seg], seg=seg)
+    w = np.full(seg // 2 + 1, 2.0)
+    w[0] = w[-1] = 1.0
+    # one-sided Parseval: sum_k w_k |X_k|^2 = seg sum_t d_t^2, and P_k = |X_k|^2 / seg here
+    assert nseg[0] == 1
+    np.testing.assert_allclose(np.sum(w * P[0]), np.sum(d * d), rtol=1e-12)
+    # white noise of variance s^2 averages to s^2 (64 segments)
+    d = rng.standard_normal(64 * seg) * 1.3
+    P, nseg = O.periodogram(d, np.zeros(d.size, np.int32), [d.size], seg=seg)
+    assert nseg[0] == 64
+    assert abs(np.mean(P[0, 1:-1]) / 1.69 - 1) < 0.02
+
+
+def test_periodogram_cosine_and_gaps():
+    seg, k0, amp = 512, 37, 0.8
+    t = np.arange(2 * seg)
+    d = amp * np.cos(2 * np.pi * k0 * t / seg)
+    pix = np.zeros(t.size, np.int32)
+    P, _ = O.periodogram(d, pix, [t.size], seg=seg)
+    np.testing.assert_allclose(P[0, k0], amp ** 2 * seg / 4, rtol=1e-12)      # |X_k0| = amp seg / 2
+    assert np.max(np.delete(P[0], k0)) < 1e-20 * P[0, k0]
+    # flagged samples count neither as data nor in the normalisation
+    pix[::2] = -1
+    Pg, _ = O.periodogram(d, pix, [t.size], seg=seg)
+    manual = np.zeros(seg // 2 + 1)
+    for s_ in range(2):
+        x = np.where(pix[s_ * seg:(s_ + 1) * seg] >= 0, d[s_ * seg:(s_ + 1) * seg], 0.0)
+        manual += np.abs(np.fft.rfft(x)) ** 2 / (seg // 2)
+    np.testing.assert_allclose(Pg[0], manual / 2, rtol=1e-12)
+
+
+def test_fit_recovers_an_exact_model():
+    seg = 4096
+    theta = np.array([math.log(1.21), math.log(0.004), 1.7])
+    f = np.arange(seg // 2 + 1) / seg
+    P = np.zeros(f.size)
+    P[1:] = O.psd_model(f[1:], theta)
+    P[0] = P[1]
+    np.testing.assert_allclose(O.fit_psd(P, seg), theta, rtol=1e-8, atol=1e-10)
+
+
+def test_fit_of_a_noise_realisation():
+    # 1/f noise with sigma 1.1, f_knee 1 Hz at 100 Hz, alpha 1.5, 32 segments
+    g = __import__("torch").Generator().manual_seed(9)
+    d = synth.noise_block(32 * O.NOISE_SEG, 100.0, 1.1, 1.0, 1.5, g).numpy()
+    bands, th = O.estimate_bands(d, np.zeros(d.size, np.int32), [d.size], 1024)
+    assert abs(math.exp(th[0, 0]) / 1.21 - 1) < 0.05
+    assert abs(math.exp(th[0, 1]) / 0.01 - 1) < 0.25
+    assert abs(th[0, 2] - 1.5) < 0.15
+    # the band of the true PSD on the same grid and window: close to the estimated one
+    true = O.band_from_psd(np.array([math.log(1.21), math.log(0.01), 1.5]), 1024)
+    assert abs(bands[0, 0] / true[0] - 1) < 0.1
+
+
+def test_band_from_psd_closed_forms():
+    seg, lam = 64, 10
+    # white PSD (f_knee -> 0) with 1/P(0) := 0: c_tau = (delta_tau - 1/seg) / sigma^2, windowed
+    c = O.band_from_psd(np.array([math.log(2.0), -200.0, 1.0]), lam, seg)
+    tau = np.arange(lam + 1)
+    np.testing.assert_allclose(c, 0.5 * ((tau == 0) - 1.0 / seg) * np.exp(-0.5 * (tau / (lam / 2)) ** 2),
+                               rtol=1e-12, atol=1e-15)
+    # brute-force inverse DFT with explicit cosines and the Gaussian window
+    theta = np.array([math.log(1.3), math.log(0.05), 1.2])
+    f = np.arange(seg // 2 + 1) / seg
+    S = np.zeros(f.size)
+    S[1:] = 1.0 / O.psd_model(f[1:], theta)
+    full = np.concatenate([S, S[-2:0:-1]])
+    ref = np.array([sum(full[k] * math.cos(2 * math.pi * k * t / seg) for k in range(seg)) / seg
+                    * math.exp(-0.5 * (t / (lam / 2)) ** 2) for t in range(lam + 1)])
+    np.testing.assert_allclose(O.band_from_psd(theta, lam, seg), ref, rtol=1e-12, atol=1e-15)
