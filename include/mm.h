@@ -250,6 +250,29 @@ enum { MM_ECG_ORTHOMIN = 0, MM_ECG_ORTHODIR = 1 };
 int mm_ecg_solve(mm_plan_t plan, const double* b, double* x, int t, int variant, const mm_solve_opts* opts,
                  mm_solve_info* info, void* stream);
 
+/* Noise weights estimated from the data (Sect. 2.2, how the weights are computed; the PSD model of
+ * Eq. noisepowermodel with f_0 = 0).  For every block b of n_det * n_int (detector-major, block_len
+ * HOST [n_det * n_int]):
+ *   1. the averaged periodogram of its gap-masked TOD: max(1, floor(n / 32768)) segments of 32768
+ *      samples (one zero-padded segment for a shorter block; a partial last segment is left out),
+ *      P_k = |X_k|^2 / (kept samples of the segment), X the real DFT, averaged over segments;
+ *   2. a Levenberg-Marquardt fit of log P_k by log(sigma^2 (1 + (f_knee / f_k)^alpha)) over
+ *      k = 1..16384, f_k = k / 32768 cycles per sample, from a closed-form start (sigma^2 = mean of
+ *      P_k over k >= 8192; a line through log(P_k / sigma^2 - 1) against log f_k over P_k > 3 sigma^2),
+ *      steps bounded by 1 per parameter; without a 1/f excess (white noise) f_knee and alpha are
+ *      not identifiable and any point of the flat valley may be returned;
+ *   3. the first row of the block's inverse-noise Toeplitz matrix: 1/P on the 32768-point grid
+ *      (1/P(0) := 0), inverse real DFT, Gaussian window N(0, lambda/2) over the lags, cut at lambda.
+ *   pix, d   [N] device: int32 pixel (-1 = flagged sample) and float64 TOD.
+ *   band     [n_det * n_int][lambda + 1] float64 device, written (zeros for a block without a kept
+ *            sample); usable as mm_problem_desc.band.
+ *   params   optional HOST [n_det * n_int][3]: log sigma^2, log f_knee (cycles per sample), alpha.
+ * Transforms in FP32 (the tiles' shared-memory FFT), the fit with FP32 terms and FP64 sums.
+ * Synchronous; allocates and frees its own scratch.  MM_EINVAL for bad sizes or lambda outside
+ * [0, 12288]. */
+int mm_estimate_bands(int32_t n_det, int32_t n_int, const int64_t* block_len, const int32_t* pix,
+                      const double* d, int32_t lambda, double* band, double* params, void* stream);
+
 /* Build the two-level a-posteriori deflation space of the plan (Sect. 3.2): m steps of the Lanczos
  * algorithm (Algorithm 3) on A (not M_BD A) from v_1 = b / ||b|| (x_0 = 0), storing A V_m; the
  * Ritz vectors of T_m = X Theta X^T give Z = V_m X and Z' = (A V_m) X (all m of them, as the paper

@@ -29,7 +29,7 @@ EXPORTS = ("mm_plan", "mm_plan_query", "mm_plan_destroy", "mm_apply_P", "mm_appl
            "mm_apply_Ninv", "mm_rhs", "mm_apply_A", "mm_precond", "mm_pcg_solve", "mm_last_error",
            "mm_apply_A_noalloc", "mm_block_cg_solve", "mm_ecg_solve", "mm_deflation_build", "mm_deflation_build_apriori", "mm_deflation_get",
            "mm_deflation_apply", "mm_server_create", "mm_submit", "mm_poll", "mm_wait",
-           "mm_server_destroy")
+           "mm_server_destroy", "mm_estimate_bands")
 
 
 class ProblemDesc(ctypes.Structure):
@@ -88,6 +88,7 @@ def _load():
                                  ctypes.POINTER(SolveInfo), vp]
     lib.mm_deflation_build.argtypes = [vp, vp, i32, i32, vp]
     lib.mm_deflation_build_apriori.argtypes = [vp, i32, vp]
+    lib.mm_estimate_bands.argtypes = [i32, i32, vp, vp, vp, i32, vp, vp, vp]
     lib.mm_deflation_get.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp, vp, vp]
     lib.mm_deflation_apply.argtypes = [vp, vp, vp, i32, vp]
     lib.mm_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
@@ -304,6 +305,21 @@ def mm_deflation_build(plan: Plan, b: torch.Tensor, m: int, precision: int = MM_
     _dev(b, torch.float64, "b")
     _check(_lib.mm_deflation_build(ctypes.c_void_p(plan.handle), _ptr(b), m, precision,
                                    _stream_ptr(stream)))
+
+
+def mm_estimate_bands(n_det: int, n_int: int, block_len: Sequence[int], pix: torch.Tensor, d: torch.Tensor,
+                      lam: int, stream=None):
+    """Noise weights from the data: (bands [n_blocks, lam + 1] float64 CUDA tensor,
+    params [n_blocks, 3] numpy: log sigma^2, log f_knee in cycles per sample, alpha)."""
+    import numpy as np
+    _dev(pix, torch.int32, "pix"); _dev(d, torch.float64, "d")
+    nb = n_det * n_int
+    bl = (ctypes.c_int64 * nb)(*[int(v) for v in block_len])
+    bands = torch.empty(nb, lam + 1, dtype=torch.float64, device=d.device)
+    params = np.zeros((nb, 3))
+    _check(_lib.mm_estimate_bands(n_det, n_int, bl, _ptr(pix), _ptr(d), lam, _ptr(bands),
+                                  params.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream)))
+    return bands, params
 
 
 def mm_deflation_build_apriori(plan: Plan, precision: int = MM_FP64, stream=None):
