@@ -26,7 +26,10 @@ Galerkin condition P_k^T R_k = 0, and Orthomin == Orthodir on a well-conditioned
 a-priori deflation space by hit counts taken sample by sample, the partition of unity, and the
 same deflation identities as the a-posteriori one; the noise-weight estimator by one-sided
 Parseval, a pure cosine, gap handling by hand, exact recovery of a noise-free model, a noise
-realisation with known parameters, and the closed form and a brute-force inverse DFT of the band).
+realisation with known parameters, and the closed form and a brute-force inverse DFT of the band;
+the template filter by F_T T = 0, symmetry and positivity, closed forms of every template column,
+the no-template limit equal to the diagonal-weighted operator, and exact recovery of a map from
+data that carries template signals).
 """
 from __future__ import annotations
 
@@ -39,6 +42,7 @@ import numpy as np
 import scipy.linalg
 import scipy.optimize
 import scipy.signal
+import scipy.special
 
 __all__ = [
     "pointing_weights", "block_offsets", "sample_block", "bd_blocks", "excise", "OraclePlan",
@@ -803,3 +807,108 @@ def estimate_bands(d, pix, block_len, lam: int, seg: int = NOISE_SEG):
 
 __all__ += ["NOISE_SEG", "periodogram", "psd_model", "psd_fit_init", "fit_psd", "band_from_psd",
             "estimate_bands"]
+
+
+# ------------------------------------------------------------------------------------------
+# template map-making with diagonal weights (Sect. 2, Eq. genMapEstimator with the filtering
+# operator F_T; the templates of Appendix A)
+# ------------------------------------------------------------------------------------------
+
+
+@dataclass
+class Templates:
+    """Template classes of every block (detector x stationary interval): n_poly Legendre orders,
+    n_az azimuth bins (or interpolation nodes when interp), n_hwp harmonics of the HWP angle."""
+
+    n_poly: int = 0
+    n_az: int = 0
+    n_hwp: int = 0
+    interp: bool = False
+
+    @property
+    def k(self) -> int:
+        return self.n_poly + self.n_az + 2 * self.n_hwp
+
+
+def template_matrix(n: int, az, hwp, kept, tm: Templates) -> np.ndarray:
+    """The templates of one block of n samples as columns [n, K] (Appendix A), one interval per
+    block:
+      Legendre P_k(x), k < n_poly, at x = 2 tau / (n - 1) - 1 (x = 0 when n = 1), rescaled by
+      sqrt((2k + 1) / n) so that the columns are orthonormal up to the discretisation;
+      azimuth: the grid spans [min, max] of az over the block's kept samples; binned: value 1 in
+      bin floor((az - lo) / (hi - lo) n_az) (clamped to n_az - 1; bin 0 when hi = lo); interpolated:
+      nodes lo + i (hi - lo) / (n_az - 1), the two nodes bracketing az get (phi_{i+1} - az) / step
+      and (az - phi_i) / step (node 0 alone when hi = lo or n_az = 1);
+      HWP: cos(k phi), sin(k phi), k = 1..n_hwp.
+    Rows of masked samples are kept (the weights zero them)."""
+    az = np.asarray(az, dtype=np.float64)
+    hwp = np.asarray(hwp, dtype=np.float64)
+    T = np.zeros((n, tm.k))
+    tau = np.arange(n)
+    x = 2.0 * tau / (n - 1) - 1.0 if n > 1 else np.zeros(n)
+    for k in range(tm.n_poly):
+        T[:, k] = scipy.special.eval_legendre(k, x) * math.sqrt((2 * k + 1) / n)
+    c0 = tm.n_poly
+    if tm.n_az > 0:
+        sel = np.asarray(kept, dtype=bool)
+        lo = float(az[sel].min()) if sel.any() else 0.0
+        hi = float(az[sel].max()) if sel.any() else 0.0
+        if tm.interp:
+            if hi > lo and tm.n_az > 1:
+                step = (hi - lo) / (tm.n_az - 1)
+                pos = np.clip((az - lo) / step, 0.0, tm.n_az - 1)
+                i = np.minimum(np.floor(pos).astype(np.int64), tm.n_az - 2)
+                frac = pos - i
+                T[tau, c0 + i] = 1.0 - frac
+                T[tau, c0 + i + 1] = frac
+            else:
+                T[:, c0] = 1.0
+        else:
+            if hi > lo:
+                b = np.floor((az - lo) / (hi - lo) * tm.n_az).astype(np.int64)
+                b = np.clip(b, 0, tm.n_az - 1)
+            else:
+                b = np.zeros(n, dtype=np.int64)
+            T[tau, c0 + b] = 1.0
+    c0 += tm.n_az
+    for k in range(1, tm.n_hwp + 1):
+        T[:, c0 + 2 * (k - 1)] = np.cos(k * hwp)
+        T[:, c0 + 2 * (k - 1) + 1] = np.sin(k * hwp)
+    return T
+
+
+def template_filter(plan: OraclePlan, weights, tm: Templates, az, hwp, v, rcond: float = 1e-12) -> np.ndarray:
+    """F_T v = W v - W T (T^T W T)^+ T^T W v block by block (Sect. 2, Eq. genMapEstimator; the
+    kernel inverted by SVD with singular values below rcond of the largest dropped, as the templates
+    package does), W = diag(w_b) on the kept samples of block b and 0 on masked ones (G)."""
+    v = np.asarray(v, dtype=np.float64)
+    out = np.zeros_like(v)
+    for b in range(plan.block_len.size):
+        lo, hi = plan.offsets[b], plan.offsets[b + 1]
+        n = int(hi - lo)
+        if n == 0:
+            continue
+        kept = plan.lpix[lo:hi] >= 0
+        w = np.where(kept, float(weights[b]), 0.0)
+        wv = w * v[lo:hi]
+        if tm.k == 0:
+            out[lo:hi] = wv
+            continue
+        T = template_matrix(n, az[lo:hi], hwp[lo:hi], kept, tm)
+        K = T.T @ (w[:, None] * T)
+        c = np.linalg.pinv(K, rcond=rcond, hermitian=True) @ (T.T @ wv)
+        out[lo:hi] = wv - w * (T @ c)
+    return out
+
+
+def apply_A_templates(plan: OraclePlan, weights, tm: Templates, az, hwp, x) -> np.ndarray:
+    """A x = P~^T F_T P~ x."""
+    return point(plan, template_filter(plan, weights, tm, az, hwp, unpoint(plan, x)))
+
+
+def rhs_templates(plan: OraclePlan, weights, tm: Templates, az, hwp, d) -> np.ndarray:
+    """b = P~^T F_T G d (F_T carries the mask)."""
+    return point(plan, template_filter(plan, weights, tm, az, hwp, np.asarray(d, dtype=np.float64)))
+
+
+__all__ += ["Templates", "template_matrix", "template_filter", "apply_A_templates", "rhs_templates"]

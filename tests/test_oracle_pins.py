@@ -482,3 +482,90 @@ def test_band_from_psd_closed_forms():
     ref = np.array([sum(full[k] * math.cos(2 * math.pi * k * t / seg) for k in range(seg)) / seg
                     * math.exp(-0.5 * (t / (lam / 2)) ** 2) for t in range(lam + 1)])
     np.testing.assert_allclose(O.band_from_psd(theta, lam, seg), ref, rtol=1e-12, atol=1e-15)
+
+
+# ---------------------------------------------------------------- template map-making (Appendix A)
+
+def tmpl_problem(seed=51, lens=(3000, 2500, 0, 1700), n_pix=50):
+    p = synth.random_problem(len(lens), list(lens), n_pix, 0, seed, gap_frac=0.05, hits_per_pix_min=6)
+    nb = synth.to_numpy(p)
+    rng = np.random.default_rng(seed)
+    n = int(np.sum(lens))
+    az = np.concatenate([np.abs(np.sin(np.linspace(0, 9, m))) * 10 + rng.normal(0, 0.01, m) for m in lens]) if n else np.zeros(0)
+    hwp = (2 * np.pi * 0.37 * np.arange(n)) % (2 * np.pi)
+    w = 0.5 + rng.random(len(lens))
+    band = w[:, None]                                  # lambda = 0: c_0 = w_b (diagonal weights)
+    pl = O.make_plan(nb["pix"], nb["psi"], nb["block_len"], band, nb["n_pix"])
+    return pl, nb, w, az.astype(np.float32), hwp.astype(np.float32)
+
+
+@pytest.mark.parametrize("interp", [False, True])
+def test_template_filter_annihilates_templates_and_is_symmetric(interp):
+    pl, nb, w, az, hwp = tmpl_problem()
+    tm = O.Templates(n_poly=3, n_az=5, n_hwp=2, interp=interp)
+    rng = np.random.default_rng(1)
+    for b in (0, 1, 3):
+        lo, hi = pl.offsets[b], pl.offsets[b + 1]
+        kept = pl.lpix[lo:hi] >= 0
+        T = O.template_matrix(int(hi - lo), az[lo:hi], hwp[lo:hi], kept, tm)
+        for j in range(T.shape[1]):                     # F_T T = 0
+            v = np.zeros(pl.lpix.size)
+            v[lo:hi] = T[:, j]
+            out = O.template_filter(pl, w, tm, az, hwp, v)
+            assert np.max(np.abs(out)) <= 1e-10 * np.max(np.abs(w[b] * T[:, j]))
+    u, v = rng.standard_normal((2, pl.lpix.size))     # <u, F v> = <F u, v>, <v, F v> >= 0
+    Fu, Fv = O.template_filter(pl, w, tm, az, hwp, u), O.template_filter(pl, w, tm, az, hwp, v)
+    assert abs(np.dot(u, Fv) - np.dot(Fu, v)) <= 1e-11 * np.linalg.norm(u) * np.linalg.norm(Fv)
+    assert np.dot(v, Fv) >= -1e-12 * np.dot(v, v)
+
+
+def test_template_columns_by_definition():
+    n = 200
+    az = np.linspace(3.0, 7.0, n)
+    hwp = np.linspace(0.0, 12.0, n)
+    kept = np.ones(n, bool)
+    T = O.template_matrix(n, az, hwp, kept, O.Templates(n_poly=3, n_az=4, n_hwp=1))
+    x = 2 * np.arange(n) / (n - 1) - 1
+    np.testing.assert_allclose(T[:, 0], math.sqrt(1 / n), rtol=1e-15)
+    np.testing.assert_allclose(T[:, 1], x * math.sqrt(3 / n), rtol=1e-12)
+    np.testing.assert_allclose(T[:, 2], 0.5 * (3 * x * x - 1) * math.sqrt(5 / n), rtol=1e-12, atol=1e-15)
+    bins = T[:, 3:7]
+    np.testing.assert_array_equal(bins.sum(axis=1), 1.0)                        # one bin per sample
+    np.testing.assert_array_equal(np.argmax(bins, axis=1), np.minimum(((az - 3) / 4 * 4).astype(int), 3))
+    np.testing.assert_allclose(T[:, 7], np.cos(hwp), rtol=1e-15)
+    np.testing.assert_allclose(T[:, 8], np.sin(hwp), rtol=1e-15, atol=1e-15)
+    Ti = O.template_matrix(n, az, hwp, kept, O.Templates(n_az=5, interp=True))
+    np.testing.assert_allclose(Ti.sum(axis=1), 1.0, rtol=1e-14)                 # partition of unity
+    np.testing.assert_allclose(Ti @ np.linspace(3, 7, 5), az, rtol=1e-13)      # reproduces linear az
+    assert np.all(np.count_nonzero(Ti, axis=1) <= 2)
+
+
+def test_no_templates_is_the_diagonal_weighted_operator():
+    pl, nb, w, az, hwp = tmpl_problem(seed=52)
+    x = np.random.default_rng(2).standard_normal((pl.n_obs, 3))
+    np.testing.assert_allclose(O.apply_A_templates(pl, w, O.Templates(), az, hwp, x), O.apply_A(pl, x),
+                               rtol=1e-12, atol=1e-12)
+
+
+def test_templates_remove_a_template_signal_from_the_map():
+    # d = P m + sum of template signals (no noise): the template map-maker recovers m exactly,
+    # the diagonal-weighted (binned) solution does not
+    pl, nb, w, az, hwp = tmpl_problem(seed=53, lens=(6000, 5000, 4000), n_pix=30)
+    tm = O.Templates(n_poly=2, n_az=4, n_hwp=2)
+    rng = np.random.default_rng(3)
+    m = rng.standard_normal((pl.n_obs, 3))
+    d = O.unpoint(pl, m)
+    for b in range(3):
+        lo, hi = pl.offsets[b], pl.offsets[b + 1]
+        T = O.template_matrix(int(hi - lo), az[lo:hi], hwp[lo:hi], pl.lpix[lo:hi] >= 0, tm)
+        d[lo:hi] += T @ (rng.standard_normal(tm.k) * 5)
+    A = np.stack([O.apply_A_templates(pl, w, tm, az, hwp, e.reshape(-1, 3)).reshape(-1)
+                  for e in np.eye(3 * pl.n_obs)], axis=1)
+    b = O.rhs_templates(pl, w, tm, az, hwp, d).reshape(-1)
+    x = np.linalg.lstsq(A, b, rcond=None)[0].reshape(-1, 3)
+    # the total-intensity offset is degenerate with the constant templates: compare Q, U and the
+    # I map up to its mean
+    np.testing.assert_allclose(x[:, 1:], m[:, 1:], atol=1e-8)
+    np.testing.assert_allclose(x[:, 0] - x[:, 0].mean(), m[:, 0] - m[:, 0].mean(), atol=1e-8)
+    xb = O.pcg(pl, O.rhs(pl, d), tol=1e-12).x
+    assert np.max(np.abs(xb[:, 1:] - m[:, 1:])) > 1e-3
