@@ -250,6 +250,36 @@ enum { MM_ECG_ORTHOMIN = 0, MM_ECG_ORTHODIR = 1 };
 int mm_ecg_solve(mm_plan_t plan, const double* b, double* x, int t, int variant, const mm_solve_opts* opts,
                  mm_solve_info* info, void* stream);
 
+/* Template map-making with diagonal weights (Sect. 2, Eq. genMapEstimator with the filtering operator
+ * F_T = W - W T (T^T W T)^+ T^T W; the templates of Appendix A).  Attaches templates to a plan built
+ * with lambda = 0, whose band rows c_0 = w_b are the diagonal weights W of each block; from then on
+ * mm_apply_A, mm_rhs, mm_pcg_solve, mm_block_cg_solve, mm_ecg_solve and the deflation builders use
+ * A = P~^T F_T P~ and b = P~^T F_T G d (the block-Jacobi preconditioner stays (P~^T W P~)^-1).
+ * Templates per block (detector x stationary interval), one interval per block:
+ *   n_poly    Legendre orders 0..n_poly-1 on x = 2 tau / (n - 1) - 1, scaled by sqrt((2k + 1) / n)
+ *             (0..16);
+ *   n_az      azimuth templates over the block's azimuth range [min, max] of its kept samples
+ *             (0..64): az_interp = 0, bins (value 1 in bin floor((az - min) / (max - min) n_az));
+ *             az_interp = 1, linear interpolation between n_az equally spaced nodes;
+ *   n_hwp     harmonics cos(k phi), sin(k phi), k = 1..n_hwp, of the HWP angle phi (0..8).
+ *   n_poly + n_az + 2 n_hwp must lie in [1, 64].
+ *   az, hwp   [N] float32 per sample (host, or device with inputs_on_device); copied.
+ * Each block's kernel T^T W T is built in FP64 and pseudo-inverted (eigenvalues below 1e-12 of the
+ * largest dropped); azimuth bins are decided once in FP64.  The FP32 operator filters in FP32, the
+ * FP64-class one in IEEE FP64 (also on df64 plans).  Replaces previous templates.  Synchronous.
+ * MM_EINVAL for a plan with lambda > 0 or counts out of range; mm_apply_A_noalloc rejects such
+ * plans. */
+typedef struct {
+  int32_t n_poly;
+  int32_t n_az;
+  int32_t n_hwp;
+  int32_t az_interp;
+  const float* az;
+  const float* hwp;
+  int32_t inputs_on_device;
+} mm_templates_desc;
+int mm_templates_set(mm_plan_t plan, const mm_templates_desc* t, void* stream);
+
 /* Noise weights estimated from the data (Sect. 2.2, how the weights are computed; the PSD model of
  * Eq. noisepowermodel with f_0 = 0).  For every block b of n_det * n_int (detector-major, block_len
  * HOST [n_det * n_int]):

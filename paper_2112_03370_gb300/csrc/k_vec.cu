@@ -325,6 +325,7 @@ __global__ void k_cg_init(CgWork w) {
     s.iters = 0;
     s.n_true = 0;
     s.since_rep = 0;
+    s.restart_req = 0;
     s.status = MM_OK;
     s.paused = 0;
     s.done = (t[0] == 0.0) ? 1 : 0;
@@ -394,10 +395,18 @@ __global__ void k_cg_dot_pq(CgWork w) {
     s.pq = t[0];
     const double alpha = s.rz / t[0];
     if (!(t[0] > 0.0) || !isfinite(alpha)) {
-      s.status = MM_EBREAKDOWN;
-      s.done = 1;
-      s.halt = 1;
       s.alpha = 0.0;
+      if (w.fp32 && s.since_rep > 0 && isfinite(t[0])) {
+        // FP32 operator noise along a (near-)null direction of a semi-definite A (e.g. a map offset
+        // degenerate with templates): restart from the FP64-class true residual instead of failing
+        s.paused = 1;
+        s.restart_req = 1;
+        s.halt = 1;
+      } else {
+        s.status = MM_EBREAKDOWN;
+        s.done = 1;
+        s.halt = 1;
+      }
     } else {
       s.alpha = alpha;
     }
@@ -488,7 +497,8 @@ __global__ void k_cg_replace(CgWork w) {
     // recursive one; when it is more than twice as large in norm (the recursion has run below the
     // FP32 operator's accuracy) p was built for a residual that no longer exists, and CG restarts
     // from p = z.
-    const bool restart = t[0] > 4.0 * s.rr;
+    const bool restart = t[0] > 4.0 * s.rr || s.restart_req != 0;
+    s.restart_req = 0;
     s.rr = t[0];
     s.rr_true = t[0];
     s.rz = t[1];

@@ -15,6 +15,7 @@
 #include "mm_cg.cuh"
 #include "mm_defl.cuh"
 #include "mm_internal.cuh"
+#include "mm_tmpl.cuh"
 
 namespace mm {
 
@@ -128,6 +129,14 @@ void free_defl(DeflState* d) {
   delete d;
 }
 
+void free_tmpl(TmplState* t) {
+  if (!t) return;
+  dfree(t->az); dfree(t->hwp); dfree(t->az_bin); dfree(t->az_frac); dfree(t->xscale); dfree(t->xoff);
+  dfree(t->pscale);
+  dfree(t->kinv);
+  delete t;
+}
+
 void free_plan(Plan* P) {
   if (!P) return;
   int cur = 0;
@@ -142,6 +151,7 @@ void free_plan(Plan* P) {
   free_cg(reinterpret_cast<CgState*>(P->cg));
   free_blk(reinterpret_cast<BlkState*>(P->blk));
   free_defl(reinterpret_cast<DeflState*>(P->defl));
+  free_tmpl(reinterpret_cast<TmplState*>(P->tmpl));
   if (P->stream) cudaStreamDestroy(P->stream);
   cudaSetDevice(cur);
   delete P;
@@ -555,6 +565,19 @@ bool capturing(cudaStream_t s) {
 // y4 (accumulated, pre-zeroed by the caller) += A x4 with the FP64-class operators, [nrhs][n_obs][4]
 int apply64_internal(Plan* P, const double* x4, double* y4, int nrhs, cudaStream_t s,
                      const int32_t* done = nullptr, int done_stride = 0) {
+  if (P->tmpl) {   // template map-making: P^T F_T P, column by column in FP64
+    const TmplState* ts = reinterpret_cast<const TmplState*>(P->tmpl);
+    if (capturing(s) && !(P->td_a && P->td_cap >= (size_t)P->N))
+      return fail(MM_EINVAL, "template buffers must be allocated before graph capture");
+    MM_TRY(ensure_td(P));
+    for (int r = 0; r < nrhs; r++) {
+      MM_CUDA(launch_unpoint64(P->lpix, P->w64, P->N, x4 + (size_t)r * P->n_obs * 4, P->td_a, s));
+      MM_CUDA(launch_tmpl_filter64(ts->dev, P->n_blocks, P->td_a, P->N, 1, s));
+      MM_CUDA(launch_point64(P->lpix, P->w64, P->N, P->td_a, y4 + (size_t)r * P->n_obs * 4, s));
+    }
+    (void)done; (void)done_stride;
+    return MM_OK;
+  }
   if (P->df64) {
     const int k = df_cols(P, nrhs);
     if (capturing(s) && (P->tdf_cap < (size_t)k * df_stride(P) || P->mapdf_cap < (size_t)k * P->n_obs * 2))
@@ -623,6 +646,19 @@ int apply32_internal(Plan* P, const float* x32, float* y32, int nrhs, cudaStream
   a.y_stride = P->n_obs * 4;
   a.done = done;
   a.done_stride = done_stride;
+  if (P->tmpl) {   // template map-making: t = P x, t <- F_T t, y += P^T t (FP32)
+    const TmplState* ts = reinterpret_cast<const TmplState*>(P->tmpl);
+    MM_TRY(ensure_t32(P, nrhs));
+    if (!P->t32 || P->t32_cap < (size_t)nrhs * (size_t)t32_stride(P))
+      return fail(MM_EINVAL, "template plans need nrhs * N * 4 bytes <= 24 GiB of un-pointed buffer");
+    MM_CUDA(launch_unpoint32(P->lpix, P->w32, P->N, x32, P->n_obs * 4, nrhs, done, done_stride, P->t32,
+                             t32_stride(P), s));
+    if (mid) MM_CUDA(cudaEventRecord(mid, s));
+    MM_CUDA(launch_tmpl_filter32(ts->dev, P->n_blocks, P->t32, t32_stride(P), nrhs, done, done_stride, s));
+    MM_CUDA(launch_point32t(P->lpix, P->w32, P->N, P->t32, t32_stride(P), y32, P->n_obs * 4, nrhs, done,
+                            done_stride, s));
+    return MM_OK;
+  }
   // Un-point first at full occupancy (t = P x into a plan-owned FP32 buffer), then the tiles
   // stream t instead of gathering the map themselves; fused gather when the buffer would be large.
   const size_t t_elems = (size_t)nrhs * (size_t)t32_stride(P);
@@ -1137,7 +1173,17 @@ int mm_rhs(mm_plan_t plan, const void* d, int d_is_fp32, int nrhs, double* b, vo
   MM_TRY(ensure_maps(P, nrhs, false));
   const size_t n4 = (size_t)nrhs * P->n_obs * 4;
   MM_CUDA(cudaMemsetAsync(P->map64_out, 0, n4 * sizeof(double), s));
-  if (P->algo == MM_TPLZ_DIRECT) {
+  if (P->tmpl) {   // template map-making: b = P^T F_T G d
+    const TmplState* ts = reinterpret_cast<const TmplState*>(P->tmpl);
+    MM_TRY(ensure_td(P));
+    const size_t esz = d_is_fp32 ? sizeof(float) : sizeof(double);
+    for (int r = 0; r < nrhs; r++) {
+      const void* dr = reinterpret_cast<const char*>(d) + (size_t)r * P->N * esz;
+      MM_CUDA(launch_mask_d(P->lpix, dr, d_is_fp32, P->N, P->td_a, s));
+      MM_CUDA(launch_tmpl_filter64(ts->dev, P->n_blocks, P->td_a, P->N, 1, s));
+      MM_CUDA(launch_point64(P->lpix, P->w64, P->N, P->td_a, P->map64_out + (size_t)r * P->n_obs * 4, s));
+    }
+  } else if (P->algo == MM_TPLZ_DIRECT) {
     MM_TRY(ensure_td(P));
     const size_t esz = d_is_fp32 ? sizeof(float) : sizeof(double);
     for (int r = 0; r < nrhs; r++) {
@@ -1231,7 +1277,7 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
   CgState* c = nullptr;
   MM_TRY(ensure_cg(P, nrhs, fp32, &c));
   CgWork w = make_work(P, c, nrhs, fp32, opts->tol, opts->max_iter);
-  if (P->algo == MM_TPLZ_DIRECT) MM_TRY(ensure_td(P));
+  if (P->algo == MM_TPLZ_DIRECT || P->tmpl) MM_TRY(ensure_td(P));
   if (fp32) MM_TRY(ensure_t32(P, nrhs));
   MM_TRY(ensure_df(P, nrhs));
   DeflWork dw{};
@@ -1919,6 +1965,71 @@ int mm_deflation_build_apriori(mm_plan_t plan, int precision, void* stream) {
   d->theta.assign(k, 0.0);
   d->k = k;
   d->n = n;
+  return MM_OK;
+}
+
+int mm_templates_set(mm_plan_t plan, const mm_templates_desc* t, void* stream) {
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  if (!P || !t) return fail(MM_EINVAL, "bad argument");
+  if (P->lambda != 0) return fail(MM_EINVAL, "template map-making uses diagonal weights: the plan's lambda must be 0");
+  if (t->n_poly < 0 || t->n_poly > kMaxPoly) return fail(MM_EINVAL, "n_poly must lie in [0, 16]");
+  if (t->n_az < 0 || t->n_az > kMaxTmpl) return fail(MM_EINVAL, "n_az must lie in [0, 64]");
+  if (t->n_hwp < 0 || t->n_hwp > kMaxHwp) return fail(MM_EINVAL, "n_hwp must lie in [0, 8]");
+  const int k = t->n_poly + t->n_az + 2 * t->n_hwp;
+  if (k < 1 || k > kMaxTmpl) return fail(MM_EINVAL, "n_poly + n_az + 2 n_hwp must lie in [1, 64]");
+  if ((t->n_az > 0 && !t->az) || (t->n_hwp > 0 && !t->hwp)) return fail(MM_EINVAL, "az / hwp missing");
+  DeviceGuard g(P->device);
+  cudaStream_t us = as_stream(stream);
+  cudaStream_t s = P->stream;
+  cudaEvent_t ev;
+  MM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  MM_CUDA(cudaEventRecord(ev, us));
+  MM_CUDA(cudaStreamWaitEvent(s, ev, 0));
+  cudaEventDestroy(ev);
+  free_tmpl(reinterpret_cast<TmplState*>(P->tmpl));
+  P->tmpl = nullptr;
+  P->buf_gen++;
+  TmplState* ts = new TmplState();
+  P->tmpl = ts;
+  const int nb = P->n_blocks;
+  const cudaMemcpyKind kind = t->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (t->n_az > 0) {
+    MM_TRY(dalloc(P, &ts->az, P->N));
+    MM_TRY(dalloc(P, &ts->az_bin, P->N));
+    MM_CUDA(cudaMemcpyAsync(ts->az, t->az, P->N * sizeof(float), kind, s));
+    if (t->az_interp) MM_TRY(dalloc(P, &ts->az_frac, P->N));
+  }
+  if (t->n_hwp > 0) {
+    MM_TRY(dalloc(P, &ts->hwp, P->N));
+    MM_CUDA(cudaMemcpyAsync(ts->hwp, t->hwp, P->N * sizeof(float), kind, s));
+  }
+  // Legendre abscissa scale 2 / (n - 1) and the orthonormal rescaling sqrt((2k + 1) / n) per block
+  std::vector<double> xs(nb), xo(nb), ps((size_t)nb * std::max(t->n_poly, 1));
+  for (int b = 0; b < nb; b++) {
+    const int64_t n = P->block_off[b + 1] - P->block_off[b];
+    xs[b] = n > 1 ? 2.0 / (double)(n - 1) : 0.0;
+    xo[b] = n > 1 ? 1.0 : 0.0;
+    for (int q = 0; q < t->n_poly; q++) ps[(size_t)b * t->n_poly + q] = n > 0 ? std::sqrt((2.0 * q + 1.0) / (double)n) : 0.0;
+  }
+  MM_TRY(dalloc(P, &ts->xscale, nb));
+  MM_TRY(dalloc(P, &ts->xoff, nb));
+  MM_CUDA(cudaMemcpyAsync(ts->xoff, xo.data(), nb * sizeof(double), cudaMemcpyHostToDevice, s));
+  MM_TRY(dalloc(P, &ts->pscale, ps.size()));
+  MM_TRY(dalloc(P, &ts->kinv, (size_t)nb * k * k));
+  MM_CUDA(cudaMemcpyAsync(ts->xscale, xs.data(), nb * sizeof(double), cudaMemcpyHostToDevice, s));
+  MM_CUDA(cudaMemcpyAsync(ts->pscale, ps.data(), ps.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  TmplDev& d = ts->dev;
+  d.n_poly = t->n_poly; d.n_az = t->n_az; d.n_hwp = t->n_hwp; d.interp = t->az_interp ? 1 : 0; d.k = k;
+  d.off = P->block_off_dev; d.lpix = P->lpix; d.w = P->c0_blk; d.xscale = ts->xscale; d.xoff = ts->xoff;
+  d.pscale = ts->pscale;
+  d.az = ts->az; d.hwp = ts->hwp; d.az_bin = ts->az_bin; d.az_frac = ts->az_frac; d.kinv = ts->kinv;
+  d.az_bin_w = ts->az_bin; d.az_frac_w = ts->az_frac; d.kinv_w = ts->kinv;
+  Scratch scr;
+  double *K = nullptr, *work = nullptr, *U = nullptr, *w = nullptr;
+  MM_TRY(scr.alloc(&K, (size_t)nb * k * k)); MM_TRY(scr.alloc(&work, (size_t)nb * k * k));
+  MM_TRY(scr.alloc(&U, (size_t)nb * k * k)); MM_TRY(scr.alloc(&w, (size_t)nb * k));
+  MM_CUDA(launch_tmpl_setup(d, nb, K, work, U, w, s));
+  MM_CUDA(cudaStreamSynchronize(s));
   return MM_OK;
 }
 

@@ -24,7 +24,7 @@ struct CgScalars {
   int32_t iters;
   int32_t n_true;   // FP64 true-residual evaluations
   int32_t since_rep;
-  int32_t pad_;
+  int32_t restart_req;   // FP32 path: the next residual replacement restarts from p = z
 };
 static_assert(sizeof(CgScalars) == 96, "layout");
 constexpr int kScalStrideInts = (int)(sizeof(CgScalars) / sizeof(int32_t));

@@ -140,6 +140,7 @@ struct Plan {
   void* cg = nullptr;                  // solver workspace (mm_api.cu)
   void* blk = nullptr;                 // block-CG workspace (mm_api.cu)
   void* defl = nullptr;                // two-level deflation space (mm_api.cu)
+  void* tmpl = nullptr;                // template map-making state (TmplState, mm_tmpl.cuh)
   uint64_t buf_gen = 0;                // bumped whenever a buffer a captured graph may read is reallocated
 
   size_t bytes = 0;

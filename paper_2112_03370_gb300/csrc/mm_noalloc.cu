@@ -91,6 +91,9 @@ extern "C" int mm_apply_A_noalloc(mm_plan_t plan, const double* x, double* y, in
   if (P->algo == MM_TPLZ_DIRECT)
     return fail(MM_EINVAL, "mm_apply_A_noalloc needs an FFT plan (the direct band sum needs a "
                            "time-domain buffer of N samples)");
+  if (P->tmpl)
+    return fail(MM_EINVAL, "mm_apply_A_noalloc does not apply template filters (they need a "
+                           "time-domain buffer of N samples)");
   const bool fp32 = P->precision == MM_FP32;
   const size_t elem = fp32 ? sizeof(float) : sizeof(double);
   const size_t tot = (size_t)nrhs * (size_t)P->n_obs;

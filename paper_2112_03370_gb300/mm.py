@@ -29,7 +29,13 @@ EXPORTS = ("mm_plan", "mm_plan_query", "mm_plan_destroy", "mm_apply_P", "mm_appl
            "mm_apply_Ninv", "mm_rhs", "mm_apply_A", "mm_precond", "mm_pcg_solve", "mm_last_error",
            "mm_apply_A_noalloc", "mm_block_cg_solve", "mm_ecg_solve", "mm_deflation_build", "mm_deflation_build_apriori", "mm_deflation_get",
            "mm_deflation_apply", "mm_server_create", "mm_submit", "mm_poll", "mm_wait",
-           "mm_server_destroy", "mm_estimate_bands")
+           "mm_server_destroy", "mm_estimate_bands", "mm_templates_set")
+
+
+class TemplatesDesc(ctypes.Structure):
+    _fields_ = [("n_poly", ctypes.c_int32), ("n_az", ctypes.c_int32), ("n_hwp", ctypes.c_int32),
+                ("az_interp", ctypes.c_int32), ("az", ctypes.c_void_p), ("hwp", ctypes.c_void_p),
+                ("inputs_on_device", ctypes.c_int32)]
 
 
 class ProblemDesc(ctypes.Structure):
@@ -89,6 +95,7 @@ def _load():
     lib.mm_deflation_build.argtypes = [vp, vp, i32, i32, vp]
     lib.mm_deflation_build_apriori.argtypes = [vp, i32, vp]
     lib.mm_estimate_bands.argtypes = [i32, i32, vp, vp, vp, i32, vp, vp, vp]
+    lib.mm_templates_set.argtypes = [vp, ctypes.POINTER(TemplatesDesc), vp]
     lib.mm_deflation_get.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp, vp, vp]
     lib.mm_deflation_apply.argtypes = [vp, vp, vp, i32, vp]
     lib.mm_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
@@ -305,6 +312,18 @@ def mm_deflation_build(plan: Plan, b: torch.Tensor, m: int, precision: int = MM_
     _dev(b, torch.float64, "b")
     _check(_lib.mm_deflation_build(ctypes.c_void_p(plan.handle), _ptr(b), m, precision,
                                    _stream_ptr(stream)))
+
+
+def mm_templates_set(plan: Plan, n_poly: int = 0, n_az: int = 0, n_hwp: int = 0, az_interp: bool = False,
+                     az: Optional[torch.Tensor] = None, hwp: Optional[torch.Tensor] = None, stream=None):
+    """Attach template classes to a lambda = 0 plan (az, hwp: float32 [N] CUDA tensors)."""
+    for name, v in (("az", az), ("hwp", hwp)):
+        if v is not None:
+            _dev(v, torch.float32, name)
+    t = TemplatesDesc(n_poly=n_poly, n_az=n_az, n_hwp=n_hwp, az_interp=1 if az_interp else 0,
+                      az=_ptr(az) if az is not None else None, hwp=_ptr(hwp) if hwp is not None else None,
+                      inputs_on_device=1)
+    _check(_lib.mm_templates_set(ctypes.c_void_p(plan.handle), ctypes.byref(t), _stream_ptr(stream)))
 
 
 def mm_estimate_bands(n_det: int, n_int: int, block_len: Sequence[int], pix: torch.Tensor, d: torch.Tensor,
