@@ -56,7 +56,8 @@ def args_parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-dets", type=int, default=16)
     p.add_argument("--workload", default="ground",
-                   choices=["ground", "batched", "satellite", "serving", "ecg", "deflation", "noise"])
+                   choices=["ground", "batched", "satellite", "serving", "ecg", "deflation", "noise",
+                            "templates"])
     p.add_argument("--nrhs", type=int, default=64, help="batched: noise realisations")
     p.add_argument("--widths", default="8,16,32,64", help="batched: block widths")
     p.add_argument("--enlarge", default="1,4,16,64", help="ecg: enlarging factors t")
@@ -550,6 +551,74 @@ def run_noise(a):
                          "sample": f"one block of {n0} samples, numpy/scipy"}}), flush=True)
 
 
+def run_templates(a):
+    """Template map-making with diagonal weights (lambda = 0) on the ground geometry (512 det x 4
+    intervals x 524,288 samples): Legendre trends (3 orders), 30 azimuth bins and 6 HWP harmonics per
+    block, the template classes of the validation in Sect. 4 with one interval per block; ground
+    pickup and an HWP-synchronous signal are injected on top of sky + 1/f noise.  Times the setup
+    (bins, T^T W T, pseudo-inverse), the RHS and a mixed-precision solve; the oracle's template
+    operator on one block is the CPU baseline."""
+    import numpy as np
+    import torch
+    import oracle as O
+    import synth
+    import paper_2112_03370_gb300.mm as mm
+    dev = torch.device("cuda")
+    cfg = synth.ground_config(n_det=a.dets, lam=0)
+    prob = synth.make_ground_problem(cfg, device=dev)
+    az, hwp = synth.ground_template_streams(cfg, device=dev)
+    prob.d += synth.template_systematics(cfg, az, hwp, seed=synth.seed_for(cfg.config_id, 11))
+    torch.cuda.synchronize()
+    plan = mm.mm_plan(prob.n_det, prob.n_int, prob.block_len.tolist(), prob.n_pix, prob.pix, prob.psi,
+                      prob.lam, prob.band.to(dev), precision=mm.MM_FP32_DF64)
+    N = plan.n_samples
+    tm = dict(n_poly=3, n_az=30, n_hwp=6)
+    mm.mm_templates_set(plan, **tm, az=az, hwp=hwp)
+    _, t_setup = _timed(lambda: mm.mm_templates_set(plan, **tm, az=az, hwp=hwp))
+    b = torch.empty(plan.n_obs, 3, dtype=torch.float64, device=dev)
+    mm.mm_rhs(plan, prob.d, b)
+    _, t_rhs = _timed(lambda: mm.mm_rhs(plan, prob.d, b))
+    x = torch.empty_like(b)
+    tol = cfg.tol
+    mm.mm_pcg_solve(plan, b, x, tol=tol, precision=mm.MM_FP32, raise_on_error=False)
+    infos, t_solve = _timed(lambda: mm.mm_pcg_solve(plan, b, x, tol=tol, precision=mm.MM_FP32,
+                                                    raise_on_error=False))
+    inf = infos[0]
+    pinf = mm.mm_pcg_solve(plan, b, x, tol=tol, precision=mm.MM_FP32, profile=True, raise_on_error=False)[0]
+    ms32 = pinf.t_apply32_ms / max(1, pinf.n_apply32)
+    ms_up = pinf.t_unpoint32_ms / max(1, pinf.n_apply32)
+    ms64 = pinf.t_apply64_ms / max(1, pinf.n_apply64)
+    # Q, U of the solution against the input sky (I carries an offset degenerate with the templates)
+    ms = prob.m_sky.to(dev)[plan.obs_to_global.long()]
+    qu_err = float(torch.sqrt(((x[:, 1:] - ms[:, 1:]) ** 2).mean()) / torch.sqrt((ms[:, 1:] ** 2).mean()))
+    # CPU baseline: the oracle's template operator on one block
+    n0 = int(prob.block_len[0])
+    nb0 = {"pix": prob.pix[:n0].cpu().numpy(), "psi": prob.psi[:n0].cpu().numpy()}
+    op0 = O.make_plan(nb0["pix"], nb0["psi"], [n0], prob.band[:1].numpy(), prob.n_pix)
+    tmo = O.Templates(**tm)
+    x0 = np.random.default_rng(0).standard_normal((op0.n_obs, 3))
+    t0 = time.perf_counter()
+    O.apply_A_templates(op0, prob.band[:1, 0].numpy(), tmo, az[:n0].cpu().numpy(), hwp[:n0].cpu().numpy(), x0)
+    t_cpu = time.perf_counter() - t0
+    up_b, filt_b, pt_b = 16, 36, 16   # un-point (lpix, w32, t write), filter, point (lpix, w32, t read)
+    print(json.dumps({
+        "workload": "templates", "metric": "TOD samples/s per PCG iteration, template map-making",
+        "value": N * inf.iters / t_solve, "unit": "samples/s", "higher_is_better": True,
+        "config": {"workload": f"ground: {prob.n_det} det x {prob.n_int} int x {cfg.n_samp} samples, "
+                               f"{cfg.side}^2 IQU, lambda 0 (diagonal weights), templates "
+                               f"n_poly {tm['n_poly']}, n_az {tm['n_az']}, n_hwp {tm['n_hwp']} "
+                               f"(K = {tmo.k} per block), ground pickup + HWPSS injected",
+                   "n_samples": N, "n_obs": plan.n_obs, "blocks": prob.n_det * prob.n_int, "tol": tol},
+        "setup_s": t_setup, "rhs_s": t_rhs, "solve_s": t_solve, "iters": inf.iters, "status": inf.status,
+        "true_rel_res": inf.true_rel_res, "qu_rel_err_vs_input_sky": qu_err,
+        "fp32_apply_ms": ms32, "fp32_unpoint_ms": ms_up, "fp32_filter_point_ms": ms32 - ms_up,
+        "fp64_apply_ms": ms64,
+        "fp32_apply_GBps_algorithmic": N * (up_b + filt_b + pt_b) / (ms32 * 1e-3) / 1e9,
+        "cpu_baseline": {"value": n0 / t_cpu, "unit": "samples/s through the template operator",
+                         "cores": 1, "kind": "oracle",
+                         "sample": f"one block of {n0} samples, numpy (dense T)"}}), flush=True)
+
+
 def run_satellite(a):
     """Satellite-like full sky: BD vs two-level (16 Ritz vectors) mixed-precision solves."""
     import torch
@@ -698,6 +767,8 @@ def main():
         run_deflation(a)
     elif a.workload == "noise":
         run_noise(a)
+    elif a.workload == "templates":
+        run_templates(a)
     else:
         run_ours(a)
 

@@ -131,7 +131,9 @@ void free_defl(DeflState* d) {
 
 void free_tmpl(TmplState* t) {
   if (!t) return;
-  dfree(t->az); dfree(t->hwp); dfree(t->az_bin); dfree(t->az_frac); dfree(t->xscale); dfree(t->xoff);
+  dfree(t->az); dfree(t->hwp); dfree(t->az_bin); dfree(t->az_frac); dfree(t->bin8); dfree(t->frac32);
+  dfree(t->fracdf); dfree(t->hwpdf);
+  dfree(t->xscale); dfree(t->xoff);
   dfree(t->pscale);
   dfree(t->kinv);
   delete t;
@@ -525,10 +527,9 @@ int df_cols(const Plan* P, int nrhs) {
   return (int)std::min<int64_t>(nrhs, k);
 }
 
-// df64 working buffers for nrhs columns (allocated outside graph capture)
-int ensure_df(Plan* P, int nrhs) {
-  if (!P->df64) return MM_OK;
-  const size_t t_elems = (size_t)df_cols(P, nrhs) * (size_t)df_stride(P);
+// df64 TOD buffer for ncols columns and df64 maps for ncols columns (allocated outside graph capture)
+int ensure_tdf(Plan* P, int ncols) {
+  const size_t t_elems = (size_t)ncols * (size_t)df_stride(P);
   if (P->tdf_cap < t_elems) {
     P->buf_gen++;
     dfree(P->tdf);
@@ -536,7 +537,10 @@ int ensure_df(Plan* P, int nrhs) {
     MM_TRY(dalloc(P, &P->tdf, t_elems));
     P->tdf_cap = t_elems;
   }
-  const size_t m_elems = (size_t)df_cols(P, nrhs) * (size_t)P->n_obs * 2;
+  return MM_OK;
+}
+int ensure_mapdf(Plan* P, int ncols) {
+  const size_t m_elems = (size_t)ncols * (size_t)P->n_obs * 2;
   if (P->mapdf_cap < m_elems) {
     P->buf_gen++;
     dfree(P->mapdf);
@@ -545,6 +549,13 @@ int ensure_df(Plan* P, int nrhs) {
     P->mapdf_cap = m_elems;
   }
   return MM_OK;
+}
+// df64 working buffers of the df64 Toeplitz operator for nrhs columns
+int ensure_df(Plan* P, int nrhs) {
+  if (P->tmpl) return ensure_mapdf(P, nrhs);
+  if (!P->df64) return MM_OK;
+  MM_TRY(ensure_tdf(P, df_cols(P, nrhs)));
+  return ensure_mapdf(P, df_cols(P, nrhs));
 }
 
 TileArgs df_args(const Plan* P) {
@@ -565,17 +576,14 @@ bool capturing(cudaStream_t s) {
 // y4 (accumulated, pre-zeroed by the caller) += A x4 with the FP64-class operators, [nrhs][n_obs][4]
 int apply64_internal(Plan* P, const double* x4, double* y4, int nrhs, cudaStream_t s,
                      const int32_t* done = nullptr, int done_stride = 0) {
-  if (P->tmpl) {   // template map-making: P^T F_T P, column by column in FP64
+  if (P->tmpl) {   // template map-making: P^T F_T P in one fused df64 kernel, from the df64 map
     const TmplState* ts = reinterpret_cast<const TmplState*>(P->tmpl);
-    if (capturing(s) && !(P->td_a && P->td_cap >= (size_t)P->N))
-      return fail(MM_EINVAL, "template buffers must be allocated before graph capture");
-    MM_TRY(ensure_td(P));
-    for (int r = 0; r < nrhs; r++) {
-      MM_CUDA(launch_unpoint64(P->lpix, P->w64, P->N, x4 + (size_t)r * P->n_obs * 4, P->td_a, s));
-      MM_CUDA(launch_tmpl_filter64(ts->dev, P->n_blocks, P->td_a, P->N, 1, s));
-      MM_CUDA(launch_point64(P->lpix, P->w64, P->N, P->td_a, y4 + (size_t)r * P->n_obs * 4, s));
-    }
-    (void)done; (void)done_stride;
+    const size_t m_elems = (size_t)nrhs * P->n_obs * 2;
+    if (capturing(s) && P->mapdf_cap < m_elems) return fail(MM_EINVAL, "df64 buffers must be allocated before graph capture");
+    MM_TRY(ensure_mapdf(P, nrhs));
+    MM_CUDA(launch_map_to_df(x4, (int64_t)nrhs * P->n_obs, P->mapdf, s));
+    MM_CUDA(launch_tmpl_apply_df(ts->dev, P->n_blocks, P->wdf, P->mapdf, P->n_obs * 2, nullptr, 0, y4, P->n_obs * 4,
+                                 nrhs, done, done_stride, s));
     return MM_OK;
   }
   if (P->df64) {
@@ -646,17 +654,11 @@ int apply32_internal(Plan* P, const float* x32, float* y32, int nrhs, cudaStream
   a.y_stride = P->n_obs * 4;
   a.done = done;
   a.done_stride = done_stride;
-  if (P->tmpl) {   // template map-making: t = P x, t <- F_T t, y += P^T t (FP32)
+  if (P->tmpl) {   // template map-making: y += P^T F_T P x in one fused kernel (FP32), no TOD buffer
     const TmplState* ts = reinterpret_cast<const TmplState*>(P->tmpl);
-    MM_TRY(ensure_t32(P, nrhs));
-    if (!P->t32 || P->t32_cap < (size_t)nrhs * (size_t)t32_stride(P))
-      return fail(MM_EINVAL, "template plans need nrhs * N * 4 bytes <= 24 GiB of un-pointed buffer");
-    MM_CUDA(launch_unpoint32(P->lpix, P->w32, P->N, x32, P->n_obs * 4, nrhs, done, done_stride, P->t32,
-                             t32_stride(P), s));
     if (mid) MM_CUDA(cudaEventRecord(mid, s));
-    MM_CUDA(launch_tmpl_filter32(ts->dev, P->n_blocks, P->t32, t32_stride(P), nrhs, done, done_stride, s));
-    MM_CUDA(launch_point32t(P->lpix, P->w32, P->N, P->t32, t32_stride(P), y32, P->n_obs * 4, nrhs, done,
-                            done_stride, s));
+    MM_CUDA(launch_tmpl_apply32(ts->dev, P->n_blocks, P->w32, x32, P->n_obs * 4, y32, P->n_obs * 4, nrhs, done,
+                                done_stride, s));
     return MM_OK;
   }
   // Un-point first at full occupancy (t = P x into a plan-owned FP32 buffer), then the tiles
@@ -1173,15 +1175,17 @@ int mm_rhs(mm_plan_t plan, const void* d, int d_is_fp32, int nrhs, double* b, vo
   MM_TRY(ensure_maps(P, nrhs, false));
   const size_t n4 = (size_t)nrhs * P->n_obs * 4;
   MM_CUDA(cudaMemsetAsync(P->map64_out, 0, n4 * sizeof(double), s));
-  if (P->tmpl) {   // template map-making: b = P^T F_T G d
+  if (P->tmpl) {   // template map-making: b = P^T F_T G d (the TOD split to df64, then one fused kernel)
     const TmplState* ts = reinterpret_cast<const TmplState*>(P->tmpl);
-    MM_TRY(ensure_td(P));
+    const int k = df_cols(P, nrhs);
+    MM_TRY(ensure_tdf(P, k));
     const size_t esz = d_is_fp32 ? sizeof(float) : sizeof(double);
-    for (int r = 0; r < nrhs; r++) {
-      const void* dr = reinterpret_cast<const char*>(d) + (size_t)r * P->N * esz;
-      MM_CUDA(launch_mask_d(P->lpix, dr, d_is_fp32, P->N, P->td_a, s));
-      MM_CUDA(launch_tmpl_filter64(ts->dev, P->n_blocks, P->td_a, P->N, 1, s));
-      MM_CUDA(launch_point64(P->lpix, P->w64, P->N, P->td_a, P->map64_out + (size_t)r * P->n_obs * 4, s));
+    for (int r0 = 0; r0 < nrhs; r0 += k) {
+      const int g = std::min(k, nrhs - r0);
+      MM_CUDA(launch_d_to_df(P->lpix, reinterpret_cast<const char*>(d) + (size_t)r0 * P->N * esz, d_is_fp32,
+                             P->N, g, P->tdf, df_stride(P), s));
+      MM_CUDA(launch_tmpl_apply_df(ts->dev, P->n_blocks, P->wdf, nullptr, 0, P->tdf, df_stride(P),
+                                   P->map64_out + (size_t)r0 * P->n_obs * 4, P->n_obs * 4, g, nullptr, 0, s));
     }
   } else if (P->algo == MM_TPLZ_DIRECT) {
     MM_TRY(ensure_td(P));
@@ -1277,7 +1281,7 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
   CgState* c = nullptr;
   MM_TRY(ensure_cg(P, nrhs, fp32, &c));
   CgWork w = make_work(P, c, nrhs, fp32, opts->tol, opts->max_iter);
-  if (P->algo == MM_TPLZ_DIRECT || P->tmpl) MM_TRY(ensure_td(P));
+  if (P->algo == MM_TPLZ_DIRECT) MM_TRY(ensure_td(P));
   if (fp32) MM_TRY(ensure_t32(P, nrhs));
   MM_TRY(ensure_df(P, nrhs));
   DeflWork dw{};
@@ -1996,12 +2000,22 @@ int mm_templates_set(mm_plan_t plan, const mm_templates_desc* t, void* stream) {
   if (t->n_az > 0) {
     MM_TRY(dalloc(P, &ts->az, P->N));
     MM_TRY(dalloc(P, &ts->az_bin, P->N));
+    MM_TRY(dalloc(P, &ts->bin8, P->N));
     MM_CUDA(cudaMemcpyAsync(ts->az, t->az, P->N * sizeof(float), kind, s));
-    if (t->az_interp) MM_TRY(dalloc(P, &ts->az_frac, P->N));
+    if (t->az_interp) {
+      MM_TRY(dalloc(P, &ts->az_frac, P->N));
+      MM_TRY(dalloc(P, &ts->frac32, P->N));
+      MM_TRY(dalloc(P, &ts->fracdf, P->N));
+    }
   }
   if (t->n_hwp > 0) {
     MM_TRY(dalloc(P, &ts->hwp, P->N));
+    MM_TRY(dalloc(P, &ts->hwpdf, P->N));
     MM_CUDA(cudaMemcpyAsync(ts->hwp, t->hwp, P->N * sizeof(float), kind, s));
+  }
+  if (!P->wdf) {   // df64 pointing weights of the FP64-class template operator
+    MM_TRY(dalloc(P, &P->wdf, P->N));
+    MM_CUDA(launch_weights_df(P->psi, P->N, P->wdf, s));
   }
   // Legendre abscissa scale 2 / (n - 1) and the orthonormal rescaling sqrt((2k + 1) / n) per block
   std::vector<double> xs(nb), xo(nb), ps((size_t)nb * std::max(t->n_poly, 1));
@@ -2020,10 +2034,13 @@ int mm_templates_set(mm_plan_t plan, const mm_templates_desc* t, void* stream) {
   MM_CUDA(cudaMemcpyAsync(ts->pscale, ps.data(), ps.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   TmplDev& d = ts->dev;
   d.n_poly = t->n_poly; d.n_az = t->n_az; d.n_hwp = t->n_hwp; d.interp = t->az_interp ? 1 : 0; d.k = k;
+  d.n_total = P->N;
   d.off = P->block_off_dev; d.lpix = P->lpix; d.w = P->c0_blk; d.xscale = ts->xscale; d.xoff = ts->xoff;
   d.pscale = ts->pscale;
   d.az = ts->az; d.hwp = ts->hwp; d.az_bin = ts->az_bin; d.az_frac = ts->az_frac; d.kinv = ts->kinv;
   d.az_bin_w = ts->az_bin; d.az_frac_w = ts->az_frac; d.kinv_w = ts->kinv;
+  d.bin8 = ts->bin8; d.frac32 = ts->frac32; d.bin8_w = ts->bin8; d.frac32_w = ts->frac32;
+  d.fracdf = ts->fracdf; d.hwpdf = ts->hwpdf; d.fracdf_w = ts->fracdf; d.hwpdf_w = ts->hwpdf;
   Scratch scr;
   double *K = nullptr, *work = nullptr, *U = nullptr, *w = nullptr;
   MM_TRY(scr.alloc(&K, (size_t)nb * k * k)); MM_TRY(scr.alloc(&work, (size_t)nb * k * k));

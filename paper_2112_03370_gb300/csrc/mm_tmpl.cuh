@@ -13,6 +13,7 @@ constexpr int kMaxHwp = 8;
 // What the template kernels read (device pointers).
 struct TmplDev {
   int n_poly, n_az, n_hwp, interp, k;
+  int64_t n_total;           // samples of the plan (N)
   const int64_t* off;        // [n_blocks + 1] block offsets
   const int32_t* lpix;       // [N] (masked samples have weight 0)
   const double* w;           // [n_blocks] diagonal weight w_b (the band's c_0)
@@ -23,9 +24,17 @@ struct TmplDev {
   const float* hwp;          // [N] HWP angle
   const int32_t* az_bin;     // [N] bin, or left interpolation node
   const double* az_frac;     // [N] weight of the right node (interpolation)
+  const uint8_t* bin8;       // [N] the same bin as uint8 (n_az <= 64), for the fused operators
+  const float* frac32;       // [N] az_frac rounded to FP32 (interpolation)
+  const float2* fracdf;      // [N] az_frac as df64 (interpolation)
+  const float4* hwpdf;       // [N] cos(phi), sin(phi) of the HWP angle as df64 (hi, lo, hi, lo)
   const double* kinv;        // [n_blocks][k][k] pseudo-inverse of T^T W T
   int32_t* az_bin_w;         // writable aliases used by the setup kernels
   double* az_frac_w;
+  uint8_t* bin8_w;
+  float* frac32_w;
+  float2* fracdf_w;
+  float4* hwpdf_w;
   double* kinv_w;
 };
 
@@ -36,6 +45,10 @@ struct TmplState {
   float* hwp = nullptr;
   int32_t* az_bin = nullptr;
   double* az_frac = nullptr;
+  uint8_t* bin8 = nullptr;
+  float* frac32 = nullptr;
+  float2* fracdf = nullptr;
+  float4* hwpdf = nullptr;
   double* xscale = nullptr;
   double* xoff = nullptr;
   double* pscale = nullptr;
@@ -44,13 +57,18 @@ struct TmplState {
 
 // bins, T^T W T and its pseudo-inverse (scratch K, work, U: [nb][k][k]; w: [nb][k])
 cudaError_t launch_tmpl_setup(TmplDev& d, int nb, double* K, double* work, double* U, double* w, cudaStream_t s);
-// t <- F_T t for nrhs columns of stride t_stride (FP32 honours per-column done flags)
-cudaError_t launch_tmpl_filter32(const TmplDev& d, int nb, float* t, int64_t t_stride, int nrhs, const int32_t* done,
-                                 int done_stride, cudaStream_t s);
-cudaError_t launch_tmpl_filter64(const TmplDev& d, int nb, double* t, int64_t t_stride, int nrhs, cudaStream_t s);
-// y (FP32 float4 maps [nrhs][n_obs][4], accumulated) += P^T t
-cudaError_t launch_point32t(const int32_t* lpix, const float2* w32, int64_t N, const float* t, int64_t t_stride,
-                            float* y4, int64_t y_stride, int nrhs, const int32_t* done, int done_stride,
-                            cudaStream_t s);
+// Fused FP32 template operator y += P^T F_T P x for nrhs float4 maps ([nrhs][n_obs][4], stride in
+// floats), columns with a nonzero done flag skipped: one 8-CTA cluster per block, no TOD buffer.
+cudaError_t launch_tmpl_apply32(const TmplDev& d, int nb, const float2* w32, const float* x32, int64_t x_stride,
+                                float* y32, int64_t y_stride, int nrhs, const int32_t* done, int done_stride,
+                                cudaStream_t s);
+// Fused FP64-class (df64) template operator into FP64 maps y [nrhs][n_obs][4] (accumulated, stride in
+// doubles), columns with a nonzero done flag skipped.  wdf: (cos 2psi, sin 2psi) as df64 per sample.
+// Map mode (tdf == nullptr): y += P^T F_T P x with x as the df64 map mdf [nrhs][n_obs][2] float4
+// (I, Q | U, 0), m_stride4 float4 per column.  TOD mode: y += P^T F_T t with t the df64 TOD tdf
+// [nrhs][t_stride] float2 (the right-hand side P^T F_T G d).
+cudaError_t launch_tmpl_apply_df(const TmplDev& d, int nb, const float4* wdf, const float4* mdf, int64_t m_stride4,
+                                 const float2* tdf, int64_t t_stride, double* y, int64_t y_stride, int nrhs,
+                                 const int32_t* done, int done_stride, cudaStream_t s);
 
 }  // namespace mm

@@ -176,6 +176,67 @@ def flag_gaps(pix: torch.Tensor, frac: float, seed: int, run: int = 37) -> torch
     return out
 
 
+def ground_template_streams(cfg: GroundConfig, device="cpu", det_range: Optional[tuple] = None,
+                            az_span_deg: float = 10.0):
+    """Boresight azimuth and HWP angle per sample of the ground raster (det-major like
+    ``ground_pointing``): float32 [N] each.
+
+    The azimuth follows the raster's fast coordinate across a constant-elevation sweep of
+    ``az_span_deg`` degrees (the same for every detector); the HWP angle is 2 pi hwp_hz t wrapped to
+    [0, 2 pi), the rotation that ``ground_pointing`` folds into psi.
+    """
+    d0, d1 = det_range if det_range is not None else (0, cfg.n_det)
+    dev = torch.device(device)
+    n = cfg.n_samp
+    sweep = int(round(cfg.side / cfg.speed))
+    i = torch.arange(n, device=dev, dtype=torch.int64)
+    s = i // sweep
+    u = torch.floor((i % sweep).to(torch.float64) * cfg.speed)
+    xb = torch.where(s % 2 == 0, u, (cfg.side - 1) - u)
+    az_blk = (180.0 + az_span_deg * xb / (cfg.side - 1)).to(torch.float32)
+    two_pi = 2.0 * math.pi
+    hwp_int = []
+    for k in range(cfg.n_int):
+        t = (k * n + i).to(torch.float64) / cfg.fs
+        h = torch.remainder(two_pi * cfg.hwp_hz * t, two_pi).to(torch.float32)
+        hwp_int.append(torch.where(h >= two_pi, torch.zeros_like(h), h))
+    hwp_det = torch.cat(hwp_int)
+    n_det = d1 - d0
+    return az_blk.repeat(n_det * cfg.n_int), hwp_det.repeat(n_det)
+
+
+def template_systematics(cfg: GroundConfig, az: torch.Tensor, hwp: torch.Tensor, seed: int,
+                         n_harm: int = 6, bin_deg: float = 0.33) -> torch.Tensor:
+    """Ground pickup and HWP-synchronous signal per sample (float64 [N], det-major blocks of n_samp):
+
+    * ground: a step function of azimuth, g_i = 1 + 0.01 i in bins of ``bin_deg`` from the
+      sweep's lowest azimuth (the same ground map for every detector);
+    * HWP: sum_n A_n (1 + eps t) cos(n phi) + B_n (1 + eps t) sin(n phi), n = 1..n_harm, with A_n,
+      B_n ~ N(0.1, 0.001) per detector and a 1 % drift per 1000 s (t from the block's start).
+    The shapes follow the template-marginalisation validation of Sect. 4 (Eqs. of the SSS and
+    HWPSS signals); the amplitudes are in the sky's units.
+    """
+    n = cfg.n_samp
+    nb = az.numel() // n
+    dev = az.device
+    a64 = az.to(torch.float64).view(nb, n)
+    lo = a64.min(dim=1, keepdim=True).values
+    g = 1.0 + 0.01 * torch.floor((a64 - lo) / bin_deg)
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    amp = (0.1 + 0.001 * torch.randn(cfg.n_det, 2, n_harm, generator=gen, dtype=torch.float64)).to(dev)
+    t = torch.arange(n, dtype=torch.float64, device=dev) / cfg.fs
+    drift = 1.0 + 0.01 * t / 1000.0
+    out = g.reshape(-1).clone()
+    phi = hwp.to(torch.float64).view(nb, n)
+    for b in range(nb):
+        det = b // cfg.n_int
+        h = torch.zeros(n, dtype=torch.float64, device=dev)
+        for m in range(1, n_harm + 1):
+            h += amp[det, 0, m - 1] * torch.cos(m * phi[b]) + amp[det, 1, m - 1] * torch.sin(m * phi[b])
+        out[b * n:(b + 1) * n] += drift * h
+    return out
+
+
 @dataclass
 class SatelliteConfig:
     """Precessing spin scan on the full sky, equal-area lat-long pixels (rings in z x phi)."""

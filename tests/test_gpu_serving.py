@@ -65,16 +65,21 @@ def test_alone_equals_mix_and_oracle(probs):
 
 
 def test_request_admitted_while_another_runs(probs):
+    # the long request runs a fixed 3000 iterations (unreachable tolerance), far longer than the
+    # 50 ms after which the short one arrives, so the two always share launches
     m = mm()
     srv = m.Server(max_slots=4)
-    big = submit(srv, probs[1])
-    time.sleep(0.01)
+    p = probs[1]
+    long_rid = srv.submit(p["n_det"], p["n_int"], p["block_len"].tolist(), p["n_pix"], p["pix"], p["psi"],
+                          p["lam"], p["band"], p["d"], tol=1e-30, max_iter=3000)
+    time.sleep(0.05)
     small = submit(srv, probs[0])
     ms, i_small = srv.wait(small)
-    mb, i_big = srv.wait(big)
+    mb, i_long = srv.wait(long_rid, raise_on_error=False)
     srv.close()
-    assert i_small.status == 0 and i_big.status == 0
-    assert i_small.batch >= 2 and i_big.batch >= 2            # they ran side by side
+    assert i_small.status == 0 and i_small.true_rel_res < TOL
+    assert i_long.status == m.MM_ENOTCONV and i_long.iters == 3000
+    assert i_small.batch >= 2 and i_long.batch >= 2           # they ran side by side
 
 
 def test_admission_respects_budget_and_bad_request(probs):
