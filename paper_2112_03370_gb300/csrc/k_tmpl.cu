@@ -27,48 +27,6 @@ namespace cg = cooperative_groups;
 
 constexpr int kTNT = 256;
 
-// Legendre values P_k(x) sqrt((2k + 1) / n), k < n_poly (<= kMaxPoly), into constant-indexed p[]
-template <typename T>
-__device__ __forceinline__ void legendre(const TmplDev& d, int b, int64_t tau, T (&p)[kMaxPoly]) {
-  T x;
-  if constexpr (sizeof(T) == 4) x = (float)tau * (float)d.xscale[b] - (float)d.xoff[b];
-  else x = (double)tau * d.xscale[b] - d.xoff[b];
-  T pm = T(1), pc = x;
-#pragma unroll
-  for (int k = 0; k < kMaxPoly; k++) {
-    if (k >= d.n_poly) break;
-    T v;
-    if (k == 0) {
-      v = T(1);
-    } else if (k == 1) {
-      v = x;
-    } else {
-      v = ((T)(2 * k - 1) * x * pc - (T)(k - 1) * pm) / (T)k;
-      pm = pc;
-      pc = v;
-    }
-    p[k] = v * (T)d.pscale[b * d.n_poly + k];
-  }
-}
-
-// cos(k phi), sin(k phi), k = 1..n_hwp (<= kMaxHwp), by the angle-addition recurrence
-template <typename T>
-__device__ __forceinline__ void harmonics(const TmplDev& d, int64_t g, T (&hc)[kMaxHwp], T (&hs)[kMaxHwp]) {
-  T s1, c1;
-  if constexpr (sizeof(T) == 4) sincosf(d.hwp[g], &s1, &c1);
-  else sincos((double)d.hwp[g], &s1, &c1);
-  T ck = c1, sk = s1;
-#pragma unroll
-  for (int k = 0; k < kMaxHwp; k++) {
-    if (k >= d.n_hwp) break;
-    hc[k] = ck;
-    hs[k] = sk;
-    const T cn = ck * c1 - sk * s1, sn = sk * c1 + ck * s1;
-    ck = cn;
-    sk = sn;
-  }
-}
-
 // per block: lo/hi of az over kept samples, then bins / interpolation fractions of every sample (FP64)
 __global__ void k_tmpl_bins(const int32_t* __restrict__ lpix, const float* __restrict__ az,
                             const int64_t* __restrict__ off, int n_az, int interp, int32_t* __restrict__ bin,
@@ -125,115 +83,6 @@ __global__ void k_tmpl_bins(const int32_t* __restrict__ lpix, const float* __res
   }
 }
 
-// K_b = T^T W T in FP64: 32-sample tiles staged in shared memory, each thread owns a few (i <= j)
-constexpr int kGramTile = 32;
-constexpr int kGramPairs = (kMaxTmpl * (kMaxTmpl + 1) / 2 + kTNT - 1) / kTNT;
-__global__ void __launch_bounds__(kTNT) k_tmpl_gram(TmplDev d, double* __restrict__ K) {
-  __shared__ double rows[kGramTile][kMaxTmpl + 1];
-  __shared__ double wsm[kGramTile];
-  const int b = blockIdx.x;
-  const int k = d.k;
-  const int64_t lo = d.off[b], hi = d.off[b + 1];
-  const double wb = d.w[b];
-  const int npairs = k * (k + 1) / 2;
-  int pi[kGramPairs], pj[kGramPairs];
-  double acc[kGramPairs];
-#pragma unroll
-  for (int r = 0; r < kGramPairs; r++) {
-    acc[r] = 0.0;
-    int p = threadIdx.x + r * kTNT, i = 0;
-    if (p < npairs) {
-      while (p >= k - i) {   // row i of the upper triangle holds k - i pairs
-        p -= k - i;
-        i++;
-      }
-    }
-    pi[r] = i;
-    pj[r] = i + p;
-  }
-  for (int64_t base = lo; base < hi; base += kGramTile) {
-    if (threadIdx.x < kGramTile) {
-      const int64_t g = base + threadIdx.x;
-      double* row = rows[threadIdx.x];
-      for (int j = 0; j < k; j++) row[j] = 0.0;
-      if (g < hi) {
-        if (d.n_poly > 0) {
-          double p[kMaxPoly];
-          legendre<double>(d, b, g - lo, p);
-#pragma unroll
-          for (int q = 0; q < kMaxPoly; q++)
-            if (q < d.n_poly) row[q] = p[q];
-        }
-        if (d.n_az > 0) {
-          const int i = d.az_bin[g];
-          if (d.interp) {
-            const double fr = d.az_frac[g];
-            row[d.n_poly + i] = 1.0 - fr;
-            if (i + 1 < d.n_az) row[d.n_poly + i + 1] = fr;
-          } else {
-            row[d.n_poly + i] = 1.0;
-          }
-        }
-        if (d.n_hwp > 0) {
-          double hc[kMaxHwp], hs[kMaxHwp];
-          harmonics<double>(d, g, hc, hs);
-          const int h0 = d.n_poly + d.n_az;
-#pragma unroll
-          for (int q = 0; q < kMaxHwp; q++)
-            if (q < d.n_hwp) {
-              row[h0 + 2 * q] = hc[q];
-              row[h0 + 2 * q + 1] = hs[q];
-            }
-        }
-        wsm[threadIdx.x] = d.lpix[g] >= 0 ? wb : 0.0;
-      } else {
-        wsm[threadIdx.x] = 0.0;
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kGramPairs; r++) {
-      if (threadIdx.x + r * kTNT < npairs) {
-        double s = acc[r];
-        for (int t = 0; t < kGramTile; t++) s += wsm[t] * rows[t][pi[r]] * rows[t][pj[r]];
-        acc[r] = s;
-      }
-    }
-    __syncthreads();
-  }
-  double* Kb = K + (int64_t)b * k * k;
-#pragma unroll
-  for (int r = 0; r < kGramPairs; r++) {
-    if (threadIdx.x + r * kTNT < npairs) {
-      Kb[pi[r] * k + pj[r]] = acc[r];
-      Kb[pj[r] * k + pi[r]] = acc[r];
-    }
-  }
-}
-
-// per block (one thread): Kinv_b = pseudo-inverse of K_b, eigenvalues below rcond * max |w| dropped
-__global__ void k_tmpl_pinv(const double* __restrict__ K, int k, int nb, double rcond, double* __restrict__ work,
-                            double* __restrict__ U, double* __restrict__ w, double* __restrict__ Kinv) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nb) return;
-  const double* Kb = K + (int64_t)b * k * k;
-  double* A = work + (int64_t)b * k * k;
-  double* Ub = U + (int64_t)b * k * k;
-  double* wb = w + (int64_t)b * k;
-  double* out = Kinv + (int64_t)b * k * k;
-  for (int i = 0; i < k * k; i++) A[i] = Kb[i];
-  jacobi_eig(A, k, wb, Ub);
-  double mx = 0.0;
-  for (int i = 0; i < k; i++) mx = fmax(mx, fabs(wb[i]));
-  for (int i = 0; i < k; i++)
-    for (int j = 0; j < k; j++) {
-      double s = 0.0;
-      for (int l = 0; l < k; l++)
-        if (fabs(wb[l]) > rcond * mx) s += Ub[i * k + l] * Ub[j * k + l] / wb[l];
-      out[i * k + j] = s;
-    }
-}
-
 // ---- fused FP32 template operator -------------------------------------------------------------
 // One cluster of kTC CTAs per block; CTA r streams the r-th contiguous slice of the block twice.
 // Pass 1 un-points x (t = P x, the map gathered from L2), forms v = w_b t and accumulates the slice's
@@ -242,41 +91,78 @@ __global__ void k_tmpl_pinv(const double* __restrict__ K, int k, int nb, double 
 // c = Kinv a from them in the same order, and pass 2 recomputes t and scatters w_b (t - T c) into y.
 constexpr int kTC = 8;     // CTAs per block
 constexpr int kTA = 256;   // threads per CTA
+constexpr int kU = 4;      // samples per thread and step of the FP32 operator (loads in flight)
+constexpr int kUdf = 2;    // the same for the df64 operator
 
-// unscaled Legendre P_0..P_{n-1}(x) by k P_k = (2k - 1) x P_{k-1} - (k - 1) P_{k-2}
+// Unscaled Legendre P_k(x), k < n, by k P_k = (2k - 1) x P_{k-1} - (k - 1) P_{k-2}, generated and
+// consumed on the fly: acc[k] += P_k(x) v (pass 1), or the dot product sum_k c[k] P_k(x) (pass 2).
 template <int NP>
-__device__ __forceinline__ void legendre_raw(float x, int n, float (&p)[NP]) {
+__device__ __forceinline__ void legendre_acc(float x, int n, float v, float (&acc)[NP]) {
   float pm = 1.f, pc = x;
 #pragma unroll
   for (int k = 0; k < NP; k++) {
     if (k >= n) break;
     if (k == 0) {
-      p[k] = 1.f;
+      acc[k] += v;
     } else if (k == 1) {
-      p[k] = x;
+      acc[k] += x * v;
     } else {
-      const float v = ((float)(2 * k - 1) / (float)k) * x * pc - ((float)(k - 1) / (float)k) * pm;
+      const float pn = ((float)(2 * k - 1) / (float)k) * x * pc - ((float)(k - 1) / (float)k) * pm;
       pm = pc;
-      pc = v;
-      p[k] = v;
+      pc = pn;
+      acc[k] += pn * v;
     }
   }
 }
+template <int NP>
+__device__ __forceinline__ float legendre_dot(float x, int n, const float (&c)[NP]) {
+  float pm = 1.f, pc = x, s = 0.f;
+#pragma unroll
+  for (int k = 0; k < NP; k++) {
+    if (k >= n) break;
+    if (k == 0) {
+      s = c[0];
+    } else if (k == 1) {
+      s += c[1] * x;
+    } else {
+      const float pn = ((float)(2 * k - 1) / (float)k) * x * pc - ((float)(k - 1) / (float)k) * pm;
+      pm = pc;
+      pc = pn;
+      s += c[k] * pn;
+    }
+  }
+  return s;
+}
 
+// cos(k phi), sin(k phi), k = 1..n, by the angle-addition recurrence from cos(phi), sin(phi) (FP32
+// roundings of the FP64 values, precomputed), generated and consumed on the fly: ac[k-1] += cos(k phi) v, as[k-1] += sin(k phi) v, or sum_k cc[k-1] cos(k phi) + cs[k-1] sin(k phi)
 template <int NH>
-__device__ __forceinline__ void harmonics32(float phi, int n, float (&hc)[NH], float (&hs)[NH]) {
-  float s1, c1;
-  sincosf(phi, &s1, &c1);
+__device__ __forceinline__ void harmonics_acc(float2 cs1, int n, float v, float (&ac)[NH], float (&as)[NH]) {
+  const float c1 = cs1.x, s1 = cs1.y;
   float ck = c1, sk = s1;
 #pragma unroll
   for (int k = 0; k < NH; k++) {
     if (k >= n) break;
-    hc[k] = ck;
-    hs[k] = sk;
+    ac[k] += ck * v;
+    as[k] += sk * v;
     const float cn = ck * c1 - sk * s1, sn = sk * c1 + ck * s1;
     ck = cn;
     sk = sn;
   }
+}
+template <int NH>
+__device__ __forceinline__ float harmonics_dot(float2 cs1, int n, const float (&cc)[NH], const float (&cs)[NH]) {
+  const float c1 = cs1.x, s1 = cs1.y;
+  float ck = c1, sk = s1, s = 0.f;
+#pragma unroll
+  for (int k = 0; k < NH; k++) {
+    if (k >= n) break;
+    s += cc[k] * ck + cs[k] * sk;
+    const float cn = ck * c1 - sk * s1, sn = sk * c1 + ck * s1;
+    ck = cn;
+    sk = sn;
+  }
+  return s;
 }
 
 // Warp-collective: the lanes' (bin, value) pairs summed per run of equal bins (lanes are consecutive
@@ -337,6 +223,13 @@ __global__ void __cluster_dims__(kTC, 1, 1) __launch_bounds__(kTA)
   const float wb = (float)d.w[b];
   const float xs = (float)d.xscale[b], xo = (float)d.xoff[b];
   const float4* xr = x + rhs * x_stride4;
+  // slice-relative 32-bit indexing (blocks are shorter than 2^31 samples)
+  const int m = (int)(s_hi - s_lo), tau0 = (int)(s_lo - lo);
+  const int32_t* lp = d.lpix + s_lo;
+  const float2* wp = w32 + s_lo;
+  const float2* hp = nh > 0 ? d.hwp32 + s_lo : nullptr;
+  const uint8_t* bp = naz > 0 ? d.bin8 + s_lo : nullptr;
+  const float* fp = (naz > 0 && d.interp) ? d.frac32 + s_lo : nullptr;
   for (int j = tid; j < kMaxTmpl; j += kTA) a_sm[j] = 0.0;
   __syncthreads();
 
@@ -346,40 +239,39 @@ __global__ void __cluster_dims__(kTC, 1, 1) __launch_bounds__(kTA)
   for (int q = 0; q < NP; q++) ap[q] = 0.f;
 #pragma unroll
   for (int q = 0; q < NH; q++) ahc[q] = ahs[q] = 0.f;
-  for (int64_t g0 = s_lo + (tid - lane); g0 < s_hi; g0 += kTA) {   // warp-uniform trip count
-    const int64_t g = g0 + lane;
-    float v = 0.f, fr = 0.f;
-    int bin = -1;
-    if (g < s_hi) {
-      const int32_t p = d.lpix[g];
-      if (p >= 0) {
-        const float2 cs = w32[g];
-        const float4 m = xr[p];
-        v = wb * (m.x + cs.x * m.y + cs.y * m.z);
-        if (np > 0) {
-          float pl[NP];
-          legendre_raw<NP>((float)(g - lo) * xs - xo, np, pl);
+  // warp w takes kU runs of 32 consecutive samples per step (warp-uniform trip count); the loads of
+  // all kU samples are issued before their map gathers, and those before any arithmetic
+  for (int i0 = warp * 32 * kU; i0 < m; i0 += kTA * kU) {
+    int32_t pp[kU];
+    float2 cs[kU], hw[kU];
+    float fr[kU];
+    int bn[kU];
 #pragma unroll
-          for (int q = 0; q < NP; q++)
-            if (q < np) ap[q] += pl[q] * v;
-        }
-        if (nh > 0) {
-          float hc[NH], hs[NH];
-          harmonics32<NH>(d.hwp[g], nh, hc, hs);
-#pragma unroll
-          for (int q = 0; q < NH; q++)
-            if (q < nh) {
-              ahc[q] += hc[q] * v;
-              ahs[q] += hs[q] * v;
-            }
-        }
-        if (naz > 0) {
-          bin = d.bin8[g];
-          if (d.interp) fr = d.frac32[g];
-        }
-      }
+    for (int u = 0; u < kU; u++) {
+      const int i = i0 + u * 32 + lane;
+      const bool in = i < m;
+      pp[u] = in ? lp[i] : -1;
+      cs[u] = in ? wp[i] : make_float2(0.f, 0.f);
+      hw[u] = (in && nh > 0) ? hp[i] : make_float2(1.f, 0.f);
+      bn[u] = (in && naz > 0) ? (int)bp[i] : -1;
+      fr[u] = (in && naz > 0 && d.interp) ? fp[i] : 0.f;
     }
-    if (naz > 0) az_run_sums(a_sm + c0, bin, v, fr, d.interp, naz, lane);
+    float4 m[kU];
+#pragma unroll
+    for (int u = 0; u < kU; u++) m[u] = pp[u] >= 0 ? xr[pp[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < kU; u++) {
+      const int i = i0 + u * 32 + lane;
+      float v = 0.f;
+      int bin = -1;
+      if (pp[u] >= 0) {
+        v = wb * (m[u].x + cs[u].x * m[u].y + cs[u].y * m[u].z);
+        if (np > 0) legendre_acc<NP>((float)(tau0 + i) * xs - xo, np, v, ap);
+        if (nh > 0) harmonics_acc<NH>(hw[u], nh, v, ahc, ahs);
+        bin = bn[u];
+      }
+      if (naz > 0) az_run_sums(a_sm + c0, bin, v, fr[u], d.interp, naz, lane);
+    }
   }
   // register terms: warp sums in FP64, then across warps
 #pragma unroll
@@ -440,38 +332,40 @@ __global__ void __cluster_dims__(kTC, 1, 1) __launch_bounds__(kTA)
 
   // ---- pass 2: y += P^T w_b (t - T c) ----
   float4* yr = y + rhs * y_stride4;
-  for (int64_t g = s_lo + tid; g < s_hi; g += kTA) {
-    const int32_t p = d.lpix[g];
-    if (p < 0) continue;
-    const float2 cs = w32[g];
-    const float4 m = xr[p];
-    const float t = m.x + cs.x * m.y + cs.y * m.z;
-    float sv = 0.f;
-    if (np > 0) {
-      float pl[NP];
-      legendre_raw<NP>((float)(g - lo) * xs - xo, np, pl);
+  for (int i0 = warp * 32 * kU; i0 < m; i0 += kTA * kU) {
+    int32_t pp[kU];
+    float2 cs[kU], hw[kU];
+    float fr[kU];
+    int bn[kU];
 #pragma unroll
-      for (int q = 0; q < NP; q++)
-        if (q < np) sv += cp[q] * pl[q];
+    for (int u = 0; u < kU; u++) {
+      const int i = i0 + u * 32 + lane;
+      const bool in = i < m;
+      pp[u] = in ? lp[i] : -1;
+      cs[u] = in ? wp[i] : make_float2(0.f, 0.f);
+      hw[u] = (in && nh > 0) ? hp[i] : make_float2(1.f, 0.f);
+      bn[u] = (in && naz > 0) ? (int)bp[i] : 0;
+      fr[u] = (in && naz > 0 && d.interp) ? fp[i] : 0.f;
     }
-    if (naz > 0) {
-      const int i = d.bin8[g];
-      if (d.interp) {
-        const float fr = d.frac32[g];
-        sv += (1.f - fr) * caz[i] + fr * caz[i + 1];   // caz[naz] = 0 covers i + 1 = naz
-      } else {
-        sv += caz[i];
+    float4 m[kU];
+#pragma unroll
+    for (int u = 0; u < kU; u++) m[u] = pp[u] >= 0 ? xr[pp[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < kU; u++) {
+      if (pp[u] < 0) continue;
+      const int i = i0 + u * 32 + lane;
+      const float t = m[u].x + cs[u].x * m[u].y + cs[u].y * m[u].z;
+      float sv = 0.f;
+      if (np > 0) sv += legendre_dot<NP>((float)(tau0 + i) * xs - xo, np, cp);
+      if (naz > 0) {
+        const int i = bn[u];
+        if (d.interp) sv += (1.f - fr[u]) * caz[i] + fr[u] * caz[i + 1];   // caz[naz] = 0 covers i + 1 = naz
+        else sv += caz[i];
       }
+      if (nh > 0) sv += harmonics_dot<NH>(hw[u], nh, chc, chs);
+      const float yv = wb * (t - sv);
+      atomicAdd(yr + pp[u], make_float4(yv, cs[u].x * yv, cs[u].y * yv, 0.f));
     }
-    if (nh > 0) {
-      float hc[NH], hs[NH];
-      harmonics32<NH>(d.hwp[g], nh, hc, hs);
-#pragma unroll
-      for (int q = 0; q < NH; q++)
-        if (q < nh) sv += chc[q] * hc[q] + chs[q] * hs[q];
-    }
-    const float yv = wb * (t - sv);
-    atomicAdd(yr + p, make_float4(yv, cs.x * yv, cs.y * yv, 0.f));
   }
   asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory");
 }
@@ -505,42 +399,79 @@ __device__ __forceinline__ df df_mul_f(df a, float m) {
   return fast_two_sum(p, e);
 }
 
-// Q_k(x) = k! P_k(x), k < n: Q_k = (2k - 1) x Q_{k-1} - (k - 1)^2 Q_{k-2}
+// Q_k(x) = k! P_k(x), k < n, by Q_k = (2k - 1) x Q_{k-1} - (k - 1)^2 Q_{k-2} (exact FP32 multipliers),
+// generated and consumed on the fly: acc[k] += Q_k v, or sum_k c[k] Q_k
 template <int NP>
-__device__ __forceinline__ void legendre_q_df(df x, int n, df (&q)[NP]) {
+__device__ __forceinline__ void legendre_q_acc(df x, int n, df v, df (&acc)[NP]) {
   df qm = df_make(1.f, 0.f), qc = x;
 #pragma unroll
   for (int k = 0; k < NP; k++) {
     if (k >= n) break;
     if (k == 0) {
-      q[k] = df_make(1.f, 0.f);
+      acc[k] = acc[k] + v;
     } else if (k == 1) {
-      q[k] = x;
+      acc[k] = df_fma(x, v, acc[k]);
     } else {
-      const df v = df_prod_sum(df_mul_f(x, (float)(2 * k - 1)), qc, df_make(-(float)((k - 1) * (k - 1)), 0.f), qm);
+      const df qn = df_prod_sum(df_mul_f(x, (float)(2 * k - 1)), qc, df_make(-(float)((k - 1) * (k - 1)), 0.f), qm);
       qm = qc;
-      qc = v;
-      q[k] = v;
+      qc = qn;
+      acc[k] = df_fma(qn, v, acc[k]);
     }
   }
 }
+template <int NP>
+__device__ __forceinline__ df legendre_q_dot(df x, int n, const df (&c)[NP], df s) {
+  df qm = df_make(1.f, 0.f), qc = x;
+#pragma unroll
+  for (int k = 0; k < NP; k++) {
+    if (k >= n) break;
+    if (k == 0) {
+      s = s + c[0];
+    } else if (k == 1) {
+      s = df_fma(c[1], x, s);
+    } else {
+      const df qn = df_prod_sum(df_mul_f(x, (float)(2 * k - 1)), qc, df_make(-(float)((k - 1) * (k - 1)), 0.f), qm);
+      qm = qc;
+      qc = qn;
+      s = df_fma(c[k], qn, s);
+    }
+  }
+  return s;
+}
 
-// cos(k phi), sin(k phi), k = 1..n, from cos(phi), sin(phi) by complex multiplication
+// cos(k phi), sin(k phi), k = 1..n, from cos(phi), sin(phi) by complex multiplication, generated and
+// consumed on the fly
 template <int NH>
-__device__ __forceinline__ void harmonics_df(float4 cs1, int n, df (&hc)[NH], df (&hs)[NH]) {
+__device__ __forceinline__ void harmonics_df_acc(float4 cs1, int n, df v, df (&ac)[NH], df (&as)[NH]) {
   const df c1 = df_make(cs1.x, cs1.y), s1 = df_make(cs1.z, cs1.w);
   df ck = c1, sk = s1;
 #pragma unroll
   for (int k = 0; k < NH; k++) {
     if (k >= n) break;
-    hc[k] = ck;
-    hs[k] = sk;
+    ac[k] = df_fma(ck, v, ac[k]);
+    as[k] = df_fma(sk, v, as[k]);
     if (k + 1 < n) {
       const df cn = df_prod_sum(ck, c1, -sk, s1), sn = df_prod_sum(sk, c1, ck, s1);
       ck = cn;
       sk = sn;
     }
   }
+}
+template <int NH>
+__device__ __forceinline__ df harmonics_df_dot(float4 cs1, int n, const df (&cc)[NH], const df (&cs)[NH], df s) {
+  const df c1 = df_make(cs1.x, cs1.y), s1 = df_make(cs1.z, cs1.w);
+  df ck = c1, sk = s1;
+#pragma unroll
+  for (int k = 0; k < NH; k++) {
+    if (k >= n) break;
+    s = s + df_prod_sum(cc[k], ck, cs[k], sk);
+    if (k + 1 < n) {
+      const df cn = df_prod_sum(ck, c1, -sk, s1), sn = df_prod_sum(sk, c1, ck, s1);
+      ck = cn;
+      sk = sn;
+    }
+  }
+  return s;
 }
 
 __device__ __forceinline__ df shfl_down_df(df v, int off) {
@@ -609,14 +540,42 @@ __global__ void __cluster_dims__(kTC, 1, 1) __launch_bounds__(kTA)
   for (int j = tid; j < kMaxTmpl; j += kTA) a_sm[j] = 0.0;
   __syncthreads();
 
-  auto tod = [&](int64_t g, int32_t p, float4 w4) -> df {
+  // the un-pointed value of sample g from its loaded parts: the df64 TOD (TOD mode) or the map's I, Q,
+  // U at p with the pointing weights w4
+  auto unpoint = [&](float2 tv, float4 w4, float4 iq, float4 u4) -> df {
     if constexpr (TOD) {
-      const float2 v = tr[g];
-      return df_make(v.x, v.y);
+      return df_make(tv.x, tv.y);
     } else {
-      const float4 iq = mr[2 * (int64_t)p], u4 = mr[2 * (int64_t)p + 1];
       return df_make(iq.x, iq.y) +
              df_prod_sum(df_make(w4.x, w4.y), df_make(iq.z, iq.w), df_make(w4.z, w4.w), df_make(u4.x, u4.y));
+    }
+  };
+  // loads of kUdf samples of the warp's step (sample g0 + u 32 + lane), then their map gathers
+  struct Ld {
+    int32_t p;
+    float4 w4, h4, iq, u4;
+    float2 tv, fr;
+    int bin;
+  };
+  auto load = [&](int64_t g0, Ld (&L)[kUdf], bool need_w) {
+#pragma unroll
+    for (int u = 0; u < kUdf; u++) {
+      const int64_t g = g0 + u * 32 + lane;
+      const bool in = g < s_hi;
+      L[u].p = in ? d.lpix[g] : -1;
+      L[u].w4 = (in && need_w) ? wdf[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+      L[u].h4 = (in && nh > 0) ? d.hwpdf[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+      L[u].bin = (in && naz > 0) ? (int)d.bin8[g] : 0;
+      L[u].fr = (in && naz > 0 && d.interp) ? d.fracdf[g] : make_float2(0.f, 0.f);
+      if constexpr (TOD) L[u].tv = in ? tr[g] : make_float2(0.f, 0.f);
+    }
+    if constexpr (!TOD) {
+#pragma unroll
+      for (int u = 0; u < kUdf; u++) {
+        const int32_t p = L[u].p;
+        L[u].iq = p >= 0 ? mr[2 * (int64_t)p] : make_float4(0.f, 0.f, 0.f, 0.f);
+        L[u].u4 = p >= 0 ? mr[2 * (int64_t)p + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     }
   };
 
@@ -626,42 +585,22 @@ __global__ void __cluster_dims__(kTC, 1, 1) __launch_bounds__(kTA)
   for (int q = 0; q < NP; q++) aq[q] = df_make(0.f, 0.f);
 #pragma unroll
   for (int q = 0; q < NH; q++) ahc[q] = ahs[q] = df_make(0.f, 0.f);
-  for (int64_t g0 = s_lo + (tid - lane); g0 < s_hi; g0 += kTA) {
-    const int64_t g = g0 + lane;
-    df v = df_make(0.f, 0.f), fr = df_make(0.f, 0.f);
-    int bin = -1;
-    if (g < s_hi) {
-      const int32_t p = d.lpix[g];
-      if (p >= 0) {
-        const float4 w4 = TOD ? make_float4(0.f, 0.f, 0.f, 0.f) : wdf[g];
-        v = wb * tod(g, p, w4);
-        if (np > 0) {
-          df ql[NP];
-          legendre_q_df<NP>(legendre_x(g - lo, nm1, inv), np, ql);
+  for (int64_t g0 = s_lo + (int64_t)warp * 32 * kUdf; g0 < s_hi; g0 += (int64_t)kTA * kUdf) {
+    Ld L[kUdf];
+    load(g0, L, !TOD);
 #pragma unroll
-          for (int q = 0; q < NP; q++)
-            if (q < np) aq[q] = df_fma(ql[q], v, aq[q]);
-        }
-        if (nh > 0) {
-          df hc[NH], hs[NH];
-          harmonics_df<NH>(d.hwpdf[g], nh, hc, hs);
-#pragma unroll
-          for (int q = 0; q < NH; q++)
-            if (q < nh) {
-              ahc[q] = df_fma(hc[q], v, ahc[q]);
-              ahs[q] = df_fma(hs[q], v, ahs[q]);
-            }
-        }
-        if (naz > 0) {
-          bin = d.bin8[g];
-          if (d.interp) {
-            const float2 f = d.fracdf[g];
-            fr = df_make(f.x, f.y);
-          }
-        }
+    for (int u = 0; u < kUdf; u++) {
+      const int64_t g = g0 + u * 32 + lane;
+      df v = df_make(0.f, 0.f);
+      int bin = -1;
+      if (L[u].p >= 0) {
+        v = wb * unpoint(L[u].tv, L[u].w4, L[u].iq, L[u].u4);
+        if (np > 0) legendre_q_acc<NP>(legendre_x(g - lo, nm1, inv), np, v, aq);
+        if (nh > 0) harmonics_df_acc<NH>(L[u].h4, nh, v, ahc, ahs);
+        bin = L[u].bin;
       }
+      if (naz > 0) az_run_sums_df(a_sm + c0, bin, v, df_make(L[u].fr.x, L[u].fr.y), d.interp, naz, lane);
     }
-    if (naz > 0) az_run_sums_df(a_sm + c0, bin, v, fr, d.interp, naz, lane);
   }
 #pragma unroll
   for (int q = 0; q < NP; q++)
@@ -721,54 +660,376 @@ __global__ void __cluster_dims__(kTC, 1, 1) __launch_bounds__(kTA)
 
   // ---- pass 2 ----
   double* yr = y + rhs * y_stride;
-  for (int64_t g = s_lo + tid; g < s_hi; g += kTA) {
-    const int32_t p = d.lpix[g];
-    if (p < 0) continue;
-    const float4 w4 = wdf[g];
-    const df t = tod(g, p, w4);
-    df sv = df_make(0.f, 0.f);
-    if (np > 0) {
-      df ql[NP];
-      legendre_q_df<NP>(legendre_x(g - lo, nm1, inv), np, ql);
+  for (int64_t g0 = s_lo + (int64_t)warp * 32 * kUdf; g0 < s_hi; g0 += (int64_t)kTA * kUdf) {
+    Ld L[kUdf];
+    load(g0, L, true);
 #pragma unroll
-      for (int q = 0; q < NP; q++)
-        if (q < np) sv = df_fma(cq[q], ql[q], sv);
-    }
-    if (naz > 0) {
-      const int i = d.bin8[g];
-      if (d.interp) {
-        const float2 f = d.fracdf[g];
-        const df ci = caz[i];
-        sv = df_fma(df_make(f.x, f.y), caz[i + 1] - ci, sv + ci);
-      } else {
-        sv = sv + caz[i];
+    for (int u = 0; u < kUdf; u++) {
+      const int32_t p = L[u].p;
+      if (p < 0) continue;
+      const int64_t g = g0 + u * 32 + lane;
+      const float4 w4 = L[u].w4;
+      const df t = unpoint(L[u].tv, w4, L[u].iq, L[u].u4);
+      df sv = df_make(0.f, 0.f);
+      if (np > 0) sv = legendre_q_dot<NP>(legendre_x(g - lo, nm1, inv), np, cq, sv);
+      if (naz > 0) {
+        const int i = L[u].bin;
+        if (d.interp) {
+          const df ci = caz[i];
+          sv = df_fma(df_make(L[u].fr.x, L[u].fr.y), caz[i + 1] - ci, sv + ci);
+        } else {
+          sv = sv + caz[i];
+        }
       }
+      if (nh > 0) sv = harmonics_df_dot<NH>(L[u].h4, nh, chc, chs, sv);
+      const df yv = wb * (t - sv);
+      double* yp = yr + 4 * (int64_t)p;
+      atomicAdd(yp, df_to_double(yv));
+      atomicAdd(yp + 1, df_to_double(df_make(w4.x, w4.y) * yv));
+      atomicAdd(yp + 2, df_to_double(df_make(w4.z, w4.w) * yv));
     }
-    if (nh > 0) {
-      df hc[NH], hs[NH];
-      harmonics_df<NH>(d.hwpdf[g], nh, hc, hs);
-#pragma unroll
-      for (int q = 0; q < NH; q++)
-        if (q < nh) sv = sv + df_prod_sum(chc[q], hc[q], chs[q], hs[q]);
-    }
-    const df yv = wb * (t - sv);
-    double* yp = yr + 4 * (int64_t)p;
-    atomicAdd(yp, df_to_double(yv));
-    atomicAdd(yp + 1, df_to_double(df_make(w4.x, w4.y) * yv));
-    atomicAdd(yp + 2, df_to_double(df_make(w4.z, w4.w) * yv));
   }
   asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory");
 }
 
+// ---- T^T W T per block (setup) --------------------------------------------------------------------
+// One 8-CTA cluster per block, each CTA a slice.  The dense templates (Legendre, HWP) of a 64-sample
+// tile are generated once in df64 into shared memory; threads owning a (dense, dense) pair accumulate
+// its products over the tile (df64, folded into FP64 per tile).  The azimuth rows come from sweeps of
+// short sample segments that sum each run of one bin (df64) and add it to the bin's entry; the
+// azimuth-azimuth block is the kept-sample count per bin (binned) or the three interpolation weight
+// products.  The slices meet over distributed shared memory and rank 0 writes K_b = w_b (...), the
+// Legendre columns carrying their scale sqrt((2q + 1) / n) / q!.
+constexpr int kGT = 64;                                   // samples per tile
+constexpr int kGSeg = 8;                                  // azimuth sweep segments per tile
+constexpr int kMaxDense = kMaxPoly + 2 * kMaxHwp;
+constexpr int kMaxPairs = kMaxDense * (kMaxDense + 1) / 2;
+constexpr int kGP = (kMaxPairs + kTA - 1) / kTA;          // pairs per thread when they outnumber threads
+
+__device__ __forceinline__ int dense_pair(int i, int j, int D) { return i * D - i * (i - 1) / 2 + (j - i); }
+
+__global__ void __cluster_dims__(kTC, 1, 1) __launch_bounds__(kTA) k_tmpl_gram(TmplDev d, double* __restrict__ K) {
+  __shared__ df Td[kMaxDense][kGT];
+  __shared__ int sbin[kGT];
+  __shared__ df sfr[kGT];
+  __shared__ double Sd[kMaxPairs];
+  __shared__ double Saz[kMaxDense][kMaxTmpl + 1];
+  __shared__ double Sdiag[kMaxTmpl + 1], Soff[kMaxTmpl + 1];
+  cg::cluster_group cl = cg::this_cluster();
+  const int b = blockIdx.x / kTC, rank = (int)cl.block_rank();
+  const int tid = threadIdx.x;
+  const int k = d.k, np = d.n_poly, naz = d.n_az, nh = d.n_hwp, c0 = np, h0 = np + naz;
+  const int D = np + 2 * nh, NP2 = D * (D + 1) / 2;
+  const int64_t lo = d.off[b], n = d.off[b + 1] - lo;
+  const int64_t per = (n + kTC - 1) / kTC;
+  const int64_t s_lo = lo + min(n, per * rank), s_hi = lo + min(n, per * (rank + 1));
+  const int64_t nm1 = n > 1 ? n - 1 : 0;
+  const df inv = n > 1 ? df(1.0 / (double)nm1) : df_make(0.f, 0.f);
+  for (int j = tid; j < kMaxPairs; j += kTA) Sd[j] = 0.0;
+  for (int j = tid; j < kMaxDense * (kMaxTmpl + 1); j += kTA) (&Saz[0][0])[j] = 0.0;
+  for (int j = tid; j <= kMaxTmpl; j += kTA) Sdiag[j] = Soff[j] = 0.0;
+  // pair ownership: H sample phases per pair when pairs are few, else up to kGP pairs per thread
+  const int H = NP2 > 0 && NP2 <= kTA ? min(8, kTA / NP2) : 1;
+  int pi[kGP], pj[kGP], np_own = 0, phase = 0;
+  if (NP2 > 0 && NP2 <= kTA) {
+    if (tid < NP2 * H) {
+      int p = tid % NP2, i = 0;
+      while (p >= D - i) { p -= D - i; i++; }
+      pi[0] = i;
+      pj[0] = i + p;
+      np_own = 1;
+      phase = tid / NP2;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < kGP; r++) {
+      int p = tid + r * kTA, i = 0;
+      if (p < NP2) {
+        while (p >= D - i) { p -= D - i; i++; }
+        pi[r] = i;
+        pj[r] = i + p;
+        np_own = r + 1;
+      }
+    }
+  }
+  double acc[kGP];
+#pragma unroll
+  for (int r = 0; r < kGP; r++) acc[r] = 0.0;
+  __syncthreads();
+
+  for (int64_t base = s_lo; base < s_hi; base += kGT) {
+    // ---- phase A: the tile's dense template values, bins and fractions ----
+    if (tid < kGT) {
+      const int64_t g = base + tid;
+      const bool kept = g < s_hi && d.lpix[g] >= 0;
+      if (kept) {
+        if (np > 0) {
+          const df x = legendre_x(g - lo, nm1, inv);
+          df qm = df_make(1.f, 0.f), qc = x;
+          for (int q = 0; q < np; q++) {
+            df v;
+            if (q == 0) v = df_make(1.f, 0.f);
+            else if (q == 1) v = x;
+            else {
+              v = df_prod_sum(df_mul_f(x, (float)(2 * q - 1)), qc, df_make(-(float)((q - 1) * (q - 1)), 0.f), qm);
+              qm = qc;
+              qc = v;
+            }
+            Td[q][tid] = v;
+          }
+        }
+        if (nh > 0) {
+          const float4 h4 = d.hwpdf[g];
+          const df c1 = df_make(h4.x, h4.y), s1 = df_make(h4.z, h4.w);
+          df ck = c1, sk = s1;
+          for (int q = 0; q < nh; q++) {
+            Td[np + 2 * q][tid] = ck;
+            Td[np + 2 * q + 1][tid] = sk;
+            const df cn = df_prod_sum(ck, c1, -sk, s1), sn = df_prod_sum(sk, c1, ck, s1);
+            ck = cn;
+            sk = sn;
+          }
+        }
+        sbin[tid] = naz > 0 ? (int)d.bin8[g] : -1;
+        if (naz > 0 && d.interp) {
+          const float2 f = d.fracdf[g];
+          sfr[tid] = df_make(f.x, f.y);
+        } else {
+          sfr[tid] = df_make(0.f, 0.f);
+        }
+      } else {
+        for (int q = 0; q < D; q++) Td[q][tid] = df_make(0.f, 0.f);
+        sbin[tid] = -1;
+        sfr[tid] = df_make(0.f, 0.f);
+      }
+    }
+    __syncthreads();
+    // ---- phase B: dense x dense ----
+#pragma unroll
+    for (int r = 0; r < kGP; r++) {
+      if (r < np_own) {
+        const df* ti = Td[pi[r]];
+        const df* tj = Td[pj[r]];
+        df t = df_make(0.f, 0.f);
+        for (int q = phase; q < kGT; q += H) t = df_fma(ti[q], tj[q], t);
+        acc[r] += df_to_double(t);
+      }
+    }
+    // ---- phase C: azimuth rows (column c < D: dense c; c == D: azimuth x azimuth) ----
+    if (naz > 0) {
+      constexpr int seg = kGT / kGSeg;
+      for (int item = tid; item < (D + 1) * kGSeg; item += kTA) {
+        const int c = item / kGSeg, q0 = (item % kGSeg) * seg;
+        int cur = -1;
+        df r0 = df_make(0.f, 0.f), r1 = df_make(0.f, 0.f), r2 = df_make(0.f, 0.f);
+        int cnt = 0;
+        auto flush = [&]() {
+          if (cur < 0) return;
+          if (c < D) {
+            atomicAdd(&Saz[c][cur], df_to_double(r0));
+            if (d.interp && cur + 1 < naz) atomicAdd(&Saz[c][cur + 1], df_to_double(r1));
+          } else if (!d.interp) {
+            atomicAdd(&Sdiag[cur], (double)cnt);
+          } else {
+            atomicAdd(&Sdiag[cur], df_to_double(r0));
+            if (cur + 1 < naz) {
+              atomicAdd(&Sdiag[cur + 1], df_to_double(r1));
+              atomicAdd(&Soff[cur], df_to_double(r2));
+            }
+          }
+          r0 = r1 = r2 = df_make(0.f, 0.f);
+          cnt = 0;
+        };
+        for (int q = q0; q < q0 + seg; q++) {
+          const int bq = sbin[q];
+          if (bq < 0) continue;
+          if (bq != cur) {
+            flush();
+            cur = bq;
+          }
+          if (c < D) {
+            const df v = Td[c][q];
+            if (d.interp) {
+              r1 = df_fma(sfr[q], v, r1);
+              r0 = r0 + (v - sfr[q] * v);
+            } else {
+              r0 = r0 + v;
+            }
+          } else if (!d.interp) {
+            cnt++;
+          } else {
+            const df f = sfr[q], omf = df_make(1.f, 0.f) - f;
+            r0 = df_fma(omf, omf, r0);
+            r1 = df_fma(f, f, r1);
+            r2 = df_fma(omf, f, r2);
+          }
+        }
+        flush();
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < kGP; r++)
+    if (r < np_own) atomicAdd(&Sd[dense_pair(pi[r], pj[r], D)], acc[r]);
+  cl.sync();
+  if (rank == 0) {
+    const double wb = d.w[b];
+    double* Kb = K + (int64_t)b * k * k;
+    for (int e = tid; e < k * k; e += kTA) {
+      const int i = e / k, j = e % k;
+      const bool ai = i >= c0 && i < h0, aj = j >= c0 && j < h0;
+      double v = 0.0;
+      auto sc = [&](int t) -> double {   // scale of template t (dense)
+        if (t < np) {
+          double f = 1.0;
+          for (int m = 2; m <= t; m++) f *= (double)m;
+          return d.pscale[(int64_t)b * np + t] / f;
+        }
+        return 1.0;
+      };
+      auto di = [&](int t) { return t < np ? t : np + (t - h0); };
+      if (!ai && !aj) {
+        const int x = min(di(i), di(j)), y = max(di(i), di(j));
+        const int pidx = dense_pair(x, y, D);
+        for (int r = 0; r < kTC; r++) v += cl.map_shared_rank(Sd, r)[pidx];
+        v *= sc(i) * sc(j);
+      } else if (ai != aj) {
+        const int t = ai ? j : i, bz = (ai ? i : j) - c0;
+        for (int r = 0; r < kTC; r++) v += cl.map_shared_rank(&Saz[0][0], r)[di(t) * (kMaxTmpl + 1) + bz];
+        v *= sc(t);
+      } else {
+        const int bi = i - c0, bj = j - c0;
+        if (bi == bj) {
+          for (int r = 0; r < kTC; r++) v += cl.map_shared_rank(Sdiag, r)[bi];
+        } else if (d.interp && (bi - bj == 1 || bj - bi == 1)) {
+          for (int r = 0; r < kTC; r++) v += cl.map_shared_rank(Soff, r)[min(bi, bj)];
+        }
+      }
+      Kb[e] = wb * v;
+    }
+  }
+  cl.sync();   // rank 0 has read every slice's shared memory
+}
+
+// Kinv_b = pseudo-inverse of K_b (eigenvalues below rcond * max |w| dropped): cyclic Jacobi with the
+// round-robin ordering of disjoint rotation pairs (each round's rotations commute and are applied at
+// once), one CTA per block, A and the eigenvectors U in shared memory.
+constexpr int kPinvThreads = 256;
+__global__ void __launch_bounds__(kPinvThreads) k_tmpl_pinv(const double* __restrict__ K, int k, double rcond,
+                                                            double* __restrict__ Kinv) {
+  extern __shared__ double pv_sm[];
+  const int ld = k + 1, kk = k + (k & 1), npair = kk / 2;
+  double* A = pv_sm;
+  double* U = A + k * ld;
+  double* cs = U + k * ld;        // [npair][2]
+  double* red = cs + 2 * 32;      // [kPinvThreads][2]
+  __shared__ int pp[32], qq[32];
+  __shared__ int stop;
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const double* Kb = K + (int64_t)b * k * k;
+  for (int e = tid; e < k * k; e += kPinvThreads) {
+    const int i = e / k, j = e % k;
+    A[i * ld + j] = Kb[e];
+    U[i * ld + j] = i == j ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 60; sweep++) {
+    double off = 0.0, tot = 0.0;
+    for (int e = tid; e < k * k; e += kPinvThreads) {
+      const int i = e / k, j = e % k;
+      const double a2 = A[i * ld + j] * A[i * ld + j];
+      tot += a2;
+      if (i != j) off += a2;
+    }
+    red[2 * tid] = off;
+    red[2 * tid + 1] = tot;
+    __syncthreads();
+    for (int sh = kPinvThreads / 2; sh > 0; sh >>= 1) {
+      if (tid < sh) {
+        red[2 * tid] += red[2 * (tid + sh)];
+        red[2 * tid + 1] += red[2 * (tid + sh) + 1];
+      }
+      __syncthreads();
+    }
+    if (tid == 0) stop = (red[0] <= 1e-30 * red[1] || red[0] == 0.0) ? 1 : 0;
+    __syncthreads();
+    if (stop) break;
+    for (int r = 0; r < kk - 1; r++) {
+      if (tid < npair) {
+        int p, q;
+        if (tid == 0) {
+          p = r;
+          q = kk - 1;
+        } else {
+          p = (r + tid) % (kk - 1);
+          q = (r - tid + kk - 1) % (kk - 1);
+        }
+        if (p > q) { const int t = p; p = q; q = t; }
+        double c = 1.0, sn = 0.0;
+        if (q < k) {
+          const double apq = A[p * ld + q];
+          if (apq != 0.0) {
+            const double theta = (A[q * ld + q] - A[p * ld + p]) / (2.0 * apq);
+            const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            sn = t * c;
+          }
+        }
+        pp[tid] = p;
+        qq[tid] = q < k ? q : -1;
+        cs[2 * tid] = c;
+        cs[2 * tid + 1] = sn;
+      }
+      __syncthreads();
+      for (int it = tid; it < k * npair; it += kPinvThreads) {   // A <- A J, U <- U J (columns p, q)
+        const int i = it / npair, m = it % npair, p = pp[m], q = qq[m];
+        if (q < 0) continue;
+        const double c = cs[2 * m], sn = cs[2 * m + 1];
+        const double arp = A[i * ld + p], arq = A[i * ld + q];
+        A[i * ld + p] = c * arp - sn * arq;
+        A[i * ld + q] = sn * arp + c * arq;
+        const double urp = U[i * ld + p], urq = U[i * ld + q];
+        U[i * ld + p] = c * urp - sn * urq;
+        U[i * ld + q] = sn * urp + c * urq;
+      }
+      __syncthreads();
+      for (int it = tid; it < npair * k; it += kPinvThreads) {   // A <- J^T A (rows p, q)
+        const int m = it / k, j = it % k, p = pp[m], q = qq[m];
+        if (q < 0) continue;
+        const double c = cs[2 * m], sn = cs[2 * m + 1];
+        const double apj = A[p * ld + j], aqj = A[q * ld + j];
+        A[p * ld + j] = c * apj - sn * aqj;
+        A[q * ld + j] = sn * apj + c * aqj;
+      }
+      __syncthreads();
+    }
+  }
+  // pseudo-inverse from the eigen-decomposition
+  double mx = 0.0;
+  for (int i = 0; i < k; i++) mx = fmax(mx, fabs(A[i * ld + i]));
+  double* out = Kinv + (int64_t)b * k * k;
+  for (int e = tid; e < k * k; e += kPinvThreads) {
+    const int i = e / k, j = e % k;
+    double sum = 0.0;
+    for (int l = 0; l < k; l++) {
+      const double wl = A[l * ld + l];
+      if (fabs(wl) > rcond * mx) sum += U[i * ld + l] * U[j * ld + l] / wl;
+    }
+    out[e] = sum;
+  }
+}
+
 // df64 copies of cos/sin of the HWP angle and of the interpolation fractions (setup)
 __global__ void k_tmpl_df_tables(const float* __restrict__ hwp, const double* __restrict__ frac, int64_t N,
-                                 float4* __restrict__ hwpdf, float2* __restrict__ fracdf) {
+                                 float4* __restrict__ hwpdf, float2* __restrict__ hwp32, float2* __restrict__ fracdf) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     if (hwpdf) {
       double sn, cs;
       sincos((double)hwp[i], &sn, &cs);
       const df c(cs), s(sn);
       hwpdf[i] = make_float4(c.hi, c.lo, s.hi, s.lo);
+      hwp32[i] = make_float2(c.hi, s.hi);
     }
     if (fracdf) {
       const df f(frac[i]);
@@ -779,13 +1040,19 @@ __global__ void k_tmpl_df_tables(const float* __restrict__ hwp, const double* __
 
 }  // namespace
 
-cudaError_t launch_tmpl_setup(TmplDev& d, int nb, double* K, double* work, double* U, double* w, cudaStream_t s) {
+cudaError_t launch_tmpl_setup(TmplDev& d, int nb, double* K, cudaStream_t s) {
+  if (nb <= 0) return cudaSuccess;
   if (d.n_az > 0)
     k_tmpl_bins<<<nb, kTNT, 0, s>>>(d.lpix, d.az, d.off, d.n_az, d.interp, d.az_bin_w, d.az_frac_w, d.bin8_w,
                                     d.frac32_w);
-  if (d.hwpdf_w || d.fracdf_w) k_tmpl_df_tables<<<152 * 8, 256, 0, s>>>(d.hwp, d.az_frac, d.n_total, d.hwpdf_w, d.fracdf_w);
-  k_tmpl_gram<<<nb, kTNT, 0, s>>>(d, K);
-  k_tmpl_pinv<<<(nb + 31) / 32, 32, 0, s>>>(K, d.k, nb, 1e-12, work, U, w, d.kinv_w);
+  if (d.hwpdf_w || d.fracdf_w)
+    k_tmpl_df_tables<<<152 * 8, 256, 0, s>>>(d.hwp, d.az_frac, d.n_total, d.hwpdf_w, d.hwp32_w, d.fracdf_w);
+  k_tmpl_gram<<<nb * kTC, kTA, 0, s>>>(d, K);
+  const int k = d.k;
+  const size_t smem = (size_t)(2 * k * (k + 1) + 2 * 32 + 2 * kPinvThreads) * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_tmpl_pinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_tmpl_pinv<<<nb, kPinvThreads, smem, s>>>(K, k, 1e-12, d.kinv_w);
   return cudaGetLastError();
 }
 

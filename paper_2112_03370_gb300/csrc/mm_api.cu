@@ -131,8 +131,7 @@ void free_defl(DeflState* d) {
 
 void free_tmpl(TmplState* t) {
   if (!t) return;
-  dfree(t->az); dfree(t->hwp); dfree(t->az_bin); dfree(t->az_frac); dfree(t->bin8); dfree(t->frac32);
-  dfree(t->fracdf); dfree(t->hwpdf);
+  dfree(t->bin8); dfree(t->frac32); dfree(t->fracdf); dfree(t->hwpdf); dfree(t->hwp32);
   dfree(t->xscale); dfree(t->xoff);
   dfree(t->pscale);
   dfree(t->kinv);
@@ -1980,6 +1979,9 @@ int mm_templates_set(mm_plan_t plan, const mm_templates_desc* t, void* stream) {
   if (t->n_az < 0 || t->n_az > kMaxTmpl) return fail(MM_EINVAL, "n_az must lie in [0, 64]");
   if (t->n_hwp < 0 || t->n_hwp > kMaxHwp) return fail(MM_EINVAL, "n_hwp must lie in [0, 8]");
   const int k = t->n_poly + t->n_az + 2 * t->n_hwp;
+  for (int b = 0; b < P->n_blocks; b++)
+    if (P->block_off[b + 1] - P->block_off[b] >= ((int64_t)1 << 31))
+      return fail(MM_EINVAL, "template map-making needs blocks shorter than 2^31 samples");
   if (k < 1 || k > kMaxTmpl) return fail(MM_EINVAL, "n_poly + n_az + 2 n_hwp must lie in [1, 64]");
   if ((t->n_az > 0 && !t->az) || (t->n_hwp > 0 && !t->hwp)) return fail(MM_EINVAL, "az / hwp missing");
   DeviceGuard g(P->device);
@@ -1997,21 +1999,28 @@ int mm_templates_set(mm_plan_t plan, const mm_templates_desc* t, void* stream) {
   P->tmpl = ts;
   const int nb = P->n_blocks;
   const cudaMemcpyKind kind = t->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  // the angles, int32 bins and FP64 fractions only feed the setup kernels: scratch, freed on return;
+  // the operators keep uint8 bins, FP32 / df64 fractions and cos/sin of the HWP angle
+  Scratch scr;
+  float *az = nullptr, *hwp = nullptr;
+  int32_t* az_bin = nullptr;
+  double* az_frac = nullptr;
   if (t->n_az > 0) {
-    MM_TRY(dalloc(P, &ts->az, P->N));
-    MM_TRY(dalloc(P, &ts->az_bin, P->N));
+    MM_TRY(scr.alloc(&az, P->N));
+    MM_TRY(scr.alloc(&az_bin, P->N));
     MM_TRY(dalloc(P, &ts->bin8, P->N));
-    MM_CUDA(cudaMemcpyAsync(ts->az, t->az, P->N * sizeof(float), kind, s));
+    MM_CUDA(cudaMemcpyAsync(az, t->az, P->N * sizeof(float), kind, s));
     if (t->az_interp) {
-      MM_TRY(dalloc(P, &ts->az_frac, P->N));
+      MM_TRY(scr.alloc(&az_frac, P->N));
       MM_TRY(dalloc(P, &ts->frac32, P->N));
       MM_TRY(dalloc(P, &ts->fracdf, P->N));
     }
   }
   if (t->n_hwp > 0) {
-    MM_TRY(dalloc(P, &ts->hwp, P->N));
+    MM_TRY(scr.alloc(&hwp, P->N));
     MM_TRY(dalloc(P, &ts->hwpdf, P->N));
-    MM_CUDA(cudaMemcpyAsync(ts->hwp, t->hwp, P->N * sizeof(float), kind, s));
+    MM_TRY(dalloc(P, &ts->hwp32, P->N));
+    MM_CUDA(cudaMemcpyAsync(hwp, t->hwp, P->N * sizeof(float), kind, s));
   }
   if (!P->wdf) {   // df64 pointing weights of the FP64-class template operator
     MM_TRY(dalloc(P, &P->wdf, P->N));
@@ -2037,16 +2046,18 @@ int mm_templates_set(mm_plan_t plan, const mm_templates_desc* t, void* stream) {
   d.n_total = P->N;
   d.off = P->block_off_dev; d.lpix = P->lpix; d.w = P->c0_blk; d.xscale = ts->xscale; d.xoff = ts->xoff;
   d.pscale = ts->pscale;
-  d.az = ts->az; d.hwp = ts->hwp; d.az_bin = ts->az_bin; d.az_frac = ts->az_frac; d.kinv = ts->kinv;
-  d.az_bin_w = ts->az_bin; d.az_frac_w = ts->az_frac; d.kinv_w = ts->kinv;
+  d.az = az; d.hwp = hwp; d.az_bin = az_bin; d.az_frac = az_frac; d.kinv = ts->kinv;
+  d.az_bin_w = az_bin; d.az_frac_w = az_frac; d.kinv_w = ts->kinv;
   d.bin8 = ts->bin8; d.frac32 = ts->frac32; d.bin8_w = ts->bin8; d.frac32_w = ts->frac32;
   d.fracdf = ts->fracdf; d.hwpdf = ts->hwpdf; d.fracdf_w = ts->fracdf; d.hwpdf_w = ts->hwpdf;
-  Scratch scr;
-  double *K = nullptr, *work = nullptr, *U = nullptr, *w = nullptr;
-  MM_TRY(scr.alloc(&K, (size_t)nb * k * k)); MM_TRY(scr.alloc(&work, (size_t)nb * k * k));
-  MM_TRY(scr.alloc(&U, (size_t)nb * k * k)); MM_TRY(scr.alloc(&w, (size_t)nb * k));
-  MM_CUDA(launch_tmpl_setup(d, nb, K, work, U, w, s));
+  d.hwp32 = ts->hwp32; d.hwp32_w = ts->hwp32;
+  double* K = nullptr;
+  MM_TRY(scr.alloc(&K, (size_t)nb * k * k));
+  MM_CUDA(launch_tmpl_setup(d, nb, K, s));
   MM_CUDA(cudaStreamSynchronize(s));
+  // the scratch inputs are gone once this returns
+  d.az = nullptr; d.hwp = nullptr; d.az_bin = nullptr; d.az_frac = nullptr;
+  d.az_bin_w = nullptr; d.az_frac_w = nullptr;
   return MM_OK;
 }
 

@@ -21,13 +21,14 @@ struct TmplDev {
   const double* xoff;        // [n_blocks] 1 (0 when n_b <= 1, where x = 0)
   const double* pscale;      // [n_blocks][n_poly] sqrt((2k + 1) / n_b)
   const float* az;           // [N] azimuth (setup only)
-  const float* hwp;          // [N] HWP angle
-  const int32_t* az_bin;     // [N] bin, or left interpolation node
-  const double* az_frac;     // [N] weight of the right node (interpolation)
+  const float* hwp;          // [N] HWP angle (setup only)
+  const int32_t* az_bin;     // [N] bin, or left interpolation node (setup only)
+  const double* az_frac;     // [N] weight of the right node (interpolation; setup only)
   const uint8_t* bin8;       // [N] the same bin as uint8 (n_az <= 64), for the fused operators
   const float* frac32;       // [N] az_frac rounded to FP32 (interpolation)
   const float2* fracdf;      // [N] az_frac as df64 (interpolation)
   const float4* hwpdf;       // [N] cos(phi), sin(phi) of the HWP angle as df64 (hi, lo, hi, lo)
+  const float2* hwp32;       // [N] cos(phi), sin(phi) rounded to FP32
   const double* kinv;        // [n_blocks][k][k] pseudo-inverse of T^T W T
   int32_t* az_bin_w;         // writable aliases used by the setup kernels
   double* az_frac_w;
@@ -35,28 +36,26 @@ struct TmplDev {
   float* frac32_w;
   float2* fracdf_w;
   float4* hwpdf_w;
+  float2* hwp32_w;
   double* kinv_w;
 };
 
 // Host-side state owned by a plan.
 struct TmplState {
   TmplDev dev{};
-  float* az = nullptr;
-  float* hwp = nullptr;
-  int32_t* az_bin = nullptr;
-  double* az_frac = nullptr;
   uint8_t* bin8 = nullptr;
   float* frac32 = nullptr;
   float2* fracdf = nullptr;
   float4* hwpdf = nullptr;
+  float2* hwp32 = nullptr;
   double* xscale = nullptr;
   double* xoff = nullptr;
   double* pscale = nullptr;
   double* kinv = nullptr;
 };
 
-// bins, T^T W T and its pseudo-inverse (scratch K, work, U: [nb][k][k]; w: [nb][k])
-cudaError_t launch_tmpl_setup(TmplDev& d, int nb, double* K, double* work, double* U, double* w, cudaStream_t s);
+// bins, df64 tables, T^T W T and its pseudo-inverse (scratch K: [nb][k][k])
+cudaError_t launch_tmpl_setup(TmplDev& d, int nb, double* K, cudaStream_t s);
 // Fused FP32 template operator y += P^T F_T P x for nrhs float4 maps ([nrhs][n_obs][4], stride in
 // floats), columns with a nonzero done flag skipped: one 8-CTA cluster per block, no TOD buffer.
 cudaError_t launch_tmpl_apply32(const TmplDev& d, int nb, const float2* w32, const float* x32, int64_t x_stride,
