@@ -12,6 +12,7 @@
 
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "df64.cuh"
@@ -88,7 +89,8 @@ __global__ void k_tmpl_bins(const int32_t* __restrict__ lpix, const float* __res
 // Pass 1 un-points x (t = P x, the map gathered from L2), forms v = w_b t and accumulates the slice's
 // T^T v: Legendre and HWP terms in registers, azimuth bins as one shared-memory atomic per run of
 // equal bins within a warp.  The slices' sums meet over distributed shared memory, every CTA forms
-// c = Kinv a from them in the same order, and pass 2 recomputes t and scatters w_b (t - T c) into y.
+// c = Kinv a from them in the same order, and pass 2 scatters -w_b T c into y.  The diagonal part
+// P^T W P x of the operator is added per pixel (k_tmpl_mx32), so pass 2 needs no map gather.
 constexpr int kTC = 8;     // CTAs per block
 constexpr int kTA = 256;   // threads per CTA
 constexpr int kU = 4;      // samples per thread and step of the FP32 operator (loads in flight)
@@ -166,9 +168,10 @@ __device__ __forceinline__ float harmonics_dot(float2 cs1, int n, const float (&
 }
 
 // Warp-collective: the lanes' (bin, value) pairs summed per run of equal bins (lanes are consecutive
-// samples, so a run is a stretch of constant azimuth bin); the run's first lane adds the sum to a[bin]
-// (and the right-node share to a[bin + 1] when interpolating).  bin < 0 marks a lane with no sample.
-__device__ __forceinline__ void az_run_sums(double* a, int bin, float v, float fr, int interp, int n_az,
+// samples, so a run is a stretch of constant azimuth bin); the run's first lane adds the sum to the
+// warp's own FP32 accumulator a[bin] (and the right-node share to a[bin + 1] when interpolating) with a
+// native shared-memory atomic.  bin < 0 marks a lane with no sample.
+__device__ __forceinline__ void az_run_sums(float* a, int bin, float v, float fr, int interp, int n_az,
                                             int lane) {
   const int prev = __shfl_up_sync(0xffffffffu, bin, 1);
   const int next = __shfl_down_sync(0xffffffffu, bin, 1);
@@ -190,8 +193,8 @@ __device__ __forceinline__ void az_run_sums(double* a, int bin, float v, float f
     }
   }
   if (head && bin >= 0) {
-    atomicAdd(a + bin, (double)s0);
-    if (interp && bin + 1 < n_az) atomicAdd(a + bin + 1, (double)s1);
+    atomicAdd(a + bin, s0);
+    if (interp && bin + 1 < n_az) atomicAdd(a + bin + 1, s1);
   }
 }
 
@@ -210,6 +213,7 @@ __global__ void __cluster_dims__(kTC, 1, 1) __launch_bounds__(kTA)
   __shared__ double red[kW][NP + 2 * NH];        // per-warp sums of the register terms
   __shared__ double c_sm[kMaxTmpl];              // c = Kinv a (the whole block's a)
   __shared__ float caz[kMaxTmpl + 1];            // azimuth part of c in FP32 (+1: a zero right node)
+  __shared__ float az_w[kW][kMaxTmpl];           // per-warp azimuth sums of pass 1
   const int rhs = blockIdx.y;
   // every CTA of a cluster reads the same flag, so the cluster leaves together
   if (done != nullptr && done[(int64_t)rhs * done_stride] != 0) return;
@@ -231,6 +235,7 @@ __global__ void __cluster_dims__(kTC, 1, 1) __launch_bounds__(kTA)
   const uint8_t* bp = naz > 0 ? d.bin8 + s_lo : nullptr;
   const float* fp = (naz > 0 && d.interp) ? d.frac32 + s_lo : nullptr;
   for (int j = tid; j < kMaxTmpl; j += kTA) a_sm[j] = 0.0;
+  for (int j = tid; j < kW * kMaxTmpl; j += kTA) (&az_w[0][0])[j] = 0.f;
   __syncthreads();
 
   // ---- pass 1: a = T^T W P x over the slice ----
@@ -270,7 +275,7 @@ __global__ void __cluster_dims__(kTC, 1, 1) __launch_bounds__(kTA)
         if (nh > 0) harmonics_acc<NH>(hw[u], nh, v, ahc, ahs);
         bin = bn[u];
       }
-      if (naz > 0) az_run_sums(a_sm + c0, bin, v, fr[u], d.interp, naz, lane);
+      if (naz > 0) az_run_sums(az_w[warp], bin, v, fr[u], d.interp, naz, lane);
     }
   }
   // register terms: warp sums in FP64, then across warps
@@ -298,6 +303,12 @@ __global__ void __cluster_dims__(kTC, 1, 1) __launch_bounds__(kTA)
     double t = 0.0;
     for (int w = 0; w < kW; w++) t += red[w][tid];
     a_sm[h0 + (tid - NP)] = t;
+  }
+  if (tid >= kTA - kMaxTmpl && tid - (kTA - kMaxTmpl) < naz) {   // azimuth bins: the warps' sums
+    const int j = tid - (kTA - kMaxTmpl);
+    double t = 0.0;
+    for (int w = 0; w < kW; w++) t += (double)az_w[w][j];
+    a_sm[c0 + j] = t;
   }
   // ---- the block's a over the cluster, c = Kinv a ----
   cl.sync();
@@ -330,7 +341,7 @@ __global__ void __cluster_dims__(kTC, 1, 1) __launch_bounds__(kTA)
   for (int j = tid; j <= naz; j += kTA) caz[j] = j < naz ? (float)c_sm[c0 + j] : 0.f;
   __syncthreads();
 
-  // ---- pass 2: y += P^T w_b (t - T c) ----
+  // ---- pass 2: y -= P^T w_b T c (the diagonal part M x is added per pixel) ----
   float4* yr = y + rhs * y_stride4;
   for (int i0 = warp * 32 * kU; i0 < m; i0 += kTA * kU) {
     int32_t pp[kU];
@@ -347,23 +358,19 @@ __global__ void __cluster_dims__(kTC, 1, 1) __launch_bounds__(kTA)
       bn[u] = (in && naz > 0) ? (int)bp[i] : 0;
       fr[u] = (in && naz > 0 && d.interp) ? fp[i] : 0.f;
     }
-    float4 m[kU];
-#pragma unroll
-    for (int u = 0; u < kU; u++) m[u] = pp[u] >= 0 ? xr[pp[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int u = 0; u < kU; u++) {
       if (pp[u] < 0) continue;
       const int i = i0 + u * 32 + lane;
-      const float t = m[u].x + cs[u].x * m[u].y + cs[u].y * m[u].z;
       float sv = 0.f;
       if (np > 0) sv += legendre_dot<NP>((float)(tau0 + i) * xs - xo, np, cp);
       if (naz > 0) {
-        const int i = bn[u];
-        if (d.interp) sv += (1.f - fr[u]) * caz[i] + fr[u] * caz[i + 1];   // caz[naz] = 0 covers i + 1 = naz
-        else sv += caz[i];
+        const int j = bn[u];
+        if (d.interp) sv += (1.f - fr[u]) * caz[j] + fr[u] * caz[j + 1];   // caz[naz] = 0 covers j + 1 = naz
+        else sv += caz[j];
       }
       if (nh > 0) sv += harmonics_dot<NH>(hw[u], nh, chc, chs);
-      const float yv = wb * (t - sv);
+      const float yv = -wb * sv;
       atomicAdd(yr + pp[u], make_float4(yv, cs[u].x * yv, cs[u].y * yv, 0.f));
     }
   }
@@ -557,7 +564,7 @@ __global__ void __cluster_dims__(kTC, 1, 1) __launch_bounds__(kTA)
     float2 tv, fr;
     int bin;
   };
-  auto load = [&](int64_t g0, Ld (&L)[kUdf], bool need_w) {
+  auto load = [&](int64_t g0, Ld (&L)[kUdf], bool need_w, bool gather) {
 #pragma unroll
     for (int u = 0; u < kUdf; u++) {
       const int64_t g = g0 + u * 32 + lane;
@@ -570,11 +577,13 @@ __global__ void __cluster_dims__(kTC, 1, 1) __launch_bounds__(kTA)
       if constexpr (TOD) L[u].tv = in ? tr[g] : make_float2(0.f, 0.f);
     }
     if constexpr (!TOD) {
+      if (gather) {
 #pragma unroll
-      for (int u = 0; u < kUdf; u++) {
-        const int32_t p = L[u].p;
-        L[u].iq = p >= 0 ? mr[2 * (int64_t)p] : make_float4(0.f, 0.f, 0.f, 0.f);
-        L[u].u4 = p >= 0 ? mr[2 * (int64_t)p + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int u = 0; u < kUdf; u++) {
+          const int32_t p = L[u].p;
+          L[u].iq = p >= 0 ? mr[2 * (int64_t)p] : make_float4(0.f, 0.f, 0.f, 0.f);
+          L[u].u4 = p >= 0 ? mr[2 * (int64_t)p + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
       }
     }
   };
@@ -587,7 +596,7 @@ __global__ void __cluster_dims__(kTC, 1, 1) __launch_bounds__(kTA)
   for (int q = 0; q < NH; q++) ahc[q] = ahs[q] = df_make(0.f, 0.f);
   for (int64_t g0 = s_lo + (int64_t)warp * 32 * kUdf; g0 < s_hi; g0 += (int64_t)kTA * kUdf) {
     Ld L[kUdf];
-    load(g0, L, !TOD);
+    load(g0, L, !TOD, true);
 #pragma unroll
     for (int u = 0; u < kUdf; u++) {
       const int64_t g = g0 + u * 32 + lane;
@@ -662,14 +671,13 @@ __global__ void __cluster_dims__(kTC, 1, 1) __launch_bounds__(kTA)
   double* yr = y + rhs * y_stride;
   for (int64_t g0 = s_lo + (int64_t)warp * 32 * kUdf; g0 < s_hi; g0 += (int64_t)kTA * kUdf) {
     Ld L[kUdf];
-    load(g0, L, true);
+    load(g0, L, true, false);
 #pragma unroll
     for (int u = 0; u < kUdf; u++) {
       const int32_t p = L[u].p;
       if (p < 0) continue;
       const int64_t g = g0 + u * 32 + lane;
       const float4 w4 = L[u].w4;
-      const df t = unpoint(L[u].tv, w4, L[u].iq, L[u].u4);
       df sv = df_make(0.f, 0.f);
       if (np > 0) sv = legendre_q_dot<NP>(legendre_x(g - lo, nm1, inv), np, cq, sv);
       if (naz > 0) {
@@ -682,7 +690,10 @@ __global__ void __cluster_dims__(kTC, 1, 1) __launch_bounds__(kTA)
         }
       }
       if (nh > 0) sv = harmonics_df_dot<NH>(L[u].h4, nh, chc, chs, sv);
-      const df yv = wb * (t - sv);
+      // TOD mode: w_b (t - T c); map mode: -w_b T c (the diagonal part M x is added per pixel)
+      df yv;
+      if constexpr (TOD) yv = wb * (df_make(L[u].tv.x, L[u].tv.y) - sv);
+      else yv = -(wb * sv);
       double* yp = yr + 4 * (int64_t)p;
       atomicAdd(yp, df_to_double(yv));
       atomicAdd(yp + 1, df_to_double(df_make(w4.x, w4.y) * yv));
@@ -1038,6 +1049,44 @@ __global__ void k_tmpl_df_tables(const float* __restrict__ hwp, const double* __
   }
 }
 
+// y += M x per pixel, M = P^T W P (symmetric 3 x 3: m00 m01 m02 m11 m12 m22)
+__global__ void k_tmpl_mx32(const float4* __restrict__ M, int64_t n, const float4* __restrict__ x,
+                            float4* __restrict__ y, const int32_t* __restrict__ done, int done_stride) {
+  const int rhs = blockIdx.y;
+  if (done != nullptr && done[(int64_t)rhs * done_stride] != 0) return;
+  const float4* xr = x + rhs * n;
+  float4* yr = y + rhs * n;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const float4 a = M[2 * p], c = M[2 * p + 1], v = xr[p];
+    float4 o = yr[p];
+    o.x += a.x * v.x + a.y * v.y + a.z * v.z;
+    o.y += a.y * v.x + a.w * v.y + c.x * v.z;
+    o.z += a.z * v.x + c.x * v.y + c.y * v.z;
+    yr[p] = o;
+  }
+}
+__global__ void k_tmpl_mx64(const double* __restrict__ M, int64_t n, const double* __restrict__ x,
+                            double* __restrict__ y, const int32_t* __restrict__ done, int done_stride) {
+  const int rhs = blockIdx.y;
+  if (done != nullptr && done[(int64_t)rhs * done_stride] != 0) return;
+  const double* xr = x + rhs * n * 4;
+  double* yr = y + rhs * n * 4;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const double* m = M + 6 * p;
+    const double v0 = xr[4 * p], v1 = xr[4 * p + 1], v2 = xr[4 * p + 2];
+    yr[4 * p] += m[0] * v0 + m[1] * v1 + m[2] * v2;
+    yr[4 * p + 1] += m[1] * v0 + m[3] * v1 + m[4] * v2;
+    yr[4 * p + 2] += m[2] * v0 + m[4] * v1 + m[5] * v2;
+  }
+}
+__global__ void k_m64_to_32(const double* __restrict__ M, int64_t n, float4* __restrict__ out) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const double* m = M + 6 * p;
+    out[2 * p] = make_float4((float)m[0], (float)m[1], (float)m[2], (float)m[3]);
+    out[2 * p + 1] = make_float4((float)m[4], (float)m[5], 0.f, 0.f);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_tmpl_setup(TmplDev& d, int nb, double* K, cudaStream_t s) {
@@ -1093,6 +1142,29 @@ cudaError_t launch_tmpl_apply_df(const TmplDev& d, int nb, const float4* wdf, co
   else if (d.n_poly <= 4) MM_TMPL_DF(4, kMaxHwp);
   else MM_TMPL_DF(kMaxPoly, kMaxHwp);
 #undef MM_TMPL_DF
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tmpl_mx32(const float4* M32, int64_t n_obs, const float* x, float* y, int nrhs, const int32_t* done,
+                             int done_stride, cudaStream_t s) {
+  if (n_obs == 0 || nrhs <= 0) return cudaSuccess;
+  const unsigned g = (unsigned)std::min<int64_t>((n_obs + 255) / 256, 152 * 8);
+  k_tmpl_mx32<<<dim3(g, nrhs), 256, 0, s>>>(M32, n_obs, reinterpret_cast<const float4*>(x),
+                                            reinterpret_cast<float4*>(y), done, done_stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tmpl_mx64(const double* M64, int64_t n_obs, const double* x, double* y, int nrhs,
+                             const int32_t* done, int done_stride, cudaStream_t s) {
+  if (n_obs == 0 || nrhs <= 0) return cudaSuccess;
+  const unsigned g = (unsigned)std::min<int64_t>((n_obs + 255) / 256, 152 * 8);
+  k_tmpl_mx64<<<dim3(g, nrhs), 256, 0, s>>>(M64, n_obs, x, y, done, done_stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_m64_to_32(const double* M64, int64_t n_obs, float4* M32, cudaStream_t s) {
+  if (n_obs == 0) return cudaSuccess;
+  k_m64_to_32<<<(unsigned)std::min<int64_t>((n_obs + 255) / 256, 152 * 8), 256, 0, s>>>(M64, n_obs, M32);
   return cudaGetLastError();
 }
 

@@ -131,7 +131,8 @@ void free_defl(DeflState* d) {
 
 void free_tmpl(TmplState* t) {
   if (!t) return;
-  dfree(t->bin8); dfree(t->frac32); dfree(t->fracdf); dfree(t->hwpdf); dfree(t->hwp32);
+  dfree(t->bin8); dfree(t->frac32); dfree(t->fracdf); dfree(t->hwpdf); dfree(t->hwp32); dfree(t->M64);
+  dfree(t->M32);
   dfree(t->xscale); dfree(t->xoff);
   dfree(t->pscale);
   dfree(t->kinv);
@@ -581,6 +582,7 @@ int apply64_internal(Plan* P, const double* x4, double* y4, int nrhs, cudaStream
     if (capturing(s) && P->mapdf_cap < m_elems) return fail(MM_EINVAL, "df64 buffers must be allocated before graph capture");
     MM_TRY(ensure_mapdf(P, nrhs));
     MM_CUDA(launch_map_to_df(x4, (int64_t)nrhs * P->n_obs, P->mapdf, s));
+    MM_CUDA(launch_tmpl_mx64(ts->M64, P->n_obs, x4, y4, nrhs, done, done_stride, s));
     MM_CUDA(launch_tmpl_apply_df(ts->dev, P->n_blocks, P->wdf, P->mapdf, P->n_obs * 2, nullptr, 0, y4, P->n_obs * 4,
                                  nrhs, done, done_stride, s));
     return MM_OK;
@@ -656,6 +658,7 @@ int apply32_internal(Plan* P, const float* x32, float* y32, int nrhs, cudaStream
   if (P->tmpl) {   // template map-making: y += P^T F_T P x in one fused kernel (FP32), no TOD buffer
     const TmplState* ts = reinterpret_cast<const TmplState*>(P->tmpl);
     if (mid) MM_CUDA(cudaEventRecord(mid, s));
+    MM_CUDA(launch_tmpl_mx32(ts->M32, P->n_obs, x32, y32, nrhs, done, done_stride, s));
     MM_CUDA(launch_tmpl_apply32(ts->dev, P->n_blocks, P->w32, x32, P->n_obs * 4, y32, P->n_obs * 4, nrhs, done,
                                 done_stride, s));
     return MM_OK;
@@ -2054,6 +2057,15 @@ int mm_templates_set(mm_plan_t plan, const mm_templates_desc* t, void* stream) {
   double* K = nullptr;
   MM_TRY(scr.alloc(&K, (size_t)nb * k * k));
   MM_CUDA(launch_tmpl_setup(d, nb, K, s));
+  // M = P^T W P per pixel (the operator's diagonal-weight part), FP64 and FP32
+  int32_t* hits = nullptr;
+  MM_TRY(scr.alloc(&hits, P->n_obs));
+  MM_TRY(dalloc(P, &ts->M64, 6 * P->n_obs));
+  MM_TRY(dalloc(P, &ts->M32, 2 * P->n_obs));
+  MM_CUDA(cudaMemsetAsync(ts->M64, 0, 6 * P->n_obs * sizeof(double), s));
+  MM_CUDA(cudaMemsetAsync(hits, 0, P->n_obs * sizeof(int32_t), s));
+  MM_CUDA(launch_bd_accum(P->lpix, P->psi, P->block_off_dev, P->c0_blk, nb, P->N, ts->M64, hits, s));
+  MM_CUDA(launch_m64_to_32(ts->M64, P->n_obs, ts->M32, s));
   MM_CUDA(cudaStreamSynchronize(s));
   // the scratch inputs are gone once this returns
   d.az = nullptr; d.hwp = nullptr; d.az_bin = nullptr; d.az_frac = nullptr;

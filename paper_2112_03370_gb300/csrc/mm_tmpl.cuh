@@ -48,6 +48,8 @@ struct TmplState {
   float2* fracdf = nullptr;
   float4* hwpdf = nullptr;
   float2* hwp32 = nullptr;
+  double* M64 = nullptr;     // [n_obs][6] P^T W P per pixel (m00 m01 m02 m11 m12 m22)
+  float4* M32 = nullptr;     // [n_obs][2] the same in FP32 (m00 m01 m02 m11 | m12 m22 0 0)
   double* xscale = nullptr;
   double* xoff = nullptr;
   double* pscale = nullptr;
@@ -56,8 +58,16 @@ struct TmplState {
 
 // bins, df64 tables, T^T W T and its pseudo-inverse (scratch K: [nb][k][k])
 cudaError_t launch_tmpl_setup(TmplDev& d, int nb, double* K, cudaStream_t s);
-// Fused FP32 template operator y += P^T F_T P x for nrhs float4 maps ([nrhs][n_obs][4], stride in
-// floats), columns with a nonzero done flag skipped: one 8-CTA cluster per block, no TOD buffer.
+// y += M x per pixel (M = P^T W P, the diagonal-weight part of the template operator): FP32 float4 maps
+// and FP64 maps [nrhs][n_obs][4], columns with a nonzero done flag skipped
+cudaError_t launch_tmpl_mx32(const float4* M32, int64_t n_obs, const float* x, float* y, int nrhs, const int32_t* done,
+                             int done_stride, cudaStream_t s);
+cudaError_t launch_tmpl_mx64(const double* M64, int64_t n_obs, const double* x, double* y, int nrhs,
+                             const int32_t* done, int done_stride, cudaStream_t s);
+cudaError_t launch_m64_to_32(const double* M64, int64_t n_obs, float4* M32, cudaStream_t s);
+// Fused FP32 template operator, the template part: y -= P^T W T c with c = Kinv T^T W P x, for nrhs
+// float4 maps ([nrhs][n_obs][4], stride in floats), columns with a nonzero done flag skipped: one 8-CTA
+// cluster per block, no TOD buffer.  With launch_tmpl_mx32 it forms y += P^T F_T P x.
 cudaError_t launch_tmpl_apply32(const TmplDev& d, int nb, const float2* w32, const float* x32, int64_t x_stride,
                                 float* y32, int64_t y_stride, int nrhs, const int32_t* done, int done_stride,
                                 cudaStream_t s);
