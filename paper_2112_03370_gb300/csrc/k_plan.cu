@@ -5,6 +5,7 @@
 // Excision (Sect. 2.4): a pixel with fewer than 3 hits or cond_2(B_p) > cond_max is dropped with
 // all its samples.  Local pixel ids are assigned in ascending global order over kept pixels
 // (Sect. 3.1 local indexation).
+#include "df64.cuh"
 #include "mm_internal.cuh"
 
 namespace mm {
@@ -37,17 +38,24 @@ __device__ __forceinline__ int block_of(const int64_t* __restrict__ off, int32_t
   return lo;
 }
 
-__global__ void k_bd_accum(const int32_t* __restrict__ pix, const float* __restrict__ psi,
+// Each CTA takes a contiguous chunk of the samples and its threads stride through it, so a thread's
+// block index is found once and only moves forward; the weights are the plan's FP64 (cos 2psi, sin 2psi).
+__global__ void k_bd_accum(const int32_t* __restrict__ pix, const double2* __restrict__ w64,
                            const int64_t* __restrict__ off, const double* __restrict__ c0_blk,
                            int32_t n_blocks, int64_t N, double* __restrict__ B6,
                            int32_t* __restrict__ hits) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t chunk = (N + gridDim.x - 1) / gridDim.x;
+  const int64_t c_lo = (int64_t)blockIdx.x * chunk, c_hi = min(N, c_lo + chunk);
+  int64_t i = c_lo + threadIdx.x;
+  if (i >= c_hi) return;
+  int bi = block_of(off, n_blocks, i);
+  for (; i < c_hi; i += blockDim.x) {
+    while (__ldg(off + bi + 1) <= i) bi++;
     const int32_t p = pix[i];
     if (p < 0) continue;
-    const double c0 = c0_blk[block_of(off, n_blocks, i)];
-    double s, c;
-    sincos(2.0 * (double)psi[i], &s, &c);
+    const double c0 = c0_blk[bi];
+    const double2 w = w64[i];
+    const double c = w.x, s = w.y;
     double* b = B6 + 6 * (int64_t)p;
     atomicAdd(b + 0, c0);
     atomicAdd(b + 1, c0 * c);
@@ -59,11 +67,11 @@ __global__ void k_bd_accum(const int32_t* __restrict__ pix, const float* __restr
   }
 }
 
-cudaError_t launch_bd_accum(const int32_t* pix, const float* psi, const int64_t* block_off,
+cudaError_t launch_bd_accum(const int32_t* pix, const double2* w64, const int64_t* block_off,
                             const double* c0_blk, int32_t n_blocks, int64_t N, double* B6,
                             int32_t* hits, cudaStream_t s) {
   if (N == 0) return cudaSuccess;
-  k_bd_accum<<<8 * 152, 256, 0, s>>>(pix, psi, block_off, c0_blk, n_blocks, N, B6, hits);
+  k_bd_accum<<<8 * 152, 256, 0, s>>>(pix, w64, block_off, c0_blk, n_blocks, N, B6, hits);
   return cudaGetLastError();
 }
 
@@ -250,37 +258,27 @@ cudaError_t launch_localize(const int32_t* pix, const int32_t* keep, const int32
   return cudaGetLastError();
 }
 
-__global__ void k_weights64(const float* __restrict__ psi, int64_t N, double2* __restrict__ w) {
+// (cos 2psi, sin 2psi) once per sample in FP64 (the FP64 pipe runs at 1/64 of the FP32 rate, so the
+// sine and cosine are taken once): w64 as is, w32 as their FP32 roundings, wdf (if non-null) split
+// into df64 (hi, lo) pairs
+__global__ void k_weights(const float* __restrict__ psi, int64_t N, double2* __restrict__ w64,
+                          float2* __restrict__ w32, float4* __restrict__ wdf) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     double s, c;
     sincos(2.0 * (double)psi[i], &s, &c);
-    w[i] = make_double2(c, s);
+    w64[i] = make_double2(c, s);
+    w32[i] = make_float2((float)c, (float)s);
+    if (wdf) {
+      const df dc(c), ds(s);
+      wdf[i] = make_float4(dc.hi, dc.lo, ds.hi, ds.lo);
+    }
   }
 }
 
-// (cos 2psi, sin 2psi) in FP32 with the accurate single-precision sincosf: the FP32 operator must
-// stay within a few ulp of the FP64 one, or the FP64-class residual replacement of the
-// mixed-precision solver stops converging (a systematic weight error perturbs the smallest
-// eigenvalues of A)
-__global__ void k_weights32(const float* __restrict__ psi, int64_t N, float2* __restrict__ w) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    float s, c;
-    sincosf(2.f * psi[i], &s, &c);
-    w[i] = make_float2(c, s);
-  }
-}
-
-cudaError_t launch_weights32(const float* psi, int64_t N, float2* w32, cudaStream_t s) {
+cudaError_t launch_weights(const float* psi, int64_t N, double2* w64, float2* w32, float4* wdf, cudaStream_t s) {
   if (N == 0) return cudaSuccess;
-  k_weights32<<<8 * 152, 256, 0, s>>>(psi, N, w32);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_weights64(const float* psi, int64_t N, double2* w64, cudaStream_t s) {
-  if (N == 0) return cudaSuccess;
-  k_weights64<<<8 * 152, 256, 0, s>>>(psi, N, w64);
+  k_weights<<<8 * 152, 256, 0, s>>>(psi, N, w64, w32, wdf);
   return cudaGetLastError();
 }
 

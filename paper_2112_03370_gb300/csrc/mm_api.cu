@@ -402,7 +402,12 @@ int build_plan(const mm_problem_desc* d, cudaStream_t us, Plan* P) {
   MM_TRY(scr.alloc(&scan_scratch, sl));
   MM_CUDA(cudaMemsetAsync(B6, 0, 6 * P->n_pix * sizeof(double), s));
   MM_CUDA(cudaMemsetAsync(hits, 0, P->n_pix * sizeof(int32_t), s));
-  MM_CUDA(launch_bd_accum(pix, P->psi, P->block_off_dev, P->c0_blk, nb, P->N, B6, hits, s));
+  // pointing weights first (one FP64 sincos per sample), then the BD blocks from them
+  MM_TRY(dalloc(P, &P->w64, P->N));
+  MM_TRY(dalloc(P, &P->w32, P->N));
+  if (P->df64) MM_TRY(dalloc(P, &P->wdf, P->N));
+  MM_CUDA(launch_weights(P->psi, P->N, P->w64, P->w32, P->df64 ? P->wdf : nullptr, s));
+  MM_CUDA(launch_bd_accum(pix, P->w64, P->block_off_dev, P->c0_blk, nb, P->N, B6, hits, s));
   MM_CUDA(launch_bd_finalize(B6, hits, P->n_pix, P->cond_max, keep, inv6, s));
   MM_CUDA(launch_scan_keep(keep, P->n_pix, lid, flag + 1, scan_scratch, (int64_t)sl, s));
   MM_CUDA(cudaMemcpyAsync(hflag, flag, sizeof(hflag), cudaMemcpyDeviceToHost, s));
@@ -414,10 +419,6 @@ int build_plan(const mm_problem_desc* d, cudaStream_t us, Plan* P) {
   MM_TRY(dalloc(P, &P->lpix, P->N));
   MM_CUDA(launch_compact(keep, lid, inv6, P->n_pix, P->obs_to_global, P->minv, s));
   MM_CUDA(launch_localize(pix, keep, lid, P->N, P->lpix, s));
-  MM_TRY(dalloc(P, &P->w64, P->N));
-  MM_CUDA(launch_weights64(P->psi, P->N, P->w64, s));
-  MM_TRY(dalloc(P, &P->w32, P->N));
-  MM_CUDA(launch_weights32(P->psi, P->N, P->w32, s));
 
   // Toeplitz spectra: L-point circulant spectrum of each distinct band, then the pair tables
   BandTables bt = dedupe_bands(band, nb, lam);
@@ -442,10 +443,8 @@ int build_plan(const mm_problem_desc* d, cudaStream_t us, Plan* P) {
   MM_CUDA(launch_pair_tables(H, P->n_tab, costab_d, P->tab64, P->tab32, s));
   MM_CUDA(launch_twiddles(P->tw64, P->tw32, costab_d, s));
   if (P->df64) {
-    MM_TRY(dalloc(P, &P->wdf, P->N));
     MM_TRY(dalloc(P, &P->tabdf, (size_t)P->n_tab * kM));
     MM_TRY(dalloc(P, &P->twdf, kM));
-    MM_CUDA(launch_weights_df(P->psi, P->N, P->wdf, s));
     MM_CUDA(launch_c64_to_df(P->tab64, (int64_t)P->n_tab * kM, P->tabdf, s));
     MM_CUDA(launch_c64_to_df(P->tw64, kM, P->twdf, s));
   }
@@ -2064,7 +2063,7 @@ int mm_templates_set(mm_plan_t plan, const mm_templates_desc* t, void* stream) {
   MM_TRY(dalloc(P, &ts->M32, 2 * P->n_obs));
   MM_CUDA(cudaMemsetAsync(ts->M64, 0, 6 * P->n_obs * sizeof(double), s));
   MM_CUDA(cudaMemsetAsync(hits, 0, P->n_obs * sizeof(int32_t), s));
-  MM_CUDA(launch_bd_accum(P->lpix, P->psi, P->block_off_dev, P->c0_blk, nb, P->N, ts->M64, hits, s));
+  MM_CUDA(launch_bd_accum(P->lpix, P->w64, P->block_off_dev, P->c0_blk, nb, P->N, ts->M64, hits, s));
   MM_CUDA(launch_m64_to_32(ts->M64, P->n_obs, ts->M32, s));
   MM_CUDA(cudaStreamSynchronize(s));
   // the scratch inputs are gone once this returns

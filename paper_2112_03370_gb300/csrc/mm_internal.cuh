@@ -173,7 +173,7 @@ int dalloc(Plan* p, T** ptr, size_t n) {
 // launchers (each returns a cudaError_t of its launch)
 // ---------------------------------------------------------------------------------------------
 // plan kernels (k_plan.cu)
-cudaError_t launch_bd_accum(const int32_t* pix, const float* psi, const int64_t* block_off,
+cudaError_t launch_bd_accum(const int32_t* pix, const double2* w64, const int64_t* block_off,
                             const double* c0_blk, int32_t n_blocks, int64_t N, double* B6,
                             int32_t* hits, cudaStream_t s);
 cudaError_t launch_bd_finalize(const double* B6, const int32_t* hits, int64_t n_pix,
@@ -185,8 +185,8 @@ cudaError_t launch_compact(const int32_t* keep, const int32_t* lid, const double
                            int64_t n_pix, int32_t* obs_to_global, double* minv, cudaStream_t s);
 cudaError_t launch_localize(const int32_t* pix, const int32_t* keep, const int32_t* lid,
                             int64_t N, int32_t* lpix, cudaStream_t s);
-cudaError_t launch_weights64(const float* psi, int64_t N, double2* w64, cudaStream_t s);
-cudaError_t launch_weights32(const float* psi, int64_t N, float2* w32, cudaStream_t s);
+// (cos 2psi, sin 2psi) in FP64, their FP32 roundings and (wdf non-null) their df64 split, one sincos per sample
+cudaError_t launch_weights(const float* psi, int64_t N, double2* w64, float2* w32, float4* wdf, cudaStream_t s);
 cudaError_t launch_validate(const int32_t* pix, const float* psi, int64_t N, int64_t n_pix,
                             int32_t* bad, cudaStream_t s);
 cudaError_t launch_spectra(const double* band_rows, int32_t n_tab, int32_t lambda,
