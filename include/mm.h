@@ -263,12 +263,18 @@ int mm_ecg_solve(mm_plan_t plan, const double* b, double* x, int t, int variant,
  *             az_interp = 1, linear interpolation between n_az equally spaced nodes;
  *   n_hwp     harmonics cos(k phi), sin(k phi), k = 1..n_hwp, of the HWP angle phi (0..8).
  *   n_poly + n_az + 2 n_hwp must lie in [1, 64].
- *   az, hwp   [N] float32 per sample (host, or device with inputs_on_device); copied.
- * Each block's kernel T^T W T is built in FP64 and pseudo-inverted (eigenvalues below 1e-12 of the
- * largest dropped); azimuth bins are decided once in FP64.  The FP32 operator filters in FP32, the
- * FP64-class one in IEEE FP64 (also on df64 plans).  Replaces previous templates.  Synchronous.
- * MM_EINVAL for a plan with lambda > 0 or counts out of range; mm_apply_A_noalloc rejects such
- * plans. */
+ *   az, hwp   [N] float32 per sample (host, or device with inputs_on_device); read during the call
+ *             only (the caller keeps ownership; nothing keeps a pointer to them).
+ * Setup: azimuth bins and interpolation fractions decided once in FP64 (every operator uses the
+ * same ones), cos/sin of phi tabulated in FP32 and df64, each block's kernel T^T W T built in df64
+ * (FP64-class) and pseudo-inverted (eigenvalues below 1e-12 of the largest dropped), and
+ * M = P~^T W P~ per pixel.  The operators apply A x = M x - P~^T W T c with
+ * c = (T^T W T)^+ T^T W P~ x in one fused kernel per application: FP32 for the FP32 (mixed-precision)
+ * iterations, df64 for the FP64-class operator and b on every plan precision.  Plan memory grows by
+ * about 25 B per sample (1 B bin, 8 + 16 B cos/sin of phi; + 12 B with interpolation; + 16 B of df64
+ * pointing weights on plans that lack them) and 80 B per pixel.  Replaces previous templates.
+ * Synchronous.  MM_EINVAL for a plan with lambda > 0, counts out of range or a block of 2^31 or
+ * more samples; MM_ENOMEM when the tables do not fit; mm_apply_A_noalloc rejects such plans. */
 typedef struct {
   int32_t n_poly;
   int32_t n_az;

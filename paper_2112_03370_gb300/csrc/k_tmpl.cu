@@ -4,10 +4,12 @@
 //   azimuth bins over the block's azimuth range (value 1), or linear interpolation between n_az nodes;
 //   cos(k phi), sin(k phi) of the HWP angle, k = 1..n_hwp.
 // W = diag(w_b) on the kept samples of block b (w_b = the band's c_0 of a lambda = 0 plan), 0 on masked
-// ones.  The kernel T^T W T of every block is built in FP64 and pseudo-inverted (eigenvalues below
-// 1e-12 of the largest dropped) when the templates are attached; the filter then costs two passes over
-// the block's samples per application.  Azimuth bins and interpolation fractions are decided once, in
-// FP64, so the FP32 and FP64 operators use the same templates.
+// ones.  When the templates are attached, the setup decides the azimuth bins and interpolation
+// fractions once in FP64 (so every operator uses the same templates), tabulates cos/sin of the HWP
+// angle in FP32 and df64, builds T^T W T of every block in df64 and pseudo-inverts it (eigenvalues
+// below 1e-12 of the largest dropped).  An application A x = P^T F_T P x = M x - P^T W T c, with
+// M = P^T W P per pixel and c = (T^T W T)^+ T^T W P x, then costs one fused kernel that streams each
+// block twice (FP32 for the iterations, df64 for the FP64-class operator and the right-hand side).
 #include <math.h>
 
 #include <cooperative_groups.h>
