@@ -102,3 +102,43 @@ def test_templates_rejected_where_they_do_not_apply():
     with pytest.raises(mm().MMError) as ei:
         attach(gp2, TMS[0], np.zeros(10000, np.float32), np.zeros(10000, np.float32))
     assert ei.value.code == 1
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (2, 1e-11), (1, 2e-5)])
+def test_template_apply_several_columns(precision, tol):
+    # nrhs = 3 in one call (the block and enlarged solvers apply A to several columns at once):
+    # every column equals the oracle's single-column operator
+    tm = TMS[1]
+    prob, w, az, hwp = problem(65)
+    gp, op, nb = plans(prob, precision=precision)
+    attach(gp, tm, az, hwp)
+    X = np.random.default_rng(7).standard_normal((3, op.n_obs, 3))
+    Y = torch.empty(3, op.n_obs, 3, dtype=torch.float64, device="cuda")
+    mm().mm_apply_A(gp, cuda(X), Y)
+    Yc = Y.cpu().numpy()
+    for r in range(3):
+        assert rel_max(Yc[r], O.apply_A_templates(op, w, tm, az, hwp, X[r])) < tol
+
+
+def test_template_block_cg_matches_dense_solve():
+    # block CG (mixed precision) on three right-hand sides of a template plan: the system is only
+    # semi-definite (the I offset is free), so each column is compared with a least-squares solve
+    # of the dense oracle system on Q, U, and its residual is checked with the oracle operator
+    tm = O.Templates(n_poly=2, n_az=6, n_hwp=1)
+    prob, w, az, hwp = problem(66, lens=(20000, 16000, 18000), n_pix=60)
+    gp, op, nb = plans(prob, precision=3)
+    attach(gp, tm, az, hwp)
+    rng = np.random.default_rng(8)
+    D = rng.standard_normal((3, op.lpix.size))
+    B = np.stack([O.rhs_templates(op, w, tm, az, hwp, D[r]) for r in range(3)])
+    A = np.stack([O.apply_A_templates(op, w, tm, az, hwp, e.reshape(-1, 3)).reshape(-1)
+                  for e in np.eye(3 * op.n_obs)], axis=1)
+    X = torch.empty(3, op.n_obs, 3, dtype=torch.float64, device="cuda")
+    infos = mm().mm_block_cg_solve(gp, cuda(B), X, block_width=3, tol=1e-9, max_iter=3000)
+    assert all(i.status == 0 for i in infos)
+    Xc = X.cpu().numpy()
+    for r in range(3):
+        xs = np.linalg.lstsq(A, B[r].reshape(-1), rcond=None)[0].reshape(-1, 3)
+        assert np.max(np.abs(Xc[r][:, 1:] - xs[:, 1:])) <= 1e-5 * np.max(np.abs(xs[:, 1:]))
+        res = A @ Xc[r].reshape(-1) - B[r].reshape(-1)
+        assert np.linalg.norm(res) <= 1e-8 * np.linalg.norm(B[r])

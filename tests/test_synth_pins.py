@@ -68,3 +68,29 @@ def test_ground_pointing_recipe():
     # psi = phi_det + 2 * (2 pi f_hwp t): detector 1 starts at 45 deg
     assert abs(float(psi[cfg.n_samp]) - math.pi / 4) < 1e-6
     assert float(psi.min()) >= 0 and float(psi.max()) < 2 * math.pi
+
+
+def test_ground_template_streams_and_systematics():
+    cfg = synth.tiny_config(n_det=3, n_int=2)
+    pix, psi = synth.ground_pointing(cfg)
+    az, hwp = synth.ground_template_streams(cfg)
+    n = cfg.n_samp
+    assert az.numel() == hwp.numel() == pix.numel()
+    # the HWP angle is the rotation folded into psi: psi = phi_det + 2 phi_hwp (mod 2 pi)
+    for det, k in ((0, 0), (1, 1), (2, 1)):
+        lo = (det * cfg.n_int + k) * n
+        d = np.remainder(psi[lo:lo + 1000].double().numpy() - (det % 4) * math.pi / 4
+                         - 2 * hwp[lo:lo + 1000].double().numpy(), 2 * math.pi)
+        assert np.max(np.minimum(d, 2 * math.pi - d)) < 1e-5
+    t = (n + np.arange(5)) / cfg.fs   # interval 1 continues the clock
+    np.testing.assert_allclose(hwp[n:n + 5].double().numpy(), np.remainder(2 * math.pi * cfg.hwp_hz * t, 2 * math.pi),
+                               atol=1e-6)
+    # azimuth: the raster's fast coordinate over a 10-degree sweep, the same for every detector
+    sweep = int(round(cfg.side / cfg.speed))
+    a0 = az[:2 * sweep].numpy()
+    assert a0.min() == 180.0 and a0.max() == 190.0 and a0[0] == 180.0 and a0[sweep] == 190.0
+    np.testing.assert_array_equal(az[:n].numpy(), az[2 * n:3 * n].numpy())
+    # systematics: ground steps of 0.01 per 0.33 deg from the block's lowest azimuth, plus harmonics
+    s = synth.template_systematics(cfg, az, hwp, seed=3, n_harm=0)
+    a = az[:n].double().numpy()
+    np.testing.assert_allclose(s[:n].numpy(), 1 + 0.01 * np.floor((a - a.min()) / 0.33), rtol=1e-12)
