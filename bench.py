@@ -191,6 +191,31 @@ def cpu_oracle_rate(n_dets: int, n_applies: int = 2, with_iteration: bool = True
     return n * n_applies / dt, dt, n
 
 
+def ground_config_json(cfg, world: int) -> dict:
+    """The bench line's config for the ground workload (the same for both arms)."""
+    return {"workload": f"ground: {cfg.n_det} det x {cfg.n_int} int x {cfg.n_samp} "
+                        f"samples, {cfg.side}x{cfg.side} IQU patch, lambda {cfg.lam}",
+            "n_samples": cfg.n_total, "lambda": cfg.lam, "tol": cfg.tol,
+            "step": "rhs + mixed-precision PCG solve (FP32 operators in the iterations; FP64 CG "
+                    "vectors, dots and scalars; rhs and residual replacement with "
+                    "double-float operators)",
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "l2": "inputs larger than L2 (pixel index and FP32 weights 12 B/sample, 12.9 GB)"}
+
+
+def aggregate(elapsed: float, samples: float, dist_mod=None, device="cpu"):
+    """Whole-job timing across ranks: the slowest rank's elapsed time and the samples all ranks
+    processed (replicas may run different iteration counts)."""
+    if dist_mod is None or not dist_mod.is_initialized() or dist_mod.get_world_size() == 1:
+        return elapsed, samples
+    import torch
+    t = torch.tensor([elapsed], dtype=torch.float64, device=device)
+    n = torch.tensor([samples], dtype=torch.float64, device=device)
+    dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    dist_mod.all_reduce(n, op=dist_mod.ReduceOp.SUM)
+    return float(t), float(n)
+
+
 # ------------------------------------------------------------------------------------------
 # the reference arm: the FP64 oracle on the host cores
 # ------------------------------------------------------------------------------------------
@@ -199,6 +224,7 @@ def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    import synth
     rates = []
     for i in range(a.warmup + a.steps):
         r, dt, n = cpu_oracle_rate(a.cpu_dets, n_applies=1)
@@ -212,9 +238,9 @@ def run_reference(a):
         "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": n / v * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "ground (sampled for the CPU oracle)", "n_samples_per_step": n},
+        "config": ground_config_json(synth.ground_config(), 1),
         "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample + f" ({n} samples)"},
         "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -290,13 +316,10 @@ def run_ours(a):
     barrier()
     clk = clocks.stop() if clocks else None
     elapsed = ev0.elapsed_time(ev1) / 1e3
-    if world > 1:
-        t = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t)
     applies = sum(i.n_apply32 + i.n_apply64 for i in infos)
     iters = sum(i.iters for i in infos)
-    samples = N * applies * world
+    elapsed, samples = aggregate(elapsed, float(N * applies), dist if world > 1 else None, dev)
+    _, iters_all = aggregate(elapsed, float(iters), dist if world > 1 else None, dev)
     value = samples / elapsed
     t32 = sum(i.t_apply32_ms for i in infos)
     tup = sum(i.t_unpoint32_ms for i in infos)
@@ -339,16 +362,9 @@ def run_ours(a):
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": elapsed / a.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64",
            "data": "synthetic (seeded, generated on the device)",
-           "config": {"workload": f"ground: {prob.n_det} det x {prob.n_int} int x {cfg.n_samp} "
-                                  f"samples, {cfg.side}x{cfg.side} IQU patch, lambda {cfg.lam}",
-                      "n_samples": N, "n_obs": plan.n_obs, "lambda": cfg.lam, "tol": cfg.tol,
-                      "step": "rhs + mixed-precision PCG solve (FP32 operators in the iterations; FP64 CG "
-                              "vectors, dots and scalars; rhs and residual replacement with "
-                              "double-float operators)",
-                      "parallelism": "replicas" if world > 1 else "single GPU",
-                      "l2": "inputs larger than L2 (pixel index and FP32 weights 12 B/sample, 12.9 GB)"},
+           "config": ground_config_json(cfg, world), "n_obs": plan.n_obs,
            "solves_per_s": a.steps * world / elapsed,
-           "pcg_iters_per_s": iters * world / elapsed,
+           "pcg_iters_per_s": iters_all / elapsed,
            "iters_per_solve": iters / a.steps,
            "a_applies_per_solve": applies / a.steps,
            "true_rel_res": max(i.true_rel_res for i in infos),
@@ -404,7 +420,8 @@ def run_ours(a):
             e_app += inf.n_apply32 + inf.n_apply64
         barrier()
         te = time.perf_counter() - t0
-        out["e2e"] = {"value": N * e_app * world / te, "unit": "samples/s",
+        te, e_samples = aggregate(te, float(N * e_app), dist if world > 1 else None, dev)
+        out["e2e"] = {"value": e_samples / te, "unit": "samples/s",
                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(m_host.numel() * 8),
                       "steps": a.e2e_steps, "ms_per_step": te / a.e2e_steps * 1e3,
                       "includes": "mm_plan from pinned host pix/psi/band, H2D of d (on a side stream, "
