@@ -217,8 +217,11 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
  * operators; the search blocks are FP32, X, R and the block_width x block_width matrices FP64.
  * A column stops when ||R_j|| < tol ||b_j||, confirmed by an FP64 true residual; columns above tol
  * restart from their true residual.  b, x: [nrhs][n_obs][3] device; info: HOST [nrhs]
- * (iters = block iterations to convergence).  Blocks the calling thread.  Returns the worst
- * per-column status (MM_ENOTCONV after opts->max_iter block iterations, MM_EBREAKDOWN). */
+ * (iters = block iterations to convergence).  With FP32 operators, a block that loses all its
+ * directions away from a (re)start restarts from the FP64-class true residual (operator noise along
+ * a null direction of a semi-definite A, as with templates); right after a restart that is a
+ * breakdown.  Blocks the calling thread.  Returns the worst per-column status (MM_ENOTCONV after
+ * opts->max_iter block iterations, MM_EBREAKDOWN). */
 int mm_block_cg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, int block_width,
                       const mm_solve_opts* opts, mm_solve_info* info, void* stream);
 
@@ -245,7 +248,9 @@ enum { MM_ECG_ORTHOMIN = 0, MM_ECG_ORTHODIR = 1 };
  *                FP32; MM_FP64: the plan's FP64-class operator); precond must be MM_PREC_BD.
  * b, x: [n_obs][3] float64 device; info: HOST, one entry (iters = block iterations, batch = t).
  * Blocks the calling thread.  MM_ENOTCONV after max_iter iterations, MM_EBREAKDOWN when the block
- * loses all its directions or a norm is not finite; MM_EINVAL for bad arguments or a
+ * loses all its directions on the first step from a (re)start or a norm is not finite (with FP32
+ * search blocks a block that loses all its directions later restarts from the true residual, as
+ * on semi-definite template systems); MM_EINVAL for bad arguments or a
  * MM_TPLZ_DIRECT plan. */
 int mm_ecg_solve(mm_plan_t plan, const double* b, double* x, int t, int variant, const mm_solve_opts* opts,
                  mm_solve_info* info, void* stream);

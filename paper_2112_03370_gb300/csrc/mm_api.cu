@@ -1543,8 +1543,35 @@ int mm_block_cg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, int 
     }
     int it = 0, restarts = 0, r = 0;
     bool fresh = true;   // Z = M R without the A-orthogonalisation (first step, or a restart)
+    bool cont = false;
+    // FP64-class true residual R = B - A X; columns above tol stay active and restart from it
+    // (cont) unless the iteration or restart budget is spent
+    auto true_residual = [&]() -> int {
+      MM_CUDA(cudaMemsetAsync(B->AX, 0, n4 * sizeof(double), s));
+      MM_TRY(apply64_internal(P, B->X, B->AX, sg, s));
+      MM_CUDA(launch_bresid(B->B, B->AX, sg, n, B->R, B->norm_part, kBlkCtas, B->norms, s));
+      n_kernels += 3;
+      n_apply64 += 1;
+      MM_TRY(read_norms(sg));
+      active.clear();
+      for (int j = 0; j < sg; j++) {
+        tn2[j] = B->host[j];
+        rn2[j] = tn2[j];
+        if (bn2[j] > 0.0 && !(tn2[j] < tol2 * bn2[j])) {
+          conv[j] = 0;
+          active.push_back(j);
+        }
+      }
+      cont = !(active.empty() || it >= opts->max_iter || restarts >= 8);
+      if (cont) {
+        restarts += 1;
+        fresh = true;
+      }
+      return MM_OK;
+    };
     while (!active.empty()) {
       const int t = (int)active.size();
+      const bool after_restart = fresh;
       MM_CUDA(cudaMemcpyAsync(B->idx, active.data(), t * sizeof(int), cudaMemcpyHostToDevice, s));
       MM_CUDA(launch_bprecond(P->minv, B->R, B->idx, t, n, B->Z, s));   // Z = M R[active]
       n_kernels += 1;
@@ -1566,6 +1593,14 @@ int mm_block_cg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, int 
       r = B->host_i[0];
       n_kernels += 3;
       if (r == 0) {
+        // every direction dropped: on the FP32 path away from a restart this is operator noise
+        // along a (near-)null direction of a semi-definite A (e.g. the map offset degenerate with
+        // templates), so restart from the true residual; right after a restart it is a breakdown
+        if (fp32 && !after_restart) {
+          MM_TRY(true_residual());
+          if (cont) continue;
+          break;
+        }
         for (int j : active) status[j] = MM_EBREAKDOWN;
         break;
       }
@@ -1595,25 +1630,8 @@ int mm_block_cg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, int 
       for (int j = 0; j < sg; j++) bad = bad || status[j] == MM_EBREAKDOWN;
       if (bad) break;
       if (active.empty() || it >= opts->max_iter) {
-        // FP64 true residual R = B - A X; columns above tol restart from it
-        MM_CUDA(cudaMemsetAsync(B->AX, 0, n4 * sizeof(double), s));
-        MM_TRY(apply64_internal(P, B->X, B->AX, sg, s));
-        MM_CUDA(launch_bresid(B->B, B->AX, sg, n, B->R, B->norm_part, kBlkCtas, B->norms, s));
-        n_kernels += 3;
-        n_apply64 += 1;
-        MM_TRY(read_norms(sg));
-        active.clear();
-        for (int j = 0; j < sg; j++) {
-          tn2[j] = B->host[j];
-          rn2[j] = tn2[j];
-          if (bn2[j] > 0.0 && !(tn2[j] < tol2 * bn2[j])) {
-            conv[j] = 0;
-            active.push_back(j);
-          }
-        }
-        if (active.empty() || it >= opts->max_iter || restarts >= 8) break;
-        restarts += 1;
-        fresh = true;
+        MM_TRY(true_residual());
+        if (!cont) break;
       }
     }
     for (int j = 0; j < sg; j++) {
@@ -1703,7 +1721,7 @@ int mm_ecg_solve(mm_plan_t plan, const double* b, double* x, int t, int variant,
     constexpr int kStall = 10;
     constexpr double kStallZone2 = 1e-12;
     double best = INFINITY;
-    int since_best = 0;
+    int since_best = 0, inner = 0;
     while (it < opts->max_iter) {
       MM_TRY(blk_apply(P, B, tz, fp32, s));                                   // AZ = A Z
       n_kernels += fp32 ? 2 : 3;
@@ -1715,9 +1733,17 @@ int mm_ecg_solve(mm_plan_t plan, const double* b, double* x, int t, int variant,
       const int r = B->host_i[0];
       n_kernels += 3;
       if (r == 0) {
+        // every direction dropped: on the FP32 path after the first step of a recurrence this is
+        // operator noise along a (near-)null direction of a semi-definite A (the map offset of
+        // template plans), so the recurrence restarts from the true residual as after a stall
+        if (fp32 && inner > 0) {
+          stalled = true;
+          break;
+        }
         status = MM_EBREAKDOWN;
         break;
       }
+      inner += 1;
       // P_k = Z (Z^T A Z)^{-1/2} and A P_k; alpha = P_k^T R; X += P alpha; R -= A P alpha
       MM_CUDA(launch_linv_coef(B->Linv, B->piv, B->rank, tz, B->Cmb, s));
       MM_CUDA(launch_bcombine(B->P, 0, nullptr, r, B->Z, tz, B->Cmb, tz, 1.0, 0, n, nullptr, kBlkCtas, nullptr, s));

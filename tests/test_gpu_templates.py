@@ -142,3 +142,24 @@ def test_template_block_cg_matches_dense_solve():
         assert np.max(np.abs(Xc[r][:, 1:] - xs[:, 1:])) <= 1e-5 * np.max(np.abs(xs[:, 1:]))
         res = A @ Xc[r].reshape(-1) - B[r].reshape(-1)
         assert np.linalg.norm(res) <= 1e-8 * np.linalg.norm(B[r])
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_template_ecg_matches_dense_solve(variant):
+    # enlarged CG (t = 4, FP32 search blocks) on a template plan, against a least-squares solve of
+    # the dense oracle system on Q, U (the I offset is free)
+    tm = O.Templates(n_poly=2, n_az=6, n_hwp=1)
+    prob, w, az, hwp = problem(67, lens=(20000, 16000, 18000), n_pix=60)
+    gp, op, nb = plans(prob, precision=3)
+    attach(gp, tm, az, hwp)
+    d = np.random.default_rng(9).standard_normal(op.lpix.size)
+    b = O.rhs_templates(op, w, tm, az, hwp, d)
+    A = np.stack([O.apply_A_templates(op, w, tm, az, hwp, e.reshape(-1, 3)).reshape(-1)
+                  for e in np.eye(3 * op.n_obs)], axis=1)
+    x = torch.empty(op.n_obs, 3, dtype=torch.float64, device="cuda")
+    e = mm().mm_ecg_solve(gp, cuda(b), x, 4, variant=variant, tol=1e-9, max_iter=3000)
+    assert e.status == 0
+    xs = np.linalg.lstsq(A, b.reshape(-1), rcond=None)[0].reshape(-1, 3)
+    xr = x.cpu().numpy()
+    assert np.max(np.abs(xr[:, 1:] - xs[:, 1:])) <= 1e-5 * np.max(np.abs(xs[:, 1:]))
+    assert np.linalg.norm(A @ xr.reshape(-1) - b.reshape(-1)) <= 1e-8 * np.linalg.norm(b)
