@@ -139,7 +139,8 @@ __device__ __forceinline__ float legendre_dot(float x, int n, const float (&c)[N
 }
 
 // cos(k phi), sin(k phi), k = 1..n, by the angle-addition recurrence from cos(phi), sin(phi) (FP32
-// roundings of the FP64 values, precomputed), generated and consumed on the fly: ac[k-1] += cos(k phi) v, as[k-1] += sin(k phi) v, or sum_k cc[k-1] cos(k phi) + cs[k-1] sin(k phi)
+// roundings of the FP64 values, precomputed), generated and consumed on the fly:
+// ac[k-1] += cos(k phi) v and as[k-1] += sin(k phi) v, or sum_k cc[k-1] cos(k phi) + cs[k-1] sin(k phi)
 template <int NH>
 __device__ __forceinline__ void harmonics_acc(float2 cs1, int n, float v, float (&ac)[NH], float (&as)[NH]) {
   const float c1 = cs1.x, s1 = cs1.y;

@@ -29,8 +29,11 @@ def attach(gp, tm, az, hwp):
                           az=torch.as_tensor(az, device="cuda"), hwp=torch.as_tensor(hwp, device="cuda"))
 
 
+# the mixes cover every kernel instantiation (<4,4>, <4,8>, <16,8>), binned and interpolated azimuth,
+# azimuth only, and more dense (Legendre, HWP) pairs than setup threads (16 + 2 x 8 columns: 528 pairs)
 TMS = [O.Templates(n_poly=3, n_az=6, n_hwp=2), O.Templates(n_poly=2, n_az=5, n_hwp=1, interp=True),
-       O.Templates(n_poly=16), O.Templates(n_az=64), O.Templates(n_hwp=8, n_poly=4, n_az=30)]
+       O.Templates(n_poly=16), O.Templates(n_az=64), O.Templates(n_hwp=8, n_poly=4, n_az=30),
+       O.Templates(n_poly=16, n_hwp=8)]
 
 
 @pytest.mark.parametrize("ti", range(len(TMS)))
