@@ -567,6 +567,9 @@ def run_noise(a):
     t0 = time.perf_counter()
     O.estimate_bands(prob.d[:n0].cpu().numpy(), prob.pix[:n0].cpu().numpy(), [n0], cfg.lam)
     t_cpu = time.perf_counter() - t0
+    pk, pk_kind = peaks()
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+    nbytes = 12.0 * prob.n_total   # the periodogram reads the pixel index (4 B) and d (8 B) once
     print(json.dumps({
         "workload": "noise", "metric": "TOD samples/s through the noise-weight estimation",
         "value": prob.n_total / t, "unit": "samples/s", "higher_is_better": True,
@@ -574,6 +577,10 @@ def run_noise(a):
                                f"lambda {cfg.lam}, 32768-sample segments, noise-only TOD",
                    "blocks": len(bl), "n_samples": prob.n_total},
         "s": t, "vs_true_parameters": err,
+        "roofline": {"bound": "hbm", "achieved": nbytes / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": nbytes / t / 1e9 / hbm_peak, "traffic": None,
+                     "kernel": "k_periodogram + k_psd_fit + k_band_from_fit (whole estimation; the "
+                               "periodogram reads 12 B/sample)", "peak_kind": pk_kind},
         "cpu_baseline": {"value": n0 / t_cpu, "unit": "samples/s", "cores": 1, "kind": "oracle",
                          "sample": f"one block of {n0} samples, numpy/scipy"}}), flush=True)
 
@@ -647,6 +654,8 @@ def run_templates(a):
     # pointing weights (8), cos/sin of the HWP angle (8) and the azimuth bin (1); the map gathers and
     # the per-pixel M x stay in L2
     tmpl_b = 2 * (4 + 8 + 8 + 1)
+    pk, pk_kind = peaks()
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
     print(json.dumps({
         "workload": "templates", "metric": "TOD samples/s per PCG iteration, template map-making",
         "value": N * inf.iters / t_solve, "unit": "samples/s", "higher_is_better": True,
@@ -662,6 +671,10 @@ def run_templates(a):
                             "data": "sky + ground pickup + HWPSS, no noise"},
         "fp32_apply_ms": ms32, "fp64_class_apply_ms": ms64,
         "fp32_apply_GBps_algorithmic": N * tmpl_b / (ms32 * 1e-3) / 1e9,
+        "roofline": {"bound": "hbm", "achieved": N * tmpl_b / (ms32 * 1e-3) / 1e9, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": N * tmpl_b / (ms32 * 1e-3) / 1e9 / hbm_peak, "traffic": None,
+                     "kernel": "k_tmpl_apply32 (42 B/sample over two passes) + k_tmpl_mx32",
+                     "peak_kind": pk_kind},
         "cpu_baseline": {"value": n0 / t_cpu, "unit": "samples/s through the template operator",
                          "cores": 1, "kind": "oracle",
                          "sample": f"one block of {n0} samples, numpy (dense T)"}}), flush=True)

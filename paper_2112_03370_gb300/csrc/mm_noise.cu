@@ -71,16 +71,30 @@ k_periodogram(const int32_t* __restrict__ pix, const double* __restrict__ d, con
     if (threadIdx.x == 0) *kept_sm = 0;
     __syncthreads();
     int kept = 0;
-    for (int j = threadIdx.x; j < kM; j += kTileThreads) {
-      float x[2];
+    // the pixel and data loads of NB sample pairs per thread are issued before any is used (the data
+    // load does not wait for the mask), then G d is packed as complex pairs
+    constexpr int NB = 8;
+    for (int j0 = threadIdx.x; j0 < kM; j0 += NB * kTileThreads) {
+      int32_t pv[NB][2];
+      double dv[NB][2];
 #pragma unroll
-      for (int h = 0; h < 2; h++) {
-        const int64_t t = 2 * (int64_t)j + h;
-        const bool ok = t < m && __ldg(pix + base + t) >= 0;
-        x[h] = ok ? (float)__ldg(d + base + t) : 0.f;
-        kept += ok ? 1 : 0;
+      for (int u = 0; u < NB; u++) {
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          const int64_t t = 2 * (int64_t)(j0 + u * kTileThreads) + h;
+          const bool in = j0 + u * kTileThreads < kM && t < m;
+          pv[u][h] = in ? __ldg(pix + base + t) : -1;
+          dv[u][h] = in ? __ldg(d + base + t) : 0.0;
+        }
       }
-      sm[smem_pad(j)] = make_float2(x[0], x[1]);
+#pragma unroll
+      for (int u = 0; u < NB; u++) {
+        const int j = j0 + u * kTileThreads;
+        if (j >= kM) continue;
+        const bool ok0 = pv[u][0] >= 0, ok1 = pv[u][1] >= 0;
+        kept += (ok0 ? 1 : 0) + (ok1 ? 1 : 0);
+        sm[smem_pad(j)] = make_float2(ok0 ? (float)dv[u][0] : 0.f, ok1 ? (float)dv[u][1] : 0.f);
+      }
     }
     atomicAdd(kept_sm, kept);
     __syncthreads();
@@ -90,9 +104,18 @@ k_periodogram(const int32_t* __restrict__ pix, const double* __restrict__ d, con
     used += 1;
     NoiseFFT::forward(sm, tw, ptab);
     const double inv = 1.0 / (double)n_kept;
-    for (int k = threadIdx.x; k < kBins; k += kTileThreads) {
-      const float2 X = real_spectrum(sm, k);
-      Pb[k] += ((double)X.x * X.x + (double)X.y * X.y) * inv;
+    // NB bins per thread: their row entries are read before any is updated (independent round trips)
+    for (int k0 = threadIdx.x; k0 < kBins; k0 += NB * kTileThreads) {
+      double acc[NB];
+#pragma unroll
+      for (int u = 0; u < NB; u++) acc[u] = k0 + u * kTileThreads < kBins ? Pb[k0 + u * kTileThreads] : 0.0;
+#pragma unroll
+      for (int u = 0; u < NB; u++) {
+        const int k = k0 + u * kTileThreads;
+        if (k >= kBins) continue;
+        const float2 X = real_spectrum(sm, k);
+        Pb[k] = acc[u] + ((double)X.x * X.x + (double)X.y * X.y) * inv;
+      }
     }
     __syncthreads();   // the next segment overwrites sm
   }
