@@ -146,6 +146,8 @@ typedef struct {
   int64_t n_kernels;     /* kernels launched by the solve (its own, all columns) */
   double t_queue_ms;     /* server: time from mm_submit to admission (t_ms then runs to completion) */
   double t_unpoint32_ms; /* profile = 1: part of t_apply32_ms spent in the separate t = P x kernel */
+  double t_point32_ms;   /* profile = 1: part of t_apply32_ms spent in the separate P^T kernel (0 when
+                            the Toeplitz tiles scatter P^T themselves) */
 } mm_solve_info;
 
 /* Build a plan: validate, copy inputs, compact observed pixels, build and invert the 3x3 BD
@@ -188,6 +190,9 @@ int mm_apply_A(mm_plan_t plan, const double* x, double* y, int nrhs, void* strea
  *   - nrhs * n_obs * 4 values of the plan's precision, twice (input and output), must fit in
  *     32 MiB (FP64: nrhs * n_obs <= 524,288; FP32: <= 1,048,576), else MM_EINVAL with a message;
  *   - FFT plans only (MM_TPLZ_DIRECT needs an N-sample buffer): MM_EINVAL otherwise;
+ *   - the plan's own operator arithmetic, as mm_apply_A: FP32 on MM_FP32 and MM_FP32_DF64 plans,
+ *     IEEE FP64 on MM_FP64 plans; MM_DF64 plans are refused with MM_EINVAL (their double-float
+ *     operator needs an N-sample buffer), as are plans with templates;
  *   - every call shares the array and leaves its contents behind (each call clears what it
  *     accumulates), so calls whose GPU work overlaps (several streams or threads) race: the
  *     caller must serialise them;

@@ -261,24 +261,33 @@ cudaError_t launch_localize(const int32_t* pix, const int32_t* keep, const int32
 // (cos 2psi, sin 2psi) once per sample in FP64 (the FP64 pipe runs at 1/64 of the FP32 rate, so the
 // sine and cosine are taken once): w64 as is, w32 as their FP32 roundings, wdf (if non-null) split
 // into df64 (hi, lo) pairs
+// One FP64 sincos of 2 psi per sample: the FP64 weights, their FP32 roundings, (wdf non-null) their
+// df64 split, and the angle 2 psi reduced to [-pi, pi] in FP64 and rounded once to FP32 (the FP32
+// window kernels evaluate the weights from it in registers).
 __global__ void k_weights(const float* __restrict__ psi, int64_t N, double2* __restrict__ w64,
-                          float2* __restrict__ w32, float4* __restrict__ wdf) {
+                          float2* __restrict__ w32, float4* __restrict__ wdf, float* __restrict__ ang2) {
+  constexpr double kTwoPi = 6.283185307179586476925;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = 2.0 * (double)psi[i];
     double s, c;
-    sincos(2.0 * (double)psi[i], &s, &c);
+    sincos(a, &s, &c);
     w64[i] = make_double2(c, s);
     w32[i] = make_float2((float)c, (float)s);
     if (wdf) {
       const df dc(c), ds(s);
       wdf[i] = make_float4(dc.hi, dc.lo, ds.hi, ds.lo);
     }
+    if (ang2) {
+      ang2[i] = (float)fma(-rint(a * (1.0 / kTwoPi)), kTwoPi, a);
+    }
   }
 }
 
-cudaError_t launch_weights(const float* psi, int64_t N, double2* w64, float2* w32, float4* wdf, cudaStream_t s) {
+cudaError_t launch_weights(const float* psi, int64_t N, double2* w64, float2* w32, float4* wdf, float* ang2,
+                           cudaStream_t s) {
   if (N == 0) return cudaSuccess;
-  k_weights<<<8 * 152, 256, 0, s>>>(psi, N, w64, w32, wdf);
+  k_weights<<<8 * sm_count(), 256, 0, s>>>(psi, N, w64, w32, wdf, ang2);
   return cudaGetLastError();
 }
 

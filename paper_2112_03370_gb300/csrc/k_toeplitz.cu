@@ -296,15 +296,22 @@ __device__ __forceinline__ void pair_meta(const TileArgs& a, int64_t g, int64_t 
 template <typename T, int MODE, int NB>
 __device__ __forceinline__ void gather_pairs(const TileArgs& a, int rhs, const TileDesc& td,
                                              const int64_t (&g)[NB], T (&v)[NB][2]) {
-  if constexpr (MODE == MODE_APPLY_T) {   // coalesced read of t = P x, zero outside the block
+  if constexpr (MODE == MODE_APPLY_T || MODE == MODE_NINV_T) {   // coalesced read of t, zero outside the block
     const float* t = reinterpret_cast<const float*>(a.x) + rhs * a.x_stride;
 #pragma unroll
-    for (int u = 0; u < NB; u++)
+    for (int u = 0; u < NB; u++) {
+      if (g[u] >= td.blk_lo && g[u] + 2 <= td.blk_hi) {   // g even and the column 8-byte aligned
+        const float2 f = __ldg(reinterpret_cast<const float2*>(t + g[u]));
+        v[u][0] = f.x;
+        v[u][1] = f.y;
+      } else {
 #pragma unroll
-      for (int e = 0; e < 2; e++) {
-        const int64_t gg = g[u] + e;
-        v[u][e] = (gg >= td.blk_lo && gg < td.blk_hi) ? (T)__ldg(t + gg) : T(0);
+        for (int e = 0; e < 2; e++) {
+          const int64_t gg = g[u] + e;
+          v[u][e] = (gg >= td.blk_lo && gg < td.blk_hi) ? (T)__ldg(t + gg) : T(0);
+        }
       }
+    }
     return;
   }
   int32_t p[NB][2];
@@ -558,7 +565,21 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
       cl.sync();
       other = cl.map_shared_rank(sm, rank ^ 1);
     }
-    if constexpr (CL == 1) {
+    if constexpr (MODE == MODE_NINV_T) {
+      // y of the tile's output range, float pairs (g even, so 8-byte aligned inside the range)
+      float* yo = reinterpret_cast<float*>(a.y) + rhs * a.y_stride;
+      const int n_lo = r_lo >> 1, n_hi = (r_hi + 1) >> 1;
+      for (int n = n_lo + threadIdx.x; n < n_hi; n += NT) {
+        const C z = sm[smem_pad(n)];
+        const int64_t g = td.in0 + 2 * (int64_t)n;
+        if (g >= td.out_lo && g + 2 <= td.out_hi) {
+          *reinterpret_cast<float2*>(yo + g) = make_float2(z.x, z.y);
+        } else {
+          if (g >= td.out_lo && g < td.out_hi) yo[g] = z.x;
+          if (g + 1 >= td.out_lo && g + 1 < td.out_hi) yo[g + 1] = z.y;
+        }
+      }
+    } else if constexpr (CL == 1) {
       constexpr int NB = 8;
       const int n_lo = r_lo >> 1, n_hi = (r_hi + 1) >> 1;
       for (int n0 = n_lo + threadIdx.x; n0 < n_hi; n0 += NB * NT) {
@@ -633,6 +654,7 @@ int tile_kernels_init() {
   MM_SET((k_tile<float, 1, MODE_RHS>), kSmemMax);
   MM_SET((k_tile<float, 1, MODE_APPLY, true>), kSmemMax);
   MM_SET((k_tile<float, 1, MODE_APPLY_T>), kSmemMax);
+  MM_SET((k_tile<float, 1, MODE_NINV_T>), kSmemMax);
   MM_SET((k_tile<double, 2, MODE_APPLY>), kSmemBytes64);
   MM_SET((k_tile<double, 2, MODE_RHS>), kSmemBytes64);
   MM_SET((k_tile<double, 2, MODE_NINV>), kSmemBytes64);
@@ -677,6 +699,7 @@ cudaError_t launch_tiles_fp32(int mode, const TileArgs& a, int halo_samples, cud
   if (smem > kSmemMax) return cudaErrorInvalidValue;
   if (mode == MODE_APPLY) return launch_tiles<float, 1, MODE_APPLY>(a, smem, s);
   if (mode == MODE_APPLY_T) return launch_tiles<float, 1, MODE_APPLY_T>(a, smem, s);
+  if (mode == MODE_NINV_T) return launch_tiles<float, 1, MODE_NINV_T>(a, smem, s);
   if (mode == MODE_RHS) return launch_tiles<float, 1, MODE_RHS>(a, smem, s);
   return cudaErrorInvalidValue;
 }
@@ -718,7 +741,7 @@ cudaError_t launch_unpoint32(const int32_t* lpix, const float2* w32, int64_t N, 
                              int64_t t_stride, cudaStream_t s) {
   if (N == 0 || nrhs <= 0) return cudaSuccess;
   int64_t g = (N + 1023) / 1024;
-  if (g > 152 * 16) g = 152 * 16;
+  if (g > 16 * sm_count()) g = 16 * sm_count();
   k_unpoint32<<<dim3((unsigned)g, nrhs), 256, 0, s>>>(lpix, w32, N, reinterpret_cast<const float4*>(x4),
                                                      x_stride / 4, done, done_stride, t, t_stride);
   return cudaGetLastError();

@@ -26,6 +26,22 @@ int fail(int code, const std::string& msg) {
   g_err = msg;
   return code;
 }
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 152;
+  if (dev >= 64) {
+    int n = 0;
+    return cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0 ? n : 152;
+  }
+  if (cached[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 152;
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
 int cuda_fail(cudaError_t e, const char* what) {
   g_err = std::string(what) + ": " + cudaGetErrorString(e);
   return MM_ECUDA;
@@ -150,6 +166,7 @@ void free_plan(Plan* P) {
   dfree(P->tw32); dfree(P->tw64); dfree(P->tiles); dfree(P->segs); dfree(P->map32_in); dfree(P->map32_out);
   dfree(P->map64_in); dfree(P->map64_out); dfree(P->td_a); dfree(P->td_b); dfree(P->t32);
   dfree(P->wdf); dfree(P->tabdf); dfree(P->twdf); dfree(P->tdf); dfree(P->mapdf);
+  dfree(P->ang2); dfree(P->groups); dfree(P->slot); dfree(P->slot_pix); dfree(P->u32);
   free_cg(reinterpret_cast<CgState*>(P->cg));
   free_blk(reinterpret_cast<BlkState*>(P->blk));
   free_defl(reinterpret_cast<DeflState*>(P->defl));
@@ -317,6 +334,110 @@ struct Scratch {
   }
 };
 
+// Pixel windows of time-aligned detector groups for the FP32 operators (P and P^T of the FP32
+// A-application; Sect. 3.1 local pixel indexation applied per group of samples).  The detectors of
+// every stationary interval are taken in groups of up to kWinDets, over windows of W = 2^k samples
+// of relative time (about kWinSamples samples per group, W >= 32).  A group whose kept samples see
+// more than kWinCap distinct pixels is split, its window halved down to 32 samples and then its
+// detectors halved, until every group fits; then each group's pixel-sorted slot table and every
+// sample's slot are written.
+int build_windows(Plan* P, cudaStream_t s) {
+  constexpr int kWinDets = 512;
+  constexpr int64_t kWinSamples = 32768;
+  constexpr int kMinLogW = 5;
+  const std::vector<int64_t>& off = P->block_off;
+  for (int b = 0; b < P->n_blocks; b++)
+    if (off[b + 1] - off[b] > ((int64_t)1 << 30)) return MM_OK;   // blocks that long keep the fused tiles
+  std::vector<PGroup> pending, done;
+  for (int i = 0; i < P->n_int; i++) {
+    for (int d0 = 0; d0 < P->n_det; d0 += kWinDets) {
+      const int nd = std::min(kWinDets, P->n_det - d0);
+      int64_t maxlen = 0;
+      for (int d = d0; d < d0 + nd; d++) {
+        const int b = d * P->n_int + i;
+        maxlen = std::max(maxlen, off[b + 1] - off[b]);
+      }
+      int log_w = kMinLogW;
+      while (log_w < 30 && ((int64_t)nd << (log_w + 1)) <= kWinSamples) log_w++;
+      for (int64_t w0 = 0; w0 < maxlen; w0 += (int64_t)1 << log_w) {
+        PGroup g{};
+        g.b0 = d0 * P->n_int + i;
+        g.n_blk = nd;
+        g.b_stride = P->n_int;
+        g.log_w = log_w;
+        g.w0 = w0;
+        pending.push_back(g);
+      }
+    }
+  }
+  Scratch scr;
+  for (int round = 0; !pending.empty(); round++) {
+    if (round > 64) return fail(MM_EINVAL, "pixel windows: splitting did not converge");
+    PGroup* gd = nullptr;
+    int32_t* cnt = nullptr;
+    MM_TRY(scr.alloc(&gd, pending.size()));
+    MM_TRY(scr.alloc(&cnt, pending.size()));
+    MM_CUDA(cudaMemcpyAsync(gd, pending.data(), pending.size() * sizeof(PGroup), cudaMemcpyHostToDevice, s));
+    MM_CUDA(launch_win_build(gd, (int64_t)pending.size(), P->block_off_dev, P->lpix, cnt, nullptr, nullptr, s));
+    std::vector<int32_t> hc(pending.size());
+    MM_CUDA(cudaMemcpyAsync(hc.data(), cnt, hc.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    MM_CUDA(cudaStreamSynchronize(s));
+    std::vector<PGroup> next;
+    for (size_t k = 0; k < pending.size(); k++) {
+      PGroup g = pending[k];
+      if (hc[k] >= 0) {
+        g.n_slots = hc[k];
+        done.push_back(g);
+      } else if (g.log_w > kMinLogW) {
+        g.log_w--;
+        PGroup h = g;
+        h.w0 += (int64_t)1 << g.log_w;
+        next.push_back(g);
+        next.push_back(h);
+      } else if (g.n_blk > 1) {
+        const int half = g.n_blk / 2;
+        PGroup h = g;
+        g.n_blk = half;
+        h.b0 += half * g.b_stride;
+        h.n_blk -= half;
+        next.push_back(g);
+        next.push_back(h);
+      } else {
+        return fail(MM_EINVAL, "pixel windows: a single detector chunk exceeds the window capacity");
+      }
+    }
+    pending.swap(next);
+  }
+  // process groups interval by interval, in time order, detectors ascending
+  std::sort(done.begin(), done.end(), [&](const PGroup& a, const PGroup& b) {
+    const int ia = a.b0 % P->n_int, ib = b.b0 % P->n_int;
+    if (ia != ib) return ia < ib;
+    if (a.w0 != b.w0) return a.w0 < b.w0;
+    return a.b0 < b.b0;
+  });
+  int64_t total = 0;
+  for (PGroup& g : done) {
+    g.slot_off = total;
+    total += g.n_slots;
+  }
+  P->n_groups = (int64_t)done.size();
+  P->n_slots_total = total;
+  P->win_repeat = total > 0 ? (double)P->N / (double)total : 0.0;
+  MM_TRY(dalloc(P, &P->groups, done.size()));
+  MM_TRY(dalloc(P, &P->slot, P->N));
+  MM_TRY(dalloc(P, &P->slot_pix, (size_t)std::max<int64_t>(total, 1)));
+  int32_t* err = nullptr;
+  MM_TRY(scr.alloc(&err, 1));
+  MM_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
+  MM_CUDA(cudaMemcpyAsync(P->groups, done.data(), done.size() * sizeof(PGroup), cudaMemcpyHostToDevice, s));
+  MM_CUDA(launch_win_build(P->groups, P->n_groups, P->block_off_dev, P->lpix, err, P->slot, P->slot_pix, s));
+  int32_t herr = 0;
+  MM_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  MM_CUDA(cudaStreamSynchronize(s));
+  if (herr != 0) return fail(MM_ECUDA, "pixel windows: slot tables do not match the counts");
+  return MM_OK;
+}
+
 int build_plan(const mm_problem_desc* d, cudaStream_t us, Plan* P) {
   MM_CUDA(cudaGetDevice(&P->device));
   MM_TRY(tile_kernels_init());
@@ -406,7 +527,9 @@ int build_plan(const mm_problem_desc* d, cudaStream_t us, Plan* P) {
   MM_TRY(dalloc(P, &P->w64, P->N));
   MM_TRY(dalloc(P, &P->w32, P->N));
   if (P->df64) MM_TRY(dalloc(P, &P->wdf, P->N));
-  MM_CUDA(launch_weights(P->psi, P->N, P->w64, P->w32, P->df64 ? P->wdf : nullptr, s));
+  const bool windows = P->precision == MM_FP32 && P->algo == MM_TPLZ_FFT;
+  if (windows) MM_TRY(dalloc(P, &P->ang2, P->N));
+  MM_CUDA(launch_weights(P->psi, P->N, P->w64, P->w32, P->df64 ? P->wdf : nullptr, P->ang2, s));
   MM_CUDA(launch_bd_accum(pix, P->w64, P->block_off_dev, P->c0_blk, nb, P->N, B6, hits, s));
   MM_CUDA(launch_bd_finalize(B6, hits, P->n_pix, P->cond_max, keep, inv6, s));
   MM_CUDA(launch_scan_keep(keep, P->n_pix, lid, flag + 1, scan_scratch, (int64_t)sl, s));
@@ -419,6 +542,7 @@ int build_plan(const mm_problem_desc* d, cudaStream_t us, Plan* P) {
   MM_TRY(dalloc(P, &P->lpix, P->N));
   MM_CUDA(launch_compact(keep, lid, inv6, P->n_pix, P->obs_to_global, P->minv, s));
   MM_CUDA(launch_localize(pix, keep, lid, P->N, P->lpix, s));
+  if (windows) MM_TRY(build_windows(P, s));
 
   // Toeplitz spectra: L-point circulant spectrum of each distinct band, then the pair tables
   BandTables bt = dedupe_bands(band, nb, lam);
@@ -632,20 +756,37 @@ int apply64_internal(Plan* P, const double* x4, double* y4, int nrhs, cudaStream
 // plan-owned un-pointed buffer of the split FP32 A-application (allocated outside graph capture)
 int64_t t32_stride(const Plan* P) { return (P->N + 3) / 4 * 4; }
 
+// The split FP32 A-application keeps t = P x (and, with pixel windows, u = N^-1 t) for nrhs
+// columns; beyond kSplitTBytes the fused tiles run instead.
+bool split32_fits(const Plan* P, int nrhs) {
+  return (size_t)nrhs * (size_t)t32_stride(P) * sizeof(float) * (P->groups ? 2 : 1) <= kSplitTBytes;
+}
+
 int ensure_t32(Plan* P, int nrhs) {
+  if (!split32_fits(P, nrhs)) return MM_OK;
   const size_t t_elems = (size_t)nrhs * (size_t)t32_stride(P);
-  if (t_elems * sizeof(float) > kSplitTBytes || P->t32_cap >= t_elems) return MM_OK;
-  dfree(P->t32);
-  P->t32_cap = 0;
-  P->buf_gen++;
-  MM_TRY(dalloc(P, &P->t32, t_elems));
-  P->t32_cap = t_elems;
+  if (P->t32_cap < t_elems) {
+    dfree(P->t32);
+    P->t32_cap = 0;
+    P->buf_gen++;
+    MM_TRY(dalloc(P, &P->t32, t_elems));
+    P->t32_cap = t_elems;
+  }
+  if (P->groups && P->u32_cap < t_elems) {
+    dfree(P->u32);
+    P->u32_cap = 0;
+    P->buf_gen++;
+    MM_TRY(dalloc(P, &P->u32, t_elems));
+    P->u32_cap = t_elems;
+  }
   return MM_OK;
 }
 
-// y32 (accumulated, pre-zeroed) += A x32 in FP32, [nrhs][n_obs][4] float
+// y32 (accumulated, pre-zeroed) += A x32 in FP32, [nrhs][n_obs][4] float.  Profiling events: mid
+// after P (t = P x), mid2 after N^-1 (pixel windows only).
 int apply32_internal(Plan* P, const float* x32, float* y32, int nrhs, cudaStream_t s,
-                     const int32_t* done = nullptr, int done_stride = 0, cudaEvent_t mid = nullptr) {
+                     const int32_t* done = nullptr, int done_stride = 0, cudaEvent_t mid = nullptr,
+                     cudaEvent_t mid2 = nullptr) {
   TileArgs a = base_args(P, true);
   a.tiles = P->segs;
   a.n_tiles = P->n_segs;
@@ -660,24 +801,40 @@ int apply32_internal(Plan* P, const float* x32, float* y32, int nrhs, cudaStream
     MM_CUDA(launch_tmpl_mx32(ts->M32, P->n_obs, x32, y32, nrhs, done, done_stride, s));
     MM_CUDA(launch_tmpl_apply32(ts->dev, P->n_blocks, P->w32, x32, P->n_obs * 4, y32, P->n_obs * 4, nrhs, done,
                                 done_stride, s));
+    if (mid2) MM_CUDA(cudaEventRecord(mid2, s));
     return MM_OK;
   }
-  // Un-point first at full occupancy (t = P x into a plan-owned FP32 buffer), then the tiles
-  // stream t instead of gathering the map themselves; fused gather when the buffer would be large.
-  const size_t t_elems = (size_t)nrhs * (size_t)t32_stride(P);
-  if (t_elems * sizeof(float) <= kSplitTBytes) {
+  if (split32_fits(P, nrhs)) {
     MM_TRY(ensure_t32(P, nrhs));
-    MM_CUDA(launch_unpoint32(P->lpix, P->w32, P->N, x32, P->n_obs * 4, nrhs, done, done_stride, P->t32,
-                             t32_stride(P), s));
+    const int64_t ts = t32_stride(P);
+    if (P->groups) {
+      // P over the pixel windows, y = N^-1 t on the segments, P^T over the windows
+      MM_CUDA(launch_unpoint_win32(P->groups, P->n_groups, P->block_off_dev, P->slot, P->slot_pix, P->ang2, x32,
+                                   P->n_obs * 4, nrhs, done, done_stride, P->t32, ts, s));
+      if (mid) MM_CUDA(cudaEventRecord(mid, s));
+      a.x = P->t32;
+      a.x_stride = ts;
+      a.y = P->u32;
+      a.y_stride = ts;
+      MM_CUDA(launch_tiles_fp32(MODE_NINV_T, a, P->seg_halo, s));
+      if (mid2) MM_CUDA(cudaEventRecord(mid2, s));
+      MM_CUDA(launch_point_win32(P->groups, P->n_groups, P->block_off_dev, P->slot, P->slot_pix, P->ang2, P->u32,
+                                 ts, nrhs, done, done_stride, y32, P->n_obs * 4, s));
+      return MM_OK;
+    }
+    // un-point first at full occupancy, then the tiles stream t and scatter P^T themselves
+    MM_CUDA(launch_unpoint32(P->lpix, P->w32, P->N, x32, P->n_obs * 4, nrhs, done, done_stride, P->t32, ts, s));
     if (mid) MM_CUDA(cudaEventRecord(mid, s));
     a.x = P->t32;
-    a.x_stride = t32_stride(P);
+    a.x_stride = ts;
     MM_CUDA(launch_tiles_fp32(MODE_APPLY_T, a, P->seg_halo, s));
+    if (mid2) MM_CUDA(cudaEventRecord(mid2, s));
   } else {
     if (mid) MM_CUDA(cudaEventRecord(mid, s));
     a.x = x32;
     a.x_stride = P->n_obs * 4;
     MM_CUDA(launch_tiles_fp32(MODE_APPLY, a, P->seg_halo, s));
+    if (mid2) MM_CUDA(cudaEventRecord(mid2, s));
   }
   return MM_OK;
 }
@@ -1334,9 +1491,9 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
   const bool profile = opts->profile != 0;
   int64_t n_kernels = 2;   // pack + init
   // profile mode: event pairs around every tile launch, summed at each host sync
-  struct EvPair { cudaEvent_t a, b, m; int is64; };
+  struct EvPair { cudaEvent_t a, b, m, m2; int is64; };
   std::vector<EvPair> pool, pending;
-  double t32 = 0.0, t64 = 0.0, tup = 0.0;
+  double t32 = 0.0, t64 = 0.0, tup = 0.0, tpt = 0.0;
   int n32 = 0, n64 = 0;
   auto take_pair = [&](int is64, EvPair* out) -> int {
     if (pool.empty()) {
@@ -1344,6 +1501,7 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
       MM_CUDA(cudaEventCreate(&e.a));
       MM_CUDA(cudaEventCreate(&e.b));
       MM_CUDA(cudaEventCreate(&e.m));
+      MM_CUDA(cudaEventCreate(&e.m2));
       pool.push_back(e);
     }
     *out = pool.back();
@@ -1358,9 +1516,11 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
       if (e.is64) { t64 += ms; n64++; } else {
         t32 += ms;
         n32++;
-        float mu = 0.f;
+        float mu = 0.f, mp = 0.f;
         MM_CUDA(cudaEventElapsedTime(&mu, e.a, e.m));
+        MM_CUDA(cudaEventElapsedTime(&mp, e.m2, e.b));
         tup += mu;
+        tpt += mp;
       }
       pool.push_back(e);
     }
@@ -1426,7 +1586,7 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
         MM_TRY(take_pair(fp32 ? 0 : 1, &e));
         MM_CUDA(cudaEventRecord(e.a, s));
         if (fp32) {
-          MM_TRY(apply32_internal(P, w.p32, w.q32, nrhs, s, halt, kScalStrideInts, e.m));
+          MM_TRY(apply32_internal(P, w.p32, w.q32, nrhs, s, halt, kScalStrideInts, e.m, e.m2));
         } else {
           MM_TRY(apply64_internal(P, w.p, w.q, nrhs, s, halt, kScalStrideInts));
         }
@@ -1463,6 +1623,7 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
     cudaEventDestroy(e.m);
+    cudaEventDestroy(e.m2);
   }
   MM_CUDA(cudaEventRecord(ev, s));
   MM_CUDA(cudaStreamWaitEvent(us, ev, 0));
@@ -1482,6 +1643,7 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
     in.t_queue_ms = 0.0;
     in.t_apply32_ms = t32;
     in.t_unpoint32_ms = tup;
+    in.t_point32_ms = tpt;
     in.t_apply64_ms = t64;
     in.n_apply32 = n32;
     in.n_apply64 = n64;

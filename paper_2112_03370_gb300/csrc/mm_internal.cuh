@@ -55,7 +55,32 @@ struct ProbPtrs {
 
 // MODE_APPLY_T: A-application whose un-pointed input t = P x was written beforehand (FP32
 // tiles: float t; df64 tiles: (hi, lo) float pairs, also used for the masked TOD of the RHS)
-enum Mode { MODE_APPLY = 0, MODE_RHS = 1, MODE_NINV = 2, MODE_APPLY_T = 3 };
+// MODE_NINV_T: FP32 y = N^-1 t on the segments, float t in and float y out (the pointing is
+// applied by the window kernels around it)
+enum Mode { MODE_APPLY = 0, MODE_RHS = 1, MODE_NINV = 2, MODE_APPLY_T = 3, MODE_NINV_T = 4 };
+
+// ---------------------------------------------------------------------------------------------
+// Pixel windows of time-aligned detector groups (P and P^T of the FP32 A-application).
+// A group is the same window [w0, w0 + W) of relative time in n_blk blocks b0, b0 + b_stride, ...
+// (the detectors of one stationary interval).  Its kept samples see n_slots distinct pixels; slot
+// k of the group is the k-th smallest of them (slot_pix[slot_off + k]), and every sample stores
+// the slot of its pixel (uint16, kNoSlot at masked samples): a pixel-sorted local index, so the
+// un-point kernel reads the group's map entries once into shared memory and the point kernel
+// sums the group's samples per pixel in shared memory before one global update per pixel.
+// ---------------------------------------------------------------------------------------------
+constexpr int kWinCap = 4096;              // most distinct pixels of a group (shared-memory window)
+constexpr int kWinThreads = 512;
+constexpr uint16_t kNoSlot = 0xFFFF;
+struct PGroup {
+  int32_t b0;        // first block of the group
+  int32_t n_blk;     // blocks in the group
+  int32_t b_stride;  // block index step (n_int: the same interval of consecutive detectors)
+  int32_t log_w;     // window length W = 2^log_w
+  int32_t n_slots;   // distinct kept pixels (0 .. kWinCap)
+  int32_t pad;
+  int64_t w0;        // window start, samples from each block's start
+  int64_t slot_off;  // first entry of the group's pixel-sorted slot table
+};
 
 // Arguments of the fused Toeplitz-tile kernels.
 struct TileArgs {
@@ -97,6 +122,7 @@ struct Plan {
   double2* w64 = nullptr;              // [N] cos 2psi, sin 2psi in FP64 (FP64 operators)
   bool df64 = false;                   // FP64-class operators run in df64 arithmetic
   float4* wdf = nullptr;               // [N] df64 weights (df64 plans)
+  float* ang2 = nullptr;               // [N] 2 psi reduced to [-pi, pi] (FP32 window kernels)
   int32_t* obs_to_global = nullptr;    // [n_obs]
   double* minv = nullptr;              // [n_obs][6] symmetric inverse BD blocks (00 01 02 11 12 22)
   double* band = nullptr;              // [n_blocks][lambda + 1]
@@ -124,6 +150,16 @@ struct Plan {
                                        // rounded up to 4)
   size_t t32_cap = 0;
   int32_t seg_halo = 0;                // largest L - vstep over the segments (samples)
+
+  // pixel windows of detector groups (FP32 operators)
+  PGroup* groups = nullptr;            // [n_groups]
+  int64_t n_groups = 0;
+  uint16_t* slot = nullptr;            // [N] pixel-sorted local index of each sample in its group
+  int32_t* slot_pix = nullptr;         // [n_slots_total] compacted pixel of each slot
+  int64_t n_slots_total = 0;
+  float* u32 = nullptr;                // [nrhs][N4] FP32 u = N^-1 t of the windowed A-application
+  size_t u32_cap = 0;
+  double win_repeat = 0.0;             // kept samples per (group, pixel) pair: the P^T reduction factor
 
   // work buffers (grown on demand)
   float* map32_in = nullptr;  size_t map32_in_cap = 0;
@@ -185,8 +221,10 @@ cudaError_t launch_compact(const int32_t* keep, const int32_t* lid, const double
                            int64_t n_pix, int32_t* obs_to_global, double* minv, cudaStream_t s);
 cudaError_t launch_localize(const int32_t* pix, const int32_t* keep, const int32_t* lid,
                             int64_t N, int32_t* lpix, cudaStream_t s);
-// (cos 2psi, sin 2psi) in FP64, their FP32 roundings and (wdf non-null) their df64 split, one sincos per sample
-cudaError_t launch_weights(const float* psi, int64_t N, double2* w64, float2* w32, float4* wdf, cudaStream_t s);
+// (cos 2psi, sin 2psi) in FP64, their FP32 roundings, (wdf non-null) their df64 split and (ang2
+// non-null) 2 psi reduced to [-pi, pi], one sincos per sample
+cudaError_t launch_weights(const float* psi, int64_t N, double2* w64, float2* w32, float4* wdf, float* ang2,
+                           cudaStream_t s);
 cudaError_t launch_validate(const int32_t* pix, const float* psi, int64_t N, int64_t n_pix,
                             int32_t* bad, cudaStream_t s);
 cudaError_t launch_spectra(const double* band_rows, int32_t n_tab, int32_t lambda,
@@ -206,6 +244,25 @@ cudaError_t launch_unpoint32(const int32_t* lpix, const float2* w32, int64_t N, 
                              int64_t x_stride, int nrhs, const int32_t* done, int done_stride, float* t,
                              int64_t t_stride, cudaStream_t s);
 cudaError_t launch_tiles_fp64(int mode, const TileArgs& a, cudaStream_t s);
+
+// pixel windows (k_window.cu)
+// count (slot_tab == nullptr: n_slots of every group, -1 when over kWinCap) or fill (slots and
+// tables of groups whose n_slots and slot_off are set)
+cudaError_t launch_win_build(const PGroup* groups, int64_t n_groups, const int64_t* block_off,
+                             const int32_t* lpix, int32_t* n_slots_out, uint16_t* slot, int32_t* slot_pix,
+                             cudaStream_t s);
+// t [nrhs][t_stride] = P x (FP32, weights from psi in registers) over the windows
+cudaError_t launch_unpoint_win32(const PGroup* groups, int64_t n_groups, const int64_t* block_off,
+                                 const uint16_t* slot, const int32_t* slot_pix, const float* psi,
+                                 const float* x4, int64_t x_stride, int nrhs, const int32_t* done,
+                                 int done_stride, float* t, int64_t t_stride, cudaStream_t s);
+// y4 [nrhs][y_stride] += P^T u (FP32) over the windows, u [nrhs][u_stride]
+cudaError_t launch_point_win32(const PGroup* groups, int64_t n_groups, const int64_t* block_off,
+                               const uint16_t* slot, const int32_t* slot_pix, const float* psi,
+                               const float* u, int64_t u_stride, int nrhs, const int32_t* done,
+                               int done_stride, float* y4, int64_t y_stride, cudaStream_t s);
+// multiprocessors of the current device (cached per device)
+int sm_count();
 // df64 tiles and their data preparation (k_df64.cu)
 cudaError_t launch_tiles_df(const TileArgs& a, cudaStream_t s);
 cudaError_t launch_weights_df(const float* psi, int64_t N, float4* wdf, cudaStream_t s);

@@ -76,7 +76,8 @@ __global__ void k_na_unpack(const void* __restrict__ y4, int64_t tot, int fp32, 
 unsigned grid_of(int64_t n) {
   int64_t g = (n + 255) / 256;
   if (g < 1) g = 1;
-  if (g > 4 * 152 * 8) g = 4 * 152 * 8;
+  const int64_t cap = 32 * (int64_t)sm_count();
+  if (g > cap) g = cap;
   return (unsigned)g;
 }
 
@@ -94,6 +95,12 @@ extern "C" int mm_apply_A_noalloc(mm_plan_t plan, const double* x, double* y, in
   if (P->tmpl)
     return fail(MM_EINVAL, "mm_apply_A_noalloc does not apply template filters (they need a "
                            "time-domain buffer of N samples)");
+  // MM_DF64 plans: mm_apply_A runs the double-float tiles, which read an N-sample un-pointed
+  // buffer; this entry point has no room for it and does not substitute other arithmetic
+  if (P->df64 && P->precision != MM_FP32)
+    return fail(MM_EINVAL, "mm_apply_A_noalloc does not run MM_DF64 plans (their double-float "
+                           "operator needs a time-domain buffer of N samples); use an MM_FP64, "
+                           "MM_FP32 or MM_FP32_DF64 plan");
   const bool fp32 = P->precision == MM_FP32;
   const size_t elem = fp32 ? sizeof(float) : sizeof(double);
   const size_t tot = (size_t)nrhs * (size_t)P->n_obs;

@@ -61,7 +61,7 @@ class SolveInfo(ctypes.Structure):
                 ("t_apply32_ms", ctypes.c_double), ("t_apply64_ms", ctypes.c_double),
                 ("n_apply32", ctypes.c_int32), ("n_apply64", ctypes.c_int32),
                 ("n_kernels", ctypes.c_int64), ("t_queue_ms", ctypes.c_double),
-                ("t_unpoint32_ms", ctypes.c_double)]
+                ("t_unpoint32_ms", ctypes.c_double), ("t_point32_ms", ctypes.c_double)]
 
 
 class MMError(RuntimeError):

@@ -18,7 +18,7 @@ from gpu_helpers import cuda, mm, plans, rel_max
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 2e-5)])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 2e-5), (3, 2e-5)])
 @pytest.mark.parametrize("nrhs", [1, 3])
 def test_noalloc_matches_apply_A_twice(precision, tol, nrhs):
     prob = synth.random_problem(4, [70001, 5, 33000, 40000], 300, 1024, seed=21, gap_frac=0.02,
@@ -47,3 +47,16 @@ def test_noalloc_rejects_oversized_working_set():
     with pytest.raises(m.MMError) as e:
         m.mm_apply_A_noalloc(gp, x, y)
     assert e.value.code == m.MM_EINVAL and "working space" in str(e.value)
+
+
+def test_noalloc_refuses_df64_plans():
+    """An MM_DF64 plan's operator is double-float arithmetic over an N-sample buffer, which the
+    fixed array cannot hold: the call is refused rather than run in other arithmetic."""
+    m = mm()
+    prob = synth.random_problem(2, [20000, 20000], 300, 64, seed=23, hits_per_pix_min=4)
+    gp, op, _ = plans(prob, precision=m.MM_DF64)
+    x = torch.zeros(1, op.n_obs, 3, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    with pytest.raises(m.MMError) as e:
+        m.mm_apply_A_noalloc(gp, x, y)
+    assert e.value.code == m.MM_EINVAL and "MM_DF64" in str(e.value)
