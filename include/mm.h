@@ -174,8 +174,12 @@ int mm_apply_Pt(mm_plan_t plan, const double* t, double* y, void* stream);
  * no wrap-around and no coupling across blocks. */
 int mm_apply_Ninv(mm_plan_t plan, const double* t, double* y, void* stream);
 
-/* b = P~^T N^-1 G d for nrhs data vectors: d [nrhs][N] device, float64 (d_is_fp32 = 0) or
- * float32 (d_is_fp32 = 1); b [nrhs][n_obs][3].  G zeroes flagged and excised samples of d. */
+/* b = P~^T N^-1 G d for nrhs data vectors: d [nrhs][N], float64 (d_is_fp32 = 0) or float32
+ * (d_is_fp32 = 1), in device memory or in host memory (pinned or pageable); b [nrhs][n_obs][3]
+ * device.  G zeroes flagged and excised samples of d.  A host d is copied by the library (on
+ * double-float plans through two 64 MiB staging buffers of the plan, each chunk's copy overlapping
+ * the previous chunk's conversion); the call then returns only after its work on the stream has
+ * finished, so the host buffer may be reused at once.  With a device d the call is asynchronous. */
 int mm_rhs(mm_plan_t plan, const void* d, int d_is_fp32, int nrhs, double* b, void* stream);
 
 /* y = A x = P~^T N^-1 P~ x (Sect. 3.2, right to left) for nrhs vectors, in the plan's precision. */
@@ -353,19 +357,24 @@ int mm_deflation_apply(mm_plan_t plan, const double* r, double* z, int nrhs, voi
  * queue and are admitted while fewer than max_slots run and the estimated device footprint of the
  * running ones stays within hbm_budget; an admitted request's plan (pointing, bands, spectra,
  * block-Jacobi blocks) and PCG state stay resident until it finishes.  Every step runs one PCG
- * iteration of every running request with a single Toeplitz-tile launch over all of their tiles
- * (FP32 operators; right-hand side and residual replacement per request with the double-float
- * FP64-class operators, as in mm_pcg_solve on an MM_FP32_DF64 plan; the request's desc->precision
- * is ignored); requests join and leave between steps.
+ * iteration of every running request; requests join and leave between steps.
+ *   FP32 requests (opts->precision MM_FP32): FP32 operators, all such requests' Toeplitz tiles in a
+ *     single launch per step; right-hand side and residual replacement per request with the
+ *     double-float FP64-class operators, as mm_pcg_solve on an MM_FP32_DF64 plan (the request's
+ *     desc->precision is ignored).
+ *   FP64-class requests (opts->precision MM_FP64): plain PCG with the plan's FP64-class operator in
+ *     every iteration, in the arithmetic desc->precision selects (IEEE FP64 for MM_FP64 / MM_FP32,
+ *     double-float for MM_DF64 / MM_FP32_DF64), one operator launch per request per step.
  */
 /* Create a server (hbm_budget in bytes, 0 = 80% of the free device memory; max_slots >= 1). */
 int mm_server_create(size_t hbm_budget, int max_slots, mm_server_t* out);
 /* Queue a map-making solve.  desc and d are HOST memory (desc->inputs_on_device must be 0) and are
- * copied before the call returns; d is the float64 TOD [N].  opts->precision must be MM_FP32.
- * Non-blocking; *id identifies the request.  MM_EINVAL on bad input (validated again at admission:
- * a request that fails there finishes with that status). */
-int mm_submit(mm_server_t server, const mm_problem_desc* desc, const double* d, const mm_solve_opts* opts,
-              mm_req_t* id);
+ * copied before the call returns; d is the TOD [N], float64 (d_is_fp32 = 0) or float32
+ * (d_is_fp32 = 1).  opts->precision is MM_FP32 or MM_FP64 (above); opts->precond must be MM_PREC_BD;
+ * MM_TPLZ_DIRECT plans are refused.  Non-blocking; *id identifies the request.  MM_EINVAL on bad
+ * input (validated again at admission: a request that fails there finishes with that status). */
+int mm_submit(mm_server_t server, const mm_problem_desc* desc, const void* d, int d_is_fp32,
+              const mm_solve_opts* opts, mm_req_t* id);
 /* MM_EBUSY while the request is queued or running; MM_OK (info filled) once it has finished. */
 int mm_poll(mm_server_t server, mm_req_t id, mm_solve_info* info);
 /* Wait up to timeout_us (< 0: forever) for the request, then copy its map into map_host

@@ -311,6 +311,21 @@ struct SmemFFT {
     pass_rem<true>(sm, tw);
   }
 
+  // The radix-16 passes alone: the caller runs the stride-1 radix-2^REM passes (the last of the
+  // forward transform, the first of the inverse) itself, fused with the pointwise step.
+  template <typename C>
+  __device__ static void forward16(C* sm, const TwiddleTab<C>& tw, const C* ptab) {
+    pass16<0, true>(sm, tw, ptab);
+    pass16<1, true>(sm, tw, ptab);
+    pass16<2, true>(sm, tw, ptab);
+  }
+  template <typename C>
+  __device__ static void inverse16(C* sm, const TwiddleTab<C>& tw, const C* ptab) {
+    pass16<2, false>(sm, tw, ptab);
+    pass16<1, false>(sm, tw, ptab);
+    pass16<0, false>(sm, tw, ptab);
+  }
+
   template <typename C>
   __device__ static void inverse(C* sm, const TwiddleTab<C>& tw, const C* ptab) {
     pass_rem<false>(sm, tw);

@@ -301,7 +301,7 @@ __device__ __forceinline__ void gather_pairs(const TileArgs& a, int rhs, const T
 #pragma unroll
     for (int u = 0; u < NB; u++) {
       if (g[u] >= td.blk_lo && g[u] + 2 <= td.blk_hi) {   // g even and the column 8-byte aligned
-        const float2 f = __ldg(reinterpret_cast<const float2*>(t + g[u]));
+        const float2 f = __ldcs(reinterpret_cast<const float2*>(t + g[u]));
         v[u][0] = f.x;
         v[u][1] = f.y;
       } else {
@@ -369,6 +369,75 @@ __device__ __forceinline__ void scatter_pairs(const TileArgs& a, int rhs, const 
     } else {
       if (p[u][0] >= 0) Map4<T>::add(a.y, rhs * a.y_stride, p[u][0], y0, c0 * y0, s0 * y0);
       if (p[u][1] >= 0) Map4<T>::add(a.y, rhs * a.y_stride, p[u][1], y1, c1 * y1, s1 * y1);
+    }
+  }
+}
+
+// ---- fused stride-1 passes and pair update (FP32 tiles) ----------------------------------------
+// After the three radix-16 passes of the forward transform (M = 2^14), position j of the
+// digit-reversed layout holds the partial transform of frequency k with j = [d0|d1|d2|r]
+// (k = d0 + 16 d1 + 256 d2 + 4096 r); the last forward pass is a radix-4 butterfly over the 4
+// consecutive positions 4q..4q+3 (q = [d0|d1|d2]), and the first inverse pass the same.  The
+// partner M - k of every frequency of quad q lies in a single quad q' (the first nonzero digit d
+// of (d0, d1, d2) becomes 16 - d, the later digits 15 - d, element e pairs with element 3 - e;
+// quad 0 pairs with itself with e <-> (4 - e) & 3, quad 8 with itself with e <-> 3 - e).  One
+// thread therefore loads both quads, runs the last forward radix-4 on each, applies
+// Z'[k] = a_k Z[k] + i b_k conj(Z[M - k]) and the first inverse radix-4, and stores them back:
+// one shared-memory round trip instead of three.
+__device__ __forceinline__ int partner_quad(int q) {
+  const int a = q >> 8, b = (q >> 4) & 15, c = q & 15;
+  if (a != 0) return ((16 - a) << 8) | ((15 - b) << 4) | (15 - c);
+  if (b != 0) return ((16 - b) << 4) | (15 - c);
+  if (c != 0) return 16 - c;
+  return 0;
+}
+
+template <typename C, typename T>
+__device__ __forceinline__ C pair_upd(C ab, C z, C zp, T sc) {
+  // s (a Z + i b conj(Zp)) = s (a x + b yp, a y + b xp)
+  return C{sc * (ab.x * z.x + ab.y * zp.y), sc * (ab.x * z.y + ab.y * zp.x)};
+}
+
+template <typename C, typename T>
+__device__ __forceinline__ void fused_rem_pair(C* sm, const C* __restrict__ tab, T sc) {
+  static_assert(kLogM == 14, "the quad pairing assumes 3 radix-16 passes and a radix-4 pass");
+  constexpr int NQ = kM / 4;
+  for (int q = threadIdx.x; q < NQ; q += kTileThreads) {
+    const int p = partner_quad(q);
+    if (p < q) continue;
+    C za[4], zb[4], ta[4], tb[4];
+    C* qa = sm + smem_pad(4 * q);   // 4 consecutive positions never cross a padding group
+    C* qb = sm + smem_pad(4 * p);
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      za[e] = qa[e];
+      zb[e] = qb[e];
+      ta[e] = ldg_c(tab + 4 * q + e);
+      tb[e] = ldg_c(tab + 4 * p + e);
+    }
+    dft_small<4, true>(za);
+    dft_small<4, true>(zb);
+    if (p == q) {
+      C o[4];
+#pragma unroll
+      for (int e = 0; e < 4; e++) o[e] = pair_upd(ta[e], za[e], za[q == 0 ? ((4 - e) & 3) : 3 - e], sc);
+      dft_small<4, false>(o);
+#pragma unroll
+      for (int e = 0; e < 4; e++) qa[e] = o[e];
+    } else {
+      C oa[4], ob[4];
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        oa[e] = pair_upd(ta[e], za[e], zb[3 - e], sc);
+        ob[3 - e] = pair_upd(tb[3 - e], zb[3 - e], za[e], sc);
+      }
+      dft_small<4, false>(oa);
+      dft_small<4, false>(ob);
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        qa[e] = oa[e];
+        qb[e] = ob[e];
+      }
     }
   }
 }
@@ -484,6 +553,12 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
       __syncthreads();
     }
 
+    if constexpr (CL == 1) {
+      FFT::forward16(sm, tw, ptab);
+      fused_rem_pair(sm, tab, sc);
+      __syncthreads();
+      FFT::inverse16(sm, tw, ptab);
+    } else {
     FFT::forward(sm, tw, ptab);
 
     // ---- pair update with the band's precomputed (a_k, b_k) in storage order ----
@@ -549,6 +624,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
     __syncthreads();
 
     FFT::inverse(sm, tw, ptab);
+    }
 
     // ---- scatter of the tile's valid outputs ----
     // output quads covering real offsets [r_lo, r_hi); rank r of a cluster owns complex indices
@@ -573,7 +649,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
         const C z = sm[smem_pad(n)];
         const int64_t g = td.in0 + 2 * (int64_t)n;
         if (g >= td.out_lo && g + 2 <= td.out_hi) {
-          *reinterpret_cast<float2*>(yo + g) = make_float2(z.x, z.y);
+          __stcs(reinterpret_cast<float2*>(yo + g), make_float2(z.x, z.y));
         } else {
           if (g >= td.out_lo && g < td.out_hi) yo[g] = z.x;
           if (g + 1 >= td.out_lo && g + 1 < td.out_hi) yo[g + 1] = z.y;

@@ -71,6 +71,10 @@ __device__ __forceinline__ void weights_of_angle(float x, float& c, float& s) { 
 
 }  // namespace
 
+// Streaming arrays (slot, angle, TOD) are read and written with the evict-first cache policy
+// (__ldcs / __stcs) so that they do not push the map, which the window gathers and the per-pixel
+// atomics reuse, out of L2.
+
 // One CTA per group.  Count mode (slot == nullptr): n_slots_out[g] = distinct kept pixels of the
 // group, or -1 above kWinCap.  Fill mode: the pixel-sorted slot table and every sample's slot.
 __global__ void __launch_bounds__(kWinThreads) k_win_build(const PGroup* __restrict__ groups,
@@ -161,7 +165,7 @@ __global__ void __launch_bounds__(kWinThreads) k_win_build(const PGroup* __restr
 }
 
 constexpr size_t kBuildSmem = (size_t)kHash * 4 + (size_t)kWinCap * 4 + (size_t)kHash * 2;
-constexpr size_t kUnpointSmem = (size_t)kWinCap * sizeof(float4);
+constexpr size_t kUnpointSmem = (size_t)(kWinCap + kWinCap / 8) * sizeof(float4);
 
 #define MM_TRY_CUDA(expr)             \
   do {                                \
@@ -192,53 +196,93 @@ cudaError_t launch_win_build(const PGroup* groups, int64_t n_groups, const int64
   return cudaGetLastError();
 }
 
+// ---- chunk walking shared by the un-point and point kernels ------------------------------------
+// A warp takes CPI = 32 / LPC chunks at a time, LPC = min(32, W / 4) lanes per chunk.  Inside a
+// chunk [lo, lo + len) the lanes walk aligned quads of 4 samples [a0, a1) (a0 = lo rounded up to
+// 4) with vector loads; the at most 3 + 3 samples before a0 and after a1 go one per lane.
+struct ChunkWalk {
+  int lpc, cpi, sub, ql;
+};
+__device__ __forceinline__ ChunkWalk chunk_walk(const PGroup& G, int lane) {
+  ChunkWalk w;
+  w.lpc = G.log_w >= 7 ? 32 : (1 << (G.log_w - 2));
+  w.cpi = 32 / w.lpc;
+  w.sub = lane / w.lpc;
+  w.ql = lane % w.lpc;
+  return w;
+}
+
+// Visit every sample of chunk c: f_quad(base, q4) for aligned quads (samples base + 4 q4 .. + 3),
+// f_one(i) for the single samples of the ragged ends.  Global sample indices are 64-bit.
+template <typename FQ, typename F1>
+__device__ __forceinline__ void visit_chunk(const PGroup& G, const int64_t* __restrict__ block_off, int c,
+                                            const ChunkWalk& w, FQ f_quad, F1 f_one) {
+  int64_t lo;
+  int len;
+  group_chunk(G, block_off, c, lo, len);
+  if (len <= 0) return;
+  const int64_t a0 = (lo + 3) & ~(int64_t)3;
+  const int head = (int)min((int64_t)len, a0 - lo);
+  const int nq = (len - head) >> 2;
+  const int tail = len - head - 4 * nq;
+  const int64_t a1 = a0 + 4 * (int64_t)nq;
+  if (w.ql < head) f_one(lo + w.ql);
+  if (w.ql < tail) f_one(a1 + w.ql);
+  for (int q = w.ql; q < nq; q += w.lpc) f_quad(a0, q);
+}
+
+// Padded shared-memory indices of slot k.  A lane holds 4 consecutive samples, so one warp-wide
+// access touches slots about 4 x (pixels per sample) apart; one padding word per 32 scalar slots
+// (accumulators) or one padding float4 per 8 slots (map window) keeps strides of 1, 2, 4 and 8
+// slots in distinct banks.
+__device__ __forceinline__ int acc_index(int k) { return k + (k >> 5); }
+__device__ __forceinline__ int win_index(int k) { return k + (k >> 3); }
+constexpr int kAccStride = kWinCap + kWinCap / 32;
+constexpr int kWinEntries = kWinCap + kWinCap / 8;
+
 // t = P x over the windows: one CTA per group, the group's map entries of column r in shared
-// memory, then one coalesced pass over the group's samples.  Unroll U keeps U independent
-// (slot, angle) load pairs in flight per lane.
+// memory, then one coalesced pass over the group's samples.
 __global__ void __launch_bounds__(kWinThreads, 3) k_unpoint_win32(
     const PGroup* __restrict__ groups, const int64_t* __restrict__ block_off,
     const uint16_t* __restrict__ slot, const int32_t* __restrict__ slot_pix, const float* __restrict__ ang2,
     const float4* __restrict__ x4, int64_t x_stride4, int nrhs, const int32_t* __restrict__ done,
     int done_stride, float* __restrict__ t, int64_t t_stride) {
-  extern __shared__ float4 win[];   // [kWinCap]
+  extern __shared__ float4 win[];   // [kWinEntries], slot k at win_index(k)
   const PGroup G = groups[blockIdx.x];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int U = 4;
+  const ChunkWalk cw = chunk_walk(G, lane);
   for (int r = 0; r < nrhs; r++) {
     if (done != nullptr && done[(int64_t)r * done_stride] != 0) continue;
     const float4* x = x4 + r * x_stride4;
     float* tr = t + r * t_stride;
     __syncthreads();   // the previous column's window is no longer read
-    for (int k = threadIdx.x; k < G.n_slots; k += kWinThreads) win[k] = __ldg(x + __ldg(slot_pix + G.slot_off + k));
+    for (int k = threadIdx.x; k < G.n_slots; k += kWinThreads)
+      win[win_index(k)] = __ldg(x + __ldg(slot_pix + G.slot_off + k));
     __syncthreads();
-    for (int c = warp; c < G.n_blk; c += kWarps) {
-      int64_t lo;
-      int len;
-      group_chunk(G, block_off, c, lo, len);
-      for (int o0 = lane; o0 < len; o0 += 32 * U) {
-        uint16_t sl[U];
-        float a[U];
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-          const int o = o0 + 32 * u;
-          sl[u] = (o < len) ? __ldg(slot + lo + o) : kNoSlot;
-          a[u] = (o < len) ? __ldg(ang2 + lo + o) : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-          const int o = o0 + 32 * u;
-          if (o < len) {
-            float v = 0.f;
-            if (sl[u] != kNoSlot) {
-              float cs, sn;
-              weights_of_angle(a[u], cs, sn);
-              const float4 m = win[sl[u]];
-              v = m.x + cs * m.y + sn * m.z;
-            }
-            tr[lo + o] = v;
-          }
-        }
-      }
+    auto value = [&](uint32_t sl, float a) -> float {
+      if (sl == kNoSlot) return 0.f;
+      float cs, sn;
+      weights_of_angle(a, cs, sn);
+      const float4 m = win[win_index((int)sl)];
+      return m.x + cs * m.y + sn * m.z;
+    };
+    for (int c0 = warp * cw.cpi; c0 < G.n_blk; c0 += kWarps * cw.cpi) {
+      const int c = c0 + cw.sub;
+      if (c >= G.n_blk) continue;
+      visit_chunk(
+          G, block_off, c, cw,
+          [&](int64_t a0, int q) {
+            const int64_t i = a0 + 4 * (int64_t)q;
+            const uint2 s2 = __ldcs(reinterpret_cast<const uint2*>(slot + i));
+            const float4 a = __ldcs(reinterpret_cast<const float4*>(ang2 + i));
+            float4 v;
+            v.x = value(s2.x & 0xFFFFu, a.x);
+            v.y = value(s2.x >> 16, a.y);
+            v.z = value(s2.y & 0xFFFFu, a.z);
+            v.w = value(s2.y >> 16, a.w);
+            __stcs(reinterpret_cast<float4*>(tr + i), v);
+          },
+          [&](int64_t i) { __stcs(tr + i, value(__ldcs(slot + i), __ldcs(ang2 + i))); });
     }
   }
 }
@@ -248,64 +292,76 @@ cudaError_t launch_unpoint_win32(const PGroup* groups, int64_t n_groups, const i
                                  const float* x4, int64_t x_stride, int nrhs, const int32_t* done,
                                  int done_stride, float* t, int64_t t_stride, cudaStream_t s) {
   if (n_groups == 0 || nrhs <= 0) return cudaSuccess;
-  if (n_groups > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  if (n_groups > 0x7fffffffLL || t_stride % 4 != 0) return cudaErrorInvalidValue;
   static cudaError_t st = cudaSuccess;
   static bool set = false;
   MM_TRY_CUDA(smem_limit_once(k_unpoint_win32, kUnpointSmem, st, set));
   k_unpoint_win32<<<(unsigned)n_groups, kWinThreads, kUnpointSmem, s>>>(groups, block_off, slot, slot_pix, ang2,
-                                                             reinterpret_cast<const float4*>(x4), x_stride / 4, nrhs,
-                                                             done, done_stride, t, t_stride);
+                                                                          reinterpret_cast<const float4*>(x4),
+                                                                          x_stride / 4, nrhs, done, done_stride, t,
+                                                                          t_stride);
   return cudaGetLastError();
 }
 
 // y += P^T u over the windows: one CTA per group and column, samples summed per slot in shared
-// memory (three FP32 shared-memory atomics per sample), then one float4 global atomic per
-// distinct pixel of the group.
+// memory (three FP32 shared-memory adds per sample), then one float4 global atomic per distinct
+// pixel of the group.
+constexpr size_t kPointSmem = (size_t)3 * kAccStride * sizeof(float);
 __global__ void __launch_bounds__(kWinThreads, 3) k_point_win32(
     const PGroup* __restrict__ groups, const int64_t* __restrict__ block_off,
     const uint16_t* __restrict__ slot, const int32_t* __restrict__ slot_pix, const float* __restrict__ ang2,
     const float* __restrict__ u, int64_t u_stride, int nrhs, const int32_t* __restrict__ done, int done_stride,
     float4* __restrict__ y4, int64_t y_stride4) {
-  __shared__ float acc[3][kWinCap];
+  extern __shared__ float acc[];   // [3][kAccStride]
   const PGroup G = groups[blockIdx.x];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int U = 4;
+  const ChunkWalk cw = chunk_walk(G, lane);
+  const int n_pad = acc_index(G.n_slots);
   for (int r = 0; r < nrhs; r++) {
     if (done != nullptr && done[(int64_t)r * done_stride] != 0) continue;
     const float* ur = u + r * u_stride;
-    for (int k = threadIdx.x; k < G.n_slots; k += kWinThreads) acc[0][k] = acc[1][k] = acc[2][k] = 0.f;
+    for (int k = threadIdx.x; k < n_pad; k += kWinThreads) {
+      acc[k] = 0.f;
+      acc[kAccStride + k] = 0.f;
+      acc[2 * kAccStride + k] = 0.f;
+    }
     __syncthreads();
-    for (int c = warp; c < G.n_blk; c += kWarps) {
-      int64_t lo;
-      int len;
-      group_chunk(G, block_off, c, lo, len);
-      for (int o0 = lane; o0 < len; o0 += 32 * U) {
-        uint16_t sl[U];
-        float a[U], yv[U];
-#pragma unroll
-        for (int q = 0; q < U; q++) {
-          const int o = o0 + 32 * q;
-          sl[q] = (o < len) ? __ldg(slot + lo + o) : kNoSlot;
-          a[q] = (o < len) ? __ldg(ang2 + lo + o) : 0.f;
-          yv[q] = (o < len) ? __ldg(ur + lo + o) : 0.f;
-        }
-#pragma unroll
-        for (int q = 0; q < U; q++) {
-          if (sl[q] != kNoSlot) {
-            float cs, sn;
-            weights_of_angle(a[q], cs, sn);
-            atomicAdd(&acc[0][sl[q]], yv[q]);
-            atomicAdd(&acc[1][sl[q]], cs * yv[q]);
-            atomicAdd(&acc[2][sl[q]], sn * yv[q]);
-          }
-        }
-      }
+    auto add = [&](uint32_t sl, float a, float y) {
+      if (sl == kNoSlot) return;
+      float cs, sn;
+      weights_of_angle(a, cs, sn);
+      const int k = acc_index((int)sl);
+      atomicAdd(acc + k, y);
+      atomicAdd(acc + kAccStride + k, cs * y);
+      atomicAdd(acc + 2 * kAccStride + k, sn * y);
+    };
+    // warps take contiguous ranges of the group's chunks (detectors), so warps running at the
+    // same time sit far apart on the focal plane and rarely add to the same pixel at once
+    const int n_it = (G.n_blk + cw.cpi - 1) / cw.cpi;
+    const int per = (n_it + kWarps - 1) / kWarps;
+    for (int it = warp * per; it < min(n_it, (warp + 1) * per); it++) {
+      const int c = it * cw.cpi + cw.sub;
+      if (c >= G.n_blk) continue;
+      visit_chunk(
+          G, block_off, c, cw,
+          [&](int64_t a0, int q) {
+            const int64_t i = a0 + 4 * (int64_t)q;
+            const uint2 s2 = __ldcs(reinterpret_cast<const uint2*>(slot + i));
+            const float4 a = __ldcs(reinterpret_cast<const float4*>(ang2 + i));
+            const float4 y = __ldcs(reinterpret_cast<const float4*>(ur + i));
+            add(s2.x & 0xFFFFu, a.x, y.x);
+            add(s2.x >> 16, a.y, y.y);
+            add(s2.y & 0xFFFFu, a.z, y.z);
+            add(s2.y >> 16, a.w, y.w);
+          },
+          [&](int64_t i) { add(__ldcs(slot + i), __ldcs(ang2 + i), __ldcs(ur + i)); });
     }
     __syncthreads();
     float4* yr = y4 + r * y_stride4;
     for (int k = threadIdx.x; k < G.n_slots; k += kWinThreads) {
       const int32_t p = __ldg(slot_pix + G.slot_off + k);
-      atomicAdd(yr + p, make_float4(acc[0][k], acc[1][k], acc[2][k], 0.f));
+      const int j = acc_index(k);
+      atomicAdd(yr + p, make_float4(acc[j], acc[kAccStride + j], acc[2 * kAccStride + j], 0.f));
     }
     __syncthreads();   // the next column clears the sums
   }
@@ -316,10 +372,13 @@ cudaError_t launch_point_win32(const PGroup* groups, int64_t n_groups, const int
                                const float* u, int64_t u_stride, int nrhs, const int32_t* done,
                                int done_stride, float* y4, int64_t y_stride, cudaStream_t s) {
   if (n_groups == 0 || nrhs <= 0) return cudaSuccess;
-  if (n_groups > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  k_point_win32<<<(unsigned)n_groups, kWinThreads, 0, s>>>(groups, block_off, slot, slot_pix, ang2, u, u_stride,
-                                                           nrhs, done, done_stride, reinterpret_cast<float4*>(y4),
-                                                           y_stride / 4);
+  if (n_groups > 0x7fffffffLL || u_stride % 4 != 0) return cudaErrorInvalidValue;
+  static cudaError_t st = cudaSuccess;
+  static bool set = false;
+  MM_TRY_CUDA(smem_limit_once(k_point_win32, kPointSmem, st, set));
+  k_point_win32<<<(unsigned)n_groups, kWinThreads, kPointSmem, s>>>(groups, block_off, slot, slot_pix, ang2, u,
+                                                                      u_stride, nrhs, done, done_stride,
+                                                                      reinterpret_cast<float4*>(y4), y_stride / 4);
   return cudaGetLastError();
 }
 

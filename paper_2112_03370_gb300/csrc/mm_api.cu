@@ -167,6 +167,9 @@ void free_plan(Plan* P) {
   dfree(P->map64_in); dfree(P->map64_out); dfree(P->td_a); dfree(P->td_b); dfree(P->t32);
   dfree(P->wdf); dfree(P->tabdf); dfree(P->twdf); dfree(P->tdf); dfree(P->mapdf);
   dfree(P->ang2); dfree(P->groups); dfree(P->slot); dfree(P->slot_pix); dfree(P->u32);
+  for (void*& b : P->stage) if (b) { cudaFree(b); b = nullptr; }
+  for (cudaEvent_t& e : P->stage_ev) if (e) { cudaEventDestroy(e); e = nullptr; }
+  if (P->copy_stream) cudaStreamDestroy(P->copy_stream);
   free_cg(reinterpret_cast<CgState*>(P->cg));
   free_blk(reinterpret_cast<BlkState*>(P->blk));
   free_defl(reinterpret_cast<DeflState*>(P->defl));
@@ -1000,7 +1003,9 @@ struct Request {
   std::vector<int32_t> pix;
   std::vector<float> psi;
   std::vector<double> band;
-  std::vector<double> d;
+  std::vector<unsigned char> d;   // the TOD, float64 or float32 (d_is_fp32)
+  int d_is_fp32 = 0;
+  bool fp32 = true;               // FP32 iterations (batched) or FP64-class iterations (own launches)
   mm_solve_opts opts{};
   size_t footprint = 0;
   int state = 0;                  // 0 queued, 1 running, 2 finished
@@ -1043,8 +1048,9 @@ struct Server {
 size_t estimate_footprint(const Request& r) {
   int64_t N = 0;
   for (int64_t v : r.block_len) N += v;
-  // pointing, FP32, FP64 and df64 weights, un-pointed FP32 and df64 buffers: 76 bytes per sample
-  return (size_t)N * 76 + (size_t)r.desc.n_pix * 480 + ((size_t)64 << 20);
+  // pointing (pixel, angle, reduced angle, window slot), FP32, FP64 and df64 weights, un-pointed
+  // FP32 and df64 buffers, N^-1 t and the TOD: 90 bytes per sample
+  return (size_t)N * 90 + (size_t)r.desc.n_pix * 480 + ((size_t)64 << 20);
 }
 
 void finish_request(Server* S, Request* r, int status) {
@@ -1068,25 +1074,30 @@ void finish_request(Server* S, Request* r, int status) {
   S->cv_done.notify_all();
 }
 
-// plan + right-hand side + PCG initialisation of an admitted request
+// plan + right-hand side + PCG initialisation of an admitted request.  FP32 requests get an
+// MM_FP32_DF64 plan (FP32 iterations, double-float right-hand side and replacements); FP64-class
+// requests keep the plan precision they asked for, whose FP64-class operator (IEEE FP64 for
+// MM_FP64 / MM_FP32, double-float for MM_DF64 / MM_FP32_DF64) runs in every iteration.
 int start_request(Server* S, Request* r) {
   r->desc.block_len = r->block_len.data();
   r->desc.pix = r->pix.data();
   r->desc.psi = r->psi.data();
   r->desc.band = r->band.data();
   r->desc.inputs_on_device = 0;
-  r->desc.precision = MM_FP32_DF64;
+  if (r->fp32) r->desc.precision = MM_FP32_DF64;
   r->plan = new Plan();
   int st = build_plan(&r->desc, S->stream, r->plan);
   if (st != MM_OK) return st;
   Plan* P = r->plan;
-  MM_CUDA(cudaMalloc((void**)&r->d_dev, P->N * sizeof(double)));
+  const size_t esz = r->d_is_fp32 ? sizeof(float) : sizeof(double);
+  MM_CUDA(cudaMalloc((void**)&r->d_dev, P->N * esz));
   MM_CUDA(cudaMalloc((void**)&r->b_dev, P->n_obs * 3 * sizeof(double)));
-  MM_CUDA(cudaMemcpyAsync(r->d_dev, r->d.data(), P->N * sizeof(double), cudaMemcpyHostToDevice, S->stream));
-  st = mm_rhs(reinterpret_cast<mm_plan_t>(P), r->d_dev, 0, 1, r->b_dev, S->stream);
+  MM_CUDA(cudaMemcpyAsync(r->d_dev, r->d.data(), P->N * esz, cudaMemcpyHostToDevice, S->stream));
+  st = mm_rhs(reinterpret_cast<mm_plan_t>(P), r->d_dev, r->d_is_fp32, 1, r->b_dev, S->stream);
   if (st != MM_OK) return st;
-  MM_TRY(ensure_cg(P, 1, true, &r->cg));
-  r->w = make_work(P, r->cg, 1, true, r->opts.tol, r->opts.max_iter);
+  MM_TRY(ensure_cg(P, 1, r->fp32, &r->cg));
+  if (!r->fp32) MM_TRY(ensure_df(P, 1));
+  r->w = make_work(P, r->cg, 1, r->fp32, r->opts.tol, r->opts.max_iter);
   MM_CUDA(cudaMallocHost((void**)&r->scal_host, sizeof(CgScalars)));
   MM_CUDA(launch_pack3to4(r->b_dev, P->n_obs, 1, r->cg->b, S->stream));
   MM_CUDA(launch_cg(CG_INIT, r->w, S->stream));
@@ -1101,9 +1112,10 @@ int rebuild_launch(Server* S) {
   int halo = 0;
   for (size_t i = 0; i < S->running.size(); i++) {
     Request* r = S->running[i];
+    if (!r->fp32) continue;   // FP64-class requests run their own iterations
     Plan* P = r->plan;
     for (TileDesc td : P->segs_host) {
-      td.prob = (int32_t)i;
+      td.prob = (int32_t)probs.size();
       tiles.push_back(td);
     }
     halo = std::max(halo, (int)P->seg_halo);
@@ -1185,20 +1197,32 @@ void server_loop(Server* S) {
     if (S->dirty && rebuild_launch(S) != MM_OK) break;
     const int nb = (int)S->running.size();
     for (Request* r : S->running) r->batch = std::max(r->batch, nb);
-    // one PCG iteration of every running request, one tile launch for all of them
+    // one PCG iteration of every running request: one tile launch for all FP32 requests, the
+    // FP64-class requests' own operator launches after it
     cudaStream_t s = S->stream;
-    for (Request* r : S->running) launch_cg(CG_PUPDATE, r->w, s);
-    TileArgs a{};
-    a.tiles = S->tiles_dev;
-    a.n_tiles = S->n_tiles;
-    a.nrhs = 1;
-    a.tw = S->running[0]->plan->tw32;
-    a.probs = S->probs_dev;
-    a.done_stride = 0;
-    launch_tiles_fp32_multi(a, S->halo, s);
+    const Request* first32 = nullptr;
+    for (Request* r : S->running)
+      if (r->fp32) {
+        if (!first32) first32 = r;
+        launch_cg(CG_PUPDATE, r->w, s);
+      }
+    if (first32) {
+      TileArgs a{};
+      a.tiles = S->tiles_dev;
+      a.n_tiles = S->n_tiles;
+      a.nrhs = 1;
+      a.tw = first32->plan->tw32;
+      a.probs = S->probs_dev;
+      a.done_stride = 0;
+      launch_tiles_fp32_multi(a, S->halo, s);
+    }
     for (Request* r : S->running) {
-      launch_cg(CG_DOT_PQ, r->w, s);
-      launch_cg(CG_UPDATE, r->w, s);
+      if (r->fp32) {
+        launch_cg(CG_DOT_PQ, r->w, s);
+        launch_cg(CG_UPDATE, r->w, s);
+      } else {
+        enqueue_iteration(r->plan, r->w, 1, false, s);
+      }
       r->launched += 1;
     }
     step += 1;
@@ -1210,12 +1234,20 @@ void server_loop(Server* S) {
     for (Request* r : S->running) {
       const CgScalars sc = *r->scal_host;
       const int rel_every = r->opts.reliable_every > 0 ? r->opts.reliable_every : 50;
-      if (!sc.done && (sc.paused || sc.since_rep >= rel_every)) {   // FP64 residual replacement
+      if (r->fp32 && !sc.done && (sc.paused || sc.since_rep >= rel_every)) {   // FP64 residual replacement
         Plan* P = r->plan;
         cudaMemsetAsync(r->cg->q, 0, P->n_obs * 4 * sizeof(double), s);
         apply64_internal(P, r->cg->x, r->cg->q, 1, s,
                          reinterpret_cast<const int32_t*>(r->cg->scal) + kDoneOffsetInts, kScalStrideInts);
         launch_cg(CG_REPLACE, r->w, s);
+        cudaMemcpyAsync(r->scal_host, r->cg->scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+      }
+      if (!r->fp32 && sc.done) {   // FP64-class request: the true residual for the report
+        Plan* P = r->plan;
+        cudaMemsetAsync(r->cg->q, 0, P->n_obs * 4 * sizeof(double), s);
+        apply64_internal(P, r->cg->x, r->cg->q, 1, s);
+        launch_cg(CG_TRUE_RES, r->w, s);
         cudaMemcpyAsync(r->scal_host, r->cg->scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, s);
         cudaStreamSynchronize(s);
       }
@@ -1230,7 +1262,8 @@ void server_loop(Server* S) {
         in.n_true_res = sc2.n_true;
         in.t_queue_ms = std::chrono::duration<double, std::milli>(r->t_admit - r->t_submit).count();
         in.t_ms = std::chrono::duration<double, std::milli>(Clock::now() - r->t_admit).count();
-        in.n_apply32 = r->launched;
+        in.n_apply32 = r->fp32 ? r->launched : 0;
+        in.n_apply64 = r->fp32 ? sc2.n_true : r->launched;
         int st = sc2.done ? sc2.status : MM_ETIMEOUT;
         if (st == MM_OK && !sc2.done) st = MM_ENOTCONV;
         if (collect_map(S, r) != MM_OK && st == MM_OK) st = MM_ECUDA;
@@ -1325,61 +1358,121 @@ int mm_apply_Ninv(mm_plan_t plan, const double* t, double* y, void* stream) {
   return MM_OK;
 }
 
+// Is p host memory (pinned or pageable) rather than device or managed memory?
+bool is_host_pointer(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();   // older drivers report unregistered host memory as an error
+    return true;
+  }
+  return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+constexpr size_t kStageBytes = (size_t)64 << 20;
+
+// Host TOD -> the df64 input buffer: chunks of one column go through two staging buffers, the
+// copy of chunk k + 1 (copy stream) overlapping the split of chunk k (stream s).
+int stage_d_to_df(Plan* P, const void* d, int d_is_fp32, int r0, int g, cudaStream_t s) {
+  if (!P->stage[0]) {
+    for (int i = 0; i < 2; i++) MM_TRY(dalloc(P, reinterpret_cast<unsigned char**>(&P->stage[i]), kStageBytes));
+    P->stage_bytes = kStageBytes;
+    MM_CUDA(cudaStreamCreateWithFlags(&P->copy_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : P->stage_ev) MM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  const size_t esz = d_is_fp32 ? sizeof(float) : sizeof(double);
+  const int64_t chunk = (int64_t)(P->stage_bytes / esz) & ~(int64_t)1023;
+  cudaStream_t cs = P->copy_stream;
+  MM_CUDA(cudaEventRecord(P->stage_ev[2], s));   // the buffers are free once earlier work on s is
+  MM_CUDA(cudaEventRecord(P->stage_ev[3], s));
+  int k = 0;
+  for (int r = r0; r < r0 + g; r++) {
+    const unsigned char* col = reinterpret_cast<const unsigned char*>(d) + (size_t)r * P->N * esz;
+    for (int64_t c0 = 0; c0 < P->N; c0 += chunk, k ^= 1) {
+      const int64_t n = std::min(chunk, P->N - c0);
+      MM_CUDA(cudaStreamWaitEvent(cs, P->stage_ev[2 + k], 0));
+      MM_CUDA(cudaMemcpyAsync(P->stage[k], col + (size_t)c0 * esz, (size_t)n * esz, cudaMemcpyHostToDevice, cs));
+      MM_CUDA(cudaEventRecord(P->stage_ev[k], cs));
+      MM_CUDA(cudaStreamWaitEvent(s, P->stage_ev[k], 0));
+      MM_CUDA(launch_d_to_df(P->lpix + c0, P->stage[k], d_is_fp32, n, 1,
+                             P->tdf + (size_t)(r - r0) * df_stride(P) + c0, df_stride(P), s));
+      MM_CUDA(cudaEventRecord(P->stage_ev[2 + k], s));
+    }
+  }
+  return MM_OK;
+}
+
 int mm_rhs(mm_plan_t plan, const void* d, int d_is_fp32, int nrhs, double* b, void* stream) {
   Plan* P = reinterpret_cast<Plan*>(plan);
   if (!P || !d || !b || nrhs <= 0) return fail(MM_EINVAL, "bad argument");
   DeviceGuard g(P->device);
   cudaStream_t s = as_stream(stream);
+  const bool host_d = is_host_pointer(d);
   MM_TRY(ensure_maps(P, nrhs, false));
   const size_t n4 = (size_t)nrhs * P->n_obs * 4;
+  const size_t esz = d_is_fp32 ? sizeof(float) : sizeof(double);
   MM_CUDA(cudaMemsetAsync(P->map64_out, 0, n4 * sizeof(double), s));
-  if (P->tmpl) {   // template map-making: b = P^T F_T G d (the TOD split to df64, then one fused kernel)
-    const TmplState* ts = reinterpret_cast<const TmplState*>(P->tmpl);
+  if (P->tmpl || P->df64) {   // the TOD split to df64 pairs (G d), then the df64 operator
     const int k = df_cols(P, nrhs);
-    MM_TRY(ensure_tdf(P, k));
-    const size_t esz = d_is_fp32 ? sizeof(float) : sizeof(double);
+    MM_TRY(P->tmpl ? ensure_tdf(P, k) : ensure_df(P, nrhs));
     for (int r0 = 0; r0 < nrhs; r0 += k) {
       const int g = std::min(k, nrhs - r0);
-      MM_CUDA(launch_d_to_df(P->lpix, reinterpret_cast<const char*>(d) + (size_t)r0 * P->N * esz, d_is_fp32,
-                             P->N, g, P->tdf, df_stride(P), s));
-      MM_CUDA(launch_tmpl_apply_df(ts->dev, P->n_blocks, P->wdf, nullptr, 0, P->tdf, df_stride(P),
-                                   P->map64_out + (size_t)r0 * P->n_obs * 4, P->n_obs * 4, g, nullptr, 0, s));
+      if (host_d) {
+        MM_TRY(stage_d_to_df(P, d, d_is_fp32, r0, g, s));
+      } else {
+        MM_CUDA(launch_d_to_df(P->lpix, reinterpret_cast<const char*>(d) + (size_t)r0 * P->N * esz, d_is_fp32,
+                               P->N, g, P->tdf, df_stride(P), s));
+      }
+      double* out = P->map64_out + (size_t)r0 * P->n_obs * 4;
+      if (P->tmpl) {   // template map-making: b = P^T F_T G d in one fused kernel
+        const TmplState* ts = reinterpret_cast<const TmplState*>(P->tmpl);
+        MM_CUDA(launch_tmpl_apply_df(ts->dev, P->n_blocks, P->wdf, nullptr, 0, P->tdf, df_stride(P), out,
+                                     P->n_obs * 4, g, nullptr, 0, s));
+      } else {
+        TileArgs a = df_args(P);
+        a.nrhs = g;
+        a.x = P->tdf;
+        a.y = out;
+        MM_CUDA(launch_tiles_df(a, s));
+      }
     }
   } else if (P->algo == MM_TPLZ_DIRECT) {
     MM_TRY(ensure_td(P));
-    const size_t esz = d_is_fp32 ? sizeof(float) : sizeof(double);
     for (int r = 0; r < nrhs; r++) {
       const void* dr = reinterpret_cast<const char*>(d) + (size_t)r * P->N * esz;
+      if (host_d) {   // the column into td_b, masked into td_a
+        MM_CUDA(cudaMemcpyAsync(P->td_b, dr, P->N * esz, cudaMemcpyHostToDevice, s));
+        dr = P->td_b;
+      }
       MM_CUDA(launch_mask_d(P->lpix, dr, d_is_fp32, P->N, P->td_a, s));
       MM_CUDA(launch_toeplitz_direct(P->band, P->block_off_dev, P->n_blocks, P->lambda, P->N,
                                      P->td_a, P->td_b, s));
       MM_CUDA(launch_point64(P->lpix, P->w64, P->N, P->td_b, P->map64_out + (size_t)r * P->n_obs * 4, s));
     }
-  } else if (P->df64) {
-    MM_TRY(ensure_df(P, nrhs));
-    const int k = df_cols(P, nrhs);
-    const size_t esz = d_is_fp32 ? sizeof(float) : sizeof(double);
-    for (int r0 = 0; r0 < nrhs; r0 += k) {
-      const int g = std::min(k, nrhs - r0);
-      MM_CUDA(launch_d_to_df(P->lpix, reinterpret_cast<const char*>(d) + (size_t)r0 * P->N * esz, d_is_fp32,
-                             P->N, g, P->tdf, df_stride(P), s));
-      TileArgs a = df_args(P);
-      a.nrhs = g;
-      a.x = P->tdf;
-      a.y = P->map64_out + (size_t)r0 * P->n_obs * 4;
-      MM_CUDA(launch_tiles_df(a, s));
-    }
   } else {
     TileArgs a = base_args(P, false);
-    a.nrhs = nrhs;
-    a.x = d;
     a.x_is_fp32 = d_is_fp32 ? 1 : 0;
     a.x_stride = P->N;
-    a.y = P->map64_out;
     a.y_stride = P->n_obs * 4;
-    MM_CUDA(launch_tiles_fp64(MODE_RHS, a, s));
+    if (!host_d) {
+      a.nrhs = nrhs;
+      a.x = d;
+      a.y = P->map64_out;
+      MM_CUDA(launch_tiles_fp64(MODE_RHS, a, s));
+    } else {   // one column at a time through the plan's N-sample FP64 buffer
+      MM_TRY(ensure_td(P));
+      for (int r = 0; r < nrhs; r++) {
+        MM_CUDA(cudaMemcpyAsync(P->td_a, reinterpret_cast<const char*>(d) + (size_t)r * P->N * esz, P->N * esz,
+                                cudaMemcpyHostToDevice, s));
+        a.nrhs = 1;
+        a.x = P->td_a;
+        a.y = P->map64_out + (size_t)r * P->n_obs * 4;
+        MM_CUDA(launch_tiles_fp64(MODE_RHS, a, s));
+      }
+    }
   }
   MM_CUDA(launch_unpack4to3(P->map64_out, P->n_obs, nrhs, b, s));
+  // a host TOD may be reused once the call returns
+  if (host_d) MM_CUDA(cudaStreamSynchronize(s));
   return MM_OK;
 }
 
@@ -2320,13 +2413,15 @@ int mm_server_create(size_t hbm_budget, int max_slots, mm_server_t* out) {
   return MM_OK;
 }
 
-int mm_submit(mm_server_t server, const mm_problem_desc* desc, const double* d, const mm_solve_opts* opts,
-              mm_req_t* id) {
+int mm_submit(mm_server_t server, const mm_problem_desc* desc, const void* d, int d_is_fp32,
+              const mm_solve_opts* opts, mm_req_t* id) {
   Server* S = reinterpret_cast<Server*>(server);
   if (!S || !desc || !d || !opts || !id) return fail(MM_EINVAL, "bad argument");
   MM_TRY(validate_desc(desc));
   if (desc->inputs_on_device) return fail(MM_EINVAL, "mm_submit takes host inputs");
-  if (opts->precision != MM_FP32) return fail(MM_EINVAL, "the server runs the FP32 operators (MM_FP32)");
+  if (opts->precision != MM_FP32 && opts->precision != MM_FP64)
+    return fail(MM_EINVAL, "opts->precision must be MM_FP32 or MM_FP64");
+  if (desc->toeplitz_algo == MM_TPLZ_DIRECT) return fail(MM_EINVAL, "the server runs FFT plans");
   if (opts->precond != MM_PREC_BD) return fail(MM_EINVAL, "the server runs the block-Jacobi preconditioner");
   if (!(opts->tol > 0.0) || opts->max_iter < 0) return fail(MM_EINVAL, "bad tol / max_iter");
   Request* r = new Request();
@@ -2341,7 +2436,10 @@ int mm_submit(mm_server_t server, const mm_problem_desc* desc, const double* d, 
   r->pix.assign(desc->pix, desc->pix + N);
   r->psi.assign(desc->psi, desc->psi + N);
   r->band.assign(desc->band, desc->band + (size_t)nb * (desc->lambda + 1));
-  r->d.assign(d, d + N);
+  r->d_is_fp32 = d_is_fp32 ? 1 : 0;
+  const unsigned char* db = reinterpret_cast<const unsigned char*>(d);
+  r->d.assign(db, db + (size_t)N * (d_is_fp32 ? sizeof(float) : sizeof(double)));
+  r->fp32 = opts->precision == MM_FP32;
   r->opts = *opts;
   r->footprint = estimate_footprint(*r);
   r->t_submit = Clock::now();

@@ -172,6 +172,12 @@ struct Plan {
   double* td_b = nullptr;
   size_t td_cap = 0;
 
+  // staging of host TOD in mm_rhs: two device buffers filled on a copy stream
+  void* stage[2] = {nullptr, nullptr};
+  size_t stage_bytes = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t stage_ev[4] = {nullptr, nullptr, nullptr, nullptr};   // copied[0..1], consumed[0..1]
+
   cudaStream_t stream = nullptr;       // plan-owned stream (graph capture)
   void* cg = nullptr;                  // solver workspace (mm_api.cu)
   void* blk = nullptr;                 // block-CG workspace (mm_api.cu)

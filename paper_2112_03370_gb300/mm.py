@@ -99,7 +99,7 @@ def _load():
     lib.mm_deflation_get.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp, vp, vp]
     lib.mm_deflation_apply.argtypes = [vp, vp, vp, i32, vp]
     lib.mm_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
-    lib.mm_submit.argtypes = [vp, ctypes.POINTER(ProblemDesc), vp, ctypes.POINTER(SolveOpts),
+    lib.mm_submit.argtypes = [vp, ctypes.POINTER(ProblemDesc), vp, ctypes.c_int, ctypes.POINTER(SolveOpts),
                               ctypes.POINTER(i64)]
     lib.mm_poll.argtypes = [vp, i64, ctypes.POINTER(SolveInfo)]
     lib.mm_wait.argtypes = [vp, i64, i64, vp, ctypes.POINTER(SolveInfo)]
@@ -230,10 +230,14 @@ def mm_apply_Ninv(plan: Plan, t: torch.Tensor, y: torch.Tensor, stream=None):
 
 
 def mm_rhs(plan: Plan, d: torch.Tensor, b: torch.Tensor, stream=None):
-    """b [nrhs, n_obs, 3] (or [n_obs, 3]) = P~^T N^-1 G d for d [nrhs, N] (or [N])."""
+    """b [nrhs, n_obs, 3] (or [n_obs, 3]) = P~^T N^-1 G d for d [nrhs, N] (or [N]).  d may be a CUDA
+    tensor or a CPU tensor (pinned or pageable); a CPU d is copied by the library and the call
+    returns once it has been read."""
     if d.dtype not in (torch.float64, torch.float32):
         raise TypeError("d must be float64 or float32")
-    _dev(d, d.dtype, "d"); _dev(b, torch.float64, "b")
+    if not d.is_contiguous():
+        raise ValueError("d must be contiguous")
+    _dev(b, torch.float64, "b")
     nrhs = 1 if d.dim() == 1 else d.shape[0]
     _check(_lib.mm_rhs(ctypes.c_void_p(plan.handle), _ptr(d), 1 if d.dtype == torch.float32 else 0,
                        nrhs, _ptr(b), _stream_ptr(stream)))
@@ -379,22 +383,28 @@ class Server:
         self._keep = {}
 
     def submit(self, n_det, n_int, block_len, n_pix, pix, psi, lam, band, d, tol=1e-6,
-               max_iter=5000, cond_max=1e3, reliable_every=0, deadline_us=0) -> int:
+               max_iter=5000, cond_max=1e3, reliable_every=0, deadline_us=0,
+               precision=MM_FP32, plan_precision=MM_DF64) -> int:
+        """Queue a solve (host arrays).  d float32 is passed as FP32 TOD, anything else as float64.
+        precision MM_FP32: batched FP32 iterations; MM_FP64: FP64-class iterations in the
+        arithmetic of plan_precision (IEEE FP64 for MM_FP64 / MM_FP32, double-float otherwise)."""
         import numpy as np
         pix = np.ascontiguousarray(np.asarray(pix, dtype=np.int32))
         psi = np.ascontiguousarray(np.asarray(psi, dtype=np.float32))
         band = np.ascontiguousarray(np.asarray(band, dtype=np.float64))
-        d = np.ascontiguousarray(np.asarray(d, dtype=np.float64))
+        d = np.asarray(d)
+        d_is_fp32 = 1 if d.dtype == np.float32 else 0
+        d = np.ascontiguousarray(d if d_is_fp32 else d.astype(np.float64, copy=False))
         bl = (ctypes.c_int64 * len(block_len))(*[int(v) for v in block_len])
         desc = ProblemDesc(n_det=n_det, n_int=n_int, block_len=bl, n_pix=n_pix,
                            pix=pix.ctypes.data, psi=psi.ctypes.data, lambda_=lam,
-                           band=band.ctypes.data, cond_max=cond_max, precision=MM_FP32,
+                           band=band.ctypes.data, cond_max=cond_max, precision=plan_precision,
                            toeplitz_algo=MM_TPLZ_AUTO, inputs_on_device=0, tile_steps=0)
-        opts = SolveOpts(tol=tol, max_iter=max_iter, precond=MM_PREC_BD, precision=MM_FP32,
+        opts = SolveOpts(tol=tol, max_iter=max_iter, precond=MM_PREC_BD, precision=precision,
                          reliable_every=reliable_every, deadline_us=deadline_us)
         rid = ctypes.c_int64()
         _check(_lib.mm_submit(ctypes.c_void_p(self.handle), ctypes.byref(desc),
-                              d.ctypes.data, ctypes.byref(opts), ctypes.byref(rid)))
+                              d.ctypes.data, d_is_fp32, ctypes.byref(opts), ctypes.byref(rid)))
         self._keep[rid.value] = n_pix
         return rid.value
 

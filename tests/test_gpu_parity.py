@@ -135,6 +135,29 @@ def test_rhs_matches_oracle(fp32_d):
     assert rel_max(b.cpu().numpy(), O.rhs(op, d.astype(np.float64))) < 1e-11
 
 
+@pytest.mark.parametrize("precision,algo", [(0, 0), (3, 0), (0, 3)])
+@pytest.mark.parametrize("fp32_d", [False, True])
+@pytest.mark.parametrize("pinned", [False, True])
+def test_rhs_from_host_tod_matches_oracle(precision, algo, fp32_d, pinned):
+    """The TOD may be handed over in host memory: the library stages it (IEEE FP64, double-float
+    and direct-sum plans), two columns at once, and b matches the oracle's to the FP64 tolerance."""
+    if algo == 3:
+        prob = small(9, block_len=(7001, 5, 3300, 12, 0, 4000), lam=64)
+    else:
+        prob = small(9)
+    gp, op, nb = plans(prob, precision=precision, algo=algo)
+    rng = np.random.default_rng(5)
+    d2 = np.stack([nb["d"], rng.standard_normal(nb["d"].size)])
+    d2 = d2.astype(np.float32) if fp32_d else d2
+    dh = torch.as_tensor(d2)
+    if pinned:
+        dh = dh.pin_memory()
+    b = torch.empty(2, op.n_obs, 3, dtype=torch.float64, device="cuda")
+    mm().mm_rhs(gp, dh, b)
+    for r in range(2):
+        assert rel_max(b[r].cpu().numpy(), O.rhs(op, d2[r].astype(np.float64))) < 1e-11
+
+
 # ----------------------------------------------------------------------- PCG (a8, a11)
 
 @pytest.fixture(scope="module")

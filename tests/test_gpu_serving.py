@@ -30,9 +30,9 @@ def submit(srv, p):
                       p["lam"], p["band"], p["d"], tol=TOL)
 
 
-def oracle_map(p):
+def oracle_map(p, d=None):
     op = O.make_plan(p["pix"], p["psi"], p["block_len"], p["band"], p["n_pix"])
-    x = O.pcg(op, O.rhs(op, p["d"]), tol=TOL, max_iter=5000).x
+    x = O.pcg(op, O.rhs(op, p["d"] if d is None else d), tol=TOL, max_iter=5000).x
     m = np.zeros((p["n_pix"], 3))
     m[op.obs_to_global] = x
     return m
@@ -96,3 +96,30 @@ def test_admission_respects_budget_and_bad_request(probs):
         srv.wait(bad)
     assert e.value.code == m.MM_EINVAL
     srv.close()
+
+
+def test_fp32_tod_and_fp64_class_requests_in_one_mix(probs):
+    """FP32 TOD is accepted (d_is_fp32), and FP64-class requests (double-float and IEEE FP64
+    operators in every iteration) are served next to a mixed-precision one: each matches the
+    oracle's PCG at the same tol, within the FP64 tolerance for the FP64-class requests."""
+    m = mm()
+    p = probs[1]
+    args = (p["n_det"], p["n_int"], p["block_len"].tolist(), p["n_pix"], p["pix"], p["psi"], p["lam"],
+            p["band"])
+    d32 = p["d"].astype(np.float32)
+    srv = m.Server(max_slots=8)
+    r32 = srv.submit(*args, d32, tol=TOL)
+    rdf = srv.submit(*args, p["d"], tol=TOL, precision=m.MM_FP64, plan_precision=m.MM_DF64)
+    r64 = srv.submit(*args, p["d"], tol=TOL, precision=m.MM_FP64, plan_precision=m.MM_FP64)
+    m32, i32 = srv.wait(r32)
+    mdf, idf = srv.wait(rdf)
+    m64, i64 = srv.wait(r64)
+    srv.close()
+    ref = oracle_map(p)
+    ref32 = oracle_map(p, d32.astype(np.float64))
+    assert i32.status == 0 and i32.true_rel_res < TOL and i32.n_apply32 > 0
+    assert np.linalg.norm(m32 - ref32) <= 1e-5 * np.linalg.norm(ref32)
+    for mp, info in ((mdf, idf), (m64, i64)):
+        assert info.status == 0 and info.true_rel_res < TOL
+        assert info.n_apply32 == 0 and info.n_apply64 >= info.iters   # FP64-class in every iteration
+        assert np.linalg.norm(mp - ref) <= 1e-6 * np.linalg.norm(ref)
