@@ -60,8 +60,15 @@ typedef enum {
  *   MM_FP32_DF64  FP32 operators for the CG iterations; FP64-class operators (right-hand side,
  *                 residual replacement, true residual) in double-float. */
 enum { MM_FP64 = 0, MM_FP32 = 1, MM_DF64 = 2, MM_FP32_DF64 = 3 };
-/* Algorithm of the block-Toeplitz product. */
-enum { MM_TPLZ_AUTO = 0, MM_TPLZ_FFT = 1, MM_TPLZ_DIRECT = 3 };
+/* Algorithm of the block-Toeplitz product.
+ *   MM_TPLZ_FFT     shared-memory overlap-save FFT tiles (every precision).
+ *   MM_TPLZ_GEMM    the FP32 operators' N^-1 as banded Toeplitz-block GEMMs on the tensor cores
+ *                   (tcgen05, 3xTF32, lambda <= 128, plans with FP32 operators); the FP64-class
+ *                   operators keep the FFT tiles.
+ *   MM_TPLZ_DIRECT  band sum by the definition (checks, tiny lambda).
+ *   MM_TPLZ_AUTO    MM_TPLZ_GEMM where it measured faster than the FFT (FP32 operators, lambda up
+ *                   to the measured crossover), else MM_TPLZ_FFT. */
+enum { MM_TPLZ_AUTO = 0, MM_TPLZ_FFT = 1, MM_TPLZ_GEMM = 2, MM_TPLZ_DIRECT = 3 };
 /* Preconditioner: block-Jacobi, or the two-level a-posteriori A-DEF1 preconditioner built by
  * mm_deflation_build (Sect. 3.2, Eq. 2lvlDef). */
 enum { MM_PREC_BD = 0, MM_PREC_2LVL_POST = 1 };
@@ -81,8 +88,8 @@ enum { MM_PREC_BD = 0, MM_PREC_2LVL_POST = 1 };
  *                  excised together with their samples (Sect. 2.4); <= 0 selects 1e3.
  *   precision      MM_FP64, MM_FP32, MM_DF64 or MM_FP32_DF64 (above): arithmetic of mm_apply_A
  *                  (FP32 for MM_FP32 and MM_FP32_DF64) and of mm_rhs (the FP64-class operators).
- *   toeplitz_algo  MM_TPLZ_AUTO/MM_TPLZ_FFT (shared-memory overlap-save FFT) or MM_TPLZ_DIRECT
- *                  (band sum by the definition, O(lambda) per sample; for checks and tiny lambda).
+ *   toeplitz_algo  MM_TPLZ_AUTO, MM_TPLZ_FFT, MM_TPLZ_GEMM or MM_TPLZ_DIRECT (above); MM_TPLZ_GEMM
+ *                  needs lambda <= 128 and FP32 operators (MM_FP32 or MM_FP32_DF64), else MM_EINVAL.
  *   inputs_on_device  non-zero: pix, psi and band are device pointers; zero: host pointers.
  *   tile_steps     FP32 operators: overlap-save tiles walked by one CTA, which keeps the overlap
  *                  of consecutive tiles in shared memory (0 = chosen from the problem size).
@@ -214,6 +221,46 @@ int mm_precond(mm_plan_t plan, const double* r, double* z, int nrhs, void* strea
 int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_solve_opts* opts,
                  mm_solve_info* info, void* stream);
 
+/* Solve the map-making problem from the TOD: x = (P~^T N^-1 P~)^-1 P~^T N^-1 G d for nrhs data
+ * vectors d [nrhs][N] (float64, or float32 with d_is_fp32; device memory, or host memory that the call
+ * copies into a plan-owned device buffer grown on first use), by PCG (Algorithm 1) from
+ * x_0 = 0 with the options of mm_pcg_solve.  With FP32 iterations (opts->precision MM_FP32) on an
+ * MM_FP32_DF64 plan and the block-Jacobi preconditioner, the right-hand side is formed with the FP32
+ * operators and every true residual is evaluated from the data as P~^T N^-1 G (d - P~ x) with the
+ * double-float operator, so one FP64-class pass serves both the right-hand side's accuracy and the
+ * final check (mm_rhs + mm_pcg_solve take two); the stop rule still requires the FP64-class true
+ * residual below tol ||b||.  Any other combination runs mm_rhs (FP64-class b, written into x first)
+ * and mm_pcg_solve.  x: [nrhs][n_obs][3] device; info: HOST [nrhs].  Blocks the calling thread.  The
+ * paper's problem statement (Sect. 2): the TOD in, the map out. */
+int mm_solve_tod(mm_plan_t plan, const void* d, int d_is_fp32, double* x, int nrhs, const mm_solve_opts* opts,
+                 mm_solve_info* info, void* stream);
+
+/* Autotuner of the FP32 A-application (an interface of this library; the paper has none).  Times
+ * the plan's own FP32 A x (CUDA events on the plan's stream, median of a few runs, inputs of the
+ * plan's size) over candidate configurations and keeps the fastest:
+ *   1. FP32 overlap-save tiles walked per segment (1, 2, 4, ..., 32; a CTA keeps the overlap of
+ *      consecutive tiles in shared memory, more segments keep more SMs busy);
+ *   2. target samples per pixel-window group of P and P^T (8192 ... 65536);
+ *   3. block width for mm_block_cg_solve with block_width = 0: the widest of 1, 2, 4, ..., max_width
+ *      whose device time per column of A X is within 2% of the best.
+ * Results and every timing go to *out (HOST).  Rebuilds the plan's segments and windows (captured
+ * solver graphs are captured again at the next solve).  Synchronous.  MM_EINVAL unless the plan
+ * has FP32 operators with pixel windows (MM_FP32 or MM_FP32_DF64 FFT plan without templates). */
+typedef struct {
+  int32_t tile_steps;        /* chosen tiles per segment */
+  int32_t win_samples;       /* chosen samples per window group */
+  int32_t block_width;       /* chosen block width (columns per batched A X) */
+  int32_t n_steps, n_win, n_width;
+  int32_t steps_cand[8];
+  double steps_ms[8];        /* one-column FP32 A x per candidate (ms) */
+  int32_t win_cand[8];
+  double win_ms[8];
+  int32_t width_cand[8];
+  double width_ms_per_col[8];
+  double apply_ms;           /* one-column FP32 A x with the chosen configuration (ms) */
+} mm_tune_info;
+int mm_autotune(mm_plan_t plan, int max_width, mm_tune_info* out, void* stream);
+
 /* Solve A X = B for nrhs right-hand sides by block conjugate gradients: Algorithm 2 (Sect. 3.2)
  * in its block Orthomin form, applied with R_0 = [b_1 .. b_s] (s independent right-hand sides,
  * e.g. noise realisations, instead of one right-hand side split over subdomains):
@@ -221,7 +268,8 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
  *   dependent are dropped; the paper leaves this case open), alpha_k = P_k^T R_{k-1},
  *   X_k = X_{k-1} + P_k alpha_k, R_k = R_{k-1} - A P_k alpha_k,
  *   Z_{k+1} = (I - P_k P_k^T A) M_BD R_k over the columns not yet converged.
- * The nrhs columns are solved in groups of block_width (0: min(nrhs, 64); at most 64), each group
+ * The nrhs columns are solved in groups of block_width (0: min(nrhs, 64), or min(nrhs, the width
+ * mm_autotune chose); at most 64), each group
  * sharing one batched A-application per iteration.  opts->precision selects FP32 or FP64
  * operators; the search blocks are FP32, X, R and the block_width x block_width matrices FP64.
  * A column stops when ||R_j|| < tol ||b_j||, confirmed by an FP64 true residual; columns above tol

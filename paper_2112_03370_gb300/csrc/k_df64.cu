@@ -101,9 +101,28 @@ __global__ void k_d_to_df(const int32_t* __restrict__ lpix, const D* __restrict_
   }
 }
 
+// t -= G d in df64 for the kept samples (t is 0 at the others): with t = P x this is the
+// time-domain residual of the right-hand side, so N^-1 and P^T of it give A x - b
+template <typename D>
+__global__ void k_sub_d_df(const int32_t* __restrict__ lpix, const D* __restrict__ d, int64_t N, int64_t d_stride,
+                           float2* __restrict__ t, int64_t t_stride) {
+  const int rhs = blockIdx.y;
+  const D* dr = d + rhs * d_stride;
+  float2* tr = t + rhs * t_stride;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    if (__ldg(lpix + i) < 0) continue;
+    df v;
+    if constexpr (sizeof(D) == 4) v = df_make(dr[i], 0.f);
+    else v = df((double)dr[i]);
+    const float2 a = tr[i];
+    const df r = df_make(a.x, a.y) - v;
+    tr[i] = make_float2(r.hi, r.lo);
+  }
+}
+
 unsigned grid_for(int64_t n, int per_block) {
   int64_t g = (n + per_block - 1) / per_block;
-  if (g > 152 * 16) g = 152 * 16;
+  if (g > 16 * sm_count()) g = 16 * sm_count();
   return (unsigned)(g > 0 ? g : 1);
 }
 
@@ -111,7 +130,7 @@ unsigned grid_for(int64_t n, int per_block) {
 
 cudaError_t launch_weights_df(const float* psi, int64_t N, float4* wdf, cudaStream_t s) {
   if (N == 0) return cudaSuccess;
-  k_weights_df<<<8 * 152, 256, 0, s>>>(psi, N, wdf);
+  k_weights_df<<<8 * sm_count(), 256, 0, s>>>(psi, N, wdf);
   return cudaGetLastError();
 }
 
@@ -144,6 +163,17 @@ cudaError_t launch_d_to_df(const int32_t* lpix, const void* d, int d_is_fp32, in
     k_d_to_df<float><<<grid, 256, 0, s>>>(lpix, reinterpret_cast<const float*>(d), N, N, t, t_stride);
   else
     k_d_to_df<double><<<grid, 256, 0, s>>>(lpix, reinterpret_cast<const double*>(d), N, N, t, t_stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sub_d_df(const int32_t* lpix, const void* d, int d_is_fp32, int64_t N, int nrhs, float2* t,
+                            int64_t t_stride, cudaStream_t s) {
+  if (N == 0 || nrhs <= 0) return cudaSuccess;
+  const dim3 grid(grid_for(N, 256), nrhs);
+  if (d_is_fp32)
+    k_sub_d_df<float><<<grid, 256, 0, s>>>(lpix, reinterpret_cast<const float*>(d), N, N, t, t_stride);
+  else
+    k_sub_d_df<double><<<grid, 256, 0, s>>>(lpix, reinterpret_cast<const double*>(d), N, N, t, t_stride);
   return cudaGetLastError();
 }
 

@@ -142,9 +142,9 @@ __device__ __forceinline__ void quad_meta(const TileArgs& a, int64_t g, int64_t 
 template <typename T, int MODE, int NQ>
 __device__ __forceinline__ void gather_quads(const TileArgs& a, int rhs, const TileDesc& td,
                                              const int64_t (&g)[NQ], T (&v)[NQ][4]) {
-  if constexpr (MODE == MODE_APPLY_T) {
+  if constexpr (MODE == MODE_APPLY_T || MODE == MODE_NINV_T) {
     // df64 tiles: un-pointed input t = P x (or the masked TOD) as (hi, lo) pairs
-    static_assert(std::is_same<T, df>::value, "2-CTA APPLY_T tiles are the df64 ones");
+    static_assert(std::is_same<T, df>::value, "2-CTA APPLY_T / NINV_T tiles are the df64 ones");
     const float2* t = reinterpret_cast<const float2*>(a.x) + rhs * a.x_stride;
 #pragma unroll
     for (int u = 0; u < NQ; u++) {
@@ -484,6 +484,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
   FFT::build_pass_tables(ptab, tw);
   __syncthreads();
 
+  float umax = 0.f;   // MODE_NINV_T df64 tiles: largest |u| this thread wrote
   const int n_steps = (CL == 1) ? seg.n_steps : 1;   // only the FP32 kernel walks segments
   for (int step = 0; step < n_steps; step++) {
     TileDesc td = seg;
@@ -641,7 +642,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
       cl.sync();
       other = cl.map_shared_rank(sm, rank ^ 1);
     }
-    if constexpr (MODE == MODE_NINV_T) {
+    if constexpr (MODE == MODE_NINV_T && CL == 1) {
       // y of the tile's output range, float pairs (g even, so 8-byte aligned inside the range)
       float* yo = reinterpret_cast<float*>(a.y) + rhs * a.y_stride;
       const int n_lo = r_lo >> 1, n_hi = (r_hi + 1) >> 1;
@@ -702,11 +703,40 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
             for (int e = 0; e < 4; e++) y[u][e] = T(0);
           }
         }
-        scatter_quads<T, MODE, NQ>(a, rhs, td, g, y);
+        if constexpr (MODE == MODE_NINV_T) {
+          // df64 u as (hi, lo) pairs over the tile's output range, and the CTA's max |u|
+          float2* yo = reinterpret_cast<float2*>(a.y) + rhs * a.y_stride;
+#pragma unroll
+          for (int u = 0; u < NQ; u++) {
+            if (g[u] >= td.out_lo && g[u] + 4 <= td.out_hi) {   // g a multiple of 4: 32-byte aligned
+              float4* q4 = reinterpret_cast<float4*>(yo + g[u]);
+              q4[0] = make_float4(y[u][0].hi, y[u][0].lo, y[u][1].hi, y[u][1].lo);
+              q4[1] = make_float4(y[u][2].hi, y[u][2].lo, y[u][3].hi, y[u][3].lo);
+            } else {
+#pragma unroll
+              for (int e = 0; e < 4; e++)
+                if (g[u] + e >= td.out_lo && g[u] + e < td.out_hi) yo[g[u] + e] = make_float2(y[u][e].hi, y[u][e].lo);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+              if (g[u] + e >= td.out_lo && g[u] + e < td.out_hi) {
+                const float m = fabsf(y[u][e].hi);
+                umax = (m == m) ? fmaxf(umax, m) : __int_as_float(0x7f800000);   // NaN -> +inf
+              }
+          }
+        } else {
+          scatter_quads<T, MODE, NQ>(a, rhs, td, g, y);
+        }
       }
     }
     if constexpr (CL == 2) cg::this_cluster().sync();
     else __syncthreads();   // the next tile overwrites the buffer
+  }
+  if constexpr (MODE == MODE_NINV_T && CL == 2) {
+    if (a.amax != nullptr) {   // non-negative floats order like their bit patterns
+      for (int o = 16; o > 0; o >>= 1) umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+      if ((threadIdx.x & 31) == 0) atomicMax(a.amax + rhs, __float_as_uint(umax));
+    }
   }
 }
 
@@ -735,6 +765,7 @@ int tile_kernels_init() {
   MM_SET((k_tile<double, 2, MODE_RHS>), kSmemBytes64);
   MM_SET((k_tile<double, 2, MODE_NINV>), kSmemBytes64);
   MM_SET((k_tile<df, 2, MODE_APPLY_T>), kSmemBytes64);
+  MM_SET((k_tile<df, 2, MODE_NINV_T>), kSmemBytes64);
 #undef MM_SET
   if (e == cudaSuccess) {
     // 2-CTA clusters with 136 KB of dynamic shared memory each are a non-portable size only in
@@ -836,6 +867,13 @@ int fp32_max_halo_samples() { return (int)((kSmemMax - kSmemBytes32) / sizeof(fl
 cudaError_t launch_tiles_df(const TileArgs& a, cudaStream_t s) {
   if (a.x_stride % 4 != 0) return cudaErrorInvalidValue;
   return launch_tiles<df, 2, MODE_APPLY_T>(a, kSmemBytes64, s);
+}
+
+// df64 u = N^-1 t: t and u (hi, lo) pairs [nrhs][x_stride] / [nrhs][y_stride] (multiples of 4),
+// a.amax (per column, zeroed by the caller) receives the bits of max |u|
+cudaError_t launch_ninv_df(const TileArgs& a, cudaStream_t s) {
+  if (a.x_stride % 4 != 0 || a.y_stride % 4 != 0) return cudaErrorInvalidValue;
+  return launch_tiles<df, 2, MODE_NINV_T>(a, kSmemBytes64, s);
 }
 
 cudaError_t launch_tiles_fp64(int mode, const TileArgs& a, cudaStream_t s) {

@@ -14,6 +14,9 @@
 // The weights (cos 2psi, sin 2psi) are evaluated in registers from the angle 2psi reduced to
 // [-pi, pi] once at plan time in FP64, so the kernels stream 6 bytes of pointing per sample
 // (slot + angle) instead of a pixel index and two precomputed weights.
+#include <algorithm>
+
+#include "df64.cuh"
 #include "mm_internal.cuh"
 
 namespace mm {
@@ -379,6 +382,137 @@ cudaError_t launch_point_win32(const PGroup* groups, int64_t n_groups, const int
   k_point_win32<<<(unsigned)n_groups, kWinThreads, kPointSmem, s>>>(groups, block_off, slot, slot_pix, ang2, u,
                                                                       u_stride, nrhs, done, done_stride,
                                                                       reinterpret_cast<float4*>(y4), y_stride / 4);
+  return cudaGetLastError();
+}
+
+// ---- FP32 right-hand side input: t = G d rounded to FP32 (0 at flagged and excised samples) ----
+template <typename D>
+__global__ void k_d_to_t32(const int32_t* __restrict__ lpix, const D* __restrict__ d, int64_t N, int64_t d_stride,
+                           float* __restrict__ t, int64_t t_stride) {
+  const D* dr = d + blockIdx.y * d_stride;
+  float* tr = t + blockIdx.y * t_stride;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    __stcs(tr + i, (__ldg(lpix + i) >= 0) ? (float)__ldcs(dr + i) : 0.f);
+}
+
+cudaError_t launch_d_to_t32(const int32_t* lpix, const void* d, int d_is_fp32, int64_t N, int nrhs, float* t,
+                            int64_t t_stride, cudaStream_t s) {
+  if (N == 0 || nrhs <= 0) return cudaSuccess;
+  const int64_t g = std::min<int64_t>((N + 255) / 256, 16 * (int64_t)sm_count());
+  const dim3 grid((unsigned)g, nrhs);
+  if (d_is_fp32)
+    k_d_to_t32<float><<<grid, 256, 0, s>>>(lpix, reinterpret_cast<const float*>(d), N, N, t, t_stride);
+  else
+    k_d_to_t32<double><<<grid, 256, 0, s>>>(lpix, reinterpret_cast<const double*>(d), N, N, t, t_stride);
+  return cudaGetLastError();
+}
+
+// ---- the FP64-class (double-float) P^T over the windows ------------------------------------------
+// Each group's sums are 64-bit fixed-point integers in shared memory: integer shared-memory
+// atomics are native, and integer sums do not depend on the order of the additions.  The column's
+// u values are bounded by umax (the df64 N^-1 tiles record max |u|), the weights by 1 and a slot
+// receives at most 2^15 samples, so with 2^k, k = 45 - floor(log2 umax), a slot's sum stays below
+// 2^61 while one unit is about 2^-46 umax, under the double-float operator's own relative error.
+
+// round(f 2^k) as a 64-bit integer with integer instructions only (the FP32 -> 64-bit conversion
+// instruction runs on the FP64 pipe); zero and subnormal f give 0
+__device__ __forceinline__ long long fixed_of(float f, int k) {
+  const uint32_t b = __float_as_uint(f);
+  const int e = (int)((b >> 23) & 0xffu);
+  if (e == 0) return 0;
+  const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
+  const int sh = e - 150 + k;
+  long long v;
+  if (sh >= 0) v = m << min(sh, 39);
+  else if (sh > -40) v = (m + (1ll << (-sh - 1))) >> (-sh);
+  else v = 0;
+  return (b >> 31) ? -v : v;
+}
+__device__ __forceinline__ long long fixed_of(df v, int k) { return fixed_of(v.hi, k) + fixed_of(v.lo, k); }
+
+constexpr size_t kPointDfSmem = (size_t)3 * kAccStride * sizeof(unsigned long long);
+
+__global__ void __launch_bounds__(kWinThreads, 2) k_point_win_df(
+    const PGroup* __restrict__ groups, const int64_t* __restrict__ block_off,
+    const uint16_t* __restrict__ slot, const int32_t* __restrict__ slot_pix, const float4* __restrict__ wdf,
+    const float2* __restrict__ u, int64_t u_stride, const uint32_t* __restrict__ amax, int nrhs,
+    const int32_t* __restrict__ done, int done_stride, double* __restrict__ y4, int64_t y_stride) {
+  extern __shared__ unsigned long long acc64[];   // [3][kAccStride]
+  const PGroup G = groups[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const ChunkWalk cw = chunk_walk(G, lane);
+  const int n_pad = acc_index(G.n_slots);
+  for (int r = 0; r < nrhs; r++) {
+    if (done != nullptr && done[(int64_t)r * done_stride] != 0) continue;
+    const uint32_t ub = __ldg(amax + r);
+    if (ub == 0u) continue;   // u = 0: nothing to add
+    double* yr = y4 + r * y_stride;
+    if (ub >= 0x7f800000u) {   // a non-finite u: poison the outputs so the solver sees it
+      for (int k = threadIdx.x; k < G.n_slots; k += kWinThreads)
+        atomicAdd(yr + 4 * (int64_t)__ldg(slot_pix + G.slot_off + k), __longlong_as_double(0x7ff8000000000000ll));
+      continue;
+    }
+    const int e_u = (int)((ub >> 23) & 0xffu) - 127;   // umax in [2^e_u, 2^(e_u + 1)) (subnormal: e_u = -127)
+    const int ks = 45 - e_u;
+    const double unit = __longlong_as_double((long long)(1023 - ks) << 52);   // 2^-ks
+    const float2* ur = u + r * u_stride;
+    for (int k = threadIdx.x; k < n_pad; k += kWinThreads) {
+      acc64[k] = 0ull;
+      acc64[kAccStride + k] = 0ull;
+      acc64[2 * kAccStride + k] = 0ull;
+    }
+    __syncthreads();
+    auto add = [&](uint32_t sl, float4 w, float2 y2) {
+      if (sl == kNoSlot) return;
+      const df y = df_make(y2.x, y2.y);
+      const df cy = df_make(w.x, w.y) * y, sy = df_make(w.z, w.w) * y;
+      const int k = acc_index((int)sl);
+      atomicAdd(acc64 + k, (unsigned long long)fixed_of(y, ks));
+      atomicAdd(acc64 + kAccStride + k, (unsigned long long)fixed_of(cy, ks));
+      atomicAdd(acc64 + 2 * kAccStride + k, (unsigned long long)fixed_of(sy, ks));
+    };
+    const int n_it = (G.n_blk + cw.cpi - 1) / cw.cpi;
+    const int per = (n_it + kWarps - 1) / kWarps;
+    for (int it = warp * per; it < min(n_it, (warp + 1) * per); it++) {
+      const int c = it * cw.cpi + cw.sub;
+      if (c >= G.n_blk) continue;
+      visit_chunk(
+          G, block_off, c, cw,
+          [&](int64_t a0, int q) {
+            const int64_t i = a0 + 4 * (int64_t)q;
+            const uint2 s2 = __ldcs(reinterpret_cast<const uint2*>(slot + i));
+            add(s2.x & 0xFFFFu, __ldcs(wdf + i), __ldcs(ur + i));
+            add(s2.x >> 16, __ldcs(wdf + i + 1), __ldcs(ur + i + 1));
+            add(s2.y & 0xFFFFu, __ldcs(wdf + i + 2), __ldcs(ur + i + 2));
+            add(s2.y >> 16, __ldcs(wdf + i + 3), __ldcs(ur + i + 3));
+          },
+          [&](int64_t i) { add(__ldcs(slot + i), __ldcs(wdf + i), __ldcs(ur + i)); });
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < G.n_slots; k += kWinThreads) {
+      const int64_t p = __ldg(slot_pix + G.slot_off + k);
+      const int j = acc_index(k);
+      atomicAdd(yr + 4 * p, (double)(long long)acc64[j] * unit);
+      atomicAdd(yr + 4 * p + 1, (double)(long long)acc64[kAccStride + j] * unit);
+      atomicAdd(yr + 4 * p + 2, (double)(long long)acc64[2 * kAccStride + j] * unit);
+    }
+    __syncthreads();   // the next column clears the sums
+  }
+}
+
+cudaError_t launch_point_win_df(const PGroup* groups, int64_t n_groups, const int64_t* block_off,
+                                const uint16_t* slot, const int32_t* slot_pix, const float4* wdf,
+                                const float2* u, int64_t u_stride, const uint32_t* amax, int nrhs,
+                                const int32_t* done, int done_stride, double* y4, int64_t y_stride,
+                                cudaStream_t s) {
+  if (n_groups == 0 || nrhs <= 0) return cudaSuccess;
+  if (n_groups > 0x7fffffffLL || u_stride % 4 != 0 || y_stride % 4 != 0) return cudaErrorInvalidValue;
+  static cudaError_t st = cudaSuccess;
+  static bool set = false;
+  MM_TRY_CUDA(smem_limit_once(k_point_win_df, kPointDfSmem, st, set));
+  k_point_win_df<<<(unsigned)n_groups, kWinThreads, kPointDfSmem, s>>>(groups, block_off, slot, slot_pix, wdf, u,
+                                                                         u_stride, amax, nrhs, done, done_stride, y4,
+                                                                         y_stride);
   return cudaGetLastError();
 }
 

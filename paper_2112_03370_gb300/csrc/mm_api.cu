@@ -167,9 +167,13 @@ void free_plan(Plan* P) {
   dfree(P->map64_in); dfree(P->map64_out); dfree(P->td_a); dfree(P->td_b); dfree(P->t32);
   dfree(P->wdf); dfree(P->tabdf); dfree(P->twdf); dfree(P->tdf); dfree(P->mapdf);
   dfree(P->ang2); dfree(P->groups); dfree(P->slot); dfree(P->slot_pix); dfree(P->u32);
+  dfree(P->udf); dfree(P->amax);
+  dfree(P->tc_tiles); dfree(P->tc_tab); dfree(P->tc_scale); dfree(P->tc_err);
+  if (P->tc_bmat) { cudaFree(P->tc_bmat); P->tc_bmat = nullptr; }
   for (void*& b : P->stage) if (b) { cudaFree(b); b = nullptr; }
   for (cudaEvent_t& e : P->stage_ev) if (e) { cudaEventDestroy(e); e = nullptr; }
   if (P->copy_stream) cudaStreamDestroy(P->copy_stream);
+  if (P->tod_buf) cudaFree(P->tod_buf);
   free_cg(reinterpret_cast<CgState*>(P->cg));
   free_blk(reinterpret_cast<BlkState*>(P->blk));
   free_defl(reinterpret_cast<DeflState*>(P->defl));
@@ -302,8 +306,14 @@ int validate_desc(const mm_problem_desc* d) {
       d->precision != MM_FP32_DF64)
     return fail(MM_EINVAL, "bad precision");
   if (d->toeplitz_algo != MM_TPLZ_AUTO && d->toeplitz_algo != MM_TPLZ_FFT &&
-      d->toeplitz_algo != MM_TPLZ_DIRECT)
+      d->toeplitz_algo != MM_TPLZ_GEMM && d->toeplitz_algo != MM_TPLZ_DIRECT)
     return fail(MM_EINVAL, "bad toeplitz_algo");
+  if (d->toeplitz_algo == MM_TPLZ_GEMM) {
+    if (d->lambda > kTcMaxJ0 * 32)
+      return fail(MM_EINVAL, "MM_TPLZ_GEMM needs lambda <= " + std::to_string(kTcMaxJ0 * 32));
+    if (d->precision != MM_FP32 && d->precision != MM_FP32_DF64)
+      return fail(MM_EINVAL, "MM_TPLZ_GEMM runs the FP32 operators: use MM_FP32 or MM_FP32_DF64");
+  }
   return MM_OK;
 }
 
@@ -315,8 +325,9 @@ int validate_desc(const mm_problem_desc* d) {
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-// largest un-pointed FP32 buffer the split A-application may allocate (nrhs * N * 4 bytes)
-constexpr size_t kSplitTBytes = (size_t)24 << 30;
+// largest time-domain working set (t, and u = N^-1 t with pixel windows, for the columns of one
+// pass) the split A-applications may allocate per precision
+constexpr size_t kSplitTBytes = (size_t)48 << 30;
 
 // Plan-time scratch: freed when the plan build returns, on every path.
 struct Scratch {
@@ -337,17 +348,45 @@ struct Scratch {
   }
 };
 
+// FP32 segments of up to `steps` consecutive tiles (replacing previous ones: captured graphs
+// must be captured again)
+int build_segments(Plan* P, int steps, cudaStream_t s) {
+  BandTables bt;
+  bt.blk_tab = P->blk_tab;
+  bt.blk_scale = P->blk_scale;
+  std::vector<TileDesc> segs = make_tiles(P->block_off, bt, P->lambda, std::max(1, steps), fp32_max_halo_samples(),
+                                          &P->seg_halo);
+  if (P->segs) {
+    P->buf_gen++;
+    dfree(P->segs);
+  }
+  P->n_segs = (int64_t)segs.size();
+  P->segs_host = segs;
+  P->tile_steps = std::max(1, steps);
+  MM_TRY(dalloc(P, &P->segs, segs.size()));
+  MM_CUDA(cudaMemcpyAsync(P->segs, segs.data(), segs.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, s));
+  return MM_OK;
+}
+
 // Pixel windows of time-aligned detector groups for the FP32 operators (P and P^T of the FP32
 // A-application; Sect. 3.1 local pixel indexation applied per group of samples).  The detectors of
 // every stationary interval are taken in groups of up to kWinDets, over windows of W = 2^k samples
-// of relative time (about kWinSamples samples per group, W >= 32).  A group whose kept samples see
+// of relative time (about win_samples samples per group, W >= 32).  A group whose kept samples see
 // more than kWinCap distinct pixels is split, its window halved down to 32 samples and then its
 // detectors halved, until every group fits; then each group's pixel-sorted slot table and every
 // sample's slot are written.
 int build_windows(Plan* P, cudaStream_t s) {
   constexpr int kWinDets = 512;
-  constexpr int64_t kWinSamples = 32768;
+  const int64_t kWinSamples = P->win_samples;
   constexpr int kMinLogW = 5;
+  // a rebuild (autotuning) replaces the previous windows; captured graphs must be captured again
+  if (P->groups) {
+    P->buf_gen++;
+    dfree(P->groups);
+    dfree(P->slot);
+    dfree(P->slot_pix);
+    P->n_groups = 0;
+  }
   const std::vector<int64_t>& off = P->block_off;
   for (int b = 0; b < P->n_blocks; b++)
     if (off[b + 1] - off[b] > ((int64_t)1 << 30)) return MM_OK;   // blocks that long keep the fused tiles
@@ -452,6 +491,8 @@ int build_plan(const mm_problem_desc* d, cudaStream_t us, Plan* P) {
   // P->precision: arithmetic of the CG-iteration operators; P->df64: FP64-class ones in df64
   P->precision = (d->precision == MM_FP32 || d->precision == MM_FP32_DF64) ? MM_FP32 : MM_FP64;
   P->algo = (d->toeplitz_algo == MM_TPLZ_DIRECT) ? MM_TPLZ_DIRECT : MM_TPLZ_FFT;
+  P->tc = P->precision == MM_FP32 && P->algo == MM_TPLZ_FFT && d->lambda <= kTcMaxJ0 * 32 &&
+          (d->toeplitz_algo == MM_TPLZ_GEMM || (d->toeplitz_algo == MM_TPLZ_AUTO && d->lambda <= kTcAutoLambda));
   P->df64 = (d->precision == MM_DF64 || d->precision == MM_FP32_DF64) && P->algo == MM_TPLZ_FFT;
   P->cond_max = d->cond_max > 0 ? d->cond_max : 1e3;
   const int nb = P->n_blocks, lam = P->lambda;
@@ -530,8 +571,8 @@ int build_plan(const mm_problem_desc* d, cudaStream_t us, Plan* P) {
   MM_TRY(dalloc(P, &P->w64, P->N));
   MM_TRY(dalloc(P, &P->w32, P->N));
   if (P->df64) MM_TRY(dalloc(P, &P->wdf, P->N));
-  const bool windows = P->precision == MM_FP32 && P->algo == MM_TPLZ_FFT;
-  if (windows) MM_TRY(dalloc(P, &P->ang2, P->N));
+  const bool windows = (P->precision == MM_FP32 || P->df64) && P->algo == MM_TPLZ_FFT;
+  if (P->precision == MM_FP32 && P->algo == MM_TPLZ_FFT) MM_TRY(dalloc(P, &P->ang2, P->N));
   MM_CUDA(launch_weights(P->psi, P->N, P->w64, P->w32, P->df64 ? P->wdf : nullptr, P->ang2, s));
   MM_CUDA(launch_bd_accum(pix, P->w64, P->block_off_dev, P->c0_blk, nb, P->N, B6, hits, s));
   MM_CUDA(launch_bd_finalize(B6, hits, P->n_pix, P->cond_max, keep, inv6, s));
@@ -569,6 +610,24 @@ int build_plan(const mm_problem_desc* d, cudaStream_t us, Plan* P) {
   MM_CUDA(launch_spectra(rows_d, P->n_tab, lam, H, costab_d, s));
   MM_CUDA(launch_pair_tables(H, P->n_tab, costab_d, P->tab64, P->tab32, s));
   MM_CUDA(launch_twiddles(P->tw64, P->tw32, costab_d, s));
+  if (P->tc) {   // tensor-core Toeplitz product: T_J images, tiles, per-block table and scale
+    unsigned char* bm = nullptr;
+    MM_TRY(dalloc(P, &bm, tc_bmat_bytes(P->n_tab)));
+    P->tc_bmat = bm;
+    MM_CUDA(launch_tc_bmat(rows_d, lam, P->n_tab, P->tc_bmat, s));
+    const std::vector<TcTile> tt = tc_tiles(P->block_off);
+    P->n_tc_tiles = (int64_t)tt.size();
+    MM_TRY(dalloc(P, &P->tc_tiles, tt.size()));
+    MM_TRY(dalloc(P, &P->tc_tab, nb));
+    MM_TRY(dalloc(P, &P->tc_scale, nb));
+    MM_TRY(dalloc(P, &P->tc_err, 1));
+    std::vector<float> scf(bt.blk_scale.begin(), bt.blk_scale.end());
+    MM_CUDA(cudaMemcpyAsync(P->tc_tiles, tt.data(), tt.size() * sizeof(TcTile), cudaMemcpyHostToDevice, s));
+    MM_CUDA(cudaMemcpyAsync(P->tc_tab, bt.blk_tab.data(), nb * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    MM_CUDA(cudaMemcpyAsync(P->tc_scale, scf.data(), nb * sizeof(float), cudaMemcpyHostToDevice, s));
+    MM_CUDA(cudaMemsetAsync(P->tc_err, 0, sizeof(int32_t), s));
+    MM_CUDA(cudaStreamSynchronize(s));   // host vectors go out of scope
+  }
   if (P->df64) {
     MM_TRY(dalloc(P, &P->tabdf, (size_t)P->n_tab * kM));
     MM_TRY(dalloc(P, &P->twdf, kM));
@@ -582,15 +641,12 @@ int build_plan(const mm_problem_desc* d, cudaStream_t us, Plan* P) {
   P->n_tiles = (int64_t)tiles.size();
   MM_TRY(dalloc(P, &P->tiles, tiles.size()));
   MM_CUDA(cudaMemcpyAsync(P->tiles, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, s));
+  P->blk_tab = bt.blk_tab;
+  P->blk_scale = bt.blk_scale;
   // FP32 segments: enough of them to keep every SM busy (about 8 per SM), at most 16 tiles each
   const int64_t steps = d->tile_steps > 0 ? d->tile_steps
-                                           : std::max<int64_t>(1, std::min<int64_t>(16, P->n_tiles / (8 * 152)));
-  std::vector<TileDesc> segs = make_tiles(P->block_off, bt, lam, (int)steps, fp32_max_halo_samples(),
-                                          &P->seg_halo);
-  P->n_segs = (int64_t)segs.size();
-  P->segs_host = segs;
-  MM_TRY(dalloc(P, &P->segs, segs.size()));
-  MM_CUDA(cudaMemcpyAsync(P->segs, segs.data(), segs.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, s));
+                                           : std::max<int64_t>(1, std::min<int64_t>(16, P->n_tiles / (8 * sm_count())));
+  MM_TRY(build_segments(P, (int)steps, s));
   MM_CUDA(cudaStreamSynchronize(s));
 
   // the band's symbol sampled on the tile's circulant must be positive (A is then SPD)
@@ -648,7 +704,7 @@ TileArgs base_args(const Plan* P, bool fp32) {
 // column starts 16-byte aligned), and how many columns one pass of it holds
 int64_t df_stride(const Plan* P) { return (P->N + 3) / 4 * 4; }
 int df_cols(const Plan* P, int nrhs) {
-  const int64_t per = df_stride(P) * (int64_t)sizeof(float2);
+  const int64_t per = df_stride(P) * (int64_t)sizeof(float2) * (P->groups && !P->tmpl ? 2 : 1);
   const int64_t k = std::max<int64_t>(1, (int64_t)kSplitTBytes / per);
   return (int)std::min<int64_t>(nrhs, k);
 }
@@ -676,12 +732,39 @@ int ensure_mapdf(Plan* P, int ncols) {
   }
   return MM_OK;
 }
+// N^-1 t of the windowed df64 operator and the per-column max |u| (allocated outside graph capture)
+int ensure_udf(Plan* P, int ncols) {
+  const size_t t_elems = (size_t)ncols * (size_t)df_stride(P);
+  if (P->udf_cap < t_elems) {
+    P->buf_gen++;
+    dfree(P->udf);
+    P->udf_cap = 0;
+    MM_TRY(dalloc(P, &P->udf, t_elems));
+    P->udf_cap = t_elems;
+  }
+  if (P->amax_cap < (size_t)ncols) {
+    P->buf_gen++;
+    dfree(P->amax);
+    P->amax_cap = 0;
+    MM_TRY(dalloc(P, &P->amax, (size_t)ncols));
+    P->amax_cap = (size_t)ncols;
+  }
+  return MM_OK;
+}
+
 // df64 working buffers of the df64 Toeplitz operator for nrhs columns
 int ensure_df(Plan* P, int nrhs) {
   if (P->tmpl) return ensure_mapdf(P, nrhs);
   if (!P->df64) return MM_OK;
   MM_TRY(ensure_tdf(P, df_cols(P, nrhs)));
+  if (P->groups) MM_TRY(ensure_udf(P, df_cols(P, nrhs)));
   return ensure_mapdf(P, df_cols(P, nrhs));
+}
+
+bool df_ready(const Plan* P, int nrhs) {
+  const int k = df_cols(P, nrhs);
+  return P->tdf_cap >= (size_t)k * df_stride(P) && P->mapdf_cap >= (size_t)k * P->n_obs * 2 &&
+         (!P->groups || (P->udf_cap >= (size_t)k * df_stride(P) && P->amax_cap >= (size_t)k));
 }
 
 TileArgs df_args(const Plan* P) {
@@ -694,14 +777,44 @@ TileArgs df_args(const Plan* P) {
   return a;
 }
 
+// y4 (FP64 map [g][n_obs][4], accumulated) += P^T N^-1 of the g df64 columns in P->tdf: with pixel
+// windows, u = N^-1 t into P->udf, then P^T over the windows; otherwise the tiles scatter P^T
+int df_ninv_point(Plan* P, int g, const int32_t* done, int done_stride, double* y4, cudaStream_t s) {
+  TileArgs a = df_args(P);
+  a.nrhs = g;
+  a.x = P->tdf;
+  a.done = done;
+  a.done_stride = done_stride;
+  if (!P->groups) {
+    a.y = y4;
+    MM_CUDA(launch_tiles_df(a, s));
+    return MM_OK;
+  }
+  MM_CUDA(cudaMemsetAsync(P->amax, 0, (size_t)g * sizeof(uint32_t), s));
+  a.y = P->udf;
+  a.y_stride = df_stride(P);
+  a.amax = P->amax;
+  MM_CUDA(launch_ninv_df(a, s));
+  MM_CUDA(launch_point_win_df(P->groups, P->n_groups, P->block_off_dev, P->slot, P->slot_pix, P->wdf, P->udf,
+                              df_stride(P), P->amax, g, done, done_stride, y4, P->n_obs * 4, s));
+  return MM_OK;
+}
+
 bool capturing(cudaStream_t s) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
 }
 
-// y4 (accumulated, pre-zeroed by the caller) += A x4 with the FP64-class operators, [nrhs][n_obs][4]
+// TOD of a solve that evaluates its residuals from the data: d [nrhs][N] device, float32 or float64
+struct TodSrc {
+  const void* d;
+  int d_is_fp32;
+};
+
+// y4 (accumulated, pre-zeroed by the caller) += A x4 with the FP64-class operators, [nrhs][n_obs][4].
+// With tod (double-float plans with pixel windows): y4 += P^T N^-1 (P x - G d) = A x - b instead.
 int apply64_internal(Plan* P, const double* x4, double* y4, int nrhs, cudaStream_t s,
-                     const int32_t* done = nullptr, int done_stride = 0) {
+                     const int32_t* done = nullptr, int done_stride = 0, const TodSrc* tod = nullptr) {
   if (P->tmpl) {   // template map-making: P^T F_T P in one fused df64 kernel, from the df64 map
     const TmplState* ts = reinterpret_cast<const TmplState*>(P->tmpl);
     const size_t m_elems = (size_t)nrhs * P->n_obs * 2;
@@ -715,7 +828,7 @@ int apply64_internal(Plan* P, const double* x4, double* y4, int nrhs, cudaStream
   }
   if (P->df64) {
     const int k = df_cols(P, nrhs);
-    if (capturing(s) && (P->tdf_cap < (size_t)k * df_stride(P) || P->mapdf_cap < (size_t)k * P->n_obs * 2))
+    if (capturing(s) && !df_ready(P, nrhs))
       return fail(MM_EINVAL, "df64 buffers must be allocated before graph capture");
     MM_TRY(ensure_df(P, nrhs));
     for (int r0 = 0; r0 < nrhs; r0 += k) {
@@ -724,13 +837,12 @@ int apply64_internal(Plan* P, const double* x4, double* y4, int nrhs, cudaStream
       MM_CUDA(launch_map_to_df(x4 + (size_t)r0 * P->n_obs * 4, (int64_t)g * P->n_obs, P->mapdf, s));
       MM_CUDA(launch_unpoint_df(P->lpix, P->wdf, P->N, P->mapdf, P->n_obs, g, dn, done_stride, P->tdf,
                                 df_stride(P), s));
-      TileArgs a = df_args(P);
-      a.nrhs = g;
-      a.x = P->tdf;
-      a.y = y4 + (size_t)r0 * P->n_obs * 4;
-      a.done = dn;
-      a.done_stride = done_stride;
-      MM_CUDA(launch_tiles_df(a, s));
+      if (tod) {
+        const size_t esz = tod->d_is_fp32 ? sizeof(float) : sizeof(double);
+        MM_CUDA(launch_sub_d_df(P->lpix, reinterpret_cast<const char*>(tod->d) + (size_t)r0 * P->N * esz,
+                                tod->d_is_fp32, P->N, g, P->tdf, df_stride(P), s));
+      }
+      MM_TRY(df_ninv_point(P, g, dn, done_stride, y4 + (size_t)r0 * P->n_obs * 4, s));
     }
     return MM_OK;
   }
@@ -759,15 +871,42 @@ int apply64_internal(Plan* P, const double* x4, double* y4, int nrhs, cudaStream
 // plan-owned un-pointed buffer of the split FP32 A-application (allocated outside graph capture)
 int64_t t32_stride(const Plan* P) { return (P->N + 3) / 4 * 4; }
 
-// The split FP32 A-application keeps t = P x (and, with pixel windows, u = N^-1 t) for nrhs
-// columns; beyond kSplitTBytes the fused tiles run instead.
-bool split32_fits(const Plan* P, int nrhs) {
-  return (size_t)nrhs * (size_t)t32_stride(P) * sizeof(float) * (P->groups ? 2 : 1) <= kSplitTBytes;
+// u = N^-1 t for g FP32 columns (t, u [g][ts]): tensor-core GEMM tiles on MM_TPLZ_GEMM plans,
+// overlap-save FFT segments otherwise
+int ninv32(Plan* P, const float* t, float* u, int64_t ts, int g, const int32_t* done, int done_stride,
+           cudaStream_t s) {
+  if (P->tc) {
+    MM_CUDA(launch_tplz_tc(P->tc_tiles, P->n_tc_tiles, P->block_off_dev, P->tc_tab, P->tc_scale, P->tc_bmat,
+                           P->lambda, t, ts, u, ts, g, done, done_stride, P->tc_err, s));
+    return MM_OK;
+  }
+  TileArgs a = base_args(P, true);
+  a.tiles = P->segs;
+  a.n_tiles = P->n_segs;
+  a.nrhs = g;
+  a.x = t;
+  a.x_stride = ts;
+  a.y = u;
+  a.y_stride = ts;
+  a.done = done;
+  a.done_stride = done_stride;
+  MM_CUDA(launch_tiles_fp32(MODE_NINV_T, a, P->seg_halo, s));
+  return MM_OK;
+}
+
+// The split FP32 A-application keeps t = P x (and, with pixel windows, u = N^-1 t) for the
+// columns of one pass; a pass holds as many columns as fit in kSplitTBytes (at least one), and
+// more columns run in several passes.  Only when a single column does not fit do the fused tiles
+// run instead.
+int split32_cols(const Plan* P, int nrhs) {
+  const size_t per = (size_t)t32_stride(P) * sizeof(float) * (P->groups ? 2 : 1);
+  return (int)std::min<size_t>((size_t)nrhs, kSplitTBytes / per);
 }
 
 int ensure_t32(Plan* P, int nrhs) {
-  if (!split32_fits(P, nrhs)) return MM_OK;
-  const size_t t_elems = (size_t)nrhs * (size_t)t32_stride(P);
+  const int k = split32_cols(P, nrhs);
+  if (k == 0) return MM_OK;
+  const size_t t_elems = (size_t)k * (size_t)t32_stride(P);
   if (P->t32_cap < t_elems) {
     dfree(P->t32);
     P->t32_cap = 0;
@@ -807,24 +946,32 @@ int apply32_internal(Plan* P, const float* x32, float* y32, int nrhs, cudaStream
     if (mid2) MM_CUDA(cudaEventRecord(mid2, s));
     return MM_OK;
   }
-  if (split32_fits(P, nrhs)) {
+  const int kc = split32_cols(P, nrhs);
+  if (kc > 0 && P->groups) {
+    if (capturing(s) && P->u32_cap < (size_t)kc * t32_stride(P))
+      return fail(MM_EINVAL, "FP32 buffers must be allocated before graph capture");
     MM_TRY(ensure_t32(P, nrhs));
     const int64_t ts = t32_stride(P);
-    if (P->groups) {
-      // P over the pixel windows, y = N^-1 t on the segments, P^T over the windows
-      MM_CUDA(launch_unpoint_win32(P->groups, P->n_groups, P->block_off_dev, P->slot, P->slot_pix, P->ang2, x32,
-                                   P->n_obs * 4, nrhs, done, done_stride, P->t32, ts, s));
-      if (mid) MM_CUDA(cudaEventRecord(mid, s));
-      a.x = P->t32;
-      a.x_stride = ts;
-      a.y = P->u32;
-      a.y_stride = ts;
-      MM_CUDA(launch_tiles_fp32(MODE_NINV_T, a, P->seg_halo, s));
-      if (mid2) MM_CUDA(cudaEventRecord(mid2, s));
+    const int64_t ms = P->n_obs * 4;
+    // P over the pixel windows, u = N^-1 t on the segments, P^T over the windows; kc columns per
+    // pass (the window kernels read a group's pointing once per pass and reuse it from L2 for
+    // every column of the pass)
+    for (int r0 = 0; r0 < nrhs; r0 += kc) {
+      const int g = std::min(kc, nrhs - r0);
+      const int32_t* dn = done ? done + (int64_t)r0 * done_stride : nullptr;
+      MM_CUDA(launch_unpoint_win32(P->groups, P->n_groups, P->block_off_dev, P->slot, P->slot_pix, P->ang2,
+                                   x32 + (size_t)r0 * ms, ms, g, dn, done_stride, P->t32, ts, s));
+      if (mid && r0 == 0) MM_CUDA(cudaEventRecord(mid, s));
+      MM_TRY(ninv32(P, P->t32, P->u32, ts, g, dn, done_stride, s));
+      if (mid2 && r0 + kc >= nrhs) MM_CUDA(cudaEventRecord(mid2, s));
       MM_CUDA(launch_point_win32(P->groups, P->n_groups, P->block_off_dev, P->slot, P->slot_pix, P->ang2, P->u32,
-                                 ts, nrhs, done, done_stride, y32, P->n_obs * 4, s));
-      return MM_OK;
+                                 ts, g, dn, done_stride, y32 + (size_t)r0 * ms, ms, s));
     }
+    return MM_OK;
+  }
+  if (kc >= nrhs) {
+    MM_TRY(ensure_t32(P, nrhs));
+    const int64_t ts = t32_stride(P);
     // un-point first at full occupancy, then the tiles stream t and scatter P^T themselves
     MM_CUDA(launch_unpoint32(P->lpix, P->w32, P->N, x32, P->n_obs * 4, nrhs, done, done_stride, P->t32, ts, s));
     if (mid) MM_CUDA(cudaEventRecord(mid, s));
@@ -839,6 +986,28 @@ int apply32_internal(Plan* P, const float* x32, float* y32, int nrhs, cudaStream
     MM_CUDA(launch_tiles_fp32(MODE_APPLY, a, P->seg_halo, s));
     if (mid2) MM_CUDA(cudaEventRecord(mid2, s));
   }
+  return MM_OK;
+}
+
+// b4 [nrhs][n_obs][4] (FP64) = P^T N^-1 G d with the FP32 operators over the pixel windows (the
+// start of a solve whose true residuals come from the TOD); needs an FP32 plan with windows
+int rhs32_internal(Plan* P, const void* d, int d_is_fp32, int nrhs, double* b4, cudaStream_t s) {
+  MM_TRY(ensure_maps(P, nrhs, true));
+  MM_TRY(ensure_t32(P, nrhs));
+  const int kc = split32_cols(P, nrhs);
+  if (kc == 0 || !P->groups) return fail(MM_EINVAL, "the FP32 right-hand side needs pixel windows");
+  const int64_t ts = t32_stride(P), ms = P->n_obs * 4;
+  const size_t esz = d_is_fp32 ? sizeof(float) : sizeof(double);
+  MM_CUDA(cudaMemsetAsync(P->map32_out, 0, (size_t)nrhs * ms * sizeof(float), s));
+  for (int r0 = 0; r0 < nrhs; r0 += kc) {
+    const int g = std::min(kc, nrhs - r0);
+    MM_CUDA(launch_d_to_t32(P->lpix, reinterpret_cast<const char*>(d) + (size_t)r0 * P->N * esz, d_is_fp32, P->N, g,
+                            P->t32, ts, s));
+    MM_TRY(ninv32(P, P->t32, P->u32, ts, g, nullptr, 0, s));
+    MM_CUDA(launch_point_win32(P->groups, P->n_groups, P->block_off_dev, P->slot, P->slot_pix, P->ang2, P->u32, ts,
+                               g, nullptr, 0, P->map32_out + (size_t)r0 * ms, ms, s));
+  }
+  MM_CUDA(launch_to64(P->map32_out, (int64_t)nrhs * P->n_obs, b4, s));
   return MM_OK;
 }
 
@@ -1359,7 +1528,7 @@ int mm_apply_Ninv(mm_plan_t plan, const double* t, double* y, void* stream) {
 }
 
 // Is p host memory (pinned or pageable) rather than device or managed memory?
-bool is_host_pointer(const void* p) {
+static bool is_host_pointer(const void* p) {
   cudaPointerAttributes at{};
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();   // older drivers report unregistered host memory as an error
@@ -1372,7 +1541,7 @@ constexpr size_t kStageBytes = (size_t)64 << 20;
 
 // Host TOD -> the df64 input buffer: chunks of one column go through two staging buffers, the
 // copy of chunk k + 1 (copy stream) overlapping the split of chunk k (stream s).
-int stage_d_to_df(Plan* P, const void* d, int d_is_fp32, int r0, int g, cudaStream_t s) {
+static int stage_d_to_df(Plan* P, const void* d, int d_is_fp32, int r0, int g, cudaStream_t s) {
   if (!P->stage[0]) {
     for (int i = 0; i < 2; i++) MM_TRY(dalloc(P, reinterpret_cast<unsigned char**>(&P->stage[i]), kStageBytes));
     P->stage_bytes = kStageBytes;
@@ -1428,11 +1597,7 @@ int mm_rhs(mm_plan_t plan, const void* d, int d_is_fp32, int nrhs, double* b, vo
         MM_CUDA(launch_tmpl_apply_df(ts->dev, P->n_blocks, P->wdf, nullptr, 0, P->tdf, df_stride(P), out,
                                      P->n_obs * 4, g, nullptr, 0, s));
       } else {
-        TileArgs a = df_args(P);
-        a.nrhs = g;
-        a.x = P->tdf;
-        a.y = out;
-        MM_CUDA(launch_tiles_df(a, s));
+        MM_TRY(df_ninv_point(P, g, nullptr, 0, out, s));
       }
     }
   } else if (P->algo == MM_TPLZ_DIRECT) {
@@ -1510,10 +1675,13 @@ int mm_precond(mm_plan_t plan, const double* r, double* z, int nrhs, void* strea
   return MM_OK;
 }
 
-int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_solve_opts* opts,
-                 mm_solve_info* info, void* stream) {
-  Plan* P = reinterpret_cast<Plan*>(plan);
-  if (!P || !b || !x || !opts || !info || nrhs <= 0) return fail(MM_EINVAL, "bad argument");
+// PCG (Algorithm 1) from b, or, with tod (FP32 iterations on a double-float plan with pixel
+// windows), from the TOD: b is formed with the FP32 operators and every true residual is
+// evaluated as P^T N^-1 G (d - P x) with the double-float operator, one FP64-class pass for the
+// right-hand side and the final check together.
+static int pcg_solve_impl(Plan* P, const double* b, const TodSrc* tod, double* x, int nrhs, const mm_solve_opts* opts,
+                   mm_solve_info* info, void* stream) {
+  if (!P || (!b && !tod) || !x || !opts || !info || nrhs <= 0) return fail(MM_EINVAL, "bad argument");
   if (!(opts->tol > 0.0) || opts->max_iter < 0) return fail(MM_EINVAL, "bad tol / max_iter");
   if (opts->precond != MM_PREC_BD && opts->precond != MM_PREC_2LVL_POST)
     return fail(MM_EINVAL, "unsupported preconditioner");
@@ -1547,7 +1715,11 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
   MM_CUDA(cudaEventRecord(ev, us));
   MM_CUDA(cudaStreamWaitEvent(s, ev, 0));
 
-  MM_CUDA(launch_pack3to4(b, P->n_obs, nrhs, c->b, s));
+  if (tod) {
+    MM_TRY(rhs32_internal(P, tod->d, tod->d_is_fp32, nrhs, c->b, s));
+  } else {
+    MM_CUDA(launch_pack3to4(b, P->n_obs, nrhs, c->b, s));
+  }
   MM_CUDA(launch_cg(CG_INIT, w, s));
   if (dwp) MM_CUDA(launch_defl_step(dw, w, s));
 
@@ -1620,13 +1792,20 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
     pending.clear();
     return MM_OK;
   };
+  // q before an FP64-class A x: 0, or b for the TOD form (q = b + P^T N^-1 (P x - G d), r = b - q)
+  auto clear_q = [&]() -> int {
+    const size_t bytes = (size_t)nrhs * P->n_obs * 4 * sizeof(double);
+    if (tod) MM_CUDA(cudaMemcpyAsync(c->q, c->b, bytes, cudaMemcpyDeviceToDevice, s));
+    else MM_CUDA(cudaMemsetAsync(c->q, 0, bytes, s));
+    return MM_OK;
+  };
   auto timed_apply64 = [&](const int32_t* done_flags) -> int {
     EvPair e{};
     if (profile) {
       MM_TRY(take_pair(1, &e));
       MM_CUDA(cudaEventRecord(e.a, s));
     }
-    MM_TRY(apply64_internal(P, c->x, c->q, nrhs, s, done_flags, done_flags ? kScalStrideInts : 0));
+    MM_TRY(apply64_internal(P, c->x, c->q, nrhs, s, done_flags, done_flags ? kScalStrideInts : 0, tod));
     if (profile) {
       MM_CUDA(cudaEventRecord(e.b, s));
       pending.push_back(e);
@@ -1655,8 +1834,8 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
       break;
     }
     if (need_rep) {
-      // residual replacement: r = b - A x with A in FP64
-      MM_CUDA(cudaMemsetAsync(c->q, 0, (size_t)nrhs * P->n_obs * 4 * sizeof(double), s));
+      // residual replacement: r = b - A x with A in FP64 (from the TOD: q = b + A x - b_exact)
+      MM_TRY(clear_q());
       MM_TRY(timed_apply64(reinterpret_cast<const int32_t*>(c->scal) + kDoneOffsetInts));
       MM_CUDA(launch_cg(CG_REPLACE, w, s));
       n_kernels += 1;
@@ -1702,7 +1881,7 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
   for (int r = 0; r < nrhs; r++)
     if (!(c->scal_host[r].done && c->scal_host[r].status == MM_OK)) need_true = true;
   if (need_true) {
-    MM_CUDA(cudaMemsetAsync(c->q, 0, (size_t)nrhs * P->n_obs * 4 * sizeof(double), s));
+    MM_TRY(clear_q());
     MM_TRY(timed_apply64(nullptr));
     MM_CUDA(launch_cg(CG_TRUE_RES, w, s));
     n_kernels += 1;
@@ -1712,6 +1891,11 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
   MM_CUDA(cudaMemcpyAsync(c->scal_host, c->scal, nrhs * sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
   MM_CUDA(cudaStreamSynchronize(s));
   MM_TRY(drain());
+  if (P->tc) {   // a timed-out tensor-core wait leaves its tile unwritten: the solve cannot be trusted
+    int32_t e = 0;
+    MM_CUDA(cudaMemcpy(&e, P->tc_err, sizeof(e), cudaMemcpyDeviceToHost));
+    if (e != 0) return fail(MM_ECUDA, "a tensor-core Toeplitz tile timed out waiting for its MMAs");
+  }
   for (EvPair& e : pool) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
@@ -1750,6 +1934,145 @@ int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_
   return worst;
 }
 
+// median device time (ms) of one FP32 A-application of `ncols` columns on the plan's stream
+static int time_apply32(Plan* P, int ncols, int reps, double* ms_out) {
+  cudaStream_t s = P->stream;
+  MM_TRY(ensure_maps(P, ncols, true));
+  MM_TRY(ensure_t32(P, ncols));
+  const size_t bytes = (size_t)ncols * P->n_obs * 4 * sizeof(float);
+  MM_CUDA(cudaMemsetAsync(P->map32_in, 0x3f, bytes, s));   // every value 0.747: timing only
+  MM_CUDA(cudaMemsetAsync(P->map32_out, 0, bytes, s));
+  MM_TRY(apply32_internal(P, P->map32_in, P->map32_out, ncols, s));   // warm-up
+  std::vector<float> t(reps);
+  cudaEvent_t a, b;
+  MM_CUDA(cudaEventCreate(&a));
+  MM_CUDA(cudaEventCreate(&b));
+  int st = MM_OK;
+  for (int k = 0; k < reps && st == MM_OK; k++) {
+    cudaEventRecord(a, s);
+    st = apply32_internal(P, P->map32_in, P->map32_out, ncols, s);
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    cudaEventElapsedTime(&t[k], a, b);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (st != MM_OK) return st;
+  MM_CUDA(cudaGetLastError());
+  std::sort(t.begin(), t.end());
+  *ms_out = t[reps / 2];
+  return MM_OK;
+}
+
+int mm_autotune(mm_plan_t plan, int max_width, mm_tune_info* out, void* stream) {
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  if (!P || !out || max_width < 0 || max_width > kMaxBlk) return fail(MM_EINVAL, "bad argument");
+  if (P->precision != MM_FP32 || P->algo != MM_TPLZ_FFT || !P->groups || P->tmpl)
+    return fail(MM_EINVAL, "mm_autotune tunes the FP32 operators of an FFT plan with pixel windows "
+                           "(MM_FP32 or MM_FP32_DF64, no templates)");
+  DeviceGuard g(P->device);
+  cudaEvent_t ev;
+  MM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  MM_CUDA(cudaEventRecord(ev, as_stream(stream)));
+  MM_CUDA(cudaStreamWaitEvent(P->stream, ev, 0));
+  cudaEventDestroy(ev);
+  std::memset(out, 0, sizeof(*out));
+  constexpr int kReps = 3;
+  // 1. tiles per segment: more tiles per CTA re-read less of the overlap, fewer leave SMs idle
+  const int steps_c[] = {1, 2, 4, 8, 16, 32};
+  double best = 1e300;
+  int best_steps = P->tile_steps;
+  for (int v : steps_c) {
+    if (v > 1 && P->n_tiles / v < sm_count()) continue;   // fewer segments than SMs
+    MM_TRY(build_segments(P, v, P->stream));
+    double ms = 0.0;
+    MM_TRY(time_apply32(P, 1, kReps, &ms));
+    out->steps_cand[out->n_steps] = v;
+    out->steps_ms[out->n_steps++] = ms;
+    if (ms < best) {
+      best = ms;
+      best_steps = v;
+    }
+  }
+  MM_TRY(build_segments(P, best_steps, P->stream));
+  // 2. samples per pixel-window group: larger groups repeat more pixels but stream shorter chunks
+  const int win_c[] = {8192, 16384, 32768, 65536};
+  best = 1e300;
+  int best_win = P->win_samples;
+  for (int v : win_c) {
+    P->win_samples = v;
+    MM_TRY(build_windows(P, P->stream));
+    double ms = 0.0;
+    MM_TRY(time_apply32(P, 1, kReps, &ms));
+    out->win_cand[out->n_win] = v;
+    out->win_ms[out->n_win++] = ms;
+    if (ms < best) {
+      best = ms;
+      best_win = v;
+    }
+  }
+  P->win_samples = best_win;
+  MM_TRY(build_windows(P, P->stream));
+  out->apply_ms = best;
+  // 3. block width: device time per column of a batched A X
+  double best_col = 1e300;
+  int best_w = 1;
+  for (int w = 1; w <= std::max(1, max_width); w *= 2) {
+    double ms = 0.0;
+    MM_TRY(time_apply32(P, w, 2, &ms));
+    out->width_cand[out->n_width] = w;
+    out->width_ms_per_col[out->n_width++] = ms / w;
+    if (ms / w <= best_col * 1.02) {   // ties go to the wider block (fewer block iterations)
+      best_col = std::min(best_col, ms / w);
+      best_w = w;
+    }
+  }
+  P->tuned_width = best_w;
+  out->tile_steps = best_steps;
+  out->win_samples = best_win;
+  out->block_width = best_w;
+  MM_CUDA(cudaStreamSynchronize(P->stream));
+  return MM_OK;
+}
+
+int mm_pcg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, const mm_solve_opts* opts,
+                 mm_solve_info* info, void* stream) {
+  return pcg_solve_impl(reinterpret_cast<Plan*>(plan), b, nullptr, x, nrhs, opts, info, stream);
+}
+
+int mm_solve_tod(mm_plan_t plan, const void* d, int d_is_fp32, double* x, int nrhs, const mm_solve_opts* opts,
+                 mm_solve_info* info, void* stream) {
+  Plan* P = reinterpret_cast<Plan*>(plan);
+  if (!P || !d || !x || !opts || !info || nrhs <= 0) return fail(MM_EINVAL, "bad argument");
+  if (is_host_pointer(d)) {   // the TOD is read at every residual: a device copy on the plan
+    DeviceGuard g(P->device);
+    const size_t bytes = (size_t)nrhs * P->N * (d_is_fp32 ? sizeof(float) : sizeof(double));
+    if (P->tod_cap < bytes) {
+      if (P->tod_buf) {
+        cudaFree(P->tod_buf);
+        P->bytes -= P->tod_cap;
+      }
+      P->tod_buf = nullptr;
+      P->tod_cap = 0;
+      unsigned char* buf = nullptr;
+      MM_TRY(dalloc(P, &buf, bytes));
+      P->tod_buf = buf;
+      P->tod_cap = bytes;
+    }
+    MM_CUDA(cudaMemcpyAsync(P->tod_buf, d, bytes, cudaMemcpyHostToDevice, as_stream(stream)));
+    d = P->tod_buf;
+  }
+  const bool tod_form = opts->precision == MM_FP32 && P->df64 && P->groups && !P->tmpl &&
+                        P->algo == MM_TPLZ_FFT && opts->precond == MM_PREC_BD;
+  if (tod_form) {
+    const TodSrc tod{d, d_is_fp32 ? 1 : 0};
+    return pcg_solve_impl(P, nullptr, &tod, x, nrhs, opts, info, stream);
+  }
+  // otherwise the FP64-class right-hand side (written into x, which the solve reads first) and PCG
+  MM_TRY(mm_rhs(plan, d, d_is_fp32, nrhs, x, stream));
+  return pcg_solve_impl(P, x, nullptr, x, nrhs, opts, info, stream);
+}
+
 int mm_block_cg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, int block_width,
                       const mm_solve_opts* opts, mm_solve_info* info, void* stream) {
   Plan* P = reinterpret_cast<Plan*>(plan);
@@ -1761,7 +2084,7 @@ int mm_block_cg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, int 
   if (P->algo == MM_TPLZ_DIRECT) return fail(MM_EINVAL, "block CG needs an FFT plan");
   DeviceGuard g(P->device);
   const auto t0 = std::chrono::steady_clock::now();
-  const int sw = block_width > 0 ? block_width : std::min(nrhs, kMaxBlk);
+  const int sw = block_width > 0 ? block_width : std::min(nrhs, P->tuned_width > 0 ? P->tuned_width : kMaxBlk);
   const bool fp32 = opts->precision == MM_FP32;
   const double tol2 = opts->tol * opts->tol;
   const int64_t n = P->n_obs;

@@ -82,6 +82,26 @@ struct PGroup {
   int64_t slot_off;  // first entry of the group's pixel-sorted slot table
 };
 
+// ---------------------------------------------------------------------------------------------
+// Tensor-core banded Toeplitz product (k_tc_toeplitz.cu): tiles of 128 rows x 32 samples of one
+// block, 3xTF32 tcgen05 MMAs over the 2 J0 + 1 row shifts, J0 = ceil(lambda / 32) <= kTcMaxJ0.
+// ---------------------------------------------------------------------------------------------
+constexpr int kTcMaxJ0 = 4;                 // lambda <= 128
+constexpr int kTcAutoLambda = -1;           // MM_TPLZ_AUTO picks the tensor cores up to this lambda
+struct TcTile {
+  int32_t blk;   // block
+  int32_t k0;    // first 32-sample row of the tile within the block
+};
+std::vector<TcTile> tc_tiles(const std::vector<int64_t>& block_off);
+size_t tc_bmat_bytes(int32_t n_tab);
+// T_J (hi, lo) of each band table in the kernel's shared-memory image layout
+cudaError_t launch_tc_bmat(const double* rows, int32_t lambda, int32_t n_tab, void* bmat, cudaStream_t s);
+// u = N^-1 t (FP32, 3xTF32 on the tensor cores), t and u [nrhs][stride]; err set on a timed-out wait
+cudaError_t launch_tplz_tc(const TcTile* tiles, int64_t n_tiles, const int64_t* block_off, const int32_t* blk_tab,
+                           const float* blk_scale, const void* bmat, int32_t lambda, const float* t,
+                           int64_t t_stride, float* u, int64_t u_stride, int nrhs, const int32_t* done,
+                           int done_stride, int32_t* err, cudaStream_t s);
+
 // Arguments of the fused Toeplitz-tile kernels.
 struct TileArgs {
   const TileDesc* tiles;
@@ -102,6 +122,7 @@ struct TileArgs {
   const int32_t* done;      // optional: skip the work of column r when done[r * done_stride] != 0
   int32_t done_stride;
   const ProbPtrs* probs;    // multi-problem launches: per-tile pointers (tile.prob), else null
+  uint32_t* amax;           // MODE_NINV_T df64 tiles (optional): per column, the bits of max |u|
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -146,6 +167,20 @@ struct Plan {
   TileDesc* segs = nullptr;            // FP32 segments (several tiles per descriptor)
   int64_t n_segs = 0;
   std::vector<TileDesc> segs_host;     // host copy (multi-problem launches)
+  std::vector<int32_t> blk_tab;        // host: spectrum table of each block
+  std::vector<double> blk_scale;       // host: band scale of each block against its table
+  int32_t tile_steps = 0;              // FP32 tiles walked per segment
+  int32_t win_samples = 32768;         // target samples per pixel-window group
+  int32_t tuned_width = 0;             // block width chosen by mm_autotune (0: not tuned)
+
+  // tensor-core Toeplitz product (MM_TPLZ_GEMM plans)
+  bool tc = false;                     // the FP32 N^-1 runs on the tensor cores
+  TcTile* tc_tiles = nullptr;          // [n_tc_tiles]
+  int64_t n_tc_tiles = 0;
+  void* tc_bmat = nullptr;             // T_J images of every table
+  int32_t* tc_tab = nullptr;           // [n_blocks] table of each block
+  float* tc_scale = nullptr;           // [n_blocks] band scale of each block
+  int32_t* tc_err = nullptr;           // set by a timed-out wait of the tensor-core kernel
   float* t32 = nullptr;                // [nrhs][N4] un-pointed FP32 input of the tiles (N4 = N
                                        // rounded up to 4)
   size_t t32_cap = 0;
@@ -159,6 +194,10 @@ struct Plan {
   int64_t n_slots_total = 0;
   float* u32 = nullptr;                // [nrhs][N4] FP32 u = N^-1 t of the windowed A-application
   size_t u32_cap = 0;
+  float2* udf = nullptr;               // [nrhs][N4] df64 u = N^-1 t of the windowed df64 operator
+  size_t udf_cap = 0;
+  uint32_t* amax = nullptr;            // [amax_cap] per column: bits of max |u| of the df64 tiles
+  size_t amax_cap = 0;
   double win_repeat = 0.0;             // kept samples per (group, pixel) pair: the P^T reduction factor
 
   // work buffers (grown on demand)
@@ -176,6 +215,8 @@ struct Plan {
   void* stage[2] = {nullptr, nullptr};
   size_t stage_bytes = 0;
   cudaStream_t copy_stream = nullptr;
+  void* tod_buf = nullptr;             // device copy of a host TOD handed to mm_solve_tod
+  size_t tod_cap = 0;
   cudaEvent_t stage_ev[4] = {nullptr, nullptr, nullptr, nullptr};   // copied[0..1], consumed[0..1]
 
   cudaStream_t stream = nullptr;       // plan-owned stream (graph capture)
@@ -262,6 +303,14 @@ cudaError_t launch_unpoint_win32(const PGroup* groups, int64_t n_groups, const i
                                  const uint16_t* slot, const int32_t* slot_pix, const float* psi,
                                  const float* x4, int64_t x_stride, int nrhs, const int32_t* done,
                                  int done_stride, float* t, int64_t t_stride, cudaStream_t s);
+// y4 [nrhs][y_stride] (FP64 map) += P^T u for df64 u ((hi, lo) pairs [nrhs][u_stride]) over the
+// windows: per group, 64-bit fixed-point sums in shared memory scaled by amax[r] (bits of the
+// column's max |u|), then one FP64 atomic per pixel and component
+cudaError_t launch_point_win_df(const PGroup* groups, int64_t n_groups, const int64_t* block_off,
+                                const uint16_t* slot, const int32_t* slot_pix, const float4* wdf,
+                                const float2* u, int64_t u_stride, const uint32_t* amax, int nrhs,
+                                const int32_t* done, int done_stride, double* y4, int64_t y_stride,
+                                cudaStream_t s);
 // y4 [nrhs][y_stride] += P^T u (FP32) over the windows, u [nrhs][u_stride]
 cudaError_t launch_point_win32(const PGroup* groups, int64_t n_groups, const int64_t* block_off,
                                const uint16_t* slot, const int32_t* slot_pix, const float* psi,
@@ -271,6 +320,8 @@ cudaError_t launch_point_win32(const PGroup* groups, int64_t n_groups, const int
 int sm_count();
 // df64 tiles and their data preparation (k_df64.cu)
 cudaError_t launch_tiles_df(const TileArgs& a, cudaStream_t s);
+// df64 u = N^-1 t (pairs in, pairs out), per-column max |u| into a.amax
+cudaError_t launch_ninv_df(const TileArgs& a, cudaStream_t s);
 cudaError_t launch_weights_df(const float* psi, int64_t N, float4* wdf, cudaStream_t s);
 cudaError_t launch_c64_to_df(const double2* in, int64_t n, float4* out, cudaStream_t s);
 cudaError_t launch_map_to_df(const double* m4, int64_t n_pix4, float4* out, cudaStream_t s);
@@ -279,6 +330,12 @@ cudaError_t launch_unpoint_df(const int32_t* lpix, const float4* wdf, int64_t N,
                               int64_t t_stride, cudaStream_t s);
 cudaError_t launch_d_to_df(const int32_t* lpix, const void* d, int d_is_fp32, int64_t N, int nrhs,
                            float2* t, int64_t t_stride, cudaStream_t s);
+// t -= G d in df64 (t [nrhs][t_stride] pairs, d [nrhs][N])
+cudaError_t launch_sub_d_df(const int32_t* lpix, const void* d, int d_is_fp32, int64_t N, int nrhs, float2* t,
+                            int64_t t_stride, cudaStream_t s);
+// t [nrhs][t_stride] = G d rounded to FP32
+cudaError_t launch_d_to_t32(const int32_t* lpix, const void* d, int d_is_fp32, int64_t N, int nrhs, float* t,
+                            int64_t t_stride, cudaStream_t s);
 int tile_kernels_init();   // sets smem attributes once per process
 int fp32_max_halo_samples();   // largest halo the FP32 segment kernel can keep in shared memory
 

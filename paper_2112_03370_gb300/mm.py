@@ -29,7 +29,7 @@ EXPORTS = ("mm_plan", "mm_plan_query", "mm_plan_destroy", "mm_apply_P", "mm_appl
            "mm_apply_Ninv", "mm_rhs", "mm_apply_A", "mm_precond", "mm_pcg_solve", "mm_last_error",
            "mm_apply_A_noalloc", "mm_block_cg_solve", "mm_ecg_solve", "mm_deflation_build", "mm_deflation_build_apriori", "mm_deflation_get",
            "mm_deflation_apply", "mm_server_create", "mm_submit", "mm_poll", "mm_wait",
-           "mm_server_destroy", "mm_estimate_bands", "mm_templates_set")
+           "mm_server_destroy", "mm_estimate_bands", "mm_templates_set", "mm_solve_tod", "mm_autotune")
 
 
 class TemplatesDesc(ctypes.Structure):
@@ -64,6 +64,15 @@ class SolveInfo(ctypes.Structure):
                 ("t_unpoint32_ms", ctypes.c_double), ("t_point32_ms", ctypes.c_double)]
 
 
+class TuneInfo(ctypes.Structure):
+    _fields_ = [("tile_steps", ctypes.c_int32), ("win_samples", ctypes.c_int32), ("block_width", ctypes.c_int32),
+                ("n_steps", ctypes.c_int32), ("n_win", ctypes.c_int32), ("n_width", ctypes.c_int32),
+                ("steps_cand", ctypes.c_int32 * 8), ("steps_ms", ctypes.c_double * 8),
+                ("win_cand", ctypes.c_int32 * 8), ("win_ms", ctypes.c_double * 8),
+                ("width_cand", ctypes.c_int32 * 8), ("width_ms_per_col", ctypes.c_double * 8),
+                ("apply_ms", ctypes.c_double)]
+
+
 class MMError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
@@ -90,6 +99,8 @@ def _load():
                                  ctypes.POINTER(SolveInfo), vp]
     lib.mm_block_cg_solve.argtypes = [vp, vp, vp, i32, i32, ctypes.POINTER(SolveOpts),
                                       ctypes.POINTER(SolveInfo), vp]
+    lib.mm_solve_tod.argtypes = [vp, vp, i32, vp, i32, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
+    lib.mm_autotune.argtypes = [vp, i32, ctypes.POINTER(TuneInfo), vp]
     lib.mm_ecg_solve.argtypes = [vp, vp, vp, i32, i32, ctypes.POINTER(SolveOpts),
                                  ctypes.POINTER(SolveInfo), vp]
     lib.mm_deflation_build.argtypes = [vp, vp, i32, i32, vp]
@@ -280,6 +291,41 @@ def mm_pcg_solve(plan: Plan, b: torch.Tensor, x: torch.Tensor, tol: float = 1e-6
     if raise_on_error and code not in (MM_OK,):
         raise MMError(code, mm_last_error())
     return list(infos)
+
+
+def mm_solve_tod(plan: Plan, d: torch.Tensor, x: torch.Tensor, tol: float = 1e-6,
+                 max_iter: int = 10000, precision: int = MM_FP64, reliable_every: int = 0,
+                 check_every: int = 0, deadline_us: int = 0, profile: bool = False, stream=None,
+                 raise_on_error=True, precond: int = MM_PREC_BD):
+    """Solve the map-making problem from the TOD d ([nrhs, N] or [N], float64 or float32, CUDA or
+    CPU) into x ([nrhs, n_obs, 3] or [n_obs, 3]); returns a list of SolveInfo."""
+    if d.dtype not in (torch.float64, torch.float32):
+        raise TypeError("d must be float64 or float32")
+    if not d.is_contiguous():
+        raise ValueError("d must be contiguous")
+    _dev(x, torch.float64, "x")
+    nrhs = 1 if d.dim() == 1 else d.shape[0]
+    opts = SolveOpts(tol=tol, max_iter=max_iter, precond=precond, precision=precision,
+                     reliable_every=reliable_every, check_every=check_every,
+                     profile=1 if profile else 0, deadline_us=deadline_us)
+    infos = (SolveInfo * nrhs)()
+    code = _lib.mm_solve_tod(ctypes.c_void_p(plan.handle), _ptr(d), 1 if d.dtype == torch.float32 else 0, _ptr(x),
+                             nrhs, ctypes.byref(opts), infos, _stream_ptr(stream))
+    if raise_on_error and code not in (MM_OK,):
+        raise MMError(code, mm_last_error())
+    return list(infos)
+
+
+def mm_autotune(plan: Plan, max_width: int = 64, stream=None) -> dict:
+    """Time and keep the fastest FP32 A-application configuration of the plan; returns the choice and
+    every timing."""
+    t = TuneInfo()
+    _check(_lib.mm_autotune(ctypes.c_void_p(plan.handle), max_width, ctypes.byref(t), _stream_ptr(stream)))
+    return {"tile_steps": t.tile_steps, "win_samples": t.win_samples, "block_width": t.block_width,
+            "apply_ms": t.apply_ms,
+            "steps_ms": {t.steps_cand[i]: t.steps_ms[i] for i in range(t.n_steps)},
+            "win_ms": {t.win_cand[i]: t.win_ms[i] for i in range(t.n_win)},
+            "width_ms_per_col": {t.width_cand[i]: t.width_ms_per_col[i] for i in range(t.n_width)}}
 
 
 def mm_block_cg_solve(plan: Plan, b: torch.Tensor, x: torch.Tensor, block_width: int = 0,

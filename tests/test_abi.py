@@ -46,7 +46,7 @@ def test_struct_layouts_match_header(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = {"mm_problem_desc": m.ProblemDesc, "mm_solve_opts": m.SolveOpts,
-               "mm_solve_info": m.SolveInfo}
+               "mm_solve_info": m.SolveInfo, "mm_tune_info": m.TuneInfo}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mm.h"', "int main(void){"]
     for cname, cls in structs.items():
         lines.append(f'printf("%zu\\n", sizeof({cname}));')
