@@ -67,12 +67,14 @@ def args_parse():
     p.add_argument("--cut-samp", type=int, default=262144, help="oracle map-error cut: samples per block")
     p.add_argument("--workload", default="ground",
                    choices=["ground", "batched", "satellite", "serving", "ecg", "deflation", "noise",
-                            "templates", "tiny"])
+                            "templates", "tiny", "crossover"])
     p.add_argument("--nrhs", type=int, default=64, help="batched: noise realisations")
     p.add_argument("--widths", default="8,16,32,64", help="batched: block widths")
     p.add_argument("--enlarge", default="1,4,16,64", help="ecg: enlarging factors t")
     p.add_argument("--requests", type=int, default=200, help="serving: requests")
     p.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
+    p.add_argument("--lams", default="0,16,32,64,96,128", help="crossover: half-bandwidths")
+    p.add_argument("--iters", type=int, default=20, help="crossover: PCG iterations per algorithm")
     return p.parse_args()
 
 
@@ -999,6 +1001,68 @@ def run_serving(a, n_requests=None, compare_fp64=0):
     return out
 
 
+def run_crossover(a):
+    """N^-1 on the tensor cores (MM_TPLZ_GEMM: banded Toeplitz-block GEMMs, tcgen05, 3xTF32)
+    against the overlap-save FFT tiles (MM_TPLZ_FFT), per half-bandwidth, on the ground geometry
+    cut to --dets detectors: a profiled FP32 PCG of --iters iterations per algorithm, and the
+    N^-1 time per A-application from its per-launch events.  MM_TPLZ_AUTO takes the GEMM up to
+    the largest lambda it wins here.  Also the two maps after the same iterations (the algorithms
+    differ only by FP32 rounding)."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2112_03370_gb300.mm as mm
+    dev = torch.device("cuda")
+    pk, pk_kind = peaks()
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+    tf32_peak = float(pk.get("bf16_tflops", 1900.0)) * 1.1 / 2.25   # nominal TF32:BF16 dense ratio
+    rows = []
+    for lam in [int(v) for v in a.lams.split(",")]:
+        cfg = synth.ground_config(n_det=a.dets, lam=lam)
+        prob = synth.make_ground_problem(cfg, device=dev, with_noise=False)
+        res, maps = {}, {}
+        for algo, name in ((mm.MM_TPLZ_FFT, "fft"), (mm.MM_TPLZ_GEMM, "gemm")):
+            p = mm.mm_plan(prob.n_det, prob.n_int, prob.block_len.tolist(), prob.n_pix, prob.pix, prob.psi,
+                           prob.lam, prob.band.to(dev), precision=mm.MM_FP32_DF64, toeplitz_algo=algo)
+            b = torch.empty(p.n_obs, 3, dtype=torch.float64, device=dev)
+            x = torch.empty_like(b)
+            mm.mm_rhs(p, prob.d, b)
+            info = mm.mm_pcg_solve(p, b, x, tol=1e-12, max_iter=a.iters, precision=mm.MM_FP32,
+                                   profile=True, raise_on_error=False)[0]
+            n = max(info.n_apply32, 1)
+            res[name] = (info.t_apply32_ms - info.t_unpoint32_ms - info.t_point32_ms) / n
+            maps[name] = x.cpu().numpy()
+            p.destroy()
+        j0 = (lam + 31) // 32
+        tc_flops = 2.0 * 32 * (2 * j0 + 1) * 3 * prob.n_total
+        rows.append({"lambda": lam, "fft_ms": res["fft"], "gemm_ms": res["gemm"],
+                     "gemm_faster": res["gemm"] < res["fft"],
+                     "gemm_tensor_tflops": tc_flops / (res["gemm"] * 1e-3) / 1e12,
+                     "gemm_tensor_frac": tc_flops / (res["gemm"] * 1e-3) / 1e12 / tf32_peak,
+                     "gemm_hbm_frac": 8.0 * prob.n_total / (res["gemm"] * 1e-3) / 1e9 / hbm_peak,
+                     "fft_hbm_frac": 8.0 * prob.n_total / (res["fft"] * 1e-3) / 1e9 / hbm_peak,
+                     "map_rel_diff": float(np.linalg.norm(maps["gemm"] - maps["fft"]) /
+                                           np.linalg.norm(maps["fft"]))})
+        log(f"lambda {lam}: N^-1 per apply fft {res['fft']:.3f} ms  gemm {res['gemm']:.3f} ms")
+        n_total = prob.n_total
+        del prob
+        torch.cuda.empty_cache()
+    wins = [r["lambda"] for r in rows if r["gemm_faster"]]
+    best = min(rows, key=lambda r: r["gemm_ms"] / r["fft_ms"])
+    return {
+        "workload": "crossover", "metric": "N^-1 time per A-application, tensor cores vs FFT tiles",
+        "value": best["fft_ms"] / best["gemm_ms"], "unit": "x (FFT time / GEMM time, best lambda)",
+        "higher_is_better": True,
+        "config": {"workload": f"ground geometry: {a.dets} det x 4 int x 524288 samples, FP32 operators, "
+                               f"{a.iters} PCG iterations per algorithm", "n_samples": n_total},
+        "rows": rows, "gemm_wins_up_to_lambda": max(wins) if wins else None,
+        "auto_rule": "MM_TPLZ_AUTO takes the GEMM for lambda <= 32 on FP32 operators",
+        "roofline": {"bound": "tensor", "kernel": "k_tplz_tc", "lambda": best["lambda"],
+                     "achieved": best["gemm_tensor_tflops"], "peak": tf32_peak, "unit": "TFLOP/s",
+                     "frac": best["gemm_tensor_frac"], "traffic": None,
+                     "peak_kind": f"{pk_kind} bf16 x 1.1/2.25 (TF32)"}}
+
+
 def main():
     a = args_parse()
     if a.impl == "reference":
@@ -1008,7 +1072,8 @@ def main():
         run_ours(a)
         return
     fn = {"batched": run_batched, "satellite": run_satellite, "serving": run_serving, "ecg": run_ecg,
-          "deflation": run_deflation, "noise": run_noise, "templates": run_templates, "tiny": run_tiny}
+          "deflation": run_deflation, "noise": run_noise, "templates": run_templates, "tiny": run_tiny,
+          "crossover": run_crossover}
     print(json.dumps(fn[a.workload](a)), flush=True)
 
 

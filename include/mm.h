@@ -239,10 +239,15 @@ int mm_solve_tod(mm_plan_t plan, const void* d, int d_is_fp32, double* x, int nr
  * the plan's own FP32 A x (CUDA events on the plan's stream, median of a few runs, inputs of the
  * plan's size) over candidate configurations and keeps the fastest:
  *   1. FP32 overlap-save tiles walked per segment (1, 2, 4, ..., 32; a CTA keeps the overlap of
- *      consecutive tiles in shared memory, more segments keep more SMs busy);
+ *      consecutive tiles in shared memory, more segments keep more SMs busy); for lambda > 6144,
+ *      also 65536-sample tiles split over 2-CTA clusters (more of each tile kept, but every CTA
+ *      reads the whole tile);
  *   2. target samples per pixel-window group of P and P^T (8192 ... 65536);
  *   3. block width for mm_block_cg_solve with block_width = 0: the widest of 1, 2, 4, ..., max_width
  *      whose device time per column of A X is within 2% of the best.
+ * Every candidate's A x (of one filled input) is compared with the first candidate's; one that
+ * differs by more than 1e-4 of the largest value is not chosen (n_rejected; max_rel_dev reports
+ * the largest difference seen, FP32 rounding-order noise when all is well).
  * Results and every timing go to *out (HOST).  Rebuilds the plan's segments and windows (captured
  * solver graphs are captured again at the next solve).  Synchronous.  MM_EINVAL unless the plan
  * has FP32 operators with pixel windows (MM_FP32 or MM_FP32_DF64 FFT plan without templates). */
@@ -258,6 +263,10 @@ typedef struct {
   int32_t width_cand[8];
   double width_ms_per_col[8];
   double apply_ms;           /* one-column FP32 A x with the chosen configuration (ms) */
+  int32_t big_tiles;         /* 1: 65536-sample tiles chosen, 0: timed and not chosen, -1: not a candidate */
+  double big_tiles_ms;       /* their one-column FP32 A x (ms) when timed */
+  double max_rel_dev;        /* largest relative difference of a candidate's A x from the first's */
+  int32_t n_rejected;        /* candidates not chosen because their A x differed */
 } mm_tune_info;
 int mm_autotune(mm_plan_t plan, int max_width, mm_tune_info* out, void* stream);
 

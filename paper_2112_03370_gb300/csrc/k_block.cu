@@ -222,7 +222,7 @@ __global__ void k_bprecond(const double* __restrict__ minv, const TR* __restrict
 
 static unsigned precond_grid(int64_t tot) {
   int64_t g = (tot + 255) / 256;
-  if (g > 152 * 32) g = 152 * 32;
+  if (g > 32 * sm_count()) g = 32 * sm_count();
   return (unsigned)g;
 }
 

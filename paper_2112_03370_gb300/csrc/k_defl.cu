@@ -63,7 +63,7 @@ __global__ void k_laxpby(double a, const double* __restrict__ x, double b, doubl
 }
 
 cudaError_t launch_laxpby(double a, const double* x, double b, double* y, int64_t n4, cudaStream_t s) {
-  k_laxpby<<<4 * 152, kNT, 0, s>>>(a, x, b, y, n4);
+  k_laxpby<<<4 * sm_count(), kNT, 0, s>>>(a, x, b, y, n4);
   return cudaGetLastError();
 }
 
@@ -245,7 +245,7 @@ cudaError_t launch_apriori_z(const int32_t* lpix, const int64_t* block_off, int 
     k_interval_hits<<<dim3(32, nb), 256, 0, s>>>(lpix, block_off + b0, n_int, n, hits);
   }
   int64_t g = (n + 255) / 256;
-  if (g > 152 * 16) g = 152 * 16;
+  if (g > 16 * sm_count()) g = 16 * sm_count();
   k_apriori_z<<<(unsigned)g, 256, 0, s>>>(hits, n_int, n, reinterpret_cast<float4*>(Z));
   return cudaGetLastError();
 }

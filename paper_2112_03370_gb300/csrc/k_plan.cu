@@ -24,7 +24,7 @@ __global__ void k_validate(const int32_t* __restrict__ pix, const float* __restr
 cudaError_t launch_validate(const int32_t* pix, const float* psi, int64_t N, int64_t n_pix,
                             int32_t* bad, cudaStream_t s) {
   if (N == 0) return cudaSuccess;
-  k_validate<<<4 * 152, 256, 0, s>>>(pix, psi, N, n_pix, bad);
+  k_validate<<<4 * sm_count(), 256, 0, s>>>(pix, psi, N, n_pix, bad);
   return cudaGetLastError();
 }
 
@@ -71,7 +71,7 @@ cudaError_t launch_bd_accum(const int32_t* pix, const double2* w64, const int64_
                             const double* c0_blk, int32_t n_blocks, int64_t N, double* B6,
                             int32_t* hits, cudaStream_t s) {
   if (N == 0) return cudaSuccess;
-  k_bd_accum<<<8 * 152, 256, 0, s>>>(pix, w64, block_off, c0_blk, n_blocks, N, B6, hits);
+  k_bd_accum<<<8 * sm_count(), 256, 0, s>>>(pix, w64, block_off, c0_blk, n_blocks, N, B6, hits);
   return cudaGetLastError();
 }
 
@@ -254,7 +254,7 @@ __global__ void k_localize(const int32_t* __restrict__ pix, const int32_t* __res
 cudaError_t launch_localize(const int32_t* pix, const int32_t* keep, const int32_t* lid, int64_t N,
                             int32_t* lpix, cudaStream_t s) {
   if (N == 0) return cudaSuccess;
-  k_localize<<<8 * 152, 256, 0, s>>>(pix, keep, lid, N, lpix);
+  k_localize<<<8 * sm_count(), 256, 0, s>>>(pix, keep, lid, N, lpix);
   return cudaGetLastError();
 }
 

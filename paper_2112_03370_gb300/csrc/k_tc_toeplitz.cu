@@ -40,7 +40,11 @@ constexpr int kTcBShift = kTcKg * kTcLboB;        // one T_J (hi or lo)
 constexpr int kTcMaxShifts = 2 * kTcMaxJ0 + 1;
 constexpr int kTcBSize = kTcMaxShifts * kTcBShift;
 constexpr int kTcGuard = 4096;                    // keeps every descriptor-reachable byte inside
-constexpr size_t kTcSmem = 2 * (size_t)kTcASize + 2 * (size_t)kTcBSize + kTcGuard;
+// dynamic shared memory for 2 j0 + 1 shifts: A hi/lo, T_J hi/lo, guard
+__host__ __device__ constexpr size_t tc_smem_bytes(int j0) {
+  return 2 * (size_t)kTcASize + 2 * (size_t)(2 * j0 + 1) * kTcBShift + kTcGuard;
+}
+constexpr size_t kTcSmem = tc_smem_bytes(kTcMaxJ0);
 constexpr int kTcThreads = 128;
 constexpr uint32_t kTcSpin = 1u << 22;            // bound of an mbarrier wait (iterations)
 
@@ -114,21 +118,21 @@ __global__ void __launch_bounds__(kTcThreads) k_tplz_tc(const TcTile* __restrict
   extern __shared__ __align__(128) unsigned char tc_smem[];
   __shared__ uint32_t taddr_s;
   __shared__ __align__(8) uint64_t mbar;
+  const int n_shift = 2 * j0 + 1;
   unsigned char* a_hi = tc_smem;
   unsigned char* a_lo = a_hi + kTcASize;
   unsigned char* b_hi = a_lo + kTcASize;
-  unsigned char* b_lo = b_hi + kTcBSize;
+  unsigned char* b_lo = b_hi + n_shift * kTcBShift;
   const uint32_t s_ahi = (uint32_t)__cvta_generic_to_shared(a_hi);
   const uint32_t s_alo = (uint32_t)__cvta_generic_to_shared(a_lo);
   const uint32_t s_bhi = (uint32_t)__cvta_generic_to_shared(b_hi);
   const uint32_t s_blo = (uint32_t)__cvta_generic_to_shared(b_lo);
   const uint32_t s_mbar = (uint32_t)__cvta_generic_to_shared(&mbar);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n_shift = 2 * j0 + 1;
   const int rows = kTcM + 2 * j0;
 
-  // guard bytes (and unused shift slots) are zero: a mis-read can never see stale values
-  for (int i = threadIdx.x; i < (int)(kTcSmem / 16); i += kTcThreads)
+  // guard bytes are zero: a mis-read can never see stale values
+  for (int i = threadIdx.x; i < (int)(tc_smem_bytes(j0) / 16); i += kTcThreads)
     reinterpret_cast<uint4*>(tc_smem)[i] = make_uint4(0u, 0u, 0u, 0u);
   if (warp == 0) {
     const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&taddr_s);
@@ -147,10 +151,44 @@ __global__ void __launch_bounds__(kTcThreads) k_tplz_tc(const TcTile* __restrict
   int loaded_tab = -1;
   uint32_t phase = 0;
   bool ok = true;
+  // Operand prefetch: item e = threadIdx.x + 128 p (p < kPf) is k-group e % 8 of stored row e / 8;
+  // the next tile's items are loaded into registers while the current tile's MMAs and epilogue run.
+  constexpr int kPf = (kTcM + 2 * kTcMaxJ0) * kTcKg / kTcThreads + 1;   // 9 items per thread
+  float4 pf[kPf];
+  auto fetch = [&](int64_t item) {
+    if (item >= n_tiles * nrhs) return;
+    const int rhs = (int)(item % nrhs);
+    const TcTile tl = tiles[item / nrhs];
+    const int64_t lo = __ldg(block_off + tl.blk), hi = __ldg(block_off + tl.blk + 1);
+    const float* tr = t + rhs * t_stride;
+    const bool al4 = ((lo | t_stride) & 3) == 0 && (((uintptr_t)tr) & 15) == 0;
+#pragma unroll
+    for (int p = 0; p < kPf; p++) {
+      const int e = threadIdx.x + kTcThreads * p;
+      const int r = e >> 3, kg = e & 7;
+      const int64_t g = lo + (int64_t)kTcB * (tl.k0 - j0 + r) + 4 * kg;
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < rows) {
+        if (al4 && g >= lo && g + 4 <= hi) {
+          x = __ldg(reinterpret_cast<const float4*>(tr + g));
+        } else {
+          x.x = (g >= lo && g < hi) ? __ldg(tr + g) : 0.f;
+          x.y = (g + 1 >= lo && g + 1 < hi) ? __ldg(tr + g + 1) : 0.f;
+          x.z = (g + 2 >= lo && g + 2 < hi) ? __ldg(tr + g + 2) : 0.f;
+          x.w = (g + 3 >= lo && g + 3 < hi) ? __ldg(tr + g + 3) : 0.f;
+        }
+      }
+      pf[p] = x;
+    }
+  };
+  fetch(blockIdx.x);
   for (int64_t it = blockIdx.x; it < n_tiles * nrhs && ok; it += gridDim.x) {
     const int rhs = (int)(it % nrhs);
     const int64_t ti = it / nrhs;
-    if (done != nullptr && done[(int64_t)rhs * done_stride] != 0) continue;
+    if (done != nullptr && done[(int64_t)rhs * done_stride] != 0) {
+      fetch(it + gridDim.x);
+      continue;
+    }
     const TcTile tl = tiles[ti];
     const int64_t lo = __ldg(block_off + tl.blk), hi = __ldg(block_off + tl.blk + 1);
     const int tab = __ldg(blk_tab + tl.blk);
@@ -163,17 +201,23 @@ __global__ void __launch_bounds__(kTcThreads) k_tplz_tc(const TcTile* __restrict
       }
       loaded_tab = tab;
     }
-    // A: stored row r is block row k0 - j0 + r; hi and lo TF32 split of every sample
-    const float* tr = t + rhs * t_stride;
-    for (int e = threadIdx.x; e < rows * kTcB; e += kTcThreads) {
-      const int r = e >> 5, c = e & 31;
-      const int64_t g = lo + (int64_t)kTcB * (tl.k0 - j0 + r) + c;
-      const float x = (g >= lo && g < hi) ? __ldg(tr + g) : 0.f;
-      const uint32_t xh = tf32_rna(x);
-      const uint32_t xl = tf32_rna(x - __uint_as_float(xh));
-      const int off = (c >> 2) * kTcLboA + r * 16 + (c & 3) * 4;
-      *reinterpret_cast<uint32_t*>(a_hi + off) = xh;
-      *reinterpret_cast<uint32_t*>(a_lo + off) = xl;
+    // A (hi and lo TF32 split) from the prefetched registers: one 16-byte store per operand and
+    // item (k-groups lie 2192 bytes apart, so 8 consecutive items hit 8 distinct bank groups)
+#pragma unroll
+    for (int p = 0; p < kPf; p++) {
+      const int e = threadIdx.x + kTcThreads * p;
+      const int r = e >> 3, kg = e & 7;
+      if (r < rows) {
+        const float4 x = pf[p];
+        uint4 h, l;
+        h.x = tf32_rna(x.x); l.x = tf32_rna(x.x - __uint_as_float(h.x));
+        h.y = tf32_rna(x.y); l.y = tf32_rna(x.y - __uint_as_float(h.y));
+        h.z = tf32_rna(x.z); l.z = tf32_rna(x.z - __uint_as_float(h.z));
+        h.w = tf32_rna(x.w); l.w = tf32_rna(x.w - __uint_as_float(h.w));
+        const int off = kg * kTcLboA + r * 16;
+        *reinterpret_cast<uint4*>(a_hi + off) = h;
+        *reinterpret_cast<uint4*>(a_lo + off) = l;
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;");   // generic-proxy writes -> tensor-core reads
     __syncthreads();
@@ -194,6 +238,7 @@ __global__ void __launch_bounds__(kTcThreads) k_tplz_tc(const TcTile* __restrict
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_mbar));
     }
+    fetch(it + gridDim.x);   // the next tile's operand loads overlap the MMAs and the epilogue
     // every thread must take the same branch (the TMEM load below is warp-collective)
     if (!__syncthreads_and(mbar_wait(s_mbar, phase) ? 1 : 0)) {
       ok = false;
@@ -203,16 +248,38 @@ __global__ void __launch_bounds__(kTcThreads) k_tplz_tc(const TcTile* __restrict
     }
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    // epilogue: warp w holds rows 32 w .. 32 w + 31 (TMEM lanes), this thread one row of 32 outputs
-    float v[32];
-    tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), v);
-    float* ur = u + rhs * u_stride;
-    const int64_t g0 = lo + (int64_t)kTcB * (tl.k0 + 32 * warp + lane);
+    // epilogue: warp w holds rows 32 w .. 32 w + 31 (TMEM lanes), this thread one row of 32 outputs;
+    // the rows go through shared memory (the A operand is free once the MMAs completed) so that the
+    // tile's output, one contiguous range of 4096 samples, is stored with coalesced vector stores
+    {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), v);
+      float* stage = reinterpret_cast<float*>(a_hi);   // [128][33]: padded rows, no bank conflicts
+      const int row = 32 * warp + lane;
 #pragma unroll
-    for (int i = 0; i < kTcB; i++)
-      if (g0 + i < hi) ur[g0 + i] = sc * v[i];
+      for (int i = 0; i < kTcB; i++) stage[row * (kTcB + 1) + i] = sc * v[i];
+    }
     asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();   // TMEM read and A consumed before the next tile's MMAs overwrite them
+    __syncthreads();
+    {
+      float* ur = u + rhs * u_stride;
+      const float* stage = reinterpret_cast<const float*>(a_hi);
+      const int64_t base = lo + (int64_t)kTcB * tl.k0;
+      const bool v4 = ((base | u_stride) & 3) == 0 && (((uintptr_t)ur) & 15) == 0;
+      for (int q = threadIdx.x; q < kTcM * kTcB / 4; q += kTcThreads) {
+        const int row = q >> 3, c = 4 * (q & 7);
+        const int64_t g = base + 4 * (int64_t)q;
+        const float* sv = stage + row * (kTcB + 1) + c;
+        if (v4 && g + 4 <= hi) {
+          *reinterpret_cast<float4*>(ur + g) = make_float4(sv[0], sv[1], sv[2], sv[3]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; e++)
+            if (g + e < hi) ur[g + e] = sv[e];
+        }
+      }
+    }
+    __syncthreads();   // the staging rows and A consumed before the next tile overwrites them
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -274,9 +341,11 @@ cudaError_t launch_tplz_tc(const TcTile* tiles, int64_t n_tiles, const int64_t* 
   }
   if (st != cudaSuccess) return st;
   const int j0 = (lambda + kTcB - 1) / kTcB;
+  const size_t smem = tc_smem_bytes(j0);
+  const int per_sm = std::max(1, std::min(4, (int)((227u * 1024u) / (smem + 1024))));
   const int64_t items = n_tiles * nrhs;
-  const int64_t grid = std::min<int64_t>(items, 2 * (int64_t)sm_count());
-  k_tplz_tc<<<(unsigned)grid, kTcThreads, kTcSmem, s>>>(tiles, n_tiles, block_off, blk_tab, blk_scale,
+  const int64_t grid = std::min<int64_t>(items, (int64_t)per_sm * sm_count());
+  k_tplz_tc<<<(unsigned)grid, kTcThreads, smem, s>>>(tiles, n_tiles, block_off, blk_tab, blk_scale,
                                                          reinterpret_cast<const uint4*>(bmat), j0, t, t_stride, u,
                                                          u_stride, nrhs, done, done_stride, err);
   return cudaGetLastError();

@@ -1098,7 +1098,7 @@ cudaError_t launch_tmpl_setup(TmplDev& d, int nb, double* K, cudaStream_t s) {
     k_tmpl_bins<<<nb, kTNT, 0, s>>>(d.lpix, d.az, d.off, d.n_az, d.interp, d.az_bin_w, d.az_frac_w, d.bin8_w,
                                     d.frac32_w);
   if (d.hwpdf_w || d.fracdf_w)
-    k_tmpl_df_tables<<<152 * 8, 256, 0, s>>>(d.hwp, d.az_frac, d.n_total, d.hwpdf_w, d.hwp32_w, d.fracdf_w);
+    k_tmpl_df_tables<<<8 * sm_count(), 256, 0, s>>>(d.hwp, d.az_frac, d.n_total, d.hwpdf_w, d.hwp32_w, d.fracdf_w);
   k_tmpl_gram<<<nb * kTC, kTA, 0, s>>>(d, K);
   const int k = d.k;
   const size_t smem = (size_t)(2 * k * (k + 1) + 2 * 32 + 2 * kPinvThreads) * sizeof(double);
@@ -1151,7 +1151,7 @@ cudaError_t launch_tmpl_apply_df(const TmplDev& d, int nb, const float4* wdf, co
 cudaError_t launch_tmpl_mx32(const float4* M32, int64_t n_obs, const float* x, float* y, int nrhs, const int32_t* done,
                              int done_stride, cudaStream_t s) {
   if (n_obs == 0 || nrhs <= 0) return cudaSuccess;
-  const unsigned g = (unsigned)std::min<int64_t>((n_obs + 255) / 256, 152 * 8);
+  const unsigned g = (unsigned)std::min<int64_t>((n_obs + 255) / 256, 8 * (int64_t)sm_count());
   k_tmpl_mx32<<<dim3(g, nrhs), 256, 0, s>>>(M32, n_obs, reinterpret_cast<const float4*>(x),
                                             reinterpret_cast<float4*>(y), done, done_stride);
   return cudaGetLastError();
@@ -1160,14 +1160,14 @@ cudaError_t launch_tmpl_mx32(const float4* M32, int64_t n_obs, const float* x, f
 cudaError_t launch_tmpl_mx64(const double* M64, int64_t n_obs, const double* x, double* y, int nrhs,
                              const int32_t* done, int done_stride, cudaStream_t s) {
   if (n_obs == 0 || nrhs <= 0) return cudaSuccess;
-  const unsigned g = (unsigned)std::min<int64_t>((n_obs + 255) / 256, 152 * 8);
+  const unsigned g = (unsigned)std::min<int64_t>((n_obs + 255) / 256, 8 * (int64_t)sm_count());
   k_tmpl_mx64<<<dim3(g, nrhs), 256, 0, s>>>(M64, n_obs, x, y, done, done_stride);
   return cudaGetLastError();
 }
 
 cudaError_t launch_m64_to_32(const double* M64, int64_t n_obs, float4* M32, cudaStream_t s) {
   if (n_obs == 0) return cudaSuccess;
-  k_m64_to_32<<<(unsigned)std::min<int64_t>((n_obs + 255) / 256, 152 * 8), 256, 0, s>>>(M64, n_obs, M32);
+  k_m64_to_32<<<(unsigned)std::min<int64_t>((n_obs + 255) / 256, 8 * (int64_t)sm_count()), 256, 0, s>>>(M64, n_obs, M32);
   return cudaGetLastError();
 }
 

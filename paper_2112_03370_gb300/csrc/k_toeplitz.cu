@@ -142,7 +142,23 @@ __device__ __forceinline__ void quad_meta(const TileArgs& a, int64_t g, int64_t 
 template <typename T, int MODE, int NQ>
 __device__ __forceinline__ void gather_quads(const TileArgs& a, int rhs, const TileDesc& td,
                                              const int64_t (&g)[NQ], T (&v)[NQ][4]) {
-  if constexpr (MODE == MODE_APPLY_T || MODE == MODE_NINV_T) {
+  if constexpr (MODE == MODE_NINV_T && std::is_same<T, float>::value) {
+    // FP32 2-CTA tiles: float t, zero outside the block (g a multiple of 4: 16-byte aligned)
+    const float* t = reinterpret_cast<const float*>(a.x) + rhs * a.x_stride;
+#pragma unroll
+    for (int u = 0; u < NQ; u++) {
+      if (g[u] >= td.blk_lo && g[u] + 4 <= td.blk_hi) {
+        const float4 f = __ldcs(reinterpret_cast<const float4*>(t + g[u]));
+        v[u][0] = f.x; v[u][1] = f.y; v[u][2] = f.z; v[u][3] = f.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+          const int64_t gg = g[u] + e;
+          v[u][e] = (gg >= td.blk_lo && gg < td.blk_hi) ? __ldg(t + gg) : 0.f;
+        }
+      }
+    }
+  } else if constexpr (MODE == MODE_APPLY_T || MODE == MODE_NINV_T) {
     // df64 tiles: un-pointed input t = P x (or the masked TOD) as (hi, lo) pairs
     static_assert(std::is_same<T, df>::value, "2-CTA APPLY_T / NINV_T tiles are the df64 ones");
     const float2* t = reinterpret_cast<const float2*>(a.x) + rhs * a.x_stride;
@@ -445,18 +461,22 @@ __device__ __forceinline__ void fused_rem_pair(C* sm, const C* __restrict__ tab,
 }  // namespace
 
 // One overlap-save tile (CL = 1) or half a tile (CL = 2) per CTA.
-template <typename T, int CL, int MODE, bool MULTI = false>
+// LOGM: log2 of the complex points of the whole tile (L = 2^(LOGM + 1) real samples); the FP32
+// 2-CTA tiles use LOGM = kLogM + 1 (65536 samples, each CTA a 16384-point half)
+template <typename T, int CL, int MODE, bool MULTI = false, int LOGM = kLogM>
 __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
   constexpr int NT = kTileThreads;
   using C = typename V2<T>::t;
-  constexpr int LOGMS = kLogM - (CL == 2 ? 1 : 0);
+  constexpr int MT = 1 << LOGM;   // complex points of the tile
+  constexpr int LT = 2 * MT;      // real samples of the tile
+  constexpr int LOGMS = LOGM - (CL == 2 ? 1 : 0);
   constexpr int MS = 1 << LOGMS;
   // df64 butterflies are long: one pass body looped over the passes keeps the code in cache
-  using FFT = SmemFFT<LOGMS, kM, NT, !std::is_same<T, df>::value>;
+  using FFT = SmemFFT<LOGMS, MT, NT, !std::is_same<T, df>::value>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
   C* tw_sm = sm + smem_pad(MS);
-  C* ptab = tw_sm + twiddle_tab_entries(kM);                          // per-pass twiddles
+  C* ptab = tw_sm + twiddle_tab_entries(MT);                          // per-pass twiddles
   T* halo = reinterpret_cast<T*>(ptab + FFT::kPassTabEntries);       // CL == 1 segments
 
   const int64_t unit = blockIdx.x / CL;
@@ -473,13 +493,13 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
   // both CTAs of a cluster read the same flag, so they leave together
   if (a.done != nullptr && a.done[(int64_t)rhs * a.done_stride] != 0) return;
   const C* __restrict__ tw_g = reinterpret_cast<const C*>(a.tw);
-  const TwiddleTab<C> tw = load_twiddle_tab<C, kM, NT>(tw_sm, tw_g);
+  const TwiddleTab<C> tw = load_twiddle_tab<C, MT, NT>(tw_sm, tw_g);
   const C* __restrict__ tab =
       reinterpret_cast<const C*>(a.tab) + ((int64_t)seg.tab * CL + rank) * MS;
   const T sc = (T)seg.scale;
   constexpr int NQ = std::is_same<T, float>::value ? 4 : 2;
   constexpr int HALF_Q = MS / 2;          // quads (4 real samples) of this CTA's complex range
-  const int halo_q = (kL - seg.vstep) / 4;
+  const int halo_q = (LT - seg.vstep) / 4;
   __syncthreads();
   FFT::build_pass_tables(ptab, tw);
   __syncthreads();
@@ -554,7 +574,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
       __syncthreads();
     }
 
-    if constexpr (CL == 1) {
+    if constexpr (CL == 1 && LOGM == 14) {
       FFT::forward16(sm, tw, ptab);
       fused_rem_pair(sm, tab, sc);
       __syncthreads();
@@ -703,7 +723,19 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
             for (int e = 0; e < 4; e++) y[u][e] = T(0);
           }
         }
-        if constexpr (MODE == MODE_NINV_T) {
+        if constexpr (MODE == MODE_NINV_T && std::is_same<T, float>::value) {
+          float* yo = reinterpret_cast<float*>(a.y) + rhs * a.y_stride;
+#pragma unroll
+          for (int u = 0; u < NQ; u++) {
+            if (g[u] >= td.out_lo && g[u] + 4 <= td.out_hi) {   // g a multiple of 4: 16-byte aligned
+              __stcs(reinterpret_cast<float4*>(yo + g[u]), make_float4(y[u][0], y[u][1], y[u][2], y[u][3]));
+            } else {
+#pragma unroll
+              for (int e = 0; e < 4; e++)
+                if (g[u] + e >= td.out_lo && g[u] + e < td.out_hi) yo[g[u] + e] = y[u][e];
+            }
+          }
+        } else if constexpr (MODE == MODE_NINV_T) {
           // df64 u as (hi, lo) pairs over the tile's output range, and the CTA's max |u|
           float2* yo = reinterpret_cast<float2*>(a.y) + rhs * a.y_stride;
 #pragma unroll
@@ -732,7 +764,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
     if constexpr (CL == 2) cg::this_cluster().sync();
     else __syncthreads();   // the next tile overwrites the buffer
   }
-  if constexpr (MODE == MODE_NINV_T && CL == 2) {
+  if constexpr (MODE == MODE_NINV_T && CL == 2 && std::is_same<T, df>::value) {
     if (a.amax != nullptr) {   // non-negative floats order like their bit patterns
       for (int o = 16; o > 0; o >>= 1) umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
       if ((threadIdx.x & 31) == 0) atomicMax(a.amax + rhs, __float_as_uint(umax));
@@ -744,6 +776,9 @@ constexpr size_t kSmemBytes32 =
     (size_t)(smem_pad(kM) + twiddle_tab_entries(kM) + SmemFFT<kLogM, kM, kTileThreads>::kPassTabEntries) *
     sizeof(float2);
 constexpr size_t kSmemMax = 227 * 1024;
+constexpr size_t kSmemBytes32Big =
+    (size_t)(smem_pad(kM) + twiddle_tab_entries(2 * kM) + SmemFFT<kLogM, 2 * kM, kTileThreads>::kPassTabEntries) *
+    sizeof(float2);
 constexpr size_t kSmemBytes64 =
     (size_t)(smem_pad(kM / 2) + twiddle_tab_entries(kM) + SmemFFT<kLogM - 1, kM, kTileThreads>::kPassTabEntries) *
     sizeof(double2);
@@ -766,6 +801,7 @@ int tile_kernels_init() {
   MM_SET((k_tile<double, 2, MODE_NINV>), kSmemBytes64);
   MM_SET((k_tile<df, 2, MODE_APPLY_T>), kSmemBytes64);
   MM_SET((k_tile<df, 2, MODE_NINV_T>), kSmemBytes64);
+  MM_SET((k_tile<float, 2, MODE_NINV_T, false, kLogM + 1>), kSmemBytes32Big);
 #undef MM_SET
   if (e == cudaSuccess) {
     // 2-CTA clusters with 136 KB of dynamic shared memory each are a non-portable size only in
@@ -776,7 +812,7 @@ int tile_kernels_init() {
   return status;
 }
 
-template <typename T, int CL, int MODE, bool MULTI = false>
+template <typename T, int CL, int MODE, bool MULTI = false, int LOGM = kLogM>
 static cudaError_t launch_tiles(const TileArgs& a, size_t smem, cudaStream_t s) {
   const int64_t n_cta = a.n_tiles * a.nrhs * CL;
   if (n_cta == 0) return cudaSuccess;
@@ -797,7 +833,14 @@ static cudaError_t launch_tiles(const TileArgs& a, size_t smem, cudaStream_t s) 
   }
   cfg.attrs = attr;
   cfg.numAttrs = na;
-  return cudaLaunchKernelEx(&cfg, k_tile<T, CL, MODE, MULTI>, a);
+  return cudaLaunchKernelEx(&cfg, k_tile<T, CL, MODE, MULTI, LOGM>, a);
+}
+
+// FP32 u = N^-1 t on 65536-sample tiles, each a 2-CTA cluster (t, u [nrhs][stride], strides
+// multiples of 4; tables of the 32768-point transform)
+cudaError_t launch_ninv32_big(const TileArgs& a, cudaStream_t s) {
+  if (a.x_stride % 4 != 0 || a.y_stride % 4 != 0) return cudaErrorInvalidValue;
+  return launch_tiles<float, 2, MODE_NINV_T, false, kLogM + 1>(a, kSmemBytes32Big, s);
 }
 
 // FP32 segments; halo_samples = largest L - vstep of the segments that walk more than one tile
@@ -888,59 +931,62 @@ cudaError_t launch_tiles_fp64(int mode, const TileArgs& a, cudaStream_t s) {
 // ---------------------------------------------------------------------------------------------
 
 // H_j = c_0 + 2 sum_{tau=1}^{lam} c_tau cos(2 pi tau j / L), j = 0..M: the L-point circulant
-// spectrum of the band (real and even because the kernel is symmetric).
+// spectrum of the band (real and even because the kernel is symmetric); L = 2M = 2^(logm + 1)
 __global__ void k_spectra(const double* __restrict__ band_rows, int32_t lambda,
-                          const double* __restrict__ costab, double* __restrict__ H) {
+                          const double* __restrict__ costab, double* __restrict__ H, int logm) {
   extern __shared__ double c_s[];
+  const int m = 1 << logm, l = 2 * m;
   const int tab = blockIdx.y;
   const double* c = band_rows + (int64_t)tab * (lambda + 1);
   for (int i = threadIdx.x; i <= lambda; i += blockDim.x) c_s[i] = c[i];
   __syncthreads();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j > kM) return;
+  if (j > m) return;
   double acc = 0.0;
   for (int tau = 1; tau <= lambda; tau++) {
-    acc = fma(c_s[tau], __ldg(costab + (((int64_t)tau * j) & (kL - 1))), acc);
+    acc = fma(c_s[tau], __ldg(costab + (((int64_t)tau * j) & (l - 1))), acc);
   }
-  H[(int64_t)tab * (kM + 1) + j] = c_s[0] + 2.0 * acc;
+  H[(int64_t)tab * (m + 1) + j] = c_s[0] + 2.0 * acc;
 }
 
 cudaError_t launch_spectra(const double* band_rows, int32_t n_tab, int32_t lambda, double* H,
-                           const double* costab, cudaStream_t s) {
+                           const double* costab, cudaStream_t s, int logm) {
   if (n_tab == 0) return cudaSuccess;
-  const int nt = 256;
+  const int nt = 256, m = 1 << logm;
   const size_t sm = (size_t)(lambda + 1) * sizeof(double);
   cudaError_t e = cudaSuccess;
   if (sm > 48 * 1024) e = cudaFuncSetAttribute(k_spectra, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   for (int32_t t0 = 0; t0 < n_tab; t0 += 65535) {   // gridDim.y limit
     const int32_t nt_y = (n_tab - t0) < 65535 ? (n_tab - t0) : 65535;
-    dim3 grid((kM + 1 + nt - 1) / nt, nt_y);
+    dim3 grid((m + 1 + nt - 1) / nt, nt_y);
     k_spectra<<<grid, nt, sm, s>>>(band_rows + (int64_t)t0 * (lambda + 1), lambda, costab,
-                                   H + (int64_t)t0 * (kM + 1));
+                                   H + (int64_t)t0 * (m + 1), logm);
   }
   return cudaGetLastError();
 }
 
-// (a_k, b_k) of the pair update for every storage position of both layouts.
-template <int CL>
+// (a_k, b_k) of the pair update for every storage position of a tile of 2^LOGM complex points
+// split over CL CTAs (the storage order of each CTA's transform)
+template <int CL, int LOGM>
 __global__ void k_pair_table(const double* __restrict__ H, const double* __restrict__ costab,
                              int32_t n_tab, void* __restrict__ out, int fp32) {
-  constexpr int LOGMS = kLogM - (CL == 2 ? 1 : 0);
+  constexpr int M = 1 << LOGM, L = 2 * M;
+  constexpr int LOGMS = LOGM - (CL == 2 ? 1 : 0);
   constexpr int MS = 1 << LOGMS;
-  using FFT = SmemFFT<LOGMS, kM, kTileThreads>;
+  using FFT = SmemFFT<LOGMS, M, kTileThreads>;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)n_tab * kM) return;
-  const int tab = (int)(idx / kM);
-  const int rem = (int)(idx % kM);
+  if (idx >= (int64_t)n_tab * M) return;
+  const int tab = (int)(idx / M);
+  const int rem = (int)(idx % M);
   const int rank = rem / MS, j = rem % MS;
   const int k = CL * FFT::freq_of(j) + rank;       // global frequency, 0 <= k < M
-  const double* h = H + (int64_t)tab * (kM + 1);
-  const double S = 0.5 * (h[k] + h[kM - k]);
-  const double D = 0.5 * (h[k] - h[kM - k]);
+  const double* h = H + (int64_t)tab * (M + 1);
+  const double S = 0.5 * (h[k] + h[M - k]);
+  const double D = 0.5 * (h[k] - h[M - k]);
   const double cth = costab[k];
-  const double sth = costab[(k - kL / 4) & (kL - 1)];
-  const double inv_m = 1.0 / (double)kM;
+  const double sth = costab[(k - L / 4) & (L - 1)];
+  const double inv_m = 1.0 / (double)M;
   const double av = (S - D * sth) * inv_m;
   const double bv = D * cth * inv_m;
   if (fp32) reinterpret_cast<float2*>(out)[idx] = make_float2((float)av, (float)bv);
@@ -953,23 +999,34 @@ cudaError_t launch_pair_tables(const double* H, int32_t n_tab, const double* cos
   const int64_t n = (int64_t)n_tab * kM;
   const int nt = 256;
   const unsigned nb = (unsigned)((n + nt - 1) / nt);
-  k_pair_table<kCl64><<<nb, nt, 0, s>>>(H, costab, n_tab, tab64, 0);
-  k_pair_table<kCl32><<<nb, nt, 0, s>>>(H, costab, n_tab, tab32, 1);
+  k_pair_table<kCl64, kLogM><<<nb, nt, 0, s>>>(H, costab, n_tab, tab64, 0);
+  k_pair_table<kCl32, kLogM><<<nb, nt, 0, s>>>(H, costab, n_tab, tab32, 1);
   return cudaGetLastError();
 }
 
-// tw[k] = W_M^k = exp(-2 pi i k / M) = cos(2 pi 2k / L) - i sin(2 pi 2k / L)
-__global__ void k_twiddles(double2* tw64, float2* tw32, const double* __restrict__ costab) {
+// FP32 pair tables of the 65536-sample 2-CTA tiles (H and costab of that length)
+cudaError_t launch_pair_table32_big(const double* H, int32_t n_tab, const double* costab, float2* tab32,
+                                    cudaStream_t s) {
+  if (n_tab == 0) return cudaSuccess;
+  const int64_t n = (int64_t)n_tab * 2 * kM;
+  k_pair_table<2, kLogM + 1><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(H, costab, n_tab, tab32, 1);
+  return cudaGetLastError();
+}
+
+// tw[k] = W_M^k = exp(-2 pi i k / M) = cos(2 pi 2k / L) - i sin(2 pi 2k / L), M = 2^logm
+__global__ void k_twiddles(double2* tw64, float2* tw32, const double* __restrict__ costab, int logm) {
+  const int m = 1 << logm, l = 2 * m;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= kM) return;
-  const double c = costab[(2 * k) & (kL - 1)];
-  const double s = costab[(2 * k - kL / 4) & (kL - 1)];
-  tw64[k] = make_double2(c, -s);
+  if (k >= m) return;
+  const double c = costab[(2 * k) & (l - 1)];
+  const double s = costab[(2 * k - l / 4) & (l - 1)];
+  if (tw64) tw64[k] = make_double2(c, -s);
   tw32[k] = make_float2((float)c, (float)-s);
 }
 
-cudaError_t launch_twiddles(double2* tw64, float2* tw32, const double* costab, cudaStream_t s) {
-  k_twiddles<<<(kM + 255) / 256, 256, 0, s>>>(tw64, tw32, costab);
+cudaError_t launch_twiddles(double2* tw64, float2* tw32, const double* costab, cudaStream_t s, int logm) {
+  const int m = 1 << logm;
+  k_twiddles<<<(m + 255) / 256, 256, 0, s>>>(tw64, tw32, costab, logm);
   return cudaGetLastError();
 }
 

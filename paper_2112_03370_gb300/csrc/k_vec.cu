@@ -7,7 +7,8 @@ namespace mm {
 
 namespace {
 constexpr int kNT = 256;
-__host__ __device__ inline unsigned grid_for(int64_t n, int per = kNT, unsigned cap = 8 * 152 * 4) {
+inline unsigned grid_for(int64_t n, int per = kNT, unsigned cap = 0) {
+  if (cap == 0) cap = 32u * (unsigned)sm_count();
   int64_t g = (n + per - 1) / per;
   if (g < 1) g = 1;
   if (g > cap) g = cap;

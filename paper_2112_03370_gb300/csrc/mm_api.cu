@@ -26,17 +26,17 @@ int fail(int code, const std::string& msg) {
   g_err = msg;
   return code;
 }
+// multiprocessors of the current device, cached per device (the GB300's 152 only if the query fails)
 int sm_count() {
+  constexpr int kFallbackSms = 152;
   static int cached[64] = {0};
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 152;
-  if (dev >= 64) {
-    int n = 0;
-    return cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0 ? n : 152;
-  }
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return kFallbackSms;
+  int n = 0;
+  if (dev >= 64)
+    return cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0 ? n : kFallbackSms;
   if (cached[dev] == 0) {
-    int n = 0;
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 152;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return kFallbackSms;
     cached[dev] = n;
   }
   return cached[dev];
@@ -169,6 +169,7 @@ void free_plan(Plan* P) {
   dfree(P->ang2); dfree(P->groups); dfree(P->slot); dfree(P->slot_pix); dfree(P->u32);
   dfree(P->udf); dfree(P->amax);
   dfree(P->tc_tiles); dfree(P->tc_tab); dfree(P->tc_scale); dfree(P->tc_err);
+  dfree(P->segs_big); dfree(P->tab32_big); dfree(P->tw32_big);
   if (P->tc_bmat) { cudaFree(P->tc_bmat); P->tc_bmat = nullptr; }
   for (void*& b : P->stage) if (b) { cudaFree(b); b = nullptr; }
   for (cudaEvent_t& e : P->stage_ev) if (e) { cudaEventDestroy(e); e = nullptr; }
@@ -258,9 +259,9 @@ BandTables dedupe_bands(const std::vector<double>& band, int nb, int lam) {
 // Tiles are grouped into segments of up to `max_steps` consecutive tiles (one CTA walks a
 // segment and keeps the overlap of consecutive windows); max_steps = 1 gives single tiles.
 std::vector<TileDesc> make_tiles(const std::vector<int64_t>& off, const BandTables& bt, int lam,
-                                 int max_steps, int max_halo, int32_t* halo_out) {
+                                 int max_steps, int max_halo, int32_t* halo_out, int64_t L = kL) {
   std::vector<TileDesc> tiles;
-  const int64_t vmax = ((int64_t)kL - 2 * (int64_t)lam - 4) & ~(int64_t)3;
+  const int64_t vmax = (L - 2 * (int64_t)lam - 4) & ~(int64_t)3;
   const int nb = (int)off.size() - 1;
   int32_t halo_used = 0;
   for (int b = 0; b < nb; b++) {
@@ -268,7 +269,7 @@ std::vector<TileDesc> make_tiles(const std::vector<int64_t>& off, const BandTabl
     if (n <= 0) continue;
     const int64_t nt = (n + vmax - 1) / vmax;
     const int64_t vstep = (((n + nt - 1) / nt) + 3) & ~(int64_t)3;
-    const int64_t halo = (int64_t)kL - vstep;
+    const int64_t halo = L - vstep;
     const int64_t steps_cap = (halo <= max_halo) ? max_steps : 1;
     const int64_t nseg = (nt + steps_cap - 1) / steps_cap;
     const int64_t per = (nt + nseg - 1) / nseg;
@@ -571,8 +572,8 @@ int build_plan(const mm_problem_desc* d, cudaStream_t us, Plan* P) {
   MM_TRY(dalloc(P, &P->w64, P->N));
   MM_TRY(dalloc(P, &P->w32, P->N));
   if (P->df64) MM_TRY(dalloc(P, &P->wdf, P->N));
-  const bool windows = (P->precision == MM_FP32 || P->df64) && P->algo == MM_TPLZ_FFT;
-  if (P->precision == MM_FP32 && P->algo == MM_TPLZ_FFT) MM_TRY(dalloc(P, &P->ang2, P->N));
+  const bool windows = (P->precision == MM_FP32 || P->df64) && P->algo == MM_TPLZ_FFT && !P->no_windows;
+  if (windows && P->precision == MM_FP32) MM_TRY(dalloc(P, &P->ang2, P->N));
   MM_CUDA(launch_weights(P->psi, P->N, P->w64, P->w32, P->df64 ? P->wdf : nullptr, P->ang2, s));
   MM_CUDA(launch_bd_accum(pix, P->w64, P->block_off_dev, P->c0_blk, nb, P->N, B6, hits, s));
   MM_CUDA(launch_bd_finalize(B6, hits, P->n_pix, P->cond_max, keep, inv6, s));
@@ -610,6 +611,28 @@ int build_plan(const mm_problem_desc* d, cudaStream_t us, Plan* P) {
   MM_CUDA(launch_spectra(rows_d, P->n_tab, lam, H, costab_d, s));
   MM_CUDA(launch_pair_tables(H, P->n_tab, costab_d, P->tab64, P->tab32, s));
   MM_CUDA(launch_twiddles(P->tw64, P->tw32, costab_d, s));
+  // FP32 N^-1 on 65536-sample tiles (2-CTA clusters) when a 32768-sample tile would keep less than
+  // 5/8 of its outputs: tables built here, used when mm_autotune measures them faster
+  P->big = P->precision == MM_FP32 && P->algo == MM_TPLZ_FFT && !P->tc && !P->no_windows && lam > kBigTileLambda;
+  if (P->big) {
+    const int lb = 2 * kL, mb = 2 * kM;
+    std::vector<double> cb(lb);
+    for (int i = 0; i < lb; i++) cb[i] = std::cos(2.0 * M_PI * (double)i / (double)lb);
+    double *cb_d = nullptr, *Hb = nullptr;
+    MM_TRY(scr.alloc(&cb_d, lb));
+    MM_TRY(scr.alloc(&Hb, (size_t)P->n_tab * (mb + 1)));
+    MM_TRY(dalloc(P, &P->tab32_big, (size_t)P->n_tab * mb));
+    MM_TRY(dalloc(P, &P->tw32_big, mb));
+    MM_CUDA(cudaMemcpyAsync(cb_d, cb.data(), lb * sizeof(double), cudaMemcpyHostToDevice, s));
+    MM_CUDA(launch_spectra(rows_d, P->n_tab, lam, Hb, cb_d, s, kLogM + 1));
+    MM_CUDA(launch_pair_table32_big(Hb, P->n_tab, cb_d, P->tab32_big, s));
+    MM_CUDA(launch_twiddles(nullptr, P->tw32_big, cb_d, s, kLogM + 1));
+    const std::vector<TileDesc> sb = make_tiles(P->block_off, bt, lam, 1, 0, nullptr, lb);
+    P->n_segs_big = (int64_t)sb.size();
+    MM_TRY(dalloc(P, &P->segs_big, sb.size()));
+    MM_CUDA(cudaMemcpyAsync(P->segs_big, sb.data(), sb.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, s));
+    MM_CUDA(cudaStreamSynchronize(s));   // host vectors go out of scope
+  }
   if (P->tc) {   // tensor-core Toeplitz product: T_J images, tiles, per-block table and scale
     unsigned char* bm = nullptr;
     MM_TRY(dalloc(P, &bm, tc_bmat_bytes(P->n_tab)));
@@ -881,6 +904,21 @@ int ninv32(Plan* P, const float* t, float* u, int64_t ts, int g, const int32_t* 
     return MM_OK;
   }
   TileArgs a = base_args(P, true);
+  if (P->big && P->use_big) {
+    a.tiles = P->segs_big;
+    a.n_tiles = P->n_segs_big;
+    a.tab = P->tab32_big;
+    a.tw = P->tw32_big;
+    a.nrhs = g;
+    a.x = t;
+    a.x_stride = ts;
+    a.y = u;
+    a.y_stride = ts;
+    a.done = done;
+    a.done_stride = done_stride;
+    MM_CUDA(launch_ninv32_big(a, s));
+    return MM_OK;
+  }
   a.tiles = P->segs;
   a.n_tiles = P->n_segs;
   a.nrhs = g;
@@ -1103,7 +1141,8 @@ int ensure_defl_work(Plan* P, DeflState* d, int nrhs, int n_blocks, DeflWork* ou
   return MM_OK;
 }
 
-constexpr int kBlkCtas = 2 * 152;
+// CTAs (and partial sums) of the block reductions: two per SM
+int blk_ctas() { return 2 * sm_count(); }
 
 int ensure_blk(Plan* P, int s, BlkState** out) {
   BlkState* b = reinterpret_cast<BlkState*>(P->blk);
@@ -1120,11 +1159,11 @@ int ensure_blk(Plan* P, int s, BlkState** out) {
     MM_TRY(dalloc(P, &b->AX, n4)); MM_TRY(dalloc(P, &b->T64, n4));
     MM_TRY(dalloc(P, &b->Z, n4)); MM_TRY(dalloc(P, &b->AZ, n4)); MM_TRY(dalloc(P, &b->P, n4));
     MM_TRY(dalloc(P, &b->AP, n4));
-    MM_TRY(dalloc(P, &b->part, (size_t)kBlkCtas * kMaxBlk * kMaxBlk));
+    MM_TRY(dalloc(P, &b->part, (size_t)blk_ctas() * kMaxBlk * kMaxBlk));
     MM_TRY(dalloc(P, &b->G, kMaxBlk * kMaxBlk)); MM_TRY(dalloc(P, &b->Linv, kMaxBlk * kMaxBlk));
     MM_TRY(dalloc(P, &b->Cmb, kMaxBlk * kMaxBlk)); MM_TRY(dalloc(P, &b->alpha, kMaxBlk * kMaxBlk));
     MM_TRY(dalloc(P, &b->C2, kMaxBlk * kMaxBlk)); MM_TRY(dalloc(P, &b->norms, kMaxBlk));
-    MM_TRY(dalloc(P, &b->norm_part, (size_t)kMaxBlk * kBlkCtas));
+    MM_TRY(dalloc(P, &b->norm_part, (size_t)kMaxBlk * blk_ctas()));
     MM_TRY(dalloc(P, &b->piv, kMaxBlk)); MM_TRY(dalloc(P, &b->rank, 4)); MM_TRY(dalloc(P, &b->idx, kMaxBlk));
     MM_CUDA(cudaMallocHost((void**)&b->host, kMaxBlk * sizeof(double)));
     MM_CUDA(cudaMallocHost((void**)&b->host_i, 4 * sizeof(int)));
@@ -1254,7 +1293,9 @@ int start_request(Server* S, Request* r) {
   r->desc.band = r->band.data();
   r->desc.inputs_on_device = 0;
   if (r->fp32) r->desc.precision = MM_FP32_DF64;
+  r->desc.toeplitz_algo = MM_TPLZ_FFT;   // the multi-problem launches run the FFT tiles
   r->plan = new Plan();
+  r->plan->no_windows = true;
   int st = build_plan(&r->desc, S->stream, r->plan);
   if (st != MM_OK) return st;
   Plan* P = r->plan;
@@ -1978,6 +2019,27 @@ int mm_autotune(mm_plan_t plan, int max_width, mm_tune_info* out, void* stream) 
   cudaEventDestroy(ev);
   std::memset(out, 0, sizeof(*out));
   constexpr int kReps = 3;
+  // every candidate's A x (of the same filled input) is checked against the first one's
+  std::vector<float> ref, cur;
+  auto check = [&](bool* pass) -> int {
+    const size_t n = (size_t)P->n_obs * 4;
+    std::vector<float>& dst = ref.empty() ? ref : cur;
+    dst.resize(n);
+    MM_CUDA(cudaMemcpyAsync(dst.data(), P->map32_out, n * sizeof(float), cudaMemcpyDeviceToHost, P->stream));
+    MM_CUDA(cudaStreamSynchronize(P->stream));
+    *pass = true;
+    if (&dst == &ref) return MM_OK;
+    double mx = 0.0, dv = 0.0;
+    for (size_t i = 0; i < n; i++) {
+      mx = std::max(mx, (double)std::fabs(ref[i]));
+      dv = std::max(dv, (double)std::fabs(cur[i] - ref[i]));
+    }
+    const double rel = mx > 0.0 ? dv / mx : dv;
+    out->max_rel_dev = std::max(out->max_rel_dev, rel);
+    *pass = std::isfinite(rel) && rel < 1e-4;
+    if (!*pass) out->n_rejected++;
+    return MM_OK;
+  };
   // 1. tiles per segment: more tiles per CTA re-read less of the overlap, fewer leave SMs idle
   const int steps_c[] = {1, 2, 4, 8, 16, 32};
   double best = 1e300;
@@ -1986,15 +2048,30 @@ int mm_autotune(mm_plan_t plan, int max_width, mm_tune_info* out, void* stream) 
     if (v > 1 && P->n_tiles / v < sm_count()) continue;   // fewer segments than SMs
     MM_TRY(build_segments(P, v, P->stream));
     double ms = 0.0;
+    bool pass = false;
     MM_TRY(time_apply32(P, 1, kReps, &ms));
+    MM_TRY(check(&pass));
     out->steps_cand[out->n_steps] = v;
     out->steps_ms[out->n_steps++] = ms;
-    if (ms < best) {
+    if (pass && ms < best) {
       best = ms;
       best_steps = v;
     }
   }
   MM_TRY(build_segments(P, best_steps, P->stream));
+  // 1b. 65536-sample tiles over 2-CTA clusters (large lambda): kept when faster
+  out->big_tiles = -1;
+  if (P->big) {
+    P->use_big = true;
+    double ms = 0.0;
+    bool pass = false;
+    MM_TRY(time_apply32(P, 1, kReps, &ms));
+    MM_TRY(check(&pass));
+    out->big_tiles_ms = ms;
+    P->use_big = pass && ms < best;
+    if (P->use_big) best = ms;
+    out->big_tiles = P->use_big ? 1 : 0;
+  }
   // 2. samples per pixel-window group: larger groups repeat more pixels but stream shorter chunks
   const int win_c[] = {8192, 16384, 32768, 65536};
   best = 1e300;
@@ -2003,10 +2080,12 @@ int mm_autotune(mm_plan_t plan, int max_width, mm_tune_info* out, void* stream) 
     P->win_samples = v;
     MM_TRY(build_windows(P, P->stream));
     double ms = 0.0;
+    bool pass = false;
     MM_TRY(time_apply32(P, 1, kReps, &ms));
+    MM_TRY(check(&pass));
     out->win_cand[out->n_win] = v;
     out->win_ms[out->n_win++] = ms;
-    if (ms < best) {
+    if (pass && ms < best) {
       best = ms;
       best_win = v;
     }
@@ -2110,7 +2189,7 @@ int mm_block_cg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, int 
     MM_CUDA(launch_pack3to4(b + (size_t)g0 * n * 3, n, sg, B->B, s));
     MM_CUDA(cudaMemsetAsync(B->X, 0, n4 * sizeof(double), s));
     MM_CUDA(cudaMemsetAsync(B->AX, 0, n4 * sizeof(double), s));
-    MM_CUDA(launch_bresid(B->B, B->AX, sg, n, B->R, B->norm_part, kBlkCtas, B->norms, s));   // R = B
+    MM_CUDA(launch_bresid(B->B, B->AX, sg, n, B->R, B->norm_part, blk_ctas(), B->norms, s));   // R = B
     n_kernels += 3;
     MM_TRY(read_norms(sg));
     std::vector<double> bn2(B->host, B->host + sg), rn2(bn2), tn2(bn2);
@@ -2127,7 +2206,7 @@ int mm_block_cg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, int 
     auto true_residual = [&]() -> int {
       MM_CUDA(cudaMemsetAsync(B->AX, 0, n4 * sizeof(double), s));
       MM_TRY(apply64_internal(P, B->X, B->AX, sg, s));
-      MM_CUDA(launch_bresid(B->B, B->AX, sg, n, B->R, B->norm_part, kBlkCtas, B->norms, s));
+      MM_CUDA(launch_bresid(B->B, B->AX, sg, n, B->R, B->norm_part, blk_ctas(), B->norms, s));
       n_kernels += 3;
       n_apply64 += 1;
       MM_TRY(read_norms(sg));
@@ -2154,8 +2233,8 @@ int mm_block_cg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, int 
       MM_CUDA(launch_bprecond(P->minv, B->R, B->idx, t, n, B->Z, s));   // Z = M R[active]
       n_kernels += 1;
       if (!fresh && r > 0) {   // Z = (I - P P^T A) M R: Z -= P (AP^T Z)
-        MM_CUDA(launch_bgram(B->AP, r, nullptr, B->Z, 0, t, nullptr, n, B->part, kBlkCtas, B->C2, s));
-        MM_CUDA(launch_bcombine(B->Z, 0, nullptr, t, B->P, r, B->C2, t, -1.0, 1, n, nullptr, kBlkCtas,
+        MM_CUDA(launch_bgram(B->AP, r, nullptr, B->Z, 0, t, nullptr, n, B->part, blk_ctas(), B->C2, s));
+        MM_CUDA(launch_bcombine(B->Z, 0, nullptr, t, B->P, r, B->C2, t, -1.0, 1, n, nullptr, blk_ctas(),
                                 nullptr, s));
         n_kernels += 3;
       }
@@ -2164,7 +2243,7 @@ int mm_block_cg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, int 
       MM_TRY(blk_apply(P, B, t, fp32, s));                                 // AZ = A Z
       n_kernels += fp32 ? 1 : 3;
       n_apply += 1;
-      MM_CUDA(launch_bgram(B->Z, t, nullptr, B->AZ, 0, t, nullptr, n, B->part, kBlkCtas, B->G, s));
+      MM_CUDA(launch_bgram(B->Z, t, nullptr, B->AZ, 0, t, nullptr, n, B->part, blk_ctas(), B->G, s));
       MM_CUDA(launch_bchol(B->G, t, 1e-10, B->Linv, B->piv, B->rank, s));
       MM_CUDA(cudaMemcpyAsync(B->host_i, B->rank, sizeof(int), cudaMemcpyDeviceToHost, s));
       MM_CUDA(cudaStreamSynchronize(s));
@@ -2183,14 +2262,14 @@ int mm_block_cg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, int 
         break;
       }
       MM_CUDA(launch_linv_coef(B->Linv, B->piv, B->rank, t, B->Cmb, s));
-      MM_CUDA(launch_bcombine(B->P, 0, nullptr, r, B->Z, t, B->Cmb, t, 1.0, 0, n, nullptr, kBlkCtas, nullptr, s));
-      MM_CUDA(launch_bcombine(B->AP, 0, nullptr, r, B->AZ, t, B->Cmb, t, 1.0, 0, n, nullptr, kBlkCtas, nullptr, s));
+      MM_CUDA(launch_bcombine(B->P, 0, nullptr, r, B->Z, t, B->Cmb, t, 1.0, 0, n, nullptr, blk_ctas(), nullptr, s));
+      MM_CUDA(launch_bcombine(B->AP, 0, nullptr, r, B->AZ, t, B->Cmb, t, 1.0, 0, n, nullptr, blk_ctas(), nullptr, s));
       // alpha = P^T R over all sg columns; X += P alpha; R -= AP alpha
-      MM_CUDA(launch_bgram(B->P, r, nullptr, B->R, 1, sg, nullptr, n, B->part, kBlkCtas, B->alpha, s));
-      MM_CUDA(launch_bcombine(B->X, 1, nullptr, sg, B->P, r, B->alpha, sg, 1.0, 1, n, nullptr, kBlkCtas,
+      MM_CUDA(launch_bgram(B->P, r, nullptr, B->R, 1, sg, nullptr, n, B->part, blk_ctas(), B->alpha, s));
+      MM_CUDA(launch_bcombine(B->X, 1, nullptr, sg, B->P, r, B->alpha, sg, 1.0, 1, n, nullptr, blk_ctas(),
                               nullptr, s));
       MM_CUDA(launch_bcombine(B->R, 1, nullptr, sg, B->AP, r, B->alpha, sg, -1.0, 1, n, B->norm_part,
-                              kBlkCtas, B->norms, s));
+                              blk_ctas(), B->norms, s));
       n_kernels += 9;
       it += 1;
       MM_TRY(read_norms(sg));
@@ -2275,7 +2354,7 @@ int mm_ecg_solve(mm_plan_t plan, const double* b, double* x, int t, int variant,
   };
   // b (column 0 of B->B), ||b||^2, x = 0, r = b
   MM_CUDA(launch_pack3to4(b, n, 1, B->B, s));
-  MM_CUDA(launch_bsum(B->B, 1, n, B->re, 0, B->norm_part, kBlkCtas, B->norms, s));
+  MM_CUDA(launch_bsum(B->B, 1, n, B->re, 0, B->norm_part, blk_ctas(), B->norms, s));
   MM_CUDA(cudaMemsetAsync(B->xe, 0, (size_t)n * 4 * sizeof(double), s));
   n_kernels += 3;
   MM_TRY(read_host(B->norms, 1));
@@ -2304,7 +2383,7 @@ int mm_ecg_solve(mm_plan_t plan, const double* b, double* x, int t, int variant,
       MM_TRY(blk_apply(P, B, tz, fp32, s));                                   // AZ = A Z
       n_kernels += fp32 ? 2 : 3;
       n_apply += 1;
-      MM_CUDA(launch_bgram(B->Z, tz, nullptr, B->AZ, 0, tz, nullptr, n, B->part, kBlkCtas, B->G, s));
+      MM_CUDA(launch_bgram(B->Z, tz, nullptr, B->AZ, 0, tz, nullptr, n, B->part, blk_ctas(), B->G, s));
       MM_CUDA(launch_bchol(B->G, tz, 1e-10, B->Linv, B->piv, B->rank, s));
       MM_CUDA(cudaMemcpyAsync(B->host_i, B->rank, sizeof(int), cudaMemcpyDeviceToHost, s));
       MM_CUDA(cudaStreamSynchronize(s));
@@ -2324,12 +2403,12 @@ int mm_ecg_solve(mm_plan_t plan, const double* b, double* x, int t, int variant,
       inner += 1;
       // P_k = Z (Z^T A Z)^{-1/2} and A P_k; alpha = P_k^T R; X += P alpha; R -= A P alpha
       MM_CUDA(launch_linv_coef(B->Linv, B->piv, B->rank, tz, B->Cmb, s));
-      MM_CUDA(launch_bcombine(B->P, 0, nullptr, r, B->Z, tz, B->Cmb, tz, 1.0, 0, n, nullptr, kBlkCtas, nullptr, s));
-      MM_CUDA(launch_bcombine(B->AP, 0, nullptr, r, B->AZ, tz, B->Cmb, tz, 1.0, 0, n, nullptr, kBlkCtas, nullptr, s));
-      MM_CUDA(launch_bgram(B->P, r, nullptr, B->R, 1, t, nullptr, n, B->part, kBlkCtas, B->alpha, s));
-      MM_CUDA(launch_bcombine(B->X, 1, nullptr, t, B->P, r, B->alpha, t, 1.0, 1, n, nullptr, kBlkCtas, nullptr, s));
-      MM_CUDA(launch_bcombine(B->R, 1, nullptr, t, B->AP, r, B->alpha, t, -1.0, 1, n, nullptr, kBlkCtas, nullptr, s));
-      MM_CUDA(launch_bsum(B->R, t, n, nullptr, 0, B->norm_part, kBlkCtas, B->norms, s));   // ||sum_i R_i||^2
+      MM_CUDA(launch_bcombine(B->P, 0, nullptr, r, B->Z, tz, B->Cmb, tz, 1.0, 0, n, nullptr, blk_ctas(), nullptr, s));
+      MM_CUDA(launch_bcombine(B->AP, 0, nullptr, r, B->AZ, tz, B->Cmb, tz, 1.0, 0, n, nullptr, blk_ctas(), nullptr, s));
+      MM_CUDA(launch_bgram(B->P, r, nullptr, B->R, 1, t, nullptr, n, B->part, blk_ctas(), B->alpha, s));
+      MM_CUDA(launch_bcombine(B->X, 1, nullptr, t, B->P, r, B->alpha, t, 1.0, 1, n, nullptr, blk_ctas(), nullptr, s));
+      MM_CUDA(launch_bcombine(B->R, 1, nullptr, t, B->AP, r, B->alpha, t, -1.0, 1, n, nullptr, blk_ctas(), nullptr, s));
+      MM_CUDA(launch_bsum(B->R, t, n, nullptr, 0, B->norm_part, blk_ctas(), B->norms, s));   // ||sum_i R_i||^2
       n_kernels += 10;
       it += 1;
       MM_TRY(read_host(B->norms, 1));
@@ -2353,19 +2432,19 @@ int mm_ecg_solve(mm_plan_t plan, const double* b, double* x, int t, int variant,
         // Z_{k+1} = (I - P_k P_k^T A) M R_k
         MM_CUDA(launch_bprecond(P->minv, B->R, nullptr, t, n, B->Z, s));
         tz = t;
-        MM_CUDA(launch_bgram(B->AP, r, nullptr, B->Z, 0, tz, nullptr, n, B->part, kBlkCtas, B->C2, s));
-        MM_CUDA(launch_bcombine(B->Z, 0, nullptr, tz, B->P, r, B->C2, tz, -1.0, 1, n, nullptr, kBlkCtas, nullptr, s));
+        MM_CUDA(launch_bgram(B->AP, r, nullptr, B->Z, 0, tz, nullptr, n, B->part, blk_ctas(), B->C2, s));
+        MM_CUDA(launch_bcombine(B->Z, 0, nullptr, tz, B->P, r, B->C2, tz, -1.0, 1, n, nullptr, blk_ctas(), nullptr, s));
         n_kernels += 4;
       } else {
         // Z_{k+1} = (I - P_k P_k^T A - P_{k-1} P_{k-1}^T A) M A P_k
         MM_CUDA(launch_bprecond32(P->minv, B->AP, r, n, B->Z, s));
         tz = r;
-        MM_CUDA(launch_bgram(B->AP, r, nullptr, B->Z, 0, tz, nullptr, n, B->part, kBlkCtas, B->C2, s));
-        MM_CUDA(launch_bcombine(B->Z, 0, nullptr, tz, B->P, r, B->C2, tz, -1.0, 1, n, nullptr, kBlkCtas, nullptr, s));
+        MM_CUDA(launch_bgram(B->AP, r, nullptr, B->Z, 0, tz, nullptr, n, B->part, blk_ctas(), B->C2, s));
+        MM_CUDA(launch_bcombine(B->Z, 0, nullptr, tz, B->P, r, B->C2, tz, -1.0, 1, n, nullptr, blk_ctas(), nullptr, s));
         n_kernels += 4;
         if (rprev > 0) {
-          MM_CUDA(launch_bgram(B->APp, rprev, nullptr, B->Z, 0, tz, nullptr, n, B->part, kBlkCtas, B->G, s));
-          MM_CUDA(launch_bcombine(B->Z, 0, nullptr, tz, B->Pp, rprev, B->G, tz, -1.0, 1, n, nullptr, kBlkCtas,
+          MM_CUDA(launch_bgram(B->APp, rprev, nullptr, B->Z, 0, tz, nullptr, n, B->part, blk_ctas(), B->G, s));
+          MM_CUDA(launch_bcombine(B->Z, 0, nullptr, tz, B->Pp, rprev, B->G, tz, -1.0, 1, n, nullptr, blk_ctas(),
                                   nullptr, s));
           n_kernels += 3;
         }
@@ -2375,10 +2454,10 @@ int mm_ecg_solve(mm_plan_t plan, const double* b, double* x, int t, int variant,
       }
     }
     // x += X 1, then the FP64-class true residual r = b - A x
-    MM_CUDA(launch_bsum(B->X, t, n, B->xe, 1, B->norm_part, kBlkCtas, B->norms, s));
+    MM_CUDA(launch_bsum(B->X, t, n, B->xe, 1, B->norm_part, blk_ctas(), B->norms, s));
     MM_CUDA(cudaMemsetAsync(B->ax, 0, (size_t)n * 4 * sizeof(double), s));
     MM_TRY(apply64_internal(P, B->xe, B->ax, 1, s));
-    MM_CUDA(launch_bresid(B->B, B->ax, 1, n, B->re, B->norm_part, kBlkCtas, B->norms, s));
+    MM_CUDA(launch_bresid(B->B, B->ax, 1, n, B->re, B->norm_part, blk_ctas(), B->norms, s));
     n_kernels += 5;
     n_apply64 += 1;
     MM_TRY(read_host(B->norms, 1));
@@ -2432,14 +2511,14 @@ int mm_deflation_build(mm_plan_t plan, const double* b, int m, int precision, vo
   double *alpha_d = nullptr, *beta_d = nullptr, *work = nullptr, *U = nullptr, *X = nullptr, *wvals = nullptr,
          *E = nullptr, *gpart = nullptr;
   float *V32 = nullptr, *AV32 = nullptr, *x32 = nullptr, *y32 = nullptr;
-  const int nblk = 4 * 152;
+  const int nblk = 4 * sm_count();
   MM_TRY(scr.alloc(&v_prev, n4)); MM_TRY(scr.alloc(&v, n4)); MM_TRY(scr.alloc(&wv, n4)); MM_TRY(scr.alloc(&av, n4));
   MM_TRY(scr.alloc(&part, nblk)); MM_TRY(scr.alloc(&dot, 2));
   MM_TRY(scr.alloc(&alpha_d, kMaxDefl)); MM_TRY(scr.alloc(&beta_d, kMaxDefl));
   MM_TRY(scr.alloc(&work, kMaxDefl * kMaxDefl)); MM_TRY(scr.alloc(&U, kMaxDefl * kMaxDefl));
   MM_TRY(scr.alloc(&X, kMaxDefl * kMaxDefl)); MM_TRY(scr.alloc(&wvals, kMaxDefl));
   MM_TRY(scr.alloc(&E, kMaxDefl * kMaxDefl));
-  MM_TRY(scr.alloc(&gpart, (size_t)2 * 152 * kMaxBlk * kMaxBlk));
+  MM_TRY(scr.alloc(&gpart, (size_t)blk_ctas() * kMaxBlk * kMaxBlk));
   MM_TRY(scr.alloc(&V32, (size_t)m * n4)); MM_TRY(scr.alloc(&AV32, (size_t)m * n4));
   if (precision == MM_FP32) { MM_TRY(scr.alloc(&x32, n4)); MM_TRY(scr.alloc(&y32, n4)); }
   auto host_dot = [&](const double* a_, const double* b_, double* out) -> int {
@@ -2506,9 +2585,9 @@ int mm_deflation_build(mm_plan_t plan, const double* b, int m, int precision, vo
   MM_TRY(dalloc(P, &d->Zp, (size_t)k * n4));
   MM_TRY(dalloc(P, &d->Einv, (size_t)k * k));
   // Z = V X, Z' = (A V) X, E = Z^T Z', Einv = pinv(E)
-  MM_CUDA(launch_bcombine(d->Z, 0, nullptr, k, V32, k, X, k, 1.0, 0, n, nullptr, 2 * 152, nullptr, s));
-  MM_CUDA(launch_bcombine(d->Zp, 0, nullptr, k, AV32, k, X, k, 1.0, 0, n, nullptr, 2 * 152, nullptr, s));
-  MM_CUDA(launch_bgram(d->Z, k, nullptr, d->Zp, 0, k, nullptr, n, gpart, 2 * 152, E, s));
+  MM_CUDA(launch_bcombine(d->Z, 0, nullptr, k, V32, k, X, k, 1.0, 0, n, nullptr, blk_ctas(), nullptr, s));
+  MM_CUDA(launch_bcombine(d->Zp, 0, nullptr, k, AV32, k, X, k, 1.0, 0, n, nullptr, blk_ctas(), nullptr, s));
+  MM_CUDA(launch_bgram(d->Z, k, nullptr, d->Zp, 0, k, nullptr, n, gpart, blk_ctas(), E, s));
   MM_CUDA(launch_pinv_sym(E, k, 1e-12, work, U, wvals + 0, d->Einv, s));
   std::vector<double> th(k);
   MM_CUDA(launch_tridiag_eig(alpha_d, beta_d, k, work, wvals, X, s));   // Ritz values again (wvals reused)
@@ -2542,7 +2621,7 @@ int mm_deflation_build_apriori(mm_plan_t plan, int precision, void* stream) {
   MM_TRY(scr.alloc(&hits, (size_t)k * n));
   MM_TRY(scr.alloc(&E, kMaxDefl * kMaxDefl)); MM_TRY(scr.alloc(&work, kMaxDefl * kMaxDefl));
   MM_TRY(scr.alloc(&U, kMaxDefl * kMaxDefl)); MM_TRY(scr.alloc(&wvals, kMaxDefl));
-  MM_TRY(scr.alloc(&gpart, (size_t)2 * 152 * kMaxBlk * kMaxBlk));
+  MM_TRY(scr.alloc(&gpart, (size_t)blk_ctas() * kMaxBlk * kMaxBlk));
   DeflState* d = reinterpret_cast<DeflState*>(P->defl);
   if (!d) {
     d = new DeflState();
@@ -2568,7 +2647,7 @@ int mm_deflation_build_apriori(mm_plan_t plan, int precision, void* stream) {
     MM_CUDA(launch_to32(P->map64_out, (int64_t)k * n, d->Zp, s));
   }
   // E = Z^T Z', Einv = pinv(E)
-  MM_CUDA(launch_bgram(d->Z, k, nullptr, d->Zp, 0, k, nullptr, n, gpart, 2 * 152, E, s));
+  MM_CUDA(launch_bgram(d->Z, k, nullptr, d->Zp, 0, k, nullptr, n, gpart, blk_ctas(), E, s));
   MM_CUDA(launch_pinv_sym(E, k, 1e-12, work, U, wvals, d->Einv, s));
   MM_CUDA(cudaStreamSynchronize(s));
   d->theta.assign(k, 0.0);

@@ -20,6 +20,7 @@ constexpr int kLogM = 14;                 // complex points per tile (both preci
 constexpr int kM = 1 << kLogM;            // 16384 complex = 32768 real samples
 constexpr int kL = 2 * kM;
 constexpr int kMaxLambda = 12288;         // keeps >= 8192 valid outputs per tile
+constexpr int kBigTileLambda = 6144;      // FP32 operators can use 65536-sample tiles above this lambda
 constexpr int kCl32 = 1;                  // FP32: one CTA holds the whole tile (128 KB smem)
 constexpr int kCl64 = 2;                  // FP64: a 2-CTA cluster holds it (2 x 128 KB smem)
 constexpr int kTileThreads = 512;
@@ -87,7 +88,8 @@ struct PGroup {
 // block, 3xTF32 tcgen05 MMAs over the 2 J0 + 1 row shifts, J0 = ceil(lambda / 32) <= kTcMaxJ0.
 // ---------------------------------------------------------------------------------------------
 constexpr int kTcMaxJ0 = 4;                 // lambda <= 128
-constexpr int kTcAutoLambda = -1;           // MM_TPLZ_AUTO picks the tensor cores up to this lambda
+constexpr int kTcAutoLambda = 32;           // MM_TPLZ_AUTO picks the tensor cores up to this lambda
+                                            // (measured crossover against the FFT tiles)
 struct TcTile {
   int32_t blk;   // block
   int32_t k0;    // first 32-sample row of the tile within the block
@@ -181,12 +183,23 @@ struct Plan {
   int32_t* tc_tab = nullptr;           // [n_blocks] table of each block
   float* tc_scale = nullptr;           // [n_blocks] band scale of each block
   int32_t* tc_err = nullptr;           // set by a timed-out wait of the tensor-core kernel
+  // FP32 N^-1 on 65536-sample tiles (2-CTA clusters) for large lambda: the tables are built for
+  // lambda > kBigTileLambda, the path is used when mm_autotune measured it faster (use_big)
+  bool big = false;
+  bool use_big = false;
+  TileDesc* segs_big = nullptr;        // one 65536-sample tile per descriptor
+  int64_t n_segs_big = 0;
+  float2* tab32_big = nullptr;         // [n_tab][2 kM] pair tables of the 32768-point transform
+  float2* tw32_big = nullptr;          // [2 kM] twiddles W_{2 kM}^k
   float* t32 = nullptr;                // [nrhs][N4] un-pointed FP32 input of the tiles (N4 = N
                                        // rounded up to 4)
   size_t t32_cap = 0;
   int32_t seg_halo = 0;                // largest L - vstep over the segments (samples)
 
-  // pixel windows of detector groups (FP32 operators)
+  // pixel windows of detector groups (FP32 operators); a server request's plan skips them (its FP32
+  // iterations run in the server's multi-problem tile launches, and a short plan build matters
+  // more for its latency than the faster windowed operators)
+  bool no_windows = false;
   PGroup* groups = nullptr;            // [n_groups]
   int64_t n_groups = 0;
   uint16_t* slot = nullptr;            // [N] pixel-sorted local index of each sample in its group
@@ -274,12 +287,20 @@ cudaError_t launch_weights(const float* psi, int64_t N, double2* w64, float2* w3
                            cudaStream_t s);
 cudaError_t launch_validate(const int32_t* pix, const float* psi, int64_t N, int64_t n_pix,
                             int32_t* bad, cudaStream_t s);
+// spectra of the L-point circulants, L = 2^(logm + 1): H [n_tab][M + 1], costab [L]
 cudaError_t launch_spectra(const double* band_rows, int32_t n_tab, int32_t lambda,
                            double* H /* [n_tab][M+1] */, const double* costab /* [L] */,
-                           cudaStream_t s);
+                           cudaStream_t s, int logm = kLogM);
 cudaError_t launch_pair_tables(const double* H, int32_t n_tab, const double* costab,
                                double2* tab64, float2* tab32, cudaStream_t s);
-cudaError_t launch_twiddles(double2* tw64, float2* tw32, const double* costab, cudaStream_t s);
+// FP32 pair tables of the 65536-sample 2-CTA tiles: tab32 [n_tab][2 kM]
+cudaError_t launch_pair_table32_big(const double* H, int32_t n_tab, const double* costab, float2* tab32,
+                                    cudaStream_t s);
+// W_M^k, k < M = 2^logm (tw64 may be null)
+cudaError_t launch_twiddles(double2* tw64, float2* tw32, const double* costab, cudaStream_t s,
+                            int logm = kLogM);
+// FP32 u = N^-1 t over 65536-sample 2-CTA tiles
+cudaError_t launch_ninv32_big(const TileArgs& a, cudaStream_t s);
 
 // Toeplitz-tile kernels (k_toeplitz.cu)
 cudaError_t launch_tiles_fp32(int mode, const TileArgs& a, int halo_samples, cudaStream_t s);

@@ -18,7 +18,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmm.so")
 MM_OK, MM_EINVAL, MM_ENOMEM, MM_ENOTSPD, MM_EBREAKDOWN, MM_ENOTCONV, MM_ETIMEOUT, MM_EBUSY, \
     MM_ECUDA = range(9)
 MM_FP64, MM_FP32, MM_DF64, MM_FP32_DF64 = 0, 1, 2, 3
-MM_TPLZ_AUTO, MM_TPLZ_FFT, MM_TPLZ_DIRECT = 0, 1, 3
+MM_TPLZ_AUTO, MM_TPLZ_FFT, MM_TPLZ_GEMM, MM_TPLZ_DIRECT = 0, 1, 2, 3
 MM_PREC_BD, MM_PREC_2LVL_POST = 0, 1
 MM_ECG_ORTHOMIN, MM_ECG_ORTHODIR = 0, 1
 STATUS_NAMES = {0: "MM_OK", 1: "MM_EINVAL", 2: "MM_ENOMEM", 3: "MM_ENOTSPD", 4: "MM_EBREAKDOWN",
@@ -70,7 +70,8 @@ class TuneInfo(ctypes.Structure):
                 ("steps_cand", ctypes.c_int32 * 8), ("steps_ms", ctypes.c_double * 8),
                 ("win_cand", ctypes.c_int32 * 8), ("win_ms", ctypes.c_double * 8),
                 ("width_cand", ctypes.c_int32 * 8), ("width_ms_per_col", ctypes.c_double * 8),
-                ("apply_ms", ctypes.c_double)]
+                ("apply_ms", ctypes.c_double), ("big_tiles", ctypes.c_int32), ("big_tiles_ms", ctypes.c_double),
+                ("max_rel_dev", ctypes.c_double), ("n_rejected", ctypes.c_int32)]
 
 
 class MMError(RuntimeError):
@@ -322,7 +323,8 @@ def mm_autotune(plan: Plan, max_width: int = 64, stream=None) -> dict:
     t = TuneInfo()
     _check(_lib.mm_autotune(ctypes.c_void_p(plan.handle), max_width, ctypes.byref(t), _stream_ptr(stream)))
     return {"tile_steps": t.tile_steps, "win_samples": t.win_samples, "block_width": t.block_width,
-            "apply_ms": t.apply_ms,
+            "apply_ms": t.apply_ms, "big_tiles": t.big_tiles, "big_tiles_ms": t.big_tiles_ms,
+            "max_rel_dev": t.max_rel_dev, "n_rejected": t.n_rejected,
             "steps_ms": {t.steps_cand[i]: t.steps_ms[i] for i in range(t.n_steps)},
             "win_ms": {t.win_cand[i]: t.win_ms[i] for i in range(t.n_win)},
             "width_ms_per_col": {t.width_cand[i]: t.width_ms_per_col[i] for i in range(t.n_width)}}

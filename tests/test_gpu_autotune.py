@@ -24,6 +24,7 @@ def test_autotune_keeps_operator_and_picks_fastest():
     assert res["steps_ms"][res["tile_steps"]] == min(res["steps_ms"].values())
     assert res["win_ms"][res["win_samples"]] == min(res["win_ms"].values())
     assert all(v > 0 for v in res["win_ms"].values())
+    assert res["n_rejected"] == 0 and res["max_rel_dev"] < 2e-5
     best = min(res["width_ms_per_col"].values())
     assert res["width_ms_per_col"][res["block_width"]] <= 1.02 * best + 1e-12
     # the rebuilt operator: A x against the oracle, FP32 tolerance

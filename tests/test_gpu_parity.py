@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
 
-Tolerances (derived from the arithmetic):
+Tolerances (derived from the arithmetic of each path):
   FP64 operators: max-norm relative error <= 1e-11 (overlap-save FFT rounding ~ 1e-15 log2 L per
   sample, times the band's dynamic range; the direct sum is ~1e-15).
   FP32 operators: <= 2e-5 (float32 rounding of weights, map and a 15-pass FFT, ~ 1e-6 typical,
@@ -112,6 +112,28 @@ def test_apply_A_fp32_matches_oracle(tile_steps):
     y = torch.empty(op.n_obs, 3, dtype=torch.float64, device="cuda")
     mm().mm_apply_A(gp, cuda(x), y)
     assert rel_max(y.cpu().numpy(), O.apply_A(op, x)) < 2e-5
+
+
+@pytest.mark.parametrize("lam", [6145, 8192, 12288])
+def test_apply_A_fp32_large_lambda_matches_oracle(lam):
+    """Above lambda = 6144 the FP32 operator can run N^-1 on 65536-sample tiles split over 2-CTA
+    clusters (the autotuner times them against 32768-sample tiles): both on ragged blocks (shorter
+    than one tile, one sample, empty), several columns."""
+    prob = small(11, block_len=(150001, 1, 70000, 0, 40000), lam=lam)
+    gp, op, _ = plans(prob, precision=3)
+    rng = np.random.default_rng(lam)
+    x = cuda(rng.standard_normal((2, op.n_obs, 3)))
+    y = torch.empty_like(x)
+    m = mm()
+    m.mm_apply_A(gp, x, y)   # 32768-sample tiles
+    for r in range(2):
+        assert rel_max(y[r].cpu().numpy(), O.apply_A(op, x[r].cpu().numpy())) < 2e-5
+    tune = m.mm_autotune(gp, max_width=1)   # times the 65536-sample 2-CTA tiles as a candidate
+    assert tune["big_tiles"] in (0, 1) and tune["big_tiles_ms"] > 0
+    assert tune["n_rejected"] == 0 and tune["max_rel_dev"] < 2e-5   # every candidate gave the same A x
+    m.mm_apply_A(gp, x, y)
+    for r in range(2):
+        assert rel_max(y[r].cpu().numpy(), O.apply_A(op, x[r].cpu().numpy())) < 2e-5
 
 
 def test_apply_A_multi_rhs():
