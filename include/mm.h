@@ -93,6 +93,11 @@ enum { MM_PREC_BD = 0, MM_PREC_2LVL_POST = 1 };
  *   inputs_on_device  non-zero: pix, psi and band are device pointers; zero: host pointers.
  *   tile_steps     FP32 operators: overlap-save tiles walked by one CTA, which keeps the overlap
  *                  of consecutive tiles in shared memory (0 = chosen from the problem size).
+ *   pt_sub         FP32 operators, the reduction of P^T: 0 = per-sample sums per pixel in shared
+ *                  memory over the pixel windows; 4096, 8192 or 16384 = segment reduction over
+ *                  pixel-sorted sub-windows of at most that many samples (runs of equal pixels
+ *                  summed in registers; the plan stores the sorted order, 8 more bytes per sample).
+ *                  Other values: MM_EINVAL.  mm_autotune times both forms.
  */
 typedef struct {
   int32_t n_det;
@@ -108,6 +113,7 @@ typedef struct {
   int32_t toeplitz_algo;
   int32_t inputs_on_device;
   int32_t tile_steps;
+  int32_t pt_sub;
 } mm_problem_desc;
 
 /*
@@ -243,6 +249,8 @@ int mm_solve_tod(mm_plan_t plan, const void* d, int d_is_fp32, double* x, int nr
  *      also 65536-sample tiles split over 2-CTA clusters (more of each tile kept, but every CTA
  *      reads the whole tile);
  *   2. target samples per pixel-window group of P and P^T (8192 ... 65536);
+ *   2b. the P^T reduction: per-sample shared-memory sums over the windows, or segment reduction
+ *      over pixel-sorted sub-windows of at most 4096, 8192 or 16384 samples;
  *   3. block width for mm_block_cg_solve with block_width = 0: the widest of 1, 2, 4, ..., max_width
  *      whose device time per column of A X is within 2% of the best.
  * Every candidate's A x (of one filled input) is compared with the first candidate's; one that
@@ -267,6 +275,10 @@ typedef struct {
   double big_tiles_ms;       /* their one-column FP32 A x (ms) when timed */
   double max_rel_dev;        /* largest relative difference of a candidate's A x from the first's */
   int32_t n_rejected;        /* candidates not chosen because their A x differed */
+  int32_t seg_sub;           /* chosen P^T: sub-window samples of the segment reduction, 0 = windows */
+  int32_t n_seg;
+  int32_t seg_cand[4];       /* 0 = per-sample sums over the windows, else sub-window samples */
+  double seg_ms[4];
 } mm_tune_info;
 int mm_autotune(mm_plan_t plan, int max_width, mm_tune_info* out, void* stream);
 

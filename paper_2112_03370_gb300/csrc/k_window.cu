@@ -385,6 +385,262 @@ cudaError_t launch_point_win32(const PGroup* groups, int64_t n_groups, const int
   return cudaGetLastError();
 }
 
+// ---- P^T by segment reduction over pixel-sorted sub-windows ----------------------------------
+// Sample l = c 2^log_s + o of sub-window sw: global index, false past its chunk's end.
+__device__ __forceinline__ bool sub_sample(const PGroup& G, const int64_t* __restrict__ block_off, int sw,
+                                           int log_s, int l, int64_t& i) {
+  int64_t lo;
+  int len;
+  group_chunk(G, block_off, l >> log_s, lo, len);
+  const int o = (sw << log_s) + (l & ((1 << log_s) - 1));
+  i = lo + o;
+  return o < len;
+}
+
+// One CTA per group: for each sub-window, the keys (slot << 16 | l) of its samples (masked ones
+// with slot kNoSlot) sorted ascending in shared memory (bitonic, padded with 0xFFFFFFFF), so equal
+// slots form runs ordered by l, then written out with each kept entry's angle.
+__global__ void __launch_bounds__(kWinThreads) k_seg_build(const PGroup* __restrict__ groups,
+                                                           const int64_t* __restrict__ block_off,
+                                                           const uint16_t* __restrict__ slot,
+                                                           const float* __restrict__ ang2, int sub_cap,
+                                                           uint32_t* __restrict__ ent,
+                                                           float* __restrict__ ent_ang,
+                                                           int32_t* __restrict__ kept) {
+  extern __shared__ __align__(16) uint32_t keys[];   // [next power of two >= sub_cap]
+  __shared__ int s_kept;
+  const PGroup G = groups[blockIdx.x];
+  const int ls = seg_log_s(G.n_blk, G.log_w, sub_cap);
+  const int n_sub = 1 << (G.log_w - ls);
+  const int64_t stride = seg_stride(G.n_blk, ls);
+  const int n_l = G.n_blk << ls;
+  int n2 = 1;
+  while (n2 < n_l) n2 <<= 1;
+  for (int sw = 0; sw < n_sub; sw++) {
+    if (threadIdx.x == 0) s_kept = 0;
+    __syncthreads();
+    int my_kept = 0;
+    for (int l = threadIdx.x; l < n2; l += kWinThreads) {
+      uint32_t key = 0xFFFFFFFFu;
+      if (l < n_l) {
+        int64_t i;
+        uint32_t sl = kNoSlot;
+        if (sub_sample(G, block_off, sw, ls, l, i)) sl = slot[i];
+        key = (sl << 16) | (uint32_t)l;
+        my_kept += sl != kNoSlot;
+      }
+      keys[l] = key;
+    }
+    atomicAdd(&s_kept, my_kept);
+    __syncthreads();
+    for (int k = 2; k <= n2; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = threadIdx.x; i < n2; i += kWinThreads) {
+          const int l = i ^ j;
+          if (l > i) {
+            const uint32_t a = keys[i], b = keys[l];
+            if ((a > b) == ((i & k) == 0)) {
+              keys[i] = b;
+              keys[l] = a;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    const int nk = s_kept;
+    const int64_t base = G.ent_off + (int64_t)sw * stride;
+    for (int j = threadIdx.x; j < stride; j += kWinThreads) {
+      uint32_t e = (uint32_t)kNoSlot << 16;
+      float a = 0.f;
+      if (j < nk) {
+        e = keys[j];
+        int64_t i;
+        sub_sample(G, block_off, sw, ls, (int)(e & 0xFFFFu), i);
+        a = __ldg(ang2 + i);
+      }
+      ent[base + j] = e;
+      ent_ang[base + j] = a;
+    }
+    if (threadIdx.x == 0) kept[G.sub0 + sw] = nk;
+    __syncthreads();   // the keys are rewritten by the next sub-window
+  }
+}
+
+constexpr int kSegSubMax = 16384;
+constexpr size_t kSegBuildSmemMax = (size_t)kSegSubMax * sizeof(uint32_t);
+constexpr size_t kPointSegSmemMax = (size_t)3 * kAccStride * sizeof(float) + (size_t)kSegSubMax * sizeof(float);
+
+static int pow2_at_least(int n) {
+  int p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+cudaError_t launch_seg_build(const PGroup* groups, int64_t n_groups, const int64_t* block_off,
+                             const uint16_t* slot, const float* ang2, int sub_cap, uint32_t* ent,
+                             float* ent_ang, int32_t* kept, cudaStream_t s) {
+  if (n_groups == 0) return cudaSuccess;
+  if (n_groups > 0x7fffffffLL || sub_cap < 32 || sub_cap > kSegSubMax) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)pow2_at_least(sub_cap) * sizeof(uint32_t);
+  static cudaError_t st = cudaSuccess;
+  static bool set = false;
+  MM_TRY_CUDA(smem_limit_once(k_seg_build, kSegBuildSmemMax, st, set));
+  k_seg_build<<<(unsigned)n_groups, kWinThreads, smem, s>>>(groups, block_off, slot, ang2, sub_cap, ent, ent_ang,
+                                                           kept);
+  return cudaGetLastError();
+}
+
+// One CTA per group and column.  Per sub-window: the sub-window's u into shared memory (one
+// coalesced pass over its chunks), then each thread reduces kSegRange consecutive sorted entries:
+// it sums (u, cos 2psi u, sin 2psi u) in registers along each run of equal slots and adds a run's
+// sums to the group's per-slot totals once, with a shared-memory atomic for the first and last run
+// of its range (which other threads may share) and a plain update for the runs between them (which
+// lie wholly in its range).  Last, one float4 global atomic per distinct pixel of the group.
+__global__ void __launch_bounds__(kWinThreads, 2) k_point_seg32(
+    const PGroup* __restrict__ groups, const int64_t* __restrict__ block_off, const uint32_t* __restrict__ ent,
+    const float* __restrict__ ent_ang, const int32_t* __restrict__ kept, const int32_t* __restrict__ slot_pix,
+    int sub_cap, const float* __restrict__ u, int64_t u_stride, int nrhs, const int32_t* __restrict__ done,
+    int done_stride, float4* __restrict__ y4, int64_t y_stride4) {
+  extern __shared__ __align__(16) float smem_f[];
+  float* acc = smem_f;                   // [3][kAccStride]
+  float* us = smem_f + 3 * kAccStride;   // [sub_cap] u of the sub-window, sample l at us[l]
+  const PGroup G = groups[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ls = seg_log_s(G.n_blk, G.log_w, sub_cap);
+  const int n_sub = 1 << (G.log_w - ls);
+  const int64_t stride = seg_stride(G.n_blk, ls);
+  PGroup S = G;   // the current sub-window as a group of window 2^log_s
+  S.log_w = ls;
+  const ChunkWalk cw = chunk_walk(S, lane);
+  const int n_pad = acc_index(G.n_slots);
+  for (int r = 0; r < nrhs; r++) {
+    if (done != nullptr && done[(int64_t)r * done_stride] != 0) continue;
+    const float* ur = u + r * u_stride;
+    for (int k = threadIdx.x; k < n_pad; k += kWinThreads) {
+      acc[k] = 0.f;
+      acc[kAccStride + k] = 0.f;
+      acc[2 * kAccStride + k] = 0.f;
+    }
+    for (int sw = 0; sw < n_sub; sw++) {
+      S.w0 = G.w0 + ((int64_t)sw << ls);
+      const int nk = __ldg(kept + G.sub0 + sw);
+      const int64_t base = G.ent_off + (int64_t)sw * stride;
+      const int n_rng = (nk + kSegRange - 1) / kSegRange;
+      // this thread's first range, loaded before the staging pass so both latencies overlap
+      uint4 pe[kSegRange / 4];
+      float4 pa[kSegRange / 4];
+      if ((int)threadIdx.x < n_rng) {
+        const uint4* ep = reinterpret_cast<const uint4*>(ent + base + (int64_t)threadIdx.x * kSegRange);
+        const float4* ap = reinterpret_cast<const float4*>(ent_ang + base + (int64_t)threadIdx.x * kSegRange);
+#pragma unroll
+        for (int v = 0; v < kSegRange / 4; v++) {
+          pe[v] = __ldcs(ep + v);
+          pa[v] = __ldcs(ap + v);
+        }
+      }
+      __syncthreads();   // the previous sub-window's u is no longer read (and the sums are cleared)
+      for (int c0 = warp * cw.cpi; c0 < S.n_blk; c0 += kWarps * cw.cpi) {
+        const int c = c0 + cw.sub;
+        if (c >= S.n_blk) continue;
+        int64_t lo;
+        int len;
+        group_chunk(S, block_off, c, lo, len);
+        const int l0 = c << ls;
+        visit_chunk(
+            S, block_off, c, cw,
+            [&](int64_t a0, int q) {
+              const int64_t i = a0 + 4 * (int64_t)q;
+              const float4 v = __ldcs(reinterpret_cast<const float4*>(ur + i));
+              const int l = l0 + (int)(i - lo);
+              us[l] = v.x;
+              us[l + 1] = v.y;
+              us[l + 2] = v.z;
+              us[l + 3] = v.w;
+            },
+            [&](int64_t i) { us[l0 + (int)(i - lo)] = __ldcs(ur + i); });
+      }
+      __syncthreads();
+      for (int g = threadIdx.x; g < n_rng; g += kWinThreads) {
+        if (g != (int)threadIdx.x) {
+          const uint4* ep = reinterpret_cast<const uint4*>(ent + base + (int64_t)g * kSegRange);
+          const float4* ap = reinterpret_cast<const float4*>(ent_ang + base + (int64_t)g * kSegRange);
+#pragma unroll
+          for (int v = 0; v < kSegRange / 4; v++) {
+            pe[v] = __ldcs(ep + v);
+            pa[v] = __ldcs(ap + v);
+          }
+        }
+        uint32_t cur = pe[0].x >> 16;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+        bool first = true;
+        auto flush = [&](bool shared_run) {
+          if (cur == kNoSlot) return;
+          const int k = acc_index((int)cur);
+          if (shared_run) {
+            atomicAdd(acc + k, s0);
+            atomicAdd(acc + kAccStride + k, s1);
+            atomicAdd(acc + 2 * kAccStride + k, s2);
+          } else {
+            acc[k] += s0;
+            acc[kAccStride + k] += s1;
+            acc[2 * kAccStride + k] += s2;
+          }
+        };
+#pragma unroll
+        for (int i = 0; i < kSegRange; i++) {
+          const uint4& e4 = pe[i / 4];
+          const float4& a4 = pa[i / 4];
+          const uint32_t e = (i % 4 == 0) ? e4.x : (i % 4 == 1) ? e4.y : (i % 4 == 2) ? e4.z : e4.w;
+          const float ang = (i % 4 == 0) ? a4.x : (i % 4 == 1) ? a4.y : (i % 4 == 2) ? a4.z : a4.w;
+          const uint32_t sl = e >> 16;
+          if (sl != cur) {
+            flush(first);
+            first = false;
+            cur = sl;
+            s0 = s1 = s2 = 0.f;
+          }
+          if (sl != kNoSlot) {
+            float cs, sn;
+            weights_of_angle(ang, cs, sn);
+            const float y = us[e & 0xFFFFu];
+            s0 += y;
+            s1 = fmaf(cs, y, s1);
+            s2 = fmaf(sn, y, s2);
+          }
+        }
+        flush(true);
+      }
+    }
+    __syncthreads();
+    float4* yr = y4 + r * y_stride4;
+    for (int k = threadIdx.x; k < G.n_slots; k += kWinThreads) {
+      const int32_t p = __ldg(slot_pix + G.slot_off + k);
+      const int j = acc_index(k);
+      atomicAdd(yr + p, make_float4(acc[j], acc[kAccStride + j], acc[2 * kAccStride + j], 0.f));
+    }
+    __syncthreads();   // the next column clears the sums
+  }
+}
+
+cudaError_t launch_point_seg32(const PGroup* groups, int64_t n_groups, const int64_t* block_off,
+                               const uint32_t* ent, const float* ent_ang, const int32_t* kept,
+                               const int32_t* slot_pix, int sub_cap, const float* u, int64_t u_stride,
+                               int nrhs, const int32_t* done, int done_stride, float* y4, int64_t y_stride,
+                               cudaStream_t s) {
+  if (n_groups == 0 || nrhs <= 0) return cudaSuccess;
+  if (n_groups > 0x7fffffffLL || u_stride % 4 != 0 || sub_cap < 32 || sub_cap > kSegSubMax)
+    return cudaErrorInvalidValue;
+  const size_t smem = (size_t)3 * kAccStride * sizeof(float) + (size_t)sub_cap * sizeof(float);
+  static cudaError_t st = cudaSuccess;
+  static bool set = false;
+  MM_TRY_CUDA(smem_limit_once(k_point_seg32, kPointSegSmemMax, st, set));
+  k_point_seg32<<<(unsigned)n_groups, kWinThreads, smem, s>>>(groups, block_off, ent, ent_ang, kept, slot_pix,
+                                                               sub_cap, u, u_stride, nrhs, done, done_stride,
+                                                               reinterpret_cast<float4*>(y4), y_stride / 4);
+  return cudaGetLastError();
+}
+
 // ---- FP32 right-hand side input: t = G d rounded to FP32 (0 at flagged and excised samples) ----
 template <typename D>
 __global__ void k_d_to_t32(const int32_t* __restrict__ lpix, const D* __restrict__ d, int64_t N, int64_t d_stride,

@@ -167,6 +167,7 @@ void free_plan(Plan* P) {
   dfree(P->map64_in); dfree(P->map64_out); dfree(P->td_a); dfree(P->td_b); dfree(P->t32);
   dfree(P->wdf); dfree(P->tabdf); dfree(P->twdf); dfree(P->tdf); dfree(P->mapdf);
   dfree(P->ang2); dfree(P->groups); dfree(P->slot); dfree(P->slot_pix); dfree(P->u32);
+  dfree(P->seg_ent); dfree(P->seg_ang); dfree(P->seg_kept);
   dfree(P->udf); dfree(P->amax);
   dfree(P->tc_tiles); dfree(P->tc_tab); dfree(P->tc_scale); dfree(P->tc_err);
   dfree(P->segs_big); dfree(P->tab32_big); dfree(P->tw32_big);
@@ -253,20 +254,24 @@ BandTables dedupe_bands(const std::vector<double>& band, int nb, int lam) {
 }
 
 // Overlap-save tiles of every block.  A block of n samples gets t = ceil(n / vmax) tiles with
-// vmax = L - 2 lambda - 4 rounded down to a multiple of 4, all with the same output step
-// vstep = ceil(n / t) rounded up to a multiple of 4 (so no tile is nearly empty).  Each tile's
-// input window starts at a multiple of 4 at most lambda + 3 samples before its first output.
+// vmax = L - 2 lambda - a rounded down to a multiple of 4, a = (block start - lambda) mod 4, all
+// with the same output step vstep = ceil(n / t) rounded up to a multiple of 4 (so no tile is
+// nearly empty).  Each tile's input window starts at the multiple of 4 a samples before
+// (first output - lambda), so its L inputs cover every output's band.
 // Tiles are grouped into segments of up to `max_steps` consecutive tiles (one CTA walks a
 // segment and keeps the overlap of consecutive windows); max_steps = 1 gives single tiles.
 std::vector<TileDesc> make_tiles(const std::vector<int64_t>& off, const BandTables& bt, int lam,
                                  int max_steps, int max_halo, int32_t* halo_out, int64_t L = kL) {
   std::vector<TileDesc> tiles;
-  const int64_t vmax = (L - 2 * (int64_t)lam - 4) & ~(int64_t)3;
   const int nb = (int)off.size() - 1;
   int32_t halo_used = 0;
   for (int b = 0; b < nb; b++) {
     const int64_t lo = off[b], hi = off[b + 1], n = hi - lo;
     if (n <= 0) continue;
+    // a tile's input starts at out_lo - lam rounded down to a multiple of 4 (a samples earlier),
+    // and its L inputs must reach out_hi + lam: vstep <= L - 2 lam - a (a multiple of 4)
+    const int64_t a = (((lo - lam) % 4) + 4) % 4;
+    const int64_t vmax = (L - 2 * (int64_t)lam - a) & ~(int64_t)3;
     const int64_t nt = (n + vmax - 1) / vmax;
     const int64_t vstep = (((n + nt - 1) / nt) + 3) & ~(int64_t)3;
     const int64_t halo = L - vstep;
@@ -303,6 +308,8 @@ int validate_desc(const mm_problem_desc* d) {
     return fail(MM_EINVAL, "lambda must lie in [0, " + std::to_string(kMaxLambda) + "]");
   if (!d->pix || !d->psi || !d->band) return fail(MM_EINVAL, "pix, psi and band must be non-NULL");
   if (d->tile_steps < 0) return fail(MM_EINVAL, "tile_steps must be >= 0");
+  if (d->pt_sub != 0 && d->pt_sub != 4096 && d->pt_sub != 8192 && d->pt_sub != 16384)
+    return fail(MM_EINVAL, "pt_sub must be 0, 4096, 8192 or 16384");
   if (d->precision != MM_FP64 && d->precision != MM_FP32 && d->precision != MM_DF64 &&
       d->precision != MM_FP32_DF64)
     return fail(MM_EINVAL, "bad precision");
@@ -383,10 +390,19 @@ int build_windows(Plan* P, cudaStream_t s) {
   // a rebuild (autotuning) replaces the previous windows; captured graphs must be captured again
   if (P->groups) {
     P->buf_gen++;
+    P->bytes -= (size_t)P->n_groups * sizeof(PGroup) + (size_t)P->N * sizeof(uint16_t) +
+                (size_t)std::max<int64_t>(P->n_slots_total, 1) * sizeof(int32_t);
     dfree(P->groups);
     dfree(P->slot);
     dfree(P->slot_pix);
     P->n_groups = 0;
+  }
+  if (P->seg_ent) {
+    P->bytes -= (size_t)P->n_ent * (sizeof(uint32_t) + sizeof(float)) + (size_t)P->n_sub_total * sizeof(int32_t);
+    dfree(P->seg_ent);
+    dfree(P->seg_ang);
+    dfree(P->seg_kept);
+    P->n_ent = P->n_sub_total = 0;
   }
   const std::vector<int64_t>& off = P->block_off;
   for (int b = 0; b < P->n_blocks; b++)
@@ -459,10 +475,18 @@ int build_windows(Plan* P, cudaStream_t s) {
     return a.b0 < b.b0;
   });
   int64_t total = 0;
+  const bool seg = P->precision == MM_FP32 && P->use_seg;   // pixel-sorted sub-windows (FP32 P^T)
+  int64_t n_ent = 0, n_sub = 0;
   for (PGroup& g : done) {
     g.slot_off = total;
     total += g.n_slots;
+    const int ls = seg_log_s(g.n_blk, g.log_w, P->seg_sub);
+    g.sub0 = (int32_t)n_sub;
+    g.ent_off = n_ent;
+    n_sub += (int64_t)1 << (g.log_w - ls);
+    n_ent += ((int64_t)1 << (g.log_w - ls)) * seg_stride(g.n_blk, ls);
   }
+  if (seg && n_sub > 0x7fffffffLL) return fail(MM_EINVAL, "pixel windows: too many sub-windows");
   P->n_groups = (int64_t)done.size();
   P->n_slots_total = total;
   P->win_repeat = total > 0 ? (double)P->N / (double)total : 0.0;
@@ -478,6 +502,15 @@ int build_windows(Plan* P, cudaStream_t s) {
   MM_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   MM_CUDA(cudaStreamSynchronize(s));
   if (herr != 0) return fail(MM_ECUDA, "pixel windows: slot tables do not match the counts");
+  if (seg) {
+    MM_TRY(dalloc(P, &P->seg_ent, (size_t)n_ent));
+    MM_TRY(dalloc(P, &P->seg_ang, (size_t)n_ent));
+    MM_TRY(dalloc(P, &P->seg_kept, (size_t)n_sub));
+    P->n_ent = n_ent;
+    P->n_sub_total = n_sub;
+    MM_CUDA(launch_seg_build(P->groups, P->n_groups, P->block_off_dev, P->slot, P->ang2, P->seg_sub, P->seg_ent,
+                             P->seg_ang, P->seg_kept, s));
+  }
   return MM_OK;
 }
 
@@ -496,6 +529,8 @@ int build_plan(const mm_problem_desc* d, cudaStream_t us, Plan* P) {
           (d->toeplitz_algo == MM_TPLZ_GEMM || (d->toeplitz_algo == MM_TPLZ_AUTO && d->lambda <= kTcAutoLambda));
   P->df64 = (d->precision == MM_DF64 || d->precision == MM_FP32_DF64) && P->algo == MM_TPLZ_FFT;
   P->cond_max = d->cond_max > 0 ? d->cond_max : 1e3;
+  P->use_seg = d->pt_sub > 0;
+  if (d->pt_sub > 0) P->seg_sub = d->pt_sub;
   const int nb = P->n_blocks, lam = P->lambda;
   P->block_off.assign(nb + 1, 0);
   for (int b = 0; b < nb; b++) {
@@ -962,6 +997,17 @@ int ensure_t32(Plan* P, int nrhs) {
   return MM_OK;
 }
 
+// y4 += P^T u (FP32) of a plan with pixel windows: segment reduction over the pixel-sorted
+// sub-windows, or per-sample shared-memory sums over the windows
+cudaError_t point32(Plan* P, const float* u, int64_t u_stride, int nrhs, const int32_t* done, int done_stride,
+                    float* y4, int64_t y_stride, cudaStream_t s) {
+  if (P->use_seg && P->seg_ent)
+    return launch_point_seg32(P->groups, P->n_groups, P->block_off_dev, P->seg_ent, P->seg_ang, P->seg_kept,
+                              P->slot_pix, P->seg_sub, u, u_stride, nrhs, done, done_stride, y4, y_stride, s);
+  return launch_point_win32(P->groups, P->n_groups, P->block_off_dev, P->slot, P->slot_pix, P->ang2, u, u_stride,
+                            nrhs, done, done_stride, y4, y_stride, s);
+}
+
 // y32 (accumulated, pre-zeroed) += A x32 in FP32, [nrhs][n_obs][4] float.  Profiling events: mid
 // after P (t = P x), mid2 after N^-1 (pixel windows only).
 int apply32_internal(Plan* P, const float* x32, float* y32, int nrhs, cudaStream_t s,
@@ -1002,8 +1048,7 @@ int apply32_internal(Plan* P, const float* x32, float* y32, int nrhs, cudaStream
       if (mid && r0 == 0) MM_CUDA(cudaEventRecord(mid, s));
       MM_TRY(ninv32(P, P->t32, P->u32, ts, g, dn, done_stride, s));
       if (mid2 && r0 + kc >= nrhs) MM_CUDA(cudaEventRecord(mid2, s));
-      MM_CUDA(launch_point_win32(P->groups, P->n_groups, P->block_off_dev, P->slot, P->slot_pix, P->ang2, P->u32,
-                                 ts, g, dn, done_stride, y32 + (size_t)r0 * ms, ms, s));
+      MM_CUDA(point32(P, P->u32, ts, g, dn, done_stride, y32 + (size_t)r0 * ms, ms, s));
     }
     return MM_OK;
   }
@@ -1042,8 +1087,7 @@ int rhs32_internal(Plan* P, const void* d, int d_is_fp32, int nrhs, double* b4, 
     MM_CUDA(launch_d_to_t32(P->lpix, reinterpret_cast<const char*>(d) + (size_t)r0 * P->N * esz, d_is_fp32, P->N, g,
                             P->t32, ts, s));
     MM_TRY(ninv32(P, P->t32, P->u32, ts, g, nullptr, 0, s));
-    MM_CUDA(launch_point_win32(P->groups, P->n_groups, P->block_off_dev, P->slot, P->slot_pix, P->ang2, P->u32, ts,
-                               g, nullptr, 0, P->map32_out + (size_t)r0 * ms, ms, s));
+    MM_CUDA(point32(P, P->u32, ts, g, nullptr, 0, P->map32_out + (size_t)r0 * ms, ms, s));
   }
   MM_CUDA(launch_to64(P->map32_out, (int64_t)nrhs * P->n_obs, b4, s));
   return MM_OK;
@@ -2091,7 +2135,32 @@ int mm_autotune(mm_plan_t plan, int max_width, mm_tune_info* out, void* stream) 
     }
   }
   P->win_samples = best_win;
+  // 2b. the FP32 P^T: per-sample sums over the windows, or segment reduction over pixel-sorted
+  // sub-windows of a few sizes (each size rebuilds the windows)
+  int best_seg = 0;
+  if (P->precision == MM_FP32) {
+    best = 1e300;
+    const int seg_c[] = {0, 4096, 8192, 16384};
+    for (int v : seg_c) {
+      P->use_seg = v > 0;
+      if (v > 0 && v != P->seg_sub) P->seg_sub = v;
+      MM_TRY(build_windows(P, P->stream));
+      double ms = 0.0;
+      bool pass = false;
+      MM_TRY(time_apply32(P, 1, kReps, &ms));
+      MM_TRY(check(&pass));
+      out->seg_cand[out->n_seg] = v;
+      out->seg_ms[out->n_seg++] = ms;
+      if (pass && ms < best) {
+        best = ms;
+        best_seg = v;
+      }
+    }
+  }
+  P->use_seg = best_seg > 0;
+  if (best_seg > 0) P->seg_sub = best_seg;
   MM_TRY(build_windows(P, P->stream));
+  out->seg_sub = best_seg;
   out->apply_ms = best;
   // 3. block width: device time per column of a batched A X
   double best_col = 1e300;

@@ -78,10 +78,27 @@ struct PGroup {
   int32_t b_stride;  // block index step (n_int: the same interval of consecutive detectors)
   int32_t log_w;     // window length W = 2^log_w
   int32_t n_slots;   // distinct kept pixels (0 .. kWinCap)
-  int32_t pad;
+  int32_t sub0;      // first sub-window of the group in the plan's sub-window list
   int64_t w0;        // window start, samples from each block's start
   int64_t slot_off;  // first entry of the group's pixel-sorted slot table
+  int64_t ent_off;   // first pixel-sorted entry of the group's sub-windows
 };
+
+// Pixel-sorted sub-windows (P^T by segment reduction).  Sub-window s of a group is the window
+// [w0 + s 2^log_s, w0 + (s + 1) 2^log_s) of every block of the group, log_s the largest with
+// n_blk 2^log_s <= sub_cap; its samples are numbered l = c 2^log_s + o (chunk c, offset o).  The
+// plan stores, per sub-window, its entries (slot << 16 | l) sorted ascending, so every slot's
+// samples form one run, masked samples (slot kNoSlot) and padding last, with each entry's angle
+// beside it; a sub-window holds seg_stride(n_blk, log_s) entries (a multiple of 16).
+constexpr int kSegRange = 16;              // entries one thread reduces at a time
+__host__ __device__ inline int seg_log_s(int n_blk, int log_w, int sub_cap) {
+  int ls = log_w;
+  while (ls > 0 && ((int64_t)n_blk << ls) > sub_cap) ls--;
+  return ls;
+}
+__host__ __device__ inline int64_t seg_stride(int n_blk, int log_s) {
+  return ((((int64_t)n_blk << log_s) + kSegRange - 1) / kSegRange) * kSegRange;
+}
 
 // ---------------------------------------------------------------------------------------------
 // Tensor-core banded Toeplitz product (k_tc_toeplitz.cu): tiles of 128 rows x 32 samples of one
@@ -212,6 +229,15 @@ struct Plan {
   uint32_t* amax = nullptr;            // [amax_cap] per column: bits of max |u| of the df64 tiles
   size_t amax_cap = 0;
   double win_repeat = 0.0;             // kept samples per (group, pixel) pair: the P^T reduction factor
+  // pixel-sorted sub-windows of the groups (P^T by segment reduction; FP32 operators)
+  bool use_seg = false;                // the FP32 P^T reduces pixel-sorted runs (else per-sample
+                                       // shared-memory atomics over the windows)
+  int32_t seg_sub = 8192;              // most samples of a sub-window
+  uint32_t* seg_ent = nullptr;         // [n_ent] sorted entries (slot << 16 | l)
+  float* seg_ang = nullptr;            // [n_ent] 2 psi of each entry
+  int32_t* seg_kept = nullptr;         // [n_sub_total] kept samples of each sub-window
+  int64_t n_ent = 0;
+  int64_t n_sub_total = 0;
 
   // work buffers (grown on demand)
   float* map32_in = nullptr;  size_t map32_in_cap = 0;
@@ -332,6 +358,16 @@ cudaError_t launch_point_win_df(const PGroup* groups, int64_t n_groups, const in
                                 const float2* u, int64_t u_stride, const uint32_t* amax, int nrhs,
                                 const int32_t* done, int done_stride, double* y4, int64_t y_stride,
                                 cudaStream_t s);
+// pixel-sorted entries of every sub-window of the groups (groups' sub0 and ent_off set)
+cudaError_t launch_seg_build(const PGroup* groups, int64_t n_groups, const int64_t* block_off,
+                             const uint16_t* slot, const float* ang2, int sub_cap, uint32_t* ent,
+                             float* ent_ang, int32_t* kept, cudaStream_t s);
+// y4 [nrhs][y_stride] += P^T u (FP32) by segment reduction over the pixel-sorted sub-windows
+cudaError_t launch_point_seg32(const PGroup* groups, int64_t n_groups, const int64_t* block_off,
+                               const uint32_t* ent, const float* ent_ang, const int32_t* kept,
+                               const int32_t* slot_pix, int sub_cap, const float* u, int64_t u_stride,
+                               int nrhs, const int32_t* done, int done_stride, float* y4, int64_t y_stride,
+                               cudaStream_t s);
 // y4 [nrhs][y_stride] += P^T u (FP32) over the windows, u [nrhs][u_stride]
 cudaError_t launch_point_win32(const PGroup* groups, int64_t n_groups, const int64_t* block_off,
                                const uint16_t* slot, const int32_t* slot_pix, const float* psi,

@@ -44,7 +44,8 @@ class ProblemDesc(ctypes.Structure):
                 ("pix", ctypes.c_void_p), ("psi", ctypes.c_void_p), ("lambda_", ctypes.c_int32),
                 ("band", ctypes.c_void_p), ("cond_max", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("toeplitz_algo", ctypes.c_int32),
-                ("inputs_on_device", ctypes.c_int32), ("tile_steps", ctypes.c_int32)]
+                ("inputs_on_device", ctypes.c_int32), ("tile_steps", ctypes.c_int32),
+                ("pt_sub", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -71,7 +72,9 @@ class TuneInfo(ctypes.Structure):
                 ("win_cand", ctypes.c_int32 * 8), ("win_ms", ctypes.c_double * 8),
                 ("width_cand", ctypes.c_int32 * 8), ("width_ms_per_col", ctypes.c_double * 8),
                 ("apply_ms", ctypes.c_double), ("big_tiles", ctypes.c_int32), ("big_tiles_ms", ctypes.c_double),
-                ("max_rel_dev", ctypes.c_double), ("n_rejected", ctypes.c_int32)]
+                ("max_rel_dev", ctypes.c_double), ("n_rejected", ctypes.c_int32),
+                ("seg_sub", ctypes.c_int32), ("n_seg", ctypes.c_int32), ("seg_cand", ctypes.c_int32 * 4),
+                ("seg_ms", ctypes.c_double * 4)]
 
 
 class MMError(RuntimeError):
@@ -185,7 +188,7 @@ class Plan:
 def mm_plan(n_det: int, n_int: int, block_len: Sequence[int], n_pix: int, pix: torch.Tensor,
             psi: torch.Tensor, lam: int, band: torch.Tensor, cond_max: float = 1e3,
             precision: int = MM_FP64, toeplitz_algo: int = MM_TPLZ_AUTO, tile_steps: int = 0,
-            stream=None) -> Plan:
+            pt_sub: int = 0, stream=None) -> Plan:
     """Build a plan.  pix/psi/band are either all CUDA tensors or all CPU tensors."""
     on_dev = pix.is_cuda
     if (psi.is_cuda != on_dev) or (band.is_cuda != on_dev):
@@ -198,7 +201,7 @@ def mm_plan(n_det: int, n_int: int, block_len: Sequence[int], n_pix: int, pix: t
     d = ProblemDesc(n_det=n_det, n_int=n_int, block_len=bl, n_pix=n_pix, pix=_ptr(pix),
                     psi=_ptr(psi), lambda_=lam, band=_ptr(band), cond_max=cond_max,
                     precision=precision, toeplitz_algo=toeplitz_algo,
-                    inputs_on_device=1 if on_dev else 0, tile_steps=tile_steps)
+                    inputs_on_device=1 if on_dev else 0, tile_steps=tile_steps, pt_sub=pt_sub)
     h = ctypes.c_void_p()
     _check(_lib.mm_plan(ctypes.byref(d), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)))
     n_obs = ctypes.c_int64()
@@ -327,7 +330,8 @@ def mm_autotune(plan: Plan, max_width: int = 64, stream=None) -> dict:
             "max_rel_dev": t.max_rel_dev, "n_rejected": t.n_rejected,
             "steps_ms": {t.steps_cand[i]: t.steps_ms[i] for i in range(t.n_steps)},
             "win_ms": {t.win_cand[i]: t.win_ms[i] for i in range(t.n_win)},
-            "width_ms_per_col": {t.width_cand[i]: t.width_ms_per_col[i] for i in range(t.n_width)}}
+            "width_ms_per_col": {t.width_cand[i]: t.width_ms_per_col[i] for i in range(t.n_width)},
+            "seg_sub": t.seg_sub, "seg_ms": {t.seg_cand[i]: t.seg_ms[i] for i in range(t.n_seg)}}
 
 
 def mm_block_cg_solve(plan: Plan, b: torch.Tensor, x: torch.Tensor, block_width: int = 0,

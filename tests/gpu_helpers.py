@@ -11,7 +11,7 @@ def mm():
     return m
 
 
-def plans(prob: synth.Problem, precision=0, algo=0, cond_max=1e3, on_device=True, tile_steps=0):
+def plans(prob: synth.Problem, precision=0, algo=0, cond_max=1e3, on_device=True, tile_steps=0, pt_sub=0):
     m = mm()
     dev = torch.device("cuda")
     if on_device:
@@ -20,7 +20,7 @@ def plans(prob: synth.Problem, precision=0, algo=0, cond_max=1e3, on_device=True
         pix, psi, band = prob.pix.cpu(), prob.psi.cpu(), prob.band.cpu()
     gp = m.mm_plan(prob.n_det, prob.n_int, prob.block_len.tolist(), prob.n_pix, pix.contiguous(),
                    psi.contiguous(), prob.lam, band.contiguous(), cond_max=cond_max,
-                   precision=precision, toeplitz_algo=algo, tile_steps=tile_steps)
+                   precision=precision, toeplitz_algo=algo, tile_steps=tile_steps, pt_sub=pt_sub)
     nb = synth.to_numpy(prob)
     op = O.make_plan(nb["pix"], nb["psi"], nb["block_len"], nb["band"], nb["n_pix"],
                      cond_max=cond_max)

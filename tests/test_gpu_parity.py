@@ -136,6 +136,42 @@ def test_apply_A_fp32_large_lambda_matches_oracle(lam):
         assert rel_max(y[r].cpu().numpy(), O.apply_A(op, x[r].cpu().numpy())) < 2e-5
 
 
+@pytest.mark.parametrize("n_pix", [1, 7, 300])
+@pytest.mark.parametrize("pt_sub", [4096, 8192, 16384])
+def test_apply_A_fp32_segment_reduction_matches_oracle(n_pix, pt_sub):
+    """The FP32 P^T by segment reduction over pixel-sorted sub-windows.  One or seven pixels make
+    runs that span many threads' ranges (their partial sums meet in shared-memory atomics); 300
+    pixels make short runs inside one range; ragged blocks (5, 12 samples, empty) and masked
+    samples leave sub-windows partly empty.  A x within the FP32 tolerance of the oracle, for
+    every sub-window size, several columns."""
+    prob = small(13, block_len=(70001, 5, 33000, 12, 0, 9000), n_pix=n_pix, lam=256, gap=0.05)
+    m = mm()
+    gp, op, _ = plans(prob, precision=m.MM_FP32_DF64, pt_sub=pt_sub)
+    rng = np.random.default_rng(n_pix)
+    x = cuda(rng.standard_normal((2, op.n_obs, 3)))
+    y = torch.empty_like(x)
+    m.mm_apply_A(gp, x, y)
+    for r in range(2):
+        assert rel_max(y[r].cpu().numpy(), O.apply_A(op, x[r].cpu().numpy())) < 2e-5
+
+
+def test_autotune_times_both_pt_forms():
+    """mm_autotune times P^T by per-sample sums over the windows and by segment reduction (three
+    sub-window sizes), checks each candidate's A x against the first's, keeps the fastest, and
+    the tuned operator still matches the oracle."""
+    prob = small(14, block_len=(70001, 5, 33000, 12, 0, 9000), n_pix=7, lam=256, gap=0.05)
+    m = mm()
+    gp, op, _ = plans(prob, precision=m.MM_FP32_DF64)
+    tune = m.mm_autotune(gp, max_width=1)
+    assert sorted(tune["seg_ms"]) == [0, 4096, 8192, 16384]
+    assert tune["seg_ms"][tune["seg_sub"]] == min(tune["seg_ms"].values())
+    assert tune["n_rejected"] == 0 and tune["max_rel_dev"] < 2e-5
+    x = cuda(np.random.default_rng(3).standard_normal((op.n_obs, 3)))
+    y = torch.empty_like(x)
+    m.mm_apply_A(gp, x, y)
+    assert rel_max(y.cpu().numpy(), O.apply_A(op, x.cpu().numpy())) < 2e-5
+
+
 def test_apply_A_multi_rhs():
     prob = small(7)
     gp, op, _ = plans(prob)
@@ -295,6 +331,10 @@ def test_invalid_inputs_rejected():
         m.mm_plan(prob.n_det, 1, prob.block_len.tolist(), prob.n_pix, allgap.cuda(),
                   prob.psi.cuda(), prob.lam, prob.band.cuda())
     assert e.value.code == m.MM_ENOTSPD
+    with pytest.raises(m.MMError) as e:   # not a sub-window size of the segment reduction
+        m.mm_plan(prob.n_det, 1, prob.block_len.tolist(), prob.n_pix, prob.pix.cuda(),
+                  prob.psi.cuda(), prob.lam, prob.band.cuda(), precision=m.MM_FP32, pt_sub=5000)
+    assert e.value.code == m.MM_EINVAL
 
 
 # ----------------------------------------------------------------------- arbitrary flag patterns
