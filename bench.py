@@ -58,6 +58,8 @@ def args_parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--dets", type=int, default=512, help="detectors (512 = the full workload)")
+    p.add_argument("--samples", type=int, default=524288,
+                   help="samples per block (524288 = the full workload; fewer: a cut for profiling)")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -382,7 +384,7 @@ def run_ours(a):
         torch.cuda.synchronize()
 
     # replicas: each rank solves its own problem (independent seeds per rank)
-    cfg = synth.ground_config(n_det=a.dets)
+    cfg = synth.ground_config(n_det=a.dets, n_samp=a.samples)
     t_gen = time.perf_counter()
     prob = synth.make_ground_problem(cfg, device=dev, real_offset=1000 * rank)
     torch.cuda.synchronize()
@@ -705,7 +707,9 @@ def run_ecg(a):
                    "precision": "FP32 search blocks and operator, FP64 X/R and t x t, df64 true residual"},
         "pcg": {"iters": ipcg.iters, "s": tpcg, "s_per_iter": tpcg / max(ipcg.iters, 1),
                 "samples_per_s_through_A": N * ipcg.iters / tpcg},
-        "ecg": res}
+        "ecg": res,
+        "orthomin_t1_s_per_iter_vs_pcg": (res["orthomin_t1"]["s_per_iter"] / (tpcg / max(ipcg.iters, 1))
+                                          if "orthomin_t1" in res else None)}
 
 
 def run_noise(a):
@@ -1018,7 +1022,7 @@ def run_crossover(a):
     tf32_peak = float(pk.get("bf16_tflops", 1900.0)) * 1.1 / 2.25   # nominal TF32:BF16 dense ratio
     rows = []
     for lam in [int(v) for v in a.lams.split(",")]:
-        cfg = synth.ground_config(n_det=a.dets, lam=lam)
+        cfg = synth.ground_config(n_det=a.dets, n_samp=a.samples, lam=lam)
         prob = synth.make_ground_problem(cfg, device=dev, with_noise=False)
         res, maps = {}, {}
         for algo, name in ((mm.MM_TPLZ_FFT, "fft"), (mm.MM_TPLZ_GEMM, "gemm")):

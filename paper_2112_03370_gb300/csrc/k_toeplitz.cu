@@ -389,6 +389,12 @@ __device__ __forceinline__ void scatter_pairs(const TileArgs& a, int rhs, const 
   }
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16; a hint, no completion to wait for).
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(bytes)
+               : "memory");
+}
+
 // ---- fused stride-1 passes and pair update (FP32 tiles) ----------------------------------------
 // After the three radix-16 passes of the forward transform (M = 2^14), position j of the
 // digit-reversed layout holds the partial transform of frequency k with j = [d0|d1|d2|r]
@@ -414,22 +420,50 @@ __device__ __forceinline__ C pair_upd(C ab, C z, C zp, T sc) {
   return C{sc * (ab.x * z.x + ab.y * zp.y), sc * (ab.x * z.y + ab.y * zp.x)};
 }
 
+// The u-th quad q <= partner_quad(q) (2049 of them): a in 1..7; a = 8 with b < 8; a = 0 with b in
+// 1..7; a = 0, b = 8 with c < 8; a = b = 0 with c in 1..7; then the two quads that pair with
+// themselves, 8 and 0.
+__device__ __forceinline__ int leader_quad(int u) {
+  if (u < 1792) return ((1 + (u >> 8)) << 8) | (u & 255);
+  if (u < 1920) return (8 << 8) | (u - 1792);
+  if (u < 2032) return ((1 + ((u - 1920) >> 4)) << 4) | ((u - 1920) & 15);
+  if (u < 2040) return (8 << 4) | (u - 2032);
+  if (u < 2047) return 1 + (u - 2040);
+  return u == 2047 ? 8 : 0;
+}
+constexpr int kLeaderQuads = 2049;
+
 template <typename C, typename T>
 __device__ __forceinline__ void fused_rem_pair(C* sm, const C* __restrict__ tab, T sc) {
   static_assert(kLogM == 14, "the quad pairing assumes 3 radix-16 passes and a radix-4 pass");
-  constexpr int NQ = kM / 4;
-  for (int q = threadIdx.x; q < NQ; q += kTileThreads) {
+  for (int u = threadIdx.x; u < kLeaderQuads; u += kTileThreads) {
+    const int q = leader_quad(u);
     const int p = partner_quad(q);
-    if (p < q) continue;
     C za[4], zb[4], ta[4], tb[4];
     C* qa = sm + smem_pad(4 * q);   // 4 consecutive positions never cross a padding group
     C* qb = sm + smem_pad(4 * p);
+    if constexpr (std::is_same<C, float2>::value) {   // a quad's 4 table entries: two 16-byte loads
+      const float4* t4a = reinterpret_cast<const float4*>(tab + 4 * q);
+      const float4* t4b = reinterpret_cast<const float4*>(tab + 4 * p);
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const float4 va = __ldg(t4a + h), vb = __ldg(t4b + h);
+        ta[2 * h] = C{va.x, va.y};
+        ta[2 * h + 1] = C{va.z, va.w};
+        tb[2 * h] = C{vb.x, vb.y};
+        tb[2 * h + 1] = C{vb.z, vb.w};
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        ta[e] = ldg_c(tab + 4 * q + e);
+        tb[e] = ldg_c(tab + 4 * p + e);
+      }
+    }
 #pragma unroll
     for (int e = 0; e < 4; e++) {
       za[e] = qa[e];
       zb[e] = qb[e];
-      ta[e] = ldg_c(tab + 4 * q + e);
-      tb[e] = ldg_c(tab + 4 * p + e);
     }
     dft_small<4, true>(za);
     dft_small<4, true>(zb);
@@ -539,6 +573,17 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs a_in) {
         }
       }
       __syncthreads();
+      if constexpr (MODE == MODE_NINV_T && std::is_same<T, float>::value) {
+        // the next tile's new input samples [in0 + L, in0 + L + vstep) start on their way to L2 now,
+        // so its gather finds them there instead of waiting on DRAM
+        if (threadIdx.x == 0 && step + 1 < n_steps) {
+          int64_t lo = max(td.in0 + LT, td.blk_lo), hi = min(td.in0 + LT + (int64_t)seg.vstep, td.blk_hi);
+          lo = (lo + 3) & ~(int64_t)3;   // 16-byte aligned and inside the block
+          hi &= ~(int64_t)3;
+          if (hi > lo)
+            prefetch_l2_bulk(reinterpret_cast<const float*>(a.x) + rhs * a.x_stride + lo, (uint32_t)((hi - lo) * 4));
+        }
+      }
       if (step + 1 < n_steps) {   // keep input samples [vstep, L) for the next tile
         const int n0 = seg.vstep / 2;
         for (int n = threadIdx.x; n < 2 * halo_q; n += NT) {

@@ -81,6 +81,10 @@ struct BlkState {
   // enlarged CG: previous search block (Orthodir), accumulated solution, residual, A x
   float *Pp = nullptr, *APp = nullptr;                               // [s][n][4] FP32
   double *xe = nullptr, *re = nullptr, *ax = nullptr;                // [n][4] FP64
+  // captured parts of a block iteration (FP32 operators), by shape; they hold raw pointers into
+  // this state and the plan, valid while neither is reallocated (graph_gen = the plan's buf_gen)
+  std::unordered_map<uint64_t, cudaGraphExec_t> graphs;
+  uint64_t graph_gen = 0;
 };
 
 // Two-level deflation space and its per-solve work buffers.
@@ -135,7 +139,39 @@ void free_blk(BlkState* b) {
   dfree(b->T64); dfree(b->Pp); dfree(b->APp); dfree(b->xe); dfree(b->re); dfree(b->ax);
   if (b->host) cudaFreeHost(b->host);
   if (b->host_i) cudaFreeHost(b->host_i);
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
   delete b;
+}
+
+// Replay on s the captured graph of `key` (bits 60-63: 1, 2 the two parts of a block CG iteration,
+// 3, 4 those of an enlarged-CG iteration; below: the shape), capturing enqueue() into it first when it is absent
+// or when the plan's buffers were reallocated since the graphs were captured.
+template <typename F>
+int blk_graph(Plan* P, BlkState* b, uint64_t key, cudaStream_t s, F&& enqueue) {
+  if (b->graph_gen != P->buf_gen) {
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+    b->graph_gen = P->buf_gen;
+  }
+  auto it = b->graphs.find(key);
+  if (it == b->graphs.end()) {
+    cudaGraph_t g = nullptr;
+    MM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const int st = enqueue();
+    const cudaError_t ce = cudaStreamEndCapture(s, &g);
+    if (st != MM_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    MM_CUDA(ce);
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    MM_CUDA(ie);
+    it = b->graphs.emplace(key, ex).first;
+  }
+  MM_CUDA(cudaGraphLaunch(it->second, s));
+  return MM_OK;
 }
 
 void free_defl(DeflState* d) {
@@ -2240,6 +2276,7 @@ int mm_block_cg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, int 
   cudaStream_t s = P->stream;
   BlkState* B = nullptr;
   MM_TRY(ensure_blk(P, sw, &B));
+  if (fp32) MM_TRY(ensure_t32(P, sw));   // the captured iterations must find the FP32 buffers allocated
   cudaEvent_t ev;
   MM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   MM_CUDA(cudaEventRecord(ev, us));
@@ -2298,26 +2335,37 @@ int mm_block_cg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, int 
     while (!active.empty()) {
       const int t = (int)active.size();
       const bool after_restart = fresh;
+      if (it >= opts->max_iter) break;
       MM_CUDA(cudaMemcpyAsync(B->idx, active.data(), t * sizeof(int), cudaMemcpyHostToDevice, s));
-      MM_CUDA(launch_bprecond(P->minv, B->R, B->idx, t, n, B->Z, s));   // Z = M R[active]
-      n_kernels += 1;
-      if (!fresh && r > 0) {   // Z = (I - P P^T A) M R: Z -= P (AP^T Z)
-        MM_CUDA(launch_bgram(B->AP, r, nullptr, B->Z, 0, t, nullptr, n, B->part, blk_ctas(), B->C2, s));
-        MM_CUDA(launch_bcombine(B->Z, 0, nullptr, t, B->P, r, B->C2, t, -1.0, 1, n, nullptr, blk_ctas(),
-                                nullptr, s));
-        n_kernels += 3;
+      // Z = M R[active], A-orthogonalised against the previous block; AZ = A Z; G = Z^T A Z and
+      // its pivoted Cholesky factor (rank r to the host).  FP32 operators: one captured graph per
+      // (t, previous r) shape, replayed every iteration of that shape.
+      const bool ortho = !fresh && r > 0;
+      const int r_prev = r;
+      auto part_a = [&]() -> int {
+        MM_CUDA(launch_bprecond(P->minv, B->R, B->idx, t, n, B->Z, s));
+        if (ortho) {   // Z = (I - P P^T A) M R: Z -= P (AP^T Z)
+          MM_CUDA(launch_bgram(B->AP, r_prev, nullptr, B->Z, 0, t, nullptr, n, B->part, blk_ctas(), B->C2, s));
+          MM_CUDA(launch_bcombine(B->Z, 0, nullptr, t, B->P, r_prev, B->C2, t, -1.0, 1, n, nullptr, blk_ctas(),
+                                  nullptr, s));
+        }
+        MM_TRY(blk_apply(P, B, t, fp32, s));
+        MM_CUDA(launch_bgram(B->Z, t, nullptr, B->AZ, 0, t, nullptr, n, B->part, blk_ctas(), B->G, s));
+        MM_CUDA(launch_bchol(B->G, t, 1e-10, B->Linv, B->piv, B->rank, s));
+        MM_CUDA(cudaMemcpyAsync(B->host_i, B->rank, sizeof(int), cudaMemcpyDeviceToHost, s));
+        return MM_OK;
+      };
+      if (fp32) {
+        const uint64_t key = (1ull << 60) | ((uint64_t)t << 16) | ((uint64_t)ortho << 15) | (uint64_t)r_prev;
+        MM_TRY(blk_graph(P, B, key, s, part_a));
+      } else {
+        MM_TRY(part_a());
       }
       fresh = false;
-      if (it >= opts->max_iter) break;
-      MM_TRY(blk_apply(P, B, t, fp32, s));                                 // AZ = A Z
-      n_kernels += fp32 ? 1 : 3;
-      n_apply += 1;
-      MM_CUDA(launch_bgram(B->Z, t, nullptr, B->AZ, 0, t, nullptr, n, B->part, blk_ctas(), B->G, s));
-      MM_CUDA(launch_bchol(B->G, t, 1e-10, B->Linv, B->piv, B->rank, s));
-      MM_CUDA(cudaMemcpyAsync(B->host_i, B->rank, sizeof(int), cudaMemcpyDeviceToHost, s));
       MM_CUDA(cudaStreamSynchronize(s));
       r = B->host_i[0];
-      n_kernels += 3;
+      n_kernels += 1 + (ortho ? 3 : 0) + (fp32 ? 1 : 3) + 3;
+      n_apply += 1;
       if (r == 0) {
         // every direction dropped: on the FP32 path away from a restart this is operator noise
         // along a (near-)null direction of a semi-definite A (e.g. the map offset degenerate with
@@ -2330,18 +2378,30 @@ int mm_block_cg_solve(mm_plan_t plan, const double* b, double* x, int nrhs, int 
         for (int j : active) status[j] = MM_EBREAKDOWN;
         break;
       }
-      MM_CUDA(launch_linv_coef(B->Linv, B->piv, B->rank, t, B->Cmb, s));
-      MM_CUDA(launch_bcombine(B->P, 0, nullptr, r, B->Z, t, B->Cmb, t, 1.0, 0, n, nullptr, blk_ctas(), nullptr, s));
-      MM_CUDA(launch_bcombine(B->AP, 0, nullptr, r, B->AZ, t, B->Cmb, t, 1.0, 0, n, nullptr, blk_ctas(), nullptr, s));
-      // alpha = P^T R over all sg columns; X += P alpha; R -= AP alpha
-      MM_CUDA(launch_bgram(B->P, r, nullptr, B->R, 1, sg, nullptr, n, B->part, blk_ctas(), B->alpha, s));
-      MM_CUDA(launch_bcombine(B->X, 1, nullptr, sg, B->P, r, B->alpha, sg, 1.0, 1, n, nullptr, blk_ctas(),
-                              nullptr, s));
-      MM_CUDA(launch_bcombine(B->R, 1, nullptr, sg, B->AP, r, B->alpha, sg, -1.0, 1, n, B->norm_part,
-                              blk_ctas(), B->norms, s));
+      // P = Z[piv] L^-T, AP likewise; alpha = P^T R over all sg columns; X += P alpha; R -= AP alpha
+      // and the residual norms to the host (FP32 operators: one captured graph per (t, r, sg))
+      auto part_b = [&]() -> int {
+        MM_CUDA(launch_linv_coef(B->Linv, B->piv, B->rank, t, B->Cmb, s));
+        MM_CUDA(launch_bcombine(B->P, 0, nullptr, r, B->Z, t, B->Cmb, t, 1.0, 0, n, nullptr, blk_ctas(), nullptr, s));
+        MM_CUDA(launch_bcombine(B->AP, 0, nullptr, r, B->AZ, t, B->Cmb, t, 1.0, 0, n, nullptr, blk_ctas(), nullptr,
+                                s));
+        MM_CUDA(launch_bgram(B->P, r, nullptr, B->R, 1, sg, nullptr, n, B->part, blk_ctas(), B->alpha, s));
+        MM_CUDA(launch_bcombine(B->X, 1, nullptr, sg, B->P, r, B->alpha, sg, 1.0, 1, n, nullptr, blk_ctas(),
+                                nullptr, s));
+        MM_CUDA(launch_bcombine(B->R, 1, nullptr, sg, B->AP, r, B->alpha, sg, -1.0, 1, n, B->norm_part,
+                                blk_ctas(), B->norms, s));
+        MM_CUDA(cudaMemcpyAsync(B->host, B->norms, sg * sizeof(double), cudaMemcpyDeviceToHost, s));
+        return MM_OK;
+      };
+      if (fp32) {
+        const uint64_t key = (2ull << 60) | ((uint64_t)t << 24) | ((uint64_t)r << 16) | (uint64_t)sg;
+        MM_TRY(blk_graph(P, B, key, s, part_b));
+      } else {
+        MM_TRY(part_b());
+      }
+      MM_CUDA(cudaStreamSynchronize(s));
       n_kernels += 9;
       it += 1;
-      MM_TRY(read_norms(sg));
       active.clear();
       for (int j = 0; j < sg; j++) {
         rn2[j] = B->host[j];
@@ -2410,6 +2470,7 @@ int mm_ecg_solve(mm_plan_t plan, const double* b, double* x, int t, int variant,
   BlkState* B = nullptr;
   MM_TRY(ensure_blk(P, t, &B));
   MM_TRY(ensure_ecg(P, B));
+  if (fp32) MM_TRY(ensure_t32(P, t));   // the captured iterations must find the FP32 buffers allocated
   cudaEvent_t ev;
   MM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   MM_CUDA(cudaEventRecord(ev, us));
@@ -2449,15 +2510,24 @@ int mm_ecg_solve(mm_plan_t plan, const double* b, double* x, int t, int variant,
     double best = INFINITY;
     int since_best = 0, inner = 0;
     while (it < opts->max_iter) {
-      MM_TRY(blk_apply(P, B, tz, fp32, s));                                   // AZ = A Z
-      n_kernels += fp32 ? 2 : 3;
-      n_apply += 1;
-      MM_CUDA(launch_bgram(B->Z, tz, nullptr, B->AZ, 0, tz, nullptr, n, B->part, blk_ctas(), B->G, s));
-      MM_CUDA(launch_bchol(B->G, tz, 1e-10, B->Linv, B->piv, B->rank, s));
-      MM_CUDA(cudaMemcpyAsync(B->host_i, B->rank, sizeof(int), cudaMemcpyDeviceToHost, s));
+      // AZ = A Z, G = Z^T A Z and its pivoted Cholesky factor (rank to the host); FP32 operators:
+      // one captured graph per shape
+      auto part_a = [&]() -> int {
+        MM_TRY(blk_apply(P, B, tz, fp32, s));
+        MM_CUDA(launch_bgram(B->Z, tz, nullptr, B->AZ, 0, tz, nullptr, n, B->part, blk_ctas(), B->G, s));
+        MM_CUDA(launch_bchol(B->G, tz, 1e-10, B->Linv, B->piv, B->rank, s));
+        MM_CUDA(cudaMemcpyAsync(B->host_i, B->rank, sizeof(int), cudaMemcpyDeviceToHost, s));
+        return MM_OK;
+      };
+      if (fp32) {
+        MM_TRY(blk_graph(P, B, (3ull << 60) | ((uint64_t)tz << 16), s, part_a));
+      } else {
+        MM_TRY(part_a());
+      }
       MM_CUDA(cudaStreamSynchronize(s));
       const int r = B->host_i[0];
-      n_kernels += 3;
+      n_kernels += (fp32 ? 2 : 3) + 3;
+      n_apply += 1;
       if (r == 0) {
         // every direction dropped: on the FP32 path after the first step of a recurrence this is
         // operator noise along a (near-)null direction of a semi-definite A (the map offset of
@@ -2470,17 +2540,50 @@ int mm_ecg_solve(mm_plan_t plan, const double* b, double* x, int t, int variant,
         break;
       }
       inner += 1;
-      // P_k = Z (Z^T A Z)^{-1/2} and A P_k; alpha = P_k^T R; X += P alpha; R -= A P alpha
-      MM_CUDA(launch_linv_coef(B->Linv, B->piv, B->rank, tz, B->Cmb, s));
-      MM_CUDA(launch_bcombine(B->P, 0, nullptr, r, B->Z, tz, B->Cmb, tz, 1.0, 0, n, nullptr, blk_ctas(), nullptr, s));
-      MM_CUDA(launch_bcombine(B->AP, 0, nullptr, r, B->AZ, tz, B->Cmb, tz, 1.0, 0, n, nullptr, blk_ctas(), nullptr, s));
-      MM_CUDA(launch_bgram(B->P, r, nullptr, B->R, 1, t, nullptr, n, B->part, blk_ctas(), B->alpha, s));
-      MM_CUDA(launch_bcombine(B->X, 1, nullptr, t, B->P, r, B->alpha, t, 1.0, 1, n, nullptr, blk_ctas(), nullptr, s));
-      MM_CUDA(launch_bcombine(B->R, 1, nullptr, t, B->AP, r, B->alpha, t, -1.0, 1, n, nullptr, blk_ctas(), nullptr, s));
-      MM_CUDA(launch_bsum(B->R, t, n, nullptr, 0, B->norm_part, blk_ctas(), B->norms, s));   // ||sum_i R_i||^2
-      n_kernels += 10;
+      // P_k = Z (Z^T A Z)^{-1/2} and A P_k; alpha = P_k^T R; X += P alpha; R -= A P alpha; the norm
+      // of sum_i R_i to the host; and already the next search block (unused when this step ends
+      // the recurrence):
+      //   Orthomin  Z_{k+1} = (I - P_k P_k^T A) M R_k
+      //   Orthodir  Z_{k+1} = (I - P_k P_k^T A - P_{k-1} P_{k-1}^T A) M A P_k
+      const int tz_next = (variant == MM_ECG_ORTHOMIN) ? t : r;
+      auto part_b = [&]() -> int {
+        MM_CUDA(launch_linv_coef(B->Linv, B->piv, B->rank, tz, B->Cmb, s));
+        MM_CUDA(launch_bcombine(B->P, 0, nullptr, r, B->Z, tz, B->Cmb, tz, 1.0, 0, n, nullptr, blk_ctas(), nullptr, s));
+        MM_CUDA(launch_bcombine(B->AP, 0, nullptr, r, B->AZ, tz, B->Cmb, tz, 1.0, 0, n, nullptr, blk_ctas(), nullptr,
+                                s));
+        MM_CUDA(launch_bgram(B->P, r, nullptr, B->R, 1, t, nullptr, n, B->part, blk_ctas(), B->alpha, s));
+        MM_CUDA(launch_bcombine(B->X, 1, nullptr, t, B->P, r, B->alpha, t, 1.0, 1, n, nullptr, blk_ctas(), nullptr,
+                                s));
+        MM_CUDA(launch_bcombine(B->R, 1, nullptr, t, B->AP, r, B->alpha, t, -1.0, 1, n, nullptr, blk_ctas(), nullptr,
+                                s));
+        MM_CUDA(launch_bsum(B->R, t, n, nullptr, 0, B->norm_part, blk_ctas(), B->norms, s));   // ||sum_i R_i||^2
+        MM_CUDA(cudaMemcpyAsync(B->host, B->norms, sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (variant == MM_ECG_ORTHOMIN) {
+          MM_CUDA(launch_bprecond(P->minv, B->R, nullptr, t, n, B->Z, s));
+        } else {
+          MM_CUDA(launch_bprecond32(P->minv, B->AP, r, n, B->Z, s));
+        }
+        MM_CUDA(launch_bgram(B->AP, r, nullptr, B->Z, 0, tz_next, nullptr, n, B->part, blk_ctas(), B->C2, s));
+        MM_CUDA(launch_bcombine(B->Z, 0, nullptr, tz_next, B->P, r, B->C2, tz_next, -1.0, 1, n, nullptr, blk_ctas(),
+                                nullptr, s));
+        if (variant == MM_ECG_ORTHODIR && rprev > 0) {
+          MM_CUDA(launch_bgram(B->APp, rprev, nullptr, B->Z, 0, tz_next, nullptr, n, B->part, blk_ctas(), B->G, s));
+          MM_CUDA(launch_bcombine(B->Z, 0, nullptr, tz_next, B->Pp, rprev, B->G, tz_next, -1.0, 1, n, nullptr,
+                                  blk_ctas(), nullptr, s));
+        }
+        return MM_OK;
+      };
+      if (fp32) {
+        // Orthodir swaps the P / Pp buffers every step: which one is current is part of the shape
+        const uint64_t key = (4ull << 60) | ((uint64_t)variant << 45) | ((uint64_t)(B->P < B->Pp) << 44) |
+                             ((uint64_t)rprev << 32) | ((uint64_t)tz << 24) | ((uint64_t)r << 16) | ((uint64_t)t << 8);
+        MM_TRY(blk_graph(P, B, key, s, part_b));
+      } else {
+        MM_TRY(part_b());
+      }
+      MM_CUDA(cudaStreamSynchronize(s));
+      n_kernels += 14 + ((variant == MM_ECG_ORTHODIR && rprev > 0) ? 3 : 0);
       it += 1;
-      MM_TRY(read_host(B->norms, 1));
       rel2 = B->host[0] / bn2;
       if (!std::isfinite(rel2)) {
         status = MM_EBREAKDOWN;
@@ -2497,26 +2600,8 @@ int mm_ecg_solve(mm_plan_t plan, const double* b, double* x, int t, int variant,
         stalled = true;
         break;
       }
-      if (variant == MM_ECG_ORTHOMIN) {
-        // Z_{k+1} = (I - P_k P_k^T A) M R_k
-        MM_CUDA(launch_bprecond(P->minv, B->R, nullptr, t, n, B->Z, s));
-        tz = t;
-        MM_CUDA(launch_bgram(B->AP, r, nullptr, B->Z, 0, tz, nullptr, n, B->part, blk_ctas(), B->C2, s));
-        MM_CUDA(launch_bcombine(B->Z, 0, nullptr, tz, B->P, r, B->C2, tz, -1.0, 1, n, nullptr, blk_ctas(), nullptr, s));
-        n_kernels += 4;
-      } else {
-        // Z_{k+1} = (I - P_k P_k^T A - P_{k-1} P_{k-1}^T A) M A P_k
-        MM_CUDA(launch_bprecond32(P->minv, B->AP, r, n, B->Z, s));
-        tz = r;
-        MM_CUDA(launch_bgram(B->AP, r, nullptr, B->Z, 0, tz, nullptr, n, B->part, blk_ctas(), B->C2, s));
-        MM_CUDA(launch_bcombine(B->Z, 0, nullptr, tz, B->P, r, B->C2, tz, -1.0, 1, n, nullptr, blk_ctas(), nullptr, s));
-        n_kernels += 4;
-        if (rprev > 0) {
-          MM_CUDA(launch_bgram(B->APp, rprev, nullptr, B->Z, 0, tz, nullptr, n, B->part, blk_ctas(), B->G, s));
-          MM_CUDA(launch_bcombine(B->Z, 0, nullptr, tz, B->Pp, rprev, B->G, tz, -1.0, 1, n, nullptr, blk_ctas(),
-                                  nullptr, s));
-          n_kernels += 3;
-        }
+      tz = tz_next;
+      if (variant == MM_ECG_ORTHODIR) {
         std::swap(B->P, B->Pp);
         std::swap(B->AP, B->APp);
         rprev = r;

@@ -64,3 +64,32 @@ def test_two_level_solve_after_space_rebuilt(tiny):
     info = mm().mm_pcg_solve(gp, cuda(b), x, tol=cfg.tol, precision=1, precond=1)[0]
     assert info.status == 0
     assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-5 * np.linalg.norm(ref.x)
+
+
+def test_block_cg_and_ecg_graphs_after_buffers_grew(tiny):
+    """The FP32 block CG and enlarged CG replay captured graphs of their iterations, keyed by shape;
+    growing the plan's FP32 buffers between solves (more right-hand sides through mm_apply_A)
+    must make them capture again rather than replay stale pointers."""
+    cfg, prob, op, b, ref = tiny
+    m = mm()
+    gp, _, _ = plans(prob, precision=3)
+    B = cuda(np.stack([b, 2.0 * b, -0.5 * b]))
+    X = torch.empty_like(B)
+    m.mm_block_cg_solve(gp, B, X, tol=cfg.tol, max_iter=5000)
+    X1 = X.cpu().numpy()
+    x = torch.empty(op.n_obs, 3, dtype=torch.float64, device="cuda")
+    m.mm_ecg_solve(gp, cuda(b), x, 4, tol=cfg.tol, max_iter=5000)
+    e1 = x.cpu().numpy()
+    W = cuda(np.random.default_rng(2).standard_normal((6, op.n_obs, 3)))
+    m.mm_apply_A(gp, W, torch.empty_like(W))          # six columns: larger FP32 t and u buffers
+    X.zero_()
+    infos = m.mm_block_cg_solve(gp, B, X, tol=cfg.tol, max_iter=5000)
+    assert all(i.status == 0 for i in infos)
+    for j, s in enumerate((1.0, 2.0, -0.5)):
+        assert np.linalg.norm(X[j].cpu().numpy() - s * ref.x) <= 1e-5 * abs(s) * np.linalg.norm(ref.x)
+        assert np.linalg.norm(X[j].cpu().numpy() - X1[j]) <= 1e-6 * abs(s) * np.linalg.norm(ref.x)
+    x.zero_()
+    info = m.mm_ecg_solve(gp, cuda(b), x, 4, tol=cfg.tol, max_iter=5000)
+    assert info.status == 0
+    assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-5 * np.linalg.norm(ref.x)
+    assert np.linalg.norm(x.cpu().numpy() - e1) <= 1e-6 * np.linalg.norm(ref.x)
