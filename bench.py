@@ -647,11 +647,21 @@ def run_batched(a, widths=None, nrhs=None):
                              max_iter=3, raise_on_error=False)   # warm-up: buffers and kernels
         infos, dt = _timed(lambda: mm.mm_block_cg_solve(plan, B, X, block_width=w, tol=cfg.tol,
                                                         raise_on_error=False))
+        # the block A X of w columns alone (FP32 operator; FP64 in and out as the solver sees it)
+        Xw, Yw = B[:w].contiguous(), torch.empty_like(B[:w])
+        mm.mm_apply_A(plan, Xw, Yw)
+        _, dta = _timed(lambda: [mm.mm_apply_A(plan, Xw, Yw) for _ in range(3)])
+        dta /= 3
+        n_blk_it = infos[0].n_apply32
         res[str(w)] = {"solves_per_s": nrhs / dt, "s": dt,
                        "iters_max": max(i.iters for i in infos),
                        "true_rel_res_max": max(i.true_rel_res for i in infos),
                        "status": sorted(set(i.status for i in infos)),
-                       "block_applies_first_group": infos[0].n_apply32}
+                       "block_applies_first_group": n_blk_it,
+                       "block_ax_ms": dta * 1e3,
+                       "block_ax_samples_per_s_per_column": w * N / dta,
+                       "block_ax_share_of_iteration": (dta * n_blk_it * (nrhs // w)) / dt}
+        del Xw, Yw
     x1 = torch.empty(2, plan.n_obs, 3, dtype=torch.float64, device=dev)
     infos, dt64 = _timed(lambda: mm.mm_pcg_solve(plan, B[:2].contiguous(), x1, tol=cfg.tol,
                                                  precision=mm.MM_FP64, raise_on_error=False))

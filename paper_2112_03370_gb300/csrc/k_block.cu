@@ -78,6 +78,78 @@ __global__ void __launch_bounds__(kNT) k_bgram(const float4* __restrict__ A, int
   }
 }
 
+// The same partial Gram products for small blocks (ta <= MA, tb <= MB): every thread streams its
+// pixels (grid-stride, coalesced) and keeps the ta tb dot products in registers; then a block
+// reduction in FP64.  (The staged kernel above keeps most threads idle when t is small.)
+template <typename TB, int MA, int MB>
+__global__ void __launch_bounds__(kNT) k_bgram_small(const float4* __restrict__ A, int ta,
+                                                      const int* __restrict__ idx_a,
+                                                      const TB* __restrict__ B, int tb,
+                                                      const int* __restrict__ idx_b, int64_t n,
+                                                      double* __restrict__ out_part) {
+  __shared__ double red[kNT / 32][MA * MB];
+  float acc[MA][MB];
+#pragma unroll
+  for (int i = 0; i < MA; i++)
+#pragma unroll
+    for (int j = 0; j < MB; j++) acc[i][j] = 0.f;
+  for (int64_t p = (int64_t)blockIdx.x * kNT + threadIdx.x; p < n; p += (int64_t)gridDim.x * kNT) {
+    float bx[MB], by[MB], bz[MB];
+#pragma unroll
+    for (int j = 0; j < MB; j++) {
+      bx[j] = by[j] = bz[j] = 0.f;
+      if (j < tb) {
+        const int64_t col = idx_b ? idx_b[j] : j;
+        if constexpr (sizeof(TB) == sizeof(float4)) {
+          const float4 v = __ldg(reinterpret_cast<const float4*>(B) + col * n + p);
+          bx[j] = v.x; by[j] = v.y; bz[j] = v.z;
+        } else {
+          const double* v = reinterpret_cast<const double*>(B) + 4 * (col * n + p);
+          bx[j] = (float)v[0]; by[j] = (float)v[1]; bz[j] = (float)v[2];
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < MA; i++) {
+      if (i < ta) {
+        const float4 a = __ldg(A + (int64_t)(idx_a ? idx_a[i] : i) * n + p);
+#pragma unroll
+        for (int j = 0; j < MB; j++) acc[i][j] += a.x * bx[j] + a.y * by[j] + a.z * bz[j];
+      }
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < MA; i++)
+#pragma unroll
+    for (int j = 0; j < MB; j++) {
+      double v = (double)acc[i][j];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][i * MB + j] = v;
+    }
+  __syncthreads();
+  if (threadIdx.x < MA * MB) {
+    const int i = threadIdx.x / MB, j = threadIdx.x % MB;
+    if (i < ta && j < tb) {
+      double v = 0.0;
+      for (int w = 0; w < kNT / 32; w++) v += red[w][threadIdx.x];
+      out_part[(int64_t)blockIdx.x * kMaxBlk * kMaxBlk + i * tb + j] = v;
+    }
+  }
+}
+
+template <int MA, int MB>
+static void bgram_small(const float* A, int ta, const int* idx_a, const void* B, int b_is_fp64, int tb,
+                        const int* idx_b, int64_t n, double* part, int nblk, cudaStream_t s) {
+  if (b_is_fp64)
+    k_bgram_small<double4_16a, MA, MB><<<nblk, kNT, 0, s>>>(reinterpret_cast<const float4*>(A), ta, idx_a,
+                                                            reinterpret_cast<const double4_16a*>(B), tb, idx_b, n,
+                                                            part);
+  else
+    k_bgram_small<float4, MA, MB><<<nblk, kNT, 0, s>>>(reinterpret_cast<const float4*>(A), ta, idx_a,
+                                                       reinterpret_cast<const float4*>(B), tb, idx_b, n, part);
+}
+
 // G[i][j] = sum over CTAs of out_part (fixed order: deterministic)
 __global__ void k_bgram_reduce(const double* __restrict__ part, int nblk, int npair,
                                double* __restrict__ G) {
@@ -93,7 +165,11 @@ cudaError_t launch_bgram(const float* A, int ta, const int* idx_a, const void* B
                          cudaStream_t s) {
   if (ta <= 0 || tb <= 0) return cudaSuccess;
   if (ta > kMaxBlk || tb > kMaxBlk) return cudaErrorInvalidValue;
-  if (b_is_fp64)
+  if (ta <= 4 && tb <= 4) {
+    bgram_small<4, 4>(A, ta, idx_a, B, b_is_fp64, tb, idx_b, n, part, nblk, s);
+  } else if (ta == 1 && tb <= 16) {
+    bgram_small<1, 16>(A, ta, idx_a, B, b_is_fp64, tb, idx_b, n, part, nblk, s);
+  } else if (b_is_fp64)
     k_bgram<double4_16a><<<nblk, kNT, 0, s>>>(reinterpret_cast<const float4*>(A), ta, idx_a,
                                               reinterpret_cast<const double4_16a*>(B), tb, idx_b, n, part);
   else

@@ -686,6 +686,18 @@ __device__ __forceinline__ long long fixed_of(float f, int k) {
 }
 __device__ __forceinline__ long long fixed_of(df v, int k) { return fixed_of(v.hi, k) + fixed_of(v.lo, k); }
 
+// round(f 2^(32 + e)) with sc = 2^e (a normal float) and |f sc| < 2^30, rounding the magnitude:
+// x = |f| sc (exact), its integer part and its fraction (x - floor(x), exact for x >= 0) times 2^32
+// as two 32-bit conversions, then the sign.
+__device__ __forceinline__ long long fixed_fast(float f, float sc) {
+  const float x = fabsf(f) * sc;
+  const float h = floorf(x);
+  const unsigned long long m =
+      ((unsigned long long)__float2uint_rn(h) << 32) + __float2uint_rn((x - h) * 4294967296.f);
+  return f < 0.f ? -(long long)m : (long long)m;
+}
+__device__ __forceinline__ long long fixed_fast(df v, float sc) { return fixed_fast(v.hi, sc) + fixed_fast(v.lo, sc); }
+
 constexpr size_t kPointDfSmem = (size_t)3 * kAccStride * sizeof(unsigned long long);
 
 __global__ void __launch_bounds__(kWinThreads, 2) k_point_win_df(
@@ -710,6 +722,10 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_point_win_df(
     }
     const int e_u = (int)((ub >> 23) & 0xffu) - 127;   // umax in [2^e_u, 2^(e_u + 1)) (subnormal: e_u = -127)
     const int ks = 45 - e_u;
+    // sums in units of 2^-ks: |y| < 2^(e_u + 1) gives |y 2^(ks - 32)| < 2^14; the fast conversion
+    // takes the scale 2^(ks - 32) as a normal float (all but umax below 2^-114)
+    const bool fast = ks - 32 <= 126;
+    const float sc = fast ? __int_as_float((ks - 32 + 127) << 23) : 0.f;
     const double unit = __longlong_as_double((long long)(1023 - ks) << 52);   // 2^-ks
     const float2* ur = u + r * u_stride;
     for (int k = threadIdx.x; k < n_pad; k += kWinThreads) {
@@ -723,9 +739,15 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_point_win_df(
       const df y = df_make(y2.x, y2.y);
       const df cy = df_make(w.x, w.y) * y, sy = df_make(w.z, w.w) * y;
       const int k = acc_index((int)sl);
-      atomicAdd(acc64 + k, (unsigned long long)fixed_of(y, ks));
-      atomicAdd(acc64 + kAccStride + k, (unsigned long long)fixed_of(cy, ks));
-      atomicAdd(acc64 + 2 * kAccStride + k, (unsigned long long)fixed_of(sy, ks));
+      if (fast) {
+        atomicAdd(acc64 + k, (unsigned long long)fixed_fast(y, sc));
+        atomicAdd(acc64 + kAccStride + k, (unsigned long long)fixed_fast(cy, sc));
+        atomicAdd(acc64 + 2 * kAccStride + k, (unsigned long long)fixed_fast(sy, sc));
+      } else {
+        atomicAdd(acc64 + k, (unsigned long long)fixed_of(y, ks));
+        atomicAdd(acc64 + kAccStride + k, (unsigned long long)fixed_of(cy, ks));
+        atomicAdd(acc64 + 2 * kAccStride + k, (unsigned long long)fixed_of(sy, ks));
+      }
     };
     const int n_it = (G.n_blk + cw.cpi - 1) / cw.cpi;
     const int per = (n_it + kWarps - 1) / kWarps;
