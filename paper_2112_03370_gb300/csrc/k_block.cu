@@ -12,71 +12,12 @@ namespace mm {
 
 namespace {
 constexpr int kNT = 256;
-constexpr int kChunk = 16;    // pixels staged in shared memory per step of a Gram CTA
 }  // namespace
 
-// out_part[blk][i][j] = sum over this CTA's pixels of <A_i, B_j> (3 components), FP32 products,
-// FP64 per-CTA totals.  ta, tb <= kMaxBlk.  A, B are float4 blocks or float64 blocks (B may be
-// FP64: R); A_i selected through idx_a (or identity when null).
-template <typename TB>
-__global__ void __launch_bounds__(kNT) k_bgram(const float4* __restrict__ A, int ta,
-                                                const int* __restrict__ idx_a,
-                                                const TB* __restrict__ B, int tb,
-                                                const int* __restrict__ idx_b, int64_t n,
-                                                double* __restrict__ out_part) {
-  __shared__ float sa[kChunk][kMaxBlk * 3 + 1];
-  __shared__ float sb[kChunk][kMaxBlk * 3 + 1];
-  const int npair = ta * tb;
-  float acc[kMaxBlk * kMaxBlk / kNT];
-#pragma unroll
-  for (int u = 0; u < kMaxBlk * kMaxBlk / kNT; u++) acc[u] = 0.f;
-  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
-  const int64_t p0 = (int64_t)blockIdx.x * per, p1 = min(n, p0 + per);
-  for (int64_t base = p0; base < p1; base += kChunk) {
-    const int cnt = (int)min((int64_t)kChunk, p1 - base);
-    for (int e = threadIdx.x; e < kChunk * ta; e += kNT) {
-      const int r = e % kChunk, i = e / kChunk;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (r < cnt) v = A[(int64_t)(idx_a ? idx_a[i] : i) * n + base + r];
-      sa[r][3 * i] = v.x; sa[r][3 * i + 1] = v.y; sa[r][3 * i + 2] = v.z;
-    }
-    for (int e = threadIdx.x; e < kChunk * tb; e += kNT) {
-      const int r = e % kChunk, j = e / kChunk;
-      float x = 0.f, y = 0.f, z = 0.f;
-      if (r < cnt) {
-        const int64_t col = idx_b ? idx_b[j] : j;
-        if constexpr (sizeof(TB) == sizeof(float4)) {
-          const float4 v = reinterpret_cast<const float4*>(B)[col * n + base + r];
-          x = v.x; y = v.y; z = v.z;
-        } else {
-          const double* v = reinterpret_cast<const double*>(B) + 4 * (col * n + base + r);
-          x = (float)v[0]; y = (float)v[1]; z = (float)v[2];
-        }
-      }
-      sb[r][3 * j] = x; sb[r][3 * j + 1] = y; sb[r][3 * j + 2] = z;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < kMaxBlk * kMaxBlk / kNT; u++) {
-      const int pr = threadIdx.x + u * kNT;
-      if (pr < npair) {
-        const int i = pr / tb, j = pr % tb;
-        float s = 0.f;
-        for (int r = 0; r < cnt; r++)
-          s += sa[r][3 * i] * sb[r][3 * j] + sa[r][3 * i + 1] * sb[r][3 * j + 1] +
-               sa[r][3 * i + 2] * sb[r][3 * j + 2];
-        acc[u] += s;
-      }
-    }
-    __syncthreads();
-  }
-  double* o = out_part + (int64_t)blockIdx.x * kMaxBlk * kMaxBlk;
-#pragma unroll
-  for (int u = 0; u < kMaxBlk * kMaxBlk / kNT; u++) {
-    const int pr = threadIdx.x + u * kNT;
-    if (pr < npair) o[pr] = (double)acc[u];
-  }
-}
+// Partial Gram products: out_part[blk][i tb + j] = sum over this CTA's contiguous range of pixels
+// of <A_i, B_j> (3 components), FP32 products and sums, FP64 per-CTA totals.  ta, tb <= kMaxBlk.
+// A is a float4 block, B a float4 or float64 block (R); columns selected through idx_a / idx_b
+// (identity when null).
 
 // The same partial Gram products for small blocks (ta <= MA, tb <= MB): every thread streams its
 // pixels (grid-stride, coalesced) and keeps the ta tb dot products in registers; then a block
@@ -150,6 +91,85 @@ static void bgram_small(const float* A, int ta, const int* idx_a, const void* B,
                                                        reinterpret_cast<const float4*>(B), tb, idx_b, n, part);
 }
 
+// The same partial Gram products for wide blocks: 64 x 64 pairs over 256 threads, each thread a
+// 4 x 4 tile of (i, j) in registers; kGR pixels of both blocks staged per step as
+// [pixel][component][column] (rows padded to keep 16-byte alignment and spread the staging stores
+// over banks), so a thread's four a values and four b values of one pixel component are two
+// 16-byte shared loads for 16 FMAs.
+constexpr int kGR = 24;   // 2 x 19.6 KB of static shared memory
+constexpr int kGRow = kMaxBlk + 4;
+template <typename TB>
+__global__ void __launch_bounds__(kNT) k_bgram_tiled(const float4* __restrict__ A, int ta,
+                                                      const int* __restrict__ idx_a,
+                                                      const TB* __restrict__ B, int tb,
+                                                      const int* __restrict__ idx_b, int64_t n,
+                                                      double* __restrict__ out_part) {
+  static_assert(kNT == 256 && kMaxBlk == 64, "16 x 16 threads of 4 x 4 pairs");
+  __shared__ __align__(16) float sa[kGR][3][kGRow];
+  __shared__ __align__(16) float sb[kGR][3][kGRow];
+  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+  double tot[4][4];   // FP64 totals of the per-chunk FP32 sums (two-level summation)
+#pragma unroll
+  for (int u = 0; u < 4; u++)
+#pragma unroll
+    for (int v = 0; v < 4; v++) tot[u][v] = 0.0;
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t p0 = (int64_t)blockIdx.x * per, p1 = min(n, p0 + per);
+  for (int64_t base = p0; base < p1; base += kGR) {
+    const int cnt = (int)min((int64_t)kGR, p1 - base);
+    // staging: consecutive threads take consecutive pixels of one column (coalesced loads)
+    for (int e = threadIdx.x; e < kGR * kMaxBlk; e += kNT) {
+      const int r = e % kGR, i = e / kGR;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < cnt && i < ta) v = __ldg(A + (int64_t)(idx_a ? idx_a[i] : i) * n + base + r);
+      sa[r][0][i] = v.x; sa[r][1][i] = v.y; sa[r][2][i] = v.z;
+      float x = 0.f, y = 0.f, z = 0.f;
+      if (r < cnt && i < tb) {
+        const int64_t col = idx_b ? idx_b[i] : i;
+        if constexpr (sizeof(TB) == sizeof(float4)) {
+          const float4 w = __ldg(reinterpret_cast<const float4*>(B) + col * n + base + r);
+          x = w.x; y = w.y; z = w.z;
+        } else {
+          const double* w = reinterpret_cast<const double*>(B) + 4 * (col * n + base + r);
+          x = (float)w[0]; y = (float)w[1]; z = (float)w[2];
+        }
+      }
+      sb[r][0][i] = x; sb[r][1][i] = y; sb[r][2][i] = z;
+    }
+    __syncthreads();
+    float acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+#pragma unroll
+      for (int v = 0; v < 4; v++) acc[u][v] = 0.f;
+    for (int r = 0; r < cnt; r++) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const float4 a = *reinterpret_cast<const float4*>(&sa[r][c][4 * ti]);
+        const float4 b = *reinterpret_cast<const float4*>(&sb[r][c][4 * tj]);
+        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+#pragma unroll
+          for (int v = 0; v < 4; v++) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+#pragma unroll
+      for (int v = 0; v < 4; v++) tot[u][v] += (double)acc[u][v];
+    __syncthreads();
+  }
+  double* o = out_part + (int64_t)blockIdx.x * kMaxBlk * kMaxBlk;
+#pragma unroll
+  for (int u = 0; u < 4; u++)
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      const int i = 4 * ti + u, j = 4 * tj + v;
+      if (i < ta && j < tb) o[i * tb + j] = tot[u][v];
+    }
+}
+
 // G[i][j] = sum over CTAs of out_part (fixed order: deterministic)
 __global__ void k_bgram_reduce(const double* __restrict__ part, int nblk, int npair,
                                double* __restrict__ G) {
@@ -169,23 +189,101 @@ cudaError_t launch_bgram(const float* A, int ta, const int* idx_a, const void* B
     bgram_small<4, 4>(A, ta, idx_a, B, b_is_fp64, tb, idx_b, n, part, nblk, s);
   } else if (ta == 1 && tb <= 16) {
     bgram_small<1, 16>(A, ta, idx_a, B, b_is_fp64, tb, idx_b, n, part, nblk, s);
-  } else if (b_is_fp64)
-    k_bgram<double4_16a><<<nblk, kNT, 0, s>>>(reinterpret_cast<const float4*>(A), ta, idx_a,
-                                              reinterpret_cast<const double4_16a*>(B), tb, idx_b, n, part);
-  else
-    k_bgram<float4><<<nblk, kNT, 0, s>>>(reinterpret_cast<const float4*>(A), ta, idx_a,
-                                         reinterpret_cast<const float4*>(B), tb, idx_b, n, part);
+  } else if (b_is_fp64) {
+    k_bgram_tiled<double4_16a><<<nblk, kNT, 0, s>>>(reinterpret_cast<const float4*>(A), ta, idx_a,
+                                                    reinterpret_cast<const double4_16a*>(B), tb, idx_b, n, part);
+  } else {
+    k_bgram_tiled<float4><<<nblk, kNT, 0, s>>>(reinterpret_cast<const float4*>(A), ta, idx_a,
+                                               reinterpret_cast<const float4*>(B), tb, idx_b, n, part);
+  }
   k_bgram_reduce<<<(ta * tb + 255) / 256, 256, 0, s>>>(part, nblk, ta * tb, G);
   return cudaGetLastError();
 }
 
-// out_j (+)= sign * sum_i A_i C[i][j] for j < v (A: float32 [t][n]; C: FP64 [t][v] row-major;
-// out: FP64 or FP32 block, column j stored at idx_out[j] (or j)).  mode 0: out = sum,
-// mode 1: out += sign * sum.  Each thread keeps 16 outputs of one pixel in registers per pass
-// over A.  With norm_part != null (FP64 outputs), per-CTA partials of ||out_j||^2 are written.
-constexpr int kCombJ = 16;
+// out_j (+)= sign * sum_i A_i C[i][j] for j < v (A: float32 [t][n]; C: FP64 [t][v] row-major with
+// leading dimension ldc; out: FP64 or FP32 block, column j stored at idx_out[j] (or j)).  mode 0:
+// out = sign * sum, mode 1: out += sign * sum.  A CTA stages kCP pixels of every input column and
+// the coefficients in shared memory, then each thread forms 8 output columns of one pixel (warp w
+// takes columns 8 w .. 8 w + 7, its lanes consecutive pixels, so the stores coalesce and each
+// warp owns its columns' norm partials).  With norm_part != null (FP64 outputs), per-CTA partials
+// of ||out_j||^2 are written.
+constexpr int kCP = 32;
 template <typename TO>
 __global__ void __launch_bounds__(kNT) k_bcombine(TO* __restrict__ out, const int* __restrict__ idx_out,
+                                                   int v, const float4* __restrict__ A, int t,
+                                                   const double* __restrict__ C, int ldc, double sign,
+                                                   int mode, int64_t n, double* __restrict__ norm_part) {
+  static_assert(kNT == 256 && kMaxBlk == 64 && kCP == 32, "8 warps x 8 columns, 32 pixels per step");
+  __shared__ __align__(16) float4 sA[kMaxBlk][kCP];     // 32 KB
+  __shared__ __align__(16) float cs[kMaxBlk][kMaxBlk];  // 16 KB
+  for (int e = threadIdx.x; e < t * v; e += kNT) cs[e / v][e % v] = (float)(sign * C[(e / v) * ldc + (e % v)]);
+  const int r = threadIdx.x & 31, g = threadIdx.x >> 5;   // pixel in the chunk, column group
+  const int j0 = 8 * g;
+  const int nj = max(0, min(8, v - j0));
+  double nrm[8];
+#pragma unroll
+  for (int jj = 0; jj < 8; jj++) nrm[jj] = 0.0;
+  const int64_t n_chunks = (n + kCP - 1) / kCP;
+  for (int64_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+    const int64_t base = ch * kCP;
+    const int cnt = (int)min((int64_t)kCP, n - base);
+    __syncthreads();   // the previous chunk is no longer read (and the coefficients are staged)
+    for (int e = threadIdx.x; e < t * kCP; e += kNT) {
+      const int i = e / kCP, q = e % kCP;
+      sA[i][q] = (q < cnt) ? __ldg(A + (int64_t)i * n + base + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    if (nj == 0 || r >= cnt) continue;
+    float ax[8], ay[8], az[8];
+#pragma unroll
+    for (int jj = 0; jj < 8; jj++) ax[jj] = ay[jj] = az[jj] = 0.f;
+    for (int i = 0; i < t; i++) {
+      const float4 a = sA[i][r];
+      const float4 c0 = *reinterpret_cast<const float4*>(&cs[i][j0]);
+      const float4 c1 = *reinterpret_cast<const float4*>(&cs[i][j0 + 4]);
+      const float c[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+      for (int jj = 0; jj < 8; jj++) {
+        ax[jj] = fmaf(a.x, c[jj], ax[jj]);
+        ay[jj] = fmaf(a.y, c[jj], ay[jj]);
+        az[jj] = fmaf(a.z, c[jj], az[jj]);
+      }
+    }
+    const int64_t p = base + r;
+#pragma unroll
+    for (int jj = 0; jj < 8; jj++) {
+      if (jj >= nj) break;
+      const int64_t col = idx_out ? idx_out[j0 + jj] : (j0 + jj);
+      if constexpr (sizeof(TO) == sizeof(float4)) {
+        float4* o = reinterpret_cast<float4*>(out) + col * n + p;
+        float4 cur = mode ? *o : make_float4(0.f, 0.f, 0.f, 0.f);
+        cur.x += ax[jj]; cur.y += ay[jj]; cur.z += az[jj];
+        cur.w = 0.f;
+        *o = cur;
+      } else {
+        double* o = reinterpret_cast<double*>(out) + 4 * (col * n + p);
+        double x0 = mode ? o[0] : 0.0, x1 = mode ? o[1] : 0.0, x2 = mode ? o[2] : 0.0;
+        x0 += (double)ax[jj]; x1 += (double)ay[jj]; x2 += (double)az[jj];
+        o[0] = x0; o[1] = x1; o[2] = x2; o[3] = 0.0;
+        nrm[jj] += x0 * x0 + x1 * x1 + x2 * x2;
+      }
+    }
+  }
+  if (norm_part) {
+#pragma unroll
+    for (int jj = 0; jj < 8; jj++) {
+      double v2 = nrm[jj];
+      for (int o = 16; o > 0; o >>= 1) v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+      if (r == 0 && jj < nj) norm_part[(int64_t)(j0 + jj) * gridDim.x + blockIdx.x] = v2;
+    }
+  }
+}
+
+// Narrow blocks (v, t <= kCombJ): each thread streams pixels (grid-stride) and forms all v outputs
+// of its pixel in registers; no staging, so a column or two costs one pass over A.
+constexpr int kCombJ = 16;
+template <typename TO>
+__global__ void __launch_bounds__(kNT) k_bcombine_stream(TO* __restrict__ out, const int* __restrict__ idx_out,
                                                    int v, const float4* __restrict__ A, int t,
                                                    const double* __restrict__ C, int ldc, double sign,
                                                    int mode, int64_t n, double* __restrict__ norm_part) {
@@ -259,14 +357,26 @@ cudaError_t launch_bcombine(void* out, int out_is_fp64, const int* idx_out, int 
                             int nblk, double* norms, cudaStream_t s) {
   if (v <= 0) return cudaSuccess;
   if (t > kMaxBlk || v > kMaxBlk) return cudaErrorInvalidValue;
-  if (out_is_fp64)
-    k_bcombine<double4_16a><<<nblk, kNT, 0, s>>>(reinterpret_cast<double4_16a*>(out), idx_out, v,
-                                                 reinterpret_cast<const float4*>(A), t, C, ldc, sign, mode,
-                                                 n, norm_part);
-  else
-    k_bcombine<float4><<<nblk, kNT, 0, s>>>(reinterpret_cast<float4*>(out), idx_out, v,
-                                            reinterpret_cast<const float4*>(A), t, C, ldc, sign, mode, n,
-                                            nullptr);
+  const bool narrow = v <= kCombJ && t <= kCombJ;
+  if (out_is_fp64) {
+    if (narrow)
+      k_bcombine_stream<double4_16a><<<nblk, kNT, 0, s>>>(reinterpret_cast<double4_16a*>(out), idx_out, v,
+                                                          reinterpret_cast<const float4*>(A), t, C, ldc, sign,
+                                                          mode, n, norm_part);
+    else
+      k_bcombine<double4_16a><<<nblk, kNT, 0, s>>>(reinterpret_cast<double4_16a*>(out), idx_out, v,
+                                                   reinterpret_cast<const float4*>(A), t, C, ldc, sign, mode,
+                                                   n, norm_part);
+  } else {
+    if (narrow)
+      k_bcombine_stream<float4><<<nblk, kNT, 0, s>>>(reinterpret_cast<float4*>(out), idx_out, v,
+                                                     reinterpret_cast<const float4*>(A), t, C, ldc, sign, mode, n,
+                                                     nullptr);
+    else
+      k_bcombine<float4><<<nblk, kNT, 0, s>>>(reinterpret_cast<float4*>(out), idx_out, v,
+                                              reinterpret_cast<const float4*>(A), t, C, ldc, sign, mode, n,
+                                              nullptr);
+  }
   if (norm_part && out_is_fp64) k_norm_reduce<<<(v + 63) / 64, 64, 0, s>>>(norm_part, nblk, v, norms);
   return cudaGetLastError();
 }
