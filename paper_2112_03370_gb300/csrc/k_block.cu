@@ -171,13 +171,22 @@ __global__ void __launch_bounds__(kNT) k_bgram_tiled(const float4* __restrict__ 
 }
 
 // G[i][j] = sum over CTAs of out_part (fixed order: deterministic)
+// One warp per output: lane l sums partials l, l + 32, ... in order, then a fixed shuffle tree
+// (deterministic, and 32 loads in flight instead of one serial chain over all CTAs).
+__device__ __forceinline__ double warp_sum_strided(const double* __restrict__ part, int64_t stride, int nblk) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int b = lane; b < nblk; b += 32) s += part[(int64_t)b * stride];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
 __global__ void k_bgram_reduce(const double* __restrict__ part, int nblk, int npair,
                                double* __restrict__ G) {
-  const int pr = blockIdx.x * blockDim.x + threadIdx.x;
+  const int pr = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (pr >= npair) return;
-  double s = 0.0;
-  for (int b = 0; b < nblk; b++) s += part[(int64_t)b * kMaxBlk * kMaxBlk + pr];
-  G[pr] = s;
+  const double s = warp_sum_strided(part + pr, (int64_t)kMaxBlk * kMaxBlk, nblk);
+  if ((threadIdx.x & 31) == 0) G[pr] = s;
 }
 
 cudaError_t launch_bgram(const float* A, int ta, const int* idx_a, const void* B, int b_is_fp64,
@@ -196,7 +205,7 @@ cudaError_t launch_bgram(const float* A, int ta, const int* idx_a, const void* B
     k_bgram_tiled<float4><<<nblk, kNT, 0, s>>>(reinterpret_cast<const float4*>(A), ta, idx_a,
                                                reinterpret_cast<const float4*>(B), tb, idx_b, n, part);
   }
-  k_bgram_reduce<<<(ta * tb + 255) / 256, 256, 0, s>>>(part, nblk, ta * tb, G);
+  k_bgram_reduce<<<(ta * tb + 7) / 8, 256, 0, s>>>(part, nblk, ta * tb, G);
   return cudaGetLastError();
 }
 
@@ -282,28 +291,28 @@ __global__ void __launch_bounds__(kNT) k_bcombine(TO* __restrict__ out, const in
 // Narrow blocks (v, t <= kCombJ): each thread streams pixels (grid-stride) and forms all v outputs
 // of its pixel in registers; no staging, so a column or two costs one pass over A.
 constexpr int kCombJ = 16;
-template <typename TO>
+template <typename TO, int J>
 __global__ void __launch_bounds__(kNT) k_bcombine_stream(TO* __restrict__ out, const int* __restrict__ idx_out,
                                                    int v, const float4* __restrict__ A, int t,
                                                    const double* __restrict__ C, int ldc, double sign,
                                                    int mode, int64_t n, double* __restrict__ norm_part) {
   __shared__ float cs[kMaxBlk * kMaxBlk];
   __shared__ double red[kNT];
-  for (int e = threadIdx.x; e < t * v; e += kNT) cs[e] = (float)C[(e / v) * ldc + (e % v)];
+  for (int e = threadIdx.x; e < t * v; e += kNT) cs[e] = (float)(sign * C[(e / v) * ldc + (e % v)]);
   __syncthreads();
-  for (int j0 = 0; j0 < v; j0 += kCombJ) {
-    const int nj = min(kCombJ, v - j0);
-    double nrm[kCombJ];
+  for (int j0 = 0; j0 < v; j0 += J) {
+    const int nj = min(J, v - j0);
+    double nrm[J];
 #pragma unroll
-    for (int jj = 0; jj < kCombJ; jj++) nrm[jj] = 0.0;
+    for (int jj = 0; jj < J; jj++) nrm[jj] = 0.0;
     for (int64_t p = (int64_t)blockIdx.x * kNT + threadIdx.x; p < n; p += (int64_t)gridDim.x * kNT) {
-      float ax[kCombJ], ay[kCombJ], az[kCombJ];
+      float ax[J], ay[J], az[J];
 #pragma unroll
-      for (int jj = 0; jj < kCombJ; jj++) ax[jj] = ay[jj] = az[jj] = 0.f;
+      for (int jj = 0; jj < J; jj++) ax[jj] = ay[jj] = az[jj] = 0.f;
       for (int i = 0; i < t; i++) {
         const float4 a = __ldg(A + (int64_t)i * n + p);
 #pragma unroll
-        for (int jj = 0; jj < kCombJ; jj++) {
+        for (int jj = 0; jj < J; jj++) {
           const float c = (jj < nj) ? cs[i * v + j0 + jj] : 0.f;
           ax[jj] = fmaf(a.x, c, ax[jj]);
           ay[jj] = fmaf(a.y, c, ay[jj]);
@@ -311,21 +320,25 @@ __global__ void __launch_bounds__(kNT) k_bcombine_stream(TO* __restrict__ out, c
         }
       }
 #pragma unroll
-      for (int jj = 0; jj < kCombJ; jj++) {
+      for (int jj = 0; jj < J; jj++) {
         if (jj >= nj) break;
         const int64_t col = idx_out ? idx_out[j0 + jj] : (j0 + jj);
         if constexpr (sizeof(TO) == sizeof(float4)) {
           float4* o = reinterpret_cast<float4*>(out) + col * n + p;
           float4 cur = mode ? *o : make_float4(0.f, 0.f, 0.f, 0.f);
-          cur.x += (float)sign * ax[jj]; cur.y += (float)sign * ay[jj]; cur.z += (float)sign * az[jj];
+          cur.x += ax[jj]; cur.y += ay[jj]; cur.z += az[jj];
           cur.w = 0.f;
           *o = cur;
         } else {
-          double* o = reinterpret_cast<double*>(out) + 4 * (col * n + p);
-          double x0 = mode ? o[0] : 0.0, x1 = mode ? o[1] : 0.0, x2 = mode ? o[2] : 0.0;
-          x0 += sign * (double)ax[jj]; x1 += sign * (double)ay[jj]; x2 += sign * (double)az[jj];
-          o[0] = x0; o[1] = x1; o[2] = x2; o[3] = 0.0;
-          nrm[jj] += x0 * x0 + x1 * x1 + x2 * x2;
+          // 16-byte accesses to the pixel's 32 bytes
+          double2* o = reinterpret_cast<double2*>(out) + 2 * (col * n + p);
+          double2 xy = mode ? o[0] : make_double2(0.0, 0.0);
+          double2 zw = mode ? o[1] : make_double2(0.0, 0.0);
+          xy.x += (double)ax[jj]; xy.y += (double)ay[jj]; zw.x += (double)az[jj];
+          zw.y = 0.0;
+          o[0] = xy;
+          o[1] = zw;
+          nrm[jj] += xy.x * xy.x + xy.y * xy.y + zw.x * zw.x;
         }
       }
     }
@@ -345,11 +358,10 @@ __global__ void __launch_bounds__(kNT) k_bcombine_stream(TO* __restrict__ out, c
 }
 
 __global__ void k_norm_reduce(const double* __restrict__ part, int nblk, int v, double* __restrict__ out) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (j >= v) return;
-  double s = 0.0;
-  for (int b = 0; b < nblk; b++) s += part[(int64_t)j * nblk + b];
-  out[j] = s;
+  const double s = warp_sum_strided(part + (int64_t)j * nblk, 1, nblk);
+  if ((threadIdx.x & 31) == 0) out[j] = s;
 }
 
 cudaError_t launch_bcombine(void* out, int out_is_fp64, const int* idx_out, int v, const float* A, int t,
@@ -359,25 +371,33 @@ cudaError_t launch_bcombine(void* out, int out_is_fp64, const int* idx_out, int 
   if (t > kMaxBlk || v > kMaxBlk) return cudaErrorInvalidValue;
   const bool narrow = v <= kCombJ && t <= kCombJ;
   if (out_is_fp64) {
-    if (narrow)
-      k_bcombine_stream<double4_16a><<<nblk, kNT, 0, s>>>(reinterpret_cast<double4_16a*>(out), idx_out, v,
-                                                          reinterpret_cast<const float4*>(A), t, C, ldc, sign,
-                                                          mode, n, norm_part);
+    if (narrow && v <= 4)   // few outputs: fewer registers, more resident warps
+      k_bcombine_stream<double4_16a, 4><<<nblk, kNT, 0, s>>>(reinterpret_cast<double4_16a*>(out), idx_out, v,
+                                                             reinterpret_cast<const float4*>(A), t, C, ldc, sign,
+                                                             mode, n, norm_part);
+    else if (narrow)
+      k_bcombine_stream<double4_16a, kCombJ><<<nblk, kNT, 0, s>>>(reinterpret_cast<double4_16a*>(out), idx_out, v,
+                                                                  reinterpret_cast<const float4*>(A), t, C, ldc,
+                                                                  sign, mode, n, norm_part);
     else
       k_bcombine<double4_16a><<<nblk, kNT, 0, s>>>(reinterpret_cast<double4_16a*>(out), idx_out, v,
                                                    reinterpret_cast<const float4*>(A), t, C, ldc, sign, mode,
                                                    n, norm_part);
   } else {
-    if (narrow)
-      k_bcombine_stream<float4><<<nblk, kNT, 0, s>>>(reinterpret_cast<float4*>(out), idx_out, v,
-                                                     reinterpret_cast<const float4*>(A), t, C, ldc, sign, mode, n,
-                                                     nullptr);
+    if (narrow && v <= 4)
+      k_bcombine_stream<float4, 4><<<nblk, kNT, 0, s>>>(reinterpret_cast<float4*>(out), idx_out, v,
+                                                        reinterpret_cast<const float4*>(A), t, C, ldc, sign, mode, n,
+                                                        nullptr);
+    else if (narrow)
+      k_bcombine_stream<float4, kCombJ><<<nblk, kNT, 0, s>>>(reinterpret_cast<float4*>(out), idx_out, v,
+                                                             reinterpret_cast<const float4*>(A), t, C, ldc, sign, mode,
+                                                             n, nullptr);
     else
       k_bcombine<float4><<<nblk, kNT, 0, s>>>(reinterpret_cast<float4*>(out), idx_out, v,
                                               reinterpret_cast<const float4*>(A), t, C, ldc, sign, mode, n,
                                               nullptr);
   }
-  if (norm_part && out_is_fp64) k_norm_reduce<<<(v + 63) / 64, 64, 0, s>>>(norm_part, nblk, v, norms);
+  if (norm_part && out_is_fp64) k_norm_reduce<<<(v + 7) / 8, 256, 0, s>>>(norm_part, nblk, v, norms);
   return cudaGetLastError();
 }
 
@@ -479,7 +499,7 @@ cudaError_t launch_bsum(const double* X, int t, int64_t n, double* out, int accu
                         int nblk, double* norm, cudaStream_t s) {
   if (t <= 0 || t > kMaxBlk) return cudaErrorInvalidValue;
   k_bsum<<<nblk, kNT, 0, s>>>(X, t, n, out, accumulate, norm_part);
-  k_norm_reduce<<<1, 64, 0, s>>>(norm_part, nblk, 1, norm);
+  k_norm_reduce<<<1, 32, 0, s>>>(norm_part, nblk, 1, norm);
   return cudaGetLastError();
 }
 
@@ -603,7 +623,7 @@ cudaError_t launch_bresid(const double* B, const double* AX, int v, int64_t n, d
                           double* norm_part, int nblk, double* norms, cudaStream_t s) {
   if (v <= 0) return cudaSuccess;
   k_bresid<<<dim3(nblk, v), kNT, 0, s>>>(B, AX, n, R, norm_part);
-  k_norm_reduce<<<(v + 63) / 64, 64, 0, s>>>(norm_part, nblk, v, norms);
+  k_norm_reduce<<<(v + 7) / 8, 256, 0, s>>>(norm_part, nblk, v, norms);
   return cudaGetLastError();
 }
 

@@ -234,6 +234,11 @@ __device__ __forceinline__ void visit_chunk(const PGroup& G, const int64_t* __re
   for (int q = w.ql; q < nq; q += w.lpc) f_quad(a0, q);
 }
 
+// Pointing loads (slot, angle): evict-first when a pass has one column; with several columns the
+// CTA reads the same group's pointing once per column, so it is kept in L2 for the later ones.
+template <typename T>
+__device__ __forceinline__ T ld_point(const T* p, bool keep) { return keep ? __ldg(p) : __ldcs(p); }
+
 // Padded shared-memory indices of slot k.  A lane holds 4 consecutive samples, so one warp-wide
 // access touches slots about 4 x (pixels per sample) apart; one padding word per 32 scalar slots
 // (accumulators) or one padding float4 per 8 slots (map window) keeps strides of 1, 2, 4 and 8
@@ -254,6 +259,7 @@ __global__ void __launch_bounds__(kWinThreads, 3) k_unpoint_win32(
   const PGroup G = groups[blockIdx.x];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const ChunkWalk cw = chunk_walk(G, lane);
+  const bool keep = nrhs > 1;
   for (int r = 0; r < nrhs; r++) {
     if (done != nullptr && done[(int64_t)r * done_stride] != 0) continue;
     const float4* x = x4 + r * x_stride4;
@@ -276,8 +282,8 @@ __global__ void __launch_bounds__(kWinThreads, 3) k_unpoint_win32(
           G, block_off, c, cw,
           [&](int64_t a0, int q) {
             const int64_t i = a0 + 4 * (int64_t)q;
-            const uint2 s2 = __ldcs(reinterpret_cast<const uint2*>(slot + i));
-            const float4 a = __ldcs(reinterpret_cast<const float4*>(ang2 + i));
+            const uint2 s2 = ld_point(reinterpret_cast<const uint2*>(slot + i), keep);
+            const float4 a = ld_point(reinterpret_cast<const float4*>(ang2 + i), keep);
             float4 v;
             v.x = value(s2.x & 0xFFFFu, a.x);
             v.y = value(s2.x >> 16, a.y);
@@ -285,7 +291,7 @@ __global__ void __launch_bounds__(kWinThreads, 3) k_unpoint_win32(
             v.w = value(s2.y >> 16, a.w);
             __stcs(reinterpret_cast<float4*>(tr + i), v);
           },
-          [&](int64_t i) { __stcs(tr + i, value(__ldcs(slot + i), __ldcs(ang2 + i))); });
+          [&](int64_t i) { __stcs(tr + i, value(ld_point(slot + i, keep), ld_point(ang2 + i, keep))); });
     }
   }
 }
@@ -320,6 +326,7 @@ __global__ void __launch_bounds__(kWinThreads, 3) k_point_win32(
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const ChunkWalk cw = chunk_walk(G, lane);
   const int n_pad = acc_index(G.n_slots);
+  const bool keep = nrhs > 1;
   for (int r = 0; r < nrhs; r++) {
     if (done != nullptr && done[(int64_t)r * done_stride] != 0) continue;
     const float* ur = u + r * u_stride;
@@ -349,15 +356,15 @@ __global__ void __launch_bounds__(kWinThreads, 3) k_point_win32(
           G, block_off, c, cw,
           [&](int64_t a0, int q) {
             const int64_t i = a0 + 4 * (int64_t)q;
-            const uint2 s2 = __ldcs(reinterpret_cast<const uint2*>(slot + i));
-            const float4 a = __ldcs(reinterpret_cast<const float4*>(ang2 + i));
+            const uint2 s2 = ld_point(reinterpret_cast<const uint2*>(slot + i), keep);
+            const float4 a = ld_point(reinterpret_cast<const float4*>(ang2 + i), keep);
             const float4 y = __ldcs(reinterpret_cast<const float4*>(ur + i));
             add(s2.x & 0xFFFFu, a.x, y.x);
             add(s2.x >> 16, a.y, y.y);
             add(s2.y & 0xFFFFu, a.z, y.z);
             add(s2.y >> 16, a.w, y.w);
           },
-          [&](int64_t i) { add(__ldcs(slot + i), __ldcs(ang2 + i), __ldcs(ur + i)); });
+          [&](int64_t i) { add(ld_point(slot + i, keep), ld_point(ang2 + i, keep), __ldcs(ur + i)); });
     }
     __syncthreads();
     float4* yr = y4 + r * y_stride4;
