@@ -43,27 +43,35 @@ __global__ void k_map_to_df(const double2* __restrict__ m, int64_t n, float4* __
   }
 }
 
-// t_i = I_p + cos 2psi_i Q_p + sin 2psi_i U_p (p = lpix_i), 0 at gaps and excised pixels; lane =
-// sample, so the pointing and weight loads coalesce and the map gathers of a scan fall on a few
-// cache lines per warp.
+// t_i = I_p + cos 2psi_i Q_p + sin 2psi_i U_p (p = lpix_i), 0 at gaps and excised pixels; with the
+// TOD (d_kind 1: float32, 2: float64) t_i = that - d_i, the time-domain residual.  Lane = sample,
+// so the pointing and weight loads coalesce and the map gathers of a scan fall on a few cache
+// lines per warp.
 __global__ void __launch_bounds__(256) k_unpoint_df(const int32_t* __restrict__ lpix,
                                                     const float4* __restrict__ w, int64_t N,
                                                     const float4* __restrict__ m, int64_t m_stride,
                                                     const int32_t* __restrict__ done, int done_stride,
+                                                    const void* __restrict__ d, int d_kind, int64_t d_stride,
                                                     float2* __restrict__ t, int64_t t_stride) {
   const int rhs = blockIdx.y;
   if (done != nullptr && done[(int64_t)rhs * done_stride] != 0) return;
   const float4* mr = m + rhs * m_stride;
   float2* tr = t + rhs * t_stride;
+  const float* d32 = reinterpret_cast<const float*>(d) + rhs * d_stride;
+  const double* d64 = reinterpret_cast<const double*>(d) + rhs * d_stride;
   constexpr int U = 4;
   for (int64_t i0 = (int64_t)blockIdx.x * 256 * U + threadIdx.x; i0 < N; i0 += (int64_t)gridDim.x * 256 * U) {
     int32_t p[U];
     float4 wv[U], iq[U], u0[U];
+    df dv[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int64_t i = i0 + u * 256;
       p[u] = (i < N) ? __ldg(lpix + i) : -1;
       wv[u] = (i < N) ? __ldg(w + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+      dv[u] = df_make(0.f, 0.f);
+      if (p[u] >= 0 && d_kind == 1) dv[u] = df_make(__ldcs(d32 + i), 0.f);
+      if (p[u] >= 0 && d_kind == 2) dv[u] = df(__ldcs(d64 + i));
     }
 #pragma unroll
     for (int u = 0; u < U; u++) {
@@ -78,8 +86,9 @@ __global__ void __launch_bounds__(256) k_unpoint_df(const int32_t* __restrict__ 
     for (int u = 0; u < U; u++) {
       const int64_t i = i0 + u * 256;
       if (i < N) {
-        const df v = df_make(iq[u].x, iq[u].y) + df_make(wv[u].x, wv[u].y) * df_make(iq[u].z, iq[u].w) +
-                     df_make(wv[u].z, wv[u].w) * df_make(u0[u].x, u0[u].y);
+        df v = df_make(iq[u].x, iq[u].y) + df_make(wv[u].x, wv[u].y) * df_make(iq[u].z, iq[u].w) +
+               df_make(wv[u].z, wv[u].w) * df_make(u0[u].x, u0[u].y);
+        if (d_kind != 0) v = v - dv[u];
         tr[i] = (p[u] >= 0) ? make_float2(v.hi, v.lo) : make_float2(0.f, 0.f);
       }
     }
@@ -98,25 +107,6 @@ __global__ void k_d_to_df(const int32_t* __restrict__ lpix, const D* __restrict_
     if constexpr (sizeof(D) == 4) v = df_make(dr[i], 0.f);
     else v = df((double)dr[i]);
     tr[i] = (__ldg(lpix + i) >= 0) ? make_float2(v.hi, v.lo) : make_float2(0.f, 0.f);
-  }
-}
-
-// t -= G d in df64 for the kept samples (t is 0 at the others): with t = P x this is the
-// time-domain residual of the right-hand side, so N^-1 and P^T of it give A x - b
-template <typename D>
-__global__ void k_sub_d_df(const int32_t* __restrict__ lpix, const D* __restrict__ d, int64_t N, int64_t d_stride,
-                           float2* __restrict__ t, int64_t t_stride) {
-  const int rhs = blockIdx.y;
-  const D* dr = d + rhs * d_stride;
-  float2* tr = t + rhs * t_stride;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    if (__ldg(lpix + i) < 0) continue;
-    df v;
-    if constexpr (sizeof(D) == 4) v = df_make(dr[i], 0.f);
-    else v = df((double)dr[i]);
-    const float2 a = tr[i];
-    const df r = df_make(a.x, a.y) - v;
-    tr[i] = make_float2(r.hi, r.lo);
   }
 }
 
@@ -148,10 +138,11 @@ cudaError_t launch_map_to_df(const double* m4, int64_t n_pix4, float4* out, cuda
 
 cudaError_t launch_unpoint_df(const int32_t* lpix, const float4* wdf, int64_t N, const float4* mapdf,
                               int64_t n_obs, int nrhs, const int32_t* done, int done_stride, float2* t,
-                              int64_t t_stride, cudaStream_t s) {
+                              int64_t t_stride, cudaStream_t s, const void* d, int d_is_fp32) {
   if (N == 0 || nrhs <= 0) return cudaSuccess;
+  const int d_kind = d == nullptr ? 0 : (d_is_fp32 ? 1 : 2);
   k_unpoint_df<<<dim3(grid_for(N, 1024), nrhs), 256, 0, s>>>(lpix, wdf, N, mapdf, 2 * n_obs, done,
-                                                             done_stride, t, t_stride);
+                                                             done_stride, d, d_kind, N, t, t_stride);
   return cudaGetLastError();
 }
 
@@ -163,17 +154,6 @@ cudaError_t launch_d_to_df(const int32_t* lpix, const void* d, int d_is_fp32, in
     k_d_to_df<float><<<grid, 256, 0, s>>>(lpix, reinterpret_cast<const float*>(d), N, N, t, t_stride);
   else
     k_d_to_df<double><<<grid, 256, 0, s>>>(lpix, reinterpret_cast<const double*>(d), N, N, t, t_stride);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_sub_d_df(const int32_t* lpix, const void* d, int d_is_fp32, int64_t N, int nrhs, float2* t,
-                            int64_t t_stride, cudaStream_t s) {
-  if (N == 0 || nrhs <= 0) return cudaSuccess;
-  const dim3 grid(grid_for(N, 256), nrhs);
-  if (d_is_fp32)
-    k_sub_d_df<float><<<grid, 256, 0, s>>>(lpix, reinterpret_cast<const float*>(d), N, N, t, t_stride);
-  else
-    k_sub_d_df<double><<<grid, 256, 0, s>>>(lpix, reinterpret_cast<const double*>(d), N, N, t, t_stride);
   return cudaGetLastError();
 }
 

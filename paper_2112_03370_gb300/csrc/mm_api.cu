@@ -929,13 +929,13 @@ int apply64_internal(Plan* P, const double* x4, double* y4, int nrhs, cudaStream
       const int g = std::min(k, nrhs - r0);
       const int32_t* dn = done ? done + (int64_t)r0 * done_stride : nullptr;
       MM_CUDA(launch_map_to_df(x4 + (size_t)r0 * P->n_obs * 4, (int64_t)g * P->n_obs, P->mapdf, s));
+      // t = P x, or with the TOD t = P x - G d (the time-domain residual: N^-1 and P^T of it give
+      // A x - b) in one pass
+      const size_t esz = (tod && tod->d_is_fp32) ? sizeof(float) : sizeof(double);
       MM_CUDA(launch_unpoint_df(P->lpix, P->wdf, P->N, P->mapdf, P->n_obs, g, dn, done_stride, P->tdf,
-                                df_stride(P), s));
-      if (tod) {
-        const size_t esz = tod->d_is_fp32 ? sizeof(float) : sizeof(double);
-        MM_CUDA(launch_sub_d_df(P->lpix, reinterpret_cast<const char*>(tod->d) + (size_t)r0 * P->N * esz,
-                                tod->d_is_fp32, P->N, g, P->tdf, df_stride(P), s));
-      }
+                                df_stride(P), s,
+                                tod ? reinterpret_cast<const char*>(tod->d) + (size_t)r0 * P->N * esz : nullptr,
+                                tod ? tod->d_is_fp32 : 0));
       MM_TRY(df_ninv_point(P, g, dn, done_stride, y4 + (size_t)r0 * P->n_obs * 4, s));
     }
     return MM_OK;

@@ -384,12 +384,9 @@ cudaError_t launch_c64_to_df(const double2* in, int64_t n, float4* out, cudaStre
 cudaError_t launch_map_to_df(const double* m4, int64_t n_pix4, float4* out, cudaStream_t s);
 cudaError_t launch_unpoint_df(const int32_t* lpix, const float4* wdf, int64_t N, const float4* mapdf,
                               int64_t n_obs, int nrhs, const int32_t* done, int done_stride, float2* t,
-                              int64_t t_stride, cudaStream_t s);
+                              int64_t t_stride, cudaStream_t s, const void* d = nullptr, int d_is_fp32 = 0);
 cudaError_t launch_d_to_df(const int32_t* lpix, const void* d, int d_is_fp32, int64_t N, int nrhs,
                            float2* t, int64_t t_stride, cudaStream_t s);
-// t -= G d in df64 (t [nrhs][t_stride] pairs, d [nrhs][N])
-cudaError_t launch_sub_d_df(const int32_t* lpix, const void* d, int d_is_fp32, int64_t N, int nrhs, float2* t,
-                            int64_t t_stride, cudaStream_t s);
 // t [nrhs][t_stride] = G d rounded to FP32
 cudaError_t launch_d_to_t32(const int32_t* lpix, const void* d, int d_is_fp32, int64_t N, int nrhs, float* t,
                             int64_t t_stride, cudaStream_t s);
