@@ -1070,7 +1070,7 @@ def run_crossover(a):
         "config": {"workload": f"ground geometry: {a.dets} det x 4 int x 524288 samples, FP32 operators, "
                                f"{a.iters} PCG iterations per algorithm", "n_samples": n_total},
         "rows": rows, "gemm_wins_up_to_lambda": max(wins) if wins else None,
-        "auto_rule": "MM_TPLZ_AUTO takes the GEMM for lambda <= 32 on FP32 operators",
+        "auto_rule": "MM_TPLZ_AUTO takes the GEMM for lambda <= 64 on FP32 operators",
         "roofline": {"bound": "tensor", "kernel": "k_tplz_tc", "lambda": best["lambda"],
                      "achieved": best["gemm_tensor_tflops"], "peak": tf32_peak, "unit": "TFLOP/s",
                      "frac": best["gemm_tensor_frac"], "traffic": None,

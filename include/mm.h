@@ -67,7 +67,7 @@ enum { MM_FP64 = 0, MM_FP32 = 1, MM_DF64 = 2, MM_FP32_DF64 = 3 };
  *                   operators keep the FFT tiles.
  *   MM_TPLZ_DIRECT  band sum by the definition (checks, tiny lambda).
  *   MM_TPLZ_AUTO    MM_TPLZ_GEMM where it measured faster than the FFT (FP32 operators, lambda up
- *                   to the measured crossover), else MM_TPLZ_FFT. */
+ *                   to 64, the measured crossover), else MM_TPLZ_FFT. */
 enum { MM_TPLZ_AUTO = 0, MM_TPLZ_FFT = 1, MM_TPLZ_GEMM = 2, MM_TPLZ_DIRECT = 3 };
 /* Preconditioner: block-Jacobi, or the two-level a-posteriori A-DEF1 preconditioner built by
  * mm_deflation_build (Sect. 3.2, Eq. 2lvlDef). */

@@ -18,9 +18,12 @@
 // start address 16 (J0 + J) bytes further on.  T_J (hi and lo) of each band table is precomputed at
 // plan time in exactly this layout and copied in once per table.
 //
-// One elected thread issues the MMAs and commits them to an mbarrier; every wait on it is bounded:
-// after the bound the kernel records an error, waits once more (bounded) for its own MMAs, frees its
-// tensor memory and leaves.
+// The input rows of a tile are one contiguous range of the block's samples: one elected thread
+// brings the next two tiles' ranges into a two-stage shared-memory ring with 1D bulk copies
+// (cp.async.bulk, completion counted on an mbarrier per stage), so the loads of later tiles run
+// under the current tile's split, MMAs and epilogue.  The same thread issues the MMAs and commits
+// them to an mbarrier.  Every wait is bounded: after the bound the kernel records an error, waits
+// once more (bounded) for its own copies and MMAs in flight, frees its tensor memory and leaves.
 #include <algorithm>
 
 #include "mm_internal.cuh"
@@ -40,9 +43,13 @@ constexpr int kTcBShift = kTcKg * kTcLboB;        // one T_J (hi or lo)
 constexpr int kTcMaxShifts = 2 * kTcMaxJ0 + 1;
 constexpr int kTcBSize = kTcMaxShifts * kTcBShift;
 constexpr int kTcGuard = 4096;                    // keeps every descriptor-reachable byte inside
-// dynamic shared memory for 2 j0 + 1 shifts: A hi/lo, T_J hi/lo, guard
+// one ring stage: the tile's 128 + 2 j0 rows of input plus up to 8 samples of 16-byte alignment
+__host__ __device__ constexpr size_t tc_stage_bytes(int j0) {
+  return (((size_t)(kTcM + 2 * j0) * kTcB + 8) * 4 + 15) / 16 * 16;
+}
+// dynamic shared memory for 2 j0 + 1 shifts: A hi/lo, T_J hi/lo, two input stages, guard
 __host__ __device__ constexpr size_t tc_smem_bytes(int j0) {
-  return 2 * (size_t)kTcASize + 2 * (size_t)(2 * j0 + 1) * kTcBShift + kTcGuard;
+  return 2 * (size_t)kTcASize + 2 * (size_t)(2 * j0 + 1) * kTcBShift + 2 * tc_stage_bytes(j0) + kTcGuard;
 }
 constexpr size_t kTcSmem = tc_smem_bytes(kTcMaxJ0);
 constexpr int kTcThreads = 128;
@@ -86,6 +93,16 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
   return false;
 }
 
+// Expect `bytes` on the mbarrier and start the 1D bulk copy of [src, src + bytes) into shared
+// memory at dst (both 16-byte aligned, bytes a multiple of 16; none when bytes is 0).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+  if (bytes > 0)
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
 // 32 consecutive TMEM columns of this warp's 32 lanes
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   uint32_t r[32];
@@ -118,18 +135,26 @@ __global__ void __launch_bounds__(kTcThreads) k_tplz_tc(const TcTile* __restrict
   extern __shared__ __align__(128) unsigned char tc_smem[];
   __shared__ uint32_t taddr_s;
   __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar_ld[2];
+  __shared__ int64_t stage_c0[2];   // first staged sample (in-column index) of each stage
+  __shared__ int stage_busy[2];     // a copy was issued into the stage and not yet waited for
   const int n_shift = 2 * j0 + 1;
   unsigned char* a_hi = tc_smem;
   unsigned char* a_lo = a_hi + kTcASize;
   unsigned char* b_hi = a_lo + kTcASize;
   unsigned char* b_lo = b_hi + n_shift * kTcBShift;
+  unsigned char* stg0 = b_lo + n_shift * kTcBShift;
+  const size_t stage_bytes = tc_stage_bytes(j0);
   const uint32_t s_ahi = (uint32_t)__cvta_generic_to_shared(a_hi);
   const uint32_t s_alo = (uint32_t)__cvta_generic_to_shared(a_lo);
   const uint32_t s_bhi = (uint32_t)__cvta_generic_to_shared(b_hi);
   const uint32_t s_blo = (uint32_t)__cvta_generic_to_shared(b_lo);
+  const uint32_t s_stg0 = (uint32_t)__cvta_generic_to_shared(stg0);
   const uint32_t s_mbar = (uint32_t)__cvta_generic_to_shared(&mbar);
+  const uint32_t s_mld0 = (uint32_t)__cvta_generic_to_shared(&mbar_ld[0]);   // stage st: + 8 st
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rows = kTcM + 2 * j0;
+  const int64_t total = n_tiles * nrhs;
 
   // guard bytes are zero: a mis-read can never see stale values
   for (int i = threadIdx.x; i < (int)(tc_smem_bytes(j0) / 16); i += kTcThreads)
@@ -141,56 +166,63 @@ __global__ void __launch_bounds__(kTcThreads) k_tplz_tc(const TcTile* __restrict
   }
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_mbar));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_mld0));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_mld0 + 8));
     asm volatile("fence.mbarrier_init.release.cluster;");
+    stage_busy[0] = stage_busy[1] = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = taddr_s;
 
-  int loaded_tab = -1;
-  uint32_t phase = 0;
-  bool ok = true;
-  // Operand prefetch: item e = threadIdx.x + 128 p (p < kPf) is k-group e % 8 of stored row e / 8;
-  // the next tile's items are loaded into registers while the current tile's MMAs and epilogue run.
-  constexpr int kPf = (kTcM + 2 * kTcMaxJ0) * kTcKg / kTcThreads + 1;   // 9 items per thread
-  float4 pf[kPf];
-  auto fetch = [&](int64_t item) {
-    if (item >= n_tiles * nrhs) return;
+  // thread 0: start the copy of item `item`'s input range into stage st.  The range is the tile's
+  // rows k0 - j0 .. k0 + 127 + j0 of its block, clipped to the column [0, t_stride) and widened to
+  // 16-byte boundaries; samples outside the block are masked when the stage is read.
+  auto issue = [&](int64_t item, int st) {
+    if (item >= total) return;
     const int rhs = (int)(item % nrhs);
     const TcTile tl = tiles[item / nrhs];
-    const int64_t lo = __ldg(block_off + tl.blk), hi = __ldg(block_off + tl.blk + 1);
-    const float* tr = t + rhs * t_stride;
-    const bool al4 = ((lo | t_stride) & 3) == 0 && (((uintptr_t)tr) & 15) == 0;
-#pragma unroll
-    for (int p = 0; p < kPf; p++) {
-      const int e = threadIdx.x + kTcThreads * p;
-      const int r = e >> 3, kg = e & 7;
-      const int64_t g = lo + (int64_t)kTcB * (tl.k0 - j0 + r) + 4 * kg;
-      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (r < rows) {
-        if (al4 && g >= lo && g + 4 <= hi) {
-          x = __ldg(reinterpret_cast<const float4*>(tr + g));
-        } else {
-          x.x = (g >= lo && g < hi) ? __ldg(tr + g) : 0.f;
-          x.y = (g + 1 >= lo && g + 1 < hi) ? __ldg(tr + g + 1) : 0.f;
-          x.z = (g + 2 >= lo && g + 2 < hi) ? __ldg(tr + g + 2) : 0.f;
-          x.w = (g + 3 >= lo && g + 3 < hi) ? __ldg(tr + g + 3) : 0.f;
-        }
-      }
-      pf[p] = x;
-    }
+    const int64_t lo = __ldg(block_off + tl.blk);
+    const int64_t start = lo + (int64_t)kTcB * (tl.k0 - j0), end = start + (int64_t)kTcB * rows;
+    const int64_t c0 = max(start, (int64_t)0) & ~(int64_t)3;
+    const int64_t c1 = min((end + 3) & ~(int64_t)3, t_stride);
+    const uint32_t bytes = c1 > c0 ? (uint32_t)((c1 - c0) * 4) : 0u;
+    stage_c0[st] = c0;
+    stage_busy[st] = 1;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier reads of the stage first
+    bulk_load(s_stg0 + (uint32_t)(st * stage_bytes), t + rhs * t_stride + c0, bytes, s_mld0 + 8 * st);
   };
-  fetch(blockIdx.x);
-  for (int64_t it = blockIdx.x; it < n_tiles * nrhs && ok; it += gridDim.x) {
+  if (threadIdx.x == 0) {
+    issue(blockIdx.x, 0);
+    issue((int64_t)blockIdx.x + gridDim.x, 1);
+  }
+  __syncthreads();
+
+  int loaded_tab = -1;
+  uint32_t phase = 0, ld_phase = 0;   // ld_phase bit st: the parity stage st waits for next
+  bool ok = true;
+  int k = 0;
+  for (int64_t it = blockIdx.x; it < total && ok; it += gridDim.x, k++) {
+    const int st = k & 1;
+    // this tile's input has arrived (every thread takes the same branch)
+    if (!__syncthreads_and(mbar_wait(s_mld0 + 8 * st, (ld_phase >> st) & 1u) ? 1 : 0)) {
+      ok = false;
+      if (threadIdx.x == 0) atomicExch(err, 1);
+      break;
+    }
+    ld_phase ^= 1u << st;
+    if (threadIdx.x == 0) stage_busy[st] = 0;
     const int rhs = (int)(it % nrhs);
-    const int64_t ti = it / nrhs;
+    const TcTile tl = tiles[it / nrhs];
+    const int64_t lo = __ldg(block_off + tl.blk), hi = __ldg(block_off + tl.blk + 1);
+    const float* stage = reinterpret_cast<const float*>(stg0 + st * stage_bytes);
+    const int64_t c0 = stage_c0[st];
     if (done != nullptr && done[(int64_t)rhs * done_stride] != 0) {
-      fetch(it + gridDim.x);
+      __syncthreads();
+      if (threadIdx.x == 0) issue(it + 2 * (int64_t)gridDim.x, st);
       continue;
     }
-    const TcTile tl = tiles[ti];
-    const int64_t lo = __ldg(block_off + tl.blk), hi = __ldg(block_off + tl.blk + 1);
     const int tab = __ldg(blk_tab + tl.blk);
     const float sc = __ldg(blk_scale + tl.blk);
     if (tab != loaded_tab) {   // T_J hi and lo of this band table (n_shift shifts)
@@ -201,27 +233,30 @@ __global__ void __launch_bounds__(kTcThreads) k_tplz_tc(const TcTile* __restrict
       }
       loaded_tab = tab;
     }
-    // A (hi and lo TF32 split) from the prefetched registers: one 16-byte store per operand and
-    // item (k-groups lie 2192 bytes apart, so 8 consecutive items hit 8 distinct bank groups)
-#pragma unroll
-    for (int p = 0; p < kPf; p++) {
-      const int e = threadIdx.x + kTcThreads * p;
+    // A (hi and lo TF32 split) from the stage: item e is k-group e % 8 of stored row e / 8, one
+    // 16-byte store per operand (k-groups lie 2192 bytes apart: 8 consecutive items, 8 bank groups)
+    for (int e = threadIdx.x; e < rows * kTcKg; e += kTcThreads) {
       const int r = e >> 3, kg = e & 7;
-      if (r < rows) {
-        const float4 x = pf[p];
-        uint4 h, l;
-        h.x = tf32_rna(x.x); l.x = tf32_rna(x.x - __uint_as_float(h.x));
-        h.y = tf32_rna(x.y); l.y = tf32_rna(x.y - __uint_as_float(h.y));
-        h.z = tf32_rna(x.z); l.z = tf32_rna(x.z - __uint_as_float(h.z));
-        h.w = tf32_rna(x.w); l.w = tf32_rna(x.w - __uint_as_float(h.w));
-        const int off = kg * kTcLboA + r * 16;
-        *reinterpret_cast<uint4*>(a_hi + off) = h;
-        *reinterpret_cast<uint4*>(a_lo + off) = l;
+      const int64_t g = lo + (int64_t)kTcB * (tl.k0 - j0 + r) + 4 * kg;
+      float x[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const bool in = g + q >= lo && g + q < hi;   // inside the block: inside the staged range
+        x[q] = in ? stage[in ? g + q - c0 : 0] : 0.f;
       }
+      uint4 h, l;
+      h.x = tf32_rna(x[0]); l.x = tf32_rna(x[0] - __uint_as_float(h.x));
+      h.y = tf32_rna(x[1]); l.y = tf32_rna(x[1] - __uint_as_float(h.y));
+      h.z = tf32_rna(x[2]); l.z = tf32_rna(x[2] - __uint_as_float(h.z));
+      h.w = tf32_rna(x[3]); l.w = tf32_rna(x[3] - __uint_as_float(h.w));
+      const int off = kg * kTcLboA + r * 16;
+      *reinterpret_cast<uint4*>(a_hi + off) = h;
+      *reinterpret_cast<uint4*>(a_lo + off) = l;
     }
     asm volatile("fence.proxy.async.shared::cta;");   // generic-proxy writes -> tensor-core reads
     __syncthreads();
     if (threadIdx.x == 0) {
+      issue(it + 2 * (int64_t)gridDim.x, st);   // the stage is free: the tile after next
       asm volatile("tcgen05.fence::after_thread_sync;");
       uint32_t acc = 0;
       for (int js = 0; js < n_shift; js++) {        // shift J = js - j0
@@ -238,7 +273,6 @@ __global__ void __launch_bounds__(kTcThreads) k_tplz_tc(const TcTile* __restrict
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_mbar));
     }
-    fetch(it + gridDim.x);   // the next tile's operand loads overlap the MMAs and the epilogue
     // every thread must take the same branch (the TMEM load below is warp-collective)
     if (!__syncthreads_and(mbar_wait(s_mbar, phase) ? 1 : 0)) {
       ok = false;
@@ -254,22 +288,22 @@ __global__ void __launch_bounds__(kTcThreads) k_tplz_tc(const TcTile* __restrict
     {
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), v);
-      float* stage = reinterpret_cast<float*>(a_hi);   // [128][33]: padded rows, no bank conflicts
+      float* stg = reinterpret_cast<float*>(a_hi);   // [128][33]: padded rows, no bank conflicts
       const int row = 32 * warp + lane;
 #pragma unroll
-      for (int i = 0; i < kTcB; i++) stage[row * (kTcB + 1) + i] = sc * v[i];
+      for (int i = 0; i < kTcB; i++) stg[row * (kTcB + 1) + i] = sc * v[i];
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     {
       float* ur = u + rhs * u_stride;
-      const float* stage = reinterpret_cast<const float*>(a_hi);
+      const float* stg = reinterpret_cast<const float*>(a_hi);
       const int64_t base = lo + (int64_t)kTcB * tl.k0;
       const bool v4 = ((base | u_stride) & 3) == 0 && (((uintptr_t)ur) & 15) == 0;
       for (int q = threadIdx.x; q < kTcM * kTcB / 4; q += kTcThreads) {
         const int row = q >> 3, c = 4 * (q & 7);
         const int64_t g = base + 4 * (int64_t)q;
-        const float* sv = stage + row * (kTcB + 1) + c;
+        const float* sv = stg + row * (kTcB + 1) + c;
         if (v4 && g + 4 <= hi) {
           *reinterpret_cast<float4*>(ur + g) = make_float4(sv[0], sv[1], sv[2], sv[3]);
         } else {
@@ -280,6 +314,11 @@ __global__ void __launch_bounds__(kTcThreads) k_tplz_tc(const TcTile* __restrict
       }
     }
     __syncthreads();   // the staging rows and A consumed before the next tile overwrites them
+  }
+  // copies still in flight (issued ahead, or a wait that ran out) land before the memory is reused
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < 2; st++)
+      if (stage_busy[st]) mbar_wait(s_mld0 + 8 * st, (ld_phase >> st) & 1u);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();

@@ -105,7 +105,7 @@ __host__ __device__ inline int64_t seg_stride(int n_blk, int log_s) {
 // block, 3xTF32 tcgen05 MMAs over the 2 J0 + 1 row shifts, J0 = ceil(lambda / 32) <= kTcMaxJ0.
 // ---------------------------------------------------------------------------------------------
 constexpr int kTcMaxJ0 = 4;                 // lambda <= 128
-constexpr int kTcAutoLambda = 32;           // MM_TPLZ_AUTO picks the tensor cores up to this lambda
+constexpr int kTcAutoLambda = 64;           // MM_TPLZ_AUTO picks the tensor cores up to this lambda
                                             // (measured crossover against the FFT tiles)
 struct TcTile {
   int32_t blk;   // block
