@@ -1316,9 +1316,15 @@ struct Server {
   int device = 0;
   cudaStream_t stream = nullptr;
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
+  std::condition_variable cv_work, cv_done, cv_plan;
   std::deque<Request*> queue;
   std::vector<Request*> running;   // touched by the server thread only
+  // planner threads build admitted requests' plans, right-hand sides and CG state on their own
+  // streams while the server thread iterates the running ones (under mu: ready, planning, n_running)
+  std::vector<std::thread> planners;
+  std::vector<Request*> ready;     // planned, joining the running set at the next step
+  int planning = 0;                // requests being planned
+  int n_running = 0;               // running.size() as the planners see it
   std::unordered_map<mm_req_t, Request*> all;
   size_t used = 0;
   bool stop = false;
@@ -1360,13 +1366,14 @@ void finish_request(Server* S, Request* r, int status) {
   r->psi.clear(); r->psi.shrink_to_fit();
   r->d.clear(); r->d.shrink_to_fit();
   S->cv_done.notify_all();
+  S->cv_plan.notify_all();   // memory and a slot are free for the next plan
 }
 
 // plan + right-hand side + PCG initialisation of an admitted request.  FP32 requests get an
 // MM_FP32_DF64 plan (FP32 iterations, double-float right-hand side and replacements); FP64-class
 // requests keep the plan precision they asked for, whose FP64-class operator (IEEE FP64 for
 // MM_FP64 / MM_FP32, double-float for MM_DF64 / MM_FP32_DF64) runs in every iteration.
-int start_request(Server* S, Request* r) {
+int start_request(Server* S, Request* r, cudaStream_t ps) {
   r->desc.block_len = r->block_len.data();
   r->desc.pix = r->pix.data();
   r->desc.psi = r->psi.data();
@@ -1376,23 +1383,62 @@ int start_request(Server* S, Request* r) {
   r->desc.toeplitz_algo = MM_TPLZ_FFT;   // the multi-problem launches run the FFT tiles
   r->plan = new Plan();
   r->plan->no_windows = true;
-  int st = build_plan(&r->desc, S->stream, r->plan);
+  int st = build_plan(&r->desc, ps, r->plan);
   if (st != MM_OK) return st;
   Plan* P = r->plan;
   const size_t esz = r->d_is_fp32 ? sizeof(float) : sizeof(double);
   MM_CUDA(cudaMalloc((void**)&r->d_dev, P->N * esz));
   MM_CUDA(cudaMalloc((void**)&r->b_dev, P->n_obs * 3 * sizeof(double)));
-  MM_CUDA(cudaMemcpyAsync(r->d_dev, r->d.data(), P->N * esz, cudaMemcpyHostToDevice, S->stream));
-  st = mm_rhs(reinterpret_cast<mm_plan_t>(P), r->d_dev, r->d_is_fp32, 1, r->b_dev, S->stream);
+  MM_CUDA(cudaMemcpyAsync(r->d_dev, r->d.data(), P->N * esz, cudaMemcpyHostToDevice, ps));
+  st = mm_rhs(reinterpret_cast<mm_plan_t>(P), r->d_dev, r->d_is_fp32, 1, r->b_dev, ps);
   if (st != MM_OK) return st;
   MM_TRY(ensure_cg(P, 1, r->fp32, &r->cg));
   if (!r->fp32) MM_TRY(ensure_df(P, 1));
   r->w = make_work(P, r->cg, 1, r->fp32, r->opts.tol, r->opts.max_iter);
   MM_CUDA(cudaMallocHost((void**)&r->scal_host, sizeof(CgScalars)));
-  MM_CUDA(launch_pack3to4(r->b_dev, P->n_obs, 1, r->cg->b, S->stream));
-  MM_CUDA(launch_cg(CG_INIT, r->w, S->stream));
+  MM_CUDA(launch_pack3to4(r->b_dev, P->n_obs, 1, r->cg->b, ps));
+  MM_CUDA(launch_cg(CG_INIT, r->w, ps));
+  MM_CUDA(cudaStreamSynchronize(ps));   // the server thread uses the state on its own stream
   r->t_admit = Clock::now();
   return MM_OK;
+}
+
+// Planner thread: takes queued requests while slots and the HBM budget allow (counting the ones
+// being planned, planned and running; a request is always taken when none is active), builds
+// each on its own stream and hands it to the server thread.
+void planner_loop(Server* S) {
+  cudaSetDevice(S->device);
+  cudaStream_t ps = nullptr;
+  if (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess) ps = nullptr;
+  while (true) {
+    Request* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lock(S->mu);
+      auto admissible = [&] {
+        if (S->queue.empty()) return false;
+        const int active = S->n_running + S->planning + (int)S->ready.size();
+        if (active >= S->max_slots) return false;
+        return active == 0 || S->used + S->queue.front()->footprint <= S->budget;
+      };
+      S->cv_plan.wait(lock, [&] { return S->stop || admissible(); });
+      if (S->stop) break;
+      r = S->queue.front();
+      S->queue.pop_front();
+      S->used += r->footprint;
+      S->planning += 1;
+      r->state = 1;
+    }
+    const int st = ps ? start_request(S, r, ps) : cuda_fail(cudaErrorInvalidResourceHandle, "planner stream");
+    {
+      std::lock_guard<std::mutex> lock(S->mu);
+      S->planning -= 1;
+      if (st == MM_OK) S->ready.push_back(r);
+    }
+    if (st != MM_OK) finish_request(S, r, st);
+    S->cv_work.notify_all();
+    S->cv_plan.notify_all();
+  }
+  if (ps) cudaStreamDestroy(ps);
 }
 
 // combined tile list and per-problem pointers of the running requests
@@ -1458,30 +1504,18 @@ void server_loop(Server* S) {
   cudaSetDevice(S->device);
   int step = 0;
   while (true) {
-    // admission
+    // admission: requests the planner threads finished join the running set
     {
       std::unique_lock<std::mutex> lock(S->mu);
-      if (S->running.empty() && S->queue.empty() && !S->stop)
+      if (S->running.empty() && S->ready.empty() && !S->stop)
         S->cv_work.wait_for(lock, std::chrono::milliseconds(50));
       if (S->stop) break;
-      while (!S->queue.empty() && (int)S->running.size() < S->max_slots &&
-             (S->running.empty() || S->used + S->queue.front()->footprint <= S->budget)) {
-        Request* r = S->queue.front();
-        S->queue.pop_front();
-        S->used += r->footprint;
-        r->state = 1;
-        lock.unlock();
-        const int st = start_request(S, r);
-        lock.lock();
-        if (st != MM_OK) {
-          lock.unlock();
-          finish_request(S, r, st);
-          lock.lock();
-          continue;
-        }
-        S->running.push_back(r);
+      if (!S->ready.empty()) {
+        for (Request* r : S->ready) S->running.push_back(r);
+        S->ready.clear();
         S->dirty = true;
       }
+      S->n_running = (int)S->running.size();
     }
     if (S->running.empty()) continue;
     if (S->dirty && rebuild_launch(S) != MM_OK) break;
@@ -1564,6 +1598,11 @@ void server_loop(Server* S) {
       }
     }
     S->running.swap(still);
+    {
+      std::lock_guard<std::mutex> lock(S->mu);
+      S->n_running = (int)S->running.size();
+    }
+    S->cv_plan.notify_all();
   }
   // abandoned requests
   for (Request* r : S->running) finish_request(S, r, MM_ECUDA);
@@ -2965,6 +3004,8 @@ int mm_server_create(size_t hbm_budget, int max_slots, mm_server_t* out) {
     return cuda_fail(e, "cudaStreamCreate");
   }
   S->th = std::thread(server_loop, S);
+  constexpr int kPlanners = 2;
+  for (int i = 0; i < kPlanners; i++) S->planners.emplace_back(planner_loop, S);
   *out = reinterpret_cast<mm_server_t>(S);
   return MM_OK;
 }
@@ -3004,7 +3045,7 @@ int mm_submit(mm_server_t server, const mm_problem_desc* desc, const void* d, in
   S->all[r->id] = r;
   S->queue.push_back(r);
   *id = r->id;
-  S->cv_work.notify_all();
+  S->cv_plan.notify_all();
   return MM_OK;
 }
 
@@ -3048,8 +3089,13 @@ void mm_server_destroy(mm_server_t server) {
     std::lock_guard<std::mutex> lock(S->mu);
     S->stop = true;
     S->cv_work.notify_all();
+    S->cv_plan.notify_all();
   }
   if (S->th.joinable()) S->th.join();
+  for (std::thread& t : S->planners)
+    if (t.joinable()) t.join();
+  for (Request* r : S->ready) finish_request(S, r, MM_ECUDA);   // planned, never run
+  S->ready.clear();
   for (auto& kv : S->all) delete kv.second;
   if (S->tiles_dev) cudaFree(S->tiles_dev);
   if (S->probs_dev) cudaFree(S->probs_dev);
