@@ -421,12 +421,14 @@ int mm_deflation_get(mm_plan_t plan, int* k, double* Z, double* theta, void* str
 int mm_deflation_apply(mm_plan_t plan, const double* r, double* z, int nrhs, void* stream);
 
 /*
- * Serving: a request loop with continuous batching (the serving form of the spec task; the
- * paper has none).  A server thread owns one CUDA stream on the current device.  Requests wait in a
- * queue and are admitted while fewer than max_slots run and the estimated device footprint of the
- * running ones stays within hbm_budget; an admitted request's plan (pointing, bands, spectra,
- * block-Jacobi blocks) and PCG state stay resident until it finishes.  Every step runs one PCG
- * iteration of every running request; requests join and leave between steps.
+ * Serving: a request loop with continuous batching (an interface of this library; the paper has
+ * none).  Requests wait in a queue and are admitted while fewer than max_slots are being planned or
+ * run and the estimated device footprint of those stays within hbm_budget (a request is always
+ * admitted when none is active).  Two planner threads build admitted requests' plans (pointing,
+ * bands, spectra, block-Jacobi blocks), right-hand sides and PCG state on their own CUDA streams;
+ * a server thread with one stream runs the iterations, one PCG iteration of every running request
+ * per step; requests join between steps once planned and leave when they finish.  Their state
+ * stays resident until then.
  *   FP32 requests (opts->precision MM_FP32): FP32 operators, all such requests' Toeplitz tiles in a
  *     single launch per step; right-hand side and residual replacement per request with the
  *     double-float FP64-class operators, as mm_pcg_solve on an MM_FP32_DF64 plan (the request's
