@@ -187,6 +187,38 @@ __device__ __forceinline__ void twiddles(const TwiddleTab<C>& tw, int base_idx, 
   }
 }
 
+// Pass tables of the radix-16 passes (R = 16): the 15 twiddles W^{j n1 M/CS} of offset n1, j = 1..15.
+// FP32 complex values are stored in pairs, (j, j + 1) for j = 1, 3, .., 13 as one 16-byte entry of
+// row (j - 1) / 2, then j = 15 alone in row 7 (float2 positions: pair row k at 2 k S + 2 n1, the last
+// at 14 S + n1), so a butterfly reads its twiddles with 7 16-byte and one 8-byte load; other
+// element types keep row j - 1 at (j - 1) S + n1.
+template <typename C>
+__host__ __device__ __forceinline__ constexpr bool paired_ptab() { return sizeof(C) == 8; }
+template <typename C>
+__host__ __device__ __forceinline__ int ptab_pos(int j, int s, int n1) {
+  if constexpr (paired_ptab<C>()) return j == 15 ? 14 * s + n1 : (j - 1) / 2 * 2 * s + 2 * n1 + ((j - 1) & 1);
+  else return (j - 1) * s + n1;
+}
+// a[j] *= twiddle j (CONJ: by its conjugate), j = 1 .. R - 1, from this pass's table
+template <int R, bool CONJ, typename C>
+__device__ __forceinline__ void ptab_twiddle(C (&a)[R], const C* __restrict__ ptab, int S, int n1) {
+  if constexpr (paired_ptab<C>() && R == 16) {
+    const float4* p4 = reinterpret_cast<const float4*>(ptab);
+#pragma unroll
+    for (int k = 0; k < 7; k++) {
+      const float4 v = p4[k * S + n1];
+      const C w0{v.x, v.y}, w1{v.z, v.w};
+      a[2 * k + 1] = CONJ ? c_mulc(a[2 * k + 1], w0) : c_mul(a[2 * k + 1], w0);
+      a[2 * k + 2] = CONJ ? c_mulc(a[2 * k + 2], w1) : c_mul(a[2 * k + 2], w1);
+    }
+    const C w15 = ptab[14 * S + n1];
+    a[15] = CONJ ? c_mulc(a[15], w15) : c_mul(a[15], w15);
+  } else {
+#pragma unroll
+    for (int j = 1; j < R; j++) a[j] = CONJ ? c_mulc(a[j], ptab[(j - 1) * S + n1]) : c_mul(a[j], ptab[(j - 1) * S + n1]);
+  }
+}
+
 // One decimation-in-frequency (FWD) or decimation-in-time (inverse) pass over sub-transforms of
 // size CS = R S with radix R and element stride S, over the MS points held by this CTA.
 // `mfull_over_cs` = M / CS.  `ptab` (optional): this pass's twiddles precomputed as
@@ -213,8 +245,7 @@ __device__ __forceinline__ void fft_pass(C* __restrict__ sm, const TwiddleTab<C>
       dft_small<R, true>(a);
       if (S > 1 && n1 != 0) {
         if (ptab) {
-#pragma unroll
-          for (int j = 1; j < R; j++) a[j] = c_mul(a[j], ptab[(j - 1) * S + n1]);
+          ptab_twiddle<R, false>(a, ptab, S, n1);
         } else {
           C w[R];
           twiddles<R>(tw, n1 * mfull_over_cs, w);
@@ -225,8 +256,7 @@ __device__ __forceinline__ void fft_pass(C* __restrict__ sm, const TwiddleTab<C>
     } else {
       if (S > 1 && n1 != 0) {
         if (ptab) {
-#pragma unroll
-          for (int j = 1; j < R; j++) a[j] = c_mulc(a[j], ptab[(j - 1) * S + n1]);
+          ptab_twiddle<R, true>(a, ptab, S, n1);
         } else {
           C w[R];
           twiddles<R>(tw, n1 * mfull_over_cs, w);
@@ -272,7 +302,7 @@ struct SmemFFT {
       const int r = i - pass_tab_offset(p);
       const int j = r / s + 1, n1 = r % s;
       const int cs = MS >> (4 * p);
-      ptab[i] = tw(j * n1 * (MFULL / cs));
+      ptab[pass_tab_offset(p) + ptab_pos<C>(j, s, n1)] = tw(j * n1 * (MFULL / cs));
     }
   }
 
