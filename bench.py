@@ -944,25 +944,33 @@ def run_deflation(a):
 
 
 def _serve(mm, pool, order, gaps, fp64: bool):
-    """Submit pool[order[i]] after gaps[i] seconds each (Poisson arrivals); returns per-request
-    latencies (ms, submit to completion), infos and the wall time from the first submission."""
+    """Submit pool[order[i]] at the arrival times t0 + gaps[0] + ... + gaps[i] (Poisson arrivals,
+    on an absolute schedule, so the time a submission takes does not thin the stream); returns
+    per-request latencies (ms, submit to completion), infos, the wall time from the first
+    arrival and the host time of the submissions (ms: mean, max)."""
     srv = mm.Server(max_slots=16)
     kw = dict(precision=mm.MM_FP64, plan_precision=mm.MM_DF64) if fp64 else {}
     p = pool[0]
     srv.wait(srv.submit(p["n_det"], p["n_int"], p["block_len"].tolist(), p["n_pix"], p["pix"], p["psi"],
                         p["lam"], p["band"], p["d"], tol=1e-6, **kw))   # warm-up
     t0 = time.perf_counter()
-    ids = []
+    t_arr = t0
+    ids, t_sub = [], []
     for k, gap in zip(order, gaps):
-        time.sleep(gap)
+        t_arr += gap
+        wait = t_arr - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
         p = pool[k]
+        ts = time.perf_counter()
         ids.append(srv.submit(p["n_det"], p["n_int"], p["block_len"].tolist(), p["n_pix"], p["pix"],
                               p["psi"], p["lam"], p["band"], p["d"], tol=1e-6, **kw))
+        t_sub.append(1e3 * (time.perf_counter() - ts))
     infos = [srv.wait(i, raise_on_error=False)[1] for i in ids]
     dt = time.perf_counter() - t0
     srv.close()
     lat = [i.t_queue_ms + i.t_ms for i in infos]
-    return lat, infos, dt
+    return lat, infos, dt, (sum(t_sub) / len(t_sub), max(t_sub))
 
 
 def run_serving(a, n_requests=None, compare_fp64=0):
@@ -990,7 +998,7 @@ def run_serving(a, n_requests=None, compare_fp64=0):
         torch.cuda.empty_cache()
     order = rng.integers(0, len(pool), size=n_requests)
     gaps = rng.exponential(1.0 / a.rate, size=n_requests)
-    lat, infos, dt = _serve(mm, pool, order, gaps, fp64=False)
+    lat, infos, dt, sub = _serve(mm, pool, order, gaps, fp64=False)
     samples = sum(int(pool[k]["pix"].size) for k in order)
     out = {
         "workload": f"serving: {n_requests} requests at mean {a.rate}/s (pool of {len(pool)} seeded shapes: "
@@ -1000,10 +1008,12 @@ def run_serving(a, n_requests=None, compare_fp64=0):
         "offered_per_s": a.rate, "total_samples": samples,
         "status": sorted(set(i.status for i in infos)), "max_batch": max(i.batch for i in infos),
         "iters_mean": float(np.mean([i.iters for i in infos])),
-        "mode": "FP32 iterations batched per launch across requests, double-float rhs and replacement"}
+        "arrivals": "absolute Poisson schedule", "submit_ms_mean": sub[0], "submit_ms_max": sub[1],
+        "mode": "FP32 iterations batched per launch across requests (P, N^-1 and P^T over pixel windows "
+                "and segments, three launches per step), double-float rhs and replacement"}
     if compare_fp64:
         k = min(compare_fp64, n_requests)
-        lat64, inf64, dt64 = _serve(mm, pool, order[:k], gaps[:k], fp64=True)
+        lat64, inf64, dt64, _ = _serve(mm, pool, order[:k], gaps[:k], fp64=True)
         lat32 = lat[:k]
         out["fp64_class_requests"] = {
             "requests": k, "solves_per_s": k / dt64, "p50_ms": float(np.percentile(lat64, 50)),

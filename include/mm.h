@@ -429,10 +429,12 @@ int mm_deflation_apply(mm_plan_t plan, const double* r, double* z, int nrhs, voi
  * a server thread with one stream runs the iterations, one PCG iteration of every running request
  * per step; requests join between steps once planned and leave when they finish.  Their state
  * stays resident until then.
- *   FP32 requests (opts->precision MM_FP32): FP32 operators, all such requests' Toeplitz tiles in a
- *     single launch per step; right-hand side and residual replacement per request with the
- *     double-float FP64-class operators, as mm_pcg_solve on an MM_FP32_DF64 plan (the request's
- *     desc->precision is ignored).
+ *   FP32 requests (opts->precision MM_FP32): FP32 operators over pixel windows, P, N^-1 and P^T of
+ *     all such requests in three shared launches per step (all their window groups, all their
+ *     tile segments); right-hand side and residual replacement per request with the double-float
+ *     FP64-class operators, as mm_pcg_solve on an MM_FP32_DF64 plan (the request's
+ *     desc->precision is ignored).  A failed launch or copy ends the running requests with
+ *     MM_ECUDA; the server goes on with the next ones.
  *   FP64-class requests (opts->precision MM_FP64): plain PCG with the plan's FP64-class operator in
  *     every iteration, in the arithmetic desc->precision selects (IEEE FP64 for MM_FP64 / MM_FP32,
  *     double-float for MM_DF64 / MM_FP32_DF64), one operator launch per request per step.
@@ -440,7 +442,7 @@ int mm_deflation_apply(mm_plan_t plan, const double* r, double* z, int nrhs, voi
 /* Create a server (hbm_budget in bytes, 0 = 80% of the free device memory; max_slots >= 1). */
 int mm_server_create(size_t hbm_budget, int max_slots, mm_server_t* out);
 /* Queue a map-making solve.  desc and d are HOST memory (desc->inputs_on_device must be 0) and are
- * copied before the call returns; d is the TOD [N], float64 (d_is_fp32 = 0) or float32
+ * copied (by up to 8 threads) before the call returns; d is the TOD [N], float64 (d_is_fp32 = 0) or float32
  * (d_is_fp32 = 1).  opts->precision is MM_FP32 or MM_FP64 (above); opts->precond must be MM_PREC_BD;
  * MM_TPLZ_DIRECT plans are refused.  Non-blocking; *id identifies the request.  MM_EINVAL on bad
  * input (validated again at admission: a request that fails there finishes with that status). */

@@ -38,32 +38,64 @@ __device__ __forceinline__ int block_of(const int64_t* __restrict__ off, int32_t
   return lo;
 }
 
-// Each CTA takes a contiguous chunk of the samples and its threads stride through it, so a thread's
-// block index is found once and only moves forward; the weights are the plan's FP64 (cos 2psi, sin 2psi).
+// Each CTA takes a contiguous chunk of the samples and its warps stride through it, lane l of a
+// warp on sample base + l, so a lane's block index is found once and only moves forward; the
+// weights are the plan's FP64 (cos 2psi, sin 2psi).  Consecutive samples of a slow scan often
+// fall on the same pixel: the lanes of each run of equal pixels are summed by a segmented scan
+// across the warp, and the run's last lane adds the sums with one set of atomics.
 __global__ void k_bd_accum(const int32_t* __restrict__ pix, const double2* __restrict__ w64,
                            const int64_t* __restrict__ off, const double* __restrict__ c0_blk,
                            int32_t n_blocks, int64_t N, double* __restrict__ B6,
                            int32_t* __restrict__ hits) {
   const int64_t chunk = (N + gridDim.x - 1) / gridDim.x;
   const int64_t c_lo = (int64_t)blockIdx.x * chunk, c_hi = min(N, c_lo + chunk);
-  int64_t i = c_lo + threadIdx.x;
-  if (i >= c_hi) return;
-  int bi = block_of(off, n_blocks, i);
-  for (; i < c_hi; i += blockDim.x) {
-    while (__ldg(off + bi + 1) <= i) bi++;
-    const int32_t p = pix[i];
-    if (p < 0) continue;
-    const double c0 = c0_blk[bi];
-    const double2 w = w64[i];
-    const double c = w.x, s = w.y;
-    double* b = B6 + 6 * (int64_t)p;
-    atomicAdd(b + 0, c0);
-    atomicAdd(b + 1, c0 * c);
-    atomicAdd(b + 2, c0 * s);
-    atomicAdd(b + 3, c0 * c * c);
-    atomicAdd(b + 4, c0 * c * s);
-    atomicAdd(b + 5, c0 * s * s);
-    atomicAdd(hits + p, 1);
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = c_lo + (threadIdx.x - lane);
+  if (warp0 >= c_hi) return;   // whole warps leave together
+  int bi = block_of(off, n_blocks, min(warp0 + lane, c_hi - 1));
+  for (int64_t base = warp0; base < c_hi; base += blockDim.x) {
+    const int64_t i = base + lane;
+    int32_t p = -1;
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (i < c_hi) {
+      while (__ldg(off + bi + 1) <= i) bi++;
+      p = pix[i];
+      if (p >= 0) {
+        const double c0 = c0_blk[bi];
+        const double2 w = w64[i];
+        const double c = w.x, sn = w.y;
+        v[0] = c0;
+        v[1] = c0 * c;
+        v[2] = c0 * sn;
+        v[3] = c0 * c * c;
+        v[4] = c0 * c * sn;
+        v[5] = c0 * sn * sn;
+      }
+    }
+    // first lane of this lane's run of equal pixels (a max-scan of the run heads)
+    const int32_t p_prev = __shfl_up_sync(0xffffffffu, p, 1);
+    int head = (lane == 0 || p_prev != p) ? lane : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int h = __shfl_up_sync(0xffffffffu, head, o);
+      if (lane >= o) head = max(head, h);
+    }
+    // segmented inclusive sums: the run's last lane holds the run's totals
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+      for (int k = 0; k < 6; k++) {
+        const double t = __shfl_up_sync(0xffffffffu, v[k], o);
+        if (lane - o >= head) v[k] += t;
+      }
+    }
+    const int32_t p_next = __shfl_down_sync(0xffffffffu, p, 1);
+    if (p >= 0 && (lane == 31 || p_next != p)) {
+      double* b = B6 + 6 * (int64_t)p;
+#pragma unroll
+      for (int k = 0; k < 6; k++) atomicAdd(b + k, v[k]);
+      atomicAdd(hits + p, lane - head + 1);
+    }
   }
 }
 

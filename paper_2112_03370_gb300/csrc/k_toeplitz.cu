@@ -839,6 +839,7 @@ int tile_kernels_init() {
   MM_SET((k_tile<float, 1, MODE_APPLY>), kSmemMax);
   MM_SET((k_tile<float, 1, MODE_RHS>), kSmemMax);
   MM_SET((k_tile<float, 1, MODE_APPLY, true>), kSmemMax);
+  MM_SET((k_tile<float, 1, MODE_NINV_T, true>), kSmemMax);
   MM_SET((k_tile<float, 1, MODE_APPLY_T>), kSmemMax);
   MM_SET((k_tile<float, 1, MODE_NINV_T>), kSmemMax);
   MM_SET((k_tile<double, 2, MODE_APPLY>), kSmemBytes64);
@@ -946,6 +947,12 @@ cudaError_t launch_tiles_fp32_multi(const TileArgs& a, int halo_samples, cudaStr
   const size_t smem = kSmemBytes32 + (size_t)halo_samples * sizeof(float);
   if (smem > kSmemMax || a.nrhs != 1 || a.probs == nullptr) return cudaErrorInvalidValue;
   return launch_tiles<float, 1, MODE_APPLY, true>(a, smem, s);
+}
+
+cudaError_t launch_ninv32_multi(const TileArgs& a, int halo_samples, cudaStream_t s) {
+  const size_t smem = kSmemBytes32 + (size_t)halo_samples * sizeof(float);
+  if (smem > kSmemMax || a.nrhs != 1 || a.probs == nullptr) return cudaErrorInvalidValue;
+  return launch_tiles<float, 1, MODE_NINV_T, true>(a, smem, s);
 }
 
 int fp32_max_halo_samples() { return (int)((kSmemMax - kSmemBytes32) / sizeof(float)); }

@@ -234,6 +234,21 @@ __device__ __forceinline__ void visit_chunk(const PGroup& G, const int64_t* __re
   for (int q = w.ql; q < nq; q += w.lpc) f_quad(a0, q);
 }
 
+// L2 prefetch of the lines of samples [lo, lo + len) of one array, spread over the LPC lanes of a
+// chunk: elements lo + k (128 / sizeof(T)) and the last one touch every line of the range, and
+// every address stays inside it.  A warp issues it for the chunk of its next iteration, so that
+// iteration's loads find their lines in L2 while this one waits on DRAM.  Used by the un-point
+// kernel and the double-float point kernel (the FP32 point kernel measured slower with it: its
+// shared-memory adds, not its loads, set its pace).
+template <typename T>
+__device__ __forceinline__ void prefetch_chunk(const T* base, int64_t lo, int len, const ChunkWalk& w) {
+  constexpr int kPerLine = 128 / (int)sizeof(T);
+  for (int o = w.ql * kPerLine; o < len; o += w.lpc * kPerLine)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(base + lo + o)));
+  if (w.ql == 0 && len > 0)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(base + lo + len - 1)));
+}
+
 // Pointing loads (slot, angle): evict-first when a pass has one column; with several columns the
 // CTA reads the same group's pointing once per column, so it is kept in L2 for the later ones.
 template <typename T>
@@ -249,14 +264,26 @@ constexpr int kAccStride = kWinCap + kWinCap / 32;
 constexpr int kWinEntries = kWinCap + kWinCap / 8;
 
 // t = P x over the windows: one CTA per group, the group's map entries of column r in shared
-// memory, then one coalesced pass over the group's samples.
+// memory, then one coalesced pass over the group's samples.  MULTI: the group's problem (one
+// column) comes from probs[G.prob].
+template <bool MULTI>
 __global__ void __launch_bounds__(kWinThreads, 3) k_unpoint_win32(
     const PGroup* __restrict__ groups, const int64_t* __restrict__ block_off,
     const uint16_t* __restrict__ slot, const int32_t* __restrict__ slot_pix, const float* __restrict__ ang2,
     const float4* __restrict__ x4, int64_t x_stride4, int nrhs, const int32_t* __restrict__ done,
-    int done_stride, float* __restrict__ t, int64_t t_stride) {
+    int done_stride, float* __restrict__ t, int64_t t_stride, const WinProb* __restrict__ probs) {
   extern __shared__ float4 win[];   // [kWinEntries], slot k at win_index(k)
   const PGroup G = groups[blockIdx.x];
+  if constexpr (MULTI) {
+    const WinProb& pp = probs[G.prob];
+    block_off = pp.block_off;
+    slot = pp.slot;
+    slot_pix = pp.slot_pix;
+    ang2 = pp.ang2;
+    x4 = reinterpret_cast<const float4*>(pp.x);
+    t = pp.t;
+    done = pp.done;
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const ChunkWalk cw = chunk_walk(G, lane);
   const bool keep = nrhs > 1;
@@ -278,6 +305,13 @@ __global__ void __launch_bounds__(kWinThreads, 3) k_unpoint_win32(
     for (int c0 = warp * cw.cpi; c0 < G.n_blk; c0 += kWarps * cw.cpi) {
       const int c = c0 + cw.sub;
       if (c >= G.n_blk) continue;
+      if (c + kWarps * cw.cpi < G.n_blk) {
+        int64_t lo;
+        int len;
+        group_chunk(G, block_off, c + kWarps * cw.cpi, lo, len);
+        prefetch_chunk(slot, lo, len, cw);
+        prefetch_chunk(ang2, lo, len, cw);
+      }
       visit_chunk(
           G, block_off, c, cw,
           [&](int64_t a0, int q) {
@@ -304,11 +338,22 @@ cudaError_t launch_unpoint_win32(const PGroup* groups, int64_t n_groups, const i
   if (n_groups > 0x7fffffffLL || t_stride % 4 != 0) return cudaErrorInvalidValue;
   static cudaError_t st = cudaSuccess;
   static bool set = false;
-  MM_TRY_CUDA(smem_limit_once(k_unpoint_win32, kUnpointSmem, st, set));
-  k_unpoint_win32<<<(unsigned)n_groups, kWinThreads, kUnpointSmem, s>>>(groups, block_off, slot, slot_pix, ang2,
-                                                                          reinterpret_cast<const float4*>(x4),
-                                                                          x_stride / 4, nrhs, done, done_stride, t,
-                                                                          t_stride);
+  MM_TRY_CUDA(smem_limit_once(k_unpoint_win32<false>, kUnpointSmem, st, set));
+  k_unpoint_win32<false><<<(unsigned)n_groups, kWinThreads, kUnpointSmem, s>>>(
+      groups, block_off, slot, slot_pix, ang2, reinterpret_cast<const float4*>(x4), x_stride / 4, nrhs, done,
+      done_stride, t, t_stride, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpoint_win32_multi(const PGroup* groups, int64_t n_groups, const WinProb* probs,
+                                       cudaStream_t s) {
+  if (n_groups == 0) return cudaSuccess;
+  if (n_groups > 0x7fffffffLL || probs == nullptr) return cudaErrorInvalidValue;
+  static cudaError_t st = cudaSuccess;
+  static bool set = false;
+  MM_TRY_CUDA(smem_limit_once(k_unpoint_win32<true>, kUnpointSmem, st, set));
+  k_unpoint_win32<true><<<(unsigned)n_groups, kWinThreads, kUnpointSmem, s>>>(
+      groups, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 1, nullptr, 0, nullptr, 0, probs);
   return cudaGetLastError();
 }
 
@@ -316,13 +361,24 @@ cudaError_t launch_unpoint_win32(const PGroup* groups, int64_t n_groups, const i
 // memory (three FP32 shared-memory adds per sample), then one float4 global atomic per distinct
 // pixel of the group.
 constexpr size_t kPointSmem = (size_t)3 * kAccStride * sizeof(float);
+template <bool MULTI>
 __global__ void __launch_bounds__(kWinThreads, 3) k_point_win32(
     const PGroup* __restrict__ groups, const int64_t* __restrict__ block_off,
     const uint16_t* __restrict__ slot, const int32_t* __restrict__ slot_pix, const float* __restrict__ ang2,
     const float* __restrict__ u, int64_t u_stride, int nrhs, const int32_t* __restrict__ done, int done_stride,
-    float4* __restrict__ y4, int64_t y_stride4) {
+    float4* __restrict__ y4, int64_t y_stride4, const WinProb* __restrict__ probs) {
   extern __shared__ float acc[];   // [3][kAccStride]
   const PGroup G = groups[blockIdx.x];
+  if constexpr (MULTI) {
+    const WinProb& pp = probs[G.prob];
+    block_off = pp.block_off;
+    slot = pp.slot;
+    slot_pix = pp.slot_pix;
+    ang2 = pp.ang2;
+    u = pp.u;
+    y4 = reinterpret_cast<float4*>(pp.y);
+    done = pp.done;
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const ChunkWalk cw = chunk_walk(G, lane);
   const int n_pad = acc_index(G.n_slots);
@@ -385,10 +441,22 @@ cudaError_t launch_point_win32(const PGroup* groups, int64_t n_groups, const int
   if (n_groups > 0x7fffffffLL || u_stride % 4 != 0) return cudaErrorInvalidValue;
   static cudaError_t st = cudaSuccess;
   static bool set = false;
-  MM_TRY_CUDA(smem_limit_once(k_point_win32, kPointSmem, st, set));
-  k_point_win32<<<(unsigned)n_groups, kWinThreads, kPointSmem, s>>>(groups, block_off, slot, slot_pix, ang2, u,
-                                                                      u_stride, nrhs, done, done_stride,
-                                                                      reinterpret_cast<float4*>(y4), y_stride / 4);
+  MM_TRY_CUDA(smem_limit_once(k_point_win32<false>, kPointSmem, st, set));
+  k_point_win32<false><<<(unsigned)n_groups, kWinThreads, kPointSmem, s>>>(
+      groups, block_off, slot, slot_pix, ang2, u, u_stride, nrhs, done, done_stride, reinterpret_cast<float4*>(y4),
+      y_stride / 4, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_point_win32_multi(const PGroup* groups, int64_t n_groups, const WinProb* probs,
+                                     cudaStream_t s) {
+  if (n_groups == 0) return cudaSuccess;
+  if (n_groups > 0x7fffffffLL || probs == nullptr) return cudaErrorInvalidValue;
+  static cudaError_t st = cudaSuccess;
+  static bool set = false;
+  MM_TRY_CUDA(smem_limit_once(k_point_win32<true>, kPointSmem, st, set));
+  k_point_win32<true><<<(unsigned)n_groups, kWinThreads, kPointSmem, s>>>(
+      groups, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 1, nullptr, 0, nullptr, 0, probs);
   return cudaGetLastError();
 }
 
@@ -758,9 +826,18 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_point_win_df(
     };
     const int n_it = (G.n_blk + cw.cpi - 1) / cw.cpi;
     const int per = (n_it + kWarps - 1) / kWarps;
-    for (int it = warp * per; it < min(n_it, (warp + 1) * per); it++) {
+    const int it_end = min(n_it, (warp + 1) * per);
+    for (int it = warp * per; it < it_end; it++) {
       const int c = it * cw.cpi + cw.sub;
       if (c >= G.n_blk) continue;
+      if (it + 1 < it_end && c + cw.cpi < G.n_blk) {
+        int64_t lo;
+        int len;
+        group_chunk(G, block_off, c + cw.cpi, lo, len);
+        prefetch_chunk(slot, lo, len, cw);
+        prefetch_chunk(wdf, lo, len, cw);
+        prefetch_chunk(ur, lo, len, cw);
+      }
       visit_chunk(
           G, block_off, c, cw,
           [&](int64_t a0, int q) {

@@ -3,6 +3,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <cmath>
@@ -432,6 +433,7 @@ int build_windows(Plan* P, cudaStream_t s) {
     dfree(P->slot);
     dfree(P->slot_pix);
     P->n_groups = 0;
+    P->groups_host.clear();
   }
   if (P->seg_ent) {
     P->bytes -= (size_t)P->n_ent * (sizeof(uint32_t) + sizeof(float)) + (size_t)P->n_sub_total * sizeof(int32_t);
@@ -538,6 +540,7 @@ int build_windows(Plan* P, cudaStream_t s) {
   MM_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   MM_CUDA(cudaStreamSynchronize(s));
   if (herr != 0) return fail(MM_ECUDA, "pixel windows: slot tables do not match the counts");
+  P->groups_host = std::move(done);
   if (seg) {
     MM_TRY(dalloc(P, &P->seg_ent, (size_t)n_ent));
     MM_TRY(dalloc(P, &P->seg_ang, (size_t)n_ent));
@@ -684,7 +687,8 @@ int build_plan(const mm_problem_desc* d, cudaStream_t us, Plan* P) {
   MM_CUDA(launch_twiddles(P->tw64, P->tw32, costab_d, s));
   // FP32 N^-1 on 65536-sample tiles (2-CTA clusters) when a 32768-sample tile would keep less than
   // 5/8 of its outputs: tables built here, used when mm_autotune measures them faster
-  P->big = P->precision == MM_FP32 && P->algo == MM_TPLZ_FFT && !P->tc && !P->no_windows && lam > kBigTileLambda;
+  P->big = P->precision == MM_FP32 && P->algo == MM_TPLZ_FFT && !P->tc && !P->no_windows && !P->no_big &&
+           lam > kBigTileLambda;
   if (P->big) {
     const int lb = 2 * kL, mb = 2 * kM;
     std::vector<double> cb(lb);
@@ -1284,14 +1288,55 @@ int blk_apply(Plan* P, BlkState* b, int t, bool fp32, cudaStream_t s) {
 // ---------------------------------------------------------------------------------------------
 using Clock = std::chrono::steady_clock;
 
+// Copy n bytes with up to 8 threads.  mm_submit copies a request's pointing and TOD (16 bytes per
+// sample with an FP64 TOD: hundreds of MB) before it returns; one thread copying into fresh pages
+// (each first touch a page fault) takes tens of ms per request and would bound the rate at which
+// a client can submit.
+void par_copy(void* dst, const void* src, size_t n) {
+  constexpr size_t kChunk = (size_t)32 << 20;
+  const int nt = (int)std::min<size_t>(8, (n + kChunk - 1) / kChunk);
+  if (nt <= 1) {
+    if (n) std::memcpy(dst, src, n);
+    return;
+  }
+  const size_t per = (n + nt - 1) / nt;
+  std::vector<std::thread> th;
+  for (int i = 1; i < nt; i++) {
+    const size_t lo = (size_t)i * per, hi = std::min(n, lo + per);
+    if (lo < hi)
+      th.emplace_back([=] { std::memcpy((char*)dst + lo, (const char*)src + lo, hi - lo); });
+  }
+  std::memcpy(dst, src, std::min(per, n));
+  for (std::thread& t : th) t.join();
+}
+
+// Owning host array whose elements are left uninitialised until par_copy writes them (a
+// std::vector would first zero-fill every page on the calling thread).
+template <typename T>
+struct HostArray {
+  std::unique_ptr<T[]> p;
+  size_t n = 0;
+  void copy_from(const T* src, size_t count) {
+    p.reset(count ? new T[count] : nullptr);
+    n = count;
+    par_copy(p.get(), src, count * sizeof(T));
+  }
+  T* data() { return p.get(); }
+  size_t size() const { return n; }
+  void release() {
+    p.reset();
+    n = 0;
+  }
+};
+
 struct Request {
   mm_req_t id = 0;
   mm_problem_desc desc{};
   std::vector<int64_t> block_len;
-  std::vector<int32_t> pix;
-  std::vector<float> psi;
+  HostArray<int32_t> pix;
+  HostArray<float> psi;
   std::vector<double> band;
-  std::vector<unsigned char> d;   // the TOD, float64 or float32 (d_is_fp32)
+  HostArray<unsigned char> d;     // the TOD, float64 or float32 (d_is_fp32)
   int d_is_fp32 = 0;
   bool fp32 = true;               // FP32 iterations (batched) or FP64-class iterations (own launches)
   mm_solve_opts opts{};
@@ -1330,12 +1375,27 @@ struct Server {
   bool stop = false;
   mm_req_t next_id = 1;
   std::thread th;
+  // one server step's launches: requests with pixel windows run P, N^-1 and P^T over all their
+  // groups and segments in three launches (wgroups / wprobs, ntiles / nprobs); requests whose plan
+  // has no windows run the fused tiles (un-pointing in the gather, per-sample scatter) in one
   TileDesc* tiles_dev = nullptr;
   size_t tiles_cap = 0;
   ProbPtrs* probs_dev = nullptr;
   size_t probs_cap = 0;
   int64_t n_tiles = 0;
   int halo = 0;
+  PGroup* wgroups_dev = nullptr;
+  size_t wgroups_cap = 0;
+  int64_t n_wgroups = 0;
+  WinProb* wprobs_dev = nullptr;
+  size_t wprobs_cap = 0;
+  TileDesc* ntiles_dev = nullptr;
+  size_t ntiles_cap = 0;
+  int64_t n_ntiles = 0;
+  ProbPtrs* nprobs_dev = nullptr;
+  size_t nprobs_cap = 0;
+  int nhalo = 0;
+  const float2* tw32 = nullptr;    // twiddles of a running request's plan (the same in every plan)
   bool dirty = true;
 };
 
@@ -1343,8 +1403,8 @@ size_t estimate_footprint(const Request& r) {
   int64_t N = 0;
   for (int64_t v : r.block_len) N += v;
   // pointing (pixel, angle, reduced angle, window slot), FP32, FP64 and df64 weights, un-pointed
-  // FP32 and df64 buffers, N^-1 t and the TOD: 90 bytes per sample
-  return (size_t)N * 90 + (size_t)r.desc.n_pix * 480 + ((size_t)64 << 20);
+  // FP32 and df64 buffers, N^-1 t in FP32 and df64 and the TOD: 100 bytes per sample
+  return (size_t)N * 100 + (size_t)r.desc.n_pix * 480 + ((size_t)64 << 20);
 }
 
 void finish_request(Server* S, Request* r, int status) {
@@ -1362,9 +1422,9 @@ void finish_request(Server* S, Request* r, int status) {
   std::lock_guard<std::mutex> lock(S->mu);
   r->state = 2;
   S->used -= std::min(S->used, r->footprint);
-  r->pix.clear(); r->pix.shrink_to_fit();
-  r->psi.clear(); r->psi.shrink_to_fit();
-  r->d.clear(); r->d.shrink_to_fit();
+  r->pix.release();
+  r->psi.release();
+  r->d.release();
   S->cv_done.notify_all();
   S->cv_plan.notify_all();   // memory and a slot are free for the next plan
 }
@@ -1382,10 +1442,12 @@ int start_request(Server* S, Request* r, cudaStream_t ps) {
   if (r->fp32) r->desc.precision = MM_FP32_DF64;
   r->desc.toeplitz_algo = MM_TPLZ_FFT;   // the multi-problem launches run the FFT tiles
   r->plan = new Plan();
-  r->plan->no_windows = true;
+  r->plan->no_windows = !r->fp32;        // FP64-class requests never run the FP32 operators
+  r->plan->no_big = true;
   int st = build_plan(&r->desc, ps, r->plan);
   if (st != MM_OK) return st;
   Plan* P = r->plan;
+  if (r->fp32 && P->groups) MM_TRY(ensure_t32(P, 1));   // t = P x and u = N^-1 t of the window path
   const size_t esz = r->d_is_fp32 ? sizeof(float) : sizeof(double);
   MM_CUDA(cudaMalloc((void**)&r->d_dev, P->N * esz));
   MM_CUDA(cudaMalloc((void**)&r->b_dev, P->n_obs * 3 * sizeof(double)));
@@ -1441,48 +1503,107 @@ void planner_loop(Server* S) {
   if (ps) cudaStreamDestroy(ps);
 }
 
-// combined tile list and per-problem pointers of the running requests
+// grow (after the stream's work that reads it) and fill one device list of a server step
+template <typename T>
+static int upload_list(const std::vector<T>& v, T*& dev, size_t& cap, cudaStream_t s) {
+  if (v.size() > cap) {
+    MM_CUDA(cudaStreamSynchronize(s));
+    if (dev) cudaFree(dev);
+    dev = nullptr;
+    cap = 0;
+    MM_CUDA(cudaMalloc((void**)&dev, (v.size() * 2 + 4) * sizeof(T)));
+    cap = v.size() * 2 + 4;
+  }
+  if (!v.empty()) MM_CUDA(cudaMemcpyAsync(dev, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  return MM_OK;
+}
+
+// combined launch lists and per-problem pointers of the running FP32 requests
 int rebuild_launch(Server* S) {
-  std::vector<TileDesc> tiles;
-  std::vector<ProbPtrs> probs;
-  int halo = 0;
+  std::vector<TileDesc> tiles, ntiles;
+  std::vector<ProbPtrs> probs, nprobs;
+  std::vector<PGroup> wgroups;
+  std::vector<WinProb> wprobs;
+  int halo = 0, nhalo = 0;
+  S->tw32 = nullptr;
   for (size_t i = 0; i < S->running.size(); i++) {
     Request* r = S->running[i];
     if (!r->fp32) continue;   // FP64-class requests run their own iterations
     Plan* P = r->plan;
-    for (TileDesc td : P->segs_host) {
-      td.prob = (int32_t)probs.size();
-      tiles.push_back(td);
-    }
-    halo = std::max(halo, (int)P->seg_halo);
+    const int32_t* halt = reinterpret_cast<const int32_t*>(r->cg->scal) + kHaltOffsetInts;
+    if (!S->tw32) S->tw32 = P->tw32;
     ProbPtrs pp{};
     pp.lpix = P->lpix;
     pp.w32 = P->w32;
     pp.w64 = P->w64;
     pp.tab = P->tab32;
-    pp.x = r->cg->p32;
-    pp.y = r->cg->q32;
-    pp.done = reinterpret_cast<const int32_t*>(r->cg->scal) + kHaltOffsetInts;
-    probs.push_back(pp);
+    pp.done = halt;
+    if (P->groups && P->t32 && P->u32) {
+      // P over the windows (x = p32 -> t), N^-1 on the segments (t -> u), P^T over the windows
+      // (u -> q32)
+      for (PGroup g : P->groups_host) {
+        g.prob = (int32_t)wprobs.size();
+        wgroups.push_back(g);
+      }
+      wprobs.push_back(WinProb{P->block_off_dev, P->slot, P->slot_pix, P->ang2, r->cg->p32, P->t32, P->u32,
+                               r->cg->q32, halt});
+      for (TileDesc td : P->segs_host) {
+        td.prob = (int32_t)nprobs.size();
+        ntiles.push_back(td);
+      }
+      nhalo = std::max(nhalo, (int)P->seg_halo);
+      pp.x = P->t32;
+      pp.y = P->u32;
+      nprobs.push_back(pp);
+    } else {
+      for (TileDesc td : P->segs_host) {
+        td.prob = (int32_t)probs.size();
+        tiles.push_back(td);
+      }
+      halo = std::max(halo, (int)P->seg_halo);
+      pp.x = r->cg->p32;
+      pp.y = r->cg->q32;
+      probs.push_back(pp);
+    }
   }
-  if (tiles.size() > S->tiles_cap) {
-    if (S->tiles_dev) cudaFree(S->tiles_dev);
-    S->tiles_cap = tiles.size() * 2;
-    MM_CUDA(cudaMalloc((void**)&S->tiles_dev, S->tiles_cap * sizeof(TileDesc)));
-  }
-  if (probs.size() > S->probs_cap) {
-    if (S->probs_dev) cudaFree(S->probs_dev);
-    S->probs_cap = probs.size() * 2 + 4;
-    MM_CUDA(cudaMalloc((void**)&S->probs_dev, S->probs_cap * sizeof(ProbPtrs)));
-  }
-  if (!tiles.empty())
-    MM_CUDA(cudaMemcpyAsync(S->tiles_dev, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, S->stream));
-  if (!probs.empty())
-    MM_CUDA(cudaMemcpyAsync(S->probs_dev, probs.data(), probs.size() * sizeof(ProbPtrs), cudaMemcpyHostToDevice, S->stream));
+  MM_TRY(upload_list(tiles, S->tiles_dev, S->tiles_cap, S->stream));
+  MM_TRY(upload_list(probs, S->probs_dev, S->probs_cap, S->stream));
+  MM_TRY(upload_list(ntiles, S->ntiles_dev, S->ntiles_cap, S->stream));
+  MM_TRY(upload_list(nprobs, S->nprobs_dev, S->nprobs_cap, S->stream));
+  MM_TRY(upload_list(wgroups, S->wgroups_dev, S->wgroups_cap, S->stream));
+  MM_TRY(upload_list(wprobs, S->wprobs_dev, S->wprobs_cap, S->stream));
   MM_CUDA(cudaStreamSynchronize(S->stream));   // host vectors go out of scope
   S->n_tiles = (int64_t)tiles.size();
   S->halo = halo;
+  S->n_ntiles = (int64_t)ntiles.size();
+  S->nhalo = nhalo;
+  S->n_wgroups = (int64_t)wgroups.size();
   S->dirty = false;
+  return MM_OK;
+}
+
+// one A-application of every running FP32 request (accumulated into its zeroed q32)
+int enqueue_multi_apply(Server* S, cudaStream_t s) {
+  if (S->n_wgroups > 0) {
+    MM_CUDA(launch_unpoint_win32_multi(S->wgroups_dev, S->n_wgroups, S->wprobs_dev, s));
+    TileArgs a{};
+    a.tiles = S->ntiles_dev;
+    a.n_tiles = S->n_ntiles;
+    a.nrhs = 1;
+    a.tw = S->tw32;
+    a.probs = S->nprobs_dev;
+    MM_CUDA(launch_ninv32_multi(a, S->nhalo, s));
+    MM_CUDA(launch_point_win32_multi(S->wgroups_dev, S->n_wgroups, S->wprobs_dev, s));
+  }
+  if (S->n_tiles > 0) {
+    TileArgs a{};
+    a.tiles = S->tiles_dev;
+    a.n_tiles = S->n_tiles;
+    a.nrhs = 1;
+    a.tw = S->tw32;
+    a.probs = S->probs_dev;
+    MM_CUDA(launch_tiles_fp32_multi(a, S->halo, s));
+  }
   return MM_OK;
 }
 
@@ -1518,62 +1639,82 @@ void server_loop(Server* S) {
       S->n_running = (int)S->running.size();
     }
     if (S->running.empty()) continue;
-    if (S->dirty && rebuild_launch(S) != MM_OK) break;
+    // a failed launch or copy ends every running request with MM_ECUDA (no result is read from a
+    // state the device did not write); the server goes on with the next requests
+    auto abort_running = [&] {
+      cudaGetLastError();   // a launch error is not sticky: clear it
+      for (Request* r : S->running) finish_request(S, r, MM_ECUDA);
+      S->running.clear();
+      S->dirty = true;
+      std::lock_guard<std::mutex> lock(S->mu);
+      S->n_running = 0;
+    };
+    if (S->dirty && rebuild_launch(S) != MM_OK) {
+      abort_running();
+      continue;
+    }
     const int nb = (int)S->running.size();
     for (Request* r : S->running) r->batch = std::max(r->batch, nb);
-    // one PCG iteration of every running request: one tile launch for all FP32 requests, the
-    // FP64-class requests' own operator launches after it
+    // one PCG iteration of every running request: the FP32 requests' A-applications in shared
+    // launches (three over the pixel windows and segments, one of fused tiles for plans without
+    // windows), the FP64-class requests' own operator launches after them
     cudaStream_t s = S->stream;
-    const Request* first32 = nullptr;
+    bool ok = true;
     for (Request* r : S->running)
-      if (r->fp32) {
-        if (!first32) first32 = r;
-        launch_cg(CG_PUPDATE, r->w, s);
-      }
-    if (first32) {
-      TileArgs a{};
-      a.tiles = S->tiles_dev;
-      a.n_tiles = S->n_tiles;
-      a.nrhs = 1;
-      a.tw = first32->plan->tw32;
-      a.probs = S->probs_dev;
-      a.done_stride = 0;
-      launch_tiles_fp32_multi(a, S->halo, s);
-    }
+      if (r->fp32) ok = ok && launch_cg(CG_PUPDATE, r->w, s) == cudaSuccess;
+    ok = ok && enqueue_multi_apply(S, s) == MM_OK;
     for (Request* r : S->running) {
       if (r->fp32) {
-        launch_cg(CG_DOT_PQ, r->w, s);
-        launch_cg(CG_UPDATE, r->w, s);
+        ok = ok && launch_cg(CG_DOT_PQ, r->w, s) == cudaSuccess;
+        ok = ok && launch_cg(CG_UPDATE, r->w, s) == cudaSuccess;
       } else {
-        enqueue_iteration(r->plan, r->w, 1, false, s);
+        ok = ok && enqueue_iteration(r->plan, r->w, 1, false, s) == MM_OK;
       }
       r->launched += 1;
+    }
+    if (!ok) {
+      abort_running();
+      continue;
     }
     step += 1;
     if (step % 4 != 0) continue;
     for (Request* r : S->running)
-      cudaMemcpyAsync(r->scal_host, r->cg->scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
+      ok = ok && cudaMemcpyAsync(r->scal_host, r->cg->scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, s) ==
+                     cudaSuccess;
+    if (!ok || cudaStreamSynchronize(s) != cudaSuccess) {
+      abort_running();
+      continue;
+    }
     std::vector<Request*> still;
     for (Request* r : S->running) {
       const CgScalars sc = *r->scal_host;
       const int rel_every = r->opts.reliable_every > 0 ? r->opts.reliable_every : 50;
+      bool r_ok = true;   // this request's replacement or report ran and its scalars were read
       if (r->fp32 && !sc.done && (sc.paused || sc.since_rep >= rel_every)) {   // FP64 residual replacement
         Plan* P = r->plan;
-        cudaMemsetAsync(r->cg->q, 0, P->n_obs * 4 * sizeof(double), s);
-        apply64_internal(P, r->cg->x, r->cg->q, 1, s,
-                         reinterpret_cast<const int32_t*>(r->cg->scal) + kDoneOffsetInts, kScalStrideInts);
-        launch_cg(CG_REPLACE, r->w, s);
-        cudaMemcpyAsync(r->scal_host, r->cg->scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, s);
-        cudaStreamSynchronize(s);
+        r_ok = cudaMemsetAsync(r->cg->q, 0, P->n_obs * 4 * sizeof(double), s) == cudaSuccess &&
+               apply64_internal(P, r->cg->x, r->cg->q, 1, s,
+                                reinterpret_cast<const int32_t*>(r->cg->scal) + kDoneOffsetInts,
+                                kScalStrideInts) == MM_OK &&
+               launch_cg(CG_REPLACE, r->w, s) == cudaSuccess &&
+               cudaMemcpyAsync(r->scal_host, r->cg->scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, s) ==
+                   cudaSuccess &&
+               cudaStreamSynchronize(s) == cudaSuccess;
       }
       if (!r->fp32 && sc.done) {   // FP64-class request: the true residual for the report
         Plan* P = r->plan;
-        cudaMemsetAsync(r->cg->q, 0, P->n_obs * 4 * sizeof(double), s);
-        apply64_internal(P, r->cg->x, r->cg->q, 1, s);
-        launch_cg(CG_TRUE_RES, r->w, s);
-        cudaMemcpyAsync(r->scal_host, r->cg->scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, s);
-        cudaStreamSynchronize(s);
+        r_ok = cudaMemsetAsync(r->cg->q, 0, P->n_obs * 4 * sizeof(double), s) == cudaSuccess &&
+               apply64_internal(P, r->cg->x, r->cg->q, 1, s) == MM_OK &&
+               launch_cg(CG_TRUE_RES, r->w, s) == cudaSuccess &&
+               cudaMemcpyAsync(r->scal_host, r->cg->scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, s) ==
+                   cudaSuccess &&
+               cudaStreamSynchronize(s) == cudaSuccess;
+      }
+      if (!r_ok) {
+        cudaGetLastError();
+        finish_request(S, r, MM_ECUDA);
+        S->dirty = true;
+        continue;
       }
       const CgScalars sc2 = *r->scal_host;
       const double el = std::chrono::duration<double, std::micro>(Clock::now() - r->t_admit).count();
@@ -3030,12 +3171,12 @@ int mm_submit(mm_server_t server, const mm_problem_desc* desc, const void* d, in
     if (v < 0) { delete r; return fail(MM_EINVAL, "negative block length"); }
     N += v;
   }
-  r->pix.assign(desc->pix, desc->pix + N);
-  r->psi.assign(desc->psi, desc->psi + N);
+  r->pix.copy_from(desc->pix, (size_t)N);
+  r->psi.copy_from(desc->psi, (size_t)N);
   r->band.assign(desc->band, desc->band + (size_t)nb * (desc->lambda + 1));
   r->d_is_fp32 = d_is_fp32 ? 1 : 0;
   const unsigned char* db = reinterpret_cast<const unsigned char*>(d);
-  r->d.assign(db, db + (size_t)N * (d_is_fp32 ? sizeof(float) : sizeof(double)));
+  r->d.copy_from(db, (size_t)N * (d_is_fp32 ? sizeof(float) : sizeof(double)));
   r->fp32 = opts->precision == MM_FP32;
   r->opts = *opts;
   r->footprint = estimate_footprint(*r);
@@ -3099,6 +3240,10 @@ void mm_server_destroy(mm_server_t server) {
   for (auto& kv : S->all) delete kv.second;
   if (S->tiles_dev) cudaFree(S->tiles_dev);
   if (S->probs_dev) cudaFree(S->probs_dev);
+  if (S->ntiles_dev) cudaFree(S->ntiles_dev);
+  if (S->nprobs_dev) cudaFree(S->nprobs_dev);
+  if (S->wgroups_dev) cudaFree(S->wgroups_dev);
+  if (S->wprobs_dev) cudaFree(S->wprobs_dev);
   if (S->stream) cudaStreamDestroy(S->stream);
   delete S;
 }

@@ -79,9 +79,26 @@ struct PGroup {
   int32_t log_w;     // window length W = 2^log_w
   int32_t n_slots;   // distinct kept pixels (0 .. kWinCap)
   int32_t sub0;      // first sub-window of the group in the plan's sub-window list
+  int32_t prob;      // multi-problem launches: the group's problem (index into the WinProb list)
   int64_t w0;        // window start, samples from each block's start
   int64_t slot_off;  // first entry of the group's pixel-sorted slot table
   int64_t ent_off;   // first pixel-sorted entry of the group's sub-windows
+};
+
+// Per-problem pointers of the multi-problem window launches of a server step (every running
+// FP32 request's groups in one launch; group g belongs to problem groups[g].prob): its plan's
+// block offsets, slots, slot tables and reduced angles, the map x read by P, the un-pointed t it
+// writes, the u = N^-1 t read by P^T, the map y it accumulates into and the column's halt flag.
+struct WinProb {
+  const int64_t* block_off;
+  const uint16_t* slot;
+  const int32_t* slot_pix;
+  const float* ang2;
+  const float* x;    // [n_obs][4]
+  float* t;          // [N]
+  const float* u;    // [N]
+  float* y;          // [n_obs][4]
+  const int32_t* done;
 };
 
 // Pixel-sorted sub-windows (P^T by segment reduction).  Sub-window s of a group is the window
@@ -213,11 +230,12 @@ struct Plan {
   size_t t32_cap = 0;
   int32_t seg_halo = 0;                // largest L - vstep over the segments (samples)
 
-  // pixel windows of detector groups (FP32 operators); a server request's plan skips them (its FP32
-  // iterations run in the server's multi-problem tile launches, and a short plan build matters
-  // more for its latency than the faster windowed operators)
+  // pixel windows of detector groups (FP32 operators); skipped by FP64-class server requests, whose
+  // plans never run the FP32 operators
   bool no_windows = false;
+  bool no_big = false;                 // skip the 65536-sample tile tables (server requests)
   PGroup* groups = nullptr;            // [n_groups]
+  std::vector<PGroup> groups_host;     // host copy (multi-problem window launches)
   int64_t n_groups = 0;
   uint16_t* slot = nullptr;            // [N] pixel-sorted local index of each sample in its group
   int32_t* slot_pix = nullptr;         // [n_slots_total] compacted pixel of each slot
@@ -332,6 +350,9 @@ cudaError_t launch_ninv32_big(const TileArgs& a, cudaStream_t s);
 cudaError_t launch_tiles_fp32(int mode, const TileArgs& a, int halo_samples, cudaStream_t s);
 // FP32 A-application over the tiles of several plans at once (a.probs set, nrhs = 1)
 cudaError_t launch_tiles_fp32_multi(const TileArgs& a, int halo_samples, cudaStream_t s);
+// u = N^-1 t of several problems' segments in one launch (a.probs: x = t, y = u, tab, done of
+// each problem; nrhs 1)
+cudaError_t launch_ninv32_multi(const TileArgs& a, int halo_samples, cudaStream_t s);
 // t [nrhs][t_stride] float32 = P x for every sample (0 at masked samples), x float4 maps
 // [nrhs][n_obs]
 cudaError_t launch_unpoint32(const int32_t* lpix, const float2* w32, int64_t N, const float* x4,
@@ -373,6 +394,12 @@ cudaError_t launch_point_win32(const PGroup* groups, int64_t n_groups, const int
                                const uint16_t* slot, const int32_t* slot_pix, const float* psi,
                                const float* u, int64_t u_stride, int nrhs, const int32_t* done,
                                int done_stride, float* y4, int64_t y_stride, cudaStream_t s);
+// the same two operators for several problems in one launch (continuous batching): groups from
+// every problem's plan, each with its prob index into probs (one column per problem)
+cudaError_t launch_unpoint_win32_multi(const PGroup* groups, int64_t n_groups, const WinProb* probs,
+                                       cudaStream_t s);
+cudaError_t launch_point_win32_multi(const PGroup* groups, int64_t n_groups, const WinProb* probs,
+                                     cudaStream_t s);
 // multiprocessors of the current device (cached per device)
 int sm_count();
 // df64 tiles and their data preparation (k_df64.cu)
