@@ -424,7 +424,7 @@ int mm_deflation_apply(mm_plan_t plan, const double* r, double* z, int nrhs, voi
  * Serving: a request loop with continuous batching (an interface of this library; the paper has
  * none).  Requests wait in a queue and are admitted while fewer than max_slots are being planned or
  * run and the estimated device footprint of those stays within hbm_budget (a request is always
- * admitted when none is active).  Two planner threads build admitted requests' plans (pointing,
+ * admitted when none is active).  Four planner threads build admitted requests' plans (pointing,
  * bands, spectra, block-Jacobi blocks), right-hand sides and PCG state on their own CUDA streams;
  * a server thread with one stream runs the iterations, one PCG iteration of every running request
  * per step; requests join between steps once planned and leave when they finish.  Their state

@@ -1133,7 +1133,10 @@ int rhs32_internal(Plan* P, const void* d, int d_is_fp32, int nrhs, double* b4, 
   return MM_OK;
 }
 
-int ensure_cg(Plan* P, int nrhs, bool fp32, CgState** out) {
+// CG state for nrhs columns; its reduction counters are zeroed on stream s, the stream of the CG
+// kernels that first use them (a memset on the legacy default stream is not ordered before work
+// on the non-blocking streams of the server's planner threads)
+int ensure_cg(Plan* P, int nrhs, bool fp32, CgState** out, cudaStream_t s) {
   CgState* c = reinterpret_cast<CgState*>(P->cg);
   if (!c) {
     c = new CgState();
@@ -1154,7 +1157,7 @@ int ensure_cg(Plan* P, int nrhs, bool fp32, CgState** out) {
     MM_TRY(dalloc(P, &c->partials, (size_t)nrhs * 1024 * 4));
     MM_TRY(dalloc(P, &c->counters, nrhs));
     MM_TRY(dalloc(P, &c->scal, nrhs));
-    MM_CUDA(cudaMemset(c->counters, 0, nrhs * sizeof(unsigned)));
+    MM_CUDA(cudaMemsetAsync(c->counters, 0, nrhs * sizeof(unsigned), s));
     MM_CUDA(cudaMallocHost((void**)&c->scal_host, nrhs * sizeof(CgScalars)));
     c->nrhs_cap = nrhs;
     c->n = P->n_obs;
@@ -1198,7 +1201,7 @@ int enqueue_iteration(Plan* P, const CgWork& w, int nrhs, bool fp32, cudaStream_
 }
 
 // per-solve buffers of the deflated preconditioner for nrhs columns
-int ensure_defl_work(Plan* P, DeflState* d, int nrhs, int n_blocks, DeflWork* out) {
+int ensure_defl_work(Plan* P, DeflState* d, int nrhs, int n_blocks, DeflWork* out, cudaStream_t s) {
   if (d->nrhs_cap < nrhs) {
     P->buf_gen++;
     dfree(d->y); dfree(d->part); dfree(d->part2); dfree(d->counters); dfree(d->counters2);
@@ -1208,8 +1211,8 @@ int ensure_defl_work(Plan* P, DeflState* d, int nrhs, int n_blocks, DeflWork* ou
     MM_TRY(dalloc(P, &d->part2, (size_t)nrhs * 1024));
     MM_TRY(dalloc(P, &d->counters, nrhs));
     MM_TRY(dalloc(P, &d->counters2, nrhs));
-    MM_CUDA(cudaMemset(d->counters, 0, nrhs * sizeof(unsigned)));
-    MM_CUDA(cudaMemset(d->counters2, 0, nrhs * sizeof(unsigned)));
+    MM_CUDA(cudaMemsetAsync(d->counters, 0, nrhs * sizeof(unsigned), s));
+    MM_CUDA(cudaMemsetAsync(d->counters2, 0, nrhs * sizeof(unsigned), s));
     d->nrhs_cap = nrhs;
   }
   (void)n_blocks;
@@ -1454,7 +1457,7 @@ int start_request(Server* S, Request* r, cudaStream_t ps) {
   MM_CUDA(cudaMemcpyAsync(r->d_dev, r->d.data(), P->N * esz, cudaMemcpyHostToDevice, ps));
   st = mm_rhs(reinterpret_cast<mm_plan_t>(P), r->d_dev, r->d_is_fp32, 1, r->b_dev, ps);
   if (st != MM_OK) return st;
-  MM_TRY(ensure_cg(P, 1, r->fp32, &r->cg));
+  MM_TRY(ensure_cg(P, 1, r->fp32, &r->cg, ps));
   if (!r->fp32) MM_TRY(ensure_df(P, 1));
   r->w = make_work(P, r->cg, 1, r->fp32, r->opts.tol, r->opts.max_iter);
   MM_CUDA(cudaMallocHost((void**)&r->scal_host, sizeof(CgScalars)));
@@ -1685,32 +1688,36 @@ void server_loop(Server* S) {
       abort_running();
       continue;
     }
-    std::vector<Request*> still;
-    for (Request* r : S->running) {
+    // FP64-class work of this check, enqueued for every request that needs it before one wait:
+    // the residual replacement of FP32 requests, the true residual of finished FP64-class ones
+    std::vector<char> enq_ok(S->running.size(), 1);
+    bool any = false;
+    for (size_t k = 0; k < S->running.size(); k++) {
+      Request* r = S->running[k];
       const CgScalars sc = *r->scal_host;
       const int rel_every = r->opts.reliable_every > 0 ? r->opts.reliable_every : 50;
-      bool r_ok = true;   // this request's replacement or report ran and its scalars were read
-      if (r->fp32 && !sc.done && (sc.paused || sc.since_rep >= rel_every)) {   // FP64 residual replacement
-        Plan* P = r->plan;
-        r_ok = cudaMemsetAsync(r->cg->q, 0, P->n_obs * 4 * sizeof(double), s) == cudaSuccess &&
-               apply64_internal(P, r->cg->x, r->cg->q, 1, s,
-                                reinterpret_cast<const int32_t*>(r->cg->scal) + kDoneOffsetInts,
-                                kScalStrideInts) == MM_OK &&
-               launch_cg(CG_REPLACE, r->w, s) == cudaSuccess &&
-               cudaMemcpyAsync(r->scal_host, r->cg->scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, s) ==
-                   cudaSuccess &&
-               cudaStreamSynchronize(s) == cudaSuccess;
-      }
-      if (!r->fp32 && sc.done) {   // FP64-class request: the true residual for the report
-        Plan* P = r->plan;
-        r_ok = cudaMemsetAsync(r->cg->q, 0, P->n_obs * 4 * sizeof(double), s) == cudaSuccess &&
-               apply64_internal(P, r->cg->x, r->cg->q, 1, s) == MM_OK &&
-               launch_cg(CG_TRUE_RES, r->w, s) == cudaSuccess &&
-               cudaMemcpyAsync(r->scal_host, r->cg->scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, s) ==
-                   cudaSuccess &&
-               cudaStreamSynchronize(s) == cudaSuccess;
-      }
-      if (!r_ok) {
+      const bool replace = r->fp32 && !sc.done && (sc.paused || sc.since_rep >= rel_every);
+      const bool report = !r->fp32 && sc.done;
+      if (!replace && !report) continue;
+      Plan* P = r->plan;
+      any = true;
+      enq_ok[k] = cudaMemsetAsync(r->cg->q, 0, P->n_obs * 4 * sizeof(double), s) == cudaSuccess &&
+                  (replace ? apply64_internal(P, r->cg->x, r->cg->q, 1, s,
+                                              reinterpret_cast<const int32_t*>(r->cg->scal) + kDoneOffsetInts,
+                                              kScalStrideInts)
+                           : apply64_internal(P, r->cg->x, r->cg->q, 1, s)) == MM_OK &&
+                  launch_cg(replace ? CG_REPLACE : CG_TRUE_RES, r->w, s) == cudaSuccess &&
+                  cudaMemcpyAsync(r->scal_host, r->cg->scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, s) ==
+                      cudaSuccess;
+    }
+    if (any && cudaStreamSynchronize(s) != cudaSuccess) {
+      abort_running();
+      continue;
+    }
+    std::vector<Request*> still;
+    for (size_t k = 0; k < S->running.size(); k++) {
+      Request* r = S->running[k];
+      if (!enq_ok[k]) {
         cudaGetLastError();
         finish_request(S, r, MM_ECUDA);
         S->dirty = true;
@@ -1999,7 +2006,7 @@ static int pcg_solve_impl(Plan* P, const double* b, const TodSrc* tod, double* x
   cudaStream_t us = as_stream(stream);
   cudaStream_t s = P->stream;
   CgState* c = nullptr;
-  MM_TRY(ensure_cg(P, nrhs, fp32, &c));
+  MM_TRY(ensure_cg(P, nrhs, fp32, &c, s));
   CgWork w = make_work(P, c, nrhs, fp32, opts->tol, opts->max_iter);
   if (P->algo == MM_TPLZ_DIRECT) MM_TRY(ensure_td(P));
   if (fp32) MM_TRY(ensure_t32(P, nrhs));
@@ -2007,7 +2014,7 @@ static int pcg_solve_impl(Plan* P, const double* b, const TodSrc* tod, double* x
   DeflWork dw{};
   const DeflWork* dwp = nullptr;
   if (opts->precond == MM_PREC_2LVL_POST) {
-    MM_TRY(ensure_defl_work(P, dst, nrhs, w.n_blocks, &dw));
+    MM_TRY(ensure_defl_work(P, dst, nrhs, w.n_blocks, &dw, s));
     dwp = &dw;
   }
 
@@ -3115,10 +3122,10 @@ int mm_deflation_apply(mm_plan_t plan, const double* r, double* z, int nrhs, voi
   DeviceGuard g(P->device);
   cudaStream_t s = as_stream(stream);
   CgState* c = nullptr;
-  MM_TRY(ensure_cg(P, nrhs, false, &c));
+  MM_TRY(ensure_cg(P, nrhs, false, &c, s));
   CgWork w = make_work(P, c, nrhs, false, 1.0, 1);
   DeflWork dw{};
-  MM_TRY(ensure_defl_work(P, d, nrhs, w.n_blocks, &dw));
+  MM_TRY(ensure_defl_work(P, d, nrhs, w.n_blocks, &dw, s));
   MM_CUDA(launch_pack3to4(r, P->n_obs, nrhs, c->r, s));
   MM_CUDA(cudaMemsetAsync(c->scal, 0, nrhs * sizeof(CgScalars), s));   // halt = 0
   MM_CUDA(launch_defl_step(dw, w, s));
@@ -3145,7 +3152,7 @@ int mm_server_create(size_t hbm_budget, int max_slots, mm_server_t* out) {
     return cuda_fail(e, "cudaStreamCreate");
   }
   S->th = std::thread(server_loop, S);
-  constexpr int kPlanners = 2;
+  constexpr int kPlanners = 4;
   for (int i = 0; i < kPlanners; i++) S->planners.emplace_back(planner_loop, S);
   *out = reinterpret_cast<mm_server_t>(S);
   return MM_OK;

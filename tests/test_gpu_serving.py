@@ -123,3 +123,22 @@ def test_fp32_tod_and_fp64_class_requests_in_one_mix(probs):
         assert info.status == 0 and info.true_rel_res < TOL
         assert info.n_apply32 == 0 and info.n_apply64 >= info.iters   # FP64-class in every iteration
         assert np.linalg.norm(mp - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+def test_many_concurrent_requests(probs):
+    """Twenty-four requests submitted at once (16 slots, so up to 16 planned and iterated side by
+    side while four planner threads build the next ones on their own streams): every one finishes
+    with status 0 and the same map as the same request solved alone."""
+    m = mm()
+    srv = m.Server(max_slots=1)
+    alone = [srv.wait(submit(srv, p))[0] for p in probs]
+    srv.close()
+    srv = m.Server(max_slots=16)
+    order = [k % len(probs) for k in range(24)]
+    ids = [submit(srv, probs[k]) for k in order]
+    out = [srv.wait(i, raise_on_error=False) for i in ids]
+    srv.close()
+    assert max(info.batch for _, info in out) >= 8
+    for k, (mp, info) in zip(order, out):
+        assert info.status == 0 and info.true_rel_res < TOL
+        assert np.linalg.norm(mp - alone[k]) <= 1e-6 * np.linalg.norm(alone[k])
