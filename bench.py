@@ -1005,7 +1005,8 @@ def run_serving(a, n_requests=None, compare_fp64=0):
                     f"dets 8-256, samples/det 2^16-2^20, side 64-512, lambda 512-8192), tol 1e-6",
         "metric": "solves/s + p50/p99 latency (Poisson arrivals)", "value": n_requests / dt,
         "unit": "solves/s", "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-        "offered_per_s": a.rate, "total_samples": samples,
+        "offered_per_s": a.rate, "offered_realised_per_s": n_requests / float(np.sum(gaps)),
+        "total_samples": samples,
         "status": sorted(set(i.status for i in infos)), "max_batch": max(i.batch for i in infos),
         "iters_mean": float(np.mean([i.iters for i in infos])),
         "arrivals": "absolute Poisson schedule", "submit_ms_mean": sub[0], "submit_ms_max": sub[1],

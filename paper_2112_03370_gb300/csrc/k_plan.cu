@@ -41,8 +41,9 @@ __device__ __forceinline__ int block_of(const int64_t* __restrict__ off, int32_t
 // Each CTA takes a contiguous chunk of the samples and its warps stride through it, lane l of a
 // warp on sample base + l, so a lane's block index is found once and only moves forward; the
 // weights are the plan's FP64 (cos 2psi, sin 2psi).  Consecutive samples of a slow scan often
-// fall on the same pixel: the lanes of each run of equal pixels are summed by a segmented scan
-// across the warp, and the run's last lane adds the sums with one set of atomics.
+// fall on the same pixel: in a warp that holds such a run, the lanes of each run of equal pixels
+// are summed by a segmented scan across the warp and the run's last lane adds the sums with one
+// set of atomics.
 __global__ void k_bd_accum(const int32_t* __restrict__ pix, const double2* __restrict__ w64,
                            const int64_t* __restrict__ off, const double* __restrict__ c0_blk,
                            int32_t n_blocks, int64_t N, double* __restrict__ B6,
@@ -72,8 +73,19 @@ __global__ void k_bd_accum(const int32_t* __restrict__ pix, const double2* __res
         v[5] = c0 * sn * sn;
       }
     }
-    // first lane of this lane's run of equal pixels (a max-scan of the run heads)
     const int32_t p_prev = __shfl_up_sync(0xffffffffu, p, 1);
+    // FP64 arithmetic runs at 1/64 of the FP32 rate on GB300: the segmented scan runs only in
+    // warps that hold a run of equal pixels; elsewhere every lane adds its own sample
+    if (!__any_sync(0xffffffffu, lane > 0 && p >= 0 && p == p_prev)) {
+      if (p >= 0) {
+        double* b = B6 + 6 * (int64_t)p;
+#pragma unroll
+        for (int k = 0; k < 6; k++) atomicAdd(b + k, v[k]);
+        atomicAdd(hits + p, 1);
+      }
+      continue;
+    }
+    // first lane of this lane's run of equal pixels (a max-scan of the run heads)
     int head = (lane == 0 || p_prev != p) ? lane : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
