@@ -308,6 +308,69 @@ cudaError_t launch_localize(const int32_t* pix, const int32_t* keep, const int32
 // One FP64 sincos of 2 psi per sample: the FP64 weights, their FP32 roundings, (wdf non-null) their
 // df64 split, and the angle 2 psi reduced to [-pi, pi] in FP64 and rounded once to FP32 (the FP32
 // window kernels evaluate the weights from it in registers).
+// cos(k pi/32), sin(k pi/32), k = 0 .. 63 (values of the circular functions rounded to FP64)
+__device__ const double2 kSinCosPi32[64] = {
+    {1.0, 0.0}, {0.9951847266721969, 0.0980171403295606},
+    {0.9807852804032304, 0.19509032201612828}, {0.9569403357322088, 0.2902846772544624},
+    {0.9238795325112867, 0.3826834323650898}, {0.881921264348355, 0.47139673682599764},
+    {0.8314696123025452, 0.5555702330196022}, {0.773010453362737, 0.6343932841636455},
+    {0.7071067811865476, 0.7071067811865476}, {0.6343932841636455, 0.773010453362737},
+    {0.5555702330196022, 0.8314696123025452}, {0.47139673682599764, 0.881921264348355},
+    {0.3826834323650898, 0.9238795325112867}, {0.2902846772544624, 0.9569403357322088},
+    {0.19509032201612828, 0.9807852804032304}, {0.0980171403295606, 0.9951847266721969},
+    {0.0, 1.0}, {-0.0980171403295606, 0.9951847266721969},
+    {-0.19509032201612828, 0.9807852804032304}, {-0.2902846772544624, 0.9569403357322088},
+    {-0.3826834323650898, 0.9238795325112867}, {-0.47139673682599764, 0.881921264348355},
+    {-0.5555702330196022, 0.8314696123025452}, {-0.6343932841636455, 0.773010453362737},
+    {-0.7071067811865476, 0.7071067811865476}, {-0.773010453362737, 0.6343932841636455},
+    {-0.8314696123025452, 0.5555702330196022}, {-0.881921264348355, 0.47139673682599764},
+    {-0.9238795325112867, 0.3826834323650898}, {-0.9569403357322088, 0.2902846772544624},
+    {-0.9807852804032304, 0.19509032201612828}, {-0.9951847266721969, 0.0980171403295606},
+    {-1.0, 0.0}, {-0.9951847266721969, -0.0980171403295606},
+    {-0.9807852804032304, -0.19509032201612828}, {-0.9569403357322088, -0.2902846772544624},
+    {-0.9238795325112867, -0.3826834323650898}, {-0.881921264348355, -0.47139673682599764},
+    {-0.8314696123025452, -0.5555702330196022}, {-0.773010453362737, -0.6343932841636455},
+    {-0.7071067811865476, -0.7071067811865476}, {-0.6343932841636455, -0.773010453362737},
+    {-0.5555702330196022, -0.8314696123025452}, {-0.47139673682599764, -0.881921264348355},
+    {-0.3826834323650898, -0.9238795325112867}, {-0.2902846772544624, -0.9569403357322088},
+    {-0.19509032201612828, -0.9807852804032304}, {-0.0980171403295606, -0.9951847266721969},
+    {0.0, -1.0}, {0.0980171403295606, -0.9951847266721969},
+    {0.19509032201612828, -0.9807852804032304}, {0.2902846772544624, -0.9569403357322088},
+    {0.3826834323650898, -0.9238795325112867}, {0.47139673682599764, -0.881921264348355},
+    {0.5555702330196022, -0.8314696123025452}, {0.6343932841636455, -0.773010453362737},
+    {0.7071067811865476, -0.7071067811865476}, {0.773010453362737, -0.6343932841636455},
+    {0.8314696123025452, -0.5555702330196022}, {0.881921264348355, -0.47139673682599764},
+    {0.9238795325112867, -0.3826834323650898}, {0.9569403357322088, -0.2902846772544624},
+    {0.9807852804032304, -0.19509032201612828}, {0.9951847266721969, -0.0980171403295606}};
+
+// (cos x, sin x) in FP64 by table lookup and angle addition (the table-driven method of
+// P. T. P. Tang, ACM TOMS 1989-91): x = k pi/32 + r with k = rint(32 x / pi) and r = x - k pi/32
+// by a two-constant Cody-Waite reduction (pi/32 = H + L, H = fl64(pi/32): k H is taken exactly
+// inside one FMA, k L has an error far below 1e-30 for |k| < 2^40); |r| <= pi/64, where the Taylor
+// series of sin r to r^9 and of cos r to r^8 leave truncation errors below 1e-19; then
+//   cos x = C_k cos r - S_k sin r,  sin x = S_k cos r + C_k sin r,  (C_k, S_k) = table[k mod 64].
+// About 20 FP64 operations instead of a general sincos (on GB300 FP64 runs at 1/64 of the FP32
+// rate, and the plan spends most of this kernel's time there).
+__device__ __forceinline__ void sincos_tab(double x, double& sn, double& cs) {
+  if (!(fabs(x) < 1e9)) {   // far outside any angle a scan produces: the general routine
+    sincos(x, &sn, &cs);
+    return;
+  }
+  constexpr double kH = 0.09817477042468103;       // fl64(pi / 32)
+  constexpr double kL = 3.827021247335479e-18;     // pi / 32 - kH
+  constexpr double k32OverPi = 10.185916357881302;  // 32 / pi
+  const double kd = rint(x * k32OverPi);
+  double r = fma(-kd, kH, x);
+  r = fma(-kd, kL, r);
+  const double z = r * r;
+  const double sr = r * fma(z, fma(z, fma(z, fma(z, 1.0 / 362880.0, -1.0 / 5040.0), 1.0 / 120.0), -1.0 / 6.0), 1.0);
+  const double cr =
+      fma(z, fma(z, fma(z, fma(z, 1.0 / 40320.0, -1.0 / 720.0), 1.0 / 24.0), -0.5), 1.0);
+  const double2 t = kSinCosPi32[(int)((long long)kd & 63)];
+  cs = fma(t.x, cr, -t.y * sr);
+  sn = fma(t.y, cr, t.x * sr);
+}
+
 __global__ void k_weights(const float* __restrict__ psi, int64_t N, double2* __restrict__ w64,
                           float2* __restrict__ w32, float4* __restrict__ wdf, float* __restrict__ ang2) {
   constexpr double kTwoPi = 6.283185307179586476925;
@@ -315,7 +378,7 @@ __global__ void k_weights(const float* __restrict__ psi, int64_t N, double2* __r
        i += (int64_t)gridDim.x * blockDim.x) {
     const double a = 2.0 * (double)psi[i];
     double s, c;
-    sincos(a, &s, &c);
+    sincos_tab(a, s, c);
     w64[i] = make_double2(c, s);
     w32[i] = make_float2((float)c, (float)s);
     if (wdf) {
